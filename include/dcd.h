@@ -1,0 +1,167 @@
+/*
+ * dcd.h -- C ABI of the GB300 (sm_103a) library for incremental dynamic
+ * community detection with Delta-screening (Zarayeneh & Kalyanaraman,
+ * "A Fast and Efficient Incremental Approach toward Dynamic Community
+ * Detection", arXiv 1904.08553).
+ *
+ * The calls follow the problem statement of Sec. III-B (detect C_t for every
+ * G_t of a dynamic graph) and the incremental approach of Sec. III-D:
+ *
+ *   dcd_create(n)                      a dynamic graph on the vertex set [0, n)
+ *   dcd_apply_batch(inserts, deletes)  stage the changes Delta_t of one step
+ *   dcd_update()                       G_t <- G_{t-1} + Delta_t, then C_t and Q_t
+ *
+ * Conventions shared by every call:
+ *   - Return value: DCD_OK (0) on success, a negative DCD_E* code otherwise.
+ *     A call that fails leaves the context exactly as it was.
+ *   - Vertex ids are int32 in [0, n); n <= 2^31 - 1.  Graphs are undirected:
+ *     an edge (u, v) and (v, u) are the same edge.  Self-loops are rejected.
+ *   - Weights are positive int32 (Sec. III-A allows any non-negative weight;
+ *     integer weights keep every decision exact).  Repeated inserts of an
+ *     edge add their weights (multiplicity).
+ *   - Pointers marked "host" are ordinary CPU memory; pointers marked
+ *     "device" are CUDA device memory of the context's device; "host or
+ *     device" pointers are told apart with cudaPointerGetAttributes.
+ *     The library never takes ownership of caller memory.
+ *   - All device work runs on the CUDA stream given to dcd_create (NULL =
+ *     the legacy default stream); every call returns with that work complete
+ *     unless the call says otherwise.
+ *   - Not thread-safe per context: one context, one host thread at a time.
+ */
+#ifndef DCD_H
+#define DCD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define DCD_OK 0
+#define DCD_EINVAL (-1)    /* bad argument: id out of range, u == v, w <= 0, n out of range */
+#define DCD_ENOMEM (-2)    /* device or host allocation failed                              */
+#define DCD_ECUDA (-3)     /* a CUDA runtime call failed (see dcd_last_cuda_error)          */
+#define DCD_ESTATE (-4)    /* call not valid in the current state                           */
+#define DCD_EOVERFLOW (-5) /* an edge weight above INT32_MAX, or 2m >= 2^62                  */
+#define DCD_ETIMEOUT (-6)  /* a bounded device-side wait gave up                            */
+
+/* ---- modes (Sec. III-C, III-D) ---- */
+#define DCD_MODE_STATIC 0  /* Static(G_t) from singletons every step (the naive approach)   */
+#define DCD_MODE_BASE 1    /* dLouvain-base: inherit C_{t-1}, R_t = V_t                     */
+#define DCD_MODE_DELTA 2   /* dLouvain-Delta-s: inherit C_{t-1}, R_t = Delta-screening      */
+#define DCD_MODE_GIVEN_R 3 /* inherit C_{t-1}, R_t supplied by dcd_set_rset (learned screen)*/
+
+typedef struct {
+  int32_t u, v; /* endpoints, u != v                               */
+  int32_t w;    /* weight > 0 for inserts; ignored for deletes     */
+} dcd_edge;
+
+typedef struct {
+  int32_t mode;       /* DCD_MODE_*; default DCD_MODE_DELTA                          */
+  int32_t max_iters;  /* local-move passes per level; default 500 (tau reading)       */
+  int32_t max_levels; /* default 64                                                   */
+  int32_t tau_inv;    /* a pass (level) gaining at most |N| / tau_inv stops it; 1e6  */
+  int32_t reserved[12];
+} dcd_config;
+
+typedef struct {
+  int64_t t;             /* time step just computed, 1-based                        */
+  int64_t n;             /* |V_t|                                                   */
+  int64_t nnz;           /* directed CSR entries of G_t (2 per undirected edge)      */
+  int64_t m2;            /* 2 m_t = sum of weighted degrees                         */
+  int64_t r_size;        /* |R_t|: vertices evaluated at level 0                    */
+  int64_t levels;        /* levels run                                              */
+  int64_t iters_total;   /* local-move passes, all levels                           */
+  int64_t iters_level0;  /* local-move passes at level 0                            */
+  int64_t moves_total;   /* single-vertex moves applied                             */
+  int64_t edges_scanned; /* sum over passes of the active vertices' degrees          */
+  int64_t communities;   /* |C_t|                                                   */
+  int64_t n_lo, n_hi;    /* N = m2^2 Q as a two's-complement 128-bit integer         */
+  double q;              /* modularity Q_t (Eq. 1), from N and m2 in FP64            */
+  int64_t ins_records;   /* staged inserts in Delta_t                               */
+  int64_t del_records;   /* staged deletes in Delta_t                               */
+  float ms_total;        /* device time of the whole update (CUDA events)           */
+  float ms_merge;        /* batch sort + CSR merge + degrees                        */
+  float ms_screen;       /* Delta-screening + R_t build                             */
+  float ms_local_move;   /* local-move kernels only (all levels)                    */
+  float ms_apply;        /* move apply + modularity tracking                        */
+  float ms_coarsen;      /* graph compaction (all levels)                           */
+  float ms_finish;       /* label composition, canonical labels                     */
+  float reserved_f[9];
+} dcd_step_stats;
+
+typedef struct dcd_ctx dcd_ctx;
+
+/* Default configuration (see the fields). */
+void dcd_config_default(dcd_config* cfg);
+
+/* Create a dynamic graph on vertices [0, n) with no edges (Sec. III-A:
+ * G(V, E) as a sequence G_1..G_T).  cfg may be NULL (defaults);
+ * cuda_stream is a cudaStream_t or NULL.  *out receives the context.
+ * Errors: DCD_EINVAL (n <= 0 or n > 2^31 - 1, out NULL), DCD_ENOMEM, DCD_ECUDA. */
+int dcd_create(int64_t n, const dcd_config* cfg, void* cuda_stream, dcd_ctx** out);
+
+/* Release every resource of the context.  NULL is accepted. */
+int dcd_destroy(dcd_ctx* ctx);
+
+/* Stage one batch of Delta_t (Sec. III-A; Sec. III-E stores each change as
+ * the ordered pairs (i,j) and (j,i) -- the library does that itself).
+ * ins: n_ins host dcd_edge (u, v, w > 0); del: n_del host dcd_edge (u, v).
+ * Deletes of the step act before its inserts; deleting an absent edge is a
+ * no-op.  Several calls before one dcd_update concatenate.  The arrays are
+ * validated whole before anything is staged and copied to the device; the
+ * caller keeps ownership.  Errors: DCD_EINVAL (any bad record: nothing is
+ * staged), DCD_ENOMEM, DCD_ECUDA. */
+int dcd_apply_batch(dcd_ctx* ctx, const dcd_edge* ins, int64_t n_ins, const dcd_edge* del,
+                    int64_t n_del);
+
+/* As dcd_apply_batch with device arrays.  The records are copied
+ * device-to-device on the context stream; validation happens on the device
+ * inside the next dcd_update, which fails with DCD_EINVAL (state unchanged,
+ * staged batch dropped) if any record is bad. */
+int dcd_apply_batch_device(dcd_ctx* ctx, const dcd_edge* d_ins, int64_t n_ins,
+                           const dcd_edge* d_del, int64_t n_del);
+
+/* Advance one time step (Sec. III-D): merge the staged batch into G_t, pick
+ * R_t by the context mode (Algorithm 2 in DCD_MODE_DELTA), run the
+ * multi-level local-move / compaction loop of Algorithm 1 with R_t at level 0,
+ * and produce C_t with canonical labels (each community is named by its
+ * smallest member id) and Q_t (Eq. 1).  The first update of a context is
+ * static (step 1).  With nothing staged the step is valid and empty.
+ * labels_out: n int32, host or device, may be NULL.  q_out, stats: host, may
+ * be NULL.  Errors: DCD_EINVAL (bad device batch), DCD_EOVERFLOW, DCD_ENOMEM,
+ * DCD_ECUDA; on error G and C are those of the previous step. */
+int dcd_update(dcd_ctx* ctx, int32_t* labels_out, double* q_out, dcd_step_stats* stats);
+
+/* Current labels C_t (n int32, host or device). */
+int dcd_get_labels(dcd_ctx* ctx, int32_t* labels_out);
+
+/* R_t of the last update: n bytes (host or device), 1 = evaluated at level 0. */
+int dcd_get_rset(dcd_ctx* ctx, uint8_t* r_out);
+
+/* Replace C_{t-1} (n int32 in [0, n), host).  A context that has not been
+ * updated yet then counts as past step 1, so its next update inherits these
+ * labels instead of running statically.  Errors: DCD_EINVAL. */
+int dcd_set_labels(dcd_ctx* ctx, const int32_t* labels);
+
+/* Supply R_t for the next update in DCD_MODE_GIVEN_R: n bytes, host. */
+int dcd_set_rset(dcd_ctx* ctx, const uint8_t* r);
+
+/* Change the mode for the following updates (DCD_MODE_*). */
+int dcd_set_mode(dcd_ctx* ctx, int32_t mode);
+
+/* The CSR of G_t: *nnz_out receives the entry count; when row_ptr/col/w are
+ * non-NULL they receive n+1 int64, nnz int32 and nnz int32 (host memory). */
+int dcd_get_graph(dcd_ctx* ctx, int64_t* nnz_out, int64_t* row_ptr, int32_t* col, int32_t* w);
+
+/* Text of a status code (static storage). */
+const char* dcd_strerror(int code);
+
+/* Text of the last CUDA error seen by this thread (static storage). */
+const char* dcd_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

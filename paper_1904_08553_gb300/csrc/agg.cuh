@@ -1,0 +1,127 @@
+// agg.cuh -- neighbour-community aggregation shared by the local-move and
+// screening kernels: exact group sums inside a warp, open-addressing tables
+// (community label -> summed edge weight) in shared or global memory, the
+// exact integer gain S and a total-order argmax.
+#pragma once
+
+#include <climits>
+
+#include "common.cuh"
+
+namespace dcd {
+
+// Gain of moving v from C to D (Sec. III-A; expanded form in the appendix
+// proof of Lemma 3.2):  S = m2 (e_{v->D} - e_{v->C\v}) - k_v (a_D - (a_C - k_v)),
+// i.e. (2m)^2 times the paper's Delta Q_{v->D}.  ST = int64 is exact when
+// m2 < 2^31 (both products stay below 2^62); otherwise ST = int128.
+template <typename ST>
+__device__ __forceinline__ ST gain(int64_t m2, int64_t kv, int64_t eD, int64_t eC, int64_t aD, int64_t aC) {
+  return (ST)m2 * (ST)(eD - eC) - (ST)kv * (ST)(aD - aC + kv);
+}
+
+template <typename ST>
+__device__ __forceinline__ ST gain_lowest();
+template <>
+__device__ __forceinline__ long long gain_lowest<long long>() {
+  return LLONG_MIN;
+}
+template <>
+__device__ __forceinline__ i128 gain_lowest<i128>() {
+  return -((i128)1 << 126) * 2;
+}
+
+__device__ __forceinline__ long long shfl_xor_st(long long x, int o) { return __shfl_xor_sync(0xffffffffu, x, o); }
+__device__ __forceinline__ i128 shfl_xor_st(i128 x, int o) {
+  unsigned long long lo = (unsigned long long)x, hi = (unsigned long long)(x >> 64);
+  lo = __shfl_xor_sync(0xffffffffu, lo, o);
+  hi = __shfl_xor_sync(0xffffffffu, hi, o);
+  return (i128)(((unsigned __int128)hi << 64) | lo);
+}
+__device__ __forceinline__ long long shfl_st(long long x, int src) { return __shfl_sync(0xffffffffu, x, src); }
+__device__ __forceinline__ i128 shfl_st(i128 x, int src) {
+  unsigned long long lo = (unsigned long long)x, hi = (unsigned long long)(x >> 64);
+  lo = __shfl_sync(0xffffffffu, lo, src);
+  hi = __shfl_sync(0xffffffffu, hi, src);
+  return (i128)(((unsigned __int128)hi << 64) | lo);
+}
+
+// (S, D) order of the greedy choice: larger gain first, then smaller label.
+template <typename ST>
+__device__ __forceinline__ bool better(ST s1, int32_t d1, ST s2, int32_t d2) {
+  return s1 > s2 || (s1 == s2 && d1 < d2);
+}
+
+// Whole-warp argmax of (S, D); every lane ends with the result.
+template <typename ST>
+__device__ __forceinline__ void warp_argmax(ST& S, int32_t& D) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ST s2 = shfl_xor_st(S, o);
+    int32_t d2 = __shfl_xor_sync(0xffffffffu, D, o);
+    if (better(s2, d2, S, D)) {
+      S = s2;
+      D = d2;
+    }
+  }
+}
+
+// Exact sum of non-negative weights over the lanes of `peers` (a match_any
+// group), from 16-bit slices reduced with redux.sync: no slice sum can carry
+// out of 32 bits, so the result is exact for any int32/int64 weight.
+__device__ __forceinline__ int64_t group_sum_exact(unsigned peers, int32_t w) {
+  unsigned lo = (unsigned)w & 0xffffu, hi = (unsigned)w >> 16;
+  unsigned slo = __reduce_add_sync(peers, lo);
+  unsigned shi = __reduce_add_sync(peers, hi);
+  return (int64_t)slo + ((int64_t)shi << 16);
+}
+__device__ __forceinline__ int64_t group_sum_exact(unsigned peers, int64_t w) {
+  unsigned long long x = (unsigned long long)w;
+  int64_t s = 0;
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    unsigned part = (unsigned)(x >> (16 * q)) & 0xffffu;
+    s += (int64_t)__reduce_add_sync(peers, part) << (16 * q);
+  }
+  return s;
+}
+
+// ---- open-addressing table: key -1 = empty; capacity a power of two that is
+// at least twice the number of distinct keys, so probing always ends. ----
+__device__ __forceinline__ void tbl_add(int32_t* keys, unsigned long long* vals, uint32_t mask, int32_t lab,
+                                        unsigned long long x) {
+  uint32_t s = hash_label(lab, mask);
+  for (;;) {
+    int32_t k = keys[s];
+    if (k == lab) {
+      atomicAdd(&vals[s], x);
+      return;
+    }
+    if (k == -1) {
+      int32_t old = atomicCAS(&keys[s], -1, lab);
+      if (old == -1 || old == lab) {
+        atomicAdd(&vals[s], x);
+        return;
+      }
+    }
+    s = (s + 1) & mask;
+  }
+}
+
+__device__ __forceinline__ int64_t tbl_get(const int32_t* keys, const unsigned long long* vals, uint32_t mask,
+                                           int32_t lab) {
+  uint32_t s = hash_label(lab, mask);
+  for (;;) {
+    int32_t k = keys[s];
+    if (k == lab) return (int64_t)vals[s];
+    if (k == -1) return 0;
+    s = (s + 1) & mask;
+  }
+}
+
+__host__ __device__ __forceinline__ uint32_t table_cap(int64_t deg) {
+  uint32_t c = 64;
+  while ((int64_t)c < 2 * deg) c <<= 1;
+  return c;
+}
+
+}  // namespace dcd

@@ -1,0 +1,414 @@
+// api.cu -- the extern "C" entry points of dcd.h and the per-step driver
+// (Sec. III-D: G_t <- G_{t-1} + Delta_t; R_t; multi-level run; C_t, Q_t).
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "prims.cuh"
+#include "state.cuh"
+
+namespace dcd {
+
+namespace {
+thread_local char g_last_cuda[512] = "no CUDA error";
+int g_sms_cache = 0;
+
+__global__ void iota_kernel(int32_t* x, int64_t n) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    x[v] = (int32_t)v;
+}
+
+// Grow a staging buffer while keeping its first `keep` elements.
+template <typename T>
+int grow_keep(DevMem* mem, Buf<T>& b, size_t need, size_t keep, cudaStream_t s) {
+  if (b.p && b.n >= need) return DCD_OK;
+  Buf<T> nb;
+  DCD_TRY(nb.alloc(mem, need + need / 2 + 1024));
+  if (keep && b.p) DCD_TRY_CUDA(cudaMemcpyAsync(nb.p, b.p, keep * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  b.reset();
+  b.p = nb.p;
+  b.n = nb.n;
+  b.mem = mem;
+  nb.p = nullptr;
+  nb.n = 0;
+  return DCD_OK;
+}
+
+bool host_records_ok(const dcd_edge* e, int64_t m, int64_t n, bool is_insert) {
+  for (int64_t i = 0; i < m; i++) {
+    const dcd_edge x = e[i];
+    if (x.u < 0 || x.v < 0 || x.u >= n || x.v >= n || x.u == x.v) return false;
+    if (is_insert && x.w <= 0) return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+void note_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  snprintf(g_last_cuda, sizeof(g_last_cuda), "%s: %s (%s:%d)", cudaGetErrorString(e), what, file, line);
+}
+
+int num_sms() {
+  if (!g_sms_cache) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms_cache, cudaDevAttrMultiProcessorCount, dev);
+    if (g_sms_cache <= 0) g_sms_cache = 1;
+  }
+  return g_sms_cache;
+}
+
+int grid_for(int64_t items, int threads, int per_sm) {
+  int64_t b = cdiv(items > 0 ? items : 1, threads);
+  int64_t cap = (int64_t)num_sms() * per_sm;
+  if (b > cap) b = cap;
+  return (int)(b < 1 ? 1 : b);
+}
+
+int DevMem::alloc(void** p, size_t bytes) {
+  cudaError_t e = pool ? cudaMallocFromPoolAsync(p, bytes, pool, stream) : cudaMallocAsync(p, bytes, stream);
+  if (e != cudaSuccess) {
+    note_cuda_error(e, "cudaMallocAsync", __FILE__, __LINE__);
+    cudaGetLastError();
+    *p = nullptr;
+    return DCD_ENOMEM;
+  }
+  return DCD_OK;
+}
+
+void DevMem::release(void* p) {
+  if (p) cudaFreeAsync(p, stream);
+}
+
+namespace {
+__global__ void count_bytes(const uint8_t* r, int64_t n, unsigned long long* out) {
+  unsigned long long c = 0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    c += r[v] != 0;
+  c = warp_sum(c);
+  if (lane_id() == 0 && c) atomicAdd(out, c);
+}
+}  // namespace
+
+}  // namespace dcd
+
+using namespace dcd;
+
+#define DCD_SCOPE(c) DCD_TRY_CUDA(cudaSetDevice((c)->device))
+
+extern "C" {
+
+void dcd_config_default(dcd_config* cfg) {
+  if (!cfg) return;
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->mode = DCD_MODE_DELTA;
+  cfg->max_iters = 500;
+  cfg->max_levels = 64;
+  cfg->tau_inv = 1000000;
+}
+
+const char* dcd_strerror(int code) {
+  switch (code) {
+    case DCD_OK: return "ok";
+    case DCD_EINVAL: return "invalid argument";
+    case DCD_ENOMEM: return "out of memory";
+    case DCD_ECUDA: return "CUDA error";
+    case DCD_ESTATE: return "invalid state";
+    case DCD_EOVERFLOW: return "integer overflow (weight above INT32_MAX or 2m >= 2^62)";
+    case DCD_ETIMEOUT: return "device wait timed out";
+    default: return "unknown error";
+  }
+}
+
+const char* dcd_last_cuda_error(void) { return dcd::g_last_cuda; }
+
+int dcd_create(int64_t n, const dcd_config* cfg, void* cuda_stream, dcd_ctx** out) {
+  if (!out || n <= 0 || n > INT32_MAX) return DCD_EINVAL;
+  *out = nullptr;
+  dcd_config cf;
+  dcd_config_default(&cf);
+  if (cfg) cf = *cfg;
+  if (cf.mode < DCD_MODE_STATIC || cf.mode > DCD_MODE_GIVEN_R || cf.max_iters <= 0 || cf.max_levels <= 0 ||
+      cf.tau_inv <= 0)
+    return DCD_EINVAL;
+  dcd_ctx* c = new (std::nothrow) dcd_ctx();
+  if (!c) return DCD_ENOMEM;
+  c->n = n;
+  c->cfg = cf;
+  c->mode = cf.mode;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->mem.stream = c->stream;
+  int rc = DCD_OK;
+  do {
+    if (cudaGetDevice(&c->device) != cudaSuccess) { rc = DCD_ECUDA; break; }
+    c->sms = num_sms();
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = c->device;
+    if (cudaMemPoolCreate(&c->mem.pool, &props) != cudaSuccess) { rc = DCD_ECUDA; break; }
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(c->mem.pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    if (cudaMallocHost(&c->hsc, sizeof(DevScalars)) != cudaSuccess) { rc = DCD_ENOMEM; break; }
+    if (cudaMallocHost(&c->hscratch, 64 * sizeof(int64_t)) != cudaSuccess) { rc = DCD_ENOMEM; break; }
+    for (auto& e : c->ev)
+      if (cudaEventCreate(&e) != cudaSuccess) { rc = DCD_ECUDA; break; }
+    if (rc) break;
+    if ((rc = c->dsc.alloc(&c->mem, 1))) break;
+    if ((rc = c->labels.alloc(&c->mem, n))) break;
+    if ((rc = c->iota.alloc(&c->mem, n))) break;
+    if ((rc = c->rset.alloc(&c->mem, n))) break;
+    if ((rc = c->rp[0].alloc(&c->mem, n + 1))) break;
+    if ((rc = c->col[0].alloc(&c->mem, 1))) break;
+    if ((rc = c->w[0].alloc(&c->mem, 1))) break;
+    iota_kernel<<<grid_for(n, 256), 256, 0, c->stream>>>(c->iota.get(), n);
+    if (cudaMemcpyAsync(c->labels.get(), c->iota.get(), n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream) !=
+        cudaSuccess) { rc = DCD_ECUDA; break; }
+    if (cudaMemsetAsync(c->rp[0].get(), 0, (n + 1) * sizeof(int64_t), c->stream) != cudaSuccess) { rc = DCD_ECUDA; break; }
+    if (cudaMemsetAsync(c->rset.get(), 0, n, c->stream) != cudaSuccess) { rc = DCD_ECUDA; break; }
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) { note_cuda_error(e, "dcd_create", __FILE__, __LINE__); rc = DCD_ECUDA; break; }
+  } while (0);
+  if (rc) {
+    dcd_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return DCD_OK;
+}
+
+int dcd_destroy(dcd_ctx* c) {
+  if (!c) return DCD_OK;
+  cudaSetDevice(c->device);
+  {
+    cudaStreamSynchronize(c->stream);
+    c->rp[0].reset(); c->rp[1].reset();
+    c->col[0].reset(); c->col[1].reset();
+    c->w[0].reset(); c->w[1].reset();
+    c->labels.reset(); c->labels_nx.reset(); c->rset.reset(); c->rgiven.reset();
+    c->ins.reset(); c->del.reset(); c->dsc.reset(); c->iota.reset();
+    cudaStreamSynchronize(c->stream);
+  }
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  if (c->hsc) cudaFreeHost(c->hsc);
+  if (c->hscratch) cudaFreeHost(c->hscratch);
+  if (c->mem.pool) cudaMemPoolDestroy(c->mem.pool);
+  delete c;
+  return DCD_OK;
+}
+
+int dcd_apply_batch(dcd_ctx* c, const dcd_edge* ins, int64_t n_ins, const dcd_edge* del, int64_t n_del) {
+  if (!c || n_ins < 0 || n_del < 0 || (n_ins && !ins) || (n_del && !del)) return DCD_EINVAL;
+  if (n_ins && !host_records_ok(ins, n_ins, c->n, true)) return DCD_EINVAL;
+  if (n_del && !host_records_ok(del, n_del, c->n, false)) return DCD_EINVAL;
+  if ((c->n_ins + n_ins + c->n_del + n_del) * 2 >= (int64_t)INT32_MAX) return DCD_EINVAL;
+  DCD_SCOPE(c);
+  DCD_TRY(grow_keep(&c->mem, c->ins, c->n_ins + n_ins, c->n_ins, c->stream));
+  DCD_TRY(grow_keep(&c->mem, c->del, c->n_del + n_del, c->n_del, c->stream));
+  if (n_ins)
+    DCD_TRY_CUDA(cudaMemcpyAsync(c->ins.get() + c->n_ins, ins, n_ins * sizeof(dcd_edge), cudaMemcpyHostToDevice,
+                                 c->stream));
+  if (n_del)
+    DCD_TRY_CUDA(cudaMemcpyAsync(c->del.get() + c->n_del, del, n_del * sizeof(dcd_edge), cudaMemcpyHostToDevice,
+                                 c->stream));
+  DCD_TRY_CUDA(cudaStreamSynchronize(c->stream));
+  c->n_ins += n_ins;
+  c->n_del += n_del;
+  return DCD_OK;
+}
+
+int dcd_apply_batch_device(dcd_ctx* c, const dcd_edge* ins, int64_t n_ins, const dcd_edge* del, int64_t n_del) {
+  if (!c || n_ins < 0 || n_del < 0 || (n_ins && !ins) || (n_del && !del)) return DCD_EINVAL;
+  if ((c->n_ins + n_ins + c->n_del + n_del) * 2 >= (int64_t)INT32_MAX) return DCD_EINVAL;
+  DCD_SCOPE(c);
+  DCD_TRY(grow_keep(&c->mem, c->ins, c->n_ins + n_ins, c->n_ins, c->stream));
+  DCD_TRY(grow_keep(&c->mem, c->del, c->n_del + n_del, c->n_del, c->stream));
+  if (n_ins)
+    DCD_TRY_CUDA(cudaMemcpyAsync(c->ins.get() + c->n_ins, ins, n_ins * sizeof(dcd_edge), cudaMemcpyDeviceToDevice,
+                                 c->stream));
+  if (n_del)
+    DCD_TRY_CUDA(cudaMemcpyAsync(c->del.get() + c->n_del, del, n_del * sizeof(dcd_edge), cudaMemcpyDeviceToDevice,
+                                 c->stream));
+  c->n_ins += n_ins;
+  c->n_del += n_del;
+  if (n_ins + n_del) c->staged_on_device = true;
+  return DCD_OK;
+}
+
+static int update_impl(dcd_ctx* c, dcd_step_stats* st) {
+  cudaStream_t s = c->stream;
+  const int64_t n = c->n;
+  DevScalars* d = c->dsc.get();
+  const bool first = c->t == 0;
+  const int mode = first ? DCD_MODE_STATIC : c->mode;
+  if (mode == DCD_MODE_GIVEN_R && !c->has_rgiven) return DCD_ESTATE;
+  DCD_TRY_CUDA(cudaEventRecord(c->ev[0], s));
+  DCD_TRY_CUDA(cudaMemsetAsync(d, 0, sizeof(DevScalars), s));
+
+  // labels of level 0: singletons (static) or C_{t-1}; the run overwrites them
+  Buf<int32_t> L0;
+  DCD_TRY(L0.alloc(&c->mem, n));
+  const int32_t* src_labels = (mode == DCD_MODE_STATIC) ? c->iota.get() : c->labels.get();
+  DCD_TRY_CUDA(cudaMemcpyAsync(L0.get(), src_labels, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+
+  MergeOut mo;
+  DCD_TRY(merge_batch(c, src_labels, &mo));
+  const int nxt = 1 - c->cur;
+  DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch + 8, c->rp[nxt].get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+  DCD_TRY_CUDA(cudaEventRecord(c->ev[1], s));
+  DCD_TRY_CUDA(cudaStreamSynchronize(s));
+  if (c->hsc->err & kErrBadRecord) return DCD_EINVAL;
+  if (c->hsc->err & kErrOverflow) return DCD_EOVERFLOW;
+  const int64_t m2 = c->hsc->m2;
+  if (m2 < 0 || m2 >= ((int64_t)1 << 62)) return DCD_EOVERFLOW;
+  const int64_t nnz_new = c->hscratch[8];
+  Csr<int32_t> g{n, nnz_new, c->rp[nxt].get(), c->col[nxt].get(), c->w[nxt].get()};
+
+  // ---- R_t ----
+  Buf<uint8_t> rnew;
+  DCD_TRY(rnew.alloc(&c->mem, n));
+  const uint8_t* active = nullptr;
+  int64_t r_size = n;
+  DCD_TRY_CUDA(cudaEventRecord(c->ev[9], s));
+  if (mode == DCD_MODE_DELTA) {
+    Buf<int64_t> a;
+    Buf<int32_t> size;
+    DCD_TRY(a.alloc(&c->mem, n));
+    DCD_TRY(size.alloc(&c->mem, n));
+    DCD_TRY(community_sums(c, n, src_labels, mo.k.get(), a.get(), size.get()));
+    DCD_TRY(screen_batch(c, g, src_labels, mo.k.get(), a.get(), mo, rnew.get()));
+    DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch + 9, &d->r_size, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    DCD_TRY_CUDA(cudaStreamSynchronize(s));
+    r_size = c->hscratch[9];
+    active = rnew.get();
+  } else if (mode == DCD_MODE_GIVEN_R) {
+    DCD_TRY_CUDA(cudaMemcpyAsync(rnew.get(), c->rgiven.get(), n, cudaMemcpyDeviceToDevice, s));
+    active = rnew.get();
+    DCD_TRY_CUDA(cudaMemsetAsync(&d->r_size, 0, sizeof(int64_t), s));
+    count_bytes<<<grid_for(n, 256), 256, 0, s>>>(rnew.get(), n, (unsigned long long*)&d->r_size);
+    DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch + 9, &d->r_size, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    DCD_TRY_CUDA(cudaStreamSynchronize(s));
+    r_size = c->hscratch[9];
+  } else {
+    DCD_TRY_CUDA(cudaMemsetAsync(rnew.get(), 1, n, s));
+  }
+  DCD_TRY_CUDA(cudaEventRecord(c->ev[10], s));
+
+  // ---- Algorithm 1 with R_t at level 0 ----
+  DCD_TRY(c->labels_nx.ensure(&c->mem, n));
+  DCD_TRY(run_louvain(c, g, L0.get(), active, mo.k, c->labels_nx.get(), st));
+  DCD_TRY_CUDA(cudaEventRecord(c->ev[11], s));
+  DCD_TRY_CUDA(cudaEventSynchronize(c->ev[11]));
+
+  // ---- commit ----
+  c->cur = nxt;
+  c->nnz = nnz_new;
+  std::swap(c->labels.p, c->labels_nx.p);
+  std::swap(c->labels.n, c->labels_nx.n);
+  std::swap(c->rset.p, rnew.p);
+  std::swap(c->rset.n, rnew.n);
+  c->t += 1;
+  if (st) {
+    float t_all = 0.f, t_merge = 0.f, t_screen = 0.f;
+    cudaEventElapsedTime(&t_all, c->ev[0], c->ev[11]);
+    cudaEventElapsedTime(&t_merge, c->ev[0], c->ev[1]);
+    cudaEventElapsedTime(&t_screen, c->ev[9], c->ev[10]);
+    st->t = c->t;
+    st->n = n;
+    st->nnz = nnz_new;
+    st->r_size = r_size;
+    st->ins_records = c->n_ins;
+    st->del_records = c->n_del;
+    st->ms_total = t_all;
+    st->ms_merge = t_merge;
+    st->ms_screen = t_screen;
+  }
+  return DCD_OK;
+}
+
+int dcd_update(dcd_ctx* c, int32_t* labels_out, double* q_out, dcd_step_stats* stats) {
+  if (!c) return DCD_EINVAL;
+  DCD_SCOPE(c);
+  dcd_step_stats st;
+  memset(&st, 0, sizeof(st));
+  const int rc = update_impl(c, &st);
+  // the staged batch is consumed by the attempt, successful or not
+  c->n_ins = c->n_del = 0;
+  c->staged_on_device = false;
+  if (rc != DCD_OK) {
+    cudaStreamSynchronize(c->stream);
+    cudaGetLastError();
+    return rc;
+  }
+  if (labels_out) {
+    DCD_TRY_CUDA(cudaMemcpyAsync(labels_out, c->labels.get(), c->n * sizeof(int32_t), cudaMemcpyDefault, c->stream));
+    DCD_TRY_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  if (q_out) *q_out = st.q;
+  if (stats) *stats = st;
+  return DCD_OK;
+}
+
+int dcd_get_labels(dcd_ctx* c, int32_t* out) {
+  if (!c || !out) return DCD_EINVAL;
+  DCD_SCOPE(c);
+  DCD_TRY_CUDA(cudaMemcpyAsync(out, c->labels.get(), c->n * sizeof(int32_t), cudaMemcpyDefault, c->stream));
+  DCD_TRY_CUDA(cudaStreamSynchronize(c->stream));
+  return DCD_OK;
+}
+
+int dcd_get_rset(dcd_ctx* c, uint8_t* out) {
+  if (!c || !out) return DCD_EINVAL;
+  DCD_SCOPE(c);
+  DCD_TRY_CUDA(cudaMemcpyAsync(out, c->rset.get(), c->n, cudaMemcpyDefault, c->stream));
+  DCD_TRY_CUDA(cudaStreamSynchronize(c->stream));
+  return DCD_OK;
+}
+
+int dcd_set_labels(dcd_ctx* c, const int32_t* labels) {
+  if (!c || !labels) return DCD_EINVAL;
+  for (int64_t v = 0; v < c->n; v++)
+    if (labels[v] < 0 || labels[v] >= c->n) return DCD_EINVAL;
+  DCD_SCOPE(c);
+  DCD_TRY_CUDA(cudaMemcpyAsync(c->labels.get(), labels, c->n * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+  DCD_TRY_CUDA(cudaStreamSynchronize(c->stream));
+  if (c->t == 0) c->t = 1;
+  return DCD_OK;
+}
+
+int dcd_set_rset(dcd_ctx* c, const uint8_t* r) {
+  if (!c || !r) return DCD_EINVAL;
+  DCD_SCOPE(c);
+  DCD_TRY(c->rgiven.ensure(&c->mem, c->n));
+  DCD_TRY_CUDA(cudaMemcpyAsync(c->rgiven.get(), r, c->n, cudaMemcpyHostToDevice, c->stream));
+  DCD_TRY_CUDA(cudaStreamSynchronize(c->stream));
+  c->has_rgiven = true;
+  return DCD_OK;
+}
+
+int dcd_set_mode(dcd_ctx* c, int32_t mode) {
+  if (!c || mode < DCD_MODE_STATIC || mode > DCD_MODE_GIVEN_R) return DCD_EINVAL;
+  c->mode = mode;
+  return DCD_OK;
+}
+
+int dcd_get_graph(dcd_ctx* c, int64_t* nnz_out, int64_t* row_ptr, int32_t* col, int32_t* w) {
+  if (!c) return DCD_EINVAL;
+  if (nnz_out) *nnz_out = c->nnz;
+  DCD_SCOPE(c);
+  const int k = c->cur;
+  if (row_ptr)
+    DCD_TRY_CUDA(cudaMemcpyAsync(row_ptr, c->rp[k].get(), (c->n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                 c->stream));
+  if (col && c->nnz)
+    DCD_TRY_CUDA(cudaMemcpyAsync(col, c->col[k].get(), c->nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  if (w && c->nnz)
+    DCD_TRY_CUDA(cudaMemcpyAsync(w, c->w[k].get(), c->nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  DCD_TRY_CUDA(cudaStreamSynchronize(c->stream));
+  return DCD_OK;
+}
+
+}  // extern "C"

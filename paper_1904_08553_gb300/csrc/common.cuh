@@ -1,0 +1,104 @@
+// common.cuh -- shared device helpers of the dcd library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dcd.h"
+
+typedef __int128 i128;
+
+namespace dcd {
+
+constexpr int kWarp = 32;
+
+// Records the failing CUDA call for dcd_last_cuda_error().
+void note_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+#define DCD_TRY_CUDA(expr)                                   \
+  do {                                                       \
+    cudaError_t e_ = (expr);                                 \
+    if (e_ != cudaSuccess) {                                 \
+      ::dcd::note_cuda_error(e_, #expr, __FILE__, __LINE__); \
+      return DCD_ECUDA;                                      \
+    }                                                        \
+  } while (0)
+
+#define DCD_TRY(expr)        \
+  do {                       \
+    int rc_ = (expr);        \
+    if (rc_ != DCD_OK) {     \
+      return rc_;            \
+    }                        \
+  } while (0)
+
+#define DCD_LAUNCH_CHECK() DCD_TRY_CUDA(cudaGetLastError())
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Grid size for grid-stride kernels: enough CTAs to fill every SM several
+// times over, never more than the work needs.
+int grid_for(int64_t items, int threads, int per_sm = 8);
+int num_sms();
+
+// Device-side error word bits (ctx->d_err).
+enum : uint32_t {
+  kErrBadRecord = 1u,   // invalid batch record
+  kErrOverflow = 2u,    // weight above INT32_MAX or 2m too large
+  kErrTableFull = 4u,   // aggregation table overflow (cannot happen when sized by degree)
+};
+
+// ---- stream-ordered device allocation (the context's memory pool) ----
+struct DevMem {
+  cudaStream_t stream = nullptr;
+  cudaMemPool_t pool = nullptr;  // the context's own pool (keeps its memory)
+  int alloc(void** p, size_t bytes);
+  void release(void* p);
+};
+
+template <typename T>
+struct Buf {
+  T* p = nullptr;
+  size_t n = 0;
+  DevMem* mem = nullptr;
+  Buf() = default;
+  Buf(const Buf&) = delete;
+  Buf& operator=(const Buf&) = delete;
+  ~Buf() { reset(); }
+  int alloc(DevMem* m, size_t count) {
+    reset();
+    mem = m;
+    n = count;
+    void* q = nullptr;
+    int rc = m->alloc(&q, (count ? count : 1) * sizeof(T));
+    p = static_cast<T*>(q);
+    return rc;
+  }
+  void reset() {
+    if (p && mem) mem->release(p);
+    p = nullptr;
+    n = 0;
+  }
+  // Keep the allocation when it is already large enough.
+  int ensure(DevMem* m, size_t count) {
+    if (p && n >= count) return DCD_OK;
+    return alloc(m, count + count / 4 + 64);
+  }
+  T* get() const { return p; }
+};
+
+// ---- small device helpers ----
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Multiplicative hash of a label into a power-of-two table.
+__device__ __forceinline__ uint32_t hash_label(int32_t x, uint32_t mask) {
+  return ((uint32_t)x * 0x9E3779B1u) >> 7 & mask;
+}
+
+}  // namespace dcd

@@ -1,0 +1,852 @@
+// louvain.cu -- Algorithm 1 (multi-level local moving with graph compaction)
+// on the GPU, with the level-0 active set R_t of Sec. III-D.
+//
+// Schedule (the paper's code visits vertices one by one in an arbitrary order;
+// this library takes the synchronous reading): every pass reads one snapshot
+// of (labels, a_C, |C|); each active vertex picks the neighbour community of
+// largest gain S (ties to the smaller label; a singleton does not move into a
+// singleton of larger label), moving only on S > 0; all moves apply together.
+// The pass loop of a level stops when no vertex moves, when the pass gained at
+// most |N| / tau_inv (tau is not given in the paper; the state is kept), or
+// after max_iters passes.  N = m2^2 Q is tracked exactly: the moved rows give
+// the change of sum_i e_{i->C(i)}, a full reduction gives sum_C a_C^2.
+//
+// Kernels (degree-binned; a bin is a list of active vertex ids):
+//   lm_warp   1..32 entries:  one warp per vertex, lanes hold the row, labels
+//             grouped with match_any and summed with redux.sync
+//   lm_block  33..4096 entries: one CTA per vertex, shared-memory table
+//             > 4096 entries: one CTA per vertex, table in global memory
+#include <vector>
+
+#include "agg.cuh"
+#include "prims.cuh"
+#include "state.cuh"
+
+namespace dcd {
+
+namespace {
+
+template <typename W>
+struct LV {
+  const int64_t* rp;
+  const int32_t* col;
+  const W* w;
+  const int64_t* k;
+  const int32_t* L;
+  const int64_t* a;
+  const int32_t* size;
+  int64_t m2;
+};
+
+__device__ __forceinline__ int32_t guard_choice(int32_t C, int32_t D, const int32_t* size) {
+  // singleton-swap guard (minimum-label rule)
+  if (D != C && size[C] == 1 && size[D] == 1 && D > C) return C;
+  return D;
+}
+
+// ---------------------------------------------------------------- local move
+
+template <typename W, typename ST>
+__global__ void __launch_bounds__(256) lm_warp(LV<W> g, const int32_t* __restrict__ list, int64_t cnt,
+                                               int32_t* __restrict__ prop) {
+  const int lane = lane_id();
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < cnt; i += nw) {
+    const int32_t v = list[i];
+    const int64_t b = g.rp[v];
+    const int d = (int)(g.rp[v + 1] - b);
+    const int32_t C = g.L[v];
+    bool valid = lane < d;
+    int32_t u = valid ? g.col[b + lane] : -1;
+    valid = valid && u != v;
+    const int32_t lab = valid ? g.L[u] : -1;
+    const W wt = valid ? g.w[b + lane] : W(0);
+    const unsigned peers = __match_any_sync(0xffffffffu, lab);
+    const int64_t e = group_sum_exact(peers, wt);
+    const bool leader = (int)(__ffs(peers) - 1) == lane;
+    const unsigned cm = __ballot_sync(0xffffffffu, valid && leader && lab == C);
+    const int64_t eCx = __shfl_sync(0xffffffffu, e, cm ? __ffs(cm) - 1 : 0);
+    const int64_t eC = cm ? eCx : 0;
+    ST S = gain_lowest<ST>();
+    int32_t D = INT_MAX;
+    if (valid && leader && lab != C) {
+      S = gain<ST>(g.m2, g.k[v], e, eC, g.a[lab], g.a[C]);
+      D = lab;
+    }
+    warp_argmax(S, D);
+    if (lane == 0) prop[i] = (D != INT_MAX && S > 0) ? guard_choice(C, D, g.size) : C;
+  }
+}
+
+template <typename W, typename ST, int THREADS>
+__global__ void __launch_bounds__(THREADS) lm_block(LV<W> g, const int32_t* __restrict__ list, int64_t cnt,
+                                                    int32_t* __restrict__ prop, int32_t* __restrict__ gkeys,
+                                                    unsigned long long* __restrict__ gvals, int64_t gcap) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int NW = THREADS / 32;
+  __shared__ ST redS[NW];
+  __shared__ int32_t redD[NW];
+  __shared__ long long s_eC;
+  const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5;
+  for (int64_t i = blockIdx.x; i < cnt; i += gridDim.x) {
+    const int32_t v = list[i];
+    const int64_t b = g.rp[v];
+    const int64_t d = g.rp[v + 1] - b;
+    const int32_t C = g.L[v];
+    const uint32_t cap = table_cap(d), mask = cap - 1;
+    int32_t* keys;
+    unsigned long long* vals;
+    if (gcap == 0) {
+      vals = reinterpret_cast<unsigned long long*>(smem);
+      keys = reinterpret_cast<int32_t*>(smem + (size_t)cap * sizeof(unsigned long long));
+    } else {
+      keys = gkeys + (int64_t)blockIdx.x * gcap;
+      vals = gvals + (int64_t)blockIdx.x * gcap;
+    }
+    for (uint32_t s = tid; s < cap; s += THREADS) {
+      keys[s] = -1;
+      vals[s] = 0;
+    }
+    __syncthreads();
+    for (int64_t e0 = 0; e0 < d; e0 += THREADS) {
+      const int64_t e = e0 + tid;
+      bool valid = e < d;
+      const int32_t u = valid ? g.col[b + e] : -1;
+      valid = valid && u != v;
+      const int32_t lab = valid ? g.L[u] : -1;
+      const W wt = valid ? g.w[b + e] : W(0);
+      const unsigned peers = __match_any_sync(0xffffffffu, lab);
+      const int64_t sum = group_sum_exact(peers, wt);
+      if (valid && (int)(__ffs(peers) - 1) == lane) tbl_add(keys, vals, mask, lab, (unsigned long long)sum);
+    }
+    __syncthreads();
+    if (tid == 0) s_eC = tbl_get(keys, vals, mask, C);
+    __syncthreads();
+    const int64_t eC = s_eC, kv = g.k[v], aC = g.a[C];
+    ST S = gain_lowest<ST>();
+    int32_t D = INT_MAX;
+    for (uint32_t s = tid; s < cap; s += THREADS) {
+      const int32_t key = keys[s];
+      if (key >= 0 && key != C) {
+        ST x = gain<ST>(g.m2, kv, (int64_t)vals[s], eC, g.a[key], aC);
+        if (better(x, key, S, D)) {
+          S = x;
+          D = key;
+        }
+      }
+    }
+    warp_argmax(S, D);
+    if (lane == 0) {
+      redS[wid] = S;
+      redD[wid] = D;
+    }
+    __syncthreads();
+    if (wid == 0) {
+      S = lane < NW ? redS[lane] : gain_lowest<ST>();
+      D = lane < NW ? redD[lane] : INT_MAX;
+      warp_argmax(S, D);
+      if (lane == 0) prop[i] = (D != INT_MAX && S > 0) ? guard_choice(C, D, g.size) : C;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- apply + N
+
+__global__ void lm_apply(const int32_t* __restrict__ list, int64_t cnt, const int32_t* __restrict__ prop,
+                         int32_t* __restrict__ L, const int64_t* __restrict__ k, unsigned long long* __restrict__ a,
+                         int32_t* __restrict__ size, int32_t* __restrict__ Lprev, int32_t* __restrict__ mvit,
+                         int32_t iter, int32_t* __restrict__ moved, int32_t* __restrict__ moved_cnt) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t base0 = (blockIdx.x * (int64_t)blockDim.x) & ~31ll;
+  for (int64_t base = base0 + (threadIdx.x & ~31); base < cnt; base += stride) {
+    const int64_t i = base + lane_id();
+    bool mv = false;
+    int32_t v = 0;
+    if (i < cnt) {
+      v = list[i];
+      const int32_t p = prop[i], c = L[v];
+      if (p != c) {
+        mv = true;
+        Lprev[v] = c;
+        L[v] = p;
+        mvit[v] = iter;
+        const unsigned long long kv = (unsigned long long)k[v];
+        atomicAdd(&a[c], 0ull - kv);
+        atomicAdd(&a[p], kv);
+        atomicSub(&size[c], 1);
+        atomicAdd(&size[p], 1);
+      }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, mv);
+    int32_t slot = 0;
+    if (lane_id() == 0 && bal) slot = atomicAdd(moved_cnt, __popc(bal));
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    if (mv) moved[slot + __popc(bal & lanemask_lt())] = v;
+  }
+}
+
+// Change of sum_i e_{i->C(i)} from the rows of the moved vertices: an entry
+// (x, y) with y unmoved also stands for its mirror (y, x), hence weight 2.
+template <typename W>
+__global__ void __launch_bounds__(256) lm_delta_in(LV<W> g, const int32_t* __restrict__ moved,
+                                                   const int32_t* __restrict__ moved_cnt,
+                                                   const int32_t* __restrict__ Lprev, const int32_t* __restrict__ mvit,
+                                                   int32_t iter, unsigned long long* __restrict__ in_delta) {
+  const int64_t cnt = *moved_cnt;
+  const int lane = lane_id();
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int64_t acc = 0;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < cnt; i += nw) {
+    const int32_t x = moved[i];
+    const int32_t ox = Lprev[x], nx = g.L[x];
+    const int64_t b = g.rp[x], e1 = g.rp[x + 1];
+    for (int64_t e = b + lane; e < e1; e += 32) {
+      const int32_t y = g.col[e];
+      const int64_t wt = (int64_t)g.w[e];
+      const bool ym = mvit[y] == iter;
+      const int32_t ny = g.L[y];
+      const int32_t oy = ym ? Lprev[y] : ny;
+      const int dlt = (int)(nx == ny) - (int)(ox == oy);
+      acc += dlt * wt * (ym ? 1 : 2);
+    }
+  }
+  acc = (int64_t)warp_sum((long long)acc);
+  if (lane == 0 && acc != 0) atomicAdd(in_delta, (unsigned long long)acc);
+}
+
+// sum over labels of a^2 as an unsigned 128-bit value: per-CTA partials, then
+// one CTA adds them.
+__global__ void __launch_bounds__(256) sumsq_partial(const int64_t* __restrict__ a, int64_t n,
+                                                     unsigned long long* __restrict__ part) {
+  __shared__ unsigned long long slo[8], shi[8];
+  unsigned __int128 s = 0;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long x = (unsigned long long)a[c];
+    s += (unsigned __int128)x * x;
+  }
+  unsigned long long lo = (unsigned long long)s, hi = (unsigned long long)(s >> 64);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long lo2 = __shfl_xor_sync(0xffffffffu, lo, o), hi2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    unsigned long long nlo = lo + lo2;
+    hi = hi + hi2 + (nlo < lo ? 1ull : 0ull);
+    lo = nlo;
+  }
+  if (lane_id() == 0) {
+    slo[threadIdx.x >> 5] = lo;
+    shi[threadIdx.x >> 5] = hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned __int128 t = 0;
+    for (int w = 0; w < 8; w++) t += ((unsigned __int128)shi[w] << 64) | slo[w];
+    part[2 * blockIdx.x] = (unsigned long long)t;
+    part[2 * blockIdx.x + 1] = (unsigned long long)(t >> 64);
+  }
+}
+
+__device__ __forceinline__ bool below_tau(i128 gain, i128 base, int64_t tau_inv) {
+  const i128 y = base < 0 ? -base : base;
+  return gain <= y / (i128)tau_inv;
+}
+
+__device__ __forceinline__ i128 ld128(const int64_t* lo) {
+  return (i128)(((unsigned __int128)(unsigned long long)lo[1] << 64) | (unsigned long long)lo[0]);
+}
+__device__ __forceinline__ void st128(int64_t* lo, i128 x) {
+  lo[0] = (int64_t)(unsigned long long)x;
+  lo[1] = (int64_t)(unsigned long long)((unsigned __int128)x >> 64);
+}
+
+// Adds the partial squares, then takes the pass decision (one thread).
+// mode 0: level start (N_start = N_cur = m2 in - sq); mode 1: after a pass.
+__global__ void lm_decide(DevScalars* d, const unsigned long long* __restrict__ part, int nparts, int mode,
+                          const int32_t* __restrict__ moved_cnt, int32_t passes_done, int32_t max_iters,
+                          int64_t tau_inv) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  unsigned __int128 sq = 0;
+  for (int p = 0; p < nparts; p++) sq += ((unsigned __int128)part[2 * p + 1] << 64) | part[2 * p];
+  d->sq_lo = (int64_t)(unsigned long long)sq;
+  d->sq_hi = (int64_t)(unsigned long long)(sq >> 64);
+  if (mode == 0) {
+    const i128 N = (i128)d->m2 * (i128)d->in_cur - (i128)sq;
+    st128(&d->n_cur_lo, N);
+    st128(&d->n_start_lo, N);
+    d->stop = 0;
+    d->moves = 0;
+    return;
+  }
+  const int32_t moves = *moved_cnt;
+  d->moves = moves;
+  if (moves == 0) {
+    d->stop = 1;
+    return;
+  }
+  const int64_t in_new = d->in_cur + d->in_delta;
+  const i128 N_new = (i128)d->m2 * (i128)in_new - (i128)sq;
+  const i128 N_old = ld128(&d->n_cur_lo);
+  d->in_cur = in_new;
+  st128(&d->n_cur_lo, N_new);
+  d->stop = (below_tau(N_new - N_old, N_old, tau_inv) || passes_done >= max_iters) ? 1 : 0;
+}
+
+// ---------------------------------------------------------------- binning
+
+__global__ void bin_count(const int64_t* __restrict__ rp, int64_t n, const uint8_t* __restrict__ active,
+                          DevScalars* d) {
+  __shared__ unsigned long long sc[4];
+  __shared__ unsigned long long sdeg;
+  __shared__ long long smax;
+  if (threadIdx.x < 4) sc[threadIdx.x] = 0;
+  if (threadIdx.x == 0) {
+    sdeg = 0;
+    smax = 0;
+  }
+  __syncthreads();
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    if (active && !active[v]) continue;
+    const int64_t deg = rp[v + 1] - rp[v];
+    atomicAdd(&sdeg, (unsigned long long)deg);
+    if (deg == 0) continue;
+    const int bin = deg <= kBinWarpMax ? 0 : deg <= kBinMidMax ? 1 : deg <= kBinLargeMax ? 2 : 3;
+    atomicAdd(&sc[bin], 1ull);
+    if (bin == 3) atomicMax(&smax, (long long)deg);
+  }
+  __syncthreads();
+  if (threadIdx.x < 4 && sc[threadIdx.x]) atomicAdd((unsigned long long*)&d->bin_cnt[threadIdx.x], sc[threadIdx.x]);
+  if (threadIdx.x == 0) {
+    atomicAdd((unsigned long long*)&d->act_deg, sdeg);
+    atomicMax((long long*)&d->bin_maxdeg, smax);
+  }
+}
+
+__global__ void bin_scatter(const int64_t* __restrict__ rp, int64_t n, const uint8_t* __restrict__ active,
+                            const DevScalars* __restrict__ d, int32_t* __restrict__ cursor,
+                            int32_t* __restrict__ list) {
+  __shared__ int32_t off[4];
+  if (threadIdx.x == 0) {
+    int64_t o = 0;
+    for (int b = 0; b < 4; b++) {
+      off[b] = (int32_t)o;
+      o += d->bin_cnt[b];
+    }
+  }
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t base0 = (blockIdx.x * (int64_t)blockDim.x) + (threadIdx.x & ~31);
+  for (int64_t base = base0; base < n; base += stride) {
+    const int64_t v = base + lane_id();
+    int bin = -1;
+    if (v < n && (!active || active[v])) {
+      const int64_t deg = rp[v + 1] - rp[v];
+      if (deg > 0) bin = deg <= kBinWarpMax ? 0 : deg <= kBinMidMax ? 1 : deg <= kBinLargeMax ? 2 : 3;
+    }
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+      const unsigned bal = __ballot_sync(0xffffffffu, bin == b);
+      if (!bal) continue;
+      int32_t slot = 0;
+      if (lane_id() == 0) slot = atomicAdd(&cursor[b], __popc(bal));
+      slot = __shfl_sync(0xffffffffu, slot, 0);
+      if (bin == b) list[off[b] + slot + __popc(bal & lanemask_lt())] = (int32_t)v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- sums
+
+__global__ void comm_sums(int64_t n, const int32_t* __restrict__ L, const int64_t* __restrict__ k,
+                          unsigned long long* __restrict__ a, int32_t* __restrict__ size) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = L[v];
+    atomicAdd(&a[c], (unsigned long long)k[v]);
+    atomicAdd(&size[c], 1);
+  }
+}
+
+__global__ void fill_iota(int32_t* __restrict__ x, int64_t n) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    x[v] = (int32_t)v;
+}
+
+__global__ void fill_i32(int32_t* __restrict__ x, int64_t n, int32_t val) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    x[v] = val;
+}
+
+// ---------------------------------------------------------------- compaction
+
+__global__ void mark_used(int64_t n, const int32_t* __restrict__ L, int32_t* __restrict__ used) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    used[L[v]] = 1;
+}
+
+// Coarse entry of fine entry (u, y, w): (cid[L[u]], cid[L[y]], w).
+template <typename W, int G>
+__global__ void __launch_bounds__(256) emit_coarse(int64_t n, const int64_t* __restrict__ rp,
+                                                   const int32_t* __restrict__ col, const W* __restrict__ w,
+                                                   const int32_t* __restrict__ L, const int32_t* __restrict__ cid,
+                                                   uint64_t* __restrict__ keys, uint64_t* __restrict__ vals) {
+  const int g = threadIdx.x % G;
+  const int64_t gid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+  const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
+  for (int64_t u = gid; u < n; u += ngroups) {
+    const uint64_t cu = (uint64_t)(uint32_t)cid[L[u]] << 32;
+    const int64_t e1 = rp[u + 1];
+    for (int64_t e = rp[u] + g; e < e1; e += G) {
+      keys[e] = cu | (uint32_t)cid[L[col[e]]];
+      vals[e] = (uint64_t)(int64_t)w[e];
+    }
+  }
+}
+
+__global__ void key_heads(const uint64_t* __restrict__ keys, int64_t m, int32_t* __restrict__ head) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+    head[e] = (e == 0 || keys[e] != keys[e - 1]) ? 1 : 0;
+}
+
+// Sum of each run of equal keys: a thread folds 16 consecutive entries and
+// flushes one atomic per run piece.  Also writes the coarse column and the
+// per-row entry counts at run heads.
+constexpr int kRunItems = 16;
+__global__ void reduce_runs(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ vals, int64_t m,
+                            const int32_t* __restrict__ head, const int32_t* __restrict__ uid,
+                            unsigned long long* __restrict__ cw, int32_t* __restrict__ ccol,
+                            int64_t* __restrict__ rowcnt) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t e0 = t * kRunItems;
+  if (e0 >= m) return;
+  const int64_t e1 = e0 + kRunItems < m ? e0 + kRunItems : m;
+  int32_t cur = -1;
+  unsigned long long acc = 0;
+  for (int64_t e = e0; e < e1; e++) {
+    const int32_t id = uid[e];
+    if (head[e]) {
+      ccol[id] = (int32_t)(keys[e] & 0xffffffffu);
+      atomicAdd((unsigned long long*)&rowcnt[keys[e] >> 32], 1ull);
+    }
+    if (id != cur) {
+      if (cur >= 0) atomicAdd(&cw[cur], acc);
+      cur = id;
+      acc = 0;
+    }
+    acc += vals[e];
+  }
+  if (cur >= 0) atomicAdd(&cw[cur], acc);
+}
+
+// k of a coarse vertex = a of its community; compose the original vertices.
+__global__ void coarse_k(int64_t n, const int32_t* __restrict__ cid, const int64_t* __restrict__ a,
+                         int64_t* __restrict__ kc) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
+    if (cid[c + 1] != cid[c]) kc[cid[c]] = a[c];
+}
+
+__global__ void compose(int64_t n0, int32_t* __restrict__ comp, const int32_t* __restrict__ L,
+                        const int32_t* __restrict__ cid) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n0; v += (int64_t)gridDim.x * blockDim.x)
+    comp[v] = cid[L[comp[v]]];
+}
+
+// ---------------------------------------------------------------- finish
+
+__global__ void final_min(int64_t n0, const int32_t* __restrict__ comp, const int32_t* __restrict__ L,
+                          int32_t* __restrict__ minid) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n0; v += (int64_t)gridDim.x * blockDim.x)
+    atomicMin(&minid[L[comp[v]]], (int32_t)v);
+}
+
+__global__ void final_labels(int64_t n0, const int32_t* __restrict__ comp, const int32_t* __restrict__ L,
+                             const int32_t* __restrict__ minid, int32_t* __restrict__ out,
+                             unsigned long long* __restrict__ ncomm) {
+  unsigned long long c = 0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n0; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t x = minid[L[comp[v]]];
+    out[v] = x;
+    c += (x == (int32_t)v);
+  }
+  c = warp_sum(c);
+  if (lane_id() == 0 && c) atomicAdd(ncomm, c);
+}
+
+// ---------------------------------------------------------------- host side
+
+inline i128 h128(int64_t lo, int64_t hi) {
+  return (i128)(((unsigned __int128)(unsigned long long)hi << 64) | (unsigned long long)lo);
+}
+
+inline bool h_below_tau(i128 gain, i128 base, int64_t tau_inv) {
+  i128 y = base < 0 ? -base : base;
+  return gain <= y / (i128)tau_inv;
+}
+
+// State of one level (labels, sums, scratch) and its pass loop.
+struct LevelRun {
+  int64_t passes = 0, moves = 0, edges = 0;
+  float ms_lm = 0.f, ms_apply = 0.f;
+};
+
+template <typename W>
+int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<int64_t>& a, Buf<int32_t>& size,
+              const uint8_t* active, LevelRun* out) {
+  cudaStream_t s = c->stream;
+  DevScalars* d = c->dsc.get();
+  const int64_t nv = g.n;
+  const int T = 256;
+
+  // ---- bins of the active vertices ----
+  DCD_TRY_CUDA(cudaMemsetAsync(&d->bin_cnt[0], 0, sizeof(int64_t) * 6, s));  // bin_cnt, maxdeg, act_deg
+  bin_count<<<grid_for(nv, T), T, 0, s>>>(g.rp, nv, active, d);
+  DCD_LAUNCH_CHECK();
+  DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+  DCD_TRY_CUDA(cudaStreamSynchronize(s));
+  int64_t cnt[4];
+  for (int b = 0; b < 4; b++) cnt[b] = c->hsc->bin_cnt[b];
+  const int64_t total = cnt[0] + cnt[1] + cnt[2] + cnt[3];
+  const int64_t hub_max = c->hsc->bin_maxdeg;
+  const int64_t act_deg = c->hsc->act_deg;
+
+  Buf<int32_t> list, cursor, prop, Lprev, mvit, moved, moved_cnt;
+  DCD_TRY(list.alloc(&c->mem, total));
+  DCD_TRY(cursor.alloc(&c->mem, 4));
+  DCD_TRY(prop.alloc(&c->mem, total));
+  DCD_TRY(Lprev.alloc(&c->mem, nv));
+  DCD_TRY(mvit.alloc(&c->mem, nv));
+  DCD_TRY(moved.alloc(&c->mem, total));
+  DCD_TRY(moved_cnt.alloc(&c->mem, 1));
+  DCD_TRY_CUDA(cudaMemsetAsync(cursor.get(), 0, 4 * sizeof(int32_t), s));
+  if (total > 0) {
+    bin_scatter<<<grid_for(nv, T), T, 0, s>>>(g.rp, nv, active, d, cursor.get(), list.get());
+    DCD_LAUNCH_CHECK();
+  }
+  fill_i32<<<grid_for(nv, T), T, 0, s>>>(mvit.get(), nv, -1);
+  DCD_LAUNCH_CHECK();
+
+  // hub tables in global memory: one region per CTA, sized for the largest hub
+  const int64_t hub_cap = cnt[3] ? (int64_t)table_cap(hub_max) : 0;
+  int64_t hub_ctas = 0;
+  Buf<int32_t> hkeys;
+  Buf<unsigned long long> hvals;
+  if (cnt[3]) {
+    const int64_t budget = (int64_t)1 << 30;  // bytes for hub tables
+    hub_ctas = budget / (hub_cap * 12);
+    if (hub_ctas < 1) hub_ctas = 1;
+    if (hub_ctas > cnt[3]) hub_ctas = cnt[3];
+    if (hub_ctas > 4 * (int64_t)c->sms) hub_ctas = 4 * (int64_t)c->sms;
+    DCD_TRY(hkeys.alloc(&c->mem, hub_ctas * hub_cap));
+    DCD_TRY(hvals.alloc(&c->mem, hub_ctas * hub_cap));
+  }
+
+  // partials of sum a^2
+  const int sq_ctas = grid_for(nv, T, 4);
+  Buf<unsigned long long> part;
+  DCD_TRY(part.alloc(&c->mem, 2 * (int64_t)sq_ctas));
+
+  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_block<W, long long, kLargeThreads>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((size_t)kLargeCap * 12)));
+  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_block<W, i128, kLargeThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)((size_t)kLargeCap * 12)));
+  LV<W> lv{g.rp, g.col, g.w, kbuf.get(), L, a.get(), size.get(), 0};
+  lv.m2 = c->hsc->m2;
+  const bool wide = lv.m2 >= ((int64_t)1 << 31);
+  const int32_t* lst = list.get();
+  const size_t mid_smem = (size_t)kMidCap * 12, large_smem = (size_t)kLargeCap * 12;
+
+  for (;;) {
+    const int32_t iter = (int32_t)out->passes;
+    DCD_TRY_CUDA(cudaEventRecord(c->ev[2], s));
+#define DCD_LM_LAUNCH(ST)                                                                                          \
+  do {                                                                                                             \
+    if (cnt[0])                                                                                                    \
+      lm_warp<W, ST><<<grid_for(cnt[0] * 32, T, 16), T, 0, s>>>(lv, lst, cnt[0], prop.get());                      \
+    if (cnt[1])                                                                                                    \
+      lm_block<W, ST, kMidThreads><<<grid_for(cnt[1] * kMidThreads, kMidThreads, 32), kMidThreads, mid_smem, s>>>( \
+          lv, lst + cnt[0], cnt[1], prop.get() + cnt[0], nullptr, nullptr, 0);                                    \
+    if (cnt[2])                                                                                                    \
+      lm_block<W, ST, kLargeThreads><<<(unsigned)(cnt[2] < 2 * c->sms ? cnt[2] : 2 * c->sms), kLargeThreads,      \
+                                       large_smem, s>>>(lv, lst + cnt[0] + cnt[1], cnt[2],                         \
+                                                        prop.get() + cnt[0] + cnt[1], nullptr, nullptr, 0);       \
+    if (cnt[3])                                                                                                    \
+      lm_block<W, ST, kHubThreads><<<(unsigned)hub_ctas, kHubThreads, 0, s>>>(                                     \
+          lv, lst + cnt[0] + cnt[1] + cnt[2], cnt[3], prop.get() + cnt[0] + cnt[1] + cnt[2], hkeys.get(),         \
+          hvals.get(), hub_cap);                                                                                   \
+  } while (0)
+    if (wide) DCD_LM_LAUNCH(i128);
+    else DCD_LM_LAUNCH(long long);
+#undef DCD_LM_LAUNCH
+    DCD_LAUNCH_CHECK();
+    DCD_TRY_CUDA(cudaEventRecord(c->ev[3], s));
+    DCD_TRY_CUDA(cudaMemsetAsync(moved_cnt.get(), 0, sizeof(int32_t), s));
+    DCD_TRY_CUDA(cudaMemsetAsync(&d->in_delta, 0, sizeof(int64_t), s));
+    if (total) {
+      lm_apply<<<grid_for(total, T), T, 0, s>>>(lst, total, prop.get(), L, kbuf.get(),
+                                                  (unsigned long long*)a.get(), size.get(), Lprev.get(), mvit.get(),
+                                                  iter, moved.get(), moved_cnt.get());
+      lm_delta_in<W><<<grid_for(total * 32, T, 16), T, 0, s>>>(lv, moved.get(), moved_cnt.get(), Lprev.get(),
+                                                               mvit.get(), iter, (unsigned long long*)&d->in_delta);
+    }
+    sumsq_partial<<<sq_ctas, T, 0, s>>>(a.get(), nv, part.get());
+    lm_decide<<<1, 32, 0, s>>>(d, part.get(), sq_ctas, 1, moved_cnt.get(), iter + 1, c->cfg.max_iters,
+                               c->cfg.tau_inv);
+    DCD_LAUNCH_CHECK();
+    DCD_TRY_CUDA(cudaEventRecord(c->ev[4], s));
+    DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+    DCD_TRY_CUDA(cudaStreamSynchronize(s));
+    float t1 = 0.f, t2 = 0.f;
+    cudaEventElapsedTime(&t1, c->ev[2], c->ev[3]);
+    cudaEventElapsedTime(&t2, c->ev[3], c->ev[4]);
+    out->ms_lm += t1;
+    out->ms_apply += t2;
+    out->passes++;
+    out->edges += act_deg;
+    out->moves += c->hsc->moves;
+    if (c->hsc->stop) break;
+  }
+  return DCD_OK;
+}
+
+// Compaction of one level: returns nc; fills the coarse graph when nc < n.
+template <typename W>
+int used_labels(dcd_ctx* c, const Csr<W>& g, const int32_t* L, Buf<int32_t>& cid, int64_t* nc) {
+  cudaStream_t s = c->stream;
+  const int T = 256;
+  const int64_t nv = g.n;
+  DCD_TRY(cid.alloc(&c->mem, nv + 1));
+  Buf<int32_t> tmp;
+  DCD_TRY(tmp.alloc(&c->mem, scan_tmp_count(nv + 1)));
+  DCD_TRY_CUDA(cudaMemsetAsync(cid.get(), 0, (nv + 1) * sizeof(int32_t), s));
+  mark_used<<<grid_for(nv, T), T, 0, s>>>(nv, L, cid.get());
+  DCD_LAUNCH_CHECK();
+  DCD_TRY(exclusive_scan<int32_t>(cid.get(), cid.get(), nv + 1, nullptr, tmp.get(), s));
+  DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch, cid.get() + nv, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  DCD_TRY_CUDA(cudaStreamSynchronize(s));
+  *nc = *reinterpret_cast<int32_t*>(c->hscratch);
+  return DCD_OK;
+}
+
+// run id of entry e: heads before-or-at e, minus one
+__global__ void incl_from_excl(const int32_t* __restrict__ head, int32_t* __restrict__ uid, int64_t m) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+    uid[e] = uid[e] + head[e] - 1;
+}
+
+struct CoarseGraph {
+  Buf<int64_t> rp;
+  Buf<int32_t> col;
+  Buf<int64_t> w;
+  Csr<int64_t> view;
+};
+
+template <typename W>
+int coarsen(dcd_ctx* c, const Csr<W>& g, const int32_t* L, const int32_t* cid, int64_t nc, CoarseGraph* out) {
+  cudaStream_t s = c->stream;
+  const int T = 256;
+  const int64_t m = g.nnz;
+  Buf<uint64_t> k0, k1, v0, v1;
+  Buf<int32_t> head, uid;
+  Buf<uint32_t> stmp;
+  DCD_TRY(k0.alloc(&c->mem, m));
+  DCD_TRY(k1.alloc(&c->mem, m));
+  DCD_TRY(v0.alloc(&c->mem, m));
+  DCD_TRY(v1.alloc(&c->mem, m));
+  DCD_TRY(head.alloc(&c->mem, m + 1));
+  DCD_TRY(uid.alloc(&c->mem, m + 1));
+  DCD_TRY(stmp.alloc(&c->mem, sort_tmp_words(m) + 2 * scan_tmp_count(m + nc + 2) + 64));
+  const int64_t avg = g.n ? (m + g.n - 1) / g.n : 1;
+#define DCD_EMIT(Gs) \
+  emit_coarse<W, Gs><<<grid_for(g.n * Gs, T), T, 0, s>>>(g.n, g.rp, g.col, g.w, L, cid, k0.get(), v0.get())
+  if (avg <= 6) DCD_EMIT(4);
+  else if (avg <= 12) DCD_EMIT(8);
+  else if (avg <= 24) DCD_EMIT(16);
+  else DCD_EMIT(32);
+#undef DCD_EMIT
+  DCD_LAUNCH_CHECK();
+  const int b = bits_for(nc - 1);
+  int ranges[4] = {0, b, 32, 32 + b};
+  bool in1 = false;
+  DCD_TRY(sort_pairs<uint64_t>(k0.get(), v0.get(), k1.get(), v1.get(), m, ranges, 2, stmp.get(), &in1, s));
+  const uint64_t* keys = in1 ? k1.get() : k0.get();
+  const uint64_t* vals = in1 ? v1.get() : v0.get();
+  key_heads<<<grid_for(m, T), T, 0, s>>>(keys, m, head.get());
+  DCD_LAUNCH_CHECK();
+  DCD_TRY(exclusive_scan<int32_t>(head.get(), uid.get(), m, uid.get() + m, reinterpret_cast<int32_t*>(stmp.get()), s));
+  DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch, uid.get() + m, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  DCD_TRY_CUDA(cudaStreamSynchronize(s));
+  const int64_t U = *reinterpret_cast<int32_t*>(c->hscratch);
+  // run id of every entry = heads up to and including it, minus one
+  incl_from_excl<<<grid_for(m, T), T, 0, s>>>(head.get(), uid.get(), m);
+  DCD_LAUNCH_CHECK();
+  DCD_TRY(out->rp.alloc(&c->mem, nc + 1));
+  DCD_TRY(out->col.alloc(&c->mem, U));
+  DCD_TRY(out->w.alloc(&c->mem, U));
+  DCD_TRY_CUDA(cudaMemsetAsync(out->rp.get(), 0, (nc + 1) * sizeof(int64_t), s));
+  DCD_TRY_CUDA(cudaMemsetAsync(out->w.get(), 0, U * sizeof(int64_t), s));
+  if (m > 0) {
+    reduce_runs<<<(unsigned)cdiv(cdiv(m, kRunItems), T), T, 0, s>>>(keys, vals, m, head.get(), uid.get(),
+                                                                    (unsigned long long*)out->w.get(), out->col.get(),
+                                                                    out->rp.get());
+    DCD_LAUNCH_CHECK();
+  }
+  DCD_TRY(exclusive_scan<int64_t>(out->rp.get(), out->rp.get(), nc + 1, nullptr, reinterpret_cast<int64_t*>(stmp.get()),
+                                  s));
+  out->view = Csr<int64_t>{nc, U, out->rp.get(), out->col.get(), out->w.get()};
+  return DCD_OK;
+}
+
+}  // namespace
+
+int community_sums(dcd_ctx* c, int64_t n, const int32_t* labels, const int64_t* k, int64_t* a, int32_t* size) {
+  cudaStream_t s = c->stream;
+  DCD_TRY_CUDA(cudaMemsetAsync(a, 0, n * sizeof(int64_t), s));
+  DCD_TRY_CUDA(cudaMemsetAsync(size, 0, n * sizeof(int32_t), s));
+  comm_sums<<<grid_for(n, 256), 256, 0, s>>>(n, labels, k, (unsigned long long*)a, size);
+  DCD_LAUNCH_CHECK();
+  return DCD_OK;
+}
+
+int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint8_t* active0, Buf<int64_t>& k0,
+                int32_t* out_labels, dcd_step_stats* st) {
+  cudaStream_t s = c->stream;
+  DevScalars* d = c->dsc.get();
+  const int T = 256;
+  const int64_t n0 = g0.n;
+  const int64_t tau = c->cfg.tau_inv;
+
+  Buf<int64_t> a;
+  Buf<int32_t> size, comp;
+  DCD_TRY(a.alloc(&c->mem, n0));
+  DCD_TRY(size.alloc(&c->mem, n0));
+  DCD_TRY(comp.alloc(&c->mem, n0));
+  DCD_TRY(community_sums(c, n0, labels0, k0.get(), a.get(), size.get()));
+  fill_iota<<<grid_for(n0, T), T, 0, s>>>(comp.get(), n0);
+  {
+    const int sq_ctas = grid_for(n0, T, 4);
+    Buf<unsigned long long> part;
+    DCD_TRY(part.alloc(&c->mem, 2 * (int64_t)sq_ctas));
+    sumsq_partial<<<sq_ctas, T, 0, s>>>(a.get(), n0, part.get());
+    lm_decide<<<1, 32, 0, s>>>(d, part.get(), sq_ctas, 0, nullptr, 0, 0, tau);
+    DCD_LAUNCH_CHECK();
+  }
+  DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+  DCD_TRY_CUDA(cudaStreamSynchronize(s));
+
+  int64_t level = 0, passes_total = 0, passes0 = 0, moves_total = 0, edges_total = 0;
+  float ms_lm = 0.f, ms_apply = 0.f, ms_coarsen = 0.f;
+  i128 N_start = h128(c->hsc->n_start_lo, c->hsc->n_start_hi);
+
+  // current level: level 0 uses g0 / labels0 / k0; later levels own their data
+  CoarseGraph cg[2];
+  Buf<int64_t> kc[2];
+  Buf<int32_t> Lc[2];
+  int which = 0;
+  const Csr<int32_t>* g_l0 = &g0;
+  const Csr<int64_t>* g_lc = nullptr;
+  int32_t* L = labels0;
+  Buf<int64_t>* kcur = &k0;
+  const uint8_t* active = active0;
+  int64_t nv = n0;
+
+  for (;;) {
+    LevelRun lr;
+    if (level == 0) {
+      DCD_TRY(run_level<int32_t>(c, *g_l0, L, *kcur, a, size, active, &lr));
+    } else {
+      DCD_TRY(run_level<int64_t>(c, *g_lc, L, *kcur, a, size, nullptr, &lr));
+    }
+    passes_total += lr.passes;
+    if (level == 0) passes0 = lr.passes;
+    moves_total += lr.moves;
+    edges_total += lr.edges;
+    ms_lm += lr.ms_lm;
+    ms_apply += lr.ms_apply;
+    const i128 N_end = h128(c->hsc->n_cur_lo, c->hsc->n_cur_hi);
+
+    DCD_TRY_CUDA(cudaEventRecord(c->ev[5], s));
+    Buf<int32_t> cid;
+    int64_t nc = 0;
+    if (level == 0) DCD_TRY(used_labels<int32_t>(c, *g_l0, L, cid, &nc));
+    else DCD_TRY(used_labels<int64_t>(c, *g_lc, L, cid, &nc));
+    level++;
+    bool stop = nc == nv || (level >= 2 && h_below_tau(N_end - N_start, N_start, tau)) || level >= c->cfg.max_levels;
+    if (stop) {
+      DCD_TRY_CUDA(cudaEventRecord(c->ev[6], s));
+      DCD_TRY_CUDA(cudaEventSynchronize(c->ev[6]));
+      float tc = 0.f;
+      cudaEventElapsedTime(&tc, c->ev[5], c->ev[6]);
+      ms_coarsen += tc;
+      break;
+    }
+    // ---- compact: next level ----
+    const int nx = which ^ 1;
+    if (level == 1) DCD_TRY(coarsen<int32_t>(c, *g_l0, L, cid.get(), nc, &cg[nx]));
+    else DCD_TRY(coarsen<int64_t>(c, *g_lc, L, cid.get(), nc, &cg[nx]));
+    DCD_TRY(kc[nx].alloc(&c->mem, nc));
+    DCD_TRY(Lc[nx].alloc(&c->mem, nc));
+    coarse_k<<<grid_for(nv, T), T, 0, s>>>(nv, cid.get(), a.get(), kc[nx].get());
+    compose<<<grid_for(n0, T), T, 0, s>>>(n0, comp.get(), L, cid.get());
+    fill_iota<<<grid_for(nc, T), T, 0, s>>>(Lc[nx].get(), nc);
+    DCD_LAUNCH_CHECK();
+    // next level starts from singletons: a = k, |C| = 1; in and sum a^2 carry over
+    DCD_TRY_CUDA(cudaMemcpyAsync(a.get(), kc[nx].get(), nc * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    fill_i32<<<grid_for(nc, T), T, 0, s>>>(size.get(), nc, 1);
+    DCD_LAUNCH_CHECK();
+    DCD_TRY_CUDA(cudaEventRecord(c->ev[6], s));
+    DCD_TRY_CUDA(cudaEventSynchronize(c->ev[6]));
+    float tc = 0.f;
+    cudaEventElapsedTime(&tc, c->ev[5], c->ev[6]);
+    ms_coarsen += tc;
+    // free the previous coarse level
+    cg[which].rp.reset();
+    cg[which].col.reset();
+    cg[which].w.reset();
+    kc[which].reset();
+    Lc[which].reset();
+    which = nx;
+    g_lc = &cg[which].view;
+    L = Lc[which].get();
+    kcur = &kc[which];
+    nv = nc;
+    active = nullptr;
+    N_start = N_end;
+  }
+
+  // ---- compose + canonical labels (smallest member id) ----
+  DCD_TRY_CUDA(cudaEventRecord(c->ev[7], s));
+  {
+    Buf<int32_t> minid;
+    DCD_TRY(minid.alloc(&c->mem, nv));
+    fill_i32<<<grid_for(nv, T), T, 0, s>>>(minid.get(), nv, INT32_MAX);
+    final_min<<<grid_for(n0, T), T, 0, s>>>(n0, comp.get(), L, minid.get());
+    DCD_TRY_CUDA(cudaMemsetAsync(&d->ncomm, 0, sizeof(int64_t), s));
+    final_labels<<<grid_for(n0, T), T, 0, s>>>(n0, comp.get(), L, minid.get(), out_labels,
+                                                (unsigned long long*)&d->ncomm);
+    DCD_LAUNCH_CHECK();
+    DCD_TRY_CUDA(cudaEventRecord(c->ev[8], s));
+    DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+    DCD_TRY_CUDA(cudaStreamSynchronize(s));
+  }
+  float tf = 0.f;
+  cudaEventElapsedTime(&tf, c->ev[7], c->ev[8]);
+  if (st) {
+    const i128 N = h128(c->hsc->n_cur_lo, c->hsc->n_cur_hi);
+    const int64_t m2 = c->hsc->m2;
+    st->levels = level;
+    st->iters_total = passes_total;
+    st->iters_level0 = passes0;
+    st->moves_total = moves_total;
+    st->edges_scanned = edges_total;
+    st->communities = c->hsc->ncomm;
+    st->n_lo = (int64_t)(unsigned long long)N;
+    st->n_hi = (int64_t)(unsigned long long)((unsigned __int128)N >> 64);
+    st->m2 = m2;
+    st->q = m2 == 0 ? 0.0 : (double)N / ((double)m2 * (double)m2);
+    st->ms_local_move = ms_lm;
+    st->ms_apply = ms_apply;
+    st->ms_coarsen = ms_coarsen;
+    st->ms_finish = tf;
+  }
+  return DCD_OK;
+}
+
+}  // namespace dcd

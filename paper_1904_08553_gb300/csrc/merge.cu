@@ -1,0 +1,338 @@
+// merge.cu -- Delta_t into G_t: batch records, radix sort by (source, sink),
+// distinct pairs, and a row-parallel sort-merge of the CSR that also produces
+// the weighted degrees d_w (Sec. III-A), 2m and sum_i e_{i->C(i)} under the
+// inherited labels.
+//
+// The changes are stored as ordered pairs (i,j) and (j,i) (Sec. III-E).  The
+// paper only adds edges; the reading for deletions is: every delete of the
+// step acts first and removes the whole edge, then every insert adds its
+// weight (a new edge or a larger multiplicity).
+#include "prims.cuh"
+#include "state.cuh"
+
+namespace dcd {
+
+namespace {
+
+constexpr uint8_t kPairIns = 1, kPairDel = 2, kPairPresent = 4, kPairAdded = 8, kPairRemoved = 16;
+
+__global__ void validate_records(const dcd_edge* __restrict__ ins, int64_t n_ins,
+                                 const dcd_edge* __restrict__ del, int64_t n_del, int64_t n,
+                                 uint32_t* __restrict__ err) {
+  int64_t tot = n_ins + n_del;
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    dcd_edge e = i < n_ins ? ins[i] : del[i - n_ins];
+    bad |= e.u < 0 || e.v < 0 || e.u >= n || e.v >= n || e.u == e.v || (i < n_ins && e.w <= 0);
+  }
+  if (__any_sync(0xffffffffu, bad) && lane_id() == 0) atomicOr(err, kErrBadRecord);
+}
+
+// Record r: inserts first (2i, 2i+1 = both orientations of insert i), then
+// deletes.  key = source << 32 | sink, value = r.
+__global__ void make_records(const dcd_edge* __restrict__ ins, int64_t n_ins, const dcd_edge* __restrict__ del,
+                             int64_t n_del, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  int64_t tot = n_ins + n_del;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    dcd_edge e = i < n_ins ? ins[i] : del[i - n_ins];
+    uint64_t a = (uint64_t)(uint32_t)e.u, b = (uint64_t)(uint32_t)e.v;
+    keys[2 * i] = a << 32 | b;
+    keys[2 * i + 1] = b << 32 | a;
+    vals[2 * i] = (uint32_t)(2 * i);
+    vals[2 * i + 1] = (uint32_t)(2 * i + 1);
+  }
+}
+
+__global__ void run_heads(const uint64_t* __restrict__ keys, int64_t R, int32_t* __restrict__ head) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < R; e += (int64_t)gridDim.x * blockDim.x)
+    head[e] = (e == 0 || keys[e] != keys[e - 1]) ? 1 : 0;
+}
+
+// One thread per run of equal keys: sum of insert weights, delete flag.
+__global__ void reduce_pairs(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t R,
+                             const int32_t* __restrict__ head, const int32_t* __restrict__ pid,
+                             const dcd_edge* __restrict__ ins, int64_t n_ins, uint64_t* __restrict__ pkey,
+                             int64_t* __restrict__ pw, uint8_t* __restrict__ pflag) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < R; e += (int64_t)gridDim.x * blockDim.x) {
+    if (!head[e]) continue;
+    uint64_t k = keys[e];
+    int64_t W = 0;
+    uint8_t f = 0;
+    for (int64_t x = e; x < R && keys[x] == k; x++) {
+      uint32_t r = vals[x];
+      if ((int64_t)r < 2 * n_ins) {
+        W += ins[r >> 1].w;
+        f |= kPairIns;
+      } else {
+        f |= kPairDel;
+      }
+    }
+    int32_t p = pid[e];
+    pkey[p] = k;
+    pw[p] = W;
+    pflag[p] = f;
+  }
+}
+
+__device__ __forceinline__ int64_t lower_bound_i32(const int32_t* __restrict__ a, int64_t lo, int64_t hi, int32_t x) {
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int64_t lower_bound_u64(const uint64_t* __restrict__ a, int64_t lo, int64_t hi, uint64_t x) {
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// Per pair: was the edge in G_{t-1}; does the merge add or remove a row entry.
+__global__ void pair_status(const uint64_t* __restrict__ pkey, const int64_t* __restrict__ pw,
+                            uint8_t* __restrict__ pflag, int64_t P, const int64_t* __restrict__ rp,
+                            const int32_t* __restrict__ col, const int32_t* __restrict__ w,
+                            int32_t* __restrict__ added, int32_t* __restrict__ removed,
+                            int64_t* __restrict__ src_cnt, uint32_t* __restrict__ err) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t k = pkey[p];
+    int32_t u = (int32_t)(k >> 32), v = (int32_t)(k & 0xffffffffu);
+    int64_t b = rp[u], e = rp[u + 1];
+    int64_t pos = lower_bound_i32(col, b, e, v);
+    bool present = pos < e && col[pos] == v;
+    uint8_t f = pflag[p];
+    bool isins = f & kPairIns, isdel = f & kPairDel;
+    bool add = isins && !present;
+    bool rem = !isins && isdel && present;
+    if (isins) {
+      int64_t nw = (present && !isdel) ? (int64_t)w[pos] + pw[p] : pw[p];
+      if (nw > INT32_MAX) atomicOr(err, kErrOverflow);
+    }
+    f |= (present ? kPairPresent : 0) | (add ? kPairAdded : 0) | (rem ? kPairRemoved : 0);
+    pflag[p] = f;
+    added[p] = add;
+    removed[p] = rem;
+    atomicAdd((unsigned long long*)&src_cnt[u], 1ull);
+  }
+}
+
+__global__ void new_degrees(const int64_t* __restrict__ rp, const int64_t* __restrict__ pair_ptr,
+                            const int32_t* __restrict__ pA, const int32_t* __restrict__ pR, int64_t n,
+                            int64_t* __restrict__ deg) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+    int64_t p0 = pair_ptr[u], p1 = pair_ptr[u + 1];
+    deg[u] = rp[u + 1] - rp[u] + (pA[p1] - pA[p0]) - (pR[p1] - pR[p0]);
+  }
+}
+
+template <int G>
+__device__ __forceinline__ int64_t group_sum(int64_t x) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o, G);
+  return x;
+}
+
+// G lanes per row.  An untouched row is copied; a touched row is merged with
+// its pairs: an old entry lands at its old offset minus the removed pairs and
+// plus the added pairs that sort before it; an added pair lands after the old
+// entries below it, corrected the same way.
+template <int G>
+__global__ void __launch_bounds__(256) merge_rows(
+    int64_t n, const int64_t* __restrict__ rp_o, const int32_t* __restrict__ col_o, const int32_t* __restrict__ w_o,
+    const int64_t* __restrict__ rp_n, int32_t* __restrict__ col_n, int32_t* __restrict__ w_n,
+    const int64_t* __restrict__ pair_ptr, const uint64_t* __restrict__ pkey, const int64_t* __restrict__ pw,
+    const uint8_t* __restrict__ pflag, const int32_t* __restrict__ pA, const int32_t* __restrict__ pR,
+    const int32_t* __restrict__ lab, int64_t* __restrict__ kdeg, unsigned long long* __restrict__ m2_acc,
+    unsigned long long* __restrict__ in_acc) {
+  const int g = threadIdx.x % G;
+  // warp-uniform loop: every lane reaches the group shuffles
+  const int64_t gid0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * (32 / G);
+  const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
+  int64_t m2_loc = 0, in_loc = 0;
+  for (int64_t ubase = gid0; ubase < n; ubase += ngroups) {
+    const int64_t u = ubase + (int64_t)(lane_id() / G);
+    int64_t ks = 0, is = 0;
+    if (u >= n) {
+      // idle group in the warp's last round
+    } else if (pair_ptr[u] == pair_ptr[u + 1]) {
+      int64_t ob = rp_o[u], oe = rp_o[u + 1], nb = rp_n[u];
+      int32_t Lu = lab[u];
+      for (int64_t e = ob + g; e < oe; e += G) {
+        int32_t c = col_o[e];
+        int32_t wv = w_o[e];
+        col_n[nb + (e - ob)] = c;
+        w_n[nb + (e - ob)] = wv;
+        ks += wv;
+        if (lab[c] == Lu) is += wv;
+      }
+    } else {
+      int64_t ob = rp_o[u], oe = rp_o[u + 1], nb = rp_n[u];
+      int64_t p0 = pair_ptr[u], p1 = pair_ptr[u + 1];
+      int32_t Lu = lab[u];
+      int32_t rA0 = pA[p0], rR0 = pR[p0];
+      uint64_t hi = (uint64_t)(uint32_t)u << 32;
+      for (int64_t e = ob + g; e < oe; e += G) {
+        int32_t c = col_o[e];
+        int64_t q = lower_bound_u64(pkey, p0, p1, hi | (uint32_t)c);
+        bool match = q < p1 && pkey[q] == (hi | (uint32_t)c);
+        uint8_t f = match ? pflag[q] : 0;
+        if (f & kPairRemoved) continue;
+        int64_t wv = w_o[e];
+        if (match && (f & kPairIns)) wv = (f & kPairDel) ? pw[q] : wv + pw[q];
+        int64_t pos = nb + (e - ob) - (pR[q] - rR0) + (pA[q] - rA0);
+        col_n[pos] = c;
+        w_n[pos] = (int32_t)wv;
+        ks += wv;
+        if (lab[c] == Lu) is += wv;
+      }
+      for (int64_t q = p0 + g; q < p1; q += G) {
+        if (!(pflag[q] & kPairAdded)) continue;
+        int32_t c = (int32_t)(pkey[q] & 0xffffffffu);
+        int64_t o = lower_bound_i32(col_o, ob, oe, c) - ob;
+        int64_t pos = nb + o - (pR[q] - rR0) + (pA[q] - rA0);
+        int64_t wv = pw[q];
+        col_n[pos] = c;
+        w_n[pos] = (int32_t)wv;
+        ks += wv;
+        if (lab[c] == Lu) is += wv;
+      }
+    }
+    ks = group_sum<G>(ks);
+    is = group_sum<G>(is);
+    if (g == 0 && u < n) kdeg[u] = ks;
+    m2_loc += ks;
+    in_loc += is;
+  }
+  // one atomic per warp (each group leader holds its group's totals)
+  int64_t m = (g == 0) ? m2_loc : 0, i = (g == 0) ? in_loc : 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    m += __shfl_xor_sync(0xffffffffu, m, o);
+    i += __shfl_xor_sync(0xffffffffu, i, o);
+  }
+  if (lane_id() == 0) {
+    atomicAdd(m2_acc, (unsigned long long)m);
+    atomicAdd(in_acc, (unsigned long long)i);
+  }
+}
+
+}  // namespace
+
+int merge_batch(dcd_ctx* c, const int32_t* labels0, MergeOut* out) {
+  cudaStream_t s = c->stream;
+  const int64_t n = c->n;
+  const int64_t n_ins = c->n_ins, n_del = c->n_del;
+  const int64_t R = 2 * (n_ins + n_del);
+  DevScalars* d = c->dsc.get();
+  uint32_t* err = &d->err;
+  const int T = 256;
+
+  if (c->staged_on_device && n_ins + n_del > 0) {
+    // device-staged records are checked before any kernel indexes with them
+    validate_records<<<grid_for(n_ins + n_del, T), T, 0, s>>>(c->ins.get(), n_ins, c->del.get(), n_del, n, err);
+    DCD_LAUNCH_CHECK();
+    DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    DCD_TRY_CUDA(cudaStreamSynchronize(s));
+    if (*reinterpret_cast<uint32_t*>(c->hscratch) & kErrBadRecord) return DCD_EINVAL;
+  }
+
+  // ---- records sorted by (source, sink) ----
+  Buf<uint64_t> k0, k1;
+  Buf<uint32_t> v0, v1;
+  Buf<int32_t> head, pid;
+  Buf<uint32_t> stmp;
+  DCD_TRY(k0.alloc(&c->mem, R));
+  DCD_TRY(k1.alloc(&c->mem, R));
+  DCD_TRY(v0.alloc(&c->mem, R));
+  DCD_TRY(v1.alloc(&c->mem, R));
+  DCD_TRY(head.alloc(&c->mem, R + 1));
+  DCD_TRY(pid.alloc(&c->mem, R + 1));
+  int64_t scan_words = sort_tmp_words(R) + scan_tmp_count(n + 1) * 2 + scan_tmp_count(R + 1) * 2 + 64;
+  DCD_TRY(stmp.alloc(&c->mem, scan_words));
+  int64_t* stmp64 = reinterpret_cast<int64_t*>(stmp.get());
+
+  uint64_t* keys = k0.get();
+  uint32_t* vals = v0.get();
+  int64_t P = 0;
+  if (R > 0) {
+    make_records<<<grid_for(R / 2, T), T, 0, s>>>(c->ins.get(), n_ins, c->del.get(), n_del, k0.get(), v0.get());
+    DCD_LAUNCH_CHECK();
+    int b = bits_for(n - 1);
+    int ranges[4] = {0, b, 32, 32 + b};
+    bool in1 = false;
+    DCD_TRY(sort_pairs<uint32_t>(k0.get(), v0.get(), k1.get(), v1.get(), R, ranges, 2, stmp.get(), &in1, s));
+    if (in1) {
+      keys = k1.get();
+      vals = v1.get();
+    }
+    run_heads<<<grid_for(R, T), T, 0, s>>>(keys, R, head.get());
+    DCD_TRY(exclusive_scan<int32_t>(head.get(), pid.get(), R, pid.get() + R, reinterpret_cast<int32_t*>(stmp.get()), s));
+    DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch, pid.get() + R, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    DCD_TRY_CUDA(cudaStreamSynchronize(s));
+    P = (int64_t)(*reinterpret_cast<int32_t*>(c->hscratch));
+  }
+  out->npairs = P;
+
+  DCD_TRY(out->pkey.alloc(&c->mem, P));
+  DCD_TRY(out->pw.alloc(&c->mem, P));
+  DCD_TRY(out->pflag.alloc(&c->mem, P));
+  DCD_TRY(out->pair_ptr.alloc(&c->mem, n + 1));
+  Buf<int32_t> added, removed;
+  DCD_TRY(added.alloc(&c->mem, P + 1));
+  DCD_TRY(removed.alloc(&c->mem, P + 1));
+  DCD_TRY_CUDA(cudaMemsetAsync(out->pair_ptr.get(), 0, (n + 1) * sizeof(int64_t), s));
+
+  const int cur = c->cur, nxt = 1 - c->cur;
+  const int64_t* rp_o = c->rp[cur].get();
+  const int32_t* col_o = c->col[cur].get();
+  const int32_t* w_o = c->w[cur].get();
+
+  if (P > 0) {
+    reduce_pairs<<<grid_for(R, T), T, 0, s>>>(keys, vals, R, head.get(), pid.get(), c->ins.get(), n_ins,
+                                              out->pkey.get(), out->pw.get(), out->pflag.get());
+    pair_status<<<grid_for(P, T), T, 0, s>>>(out->pkey.get(), out->pw.get(), out->pflag.get(), P, rp_o, col_o, w_o,
+                                             added.get(), removed.get(), out->pair_ptr.get(), err);
+    DCD_LAUNCH_CHECK();
+  }
+  // pair_ptr: per-source counts -> exclusive scan (n + 1 entries)
+  DCD_TRY(exclusive_scan<int64_t>(out->pair_ptr.get(), out->pair_ptr.get(), n + 1, nullptr, stmp64, s));
+  DCD_TRY(exclusive_scan<int32_t>(added.get(), added.get(), P + 1, nullptr, reinterpret_cast<int32_t*>(stmp.get()), s));
+  DCD_TRY(exclusive_scan<int32_t>(removed.get(), removed.get(), P + 1, nullptr,
+                                  reinterpret_cast<int32_t*>(stmp.get()), s));
+
+  // ---- new row pointers ----
+  const int64_t cap = c->nnz + 2 * n_ins;
+  DCD_TRY(c->rp[nxt].ensure(&c->mem, n + 1));
+  DCD_TRY(c->col[nxt].ensure(&c->mem, cap));
+  DCD_TRY(c->w[nxt].ensure(&c->mem, cap));
+  int64_t* rp_n = c->rp[nxt].get();
+  new_degrees<<<grid_for(n, T), T, 0, s>>>(rp_o, out->pair_ptr.get(), added.get(), removed.get(), n, rp_n);
+  DCD_LAUNCH_CHECK();
+  DCD_TRY(exclusive_scan<int64_t>(rp_n, rp_n, n + 1, nullptr, stmp64, s));
+
+  // ---- merge rows, degrees, m2, in ----
+  DCD_TRY(out->k.alloc(&c->mem, n));
+  DCD_TRY_CUDA(cudaMemsetAsync(&d->m2, 0, sizeof(int64_t), s));
+  DCD_TRY_CUDA(cudaMemsetAsync(&d->in_cur, 0, sizeof(int64_t), s));
+  const int64_t avg = (cap + n - 1) / n;
+  const int64_t* pp = out->pair_ptr.get();
+#define DCD_MERGE(Gs)                                                                                       \
+  merge_rows<Gs><<<grid_for(n * Gs, T), T, 0, s>>>(n, rp_o, col_o, w_o, rp_n, c->col[nxt].get(),            \
+                                                   c->w[nxt].get(), pp, out->pkey.get(), out->pw.get(),     \
+                                                   out->pflag.get(), added.get(), removed.get(), labels0,  \
+                                                   out->k.get(), (unsigned long long*)&d->m2,               \
+                                                   (unsigned long long*)&d->in_cur)
+  if (avg <= 6) DCD_MERGE(4);
+  else if (avg <= 12) DCD_MERGE(8);
+  else if (avg <= 24) DCD_MERGE(16);
+  else DCD_MERGE(32);
+#undef DCD_MERGE
+  DCD_LAUNCH_CHECK();
+  return DCD_OK;
+}
+
+}  // namespace dcd

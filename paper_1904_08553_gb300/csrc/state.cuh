@@ -1,0 +1,126 @@
+// state.cuh -- the context behind dcd_ctx and the internal interfaces between
+// the library's translation units.
+#pragma once
+
+#include "common.cuh"
+
+namespace dcd {
+
+// A device CSR graph of one level.  Level 0 keeps int32 weights (the caller's
+// multiplicities); compacted levels carry int64 weights.
+template <typename W>
+struct Csr {
+  int64_t n = 0;
+  int64_t nnz = 0;
+  const int64_t* rp = nullptr;
+  const int32_t* col = nullptr;
+  const W* w = nullptr;
+};
+
+// Per-step scalars kept on the device (one struct, copied back in one go).
+struct DevScalars {
+  int64_t m2;        // 2m of the current level (equal on every level)
+  int64_t in_cur;    // sum_i e_{i->C(i)} of the current labels
+  int64_t in_delta;  // change of in_cur produced by the last pass
+  int64_t sq_lo;     // sum_C a_C^2 (two words of an unsigned 128-bit value)
+  int64_t sq_hi;
+  int64_t n_cur_lo;  // N of the current labels
+  int64_t n_cur_hi;
+  int64_t n_start_lo;  // N at the start of the level
+  int64_t n_start_hi;
+  int32_t moves;     // movers of the last pass
+  int32_t stop;      // 1 = the level's pass loop stops
+  int32_t nc;        // labels in use (coarsening)
+  int32_t pad0;
+  int64_t uniq;      // distinct coarse entries (coarsening)
+  int64_t bin_cnt[4];
+  int64_t bin_maxdeg;
+  int64_t act_deg;   // sum of the active vertices' degrees
+  int64_t ncomm;     // communities at the end
+  int64_t nsrc;      // screening: distinct sources
+  int64_t npairs;    // distinct (src, dst) pairs of the batch
+  int64_t r_size;    // |R_t|
+  uint32_t err;      // kErr* bits
+  uint32_t pad1;
+};
+
+// Degree bins of the local-move kernels.
+constexpr int kBinWarpMax = 32;     // 1..32: one warp, lanes hold the row
+constexpr int kBinMidMax = 256;     // 33..256: 64-thread CTA, shared table
+constexpr int kBinLargeMax = 4096;  // 257..4096: 256-thread CTA, shared table
+                                    // >4096: 512-thread CTA, table in global memory
+constexpr int kMidThreads = 64;
+constexpr int kLargeThreads = 256;
+constexpr int kHubThreads = 512;
+constexpr int kMidCap = 512;
+constexpr int kLargeCap = 8192;
+
+}  // namespace dcd
+
+struct dcd_ctx {
+  int64_t n = 0;
+  dcd_config cfg{};
+  int32_t mode = DCD_MODE_DELTA;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int sms = 0;
+  dcd::DevMem mem;
+  int64_t t = 0;  // time steps computed
+
+  // G_t (level 0), double-buffered so a failed update leaves G_{t-1} intact.
+  int cur = 0;
+  int64_t nnz = 0;
+  dcd::Buf<int64_t> rp[2];
+  dcd::Buf<int32_t> col[2];
+  dcd::Buf<int32_t> w[2];
+
+  dcd::Buf<int32_t> labels;     // C_t (canonical)
+  dcd::Buf<int32_t> labels_nx;  // C_{t+1} under construction
+  dcd::Buf<uint8_t> rset;       // R_t of the last update
+  dcd::Buf<uint8_t> rgiven;     // R_t for DCD_MODE_GIVEN_R
+  bool has_rgiven = false;
+
+  // staged Delta_t
+  dcd::Buf<dcd_edge> ins, del;
+  int64_t n_ins = 0, n_del = 0;
+  bool staged_on_device = false;  // some records still need device validation
+
+  // device scalars + pinned host mirror
+  dcd::Buf<dcd::DevScalars> dsc;
+  dcd::DevScalars* hsc = nullptr;
+  int64_t* hscratch = nullptr;  // pinned, 64 words
+
+  dcd::Buf<int32_t> iota;  // 0..n-1 (singleton labels)
+
+  cudaEvent_t ev[16] = {};
+};
+
+namespace dcd {
+
+// merge.cu: sort the staged batch, merge it into G_t (new buffers of ctx at
+// index 1 - cur), compute k (weighted degrees), m2 and in under labels0.
+struct MergeOut {
+  Buf<int64_t> k;          // n weighted degrees of G_t
+  Buf<uint64_t> pkey;      // distinct (src << 32 | dst) pairs, sorted
+  Buf<int64_t> pw;         // summed insert weight per pair (0 = no insert)
+  Buf<uint8_t> pflag;      // bit0 insert, bit1 delete, bit2 edge was in G_{t-1}
+  Buf<int64_t> pair_ptr;   // n + 1: pairs of source u are [pair_ptr[u], pair_ptr[u+1])
+  int64_t npairs = 0;
+};
+int merge_batch(dcd_ctx* c, const int32_t* labels0, MergeOut* out);
+
+// screen.cu: Algorithm 2 plus the deletion rule -> rset (n bytes).
+int screen_batch(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* labels0, const int64_t* k,
+                 const int64_t* a, const MergeOut& mo, uint8_t* rset);
+
+// louvain.cu: Algorithm 1 from level-0 labels (modified in place into the
+// level-0 result), level-0 active flags (NULL = all), k and m2 of G_t.
+// Writes canonical labels to out_labels and fills stats.
+int run_louvain(dcd_ctx* c, const Csr<int32_t>& g, int32_t* labels0, const uint8_t* active0,
+                Buf<int64_t>& k, int32_t* out_labels, dcd_step_stats* st);
+
+// louvain.cu: community sums a (by label) and sizes from k and labels.
+int community_sums(dcd_ctx* c, int64_t n, const int32_t* labels, const int64_t* k, int64_t* a,
+                   int32_t* size);
+
+}  // namespace dcd

@@ -1,0 +1,283 @@
+"""Python binding of the C ABI in include/dcd.h (argument marshalling only).
+
+Every step of the hot path runs in libdcd.so's CUDA kernels; this module
+converts numpy arrays / torch tensors to pointers and status codes to
+exceptions.  There is no fallback: if the library is missing or fails to load,
+every call raises.
+
+The module-level functions carry the C names (dcd_create, dcd_apply_batch,
+dcd_update, ...).  ``Context`` bundles them for one dynamic graph.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "libdcd.so"
+
+DCD_OK, DCD_EINVAL, DCD_ENOMEM, DCD_ECUDA, DCD_ESTATE, DCD_EOVERFLOW, DCD_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+MODE_STATIC, MODE_BASE, MODE_DELTA, MODE_GIVEN_R = 0, 1, 2, 3
+
+EXPORTED = [
+    "dcd_config_default", "dcd_create", "dcd_destroy", "dcd_apply_batch", "dcd_apply_batch_device",
+    "dcd_update", "dcd_get_labels", "dcd_get_rset", "dcd_set_labels", "dcd_set_rset", "dcd_set_mode",
+    "dcd_get_graph", "dcd_strerror", "dcd_last_cuda_error",
+]
+
+
+class DcdError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        msg = f"{what}: {_lib_or_none_strerror(code)} ({code})"
+        if code == DCD_ECUDA and _lib is not None:
+            msg += f" [{_lib.dcd_last_cuda_error().decode()}]"
+        super().__init__(msg)
+
+
+class Edge(ctypes.Structure):
+    _fields_ = [("u", ctypes.c_int32), ("v", ctypes.c_int32), ("w", ctypes.c_int32)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("max_levels", ctypes.c_int32),
+                ("tau_inv", ctypes.c_int32), ("reserved", ctypes.c_int32 * 12)]
+
+
+_STAT_I64 = ["t", "n", "nnz", "m2", "r_size", "levels", "iters_total", "iters_level0", "moves_total",
+             "edges_scanned", "communities", "n_lo", "n_hi"]
+_STAT_F32 = ["ms_total", "ms_merge", "ms_screen", "ms_local_move", "ms_apply", "ms_coarsen", "ms_finish"]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = ([(k, ctypes.c_int64) for k in _STAT_I64] + [("q", ctypes.c_double)] +
+                [("ins_records", ctypes.c_int64), ("del_records", ctypes.c_int64)] +
+                [(k, ctypes.c_float) for k in _STAT_F32] + [("reserved_f", ctypes.c_float * 9)])
+
+    @property
+    def N(self) -> int:
+        return (self.n_hi << 64) + (self.n_lo & ((1 << 64) - 1))
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved_f"}
+        d["N"] = self.N
+        return d
+
+
+_lib = None
+
+
+def _lib_or_none_strerror(code: int) -> str:
+    if _lib is None:
+        return "error"
+    return _lib.dcd_strerror(code).decode()
+
+
+def lib():
+    """Load libdcd.so (built by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not LIB_PATH.exists():
+            raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(str(LIB_PATH))
+        P, I64, I32, INT = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int
+        sig = {
+            "dcd_config_default": (None, [P]),
+            "dcd_create": (INT, [I64, P, P, P]),
+            "dcd_destroy": (INT, [P]),
+            "dcd_apply_batch": (INT, [P, P, I64, P, I64]),
+            "dcd_apply_batch_device": (INT, [P, P, I64, P, I64]),
+            "dcd_update": (INT, [P, P, P, P]),
+            "dcd_get_labels": (INT, [P, P]),
+            "dcd_get_rset": (INT, [P, P]),
+            "dcd_set_labels": (INT, [P, P]),
+            "dcd_set_rset": (INT, [P, P]),
+            "dcd_set_mode": (INT, [P, I32]),
+            "dcd_get_graph": (INT, [P, P, P, P, P]),
+            "dcd_strerror": (ctypes.c_char_p, [INT]),
+            "dcd_last_cuda_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != DCD_OK:
+        raise DcdError(rc, what)
+
+
+def _ptr(x):
+    """Address of a numpy array, a torch tensor, an int, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _edges(a, name: str) -> np.ndarray:
+    if a is None:
+        return np.zeros((0, 3), np.int32)
+    a = np.asarray(a)
+    if a.ndim != 2 or a.shape[1] not in (2, 3):
+        raise ValueError(f"{name} must be (k, 3) [u, v, w] or (k, 2) [u, v]")
+    if a.shape[1] == 2:
+        a = np.concatenate([a, np.ones((len(a), 1), a.dtype)], axis=1)
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+# ---- C names -----------------------------------------------------------------
+
+def dcd_config_default() -> Config:
+    cfg = Config()
+    lib().dcd_config_default(ctypes.byref(cfg))
+    return cfg
+
+
+def dcd_create(n: int, cfg: Config | None = None, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().dcd_create(int(n), ctypes.byref(cfg) if cfg is not None else None, _stream_ptr(stream),
+                            ctypes.byref(h)), "dcd_create")
+    return h
+
+
+def dcd_destroy(h) -> None:
+    _check(lib().dcd_destroy(h), "dcd_destroy")
+
+
+def dcd_apply_batch(h, ins=None, dels=None) -> None:
+    i3, d3 = _edges(ins, "ins"), _edges(dels, "dels")
+    _check(lib().dcd_apply_batch(h, _ptr(i3), len(i3), _ptr(d3), len(d3)), "dcd_apply_batch")
+
+
+def dcd_apply_batch_device(h, d_ins, n_ins: int, d_del, n_del: int) -> None:
+    _check(lib().dcd_apply_batch_device(h, _ptr(d_ins), int(n_ins), _ptr(d_del), int(n_del)),
+           "dcd_apply_batch_device")
+
+
+def dcd_update(h, labels_out=None):
+    q = ctypes.c_double()
+    st = StepStats()
+    _check(lib().dcd_update(h, _ptr(labels_out), ctypes.byref(q), ctypes.byref(st)), "dcd_update")
+    return q.value, st
+
+
+def dcd_get_labels(h, out) -> None:
+    _check(lib().dcd_get_labels(h, _ptr(out)), "dcd_get_labels")
+
+
+def dcd_get_rset(h, out) -> None:
+    _check(lib().dcd_get_rset(h, _ptr(out)), "dcd_get_rset")
+
+
+def dcd_set_labels(h, labels) -> None:
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    _check(lib().dcd_set_labels(h, _ptr(lab)), "dcd_set_labels")
+
+
+def dcd_set_rset(h, r) -> None:
+    rr = np.ascontiguousarray(r, dtype=np.uint8)
+    _check(lib().dcd_set_rset(h, _ptr(rr)), "dcd_set_rset")
+
+
+def dcd_set_mode(h, mode: int) -> None:
+    _check(lib().dcd_set_mode(h, int(mode)), "dcd_set_mode")
+
+
+def dcd_get_graph(h, n: int):
+    nnz = ctypes.c_int64()
+    _check(lib().dcd_get_graph(h, ctypes.byref(nnz), None, None, None), "dcd_get_graph")
+    rp = np.zeros(n + 1, np.int64)
+    col = np.zeros(nnz.value, np.int32)
+    w = np.zeros(nnz.value, np.int32)
+    _check(lib().dcd_get_graph(h, ctypes.byref(nnz), _ptr(rp), _ptr(col), _ptr(w)), "dcd_get_graph")
+    return rp, col, w
+
+
+def dcd_strerror(code: int) -> str:
+    return lib().dcd_strerror(int(code)).decode()
+
+
+def dcd_last_cuda_error() -> str:
+    return lib().dcd_last_cuda_error().decode()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return getattr(stream, "cuda_stream", None)
+
+
+class Context:
+    """One dynamic graph on vertices [0, n) (dcd_ctx)."""
+
+    def __init__(self, n: int, mode: int = MODE_DELTA, stream=None, max_iters: int = 500,
+                 max_levels: int = 64, tau_inv: int = 1_000_000):
+        cfg = dcd_config_default()
+        cfg.mode, cfg.max_iters, cfg.max_levels, cfg.tau_inv = mode, max_iters, max_levels, tau_inv
+        self.n = int(n)
+        self._h = dcd_create(self.n, cfg, stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            dcd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def apply_batch(self, ins=None, dels=None):
+        dcd_apply_batch(self._h, ins, dels)
+
+    def apply_batch_device(self, d_ins, n_ins, d_del, n_del):
+        dcd_apply_batch_device(self._h, d_ins, n_ins, d_del, n_del)
+
+    def update(self, labels_out="host"):
+        """Advance one step.  labels_out: "host" (numpy result), None, or a
+        preallocated numpy array / CUDA tensor of n int32."""
+        out = np.empty(self.n, np.int32) if isinstance(labels_out, str) else labels_out
+        q, st = dcd_update(self._h, out)
+        return out, q, st
+
+    def labels(self) -> np.ndarray:
+        out = np.empty(self.n, np.int32)
+        dcd_get_labels(self._h, out)
+        return out
+
+    def rset(self) -> np.ndarray:
+        out = np.empty(self.n, np.uint8)
+        dcd_get_rset(self._h, out)
+        return out
+
+    def set_labels(self, labels):
+        dcd_set_labels(self._h, labels)
+
+    def set_rset(self, r):
+        dcd_set_rset(self._h, r)
+
+    def set_mode(self, mode: int):
+        dcd_set_mode(self._h, mode)
+
+    def graph(self):
+        return dcd_get_graph(self._h, self.n)
