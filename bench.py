@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Benchmark of the dLouvain-Delta-s time-step update on GB300.
+
+Metric: ms per time-step update (batch sort-merge into G_t + Delta-screening +
+multi-level local moving over R_t + compaction), with local-move GTEPS beside
+it.  Workload: the LFR-style power-law temporal graph shaped like the paper's
+largest run (2,000,000 vertices, 63M temporal edges over 12 time steps,
+degree exponent 2.5, community-size exponent 1.5, mixing 0.3, 5 % community
+drift and 2 % deletions per step), generated from a fixed seed.  Step 1 is
+the static start (untimed); W warm-up steps follow, then K timed steps.  The
+stream has 1 + W + K steps at the configuration's rate of 63M / 12 events per
+step (W = 3, K = 8 reproduce the 12-step configuration exactly).
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+LFR_N = 2_000_000
+LFR_EVENTS = 63_000_000
+LFR_STEPS = 12
+CPU_SAMPLE_N = 100_000
+METRIC = "ms per time-step update"
+BYTES_PER_ENTRY = 12   # int32 col + int32 weight + int32 neighbour label, per directed entry visited
+BYTES_PER_VERTEX = 40  # row_ptr pair, k, label, a_C, |C|, proposal, list entry per active vertex
+
+
+def workload_desc(T: int) -> str:
+    return (f"lfr_2m: LFR-style temporal graph, n=2,000,000, {LFR_EVENTS // LFR_STEPS * T:,} edge events "
+            f"over {T} steps (63M over 12 in the configuration), degree exp 2.5 on [20,20000], "
+            f"community-size exp 1.5 on [100,50000], mu=0.3, 5% drift and 2% deletes per step")
+
+
+def make_stream(n: int, T: int, replica: int = 0):
+    from paper_1904_08553_gb300 import synth
+
+    synth.build()
+    events = int(round(LFR_EVENTS / LFR_STEPS * T * n / LFR_N))
+    return synth.lfr(synth.seed_for(1, replica), n, events, T, kmax=min(20_000.0, n / 2),
+                     smax=min(50_000.0, n / 4))
+
+
+def peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in Path(self.path).read_text().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def time_oracle(T: int, steps_timed: int, budget_s: float, n: int = CPU_SAMPLE_N, warm: int = 0):
+    """Oracle (single thread) on the same generator at n vertices; returns
+    per-step seconds and the sample's nnz per timed step."""
+    import oracle
+
+    oracle.build()
+    s = make_stream(n, T, replica=0)
+    ctx = oracle.Context(n)
+    ins, dels = s.steps[0]
+    ctx.apply_batch(ins, dels)
+    ctx.update(oracle.DELTA)
+    for t in range(1, 1 + warm):
+        ctx.apply_batch(*s.steps[t])
+        ctx.update(oracle.DELTA)
+    secs, nnzs = [], []
+    t0 = time.perf_counter()
+    for t in range(1 + warm, min(T, 1 + warm + steps_timed)):
+        ins, dels = s.steps[t]
+        a = time.perf_counter()
+        ctx.apply_batch(ins, dels)
+        _, _, st = ctx.update(oracle.DELTA)
+        secs.append(time.perf_counter() - a)
+        nnzs.append(st.nnz)
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return secs, nnzs
+
+
+def cpu_baseline(T: int, nnz_full_by_step: dict, budget_s: float = 20.0):
+    secs, nnzs = time_oracle(T, steps_timed=T, budget_s=budget_s)
+    # scale each sampled step to the full workload by its graph size (the
+    # oracle's work per step grows with nnz)
+    full = []
+    for i, (s_, z) in enumerate(zip(secs, nnzs)):
+        zf = nnz_full_by_step.get(2 + i)
+        full.append(s_ * 1e3 * (zf / z if zf else LFR_N / CPU_SAMPLE_N))
+    return {
+        "value": float(np.mean(full)), "unit": "ms", "cores": 1, "kind": "oracle",
+        "sample": (f"oracle (1 thread of {os.cpu_count()}) on the same LFR generator at n={CPU_SAMPLE_N:,} "
+                   f"(events scaled alike), steps 2..{1 + len(secs)}: {np.mean(secs) * 1e3:.1f} ms/step measured, "
+                   f"scaled to n=2M by the nnz ratio of each step"),
+    }
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    T = 1 + args.warmup + args.steps
+    secs, nnzs = time_oracle(T, steps_timed=args.steps, budget_s=240.0, warm=args.warmup)
+    # full-size nnz of the same steps, estimated from the sample by the vertex ratio
+    scale = LFR_N / CPU_SAMPLE_N
+    ms = [s_ * 1e3 * scale for s_ in secs]
+    v = float(np.mean(ms))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "higher_is_better": False,
+        "n_gpus": args.gpus, "steps": len(secs), "warmup": args.warmup, "ms_per_step": v,
+        "dtype": "int64", "data": "synthetic", "scaling": "weak", "vs_baseline": None,
+        "config": {"workload": workload_desc(T), "mode": "delta"},
+        "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle",
+                         "sample": (f"oracle on the LFR generator at n={CPU_SAMPLE_N:,}, timed steps "
+                                    f"{2 + args.warmup}..{1 + args.warmup + len(secs)}, "
+                                    f"{np.mean(secs) * 1e3:.1f} ms/step measured x{scale:.0f} (vertex ratio)")},
+        "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def gpu_arm(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1904_08553_gb300 import dcd
+
+    T = 1 + args.warmup + args.steps
+    stream = make_stream(LFR_N, T, replica=rank)
+    n = stream.n
+    dev = torch.device("cuda", local)
+    d_ins, d_del = [], []
+    for ins, dels in stream.steps:
+        d_ins.append(torch.from_numpy(np.ascontiguousarray(ins)).to(dev))
+        dd = np.zeros((len(dels), 3), np.int32)
+        dd[:, :2] = dels
+        d_del.append(torch.from_numpy(dd).to(dev))
+    torch.cuda.synchronize()
+    ts = torch.cuda.current_stream(dev)
+
+    def run(ctx, t, host=False, lab_host=None):
+        ins, dels = stream.steps[t]
+        if host:
+            ctx.apply_batch(pinned[t][0], pinned[t][1])
+            return ctx.update(labels_out=lab_host)
+        ctx.apply_batch_device(d_ins[t], len(ins), d_del[t], len(dels))
+        return ctx.update(labels_out=None)
+
+    # ---- device-resident inputs ----
+    ctx = dcd.Context(n, mode=dcd.MODE_DELTA, stream=ts)
+    run(ctx, 0)
+    for t in range(1, 1 + args.warmup):
+        run(ctx, t)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    stats = []
+    launches0 = dcd.dcd_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(ts)
+        for t in range(1 + args.warmup, T):
+            _, q, st = run(ctx, t)
+            stats.append(st)
+        e1.record(ts)
+        torch.cuda.synchronize()
+    launches = dcd.dcd_kernel_launches() - launches0
+    total_ms = e0.elapsed_time(e1)
+    if world > 1:
+        x = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        total_ms = float(x.item())
+    clocks = clk.summary()
+    nnz_by_step = {1 + args.warmup + i + 1: st.nnz for i, st in enumerate(stats)}
+    ctx.close()
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        pinned = []
+        for ins, dels in stream.steps:
+            pi = torch.from_numpy(np.ascontiguousarray(ins)).pin_memory().numpy()
+            pd = torch.from_numpy(np.ascontiguousarray(dels)).pin_memory().numpy()
+            pinned.append((pi, pd))
+        lab_host = torch.empty(n, dtype=torch.int32).pin_memory().numpy()
+        ctx = dcd.Context(n, mode=dcd.MODE_DELTA, stream=ts)
+        run(ctx, 0, host=True, lab_host=lab_host)
+        for t in range(1, 1 + args.warmup):
+            run(ctx, t, host=True, lab_host=lab_host)
+        torch.cuda.synchronize()
+        h2d = 0
+        a = time.perf_counter()
+        for t in range(1 + args.warmup, T):
+            run(ctx, t, host=True, lab_host=lab_host)
+            h2d += pinned[t][0].nbytes + len(pinned[t][1]) * 12
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - a) * 1e3 / args.steps
+        ctx.close()
+        e2e = {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(h2d / args.steps),
+               "d2h_bytes_per_step": int(n * 4)}
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    ms_step = total_ms / args.steps
+    lm_ms = sum(s.ms_local_move for s in stats)
+    edges = sum(s.edges_scanned for s in stats)
+    verts = sum(s.verts_scanned for s in stats)
+    passes = sum(s.iters_total for s in stats)
+    gteps = edges / (lm_ms * 1e-3) / 1e9 if lm_ms > 0 else None
+    peak, peak_kind = peaks()
+    lm_bytes = BYTES_PER_ENTRY * edges + BYTES_PER_VERTEX * verts
+    achieved = lm_bytes / (lm_ms * 1e-3) / 1e9 if lm_ms > 0 else None
+    cpu = cpu_baseline(T, nnz_by_step) if (world == 1 and not args.no_cpu) else None
+    line = {
+        "metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded LFR-style generator)",
+        "config": {"workload": workload_desc(T), "mode": "delta", "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "l2": "inputs larger than L2 (G_t holds ~100M directed entries, ~0.8 GB)",
+                   "timed_steps": f"t={2 + args.warmup}..{T}"},
+        "local_move_gteps": gteps,
+        "steps_detail": {
+            "r_fraction": float(np.mean([s.r_size / s.n for s in stats])),
+            "q_last": stats[-1].q, "nnz_last": stats[-1].nnz, "communities_last": stats[-1].communities,
+            "ms_merge": float(np.mean([s.ms_merge for s in stats])),
+            "ms_screen": float(np.mean([s.ms_screen for s in stats])),
+            "ms_local_move": float(np.mean([s.ms_local_move for s in stats])),
+            "ms_apply": float(np.mean([s.ms_apply for s in stats])),
+            "ms_coarsen": float(np.mean([s.ms_coarsen for s in stats])),
+            "ms_finish": float(np.mean([s.ms_finish for s in stats])),
+            "passes_per_step": passes / len(stats),
+            "levels": float(np.mean([s.levels for s in stats])),
+        },
+        "roofline": {
+            "kernel": "local-move pass (lm_warp + lm_block degree bins)",
+            "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "peak_kind": peak_kind,
+            "algorithmic_bytes": f"{BYTES_PER_ENTRY} B x entries scanned + {BYTES_PER_VERTEX} B x active vertices",
+        },
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -76,11 +76,13 @@ typedef struct {
   int64_t iters_level0;  /* local-move passes at level 0                            */
   int64_t moves_total;   /* single-vertex moves applied                             */
   int64_t edges_scanned; /* sum over passes of the active vertices' degrees          */
+  int64_t verts_scanned; /* sum over passes of the active vertex counts              */
   int64_t communities;   /* |C_t|                                                   */
   int64_t n_lo, n_hi;    /* N = m2^2 Q as a two's-complement 128-bit integer         */
   double q;              /* modularity Q_t (Eq. 1), from N and m2 in FP64            */
   int64_t ins_records;   /* staged inserts in Delta_t                               */
   int64_t del_records;   /* staged deletes in Delta_t                               */
+  int64_t launches;      /* CUDA kernel launches issued by this update               */
   float ms_total;        /* device time of the whole update (CUDA events)           */
   float ms_merge;        /* batch sort + CSR merge + degrees                        */
   float ms_screen;       /* Delta-screening + R_t build                             */
@@ -154,6 +156,10 @@ int dcd_set_mode(dcd_ctx* ctx, int32_t mode);
 /* The CSR of G_t: *nnz_out receives the entry count; when row_ptr/col/w are
  * non-NULL they receive n+1 int64, nnz int32 and nnz int32 (host memory). */
 int dcd_get_graph(dcd_ctx* ctx, int64_t* nnz_out, int64_t* row_ptr, int32_t* col, int32_t* w);
+
+/* Kernel launches issued by the library in this process so far (all
+ * contexts, all devices): lets a caller count the device work of a region. */
+int64_t dcd_kernel_launches(void);
 
 /* Text of a status code (static storage). */
 const char* dcd_strerror(int code);

@@ -9,6 +9,8 @@
 
 namespace dcd {
 
+std::atomic<int64_t> g_launches{0};
+
 namespace {
 thread_local char g_last_cuda[512] = "no CUDA error";
 int g_sms_cache = 0;
@@ -123,6 +125,8 @@ const char* dcd_strerror(int code) {
 
 const char* dcd_last_cuda_error(void) { return dcd::g_last_cuda; }
 
+int64_t dcd_kernel_launches(void) { return dcd::g_launches.load(std::memory_order_relaxed); }
+
 int dcd_create(int64_t n, const dcd_config* cfg, void* cuda_stream, dcd_ctx** out) {
   if (!out || n <= 0 || n > INT32_MAX) return DCD_EINVAL;
   *out = nullptr;
@@ -162,7 +166,7 @@ int dcd_create(int64_t n, const dcd_config* cfg, void* cuda_stream, dcd_ctx** ou
     if ((rc = c->rp[0].alloc(&c->mem, n + 1))) break;
     if ((rc = c->col[0].alloc(&c->mem, 1))) break;
     if ((rc = c->w[0].alloc(&c->mem, 1))) break;
-    iota_kernel<<<grid_for(n, 256), 256, 0, c->stream>>>(c->iota.get(), n);
+    ::dcd::count_launch(), iota_kernel<<<grid_for(n, 256), 256, 0, c->stream>>>(c->iota.get(), n);
     if (cudaMemcpyAsync(c->labels.get(), c->iota.get(), n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream) !=
         cudaSuccess) { rc = DCD_ECUDA; break; }
     if (cudaMemsetAsync(c->rp[0].get(), 0, (n + 1) * sizeof(int64_t), c->stream) != cudaSuccess) { rc = DCD_ECUDA; break; }
@@ -288,7 +292,7 @@ static int update_impl(dcd_ctx* c, dcd_step_stats* st) {
     DCD_TRY_CUDA(cudaMemcpyAsync(rnew.get(), c->rgiven.get(), n, cudaMemcpyDeviceToDevice, s));
     active = rnew.get();
     DCD_TRY_CUDA(cudaMemsetAsync(&d->r_size, 0, sizeof(int64_t), s));
-    count_bytes<<<grid_for(n, 256), 256, 0, s>>>(rnew.get(), n, (unsigned long long*)&d->r_size);
+    ::dcd::count_launch(), count_bytes<<<grid_for(n, 256), 256, 0, s>>>(rnew.get(), n, (unsigned long long*)&d->r_size);
     DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch + 9, &d->r_size, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     DCD_TRY_CUDA(cudaStreamSynchronize(s));
     r_size = c->hscratch[9];
@@ -334,7 +338,9 @@ int dcd_update(dcd_ctx* c, int32_t* labels_out, double* q_out, dcd_step_stats* s
   DCD_SCOPE(c);
   dcd_step_stats st;
   memset(&st, 0, sizeof(st));
+  const int64_t launches0 = dcd::g_launches.load();
   const int rc = update_impl(c, &st);
+  st.launches = dcd::g_launches.load() - launches0;
   // the staged batch is consumed by the attempt, successful or not
   c->n_ins = c->n_del = 0;
   c->staged_on_device = false;

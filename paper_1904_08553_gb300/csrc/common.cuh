@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "dcd.h"
 
 typedef __int128 i128;
@@ -11,6 +13,11 @@ typedef __int128 i128;
 namespace dcd {
 
 constexpr int kWarp = 32;
+
+// Process-wide count of kernel launches (dcd_kernel_launches); every launch
+// site of the library is written `count_launch(), kernel<<<...>>>(...)`.
+extern std::atomic<int64_t> g_launches;
+inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // Records the failing CUDA call for dcd_last_cuda_error().
 void note_cuda_error(cudaError_t e, const char* what, const char* file, int line);

@@ -296,11 +296,12 @@ __global__ void lm_decide(DevScalars* d, const unsigned long long* __restrict__ 
 __global__ void bin_count(const int64_t* __restrict__ rp, int64_t n, const uint8_t* __restrict__ active,
                           DevScalars* d) {
   __shared__ unsigned long long sc[4];
-  __shared__ unsigned long long sdeg;
+  __shared__ unsigned long long sdeg, sact;
   __shared__ long long smax;
   if (threadIdx.x < 4) sc[threadIdx.x] = 0;
   if (threadIdx.x == 0) {
     sdeg = 0;
+    sact = 0;
     smax = 0;
   }
   __syncthreads();
@@ -308,6 +309,7 @@ __global__ void bin_count(const int64_t* __restrict__ rp, int64_t n, const uint8
     if (active && !active[v]) continue;
     const int64_t deg = rp[v + 1] - rp[v];
     atomicAdd(&sdeg, (unsigned long long)deg);
+    atomicAdd(&sact, 1ull);
     if (deg == 0) continue;
     const int bin = deg <= kBinWarpMax ? 0 : deg <= kBinMidMax ? 1 : deg <= kBinLargeMax ? 2 : 3;
     atomicAdd(&sc[bin], 1ull);
@@ -317,6 +319,7 @@ __global__ void bin_count(const int64_t* __restrict__ rp, int64_t n, const uint8
   if (threadIdx.x < 4 && sc[threadIdx.x]) atomicAdd((unsigned long long*)&d->bin_cnt[threadIdx.x], sc[threadIdx.x]);
   if (threadIdx.x == 0) {
     atomicAdd((unsigned long long*)&d->act_deg, sdeg);
+    atomicAdd((unsigned long long*)&d->ncomm, sact);
     atomicMax((long long*)&d->bin_maxdeg, smax);
   }
 }
@@ -483,7 +486,7 @@ inline bool h_below_tau(i128 gain, i128 base, int64_t tau_inv) {
 
 // State of one level (labels, sums, scratch) and its pass loop.
 struct LevelRun {
-  int64_t passes = 0, moves = 0, edges = 0;
+  int64_t passes = 0, moves = 0, edges = 0, verts = 0;
   float ms_lm = 0.f, ms_apply = 0.f;
 };
 
@@ -496,8 +499,8 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
   const int T = 256;
 
   // ---- bins of the active vertices ----
-  DCD_TRY_CUDA(cudaMemsetAsync(&d->bin_cnt[0], 0, sizeof(int64_t) * 6, s));  // bin_cnt, maxdeg, act_deg
-  bin_count<<<grid_for(nv, T), T, 0, s>>>(g.rp, nv, active, d);
+  DCD_TRY_CUDA(cudaMemsetAsync(&d->bin_cnt[0], 0, sizeof(int64_t) * 7, s));  // bins, maxdeg, act_deg, ncomm
+  ::dcd::count_launch(), bin_count<<<grid_for(nv, T), T, 0, s>>>(g.rp, nv, active, d);
   DCD_LAUNCH_CHECK();
   DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
   DCD_TRY_CUDA(cudaStreamSynchronize(s));
@@ -506,6 +509,7 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
   const int64_t total = cnt[0] + cnt[1] + cnt[2] + cnt[3];
   const int64_t hub_max = c->hsc->bin_maxdeg;
   const int64_t act_deg = c->hsc->act_deg;
+  const int64_t n_active = c->hsc->ncomm;  // bin_count leaves the active count here
 
   Buf<int32_t> list, cursor, prop, Lprev, mvit, moved, moved_cnt;
   DCD_TRY(list.alloc(&c->mem, total));
@@ -517,10 +521,10 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
   DCD_TRY(moved_cnt.alloc(&c->mem, 1));
   DCD_TRY_CUDA(cudaMemsetAsync(cursor.get(), 0, 4 * sizeof(int32_t), s));
   if (total > 0) {
-    bin_scatter<<<grid_for(nv, T), T, 0, s>>>(g.rp, nv, active, d, cursor.get(), list.get());
+    ::dcd::count_launch(), bin_scatter<<<grid_for(nv, T), T, 0, s>>>(g.rp, nv, active, d, cursor.get(), list.get());
     DCD_LAUNCH_CHECK();
   }
-  fill_i32<<<grid_for(nv, T), T, 0, s>>>(mvit.get(), nv, -1);
+  ::dcd::count_launch(), fill_i32<<<grid_for(nv, T), T, 0, s>>>(mvit.get(), nv, -1);
   DCD_LAUNCH_CHECK();
 
   // hub tables in global memory: one region per CTA, sized for the largest hub
@@ -559,16 +563,16 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
 #define DCD_LM_LAUNCH(ST)                                                                                          \
   do {                                                                                                             \
     if (cnt[0])                                                                                                    \
-      lm_warp<W, ST><<<grid_for(cnt[0] * 32, T, 16), T, 0, s>>>(lv, lst, cnt[0], prop.get());                      \
+      ::dcd::count_launch(), lm_warp<W, ST><<<grid_for(cnt[0] * 32, T, 16), T, 0, s>>>(lv, lst, cnt[0], prop.get());                      \
     if (cnt[1])                                                                                                    \
-      lm_block<W, ST, kMidThreads><<<grid_for(cnt[1] * kMidThreads, kMidThreads, 32), kMidThreads, mid_smem, s>>>( \
+      ::dcd::count_launch(), lm_block<W, ST, kMidThreads><<<grid_for(cnt[1] * kMidThreads, kMidThreads, 32), kMidThreads, mid_smem, s>>>( \
           lv, lst + cnt[0], cnt[1], prop.get() + cnt[0], nullptr, nullptr, 0);                                    \
     if (cnt[2])                                                                                                    \
-      lm_block<W, ST, kLargeThreads><<<(unsigned)(cnt[2] < 2 * c->sms ? cnt[2] : 2 * c->sms), kLargeThreads,      \
+      ::dcd::count_launch(), lm_block<W, ST, kLargeThreads><<<(unsigned)(cnt[2] < 2 * c->sms ? cnt[2] : 2 * c->sms), kLargeThreads,      \
                                        large_smem, s>>>(lv, lst + cnt[0] + cnt[1], cnt[2],                         \
                                                         prop.get() + cnt[0] + cnt[1], nullptr, nullptr, 0);       \
     if (cnt[3])                                                                                                    \
-      lm_block<W, ST, kHubThreads><<<(unsigned)hub_ctas, kHubThreads, 0, s>>>(                                     \
+      ::dcd::count_launch(), lm_block<W, ST, kHubThreads><<<(unsigned)hub_ctas, kHubThreads, 0, s>>>(                                     \
           lv, lst + cnt[0] + cnt[1] + cnt[2], cnt[3], prop.get() + cnt[0] + cnt[1] + cnt[2], hkeys.get(),         \
           hvals.get(), hub_cap);                                                                                   \
   } while (0)
@@ -580,14 +584,14 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
     DCD_TRY_CUDA(cudaMemsetAsync(moved_cnt.get(), 0, sizeof(int32_t), s));
     DCD_TRY_CUDA(cudaMemsetAsync(&d->in_delta, 0, sizeof(int64_t), s));
     if (total) {
-      lm_apply<<<grid_for(total, T), T, 0, s>>>(lst, total, prop.get(), L, kbuf.get(),
+      ::dcd::count_launch(), lm_apply<<<grid_for(total, T), T, 0, s>>>(lst, total, prop.get(), L, kbuf.get(),
                                                   (unsigned long long*)a.get(), size.get(), Lprev.get(), mvit.get(),
                                                   iter, moved.get(), moved_cnt.get());
-      lm_delta_in<W><<<grid_for(total * 32, T, 16), T, 0, s>>>(lv, moved.get(), moved_cnt.get(), Lprev.get(),
+      ::dcd::count_launch(), lm_delta_in<W><<<grid_for(total * 32, T, 16), T, 0, s>>>(lv, moved.get(), moved_cnt.get(), Lprev.get(),
                                                                mvit.get(), iter, (unsigned long long*)&d->in_delta);
     }
-    sumsq_partial<<<sq_ctas, T, 0, s>>>(a.get(), nv, part.get());
-    lm_decide<<<1, 32, 0, s>>>(d, part.get(), sq_ctas, 1, moved_cnt.get(), iter + 1, c->cfg.max_iters,
+    ::dcd::count_launch(), sumsq_partial<<<sq_ctas, T, 0, s>>>(a.get(), nv, part.get());
+    ::dcd::count_launch(), lm_decide<<<1, 32, 0, s>>>(d, part.get(), sq_ctas, 1, moved_cnt.get(), iter + 1, c->cfg.max_iters,
                                c->cfg.tau_inv);
     DCD_LAUNCH_CHECK();
     DCD_TRY_CUDA(cudaEventRecord(c->ev[4], s));
@@ -600,6 +604,7 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
     out->ms_apply += t2;
     out->passes++;
     out->edges += act_deg;
+    out->verts += n_active;
     out->moves += c->hsc->moves;
     if (c->hsc->stop) break;
   }
@@ -616,7 +621,7 @@ int used_labels(dcd_ctx* c, const Csr<W>& g, const int32_t* L, Buf<int32_t>& cid
   Buf<int32_t> tmp;
   DCD_TRY(tmp.alloc(&c->mem, scan_tmp_count(nv + 1)));
   DCD_TRY_CUDA(cudaMemsetAsync(cid.get(), 0, (nv + 1) * sizeof(int32_t), s));
-  mark_used<<<grid_for(nv, T), T, 0, s>>>(nv, L, cid.get());
+  ::dcd::count_launch(), mark_used<<<grid_for(nv, T), T, 0, s>>>(nv, L, cid.get());
   DCD_LAUNCH_CHECK();
   DCD_TRY(exclusive_scan<int32_t>(cid.get(), cid.get(), nv + 1, nullptr, tmp.get(), s));
   DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch, cid.get() + nv, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -655,7 +660,7 @@ int coarsen(dcd_ctx* c, const Csr<W>& g, const int32_t* L, const int32_t* cid, i
   DCD_TRY(stmp.alloc(&c->mem, sort_tmp_words(m) + 2 * scan_tmp_count(m + nc + 2) + 64));
   const int64_t avg = g.n ? (m + g.n - 1) / g.n : 1;
 #define DCD_EMIT(Gs) \
-  emit_coarse<W, Gs><<<grid_for(g.n * Gs, T), T, 0, s>>>(g.n, g.rp, g.col, g.w, L, cid, k0.get(), v0.get())
+  ::dcd::count_launch(), emit_coarse<W, Gs><<<grid_for(g.n * Gs, T), T, 0, s>>>(g.n, g.rp, g.col, g.w, L, cid, k0.get(), v0.get())
   if (avg <= 6) DCD_EMIT(4);
   else if (avg <= 12) DCD_EMIT(8);
   else if (avg <= 24) DCD_EMIT(16);
@@ -668,14 +673,14 @@ int coarsen(dcd_ctx* c, const Csr<W>& g, const int32_t* L, const int32_t* cid, i
   DCD_TRY(sort_pairs<uint64_t>(k0.get(), v0.get(), k1.get(), v1.get(), m, ranges, 2, stmp.get(), &in1, s));
   const uint64_t* keys = in1 ? k1.get() : k0.get();
   const uint64_t* vals = in1 ? v1.get() : v0.get();
-  key_heads<<<grid_for(m, T), T, 0, s>>>(keys, m, head.get());
+  ::dcd::count_launch(), key_heads<<<grid_for(m, T), T, 0, s>>>(keys, m, head.get());
   DCD_LAUNCH_CHECK();
   DCD_TRY(exclusive_scan<int32_t>(head.get(), uid.get(), m, uid.get() + m, reinterpret_cast<int32_t*>(stmp.get()), s));
   DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch, uid.get() + m, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   DCD_TRY_CUDA(cudaStreamSynchronize(s));
   const int64_t U = *reinterpret_cast<int32_t*>(c->hscratch);
   // run id of every entry = heads up to and including it, minus one
-  incl_from_excl<<<grid_for(m, T), T, 0, s>>>(head.get(), uid.get(), m);
+  ::dcd::count_launch(), incl_from_excl<<<grid_for(m, T), T, 0, s>>>(head.get(), uid.get(), m);
   DCD_LAUNCH_CHECK();
   DCD_TRY(out->rp.alloc(&c->mem, nc + 1));
   DCD_TRY(out->col.alloc(&c->mem, U));
@@ -683,7 +688,7 @@ int coarsen(dcd_ctx* c, const Csr<W>& g, const int32_t* L, const int32_t* cid, i
   DCD_TRY_CUDA(cudaMemsetAsync(out->rp.get(), 0, (nc + 1) * sizeof(int64_t), s));
   DCD_TRY_CUDA(cudaMemsetAsync(out->w.get(), 0, U * sizeof(int64_t), s));
   if (m > 0) {
-    reduce_runs<<<(unsigned)cdiv(cdiv(m, kRunItems), T), T, 0, s>>>(keys, vals, m, head.get(), uid.get(),
+    ::dcd::count_launch(), reduce_runs<<<(unsigned)cdiv(cdiv(m, kRunItems), T), T, 0, s>>>(keys, vals, m, head.get(), uid.get(),
                                                                     (unsigned long long*)out->w.get(), out->col.get(),
                                                                     out->rp.get());
     DCD_LAUNCH_CHECK();
@@ -700,7 +705,7 @@ int community_sums(dcd_ctx* c, int64_t n, const int32_t* labels, const int64_t* 
   cudaStream_t s = c->stream;
   DCD_TRY_CUDA(cudaMemsetAsync(a, 0, n * sizeof(int64_t), s));
   DCD_TRY_CUDA(cudaMemsetAsync(size, 0, n * sizeof(int32_t), s));
-  comm_sums<<<grid_for(n, 256), 256, 0, s>>>(n, labels, k, (unsigned long long*)a, size);
+  ::dcd::count_launch(), comm_sums<<<grid_for(n, 256), 256, 0, s>>>(n, labels, k, (unsigned long long*)a, size);
   DCD_LAUNCH_CHECK();
   return DCD_OK;
 }
@@ -719,19 +724,19 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
   DCD_TRY(size.alloc(&c->mem, n0));
   DCD_TRY(comp.alloc(&c->mem, n0));
   DCD_TRY(community_sums(c, n0, labels0, k0.get(), a.get(), size.get()));
-  fill_iota<<<grid_for(n0, T), T, 0, s>>>(comp.get(), n0);
+  ::dcd::count_launch(), fill_iota<<<grid_for(n0, T), T, 0, s>>>(comp.get(), n0);
   {
     const int sq_ctas = grid_for(n0, T, 4);
     Buf<unsigned long long> part;
     DCD_TRY(part.alloc(&c->mem, 2 * (int64_t)sq_ctas));
-    sumsq_partial<<<sq_ctas, T, 0, s>>>(a.get(), n0, part.get());
-    lm_decide<<<1, 32, 0, s>>>(d, part.get(), sq_ctas, 0, nullptr, 0, 0, tau);
+    ::dcd::count_launch(), sumsq_partial<<<sq_ctas, T, 0, s>>>(a.get(), n0, part.get());
+    ::dcd::count_launch(), lm_decide<<<1, 32, 0, s>>>(d, part.get(), sq_ctas, 0, nullptr, 0, 0, tau);
     DCD_LAUNCH_CHECK();
   }
   DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
   DCD_TRY_CUDA(cudaStreamSynchronize(s));
 
-  int64_t level = 0, passes_total = 0, passes0 = 0, moves_total = 0, edges_total = 0;
+  int64_t level = 0, passes_total = 0, passes0 = 0, moves_total = 0, edges_total = 0, verts_total = 0;
   float ms_lm = 0.f, ms_apply = 0.f, ms_coarsen = 0.f;
   i128 N_start = h128(c->hsc->n_start_lo, c->hsc->n_start_hi);
 
@@ -758,6 +763,7 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
     if (level == 0) passes0 = lr.passes;
     moves_total += lr.moves;
     edges_total += lr.edges;
+    verts_total += lr.verts;
     ms_lm += lr.ms_lm;
     ms_apply += lr.ms_apply;
     const i128 N_end = h128(c->hsc->n_cur_lo, c->hsc->n_cur_hi);
@@ -783,13 +789,13 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
     else DCD_TRY(coarsen<int64_t>(c, *g_lc, L, cid.get(), nc, &cg[nx]));
     DCD_TRY(kc[nx].alloc(&c->mem, nc));
     DCD_TRY(Lc[nx].alloc(&c->mem, nc));
-    coarse_k<<<grid_for(nv, T), T, 0, s>>>(nv, cid.get(), a.get(), kc[nx].get());
-    compose<<<grid_for(n0, T), T, 0, s>>>(n0, comp.get(), L, cid.get());
-    fill_iota<<<grid_for(nc, T), T, 0, s>>>(Lc[nx].get(), nc);
+    ::dcd::count_launch(), coarse_k<<<grid_for(nv, T), T, 0, s>>>(nv, cid.get(), a.get(), kc[nx].get());
+    ::dcd::count_launch(), compose<<<grid_for(n0, T), T, 0, s>>>(n0, comp.get(), L, cid.get());
+    ::dcd::count_launch(), fill_iota<<<grid_for(nc, T), T, 0, s>>>(Lc[nx].get(), nc);
     DCD_LAUNCH_CHECK();
     // next level starts from singletons: a = k, |C| = 1; in and sum a^2 carry over
     DCD_TRY_CUDA(cudaMemcpyAsync(a.get(), kc[nx].get(), nc * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
-    fill_i32<<<grid_for(nc, T), T, 0, s>>>(size.get(), nc, 1);
+    ::dcd::count_launch(), fill_i32<<<grid_for(nc, T), T, 0, s>>>(size.get(), nc, 1);
     DCD_LAUNCH_CHECK();
     DCD_TRY_CUDA(cudaEventRecord(c->ev[6], s));
     DCD_TRY_CUDA(cudaEventSynchronize(c->ev[6]));
@@ -816,10 +822,10 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
   {
     Buf<int32_t> minid;
     DCD_TRY(minid.alloc(&c->mem, nv));
-    fill_i32<<<grid_for(nv, T), T, 0, s>>>(minid.get(), nv, INT32_MAX);
-    final_min<<<grid_for(n0, T), T, 0, s>>>(n0, comp.get(), L, minid.get());
+    ::dcd::count_launch(), fill_i32<<<grid_for(nv, T), T, 0, s>>>(minid.get(), nv, INT32_MAX);
+    ::dcd::count_launch(), final_min<<<grid_for(n0, T), T, 0, s>>>(n0, comp.get(), L, minid.get());
     DCD_TRY_CUDA(cudaMemsetAsync(&d->ncomm, 0, sizeof(int64_t), s));
-    final_labels<<<grid_for(n0, T), T, 0, s>>>(n0, comp.get(), L, minid.get(), out_labels,
+    ::dcd::count_launch(), final_labels<<<grid_for(n0, T), T, 0, s>>>(n0, comp.get(), L, minid.get(), out_labels,
                                                 (unsigned long long*)&d->ncomm);
     DCD_LAUNCH_CHECK();
     DCD_TRY_CUDA(cudaEventRecord(c->ev[8], s));
@@ -836,6 +842,7 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
     st->iters_level0 = passes0;
     st->moves_total = moves_total;
     st->edges_scanned = edges_total;
+    st->verts_scanned = verts_total;
     st->communities = c->hsc->ncomm;
     st->n_lo = (int64_t)(unsigned long long)N;
     st->n_hi = (int64_t)(unsigned long long)((unsigned __int128)N >> 64);

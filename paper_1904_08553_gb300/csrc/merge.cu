@@ -233,7 +233,7 @@ int merge_batch(dcd_ctx* c, const int32_t* labels0, MergeOut* out) {
 
   if (c->staged_on_device && n_ins + n_del > 0) {
     // device-staged records are checked before any kernel indexes with them
-    validate_records<<<grid_for(n_ins + n_del, T), T, 0, s>>>(c->ins.get(), n_ins, c->del.get(), n_del, n, err);
+    ::dcd::count_launch(), validate_records<<<grid_for(n_ins + n_del, T), T, 0, s>>>(c->ins.get(), n_ins, c->del.get(), n_del, n, err);
     DCD_LAUNCH_CHECK();
     DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     DCD_TRY_CUDA(cudaStreamSynchronize(s));
@@ -259,7 +259,7 @@ int merge_batch(dcd_ctx* c, const int32_t* labels0, MergeOut* out) {
   uint32_t* vals = v0.get();
   int64_t P = 0;
   if (R > 0) {
-    make_records<<<grid_for(R / 2, T), T, 0, s>>>(c->ins.get(), n_ins, c->del.get(), n_del, k0.get(), v0.get());
+    ::dcd::count_launch(), make_records<<<grid_for(R / 2, T), T, 0, s>>>(c->ins.get(), n_ins, c->del.get(), n_del, k0.get(), v0.get());
     DCD_LAUNCH_CHECK();
     int b = bits_for(n - 1);
     int ranges[4] = {0, b, 32, 32 + b};
@@ -269,7 +269,7 @@ int merge_batch(dcd_ctx* c, const int32_t* labels0, MergeOut* out) {
       keys = k1.get();
       vals = v1.get();
     }
-    run_heads<<<grid_for(R, T), T, 0, s>>>(keys, R, head.get());
+    ::dcd::count_launch(), run_heads<<<grid_for(R, T), T, 0, s>>>(keys, R, head.get());
     DCD_TRY(exclusive_scan<int32_t>(head.get(), pid.get(), R, pid.get() + R, reinterpret_cast<int32_t*>(stmp.get()), s));
     DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch, pid.get() + R, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     DCD_TRY_CUDA(cudaStreamSynchronize(s));
@@ -292,9 +292,9 @@ int merge_batch(dcd_ctx* c, const int32_t* labels0, MergeOut* out) {
   const int32_t* w_o = c->w[cur].get();
 
   if (P > 0) {
-    reduce_pairs<<<grid_for(R, T), T, 0, s>>>(keys, vals, R, head.get(), pid.get(), c->ins.get(), n_ins,
+    ::dcd::count_launch(), reduce_pairs<<<grid_for(R, T), T, 0, s>>>(keys, vals, R, head.get(), pid.get(), c->ins.get(), n_ins,
                                               out->pkey.get(), out->pw.get(), out->pflag.get());
-    pair_status<<<grid_for(P, T), T, 0, s>>>(out->pkey.get(), out->pw.get(), out->pflag.get(), P, rp_o, col_o, w_o,
+    ::dcd::count_launch(), pair_status<<<grid_for(P, T), T, 0, s>>>(out->pkey.get(), out->pw.get(), out->pflag.get(), P, rp_o, col_o, w_o,
                                              added.get(), removed.get(), out->pair_ptr.get(), err);
     DCD_LAUNCH_CHECK();
   }
@@ -310,7 +310,7 @@ int merge_batch(dcd_ctx* c, const int32_t* labels0, MergeOut* out) {
   DCD_TRY(c->col[nxt].ensure(&c->mem, cap));
   DCD_TRY(c->w[nxt].ensure(&c->mem, cap));
   int64_t* rp_n = c->rp[nxt].get();
-  new_degrees<<<grid_for(n, T), T, 0, s>>>(rp_o, out->pair_ptr.get(), added.get(), removed.get(), n, rp_n);
+  ::dcd::count_launch(), new_degrees<<<grid_for(n, T), T, 0, s>>>(rp_o, out->pair_ptr.get(), added.get(), removed.get(), n, rp_n);
   DCD_LAUNCH_CHECK();
   DCD_TRY(exclusive_scan<int64_t>(rp_n, rp_n, n + 1, nullptr, stmp64, s));
 
@@ -321,7 +321,7 @@ int merge_batch(dcd_ctx* c, const int32_t* labels0, MergeOut* out) {
   const int64_t avg = (cap + n - 1) / n;
   const int64_t* pp = out->pair_ptr.get();
 #define DCD_MERGE(Gs)                                                                                       \
-  merge_rows<Gs><<<grid_for(n * Gs, T), T, 0, s>>>(n, rp_o, col_o, w_o, rp_n, c->col[nxt].get(),            \
+  ::dcd::count_launch(), merge_rows<Gs><<<grid_for(n * Gs, T), T, 0, s>>>(n, rp_o, col_o, w_o, rp_n, c->col[nxt].get(),            \
                                                    c->w[nxt].get(), pp, out->pkey.get(), out->pw.get(),     \
                                                    out->pflag.get(), added.get(), removed.get(), labels0,  \
                                                    out->k.get(), (unsigned long long*)&d->m2,               \

@@ -139,9 +139,9 @@ int exclusive_scan(const T* in, T* out, int64_t n, T* total, T* tmp, cudaStream_
     return DCD_OK;
   }
   int64_t ntiles = cdiv(n, kScanTile);
-  scan_tile_totals<T><<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, n, tmp);
-  scan_totals<T><<<1, kScanThreads, 0, s>>>(tmp, ntiles, total);
-  scan_tiles<T><<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, out, n, tmp);
+  ::dcd::count_launch(), scan_tile_totals<T><<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, n, tmp);
+  ::dcd::count_launch(), scan_totals<T><<<1, kScanThreads, 0, s>>>(tmp, ntiles, total);
+  ::dcd::count_launch(), scan_tiles<T><<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, out, n, tmp);
   DCD_LAUNCH_CHECK();
   return DCD_OK;
 }
@@ -245,9 +245,9 @@ int sort_pairs(uint64_t* k0, V* v0, uint64_t* k1, V* v1, int64_t n, const int* b
   V* vb = v1;
   for (int r = 0; r < nranges; r++) {
     for (int b = bit_ranges[2 * r]; b < bit_ranges[2 * r + 1]; b += 8) {
-      rs_histogram<<<(unsigned)ntiles, kRsThreads, 0, s>>>(ka, n, b, counts, ntiles);
+      ::dcd::count_launch(), rs_histogram<<<(unsigned)ntiles, kRsThreads, 0, s>>>(ka, n, b, counts, ntiles);
       DCD_TRY(exclusive_scan<uint32_t>(counts, counts, 256 * ntiles, nullptr, scan_tmp, s));
-      rs_scatter<V><<<(unsigned)ntiles, kRsThreads, 0, s>>>(ka, va, kb, vb, n, b, counts, ntiles);
+      ::dcd::count_launch(), rs_scatter<V><<<(unsigned)ntiles, kRsThreads, 0, s>>>(ka, va, kb, vb, n, b, counts, ntiles);
       DCD_LAUNCH_CHECK();
       uint64_t* tk = ka;
       ka = kb;

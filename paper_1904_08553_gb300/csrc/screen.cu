@@ -351,7 +351,7 @@ int screen_batch(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* labels0, cons
   int32_t* l1 = l0 + n;
   int32_t* l2 = l1 + n;
   if (mo.npairs > 0) {
-    src_bins<<<grid_for(n, T), T, 0, s>>>(n, mo.pair_ptr.get(), g.rp, cursor.get(), l0, l1, l2, hubmax.get());
+    ::dcd::count_launch(), src_bins<<<grid_for(n, T), T, 0, s>>>(n, mo.pair_ptr.get(), g.rp, cursor.get(), l0, l1, l2, hubmax.get());
     DCD_LAUNCH_CHECK();
     DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch, cursor.get(), 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch + 2, hubmax.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -379,12 +379,12 @@ int screen_batch(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* labels0, cons
   do {                                                                                                           \
     DCD_TRY_CUDA(cudaFuncSetAttribute(screen_block<ST, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
                                       (int)smem));                                                               \
-    if (c0) screen_warp<ST><<<grid_for(c0 * 32, T, 16), T, 0, s>>>(sv, l0, c0);                                  \
+    if (c0) ::dcd::count_launch(), screen_warp<ST><<<grid_for(c0 * 32, T, 16), T, 0, s>>>(sv, l0, c0);                                  \
     if (c1)                                                                                                      \
-      screen_block<ST, 256><<<(unsigned)(c1 < 2 * c->sms ? c1 : 2 * c->sms), 256, smem, s>>>(sv, l1, c1, nullptr, \
+      ::dcd::count_launch(), screen_block<ST, 256><<<(unsigned)(c1 < 2 * c->sms ? c1 : 2 * c->sms), 256, smem, s>>>(sv, l1, c1, nullptr, \
                                                                                              nullptr, 0);        \
     if (c2)                                                                                                      \
-      screen_block<ST, 512><<<(unsigned)hub_ctas, 512, 0, s>>>(sv, l2, c2, hkeys.get(), hvals.get(), hub_cap);   \
+      ::dcd::count_launch(), screen_block<ST, 512><<<(unsigned)hub_ctas, 512, 0, s>>>(sv, l2, c2, hkeys.get(), hvals.get(), hub_cap);   \
   } while (0)
     if (wide) DCD_SCREEN(i128);
     else DCD_SCREEN(long long);
@@ -392,7 +392,7 @@ int screen_batch(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* labels0, cons
     DCD_LAUNCH_CHECK();
   }
   DCD_TRY_CUDA(cudaMemsetAsync(&d->r_size, 0, sizeof(int64_t), s));
-  build_rset<<<grid_for(n, T), T, 0, s>>>(n, mark.get(), cflag.get(), labels0, rset,
+  ::dcd::count_launch(), build_rset<<<grid_for(n, T), T, 0, s>>>(n, mark.get(), cflag.get(), labels0, rset,
                                            (unsigned long long*)&d->r_size);
   DCD_LAUNCH_CHECK();
   return DCD_OK;

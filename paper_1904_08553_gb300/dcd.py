@@ -24,7 +24,7 @@ MODE_STATIC, MODE_BASE, MODE_DELTA, MODE_GIVEN_R = 0, 1, 2, 3
 EXPORTED = [
     "dcd_config_default", "dcd_create", "dcd_destroy", "dcd_apply_batch", "dcd_apply_batch_device",
     "dcd_update", "dcd_get_labels", "dcd_get_rset", "dcd_set_labels", "dcd_set_rset", "dcd_set_mode",
-    "dcd_get_graph", "dcd_strerror", "dcd_last_cuda_error",
+    "dcd_get_graph", "dcd_kernel_launches", "dcd_strerror", "dcd_last_cuda_error",
 ]
 
 
@@ -47,13 +47,14 @@ class Config(ctypes.Structure):
 
 
 _STAT_I64 = ["t", "n", "nnz", "m2", "r_size", "levels", "iters_total", "iters_level0", "moves_total",
-             "edges_scanned", "communities", "n_lo", "n_hi"]
+             "edges_scanned", "verts_scanned", "communities", "n_lo", "n_hi"]
 _STAT_F32 = ["ms_total", "ms_merge", "ms_screen", "ms_local_move", "ms_apply", "ms_coarsen", "ms_finish"]
 
 
 class StepStats(ctypes.Structure):
     _fields_ = ([(k, ctypes.c_int64) for k in _STAT_I64] + [("q", ctypes.c_double)] +
-                [("ins_records", ctypes.c_int64), ("del_records", ctypes.c_int64)] +
+                [("ins_records", ctypes.c_int64), ("del_records", ctypes.c_int64),
+                 ("launches", ctypes.c_int64)] +
                 [(k, ctypes.c_float) for k in _STAT_F32] + [("reserved_f", ctypes.c_float * 9)])
 
     @property
@@ -96,6 +97,7 @@ def lib():
             "dcd_set_rset": (INT, [P, P]),
             "dcd_set_mode": (INT, [P, I32]),
             "dcd_get_graph": (INT, [P, P, P, P, P]),
+            "dcd_kernel_launches": (I64, []),
             "dcd_strerror": (ctypes.c_char_p, [INT]),
             "dcd_last_cuda_error": (ctypes.c_char_p, []),
         }
@@ -202,6 +204,10 @@ def dcd_get_graph(h, n: int):
     w = np.zeros(nnz.value, np.int32)
     _check(lib().dcd_get_graph(h, ctypes.byref(nnz), _ptr(rp), _ptr(col), _ptr(w)), "dcd_get_graph")
     return rp, col, w
+
+
+def dcd_kernel_launches() -> int:
+    return int(lib().dcd_kernel_launches())
 
 
 def dcd_strerror(code: int) -> str:
