@@ -205,7 +205,7 @@ def gpu_arm(args):
     from paper_1904_08553_gb300 import dcd
 
     T = 1 + args.warmup + args.steps
-    stream = make_stream(LFR_N, T, replica=rank)
+    stream = make_stream(args.n, T, replica=rank)
     n = stream.n
     dev = torch.device("cuda", local)
     d_ins, d_del = [], []
@@ -340,6 +340,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--n", type=int, default=LFR_N, help="vertex count (smaller cases for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
