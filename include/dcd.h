@@ -161,6 +161,30 @@ int dcd_get_graph(dcd_ctx* ctx, int64_t* nnz_out, int64_t* row_ptr, int32_t* col
  * contexts, all devices): lets a caller count the device work of a region. */
 int64_t dcd_kernel_launches(void);
 
+/* ---- allocation-free evaluation ----
+ * No counterpart in the paper: a service for callers that cannot allocate
+ * device memory when they need the answer (their device memory is held by
+ * another allocator, such as a framework's caching allocator, or they run
+ * where cudaMalloc/cudaFree must not be called or must not synchronise).
+ *
+ * Modularity Q (Eq. 1) of the partition d_labels of the graph given as a
+ * device CSR: d_row_ptr (n+1 int64), d_col and d_w (row_ptr[n] int32 each;
+ * every undirected edge stored in both rows, positive weights), d_labels
+ * (n int32 in [0, n)).  *q_out (host) receives Q, *m2_out (host, may be NULL)
+ * 2m.  Work runs on cuda_stream (NULL = legacy default stream) and the call
+ * returns when it is done.  No device memory is allocated: the scratch is a
+ * fixed 8 MiB array that the library reserves on every GPU where it is loaded
+ * and keeps until the process exits.  The first call on a device looks up
+ * that array's device address; make that first call before any stream
+ * capture.  Every call overwrites the array (each call clears what it needs),
+ * so calls whose device work overlaps -- other streams, other host threads --
+ * race and return wrong values.
+ * Errors: DCD_EINVAL (n <= 0, n > DCD_NOALLOC_MAX_N, NULL pointer, a label or
+ * column outside [0, n)), DCD_ECUDA. */
+#define DCD_NOALLOC_MAX_N 1048056
+int dcd_modularity_noalloc(int64_t n, const int64_t* d_row_ptr, const int32_t* d_col, const int32_t* d_w,
+                           const int32_t* d_labels, void* cuda_stream, double* q_out, int64_t* m2_out);
+
 /* Text of a status code (static storage). */
 const char* dcd_strerror(int code);
 

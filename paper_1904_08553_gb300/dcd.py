@@ -25,7 +25,9 @@ EXPORTED = [
     "dcd_config_default", "dcd_create", "dcd_destroy", "dcd_apply_batch", "dcd_apply_batch_device",
     "dcd_update", "dcd_get_labels", "dcd_get_rset", "dcd_set_labels", "dcd_set_rset", "dcd_set_mode",
     "dcd_get_graph", "dcd_kernel_launches", "dcd_strerror", "dcd_last_cuda_error",
+    "dcd_modularity_noalloc",
 ]
+NOALLOC_MAX_N = 1048056
 
 
 class DcdError(RuntimeError):
@@ -98,6 +100,7 @@ def lib():
             "dcd_set_mode": (INT, [P, I32]),
             "dcd_get_graph": (INT, [P, P, P, P, P]),
             "dcd_kernel_launches": (I64, []),
+            "dcd_modularity_noalloc": (INT, [I64, P, P, P, P, P, P, P]),
             "dcd_strerror": (ctypes.c_char_p, [INT]),
             "dcd_last_cuda_error": (ctypes.c_char_p, []),
         }
@@ -204,6 +207,16 @@ def dcd_get_graph(h, n: int):
     w = np.zeros(nnz.value, np.int32)
     _check(lib().dcd_get_graph(h, ctypes.byref(nnz), _ptr(rp), _ptr(col), _ptr(w)), "dcd_get_graph")
     return rp, col, w
+
+
+def dcd_modularity_noalloc(n: int, d_row_ptr, d_col, d_w, d_labels, stream=None):
+    """Q and 2m of a partition on a device CSR, without device allocation."""
+    q = ctypes.c_double()
+    m2 = ctypes.c_int64()
+    _check(lib().dcd_modularity_noalloc(int(n), _ptr(d_row_ptr), _ptr(d_col), _ptr(d_w), _ptr(d_labels),
+                                        _stream_ptr(stream), ctypes.byref(q), ctypes.byref(m2)),
+           "dcd_modularity_noalloc")
+    return q.value, m2.value
 
 
 def dcd_kernel_launches() -> int:
