@@ -78,6 +78,61 @@ __global__ void __launch_bounds__(256) lm_warp(LV<W> g, const int32_t* __restric
   }
 }
 
+// One warp per vertex of 33..256 entries: a warp-private shared-memory table
+// (capacity 2 x degree rounded up to a power of two, at most kMidCap).
+template <typename W, typename ST>
+__global__ void __launch_bounds__(256) lm_warp_tbl(LV<W> g, const int32_t* __restrict__ list, int64_t cnt,
+                                                   int32_t* __restrict__ prop) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = lane_id(), wib = threadIdx.x >> 5;
+  unsigned long long* vals = reinterpret_cast<unsigned long long*>(smem) + (size_t)wib * kMidCap;
+  int32_t* keys = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned long long*>(smem) + 8 * kMidCap) +
+                  (size_t)wib * kMidCap;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < cnt; i += nw) {
+    const int32_t v = list[i];
+    const int64_t b = g.rp[v];
+    const int64_t d = g.rp[v + 1] - b;
+    const int32_t C = g.L[v];
+    const uint32_t cap = table_cap(d), mask = cap - 1;
+    for (uint32_t s = lane; s < cap; s += 32) {
+      keys[s] = -1;
+      vals[s] = 0;
+    }
+    __syncwarp();
+    for (int64_t e0 = 0; e0 < d; e0 += 32) {
+      const int64_t e = e0 + lane;
+      bool valid = e < d;
+      const int32_t u = valid ? g.col[b + e] : -1;
+      valid = valid && u != v;
+      const int32_t lab = valid ? g.L[u] : -1;
+      const W wt = valid ? g.w[b + e] : W(0);
+      const unsigned peers = __match_any_sync(0xffffffffu, lab);
+      const int64_t sum = group_sum_exact(peers, wt);
+      if (valid && (int)(__ffs(peers) - 1) == lane) tbl_add(keys, vals, mask, lab, (unsigned long long)sum);
+    }
+    __syncwarp();
+    long long eC = lane == 0 ? tbl_get(keys, vals, mask, C) : 0;
+    eC = __shfl_sync(0xffffffffu, eC, 0);
+    const int64_t kv = g.k[v], aC = g.a[C];
+    ST S = gain_lowest<ST>();
+    int32_t D = INT_MAX;
+    for (uint32_t s = lane; s < cap; s += 32) {
+      const int32_t key = keys[s];
+      if (key >= 0 && key != C) {
+        const ST x = gain<ST>(g.m2, kv, (int64_t)vals[s], eC, g.a[key], aC);
+        if (better(x, key, S, D)) {
+          S = x;
+          D = key;
+        }
+      }
+    }
+    warp_argmax(S, D);
+    if (lane == 0) prop[i] = (D != INT_MAX && S > 0) ? guard_choice(C, D, g.size) : C;
+    __syncwarp();
+  }
+}
+
 template <typename W, typename ST, int THREADS>
 __global__ void __launch_bounds__(THREADS) lm_block(LV<W> g, const int32_t* __restrict__ list, int64_t cnt,
                                                     int32_t* __restrict__ prop, int32_t* __restrict__ gkeys,
@@ -153,36 +208,64 @@ __global__ void __launch_bounds__(THREADS) lm_block(LV<W> g, const int32_t* __re
 
 // ---------------------------------------------------------------- apply + N
 
-__global__ void lm_apply(const int32_t* __restrict__ list, int64_t cnt, const int32_t* __restrict__ prop,
-                         int32_t* __restrict__ L, const int64_t* __restrict__ k, unsigned long long* __restrict__ a,
-                         int32_t* __restrict__ size, int32_t* __restrict__ Lprev, int32_t* __restrict__ mvit,
-                         int32_t iter, int32_t* __restrict__ moved, int32_t* __restrict__ moved_cnt) {
+// Moves of one pass.  Community sums change by warp-aggregated atomics (one
+// per distinct community of the warp); movers of long rows (list positions
+// from big_from on) go to a separate list for block-per-row processing.
+__global__ void lm_apply(const int32_t* __restrict__ list, int64_t cnt, int64_t big_from,
+                         const int32_t* __restrict__ prop, int32_t* __restrict__ L, const int64_t* __restrict__ k,
+                         unsigned long long* __restrict__ a, int32_t* __restrict__ size, int32_t* __restrict__ Lprev,
+                         int32_t* __restrict__ mvit, int32_t iter, int32_t* __restrict__ moved,
+                         int32_t* __restrict__ moved_cnt, int32_t* __restrict__ moved_big,
+                         int32_t* __restrict__ moved_big_cnt) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t base0 = (blockIdx.x * (int64_t)blockDim.x) & ~31ll;
   for (int64_t base = base0 + (threadIdx.x & ~31); base < cnt; base += stride) {
     const int64_t i = base + lane_id();
     bool mv = false;
-    int32_t v = 0;
+    int32_t v = 0, c = -1, p = -1;
+    int64_t kv = 0;
     if (i < cnt) {
       v = list[i];
-      const int32_t p = prop[i], c = L[v];
+      p = prop[i];
+      c = L[v];
       if (p != c) {
         mv = true;
         Lprev[v] = c;
         L[v] = p;
         mvit[v] = iter;
-        const unsigned long long kv = (unsigned long long)k[v];
-        atomicAdd(&a[c], 0ull - kv);
-        atomicAdd(&a[p], kv);
-        atomicSub(&size[c], 1);
-        atomicAdd(&size[p], 1);
+        kv = k[v];
+      } else {
+        c = p = -1;
       }
     }
-    const unsigned bal = __ballot_sync(0xffffffffu, mv);
+    {  // leaving c
+      const unsigned peers = __match_any_sync(0xffffffffu, c);
+      const int64_t sk = group_sum_exact(peers, kv);
+      if (mv && (int)(__ffs(peers) - 1) == (int)lane_id()) {
+        atomicAdd(&a[c], 0ull - (unsigned long long)sk);
+        atomicSub(&size[c], __popc(peers));
+      }
+    }
+    {  // joining p
+      const unsigned peers = __match_any_sync(0xffffffffu, p);
+      const int64_t sk = group_sum_exact(peers, kv);
+      if (mv && (int)(__ffs(peers) - 1) == (int)lane_id()) {
+        atomicAdd(&a[p], (unsigned long long)sk);
+        atomicAdd(&size[p], __popc(peers));
+      }
+    }
+    const bool big = mv && i >= big_from;
+    const bool small = mv && !big;
+    unsigned bal = __ballot_sync(0xffffffffu, small);
     int32_t slot = 0;
     if (lane_id() == 0 && bal) slot = atomicAdd(moved_cnt, __popc(bal));
     slot = __shfl_sync(0xffffffffu, slot, 0);
-    if (mv) moved[slot + __popc(bal & lanemask_lt())] = v;
+    if (small) moved[slot + __popc(bal & lanemask_lt())] = v;
+    bal = __ballot_sync(0xffffffffu, big);
+    slot = 0;
+    if (lane_id() == 0 && bal) slot = atomicAdd(moved_big_cnt, __popc(bal));
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    if (big) moved_big[slot + __popc(bal & lanemask_lt())] = v;
   }
 }
 
@@ -215,10 +298,37 @@ __global__ void __launch_bounds__(256) lm_delta_in(LV<W> g, const int32_t* __res
   if (lane == 0 && acc != 0) atomicAdd(in_delta, (unsigned long long)acc);
 }
 
-// sum over labels of a^2 as an unsigned 128-bit value: per-CTA partials, then
-// one CTA adds them.
-__global__ void __launch_bounds__(256) sumsq_partial(const int64_t* __restrict__ a, int64_t n,
-                                                     unsigned long long* __restrict__ part) {
+// As lm_delta_in with one CTA per moved vertex (rows above 256 entries).
+template <typename W>
+__global__ void __launch_bounds__(256) lm_delta_in_block(LV<W> g, const int32_t* __restrict__ moved,
+                                                         const int32_t* __restrict__ moved_cnt,
+                                                         const int32_t* __restrict__ Lprev,
+                                                         const int32_t* __restrict__ mvit, int32_t iter,
+                                                         unsigned long long* __restrict__ in_delta) {
+  const int64_t cnt = *moved_cnt;
+  int64_t acc = 0;
+  for (int64_t i = blockIdx.x; i < cnt; i += gridDim.x) {
+    const int32_t x = moved[i];
+    const int32_t ox = Lprev[x], nx = g.L[x];
+    const int64_t e1 = g.rp[x + 1];
+    for (int64_t e = g.rp[x] + threadIdx.x; e < e1; e += blockDim.x) {
+      const int32_t y = g.col[e];
+      const int64_t wt = (int64_t)g.w[e];
+      const bool ym = mvit[y] == iter;
+      const int32_t ny = g.L[y];
+      const int32_t oy = ym ? Lprev[y] : ny;
+      acc += ((int)(nx == ny) - (int)(ox == oy)) * wt * (ym ? 1 : 2);
+    }
+  }
+  acc = (int64_t)warp_sum((long long)acc);
+  if (lane_id() == 0 && acc != 0) atomicAdd(in_delta, (unsigned long long)acc);
+}
+
+// sum over labels of a^2 as an unsigned 128-bit value, added into acc[0..1]
+// (low, high word): every CTA adds its part with a carry into the high word,
+// so the final pair is exact whatever the order.
+__global__ void __launch_bounds__(256) sumsq_acc(const int64_t* __restrict__ a, int64_t n,
+                                                 unsigned long long* __restrict__ acc) {
   __shared__ unsigned long long slo[8], shi[8];
   unsigned __int128 s = 0;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
@@ -241,8 +351,12 @@ __global__ void __launch_bounds__(256) sumsq_partial(const int64_t* __restrict__
   if (threadIdx.x == 0) {
     unsigned __int128 t = 0;
     for (int w = 0; w < 8; w++) t += ((unsigned __int128)shi[w] << 64) | slo[w];
-    part[2 * blockIdx.x] = (unsigned long long)t;
-    part[2 * blockIdx.x + 1] = (unsigned long long)(t >> 64);
+    const unsigned long long tlo = (unsigned long long)t, thi = (unsigned long long)(t >> 64);
+    if (tlo | thi) {
+      const unsigned long long old = atomicAdd(&acc[0], tlo);
+      const unsigned long long carry = (old + tlo < old) ? 1ull : 0ull;
+      if (thi + carry) atomicAdd(&acc[1], thi + carry);
+    }
   }
 }
 
@@ -259,16 +373,14 @@ __device__ __forceinline__ void st128(int64_t* lo, i128 x) {
   lo[1] = (int64_t)(unsigned long long)((unsigned __int128)x >> 64);
 }
 
-// Adds the partial squares, then takes the pass decision (one thread).
+// The pass decision (one thread); sum a^2 is already in d->sq.
 // mode 0: level start (N_start = N_cur = m2 in - sq); mode 1: after a pass.
-__global__ void lm_decide(DevScalars* d, const unsigned long long* __restrict__ part, int nparts, int mode,
-                          const int32_t* __restrict__ moved_cnt, int32_t passes_done, int32_t max_iters,
+__global__ void lm_decide(DevScalars* d, int mode, const int32_t* __restrict__ moved_cnt,
+                          const int32_t* __restrict__ moved_big_cnt, int32_t passes_done, int32_t max_iters,
                           int64_t tau_inv) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  unsigned __int128 sq = 0;
-  for (int p = 0; p < nparts; p++) sq += ((unsigned __int128)part[2 * p + 1] << 64) | part[2 * p];
-  d->sq_lo = (int64_t)(unsigned long long)sq;
-  d->sq_hi = (int64_t)(unsigned long long)(sq >> 64);
+  const unsigned __int128 sq =
+      ((unsigned __int128)(unsigned long long)d->sq_hi << 64) | (unsigned long long)d->sq_lo;
   if (mode == 0) {
     const i128 N = (i128)d->m2 * (i128)d->in_cur - (i128)sq;
     st128(&d->n_cur_lo, N);
@@ -277,7 +389,7 @@ __global__ void lm_decide(DevScalars* d, const unsigned long long* __restrict__ 
     d->moves = 0;
     return;
   }
-  const int32_t moves = *moved_cnt;
+  const int32_t moves = *moved_cnt + *moved_big_cnt;
   d->moves = moves;
   if (moves == 0) {
     d->stop = 1;
@@ -361,10 +473,17 @@ __global__ void bin_scatter(const int64_t* __restrict__ rp, int64_t n, const uin
 
 __global__ void comm_sums(int64_t n, const int32_t* __restrict__ L, const int64_t* __restrict__ k,
                           unsigned long long* __restrict__ a, int32_t* __restrict__ size) {
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t c = L[v];
-    atomicAdd(&a[c], (unsigned long long)k[v]);
-    atomicAdd(&size[c], 1);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (blockIdx.x * (int64_t)blockDim.x) + (threadIdx.x & ~31); base < n; base += stride) {
+    const int64_t v = base + lane_id();
+    const int32_t c = v < n ? L[v] : -1;
+    const int64_t kv = v < n ? k[v] : 0;
+    const unsigned peers = __match_any_sync(0xffffffffu, c);
+    const int64_t sk = group_sum_exact(peers, kv);
+    if (c >= 0 && (int)(__ffs(peers) - 1) == (int)lane_id()) {
+      atomicAdd(&a[c], (unsigned long long)sk);
+      atomicAdd(&size[c], __popc(peers));
+    }
   }
 }
 
@@ -456,8 +575,14 @@ __global__ void compose(int64_t n0, int32_t* __restrict__ comp, const int32_t* _
 
 __global__ void final_min(int64_t n0, const int32_t* __restrict__ comp, const int32_t* __restrict__ L,
                           int32_t* __restrict__ minid) {
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n0; v += (int64_t)gridDim.x * blockDim.x)
-    atomicMin(&minid[L[comp[v]]], (int32_t)v);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (blockIdx.x * (int64_t)blockDim.x) + (threadIdx.x & ~31); base < n0; base += stride) {
+    const int64_t v = base + lane_id();
+    const int32_t c = v < n0 ? L[comp[v]] : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, c);
+    const unsigned mn = __reduce_min_sync(peers, v < n0 ? (unsigned)v : 0xffffffffu);
+    if (c >= 0 && (int)(__ffs(peers) - 1) == (int)lane_id()) atomicMin(&minid[c], (int32_t)mn);
+  }
 }
 
 __global__ void final_labels(int64_t n0, const int32_t* __restrict__ comp, const int32_t* __restrict__ L,
@@ -511,7 +636,7 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
   const int64_t act_deg = c->hsc->act_deg;
   const int64_t n_active = c->hsc->ncomm;  // bin_count leaves the active count here
 
-  Buf<int32_t> list, cursor, prop, Lprev, mvit, moved, moved_cnt;
+  Buf<int32_t> list, cursor, prop, Lprev, mvit, moved, moved_cnt, moved_big, moved_big_cnt;
   DCD_TRY(list.alloc(&c->mem, total));
   DCD_TRY(cursor.alloc(&c->mem, 4));
   DCD_TRY(prop.alloc(&c->mem, total));
@@ -519,6 +644,8 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
   DCD_TRY(mvit.alloc(&c->mem, nv));
   DCD_TRY(moved.alloc(&c->mem, total));
   DCD_TRY(moved_cnt.alloc(&c->mem, 1));
+  DCD_TRY(moved_big.alloc(&c->mem, cnt[2] + cnt[3]));
+  DCD_TRY(moved_big_cnt.alloc(&c->mem, 1));
   DCD_TRY_CUDA(cudaMemsetAsync(cursor.get(), 0, 4 * sizeof(int32_t), s));
   if (total > 0) {
     ::dcd::count_launch(), bin_scatter<<<grid_for(nv, T), T, 0, s>>>(g.rp, nv, active, d, cursor.get(), list.get());
@@ -542,11 +669,12 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
     DCD_TRY(hvals.alloc(&c->mem, hub_ctas * hub_cap));
   }
 
-  // partials of sum a^2
   const int sq_ctas = grid_for(nv, T, 4);
-  Buf<unsigned long long> part;
-  DCD_TRY(part.alloc(&c->mem, 2 * (int64_t)sq_ctas));
 
+  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_warp_tbl<W, long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)((size_t)8 * kMidCap * 12)));
+  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_warp_tbl<W, i128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)((size_t)8 * kMidCap * 12)));
   DCD_TRY_CUDA(cudaFuncSetAttribute(lm_block<W, long long, kLargeThreads>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((size_t)kLargeCap * 12)));
   DCD_TRY_CUDA(cudaFuncSetAttribute(lm_block<W, i128, kLargeThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -555,7 +683,7 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
   lv.m2 = c->hsc->m2;
   const bool wide = lv.m2 >= ((int64_t)1 << 31);
   const int32_t* lst = list.get();
-  const size_t mid_smem = (size_t)kMidCap * 12, large_smem = (size_t)kLargeCap * 12;
+  const size_t mid_smem = (size_t)8 * kMidCap * 12, large_smem = (size_t)kLargeCap * 12;
 
   for (;;) {
     const int32_t iter = (int32_t)out->passes;
@@ -565,8 +693,8 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
     if (cnt[0])                                                                                                    \
       ::dcd::count_launch(), lm_warp<W, ST><<<grid_for(cnt[0] * 32, T, 16), T, 0, s>>>(lv, lst, cnt[0], prop.get());                      \
     if (cnt[1])                                                                                                    \
-      ::dcd::count_launch(), lm_block<W, ST, kMidThreads><<<grid_for(cnt[1] * kMidThreads, kMidThreads, 32), kMidThreads, mid_smem, s>>>( \
-          lv, lst + cnt[0], cnt[1], prop.get() + cnt[0], nullptr, nullptr, 0);                                    \
+      ::dcd::count_launch(), lm_warp_tbl<W, ST><<<grid_for(cnt[1] * 32, T, 4), T, mid_smem, s>>>(                  \
+          lv, lst + cnt[0], cnt[1], prop.get() + cnt[0]);                                                          \
     if (cnt[2])                                                                                                    \
       ::dcd::count_launch(), lm_block<W, ST, kLargeThreads><<<(unsigned)(cnt[2] < 2 * c->sms ? cnt[2] : 2 * c->sms), kLargeThreads,      \
                                        large_smem, s>>>(lv, lst + cnt[0] + cnt[1], cnt[2],                         \
@@ -582,17 +710,23 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
     DCD_LAUNCH_CHECK();
     DCD_TRY_CUDA(cudaEventRecord(c->ev[3], s));
     DCD_TRY_CUDA(cudaMemsetAsync(moved_cnt.get(), 0, sizeof(int32_t), s));
-    DCD_TRY_CUDA(cudaMemsetAsync(&d->in_delta, 0, sizeof(int64_t), s));
+    DCD_TRY_CUDA(cudaMemsetAsync(moved_big_cnt.get(), 0, sizeof(int32_t), s));
+    DCD_TRY_CUDA(cudaMemsetAsync(&d->in_delta, 0, 3 * sizeof(int64_t), s));  // in_delta, sq_lo, sq_hi
     if (total) {
-      ::dcd::count_launch(), lm_apply<<<grid_for(total, T), T, 0, s>>>(lst, total, prop.get(), L, kbuf.get(),
-                                                  (unsigned long long*)a.get(), size.get(), Lprev.get(), mvit.get(),
-                                                  iter, moved.get(), moved_cnt.get());
-      ::dcd::count_launch(), lm_delta_in<W><<<grid_for(total * 32, T, 16), T, 0, s>>>(lv, moved.get(), moved_cnt.get(), Lprev.get(),
-                                                               mvit.get(), iter, (unsigned long long*)&d->in_delta);
+      ::dcd::count_launch(), lm_apply<<<grid_for(total, T), T, 0, s>>>(
+          lst, total, cnt[0] + cnt[1], prop.get(), L, kbuf.get(), (unsigned long long*)a.get(), size.get(),
+          Lprev.get(), mvit.get(), iter, moved.get(), moved_cnt.get(), moved_big.get(), moved_big_cnt.get());
+      if (cnt[0] + cnt[1])
+        ::dcd::count_launch(), lm_delta_in<W><<<grid_for((cnt[0] + cnt[1]) * 32, T, 16), T, 0, s>>>(
+            lv, moved.get(), moved_cnt.get(), Lprev.get(), mvit.get(), iter, (unsigned long long*)&d->in_delta);
+      if (cnt[2] + cnt[3])
+        ::dcd::count_launch(), lm_delta_in_block<W><<<grid_for((cnt[2] + cnt[3]) * T, T, 4), T, 0, s>>>(
+            lv, moved_big.get(), moved_big_cnt.get(), Lprev.get(), mvit.get(), iter,
+            (unsigned long long*)&d->in_delta);
     }
-    ::dcd::count_launch(), sumsq_partial<<<sq_ctas, T, 0, s>>>(a.get(), nv, part.get());
-    ::dcd::count_launch(), lm_decide<<<1, 32, 0, s>>>(d, part.get(), sq_ctas, 1, moved_cnt.get(), iter + 1, c->cfg.max_iters,
-                               c->cfg.tau_inv);
+    ::dcd::count_launch(), sumsq_acc<<<sq_ctas, T, 0, s>>>(a.get(), nv, (unsigned long long*)&d->sq_lo);
+    ::dcd::count_launch(), lm_decide<<<1, 32, 0, s>>>(d, 1, moved_cnt.get(), moved_big_cnt.get(), iter + 1,
+                                                       c->cfg.max_iters, c->cfg.tau_inv);
     DCD_LAUNCH_CHECK();
     DCD_TRY_CUDA(cudaEventRecord(c->ev[4], s));
     DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
@@ -725,14 +859,10 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
   DCD_TRY(comp.alloc(&c->mem, n0));
   DCD_TRY(community_sums(c, n0, labels0, k0.get(), a.get(), size.get()));
   ::dcd::count_launch(), fill_iota<<<grid_for(n0, T), T, 0, s>>>(comp.get(), n0);
-  {
-    const int sq_ctas = grid_for(n0, T, 4);
-    Buf<unsigned long long> part;
-    DCD_TRY(part.alloc(&c->mem, 2 * (int64_t)sq_ctas));
-    ::dcd::count_launch(), sumsq_partial<<<sq_ctas, T, 0, s>>>(a.get(), n0, part.get());
-    ::dcd::count_launch(), lm_decide<<<1, 32, 0, s>>>(d, part.get(), sq_ctas, 0, nullptr, 0, 0, tau);
-    DCD_LAUNCH_CHECK();
-  }
+  DCD_TRY_CUDA(cudaMemsetAsync(&d->sq_lo, 0, 2 * sizeof(int64_t), s));
+  ::dcd::count_launch(), sumsq_acc<<<grid_for(n0, T, 4), T, 0, s>>>(a.get(), n0, (unsigned long long*)&d->sq_lo);
+  ::dcd::count_launch(), lm_decide<<<1, 32, 0, s>>>(d, 0, nullptr, nullptr, 0, 0, tau);
+  DCD_LAUNCH_CHECK();
   DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
   DCD_TRY_CUDA(cudaStreamSynchronize(s));
 

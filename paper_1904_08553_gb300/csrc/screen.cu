@@ -11,6 +11,14 @@
 //     edge was in G_{t-1}: mark i and j; if C(i) = C(j) also mark Gamma(i).
 // R_t = marked vertices plus the members of flagged communities.  Screening
 // changes no label.
+//
+// GPU schedule (same decisions, reordered work):
+//   A  per source: aggregate row i by community, pick j*, gain1; deletes.
+//   B  sources with gain1 > 0 sorted by j* (radix sort), grouped.
+//   C  per distinct j*: aggregate row j* once, then gain2 for every source of
+//      the group (a hub chosen as j* by many sources is read once, not once
+//      per source).
+//   D  per source: mark Gamma(i), i, j*, flag C(j*).
 #include "agg.cuh"
 #include "prims.cuh"
 #include "state.cuh"
@@ -34,6 +42,11 @@ struct SV {
   int64_t m2;
   uint8_t* mark;
   uint8_t* cflag;
+  // phase A outputs / phase C inputs, indexed by position in the source list
+  const int32_t* src;
+  int32_t* jstar;
+  long long* g1;   // two words per source (low, high) of gain1
+  uint8_t* flags;  // bit0: intra-community delete (mark Gamma(i)); bit1: winner
 };
 
 // (S, D, j) order of the j* choice: larger gain, then smaller C(j), then smaller j.
@@ -57,82 +70,138 @@ __device__ __forceinline__ void warp_argmax3(ST& S, int32_t& D, int32_t& J) {
   }
 }
 
-// gain2 = S(j* -> C(i)) from one scan of row j*: weights into C(i) and into
-// C(j*) without j*'s self entries.  Returns the two sums through the warp.
-__device__ __forceinline__ void row_two_sums(const SV& g, int32_t j, int32_t Ci, int32_t Cj, int64_t* e_i,
-                                             int64_t* e_j, int tid, int nthreads) {
-  int64_t s1 = 0, s2 = 0;
-  const int64_t b = g.rp[j], e1 = g.rp[j + 1];
-  for (int64_t e = b + tid; e < e1; e += nthreads) {
-    const int32_t y = g.col[e];
-    if (y == j) continue;
-    const int32_t ly = g.L[y];
-    if (ly == Ci) s1 += g.w[e];
-    if (ly == Cj) s2 += g.w[e];
-  }
-  *e_i = s1;
-  *e_j = s2;
+__device__ __forceinline__ void st_gain(long long* p, long long x) {
+  p[0] = x;
+  p[1] = x < 0 ? -1 : 0;
 }
-
-__device__ __forceinline__ void mark_row(const SV& g, int32_t u, int tid, int nthreads) {
-  const int64_t b = g.rp[u], e1 = g.rp[u + 1];
-  for (int64_t e = b + tid; e < e1; e += nthreads) g.mark[g.col[e]] = 1;
+__device__ __forceinline__ void st_gain(long long* p, i128 x) {
+  p[0] = (long long)(unsigned long long)x;
+  p[1] = (long long)(unsigned long long)((unsigned __int128)x >> 64);
 }
-
-// ---- one warp per source of degree <= 32 in G_t ----
 template <typename ST>
-__global__ void __launch_bounds__(256) screen_warp(SV g, const int32_t* __restrict__ src, int64_t cnt) {
+__device__ __forceinline__ ST ld_gain(const long long* p);
+template <>
+__device__ __forceinline__ long long ld_gain<long long>(const long long* p) {
+  return p[0];
+}
+template <>
+__device__ __forceinline__ i128 ld_gain<i128>(const long long* p) {
+  return (i128)(((unsigned __int128)(unsigned long long)p[1] << 64) | (unsigned long long)p[0]);
+}
+
+// ---- row aggregation helpers ----
+
+// Lanes of one warp hold row v (degree <= 32), grouped by community.
+struct LaneRow {
+  int32_t lab;
+  int64_t e;
+  unsigned leaders;
+};
+
+__device__ __forceinline__ LaneRow lane_row(const SV& g, int32_t v) {
+  const int lane = lane_id();
+  const int64_t b = g.rp[v];
+  const int d = (int)(g.rp[v + 1] - b);
+  bool valid = lane < d;
+  const int32_t y = valid ? g.col[b + lane] : -1;
+  valid = valid && y != v;
+  LaneRow r;
+  r.lab = valid ? g.L[y] : -1;
+  const int32_t wt = valid ? g.w[b + lane] : 0;
+  const unsigned peers = __match_any_sync(0xffffffffu, r.lab);
+  r.e = group_sum_exact(peers, wt);
+  r.leaders = __ballot_sync(0xffffffffu, valid && (int)(__ffs(peers) - 1) == lane);
+  return r;
+}
+
+// Weight from the row into community D (whole warp calls; D may differ per lane).
+__device__ __forceinline__ int64_t lane_get(const LaneRow& r, int32_t D) {
+  int64_t out = 0;
+  for (unsigned lm = r.leaders; lm; lm &= lm - 1) {
+    const int l = __ffs(lm) - 1;
+    const int32_t ll = __shfl_sync(0xffffffffu, r.lab, l);
+    const int64_t el = __shfl_sync(0xffffffffu, r.e, l);
+    if (ll == D) out = el;
+  }
+  return out;
+}
+
+// Row v aggregated into a table by NT cooperating threads (tid in [0, NT)).
+// The caller synchronises (warp or CTA) before and after.
+__device__ __forceinline__ void table_clear(int32_t* keys, unsigned long long* vals, uint32_t cap, int tid, int NT) {
+  for (uint32_t s = tid; s < cap; s += NT) {
+    keys[s] = -1;
+    vals[s] = 0;
+  }
+}
+
+__device__ __forceinline__ void table_fill(const SV& g, int32_t v, int32_t* keys, unsigned long long* vals,
+                                           uint32_t mask, int tid, int NT) {
+  const int64_t b = g.rp[v];
+  const int64_t d = g.rp[v + 1] - b;
+  for (int64_t e0 = 0; e0 < d; e0 += NT) {
+    const int64_t e = e0 + tid;
+    bool valid = e < d;
+    const int32_t y = valid ? g.col[b + e] : -1;
+    valid = valid && y != v;
+    const int32_t lab = valid ? g.L[y] : -1;
+    const int32_t wt = valid ? g.w[b + e] : 0;
+    const unsigned peers = __match_any_sync(0xffffffffu, lab);
+    const int64_t sum = group_sum_exact(peers, wt);
+    if (valid && (int)(__ffs(peers) - 1) == (int)lane_id()) tbl_add(keys, vals, mask, lab, (unsigned long long)sum);
+  }
+}
+
+// Deleted pairs of source u: mark the endpoints; return whether one of them
+// is an intra-community delete (then Gamma(u) is marked in phase D).
+__device__ __forceinline__ bool scan_deletes(const SV& g, int32_t u, int64_t p0, int64_t p1, int tid, int NT,
+                                             bool* has_ins) {
+  const int32_t C = g.L[u];
+  bool intra = false, ins = false;
+  for (int64_t q = p0 + tid; q < p1; q += NT) {
+    const uint8_t f = g.pflag[q];
+    ins |= (f & kPairIns) != 0;
+    if ((f & kPairDel) && (f & kPairPresent)) {
+      const int32_t j = (int32_t)(g.pkey[q] & 0xffffffffu);
+      g.mark[j] = 1;
+      g.mark[u] = 1;
+      intra |= g.L[j] == C;
+    }
+  }
+  *has_ins = ins;
+  return intra;
+}
+
+// ---- phase A: j* and gain1 per source ----
+
+// Sources of degree <= 32: one warp, lanes hold the row.
+template <typename ST>
+__global__ void __launch_bounds__(256) scr_a_warp(SV g, int64_t off, int64_t cnt) {
   const int lane = lane_id();
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < cnt; i += nw) {
-    const int32_t u = src[i];
+    const int64_t idx = off + i;
+    const int32_t u = g.src[idx];
     const int32_t C = g.L[u];
     const int64_t p0 = g.pair_ptr[u], p1 = g.pair_ptr[u + 1];
-    bool intra = false, has_ins = false;
-    for (int64_t q = p0 + lane; q < p1; q += 32) {
-      const uint8_t f = g.pflag[q];
-      has_ins |= (f & kPairIns) != 0;
-      if ((f & kPairDel) && (f & kPairPresent)) {
-        const int32_t j = (int32_t)(g.pkey[q] & 0xffffffffu);
-        g.mark[j] = 1;
-        g.mark[u] = 1;
-        intra |= g.L[j] == C;
-      }
-    }
-    intra = __any_sync(0xffffffffu, intra);
+    bool has_ins;
+    const bool intra = __any_sync(0xffffffffu, scan_deletes(g, u, p0, p1, lane, 32, &has_ins));
     has_ins = __any_sync(0xffffffffu, has_ins);
-    bool mark_gamma = intra;
+    int32_t J = -1;
+    ST S = 0;
     if (has_ins) {
-      // lanes hold row u (degree <= 32): group by label
-      const int64_t b = g.rp[u];
-      const int d = (int)(g.rp[u + 1] - b);
-      bool valid = lane < d;
-      const int32_t y = valid ? g.col[b + lane] : -1;
-      valid = valid && y != u;
-      const int32_t lab = valid ? g.L[y] : -1;
-      const int32_t wt = valid ? g.w[b + lane] : 0;
-      const unsigned peers = __match_any_sync(0xffffffffu, lab);
-      const int64_t e = group_sum_exact(peers, wt);
-      const bool leader = valid && (int)(__ffs(peers) - 1) == lane;
-      const unsigned leaders = __ballot_sync(0xffffffffu, leader);
-      const unsigned cm = __ballot_sync(0xffffffffu, leader && lab == C);
-      const int64_t eCx = __shfl_sync(0xffffffffu, e, cm ? __ffs(cm) - 1 : 0);
-      const int64_t eC = cm ? eCx : 0;
+      const LaneRow r = lane_row(g, u);
+      const int64_t eC = lane_get(r, C);
       const int64_t ku = g.k[u], aC = g.a[C];
-      ST S = gain_lowest<ST>();
-      int32_t D = INT_MAX, J = INT_MAX;
+      int32_t D = INT_MAX;
+      J = INT_MAX;
+      S = gain_lowest<ST>();
       for (int64_t q0 = p0; q0 < p1; q0 += 32) {
         const int64_t q = q0 + lane;
         const bool sink = q < p1 && (g.pflag[q] & kPairIns);
         const int32_t j = sink ? (int32_t)(g.pkey[q] & 0xffffffffu) : -1;
-        const int32_t Dj = sink ? g.L[j] : -1;
-        int64_t eD = 0;
-        for (unsigned lm = leaders; lm; lm &= lm - 1) {
-          const int l = __ffs(lm) - 1;
-          const int32_t ll = __shfl_sync(0xffffffffu, lab, l);
-          const int64_t el = __shfl_sync(0xffffffffu, e, l);
-          if (ll == Dj) eD = el;
-        }
+        const int32_t Dj = sink ? g.L[j] : -2;
+        const int64_t eD = lane_get(r, Dj);
         if (sink) {
           const ST x = (Dj == C) ? ST(0) : gain<ST>(g.m2, ku, eD, eC, g.a[Dj], aC);
           if (better3(x, Dj, j, S, D, J)) {
@@ -143,66 +212,94 @@ __global__ void __launch_bounds__(256) screen_warp(SV g, const int32_t* __restri
         }
       }
       warp_argmax3(S, D, J);
-      // gain2 = S(j* -> C(i))
-      int64_t e_i = 0, e_j = 0;
-      row_two_sums(g, J, C, D, &e_i, &e_j, lane, 32);
-      e_i = warp_sum((long long)e_i);
-      e_j = warp_sum((long long)e_j);
-      const ST g2 = (D == C) ? ST(0) : gain<ST>(g.m2, g.k[J], e_i, e_j, aC, g.a[D]);
-      if (S >= g2 && S > 0) {
-        if (lane == 0) {
-          g.mark[u] = 1;
-          g.mark[J] = 1;
-          g.cflag[D] = 1;
-        }
-        mark_gamma = true;
-      }
     }
-    if (mark_gamma) {
-      if (lane == 0) g.mark[u] = 1;
-      mark_row(g, u, lane, 32);
+    if (lane == 0) {
+      g.jstar[idx] = J;
+      st_gain(&g.g1[2 * idx], S);
+      g.flags[idx] = intra ? 1 : 0;
     }
   }
 }
 
-// ---- one CTA per source of degree > 32: table in shared or global memory ----
+// Sources of degree 33..256: one warp with a warp-private shared table.
+template <typename ST>
+__global__ void __launch_bounds__(256) scr_a_wtbl(SV g, int64_t off, int64_t cnt) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = lane_id(), wib = threadIdx.x >> 5;
+  unsigned long long* vals = reinterpret_cast<unsigned long long*>(smem) + (size_t)wib * kMidCap;
+  int32_t* keys = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned long long*>(smem) + 8 * kMidCap) +
+                  (size_t)wib * kMidCap;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < cnt; i += nw) {
+    const int64_t idx = off + i;
+    const int32_t u = g.src[idx];
+    const int32_t C = g.L[u];
+    const int64_t p0 = g.pair_ptr[u], p1 = g.pair_ptr[u + 1];
+    bool has_ins;
+    const bool intra = __any_sync(0xffffffffu, scan_deletes(g, u, p0, p1, lane, 32, &has_ins));
+    has_ins = __any_sync(0xffffffffu, has_ins);
+    int32_t J = -1;
+    ST S = 0;
+    if (has_ins) {
+      const uint32_t cap = table_cap(g.rp[u + 1] - g.rp[u]), mask = cap - 1;
+      table_clear(keys, vals, cap, lane, 32);
+      __syncwarp();
+      table_fill(g, u, keys, vals, mask, lane, 32);
+      __syncwarp();
+      const int64_t eC = tbl_get(keys, vals, mask, C);
+      const int64_t ku = g.k[u], aC = g.a[C];
+      int32_t D = INT_MAX;
+      J = INT_MAX;
+      S = gain_lowest<ST>();
+      for (int64_t q = p0 + lane; q < p1; q += 32) {
+        if (!(g.pflag[q] & kPairIns)) continue;
+        const int32_t j = (int32_t)(g.pkey[q] & 0xffffffffu);
+        const int32_t Dj = g.L[j];
+        const ST x = (Dj == C) ? ST(0) : gain<ST>(g.m2, ku, tbl_get(keys, vals, mask, Dj), eC, g.a[Dj], aC);
+        if (better3(x, Dj, j, S, D, J)) {
+          S = x;
+          D = Dj;
+          J = j;
+        }
+      }
+      warp_argmax3(S, D, J);
+      __syncwarp();
+    }
+    if (lane == 0) {
+      g.jstar[idx] = J;
+      st_gain(&g.g1[2 * idx], S);
+      g.flags[idx] = intra ? 1 : 0;
+    }
+  }
+}
+
+// Sources above 256 entries: one CTA, table in shared memory (<= 4096
+// entries) or in a per-CTA region of global memory.
 template <typename ST, int THREADS>
-__global__ void __launch_bounds__(THREADS) screen_block(SV g, const int32_t* __restrict__ src, int64_t cnt,
-                                                        int32_t* __restrict__ gkeys,
-                                                        unsigned long long* __restrict__ gvals, int64_t gcap) {
+__global__ void __launch_bounds__(THREADS) scr_a_block(SV g, int64_t off, int64_t cnt, int32_t* __restrict__ gkeys,
+                                                       unsigned long long* __restrict__ gvals, int64_t gcap) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NW = THREADS / 32;
   __shared__ ST redS[NW];
   __shared__ int32_t redD[NW], redJ[NW];
-  __shared__ long long red1[NW], red2[NW];
   __shared__ int s_flags;
-  __shared__ long long s_eC;
   const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5;
   for (int64_t i = blockIdx.x; i < cnt; i += gridDim.x) {
-    const int32_t u = src[i];
+    const int64_t idx = off + i;
+    const int32_t u = g.src[idx];
     const int32_t C = g.L[u];
     const int64_t p0 = g.pair_ptr[u], p1 = g.pair_ptr[u + 1];
     if (tid == 0) s_flags = 0;
     __syncthreads();
-    int fl = 0;
-    for (int64_t q = p0 + tid; q < p1; q += THREADS) {
-      const uint8_t f = g.pflag[q];
-      if (f & kPairIns) fl |= 2;
-      if ((f & kPairDel) && (f & kPairPresent)) {
-        const int32_t j = (int32_t)(g.pkey[q] & 0xffffffffu);
-        g.mark[j] = 1;
-        g.mark[u] = 1;
-        if (g.L[j] == C) fl |= 1;
-      }
-    }
-    if (fl) atomicOr(&s_flags, fl);
+    bool has_ins;
+    const bool intra = scan_deletes(g, u, p0, p1, tid, THREADS, &has_ins);
+    if (intra || has_ins) atomicOr(&s_flags, (intra ? 1 : 0) | (has_ins ? 2 : 0));
     __syncthreads();
     const int flags = s_flags;
-    bool mark_gamma = flags & 1;
+    int32_t J = -1;
+    ST S = 0;
     if (flags & 2) {
-      const int64_t b = g.rp[u];
-      const int64_t d = g.rp[u + 1] - b;
-      const uint32_t cap = table_cap(d), mask = cap - 1;
+      const uint32_t cap = table_cap(g.rp[u + 1] - g.rp[u]), mask = cap - 1;
       int32_t* keys;
       unsigned long long* vals;
       if (gcap == 0) {
@@ -212,28 +309,15 @@ __global__ void __launch_bounds__(THREADS) screen_block(SV g, const int32_t* __r
         keys = gkeys + (int64_t)blockIdx.x * gcap;
         vals = gvals + (int64_t)blockIdx.x * gcap;
       }
-      for (uint32_t s = tid; s < cap; s += THREADS) {
-        keys[s] = -1;
-        vals[s] = 0;
-      }
+      table_clear(keys, vals, cap, tid, THREADS);
       __syncthreads();
-      for (int64_t e0 = 0; e0 < d; e0 += THREADS) {
-        const int64_t e = e0 + tid;
-        bool valid = e < d;
-        const int32_t y = valid ? g.col[b + e] : -1;
-        valid = valid && y != u;
-        const int32_t lab = valid ? g.L[y] : -1;
-        const int32_t wt = valid ? g.w[b + e] : 0;
-        const unsigned peers = __match_any_sync(0xffffffffu, lab);
-        const int64_t sum = group_sum_exact(peers, wt);
-        if (valid && (int)(__ffs(peers) - 1) == lane) tbl_add(keys, vals, mask, lab, (unsigned long long)sum);
-      }
+      table_fill(g, u, keys, vals, mask, tid, THREADS);
       __syncthreads();
-      if (tid == 0) s_eC = tbl_get(keys, vals, mask, C);
-      __syncthreads();
-      const int64_t eC = s_eC, ku = g.k[u], aC = g.a[C];
-      ST S = gain_lowest<ST>();
-      int32_t D = INT_MAX, J = INT_MAX;
+      const int64_t eC = tbl_get(keys, vals, mask, C);
+      const int64_t ku = g.k[u], aC = g.a[C];
+      int32_t D = INT_MAX;
+      J = INT_MAX;
+      S = gain_lowest<ST>();
       for (int64_t q = p0 + tid; q < p1; q += THREADS) {
         if (!(g.pflag[q] & kPairIns)) continue;
         const int32_t j = (int32_t)(g.pkey[q] & 0xffffffffu);
@@ -255,42 +339,197 @@ __global__ void __launch_bounds__(THREADS) screen_block(SV g, const int32_t* __r
       S = lane < NW ? redS[lane] : gain_lowest<ST>();
       D = lane < NW ? redD[lane] : INT_MAX;
       J = lane < NW ? redJ[lane] : INT_MAX;
-      warp_argmax3(S, D, J);  // every warp computes the same result
-      int64_t e_i = 0, e_j = 0;
-      row_two_sums(g, J, C, D, &e_i, &e_j, tid, THREADS);
-      e_i = warp_sum((long long)e_i);
-      e_j = warp_sum((long long)e_j);
-      if (lane == 0) {
-        red1[wid] = e_i;
-        red2[wid] = e_j;
-      }
-      __syncthreads();
-      e_i = lane < NW ? red1[lane] : 0;
-      e_j = lane < NW ? red2[lane] : 0;
-      e_i = warp_sum((long long)e_i);
-      e_j = warp_sum((long long)e_j);
-      const ST g2 = (D == C) ? ST(0) : gain<ST>(g.m2, g.k[J], e_i, e_j, aC, g.a[D]);
-      if (S >= g2 && S > 0) {
-        if (tid == 0) {
-          g.mark[u] = 1;
-          g.mark[J] = 1;
-          g.cflag[D] = 1;
-        }
-        mark_gamma = true;
-      }
+      warp_argmax3(S, D, J);
     }
-    if (mark_gamma) {
-      if (tid == 0) g.mark[u] = 1;
-      mark_row(g, u, tid, THREADS);
+    if (tid == 0) {
+      g.jstar[idx] = J;
+      st_gain(&g.g1[2 * idx], S);
+      g.flags[idx] = (flags & 1) ? 1 : 0;
     }
     __syncthreads();
   }
 }
 
+// ---- phase B: group the sources with gain1 > 0 by j* ----
+
+template <typename ST>
+__global__ void cand_keys(SV g, int64_t nsrc, int64_t n, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nsrc; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t j = g.jstar[i];
+    const bool cand = j >= 0 && ld_gain<ST>(&g.g1[2 * i]) > 0;
+    keys[i] = cand ? (uint64_t)j : (uint64_t)n;
+    vals[i] = (uint32_t)i;
+  }
+}
+
+// group heads of candidate keys (< n) -> group start offsets (compacted)
+__global__ void group_heads(const uint64_t* __restrict__ keys, int64_t m, int64_t n, int32_t* __restrict__ head) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+    head[e] = (keys[e] < (uint64_t)n && (e == 0 || keys[e] != keys[e - 1])) ? 1 : 0;
+}
+
+__global__ void group_starts(const int32_t* __restrict__ head, const int32_t* __restrict__ hpos, int64_t m,
+                             int32_t* __restrict__ gstart) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+    if (head[e]) gstart[hpos[e]] = (int32_t)e;
+}
+
+// lower bound of the sentinel key n in the sorted keys (one warp)
+__global__ void close_groups(const uint64_t* __restrict__ keys, int64_t m, int64_t n, int32_t* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  int64_t lo = 0, hi = m;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (keys[mid] < (uint64_t)n) lo = mid + 1; else hi = mid;
+  }
+  *out = (int32_t)lo;
+}
+
+// groups binned by the degree of their j*
+__global__ void group_bins(const uint64_t* __restrict__ keys, const int32_t* __restrict__ gstart, int64_t ng,
+                           const int64_t* __restrict__ rp, int32_t* __restrict__ cursor, int32_t* __restrict__ lists,
+                           int64_t cap_per_bin, unsigned long long* __restrict__ hub_max) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (blockIdx.x * (int64_t)blockDim.x) + (threadIdx.x & ~31); base < ng; base += stride) {
+    const int64_t gi = base + lane_id();
+    int bin = -1;
+    if (gi < ng) {
+      const int64_t j = (int64_t)keys[gstart[gi]];
+      const int64_t deg = rp[j + 1] - rp[j];
+      bin = deg <= kBinWarpMax ? 0 : deg <= kBinMidMax ? 1 : deg <= kBinLargeMax ? 2 : 3;
+      if (bin == 3) atomicMax(hub_max, (unsigned long long)deg);
+    }
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+      const unsigned bal = __ballot_sync(0xffffffffu, bin == b);
+      if (!bal) continue;
+      int32_t slot = 0;
+      if (lane_id() == 0) slot = atomicAdd(&cursor[b], __popc(bal));
+      slot = __shfl_sync(0xffffffffu, slot, 0);
+      if (bin == b) lists[b * cap_per_bin + slot + __popc(bal & lanemask_lt())] = (int32_t)gi;
+    }
+  }
+}
+
+// ---- phase C: gain2 per source, one aggregation of row j* per group ----
+
+struct GroupView {
+  const uint64_t* keys;  // sorted candidate keys (j*)
+  const uint32_t* vals;  // source-list positions in key order
+  const int32_t* gstart; // ng + 1 group starts
+  const int32_t* glist;  // groups of this bin
+};
+
+template <typename ST>
+__device__ __forceinline__ void decide(const SV& g, int64_t idx, int32_t j, int64_t e1, int64_t e2) {
+  const int32_t i = g.src[idx];
+  const int32_t Ci = g.L[i], Cj = g.L[j];
+  const ST g2 = (Cj == Ci) ? ST(0) : gain<ST>(g.m2, g.k[j], e1, e2, g.a[Ci], g.a[Cj]);
+  if (ld_gain<ST>(&g.g1[2 * idx]) >= g2) g.flags[idx] |= 2;
+}
+
+template <typename ST>
+__global__ void __launch_bounds__(256) scr_c_warp(SV g, GroupView gv, int64_t cnt) {
+  const int lane = lane_id();
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < cnt; i += nw) {
+    const int32_t gi = gv.glist[i];
+    const int64_t m0 = gv.gstart[gi], m1 = gv.gstart[gi + 1];
+    const int32_t j = (int32_t)gv.keys[m0];
+    const LaneRow r = lane_row(g, j);
+    const int64_t e2 = lane_get(r, g.L[j]);
+    for (int64_t q0 = m0; q0 < m1; q0 += 32) {
+      const int64_t q = q0 + lane;
+      const int64_t idx = q < m1 ? (int64_t)gv.vals[q] : -1;
+      const int32_t Ci = idx >= 0 ? g.L[g.src[idx]] : -2;
+      const int64_t e1 = lane_get(r, Ci);
+      if (idx >= 0) decide<ST>(g, idx, j, e1, e2);
+    }
+  }
+}
+
+template <typename ST>
+__global__ void __launch_bounds__(256) scr_c_wtbl(SV g, GroupView gv, int64_t cnt) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = lane_id(), wib = threadIdx.x >> 5;
+  unsigned long long* vals = reinterpret_cast<unsigned long long*>(smem) + (size_t)wib * kMidCap;
+  int32_t* keys = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned long long*>(smem) + 8 * kMidCap) +
+                  (size_t)wib * kMidCap;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < cnt; i += nw) {
+    const int32_t gi = gv.glist[i];
+    const int64_t m0 = gv.gstart[gi], m1 = gv.gstart[gi + 1];
+    const int32_t j = (int32_t)gv.keys[m0];
+    const uint32_t cap = table_cap(g.rp[j + 1] - g.rp[j]), mask = cap - 1;
+    table_clear(keys, vals, cap, lane, 32);
+    __syncwarp();
+    table_fill(g, j, keys, vals, mask, lane, 32);
+    __syncwarp();
+    const int64_t e2 = tbl_get(keys, vals, mask, g.L[j]);
+    for (int64_t q = m0 + lane; q < m1; q += 32) {
+      const int64_t idx = gv.vals[q];
+      decide<ST>(g, idx, j, tbl_get(keys, vals, mask, g.L[g.src[idx]]), e2);
+    }
+    __syncwarp();
+  }
+}
+
+template <typename ST, int THREADS>
+__global__ void __launch_bounds__(THREADS) scr_c_block(SV g, GroupView gv, int64_t cnt, int32_t* __restrict__ gkeys,
+                                                       unsigned long long* __restrict__ gvals, int64_t gcap) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tid = threadIdx.x;
+  for (int64_t i = blockIdx.x; i < cnt; i += gridDim.x) {
+    const int32_t gi = gv.glist[i];
+    const int64_t m0 = gv.gstart[gi], m1 = gv.gstart[gi + 1];
+    const int32_t j = (int32_t)gv.keys[m0];
+    const uint32_t cap = table_cap(g.rp[j + 1] - g.rp[j]), mask = cap - 1;
+    int32_t* keys;
+    unsigned long long* vals;
+    if (gcap == 0) {
+      vals = reinterpret_cast<unsigned long long*>(smem);
+      keys = reinterpret_cast<int32_t*>(smem + (size_t)cap * sizeof(unsigned long long));
+    } else {
+      keys = gkeys + (int64_t)blockIdx.x * gcap;
+      vals = gvals + (int64_t)blockIdx.x * gcap;
+    }
+    table_clear(keys, vals, cap, tid, THREADS);
+    __syncthreads();
+    table_fill(g, j, keys, vals, mask, tid, THREADS);
+    __syncthreads();
+    const int64_t e2 = tbl_get(keys, vals, mask, g.L[j]);
+    for (int64_t q = m0 + tid; q < m1; q += THREADS) {
+      const int64_t idx = gv.vals[q];
+      decide<ST>(g, idx, j, tbl_get(keys, vals, mask, g.L[g.src[idx]]), e2);
+    }
+    __syncthreads();
+  }
+}
+
+// ---- phase D: marks ----
+__global__ void __launch_bounds__(256) scr_mark(SV g, int64_t nsrc) {
+  const int lane = lane_id();
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t idx = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; idx < nsrc; idx += nw) {
+    const uint8_t f = g.flags[idx];
+    if (!f) continue;
+    const int32_t u = g.src[idx];
+    if (lane == 0) {
+      g.mark[u] = 1;
+      if (f & 2) {
+        const int32_t j = g.jstar[idx];
+        g.mark[j] = 1;
+        g.cflag[g.L[j]] = 1;
+      }
+    }
+    const int64_t e1 = g.rp[u + 1];
+    for (int64_t e = g.rp[u] + lane; e < e1; e += 32) g.mark[g.col[e]] = 1;
+  }
+}
+
 // Sources (vertices with at least one pair) binned by their degree in G_t.
 __global__ void src_bins(int64_t n, const int64_t* __restrict__ pair_ptr, const int64_t* __restrict__ rp,
-                         int32_t* __restrict__ cursor, int32_t* __restrict__ lst_small,
-                         int32_t* __restrict__ lst_mid, int32_t* __restrict__ lst_hub,
+                         int32_t* __restrict__ cursor, int32_t* __restrict__ lists, int64_t cap_per_bin,
                          unsigned long long* __restrict__ hub_max) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (blockIdx.x * (int64_t)blockDim.x) + (threadIdx.x & ~31); base < n; base += stride) {
@@ -298,19 +537,32 @@ __global__ void src_bins(int64_t n, const int64_t* __restrict__ pair_ptr, const 
     int bin = -1;
     if (v < n && pair_ptr[v + 1] > pair_ptr[v]) {
       const int64_t deg = rp[v + 1] - rp[v];
-      bin = deg <= kBinWarpMax ? 0 : deg <= kBinLargeMax ? 1 : 2;
-      if (bin == 2) atomicMax(hub_max, (unsigned long long)deg);
+      bin = deg <= kBinWarpMax ? 0 : deg <= kBinMidMax ? 1 : deg <= kBinLargeMax ? 2 : 3;
+      if (bin == 3) atomicMax(hub_max, (unsigned long long)deg);
     }
 #pragma unroll
-    for (int b = 0; b < 3; b++) {
+    for (int b = 0; b < 4; b++) {
       const unsigned bal = __ballot_sync(0xffffffffu, bin == b);
       if (!bal) continue;
       int32_t slot = 0;
       if (lane_id() == 0) slot = atomicAdd(&cursor[b], __popc(bal));
       slot = __shfl_sync(0xffffffffu, slot, 0);
-      int32_t* lst = b == 0 ? lst_small : b == 1 ? lst_mid : lst_hub;
-      if (bin == b) lst[slot + __popc(bal & lanemask_lt())] = (int32_t)v;
+      if (bin == b) lists[b * cap_per_bin + slot + __popc(bal & lanemask_lt())] = (int32_t)v;
     }
+  }
+}
+
+// Packs the four per-bin segments into one list (bin order).
+__global__ void pack_bins(const int32_t* __restrict__ lists, int64_t cap_per_bin, int64_t c0, int64_t c1, int64_t c2,
+                          int64_t c3, int32_t* __restrict__ out) {
+  const int64_t tot = c0 + c1 + c2 + c3;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
+    int b = 0;
+    int64_t r = i;
+    if (r >= c0) { r -= c0; b = 1;
+      if (r >= c1) { r -= c1; b = 2;
+        if (r >= c2) { r -= c2; b = 3; } } }
+    out[i] = lists[b * cap_per_bin + r];
   }
 }
 
@@ -327,6 +579,124 @@ __global__ void build_rset(int64_t n, const uint8_t* __restrict__ mark, const ui
   if (lane_id() == 0 && c) atomicAdd(count, c);
 }
 
+int hub_tables(dcd_ctx* c, int64_t count, int64_t maxdeg, Buf<int32_t>& k, Buf<unsigned long long>& v,
+               int64_t* cap, int64_t* ctas) {
+  *cap = 0;
+  *ctas = 0;
+  if (!count) return DCD_OK;
+  *cap = table_cap(maxdeg);
+  int64_t n = ((int64_t)1 << 30) / (*cap * 12);
+  if (n < 1) n = 1;
+  if (n > count) n = count;
+  if (n > 4 * (int64_t)c->sms) n = 4 * (int64_t)c->sms;
+  *ctas = n;
+  DCD_TRY(k.alloc(&c->mem, n * *cap));
+  DCD_TRY(v.alloc(&c->mem, n * *cap));
+  return DCD_OK;
+}
+
+template <typename ST>
+int screen_impl(dcd_ctx* c, SV& sv, const Csr<int32_t>& g, const int64_t* cnt, int64_t hub_max, int64_t nsrc) {
+  cudaStream_t s = c->stream;
+  const int T = 256;
+  const int64_t n = g.n;
+  const size_t wsmem = (size_t)8 * kMidCap * 12, bsmem = (size_t)kLargeCap * 12;
+  DCD_TRY_CUDA(cudaFuncSetAttribute(scr_a_wtbl<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem));
+  DCD_TRY_CUDA(cudaFuncSetAttribute(scr_c_wtbl<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem));
+  DCD_TRY_CUDA(cudaFuncSetAttribute(scr_a_block<ST, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem));
+  DCD_TRY_CUDA(cudaFuncSetAttribute(scr_c_block<ST, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem));
+  const int64_t off1 = cnt[0], off2 = off1 + cnt[1], off3 = off2 + cnt[2];
+  const int sm2 = 2 * c->sms;
+
+  // ---- A ----
+  Buf<int32_t> hk;
+  Buf<unsigned long long> hv;
+  int64_t hcap, hctas;
+  DCD_TRY(hub_tables(c, cnt[3], hub_max, hk, hv, &hcap, &hctas));
+  if (cnt[0]) count_launch(), scr_a_warp<ST><<<grid_for(cnt[0] * 32, T, 16), T, 0, s>>>(sv, 0, cnt[0]);
+  if (cnt[1]) count_launch(), scr_a_wtbl<ST><<<grid_for(cnt[1] * 32, T, 4), T, wsmem, s>>>(sv, off1, cnt[1]);
+  if (cnt[2])
+    count_launch(), scr_a_block<ST, 256><<<(unsigned)(cnt[2] < sm2 ? cnt[2] : sm2), 256, bsmem, s>>>(
+                        sv, off2, cnt[2], nullptr, nullptr, 0);
+  if (cnt[3])
+    count_launch(), scr_a_block<ST, 512><<<(unsigned)hctas, 512, 0, s>>>(sv, off3, cnt[3], hk.get(), hv.get(), hcap);
+  DCD_LAUNCH_CHECK();
+
+  // ---- B ----
+  Buf<uint64_t> k0, k1;
+  Buf<uint32_t> v0, v1, stmp;
+  Buf<int32_t> head, hpos, gstart;  // gstart: ng + 1 group starts
+  DCD_TRY(k0.alloc(&c->mem, nsrc));
+  DCD_TRY(k1.alloc(&c->mem, nsrc));
+  DCD_TRY(v0.alloc(&c->mem, nsrc));
+  DCD_TRY(v1.alloc(&c->mem, nsrc));
+  DCD_TRY(head.alloc(&c->mem, nsrc + 1));
+  DCD_TRY(hpos.alloc(&c->mem, nsrc + 1));
+  DCD_TRY(stmp.alloc(&c->mem, sort_tmp_words(nsrc) + scan_tmp_count(nsrc + 1) + 64));
+  count_launch(), cand_keys<ST><<<grid_for(nsrc, T), T, 0, s>>>(sv, nsrc, n, k0.get(), v0.get());
+  DCD_LAUNCH_CHECK();
+  const int b = bits_for(n);
+  int ranges[2] = {0, b};
+  bool in1 = false;
+  DCD_TRY(sort_pairs<uint32_t>(k0.get(), v0.get(), k1.get(), v1.get(), nsrc, ranges, 1, stmp.get(), &in1, s));
+  const uint64_t* keys = in1 ? k1.get() : k0.get();
+  const uint32_t* vals = in1 ? v1.get() : v0.get();
+  count_launch(), group_heads<<<grid_for(nsrc, T), T, 0, s>>>(keys, nsrc, n, head.get());
+  DCD_LAUNCH_CHECK();
+  DCD_TRY(exclusive_scan<int32_t>(head.get(), hpos.get(), nsrc, hpos.get() + nsrc,
+                                  reinterpret_cast<int32_t*>(stmp.get()), s));
+  // number of candidates = first position with the sentinel key: count heads, then members
+  DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch, hpos.get() + nsrc, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  DCD_TRY_CUDA(cudaStreamSynchronize(s));
+  const int64_t ng = *reinterpret_cast<int32_t*>(c->hscratch);
+  if (ng > 0) {
+    DCD_TRY(gstart.alloc(&c->mem, ng + 1));
+    count_launch(), group_starts<<<grid_for(nsrc, T), T, 0, s>>>(head.get(), hpos.get(), nsrc, gstart.get());
+    DCD_LAUNCH_CHECK();
+    // end of the last group: number of candidate keys (< n)
+    Buf<int32_t> gl, gcur;
+    Buf<unsigned long long> ghub;
+    DCD_TRY(gl.alloc(&c->mem, 4 * ng));
+    DCD_TRY(gcur.alloc(&c->mem, 4));
+    DCD_TRY(ghub.alloc(&c->mem, 1));
+    DCD_TRY_CUDA(cudaMemsetAsync(gcur.get(), 0, 4 * sizeof(int32_t), s));
+    DCD_TRY_CUDA(cudaMemsetAsync(ghub.get(), 0, sizeof(unsigned long long), s));
+    count_launch(), group_bins<<<grid_for(ng, T), T, 0, s>>>(keys, gstart.get(), ng, g.rp, gcur.get(), gl.get(), ng,
+                                                             ghub.get());
+    DCD_LAUNCH_CHECK();
+    DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch, gcur.get(), 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch + 2, ghub.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    DCD_TRY_CUDA(cudaStreamSynchronize(s));
+    const int32_t* gc = reinterpret_cast<const int32_t*>(c->hscratch);
+    const int64_t gcnt[4] = {gc[0], gc[1], gc[2], gc[3]};
+    const int64_t ghubmax = c->hscratch[2];
+    // gstart[ng] = number of candidates = lower bound of the sentinel key
+    count_launch(), close_groups<<<1, 32, 0, s>>>(keys, nsrc, n, gstart.get() + ng);
+    DCD_LAUNCH_CHECK();
+    // ---- C ----
+    Buf<int32_t> ck;
+    Buf<unsigned long long> cv;
+    int64_t ccap, cctas;
+    DCD_TRY(hub_tables(c, gcnt[3], ghubmax, ck, cv, &ccap, &cctas));
+    GroupView gv{keys, vals, gstart.get(), gl.get()};
+    if (gcnt[0]) count_launch(), scr_c_warp<ST><<<grid_for(gcnt[0] * 32, T, 16), T, 0, s>>>(sv, gv, gcnt[0]);
+    gv.glist = gl.get() + ng;
+    if (gcnt[1]) count_launch(), scr_c_wtbl<ST><<<grid_for(gcnt[1] * 32, T, 4), T, wsmem, s>>>(sv, gv, gcnt[1]);
+    gv.glist = gl.get() + 2 * ng;
+    if (gcnt[2])
+      count_launch(), scr_c_block<ST, 256><<<(unsigned)(gcnt[2] < sm2 ? gcnt[2] : sm2), 256, bsmem, s>>>(
+                          sv, gv, gcnt[2], nullptr, nullptr, 0);
+    gv.glist = gl.get() + 3 * ng;
+    if (gcnt[3])
+      count_launch(), scr_c_block<ST, 512><<<(unsigned)cctas, 512, 0, s>>>(sv, gv, gcnt[3], ck.get(), cv.get(), ccap);
+    DCD_LAUNCH_CHECK();
+  }
+  // ---- D ----
+  count_launch(), scr_mark<<<grid_for(nsrc * 32, T, 16), T, 0, s>>>(sv, nsrc);
+  DCD_LAUNCH_CHECK();
+  return DCD_OK;
+}
+
 }  // namespace
 
 int screen_batch(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* labels0, const int64_t* k, const int64_t* a,
@@ -336,64 +706,46 @@ int screen_batch(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* labels0, cons
   const int64_t n = g.n;
   const int T = 256;
   Buf<uint8_t> mark, cflag;
-  Buf<int32_t> lists, cursor;
-  Buf<unsigned long long> hubmax;
   DCD_TRY(mark.alloc(&c->mem, n));
   DCD_TRY(cflag.alloc(&c->mem, n));
-  DCD_TRY(lists.alloc(&c->mem, 3 * n));
-  DCD_TRY(cursor.alloc(&c->mem, 4));
-  DCD_TRY(hubmax.alloc(&c->mem, 1));
   DCD_TRY_CUDA(cudaMemsetAsync(mark.get(), 0, n, s));
   DCD_TRY_CUDA(cudaMemsetAsync(cflag.get(), 0, n, s));
-  DCD_TRY_CUDA(cudaMemsetAsync(cursor.get(), 0, 4 * sizeof(int32_t), s));
-  DCD_TRY_CUDA(cudaMemsetAsync(hubmax.get(), 0, sizeof(unsigned long long), s));
-  int32_t* l0 = lists.get();
-  int32_t* l1 = l0 + n;
-  int32_t* l2 = l1 + n;
   if (mo.npairs > 0) {
-    ::dcd::count_launch(), src_bins<<<grid_for(n, T), T, 0, s>>>(n, mo.pair_ptr.get(), g.rp, cursor.get(), l0, l1, l2, hubmax.get());
+    Buf<int32_t> lists, cursor, src;
+    Buf<unsigned long long> hubmax;
+    DCD_TRY(lists.alloc(&c->mem, 4 * n));
+    DCD_TRY(cursor.alloc(&c->mem, 4));
+    DCD_TRY(hubmax.alloc(&c->mem, 1));
+    DCD_TRY_CUDA(cudaMemsetAsync(cursor.get(), 0, 4 * sizeof(int32_t), s));
+    DCD_TRY_CUDA(cudaMemsetAsync(hubmax.get(), 0, sizeof(unsigned long long), s));
+    count_launch(), src_bins<<<grid_for(n, T), T, 0, s>>>(n, mo.pair_ptr.get(), g.rp, cursor.get(), lists.get(), n,
+                                                          hubmax.get());
     DCD_LAUNCH_CHECK();
     DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch, cursor.get(), 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch + 2, hubmax.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     DCD_TRY_CUDA(cudaStreamSynchronize(s));
-    const int32_t* cnts = reinterpret_cast<const int32_t*>(c->hscratch);
-    const int64_t c0 = cnts[0], c1 = cnts[1], c2 = cnts[2];
+    const int32_t* cn = reinterpret_cast<const int32_t*>(c->hscratch);
+    const int64_t cnt[4] = {cn[0], cn[1], cn[2], cn[3]};
     const int64_t hub_max = c->hscratch[2];
-    SV sv{g.rp, g.col, g.w, k, labels0, a, mo.pkey.get(), mo.pflag.get(), mo.pair_ptr.get(), c->hsc->m2,
-          mark.get(), cflag.get()};
-    const bool wide = sv.m2 >= ((int64_t)1 << 31);
-    const size_t smem = (size_t)kLargeCap * 12;
-    Buf<int32_t> hkeys;
-    Buf<unsigned long long> hvals;
-    int64_t hub_cap = 0, hub_ctas = 0;
-    if (c2) {
-      hub_cap = table_cap(hub_max);
-      hub_ctas = ((int64_t)1 << 30) / (hub_cap * 12);
-      if (hub_ctas < 1) hub_ctas = 1;
-      if (hub_ctas > c2) hub_ctas = c2;
-      if (hub_ctas > 4 * (int64_t)c->sms) hub_ctas = 4 * (int64_t)c->sms;
-      DCD_TRY(hkeys.alloc(&c->mem, hub_ctas * hub_cap));
-      DCD_TRY(hvals.alloc(&c->mem, hub_ctas * hub_cap));
-    }
-#define DCD_SCREEN(ST)                                                                                           \
-  do {                                                                                                           \
-    DCD_TRY_CUDA(cudaFuncSetAttribute(screen_block<ST, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
-                                      (int)smem));                                                               \
-    if (c0) ::dcd::count_launch(), screen_warp<ST><<<grid_for(c0 * 32, T, 16), T, 0, s>>>(sv, l0, c0);                                  \
-    if (c1)                                                                                                      \
-      ::dcd::count_launch(), screen_block<ST, 256><<<(unsigned)(c1 < 2 * c->sms ? c1 : 2 * c->sms), 256, smem, s>>>(sv, l1, c1, nullptr, \
-                                                                                             nullptr, 0);        \
-    if (c2)                                                                                                      \
-      ::dcd::count_launch(), screen_block<ST, 512><<<(unsigned)hub_ctas, 512, 0, s>>>(sv, l2, c2, hkeys.get(), hvals.get(), hub_cap);   \
-  } while (0)
-    if (wide) DCD_SCREEN(i128);
-    else DCD_SCREEN(long long);
-#undef DCD_SCREEN
+    const int64_t nsrc = cnt[0] + cnt[1] + cnt[2] + cnt[3];
+    DCD_TRY(src.alloc(&c->mem, nsrc));
+    count_launch(), pack_bins<<<grid_for(nsrc, T), T, 0, s>>>(lists.get(), n, cnt[0], cnt[1], cnt[2], cnt[3], src.get());
     DCD_LAUNCH_CHECK();
+    lists.reset();
+    Buf<int32_t> jstar;
+    Buf<long long> g1;
+    Buf<uint8_t> flags;
+    DCD_TRY(jstar.alloc(&c->mem, nsrc));
+    DCD_TRY(g1.alloc(&c->mem, 2 * nsrc));
+    DCD_TRY(flags.alloc(&c->mem, nsrc));
+    SV sv{g.rp, g.col, g.w, k, labels0, a, mo.pkey.get(), mo.pflag.get(), mo.pair_ptr.get(), c->hsc->m2,
+          mark.get(), cflag.get(), src.get(), jstar.get(), g1.get(), flags.get()};
+    if (sv.m2 >= ((int64_t)1 << 31)) DCD_TRY(screen_impl<i128>(c, sv, g, cnt, hub_max, nsrc));
+    else DCD_TRY(screen_impl<long long>(c, sv, g, cnt, hub_max, nsrc));
   }
   DCD_TRY_CUDA(cudaMemsetAsync(&d->r_size, 0, sizeof(int64_t), s));
-  ::dcd::count_launch(), build_rset<<<grid_for(n, T), T, 0, s>>>(n, mark.get(), cflag.get(), labels0, rset,
-                                           (unsigned long long*)&d->r_size);
+  count_launch(), build_rset<<<grid_for(n, T), T, 0, s>>>(n, mark.get(), cflag.get(), labels0, rset,
+                                                          (unsigned long long*)&d->r_size);
   DCD_LAUNCH_CHECK();
   return DCD_OK;
 }
