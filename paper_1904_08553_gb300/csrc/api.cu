@@ -1,6 +1,8 @@
 // api.cu -- the extern "C" entry points of dcd.h and the per-step driver
 // (Sec. III-D: G_t <- G_{t-1} + Delta_t; R_t; multi-level run; C_t, Q_t).
+#include <chrono>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -46,6 +48,16 @@ bool host_records_ok(const dcd_edge* e, int64_t m, int64_t n, bool is_insert) {
 }
 
 }  // namespace
+
+void trace(const char* what) {
+  static const bool on = getenv("DCD_TRACE") != nullptr;
+  if (!on) return;
+  using clk = std::chrono::steady_clock;
+  static thread_local clk::time_point last = clk::now();
+  const clk::time_point now = clk::now();
+  fprintf(stderr, "[dcd] %-28s %9.3f ms\n", what, std::chrono::duration<double, std::milli>(now - last).count());
+  last = now;
+}
 
 void note_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
   snprintf(g_last_cuda, sizeof(g_last_cuda), "%s: %s (%s:%d)", cudaGetErrorString(e), what, file, line);
@@ -248,6 +260,7 @@ static int update_impl(dcd_ctx* c, dcd_step_stats* st) {
   const bool first = c->t == 0;
   const int mode = first ? DCD_MODE_STATIC : c->mode;
   if (mode == DCD_MODE_GIVEN_R && !c->has_rgiven) return DCD_ESTATE;
+  trace("update: enter");
   DCD_TRY_CUDA(cudaEventRecord(c->ev[0], s));
   DCD_TRY_CUDA(cudaMemsetAsync(d, 0, sizeof(DevScalars), s));
 
@@ -264,6 +277,7 @@ static int update_impl(dcd_ctx* c, dcd_step_stats* st) {
   DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
   DCD_TRY_CUDA(cudaEventRecord(c->ev[1], s));
   DCD_TRY_CUDA(cudaStreamSynchronize(s));
+  trace("update: merge done");
   if (c->hsc->err & kErrBadRecord) return DCD_EINVAL;
   if (c->hsc->err & kErrOverflow) return DCD_EOVERFLOW;
   const int64_t m2 = c->hsc->m2;
@@ -300,12 +314,14 @@ static int update_impl(dcd_ctx* c, dcd_step_stats* st) {
     DCD_TRY_CUDA(cudaMemsetAsync(rnew.get(), 1, n, s));
   }
   DCD_TRY_CUDA(cudaEventRecord(c->ev[10], s));
+  trace("update: R_t done");
 
   // ---- Algorithm 1 with R_t at level 0 ----
   DCD_TRY(c->labels_nx.ensure(&c->mem, n));
   DCD_TRY(run_louvain(c, g, L0.get(), active, mo.k, c->labels_nx.get(), st));
   DCD_TRY_CUDA(cudaEventRecord(c->ev[11], s));
   DCD_TRY_CUDA(cudaEventSynchronize(c->ev[11]));
+  trace("update: louvain done");
 
   // ---- commit ----
   c->cur = nxt;

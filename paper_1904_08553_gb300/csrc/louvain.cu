@@ -635,6 +635,7 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
   const int64_t hub_max = c->hsc->bin_maxdeg;
   const int64_t act_deg = c->hsc->act_deg;
   const int64_t n_active = c->hsc->ncomm;  // bin_count leaves the active count here
+  trace("level: binned");
 
   Buf<int32_t> list, cursor, prop, Lprev, mvit, moved, moved_cnt, moved_big, moved_big_cnt;
   DCD_TRY(list.alloc(&c->mem, total));
@@ -742,6 +743,7 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
     out->moves += c->hsc->moves;
     if (c->hsc->stop) break;
   }
+  trace("level: passes done");
   return DCD_OK;
 }
 
@@ -903,6 +905,7 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
     int64_t nc = 0;
     if (level == 0) DCD_TRY(used_labels<int32_t>(c, *g_l0, L, cid, &nc));
     else DCD_TRY(used_labels<int64_t>(c, *g_lc, L, cid, &nc));
+    trace("level: labels counted");
     level++;
     bool stop = nc == nv || (level >= 2 && h_below_tau(N_end - N_start, N_start, tau)) || level >= c->cfg.max_levels;
     if (stop) {
@@ -932,6 +935,7 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
     float tc = 0.f;
     cudaEventElapsedTime(&tc, c->ev[5], c->ev[6]);
     ms_coarsen += tc;
+    trace("level: coarsened");
     // free the previous coarse level
     cg[which].rp.reset();
     cg[which].col.reset();

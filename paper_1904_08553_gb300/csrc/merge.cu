@@ -240,6 +240,7 @@ int merge_batch(dcd_ctx* c, const int32_t* labels0, MergeOut* out) {
     if (*reinterpret_cast<uint32_t*>(c->hscratch) & kErrBadRecord) return DCD_EINVAL;
   }
 
+  trace("merge: validated");
   // ---- records sorted by (source, sink) ----
   Buf<uint64_t> k0, k1;
   Buf<uint32_t> v0, v1;
@@ -275,6 +276,7 @@ int merge_batch(dcd_ctx* c, const int32_t* labels0, MergeOut* out) {
     DCD_TRY_CUDA(cudaStreamSynchronize(s));
     P = (int64_t)(*reinterpret_cast<int32_t*>(c->hscratch));
   }
+  trace("merge: sorted + pairs counted");
   out->npairs = P;
 
   DCD_TRY(out->pkey.alloc(&c->mem, P));

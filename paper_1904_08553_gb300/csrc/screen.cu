@@ -622,6 +622,7 @@ int screen_impl(dcd_ctx* c, SV& sv, const Csr<int32_t>& g, const int64_t* cnt, i
     count_launch(), scr_a_block<ST, 512><<<(unsigned)hctas, 512, 0, s>>>(sv, off3, cnt[3], hk.get(), hv.get(), hcap);
   DCD_LAUNCH_CHECK();
 
+  trace("screen: phase A");
   // ---- B ----
   Buf<uint64_t> k0, k1;
   Buf<uint32_t> v0, v1, stmp;
@@ -691,6 +692,7 @@ int screen_impl(dcd_ctx* c, SV& sv, const Csr<int32_t>& g, const int64_t* cnt, i
       count_launch(), scr_c_block<ST, 512><<<(unsigned)cctas, 512, 0, s>>>(sv, gv, gcnt[3], ck.get(), cv.get(), ccap);
     DCD_LAUNCH_CHECK();
   }
+  trace("screen: phases B, C");
   // ---- D ----
   count_launch(), scr_mark<<<grid_for(nsrc * 32, T, 16), T, 0, s>>>(sv, nsrc);
   DCD_LAUNCH_CHECK();
