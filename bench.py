@@ -83,6 +83,12 @@ class ClockSampler:
                  "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+        # let the sampler start up (NVML initialisation) before the timed region
+        t0 = time.time()
+        while self.proc is not None and time.time() - t0 < 5.0:
+            if Path(self.path).stat().st_size > 0:
+                break
+            time.sleep(0.05)
         return self
 
     def __exit__(self, *exc):

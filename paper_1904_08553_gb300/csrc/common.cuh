@@ -45,7 +45,7 @@ void note_cuda_error(cudaError_t e, const char* what, const char* file, int line
 
 #define DCD_LAUNCH_CHECK() DCD_TRY_CUDA(cudaGetLastError())
 
-inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // Grid size for grid-stride kernels: enough CTAs to fill every SM several
 // times over, never more than the work needs.

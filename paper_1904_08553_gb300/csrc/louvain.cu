@@ -51,16 +51,22 @@ __global__ void __launch_bounds__(256) lm_warp(LV<W> g, const int32_t* __restric
                                                int32_t* __restrict__ prop) {
   const int lane = lane_id();
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < cnt; i += nw) {
-    const int32_t v = list[i];
-    const int64_t b = g.rp[v];
-    const int d = (int)(g.rp[v + 1] - b);
+  int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  // software pipeline: the next vertex's id and row bounds load while the
+  // current row is aggregated
+  int32_t v = i < cnt ? list[i] : 0;
+  int64_t b = g.rp[v], bend = g.rp[v + 1];
+  for (; i < cnt; i += nw) {
+    const int64_t in = i + nw;
+    const int32_t vn = in < cnt ? list[in] : v;
+    const int d = (int)(bend - b);
     const int32_t C = g.L[v];
     bool valid = lane < d;
     int32_t u = valid ? g.col[b + lane] : -1;
     valid = valid && u != v;
     const int32_t lab = valid ? g.L[u] : -1;
     const W wt = valid ? g.w[b + lane] : W(0);
+    const int64_t bn = g.rp[vn], bendn = g.rp[vn + 1];
     const unsigned peers = __match_any_sync(0xffffffffu, lab);
     const int64_t e = group_sum_exact(peers, wt);
     const bool leader = (int)(__ffs(peers) - 1) == lane;
@@ -75,6 +81,9 @@ __global__ void __launch_bounds__(256) lm_warp(LV<W> g, const int32_t* __restric
     }
     warp_argmax(S, D);
     if (lane == 0) prop[i] = (D != INT_MAX && S > 0) ? guard_choice(C, D, g.size) : C;
+    v = vn;
+    b = bn;
+    bend = bendn;
   }
 }
 
@@ -504,21 +513,75 @@ __global__ void mark_used(int64_t n, const int32_t* __restrict__ L, int32_t* __r
     used[L[v]] = 1;
 }
 
-// Coarse entry of fine entry (u, y, w): (cid[L[u]], cid[L[y]], w).
-template <typename W, int G>
-__global__ void __launch_bounds__(256) emit_coarse(int64_t n, const int64_t* __restrict__ rp,
+// Coarse entries, aggregated on the fly.  Warps walk the fine CSR entry by
+// entry (1024-entry segments, so a hub row is shared by many warps); each
+// 32-entry chunk finds the row of every entry from the row boundaries held
+// one per lane, builds the key cid[L[u]] * nc + cid[L[y]] and sums equal keys
+// of the chunk with match_any + redux before one emit per distinct key.
+constexpr int64_t kSegEntries = 1024;
+
+template <typename W>
+__global__ void __launch_bounds__(256) emit_coarse(int64_t n, int64_t m, const int64_t* __restrict__ rp,
                                                    const int32_t* __restrict__ col, const W* __restrict__ w,
                                                    const int32_t* __restrict__ L, const int32_t* __restrict__ cid,
-                                                   uint64_t* __restrict__ keys, uint64_t* __restrict__ vals) {
-  const int g = threadIdx.x % G;
-  const int64_t gid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
-  const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
-  for (int64_t u = gid; u < n; u += ngroups) {
-    const uint64_t cu = (uint64_t)(uint32_t)cid[L[u]] << 32;
-    const int64_t e1 = rp[u + 1];
-    for (int64_t e = rp[u] + g; e < e1; e += G) {
-      keys[e] = cu | (uint32_t)cid[L[col[e]]];
-      vals[e] = (uint64_t)(int64_t)w[e];
+                                                   uint64_t nc, uint64_t* __restrict__ keys,
+                                                   uint64_t* __restrict__ vals, unsigned long long* __restrict__ count) {
+  const int lane = lane_id();
+  const int64_t nseg = cdiv(m, kSegEntries);
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t sg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sg < nseg; sg += nw) {
+    const int64_t E0 = sg * kSegEntries, E1 = E0 + kSegEntries < m ? E0 + kSegEntries : m;
+    int64_t r = 0;
+    if (lane == 0) {  // last row whose start is <= E0
+      int64_t lo = 0, hi = n - 1;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (rp[mid] <= E0) lo = mid; else hi = mid - 1;
+      }
+      r = lo;
+    }
+    r = __shfl_sync(0xffffffffu, r, 0);
+    for (int64_t c0 = E0; c0 < E1; c0 += 32) {
+      const int64_t e = c0 + lane;
+      const bool valid = e < E1;
+      const int64_t bk = (r + 1 + lane <= n) ? rp[r + 1 + lane] : INT64_MAX;  // end of row r + lane
+      const int64_t last = __shfl_sync(0xffffffffu, bk, 31);
+      int64_t row;
+      if (last <= c0 + 31) {
+        // more than 31 rows end inside this chunk (empty rows): search per lane
+        int64_t lo = r, hi = n - 1, x = valid ? e : c0;
+        while (lo < hi) {
+          const int64_t mid = (lo + hi + 1) >> 1;
+          if (rp[mid] <= x) lo = mid; else hi = mid - 1;
+        }
+        row = lo;
+      } else {
+        int cntv = 0;
+        const int64_t x = valid ? e : c0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int64_t v = __shfl_sync(0xffffffffu, bk, cntv + step - 1);
+          if (v <= x) cntv += step;
+        }
+        row = r + cntv;
+      }
+      const int32_t cy = valid ? cid[L[col[e]]] : 0;
+      const uint64_t cu = valid ? (uint64_t)cid[L[row]] : 0;
+      const uint64_t key = valid ? cu * nc + (uint64_t)cy : ~0ull;
+      const W wt = valid ? w[e] : W(0);
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      const int64_t sum = group_sum_exact(peers, wt);
+      const bool lead = valid && (int)(__ffs(peers) - 1) == lane;
+      const unsigned bal = __ballot_sync(0xffffffffu, lead);
+      unsigned long long slot = 0;
+      if (lane == 0 && bal) slot = atomicAdd(count, (unsigned long long)__popc(bal));
+      slot = __shfl_sync(0xffffffffu, slot, 0);
+      if (lead) {
+        const unsigned long long pos = slot + __popc(bal & lanemask_lt());
+        keys[pos] = key;
+        vals[pos] = (uint64_t)sum;
+      }
+      r = __shfl_sync(0xffffffffu, row, 31);
     }
   }
 }
@@ -533,7 +596,7 @@ __global__ void key_heads(const uint64_t* __restrict__ keys, int64_t m, int32_t*
 // per-row entry counts at run heads.
 constexpr int kRunItems = 16;
 __global__ void reduce_runs(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ vals, int64_t m,
-                            const int32_t* __restrict__ head, const int32_t* __restrict__ uid,
+                            uint64_t nc, const int32_t* __restrict__ head, const int32_t* __restrict__ uid,
                             unsigned long long* __restrict__ cw, int32_t* __restrict__ ccol,
                             int64_t* __restrict__ rowcnt) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -545,8 +608,8 @@ __global__ void reduce_runs(const uint64_t* __restrict__ keys, const uint64_t* _
   for (int64_t e = e0; e < e1; e++) {
     const int32_t id = uid[e];
     if (head[e]) {
-      ccol[id] = (int32_t)(keys[e] & 0xffffffffu);
-      atomicAdd((unsigned long long*)&rowcnt[keys[e] >> 32], 1ull);
+      ccol[id] = (int32_t)(keys[e] % nc);
+      atomicAdd((unsigned long long*)&rowcnt[keys[e] / nc], 1ull);
     }
     if (id != cur) {
       if (cur >= 0) atomicAdd(&cw[cur], acc);
@@ -783,30 +846,32 @@ template <typename W>
 int coarsen(dcd_ctx* c, const Csr<W>& g, const int32_t* L, const int32_t* cid, int64_t nc, CoarseGraph* out) {
   cudaStream_t s = c->stream;
   const int T = 256;
-  const int64_t m = g.nnz;
+  const int64_t m0 = g.nnz;
   Buf<uint64_t> k0, k1, v0, v1;
   Buf<int32_t> head, uid;
   Buf<uint32_t> stmp;
-  DCD_TRY(k0.alloc(&c->mem, m));
+  Buf<unsigned long long> cnt;
+  DCD_TRY(k0.alloc(&c->mem, m0));
+  DCD_TRY(v0.alloc(&c->mem, m0));
+  DCD_TRY(cnt.alloc(&c->mem, 1));
+  DCD_TRY_CUDA(cudaMemsetAsync(cnt.get(), 0, sizeof(unsigned long long), s));
+  if (m0 > 0) {
+    ::dcd::count_launch(), emit_coarse<W><<<grid_for(cdiv(m0, kSegEntries) * 32, T, 16), T, 0, s>>>(
+        g.n, m0, g.rp, g.col, g.w, L, cid, (uint64_t)nc, k0.get(), v0.get(), cnt.get());
+    DCD_LAUNCH_CHECK();
+  }
+  DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch, cnt.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  DCD_TRY_CUDA(cudaStreamSynchronize(s));
+  const int64_t m = c->hscratch[0];
   DCD_TRY(k1.alloc(&c->mem, m));
-  DCD_TRY(v0.alloc(&c->mem, m));
   DCD_TRY(v1.alloc(&c->mem, m));
   DCD_TRY(head.alloc(&c->mem, m + 1));
   DCD_TRY(uid.alloc(&c->mem, m + 1));
   DCD_TRY(stmp.alloc(&c->mem, sort_tmp_words(m) + 2 * scan_tmp_count(m + nc + 2) + 64));
-  const int64_t avg = g.n ? (m + g.n - 1) / g.n : 1;
-#define DCD_EMIT(Gs) \
-  ::dcd::count_launch(), emit_coarse<W, Gs><<<grid_for(g.n * Gs, T), T, 0, s>>>(g.n, g.rp, g.col, g.w, L, cid, k0.get(), v0.get())
-  if (avg <= 6) DCD_EMIT(4);
-  else if (avg <= 12) DCD_EMIT(8);
-  else if (avg <= 24) DCD_EMIT(16);
-  else DCD_EMIT(32);
-#undef DCD_EMIT
-  DCD_LAUNCH_CHECK();
-  const int b = bits_for(nc - 1);
-  int ranges[4] = {0, b, 32, 32 + b};
+  const int b = bits_for(nc * nc - 1);
+  int ranges[2] = {0, b};
   bool in1 = false;
-  DCD_TRY(sort_pairs<uint64_t>(k0.get(), v0.get(), k1.get(), v1.get(), m, ranges, 2, stmp.get(), &in1, s));
+  DCD_TRY(sort_pairs<uint64_t>(k0.get(), v0.get(), k1.get(), v1.get(), m, ranges, 1, stmp.get(), &in1, s));
   const uint64_t* keys = in1 ? k1.get() : k0.get();
   const uint64_t* vals = in1 ? v1.get() : v0.get();
   ::dcd::count_launch(), key_heads<<<grid_for(m, T), T, 0, s>>>(keys, m, head.get());
@@ -824,9 +889,9 @@ int coarsen(dcd_ctx* c, const Csr<W>& g, const int32_t* L, const int32_t* cid, i
   DCD_TRY_CUDA(cudaMemsetAsync(out->rp.get(), 0, (nc + 1) * sizeof(int64_t), s));
   DCD_TRY_CUDA(cudaMemsetAsync(out->w.get(), 0, U * sizeof(int64_t), s));
   if (m > 0) {
-    ::dcd::count_launch(), reduce_runs<<<(unsigned)cdiv(cdiv(m, kRunItems), T), T, 0, s>>>(keys, vals, m, head.get(), uid.get(),
-                                                                    (unsigned long long*)out->w.get(), out->col.get(),
-                                                                    out->rp.get());
+    ::dcd::count_launch(), reduce_runs<<<(unsigned)cdiv(cdiv(m, kRunItems), T), T, 0, s>>>(
+        keys, vals, m, (uint64_t)nc, head.get(), uid.get(), (unsigned long long*)out->w.get(), out->col.get(),
+        out->rp.get());
     DCD_LAUNCH_CHECK();
   }
   DCD_TRY(exclusive_scan<int64_t>(out->rp.get(), out->rp.get(), nc + 1, nullptr, reinterpret_cast<int64_t*>(stmp.get()),
