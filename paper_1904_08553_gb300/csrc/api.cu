@@ -95,6 +95,24 @@ void DevMem::release(void* p) {
   if (p) cudaFreeAsync(p, stream);
 }
 
+// Grows the context's pool ahead of a step: allocate and free one block of the
+// step's expected peak so that the step's many allocations are carved from
+// memory the pool already holds (growing a pool maps new memory, which is slow).
+int DevMem::reserve(size_t bytes) {
+  if (!pool) return DCD_OK;
+  uint64_t have = 0;
+  cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &have);
+  if (have >= bytes) return DCD_OK;
+  void* p = nullptr;
+  const size_t want = bytes + bytes / 4;
+  if (cudaMallocFromPoolAsync(&p, want, pool, stream) != cudaSuccess) {
+    cudaGetLastError();
+    return DCD_OK;  // not fatal: the step's own allocations will try again
+  }
+  cudaFreeAsync(p, stream);
+  return DCD_OK;
+}
+
 namespace {
 __global__ void count_bytes(const uint8_t* r, int64_t n, unsigned long long* out) {
   unsigned long long c = 0;
@@ -261,6 +279,11 @@ static int update_impl(dcd_ctx* c, dcd_step_stats* st) {
   const int mode = first ? DCD_MODE_STATIC : c->mode;
   if (mode == DCD_MODE_GIVEN_R && !c->has_rgiven) return DCD_ESTATE;
   trace("update: enter");
+  {
+    const int64_t R = 2 * (c->n_ins + c->n_del);
+    const int64_t nnz_cap = c->nnz + 2 * c->n_ins;
+    c->mem.reserve((size_t)(48 * nnz_cap + 96 * n + 64 * R) + ((size_t)64 << 20));
+  }
   DCD_TRY_CUDA(cudaEventRecord(c->ev[0], s));
   DCD_TRY_CUDA(cudaMemsetAsync(d, 0, sizeof(DevScalars), s));
 

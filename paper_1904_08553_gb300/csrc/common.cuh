@@ -65,6 +65,7 @@ struct DevMem {
   cudaMemPool_t pool = nullptr;  // the context's own pool (keeps its memory)
   int alloc(void** p, size_t bytes);
   void release(void* p);
+  int reserve(size_t bytes);
 };
 
 template <typename T>
