@@ -27,7 +27,7 @@ template <typename T>
 int grow_keep(DevMem* mem, Buf<T>& b, size_t need, size_t keep, cudaStream_t s) {
   if (b.p && b.n >= need) return DCD_OK;
   Buf<T> nb;
-  DCD_TRY(nb.alloc(mem, need + need / 2 + 1024));
+  DCD_TRY(nb.ensure(mem, need + need / 2 + 1024));
   if (keep && b.p) DCD_TRY_CUDA(cudaMemcpyAsync(nb.p, b.p, keep * sizeof(T), cudaMemcpyDeviceToDevice, s));
   b.reset();
   b.p = nb.p;
@@ -80,7 +80,7 @@ int grid_for(int64_t items, int threads, int per_sm) {
   return (int)(b < 1 ? 1 : b);
 }
 
-int DevMem::alloc(void** p, size_t bytes) {
+int DevMem::alloc_persistent(void** p, size_t bytes) {
   cudaError_t e = pool ? cudaMallocFromPoolAsync(p, bytes, pool, stream) : cudaMallocAsync(p, bytes, stream);
   if (e != cudaSuccess) {
     note_cuda_error(e, "cudaMallocAsync", __FILE__, __LINE__);
@@ -91,26 +91,45 @@ int DevMem::alloc(void** p, size_t bytes) {
   return DCD_OK;
 }
 
-void DevMem::release(void* p) {
-  if (p) cudaFreeAsync(p, stream);
+int DevMem::alloc(void** p, size_t bytes) {
+  const size_t b = (bytes + 255) & ~(size_t)255;
+  if (in_step && arena && arena_off + b <= arena_size) {
+    *p = arena + arena_off;
+    arena_off += b;
+    return DCD_OK;
+  }
+  if (in_step) overflow += b;
+  return alloc_persistent(p, bytes);
 }
 
-// Grows the context's pool ahead of a step: allocate and free one block of the
-// step's expected peak so that the step's many allocations are carved from
-// memory the pool already holds (growing a pool maps new memory, which is slow).
-int DevMem::reserve(size_t bytes) {
-  if (!pool) return DCD_OK;
-  uint64_t have = 0;
-  cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &have);
-  if (have >= bytes) return DCD_OK;
-  void* p = nullptr;
-  const size_t want = bytes + bytes / 4;
-  if (cudaMallocFromPoolAsync(&p, want, pool, stream) != cudaSuccess) {
-    cudaGetLastError();
-    return DCD_OK;  // not fatal: the step's own allocations will try again
-  }
+void DevMem::release(void* p) {
+  if (!p) return;
+  if (arena && static_cast<char*>(p) >= arena && static_cast<char*>(p) < arena + arena_size) return;
   cudaFreeAsync(p, stream);
+}
+
+int DevMem::begin_step(size_t hint) {
+  size_t target = last_use + last_use / 4;
+  if (hint > target) target = hint;
+  if (arena_size < target) {
+    if (arena) cudaFreeAsync(arena, stream);
+    arena = nullptr;
+    arena_size = 0;
+    void* q = nullptr;
+    DCD_TRY(alloc_persistent(&q, target));
+    arena = static_cast<char*>(q);
+    arena_size = target;
+  }
+  arena_off = 0;
+  overflow = 0;
+  in_step = true;
   return DCD_OK;
+}
+
+void DevMem::end_step() {
+  if (in_step) last_use = arena_off + overflow;
+  arena_off = 0;
+  in_step = false;
 }
 
 namespace {
@@ -221,7 +240,9 @@ int dcd_destroy(dcd_ctx* c) {
     c->col[0].reset(); c->col[1].reset();
     c->w[0].reset(); c->w[1].reset();
     c->labels.reset(); c->labels_nx.reset(); c->rset.reset(); c->rgiven.reset();
-    c->ins.reset(); c->del.reset(); c->dsc.reset(); c->iota.reset();
+    c->ins.reset(); c->del.reset(); c->dsc.reset(); c->iota.reset(); c->rset_nx.reset();
+    if (c->mem.arena) cudaFreeAsync(c->mem.arena, c->stream);
+    c->mem.arena = nullptr;
     cudaStreamSynchronize(c->stream);
   }
   for (auto& e : c->ev)
@@ -279,11 +300,6 @@ static int update_impl(dcd_ctx* c, dcd_step_stats* st) {
   const int mode = first ? DCD_MODE_STATIC : c->mode;
   if (mode == DCD_MODE_GIVEN_R && !c->has_rgiven) return DCD_ESTATE;
   trace("update: enter");
-  {
-    const int64_t R = 2 * (c->n_ins + c->n_del);
-    const int64_t nnz_cap = c->nnz + 2 * c->n_ins;
-    c->mem.reserve((size_t)(48 * nnz_cap + 96 * n + 64 * R) + ((size_t)64 << 20));
-  }
   DCD_TRY_CUDA(cudaEventRecord(c->ev[0], s));
   DCD_TRY_CUDA(cudaMemsetAsync(d, 0, sizeof(DevScalars), s));
 
@@ -309,8 +325,8 @@ static int update_impl(dcd_ctx* c, dcd_step_stats* st) {
   Csr<int32_t> g{n, nnz_new, c->rp[nxt].get(), c->col[nxt].get(), c->w[nxt].get()};
 
   // ---- R_t ----
-  Buf<uint8_t> rnew;
-  DCD_TRY(rnew.alloc(&c->mem, n));
+  Buf<uint8_t>& rnew = c->rset_nx;
+  DCD_TRY(rnew.ensure(&c->mem, n));
   const uint8_t* active = nullptr;
   int64_t r_size = n;
   DCD_TRY_CUDA(cudaEventRecord(c->ev[9], s));
@@ -351,8 +367,8 @@ static int update_impl(dcd_ctx* c, dcd_step_stats* st) {
   c->nnz = nnz_new;
   std::swap(c->labels.p, c->labels_nx.p);
   std::swap(c->labels.n, c->labels_nx.n);
-  std::swap(c->rset.p, rnew.p);
-  std::swap(c->rset.n, rnew.n);
+  std::swap(c->rset.p, c->rset_nx.p);
+  std::swap(c->rset.n, c->rset_nx.n);
   c->t += 1;
   if (st) {
     float t_all = 0.f, t_merge = 0.f, t_screen = 0.f;
@@ -378,7 +394,13 @@ int dcd_update(dcd_ctx* c, int32_t* labels_out, double* q_out, dcd_step_stats* s
   dcd_step_stats st;
   memset(&st, 0, sizeof(st));
   const int64_t launches0 = dcd::g_launches.load();
+  {
+    const int64_t R = 2 * (c->n_ins + c->n_del);
+    const int64_t nnz_cap = c->nnz + 2 * c->n_ins;
+    DCD_TRY(c->mem.begin_step((size_t)(64 * nnz_cap + 128 * c->n + 64 * R) + ((size_t)64 << 20)));
+  }
   const int rc = update_impl(c, &st);
+  c->mem.end_step();
   st.launches = dcd::g_launches.load() - launches0;
   // the staged batch is consumed by the attempt, successful or not
   c->n_ins = c->n_del = 0;

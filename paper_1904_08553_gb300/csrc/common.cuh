@@ -59,13 +59,23 @@ enum : uint32_t {
   kErrTableFull = 4u,   // aggregation table overflow (cannot happen when sized by degree)
 };
 
-// ---- stream-ordered device allocation (the context's memory pool) ----
+// ---- device memory of a context ----
+// Persistent buffers (the graph, labels, staging) come from the context's own
+// stream-ordered pool.  Scratch of one update comes from a step arena: one
+// block sized from the previous step's use (plus a margin), handed out by a
+// bump pointer and released as a whole when the update ends, so a step makes
+// no allocator calls once the arena has grown to the workload.
 struct DevMem {
   cudaStream_t stream = nullptr;
-  cudaMemPool_t pool = nullptr;  // the context's own pool (keeps its memory)
-  int alloc(void** p, size_t bytes);
-  void release(void* p);
-  int reserve(size_t bytes);
+  cudaMemPool_t pool = nullptr;
+  char* arena = nullptr;
+  size_t arena_size = 0, arena_off = 0, overflow = 0, last_use = 0;
+  bool in_step = false;
+  int alloc(void** p, size_t bytes);             // arena inside a step, else pool
+  int alloc_persistent(void** p, size_t bytes);  // pool
+  void release(void* p);                         // no-op for arena memory
+  int begin_step(size_t hint);
+  void end_step();
 };
 
 template <typename T>
@@ -91,10 +101,16 @@ struct Buf {
     p = nullptr;
     n = 0;
   }
-  // Keep the allocation when it is already large enough.
+  // Persistent buffer: keep the allocation when it is already large enough.
   int ensure(DevMem* m, size_t count) {
     if (p && n >= count) return DCD_OK;
-    return alloc(m, count + count / 4 + 64);
+    reset();
+    mem = m;
+    n = count + count / 4 + 64;
+    void* q = nullptr;
+    int rc = m->alloc_persistent(&q, n * sizeof(T));
+    p = static_cast<T*>(q);
+    return rc;
   }
   T* get() const { return p; }
 };

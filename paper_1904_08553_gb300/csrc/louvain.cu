@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256) lm_warp(LV<W> g, const int32_t* __restric
   }
 }
 
-// One warp per vertex of 33..256 entries: a warp-private shared-memory table
+// One warp per vertex of 33..128 entries: a warp-private shared-memory table
 // (capacity 2 x degree rounded up to a power of two, at most kMidCap).
 template <typename W, typename ST>
 __global__ void __launch_bounds__(256) lm_warp_tbl(LV<W> g, const int32_t* __restrict__ list, int64_t cnt,
@@ -418,12 +418,13 @@ __global__ void bin_count(const int64_t* __restrict__ rp, int64_t n, const uint8
                           DevScalars* d) {
   __shared__ unsigned long long sc[4];
   __shared__ unsigned long long sdeg, sact;
-  __shared__ long long smax;
+  __shared__ long long smax, smax2;
   if (threadIdx.x < 4) sc[threadIdx.x] = 0;
   if (threadIdx.x == 0) {
     sdeg = 0;
     sact = 0;
     smax = 0;
+    smax2 = 0;
   }
   __syncthreads();
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
@@ -435,6 +436,7 @@ __global__ void bin_count(const int64_t* __restrict__ rp, int64_t n, const uint8
     const int bin = deg <= kBinWarpMax ? 0 : deg <= kBinMidMax ? 1 : deg <= kBinLargeMax ? 2 : 3;
     atomicAdd(&sc[bin], 1ull);
     if (bin == 3) atomicMax(&smax, (long long)deg);
+    if (bin == 2) atomicMax(&smax2, (long long)deg);
   }
   __syncthreads();
   if (threadIdx.x < 4 && sc[threadIdx.x]) atomicAdd((unsigned long long*)&d->bin_cnt[threadIdx.x], sc[threadIdx.x]);
@@ -442,6 +444,7 @@ __global__ void bin_count(const int64_t* __restrict__ rp, int64_t n, const uint8
     atomicAdd((unsigned long long*)&d->act_deg, sdeg);
     atomicAdd((unsigned long long*)&d->ncomm, sact);
     atomicMax((long long*)&d->bin_maxdeg, smax);
+    atomicMax((long long*)&d->bin2_maxdeg, smax2);
   }
 }
 
@@ -688,6 +691,7 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
 
   // ---- bins of the active vertices ----
   DCD_TRY_CUDA(cudaMemsetAsync(&d->bin_cnt[0], 0, sizeof(int64_t) * 7, s));  // bins, maxdeg, act_deg, ncomm
+  DCD_TRY_CUDA(cudaMemsetAsync(&d->bin2_maxdeg, 0, sizeof(int64_t), s));
   ::dcd::count_launch(), bin_count<<<grid_for(nv, T), T, 0, s>>>(g.rp, nv, active, d);
   DCD_LAUNCH_CHECK();
   DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
@@ -696,6 +700,7 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
   for (int b = 0; b < 4; b++) cnt[b] = c->hsc->bin_cnt[b];
   const int64_t total = cnt[0] + cnt[1] + cnt[2] + cnt[3];
   const int64_t hub_max = c->hsc->bin_maxdeg;
+  const size_t large_smem_used = (size_t)table_cap(c->hsc->bin2_maxdeg > 0 ? c->hsc->bin2_maxdeg : 1) * 12;
   const int64_t act_deg = c->hsc->act_deg;
   const int64_t n_active = c->hsc->ncomm;  // bin_count leaves the active count here
   trace("level: binned");
@@ -757,11 +762,11 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
     if (cnt[0])                                                                                                    \
       ::dcd::count_launch(), lm_warp<W, ST><<<grid_for(cnt[0] * 32, T, 16), T, 0, s>>>(lv, lst, cnt[0], prop.get());                      \
     if (cnt[1])                                                                                                    \
-      ::dcd::count_launch(), lm_warp_tbl<W, ST><<<grid_for(cnt[1] * 32, T, 4), T, mid_smem, s>>>(                  \
+      ::dcd::count_launch(), lm_warp_tbl<W, ST><<<grid_for(cnt[1] * 32, T, 8), T, mid_smem, s>>>(                  \
           lv, lst + cnt[0], cnt[1], prop.get() + cnt[0]);                                                          \
     if (cnt[2])                                                                                                    \
-      ::dcd::count_launch(), lm_block<W, ST, kLargeThreads><<<(unsigned)(cnt[2] < 2 * c->sms ? cnt[2] : 2 * c->sms), kLargeThreads,      \
-                                       large_smem, s>>>(lv, lst + cnt[0] + cnt[1], cnt[2],                         \
+      ::dcd::count_launch(), lm_block<W, ST, kLargeThreads><<<(unsigned)(cnt[2] < 8 * c->sms ? cnt[2] : 8 * c->sms), kLargeThreads,      \
+                                       large_smem_used, s>>>(lv, lst + cnt[0] + cnt[1], cnt[2],                         \
                                                         prop.get() + cnt[0] + cnt[1], nullptr, nullptr, 0);       \
     if (cnt[3])                                                                                                    \
       ::dcd::count_launch(), lm_block<W, ST, kHubThreads><<<(unsigned)hub_ctas, kHubThreads, 0, s>>>(                                     \

@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(256) scr_a_warp(SV g, int64_t off, int64_t cnt
   }
 }
 
-// Sources of degree 33..256: one warp with a warp-private shared table.
+// Sources of degree 33..128: one warp with a warp-private shared table.
 template <typename ST>
 __global__ void __launch_bounds__(256) scr_a_wtbl(SV g, int64_t off, int64_t cnt) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(256) scr_a_wtbl(SV g, int64_t off, int64_t cnt
   }
 }
 
-// Sources above 256 entries: one CTA, table in shared memory (<= 4096
+// Sources above 128 entries: one CTA, table in shared memory (<= 4096
 // entries) or in a per-CTA region of global memory.
 template <typename ST, int THREADS>
 __global__ void __launch_bounds__(THREADS) scr_a_block(SV g, int64_t off, int64_t cnt, int32_t* __restrict__ gkeys,
@@ -614,7 +614,7 @@ int screen_impl(dcd_ctx* c, SV& sv, const Csr<int32_t>& g, const int64_t* cnt, i
   int64_t hcap, hctas;
   DCD_TRY(hub_tables(c, cnt[3], hub_max, hk, hv, &hcap, &hctas));
   if (cnt[0]) count_launch(), scr_a_warp<ST><<<grid_for(cnt[0] * 32, T, 16), T, 0, s>>>(sv, 0, cnt[0]);
-  if (cnt[1]) count_launch(), scr_a_wtbl<ST><<<grid_for(cnt[1] * 32, T, 4), T, wsmem, s>>>(sv, off1, cnt[1]);
+  if (cnt[1]) count_launch(), scr_a_wtbl<ST><<<grid_for(cnt[1] * 32, T, 8), T, wsmem, s>>>(sv, off1, cnt[1]);
   if (cnt[2])
     count_launch(), scr_a_block<ST, 256><<<(unsigned)(cnt[2] < sm2 ? cnt[2] : sm2), 256, bsmem, s>>>(
                         sv, off2, cnt[2], nullptr, nullptr, 0);
@@ -682,7 +682,7 @@ int screen_impl(dcd_ctx* c, SV& sv, const Csr<int32_t>& g, const int64_t* cnt, i
     GroupView gv{keys, vals, gstart.get(), gl.get()};
     if (gcnt[0]) count_launch(), scr_c_warp<ST><<<grid_for(gcnt[0] * 32, T, 16), T, 0, s>>>(sv, gv, gcnt[0]);
     gv.glist = gl.get() + ng;
-    if (gcnt[1]) count_launch(), scr_c_wtbl<ST><<<grid_for(gcnt[1] * 32, T, 4), T, wsmem, s>>>(sv, gv, gcnt[1]);
+    if (gcnt[1]) count_launch(), scr_c_wtbl<ST><<<grid_for(gcnt[1] * 32, T, 8), T, wsmem, s>>>(sv, gv, gcnt[1]);
     gv.glist = gl.get() + 2 * ng;
     if (gcnt[2])
       count_launch(), scr_c_block<ST, 256><<<(unsigned)(gcnt[2] < sm2 ? gcnt[2] : sm2), 256, bsmem, s>>>(

@@ -42,17 +42,18 @@ struct DevScalars {
   int64_t r_size;    // |R_t|
   uint32_t err;      // kErr* bits
   uint32_t pad1;
+  int64_t bin2_maxdeg;  // largest degree in the 129..4096 bin
 };
 
 // Degree bins of the local-move kernels.
 constexpr int kBinWarpMax = 32;     // 1..32: one warp, lanes hold the row
-constexpr int kBinMidMax = 256;     // 33..256: 64-thread CTA, shared table
-constexpr int kBinLargeMax = 4096;  // 257..4096: 256-thread CTA, shared table
+constexpr int kBinMidMax = 128;     // 33..128: one warp, warp-private shared table
+constexpr int kBinLargeMax = 4096;  // 129..4096: 256-thread CTA, shared table
                                     // >4096: 512-thread CTA, table in global memory
 constexpr int kMidThreads = 64;
 constexpr int kLargeThreads = 256;
 constexpr int kHubThreads = 512;
-constexpr int kMidCap = 512;
+constexpr int kMidCap = 256;  // table_cap(kBinMidMax)
 constexpr int kLargeCap = 8192;
 
 }  // namespace dcd
@@ -77,6 +78,7 @@ struct dcd_ctx {
   dcd::Buf<int32_t> labels;     // C_t (canonical)
   dcd::Buf<int32_t> labels_nx;  // C_{t+1} under construction
   dcd::Buf<uint8_t> rset;       // R_t of the last update
+  dcd::Buf<uint8_t> rset_nx;    // R_t under construction
   dcd::Buf<uint8_t> rgiven;     // R_t for DCD_MODE_GIVEN_R
   bool has_rgiven = false;
 
