@@ -109,9 +109,11 @@ void DevMem::release(void* p) {
 }
 
 int DevMem::begin_step(size_t hint) {
-  size_t target = last_use + last_use / 4;
-  if (hint > target) target = hint;
-  if (arena_size < target) {
+  // grow by doubling, and only when the last step came near the end (or
+  // overflowed), so a slowly growing graph re-sizes the arena rarely
+  if (arena_size < hint || last_use > arena_size - arena_size / 8) {
+    size_t target = 2 * last_use;
+    if (hint + hint / 2 > target) target = hint + hint / 2;
     if (arena) cudaFreeAsync(arena, stream);
     arena = nullptr;
     arena_size = 0;
@@ -397,7 +399,7 @@ int dcd_update(dcd_ctx* c, int32_t* labels_out, double* q_out, dcd_step_stats* s
   {
     const int64_t R = 2 * (c->n_ins + c->n_del);
     const int64_t nnz_cap = c->nnz + 2 * c->n_ins;
-    DCD_TRY(c->mem.begin_step((size_t)(64 * nnz_cap + 128 * c->n + 64 * R) + ((size_t)64 << 20)));
+    DCD_TRY(c->mem.begin_step((size_t)(40 * nnz_cap + 64 * c->n + 48 * R) + ((size_t)64 << 20)));
   }
   const int rc = update_impl(c, &st);
   c->mem.end_step();

@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256) lm_warp(LV<W> g, const int32_t* __restric
   }
 }
 
-// One warp per vertex of 33..128 entries: a warp-private shared-memory table
+// One warp per vertex of 33..256 entries: a warp-private shared-memory table
 // (capacity 2 x degree rounded up to a power of two, at most kMidCap).
 template <typename W, typename ST>
 __global__ void __launch_bounds__(256) lm_warp_tbl(LV<W> g, const int32_t* __restrict__ list, int64_t cnt,

@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(256) scr_a_warp(SV g, int64_t off, int64_t cnt
   }
 }
 
-// Sources of degree 33..128: one warp with a warp-private shared table.
+// Sources of degree 33..256: one warp with a warp-private shared table.
 template <typename ST>
 __global__ void __launch_bounds__(256) scr_a_wtbl(SV g, int64_t off, int64_t cnt) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(256) scr_a_wtbl(SV g, int64_t off, int64_t cnt
   }
 }
 
-// Sources above 128 entries: one CTA, table in shared memory (<= 4096
+// Sources above 256 entries: one CTA, table in shared memory (<= 4096
 // entries) or in a per-CTA region of global memory.
 template <typename ST, int THREADS>
 __global__ void __launch_bounds__(THREADS) scr_a_block(SV g, int64_t off, int64_t cnt, int32_t* __restrict__ gkeys,

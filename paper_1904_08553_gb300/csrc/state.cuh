@@ -47,13 +47,13 @@ struct DevScalars {
 
 // Degree bins of the local-move kernels.
 constexpr int kBinWarpMax = 32;     // 1..32: one warp, lanes hold the row
-constexpr int kBinMidMax = 128;     // 33..128: one warp, warp-private shared table
-constexpr int kBinLargeMax = 4096;  // 129..4096: 256-thread CTA, shared table
+constexpr int kBinMidMax = 256;     // 33..256: one warp, warp-private shared table
+constexpr int kBinLargeMax = 4096;  // 257..4096: 256-thread CTA, shared table
                                     // >4096: 512-thread CTA, table in global memory
 constexpr int kMidThreads = 64;
 constexpr int kLargeThreads = 256;
 constexpr int kHubThreads = 512;
-constexpr int kMidCap = 256;  // table_cap(kBinMidMax)
+constexpr int kMidCap = 512;  // table_cap(kBinMidMax)
 constexpr int kLargeCap = 8192;
 
 }  // namespace dcd
