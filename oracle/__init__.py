@@ -28,6 +28,7 @@ import numpy as np
 
 _HERE = Path(__file__).resolve().parent
 _SRC = _HERE / "dcd_oracle.c"
+_SRC_MLP = _HERE / "mlp_oracle.c"
 _LIB = _HERE / "libdcd_oracle.so"
 
 STATIC, BASE, DELTA, GIVEN_R = 0, 1, 2, 3
@@ -38,12 +39,12 @@ MAX_LEVELS = 64
 def build(force: bool = False) -> Path:
     """Compile the oracle with gcc (portable C: no target-specific flags)."""
     if force or not _LIB.exists() or _LIB.stat().st_mtime < max(
-        _SRC.stat().st_mtime, (_HERE / "dcd_oracle.h").stat().st_mtime
+        _SRC.stat().st_mtime, _SRC_MLP.stat().st_mtime, (_HERE / "dcd_oracle.h").stat().st_mtime
     ):
         tmp = _LIB.with_suffix(f".so.{os.getpid()}")
         subprocess.check_call(
             ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-Wall", "-Wextra",
-             "-Wno-unused-parameter", str(_SRC), "-o", str(tmp)]
+             "-Wno-unused-parameter", str(_SRC), str(_SRC_MLP), "-o", str(tmp), "-lm"]
         )
         os.replace(tmp, _LIB)
     return _LIB
@@ -94,6 +95,12 @@ def lib():
             "orc_get_rset": (ctypes.c_int, [P, P]),
             "orc_ctx_graph": (P, [P]),
             "orc_set_labels": (ctypes.c_int, [P, P]),
+            "orc_mlp_nparams": (ctypes.c_int, []),
+            "orc_bf16": (ctypes.c_float, [ctypes.c_float]),
+            "orc_mlp_forward": (D, [P, P, P, I64, P]),
+            "orc_mlp_grad": (D, [P, P, P, I64, P]),
+            "orc_mlp_grad_exact": (D, [P, P, P, I64, P]),
+            "orc_mlp_loss_exact": (D, [P, P, P, I64]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -296,3 +303,51 @@ class Context:
     def set_labels(self, labels) -> int:
         lab = np.ascontiguousarray(labels, dtype=np.int32)
         return int(lib().orc_set_labels(self._h, _p(lab)))
+
+
+# ---------------------------------------------------------------- learned screen (MLP)
+
+MLP_FEATURES, MLP_HIDDEN = 12, 64
+
+
+def mlp_nparams() -> int:
+    return int(lib().orc_mlp_nparams())
+
+
+def bf16(x: float) -> float:
+    return float(lib().orc_bf16(float(x)))
+
+
+def mlp_forward(params, X, y=None):
+    """Probabilities (FP64, BF16-rounded operands) and mean BCE."""
+    P = np.ascontiguousarray(params, np.float32)
+    Xf = np.ascontiguousarray(X, np.float32).reshape(-1, MLP_FEATURES)
+    yy = None if y is None else np.ascontiguousarray(y, np.float32)
+    p = np.zeros(len(Xf), np.float64)
+    loss = lib().orc_mlp_forward(_p(P), _p(Xf), _p(yy), len(Xf), _p(p))
+    return p, loss
+
+
+def mlp_grad(params, X, y):
+    P = np.ascontiguousarray(params, np.float32)
+    Xf = np.ascontiguousarray(X, np.float32).reshape(-1, MLP_FEATURES)
+    yy = np.ascontiguousarray(y, np.float32)
+    G = np.zeros(mlp_nparams(), np.float64)
+    loss = lib().orc_mlp_grad(_p(P), _p(Xf), _p(yy), len(Xf), _p(G))
+    return G, loss
+
+
+def mlp_grad_exact(params, X, y):
+    P = np.ascontiguousarray(params, np.float64)
+    Xd = np.ascontiguousarray(X, np.float64).reshape(-1, MLP_FEATURES)
+    yy = np.ascontiguousarray(y, np.float64)
+    G = np.zeros(mlp_nparams(), np.float64)
+    loss = lib().orc_mlp_grad_exact(_p(P), _p(Xd), _p(yy), len(Xd), _p(G))
+    return G, loss
+
+
+def mlp_loss_exact(params, X, y) -> float:
+    P = np.ascontiguousarray(params, np.float64)
+    Xd = np.ascontiguousarray(X, np.float64).reshape(-1, MLP_FEATURES)
+    yy = np.ascontiguousarray(y, np.float64)
+    return float(lib().orc_mlp_loss_exact(_p(P), _p(Xd), _p(yy), len(Xd)))
