@@ -161,6 +161,38 @@ int dcd_get_graph(dcd_ctx* ctx, int64_t* nnz_out, int64_t* row_ptr, int32_t* col
  * contexts, all devices): lets a caller count the device work of a region. */
 int64_t dcd_kernel_launches(void);
 
+/* ---- learned screen: the network (BASELINE north star, pattern "learned parts") ----
+ * A multilayer perceptron 12 -> 64 -> 64 -> 1 (ReLU, ReLU, sigmoid) that
+ * scores a vertex's chance of changing community at level 0.  Not in the
+ * paper: it widens or prunes the Delta-screening set R_t (DCD_MODE_LEARNED).
+ * All products run on tensor cores with BF16 operands and FP32 accumulation;
+ * training minimises the mean binary cross-entropy with Adam (beta 0.9 /
+ * 0.999, eps 1e-8) on FP32 master weights; reductions are deterministic.
+ * Parameter layout (DCD_MLP_PARAMS floats): W1[12][64] (row = input), b1[64],
+ * W2[64][64] (row = input), b2[64], W3[64], b3.  Features are float32 rows of
+ * DCD_MLP_FEATURES values (see dcd_get_screen_data). */
+#define DCD_MLP_FEATURES 12
+#define DCD_MLP_HIDDEN 64
+#define DCD_MLP_PARAMS 5057
+typedef struct dcd_mlp dcd_mlp;
+
+/* New network with He-uniform weights from SplitMix64(seed), zero biases, on
+ * the current device; work runs on cuda_stream (NULL = default stream). */
+int dcd_mlp_create(uint64_t seed, void* cuda_stream, dcd_mlp** out);
+int dcd_mlp_destroy(dcd_mlp* mlp);
+/* Copy DCD_MLP_PARAMS host floats in / out; setting also resets Adam state. */
+int dcd_mlp_set_params(dcd_mlp* mlp, const float* params);
+int dcd_mlp_get_params(dcd_mlp* mlp, float* params_out);
+/* d_p[r] = sigmoid(network(d_X[r])) for n rows (device float32, n x 12 in). */
+int dcd_mlp_forward(dcd_mlp* mlp, const float* d_X, int64_t n, float* d_p);
+/* Mean BCE of n rows against d_y (device, 0/1 float32) and its gradient
+ * (host, DCD_MLP_PARAMS floats; may be NULL); no update. */
+int dcd_mlp_grad(dcd_mlp* mlp, const float* d_X, const float* d_y, int64_t n, float* grad_out, double* loss_out);
+/* epochs passes of Adam over rows [0, n) in consecutive minibatches of
+ * `batch` rows (the caller shuffles); *loss_out = last minibatch loss. */
+int dcd_mlp_train(dcd_mlp* mlp, const float* d_X, const float* d_y, int64_t n, int64_t batch, int32_t epochs,
+                  float lr, double* loss_out);
+
 /* ---- allocation-free evaluation ----
  * No counterpart in the paper: a service for callers that cannot allocate
  * device memory when they need the answer (their device memory is held by

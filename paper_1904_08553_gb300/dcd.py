@@ -25,8 +25,10 @@ EXPORTED = [
     "dcd_config_default", "dcd_create", "dcd_destroy", "dcd_apply_batch", "dcd_apply_batch_device",
     "dcd_update", "dcd_get_labels", "dcd_get_rset", "dcd_set_labels", "dcd_set_rset", "dcd_set_mode",
     "dcd_get_graph", "dcd_kernel_launches", "dcd_strerror", "dcd_last_cuda_error",
-    "dcd_modularity_noalloc",
+    "dcd_modularity_noalloc", "dcd_mlp_create", "dcd_mlp_destroy", "dcd_mlp_set_params",
+    "dcd_mlp_get_params", "dcd_mlp_forward", "dcd_mlp_grad", "dcd_mlp_train",
 ]
+MLP_FEATURES, MLP_HIDDEN, MLP_PARAMS = 12, 64, 5057
 NOALLOC_MAX_N = 1048056
 
 
@@ -101,6 +103,13 @@ def lib():
             "dcd_get_graph": (INT, [P, P, P, P, P]),
             "dcd_kernel_launches": (I64, []),
             "dcd_modularity_noalloc": (INT, [I64, P, P, P, P, P, P, P]),
+            "dcd_mlp_create": (INT, [ctypes.c_uint64, P, P]),
+            "dcd_mlp_destroy": (INT, [P]),
+            "dcd_mlp_set_params": (INT, [P, P]),
+            "dcd_mlp_get_params": (INT, [P, P]),
+            "dcd_mlp_forward": (INT, [P, P, I64, P]),
+            "dcd_mlp_grad": (INT, [P, P, P, I64, P, P]),
+            "dcd_mlp_train": (INT, [P, P, P, I64, I64, I32, ctypes.c_float, P]),
             "dcd_strerror": (ctypes.c_char_p, [INT]),
             "dcd_last_cuda_error": (ctypes.c_char_p, []),
         }
@@ -300,3 +309,81 @@ class Context:
 
     def graph(self):
         return dcd_get_graph(self._h, self.n)
+
+
+# ---- learned screen network -------------------------------------------------
+
+def dcd_mlp_create(seed: int = 0, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().dcd_mlp_create(int(seed) & ((1 << 64) - 1), _stream_ptr(stream), ctypes.byref(h)),
+           "dcd_mlp_create")
+    return h
+
+
+def dcd_mlp_destroy(h) -> None:
+    _check(lib().dcd_mlp_destroy(h), "dcd_mlp_destroy")
+
+
+def dcd_mlp_set_params(h, params) -> None:
+    P = np.ascontiguousarray(params, dtype=np.float32)
+    if P.size != MLP_PARAMS:
+        raise ValueError(f"expected {MLP_PARAMS} parameters")
+    _check(lib().dcd_mlp_set_params(h, _ptr(P)), "dcd_mlp_set_params")
+
+
+def dcd_mlp_get_params(h) -> np.ndarray:
+    P = np.zeros(MLP_PARAMS, np.float32)
+    _check(lib().dcd_mlp_get_params(h, _ptr(P)), "dcd_mlp_get_params")
+    return P
+
+
+def dcd_mlp_forward(h, d_X, n: int, d_p) -> None:
+    _check(lib().dcd_mlp_forward(h, _ptr(d_X), int(n), _ptr(d_p)), "dcd_mlp_forward")
+
+
+def dcd_mlp_grad(h, d_X, d_y, n: int):
+    G = np.zeros(MLP_PARAMS, np.float32)
+    loss = ctypes.c_double()
+    _check(lib().dcd_mlp_grad(h, _ptr(d_X), _ptr(d_y), int(n), _ptr(G), ctypes.byref(loss)), "dcd_mlp_grad")
+    return G, loss.value
+
+
+def dcd_mlp_train(h, d_X, d_y, n: int, batch: int, epochs: int, lr: float) -> float:
+    loss = ctypes.c_double()
+    _check(lib().dcd_mlp_train(h, _ptr(d_X), _ptr(d_y), int(n), int(batch), int(epochs), float(lr),
+                               ctypes.byref(loss)), "dcd_mlp_train")
+    return loss.value
+
+
+class Mlp:
+    """The learned screen's network (dcd_mlp)."""
+
+    def __init__(self, seed: int = 0, stream=None):
+        self._h = dcd_mlp_create(seed, stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            dcd_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    params = property(lambda self: dcd_mlp_get_params(self._h),
+                      lambda self, p: dcd_mlp_set_params(self._h, p))
+
+    def forward(self, d_X, n, d_p):
+        dcd_mlp_forward(self._h, d_X, n, d_p)
+
+    def grad(self, d_X, d_y, n):
+        return dcd_mlp_grad(self._h, d_X, d_y, n)
+
+    def train(self, d_X, d_y, n, batch=4096, epochs=1, lr=1e-3):
+        return dcd_mlp_train(self._h, d_X, d_y, n, batch, epochs, lr)
