@@ -50,7 +50,8 @@ extern "C" {
 #define DCD_MODE_STATIC 0  /* Static(G_t) from singletons every step (the naive approach)   */
 #define DCD_MODE_BASE 1    /* dLouvain-base: inherit C_{t-1}, R_t = V_t                     */
 #define DCD_MODE_DELTA 2   /* dLouvain-Delta-s: inherit C_{t-1}, R_t = Delta-screening      */
-#define DCD_MODE_GIVEN_R 3 /* inherit C_{t-1}, R_t supplied by dcd_set_rset (learned screen)*/
+#define DCD_MODE_GIVEN_R 3 /* inherit C_{t-1}, R_t supplied by dcd_set_rset                */
+#define DCD_MODE_LEARNED 4 /* inherit C_{t-1}, R_t from the network around Delta-screening  */
 
 typedef struct {
   int32_t u, v; /* endpoints, u != v                               */
@@ -83,6 +84,10 @@ typedef struct {
   int64_t ins_records;   /* staged inserts in Delta_t                               */
   int64_t del_records;   /* staged deletes in Delta_t                               */
   int64_t launches;      /* CUDA kernel launches issued by this update               */
+  int64_t r_screen;      /* |R_t| of plain Delta-screening (-1: not computed)        */
+  int64_t pool;          /* vertices scored by the learned screen                   */
+  int64_t fallback;      /* 1: the judge kept plain Delta-screening for this step   */
+  double q_screen;       /* judged learned mode: Q of the other run (see dcd_set_screen) */
   float ms_total;        /* device time of the whole update (CUDA events)           */
   float ms_merge;        /* batch sort + CSR merge + degrees                        */
   float ms_screen;       /* Delta-screening + R_t build                             */
@@ -192,6 +197,28 @@ int dcd_mlp_grad(dcd_mlp* mlp, const float* d_X, const float* d_y, int64_t n, fl
  * `batch` rows (the caller shuffles); *loss_out = last minibatch loss. */
 int dcd_mlp_train(dcd_mlp* mlp, const float* d_X, const float* d_y, int64_t n, int64_t batch, int32_t epochs,
                   float lr, double* loss_out);
+
+/* Learned screen for DCD_MODE_LEARNED: every update also runs
+ * Delta-screening (R_t), scores the pool (R_t, the vertices the batch touches
+ * and their neighbours) with mlp, and evaluates R'_t = {v in R_t : p >=
+ * theta_keep} + {v in pool \ R_t : p >= theta_add} at level 0.  With judge
+ * set, the step is also run with R_t from the same state; when the learned
+ * modularity is more than 1e-3 below it, the plain result is kept and
+ * stats.fallback = 1 (q_screen then holds the rejected learned Q; otherwise
+ * the plain run's Q).  mlp stays owned by the caller and must outlive its use.
+ * Errors: DCD_EINVAL (a threshold outside [0, 1]). */
+int dcd_set_screen(dcd_ctx* ctx, dcd_mlp* mlp, float theta_keep, float theta_add, int32_t judge);
+
+/* Training data: with collection on, every update after the first computes
+ * the pool features (as in DCD_MODE_LEARNED) under C_{t-1} on G_t and, after
+ * the update, the move labels y = [community after level 0 != C_{t-1}] (train
+ * on updates in DCD_MODE_BASE).  dcd_get_screen_data copies the last update's
+ * rows: X_out (n x 12 float32), y_out (n float32), vertex_out (n int32), each
+ * host or device and may be NULL; cap is their row capacity; *n_out (host)
+ * receives n.  Errors: DCD_EINVAL (cap < n), DCD_ESTATE (no labels yet). */
+int dcd_set_collect(dcd_ctx* ctx, int32_t on);
+int dcd_get_screen_data(dcd_ctx* ctx, float* X_out, float* y_out, int32_t* vertex_out, int64_t cap,
+                        int64_t* n_out);
 
 /* ---- allocation-free evaluation ----
  * No counterpart in the paper: a service for callers that cannot allocate

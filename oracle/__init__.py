@@ -101,6 +101,7 @@ def lib():
             "orc_mlp_grad": (D, [P, P, P, I64, P]),
             "orc_mlp_grad_exact": (D, [P, P, P, I64, P]),
             "orc_mlp_loss_exact": (D, [P, P, P, I64]),
+            "orc_screen_features": (ctypes.c_int, [P, P, P, P, I64, P, I64, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -253,6 +254,21 @@ def screen(g_prev: Graph, g_t: Graph, labels0, ins=None, dels=None) -> np.ndarra
     if rc != 0:
         raise RuntimeError(f"orc_screen failed: {rc}")
     return r
+
+
+def screen_features(g_prev: Graph, g_t: Graph, labels0, ins, dels, rds):
+    """(pool mask, X n x 12) of the learned screen's features."""
+    lab = np.ascontiguousarray(labels0, dtype=np.int32)
+    ins3 = _edges3(ins)
+    del2 = _edges2(dels)
+    r = np.ascontiguousarray(rds, dtype=np.uint8)
+    pool = np.zeros(g_t.n, np.uint8)
+    X = np.zeros((g_t.n, 12), np.float32)
+    rc = lib().orc_screen_features(g_prev._h, g_t._h, _p(lab), _p(ins3), len(ins3), _p(del2), len(del2), _p(r),
+                                   _p(pool), _p(X))
+    if rc != 0:
+        raise RuntimeError(f"orc_screen_features failed: {rc}")
+    return pool, X
 
 
 class Context:

@@ -16,6 +16,7 @@
  */
 #include "dcd_oracle.h"
 
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -700,5 +701,112 @@ int orc_set_labels(orc_ctx* c, const int32_t* labels) {
     if (labels[v] < 0 || labels[v] >= c->n) return ORC_EINVAL;
   memcpy(c->labels, labels, (size_t)c->n * sizeof(int32_t));
   if (c->t == 0) c->t = 1;
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Learned-screen features (not in the paper)                          */
+/* ------------------------------------------------------------------ */
+
+/* Pool = R_t of Delta-screening, every vertex with a batch change, and the
+ * G_t-neighbours of those.  For each pool vertex of positive degree, under
+ * labels L (= C_{t-1}) on G_t, twelve float32 features (row v of X):
+ *   log1p(deg), log1p(d_w), log1p(#inserted sinks), log1p(#deleted present
+ *   sinks), inserted weight / d_w (at most 1), e_{v->C\v}/d_w, e_{v->D*}/d_w,
+ *   S(v->D*)/(d_w 2m), a_C/2m, a_{D*}/2m, log1p(|C|), [v in R_t];
+ * D* = the other neighbouring community of largest S (ties: smaller label).
+ * pool_out[v] = 1 for the rows written. */
+int orc_screen_features(const orc_graph* g_prev, const orc_graph* g_t, const int32_t* L, const int32_t* ins,
+                        int64_t n_ins, const int32_t* del, int64_t n_del, const uint8_t* rds, uint8_t* pool_out,
+                        float* X) {
+  int64_t n = g_t->n, m2;
+  int64_t* k = (int64_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+  int64_t* a = (int64_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+  int64_t* size = (int64_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+  uint8_t* touched = (uint8_t*)calloc((size_t)(n > 0 ? n : 1), 1);
+  weighted_degrees(g_t, k, &m2);
+  community_sums(n, L, k, a, size);
+  for (int64_t x = 0; x < n_ins; x++) { touched[ins[3 * x]] = 1; touched[ins[3 * x + 1]] = 1; }
+  for (int64_t x = 0; x < n_del; x++) { touched[del[2 * x]] = 1; touched[del[2 * x + 1]] = 1; }
+  for (int64_t v = 0; v < n; v++) pool_out[v] = rds[v] | touched[v];
+  for (int64_t v = 0; v < n; v++)
+    if (touched[v])
+      for (int64_t e = g_t->row_ptr[v]; e < g_t->row_ptr[v + 1]; e++) pool_out[g_t->col[e]] = 1;
+  /* distinct insert sinks, their summed weight, and distinct deleted sinks
+   * whose edge was in G_{t-1}, per source (both orientations) */
+  int64_t* nins = (int64_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+  int64_t* ndel = (int64_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+  int64_t* wins = (int64_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+  {
+    opair* p = (opair*)malloc((size_t)(2 * n_ins > 0 ? 2 * n_ins : 1) * sizeof(opair));
+    for (int64_t x = 0; x < n_ins; x++) {
+      p[2 * x].i = ins[3 * x]; p[2 * x].j = ins[3 * x + 1];
+      p[2 * x + 1].i = ins[3 * x + 1]; p[2 * x + 1].j = ins[3 * x];
+      wins[ins[3 * x]] += ins[3 * x + 2];
+      wins[ins[3 * x + 1]] += ins[3 * x + 2];
+    }
+    if (n_ins) qsort(p, (size_t)(2 * n_ins), sizeof(opair), cmp_opair);
+    for (int64_t x = 0; x < 2 * n_ins; x++)
+      if (x == 0 || p[x].i != p[x - 1].i || p[x].j != p[x - 1].j) nins[p[x].i]++;
+    free(p);
+    p = (opair*)malloc((size_t)(2 * n_del > 0 ? 2 * n_del : 1) * sizeof(opair));
+    int64_t m = 0;
+    for (int64_t x = 0; x < n_del; x++) {
+      if (find_entry(g_prev, del[2 * x], del[2 * x + 1]) < 0) continue;
+      p[m].i = del[2 * x]; p[m].j = del[2 * x + 1]; m++;
+      p[m].i = del[2 * x + 1]; p[m].j = del[2 * x]; m++;
+    }
+    if (m) qsort(p, (size_t)m, sizeof(opair), cmp_opair);
+    for (int64_t x = 0; x < m; x++)
+      if (x == 0 || p[x].i != p[x - 1].i || p[x].j != p[x - 1].j) ndel[p[x].i]++;
+    free(p);
+  }
+  int64_t maxdeg = 1;
+  for (int64_t v = 0; v < n; v++)
+    if (g_t->row_ptr[v + 1] - g_t->row_ptr[v] > maxdeg) maxdeg = g_t->row_ptr[v + 1] - g_t->row_ptr[v];
+  lw* buf = (lw*)malloc((size_t)maxdeg * sizeof(lw));
+  for (int64_t v = 0; v < n; v++) {
+    int64_t deg = g_t->row_ptr[v + 1] - g_t->row_ptr[v];
+    if (!pool_out[v] || deg == 0) { pool_out[v] = 0; continue; }
+    int32_t C = L[v];
+    int64_t cnt = 0;
+    for (int64_t e = g_t->row_ptr[v]; e < g_t->row_ptr[v + 1]; e++) {
+      if (g_t->col[e] == v) continue;
+      buf[cnt].label = L[g_t->col[e]];
+      buf[cnt].w = g_t->w[e];
+      cnt++;
+    }
+    if (cnt) qsort(buf, (size_t)cnt, sizeof(lw), cmp_lw);
+    int64_t eC = 0;
+    for (int64_t i = 0; i < cnt; i++) if (buf[i].label == C) eC += buf[i].w;
+    int32_t D = -1;
+    int64_t eD = 0;
+    i128 SD = 0;
+    for (int64_t i = 0; i < cnt;) {
+      int32_t lab = buf[i].label;
+      int64_t s = 0;
+      int64_t j = i;
+      while (j < cnt && buf[j].label == lab) s += buf[j++].w;
+      i = j;
+      if (lab == C) continue;
+      i128 S = gain_S(m2, k[v], s, eC, a[lab], a[C]);
+      if (D < 0 || S > SD) { D = lab; eD = s; SD = S; }
+    }
+    float* x = X + v * 12;
+    float fk = (float)k[v], fm = (float)m2;
+    x[0] = log1pf((float)deg);
+    x[1] = log1pf(fk);
+    x[2] = log1pf((float)nins[v]);
+    x[3] = log1pf((float)ndel[v]);
+    x[4] = k[v] > 0 ? fminf((float)wins[v] / fk, 1.f) : 0.f;
+    x[5] = k[v] > 0 ? (float)eC / fk : 0.f;
+    x[6] = k[v] > 0 ? (float)eD / fk : 0.f;
+    x[7] = (k[v] > 0 && m2 > 0 && D >= 0) ? (float)((double)SD / ((double)k[v] * (double)m2)) : 0.f;
+    x[8] = m2 > 0 ? (float)a[C] / fm : 0.f;
+    x[9] = (m2 > 0 && D >= 0) ? (float)a[D] / fm : 0.f;
+    x[10] = log1pf((float)size[C]);
+    x[11] = rds[v] ? 1.f : 0.f;
+  }
+  free(buf); free(k); free(a); free(size); free(touched); free(nins); free(ndel); free(wins);
   return ORC_OK;
 }

@@ -102,6 +102,11 @@ int orc_screen(const orc_graph* g_prev, const orc_graph* g_t, const int32_t* lab
 int orc_louvain(const orc_graph* g, const int32_t* init, const uint8_t* active,
                 int32_t* out, orc_stats* st);
 
+/* Learned-screen pool and features (not in the paper): see dcd_oracle.c. */
+int orc_screen_features(const orc_graph* g_prev, const orc_graph* g_t, const int32_t* labels, const int32_t* ins,
+                        int64_t n_ins, const int32_t* del, int64_t n_del, const uint8_t* rds, uint8_t* pool_out,
+                        float* X);
+
 /* ---- stateful incremental driver (Sec. III-D) ---- */
 orc_ctx* orc_create(int64_t n);
 void orc_destroy(orc_ctx* c);

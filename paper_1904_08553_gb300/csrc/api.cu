@@ -184,7 +184,7 @@ int dcd_create(int64_t n, const dcd_config* cfg, void* cuda_stream, dcd_ctx** ou
   dcd_config cf;
   dcd_config_default(&cf);
   if (cfg) cf = *cfg;
-  if (cf.mode < DCD_MODE_STATIC || cf.mode > DCD_MODE_GIVEN_R || cf.max_iters <= 0 || cf.max_levels <= 0 ||
+  if (cf.mode < DCD_MODE_STATIC || cf.mode > DCD_MODE_LEARNED || cf.max_iters <= 0 || cf.max_levels <= 0 ||
       cf.tau_inv <= 0)
     return DCD_EINVAL;
   dcd_ctx* c = new (std::nothrow) dcd_ctx();
@@ -243,6 +243,7 @@ int dcd_destroy(dcd_ctx* c) {
     c->w[0].reset(); c->w[1].reset();
     c->labels.reset(); c->labels_nx.reset(); c->rset.reset(); c->rgiven.reset();
     c->ins.reset(); c->del.reset(); c->dsc.reset(); c->iota.reset(); c->rset_nx.reset();
+    c->feat_X.reset(); c->feat_y.reset(); c->feat_v.reset(); c->level0.reset();
     if (c->mem.arena) cudaFreeAsync(c->mem.arena, c->stream);
     c->mem.arena = nullptr;
     cudaStreamSynchronize(c->stream);
@@ -330,18 +331,38 @@ static int update_impl(dcd_ctx* c, dcd_step_stats* st) {
   Buf<uint8_t>& rnew = c->rset_nx;
   DCD_TRY(rnew.ensure(&c->mem, n));
   const uint8_t* active = nullptr;
-  int64_t r_size = n;
+  int64_t r_size = n, r_screen = -1;
+  const bool learned = mode == DCD_MODE_LEARNED;
+  const bool collect = c->collect && !first;
+  if (learned && !c->mlp) return DCD_ESTATE;
   DCD_TRY_CUDA(cudaEventRecord(c->ev[9], s));
-  if (mode == DCD_MODE_DELTA) {
-    Buf<int64_t> a;
-    Buf<int32_t> size;
+  Buf<uint8_t> rds;  // R_t of Delta-screening
+  Buf<int64_t> a;
+  Buf<int32_t> size;
+  LearnedPool lp;
+  if (mode == DCD_MODE_DELTA || learned || collect) {
     DCD_TRY(a.alloc(&c->mem, n));
     DCD_TRY(size.alloc(&c->mem, n));
+    DCD_TRY(rds.alloc(&c->mem, n));
     DCD_TRY(community_sums(c, n, src_labels, mo.k.get(), a.get(), size.get()));
-    DCD_TRY(screen_batch(c, g, src_labels, mo.k.get(), a.get(), mo, rnew.get()));
+    DCD_TRY(screen_batch(c, g, src_labels, mo.k.get(), a.get(), mo, rds.get()));
     DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch + 9, &d->r_size, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     DCD_TRY_CUDA(cudaStreamSynchronize(s));
-    r_size = c->hscratch[9];
+    r_screen = c->hscratch[9];
+  }
+  if (learned || collect) {
+    DCD_TRY(screen_features(c, g, src_labels, mo.k.get(), a.get(), size.get(), mo, rds.get(), &lp));
+    c->feat_has_y = false;
+  }
+  if (mode == DCD_MODE_DELTA) {
+    DCD_TRY_CUDA(cudaMemcpyAsync(rnew.get(), rds.get(), n, cudaMemcpyDeviceToDevice, s));
+    r_size = r_screen;
+    active = rnew.get();
+  } else if (learned) {
+    Buf<float> p;
+    DCD_TRY(p.alloc(&c->mem, c->feat_n > 0 ? c->feat_n : 1));
+    DCD_TRY(mlp_forward_on(c->mlp, c->feat_X.get(), c->feat_n, p.get(), s));
+    DCD_TRY(learned_rset_build(c, lp, rds.get(), p.get(), rnew.get(), &r_size));
     active = rnew.get();
   } else if (mode == DCD_MODE_GIVEN_R) {
     DCD_TRY_CUDA(cudaMemcpyAsync(rnew.get(), c->rgiven.get(), n, cudaMemcpyDeviceToDevice, s));
@@ -358,11 +379,40 @@ static int update_impl(dcd_ctx* c, dcd_step_stats* st) {
   trace("update: R_t done");
 
   // ---- Algorithm 1 with R_t at level 0 ----
+  const int64_t in0 = c->hsc->in_cur;  // sum e_{i->C(i)} under C_{t-1}, for a second run
   DCD_TRY(c->labels_nx.ensure(&c->mem, n));
-  DCD_TRY(run_louvain(c, g, L0.get(), active, mo.k, c->labels_nx.get(), st));
+  if (collect) DCD_TRY(c->level0.ensure(&c->mem, n));
+  DCD_TRY(run_louvain(c, g, L0.get(), active, mo.k, c->labels_nx.get(), st, collect ? c->level0.get() : nullptr));
+  if (collect) DCD_TRY(screen_labels(c, src_labels, c->level0.get()));
+  if (learned && c->judge && st) {
+    // the judge: plain Delta-screening from the same state; keep it when the
+    // learned set loses more than 1e-3 of modularity
+    dcd_step_stats st2;
+    memset(&st2, 0, sizeof(st2));
+    Buf<int32_t> L0b, lab2;
+    DCD_TRY(L0b.alloc(&c->mem, n));
+    DCD_TRY(lab2.alloc(&c->mem, n));
+    DCD_TRY_CUDA(cudaMemcpyAsync(L0b.get(), src_labels, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    DCD_TRY_CUDA(cudaMemcpyAsync(&d->in_cur, &in0, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    DCD_TRY(run_louvain(c, g, L0b.get(), rds.get(), mo.k, lab2.get(), &st2));
+    st->q_screen = st2.q;
+    if (st->q < st2.q - 1e-3) {
+      const double ql = st->q;
+      *st = st2;
+      st->q_screen = ql;  // on a fallback, q_screen reports the rejected learned Q
+      st->fallback = 1;
+      r_size = r_screen;
+      DCD_TRY_CUDA(cudaMemcpyAsync(c->labels_nx.get(), lab2.get(), n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+      DCD_TRY_CUDA(cudaMemcpyAsync(rnew.get(), rds.get(), n, cudaMemcpyDeviceToDevice, s));
+    }
+  }
   DCD_TRY_CUDA(cudaEventRecord(c->ev[11], s));
   DCD_TRY_CUDA(cudaEventSynchronize(c->ev[11]));
   trace("update: louvain done");
+  if (st) {
+    st->r_screen = r_screen;
+    st->pool = (learned || collect) ? c->feat_n : 0;
+  }
 
   // ---- commit ----
   c->cur = nxt;
@@ -459,8 +509,42 @@ int dcd_set_rset(dcd_ctx* c, const uint8_t* r) {
 }
 
 int dcd_set_mode(dcd_ctx* c, int32_t mode) {
-  if (!c || mode < DCD_MODE_STATIC || mode > DCD_MODE_GIVEN_R) return DCD_EINVAL;
+  if (!c || mode < DCD_MODE_STATIC || mode > DCD_MODE_LEARNED) return DCD_EINVAL;
   c->mode = mode;
+  return DCD_OK;
+}
+
+int dcd_set_screen(dcd_ctx* c, dcd_mlp* mlp, float theta_keep, float theta_add, int32_t judge) {
+  if (!c || !(theta_keep >= 0.f && theta_keep <= 1.f) || !(theta_add >= 0.f && theta_add <= 1.f)) return DCD_EINVAL;
+  c->mlp = mlp;
+  c->theta_keep = theta_keep;
+  c->theta_add = theta_add;
+  c->judge = judge ? 1 : 0;
+  return DCD_OK;
+}
+
+int dcd_set_collect(dcd_ctx* c, int32_t on) {
+  if (!c) return DCD_EINVAL;
+  c->collect = on ? 1 : 0;
+  return DCD_OK;
+}
+
+int dcd_get_screen_data(dcd_ctx* c, float* X_out, float* y_out, int32_t* vertex_out, int64_t cap, int64_t* n_out) {
+  if (!c || !n_out) return DCD_EINVAL;
+  *n_out = c->feat_n;
+  if (!X_out && !y_out && !vertex_out) return DCD_OK;
+  if (cap < c->feat_n) return DCD_EINVAL;
+  if (y_out && !c->feat_has_y) return DCD_ESTATE;
+  DCD_SCOPE(c);
+  const int64_t m = c->feat_n;
+  if (m > 0) {
+    if (X_out)
+      DCD_TRY_CUDA(cudaMemcpyAsync(X_out, c->feat_X.get(), m * 12 * sizeof(float), cudaMemcpyDefault, c->stream));
+    if (y_out) DCD_TRY_CUDA(cudaMemcpyAsync(y_out, c->feat_y.get(), m * sizeof(float), cudaMemcpyDefault, c->stream));
+    if (vertex_out)
+      DCD_TRY_CUDA(cudaMemcpyAsync(vertex_out, c->feat_v.get(), m * sizeof(int32_t), cudaMemcpyDefault, c->stream));
+  }
+  DCD_TRY_CUDA(cudaStreamSynchronize(c->stream));
   return DCD_OK;
 }
 

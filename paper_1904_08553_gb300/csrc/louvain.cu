@@ -36,7 +36,21 @@ struct LV {
   const int64_t* a;
   const int32_t* size;
   int64_t m2;
+  // optional per-list-position statistics for the learned screen's features:
+  // e_{v->C\v}, e_{v->D*}, D* (-1: none) and S(v -> D*) of the best other
+  // community D* (the greedy choice before the S > 0 test and the guard)
+  int64_t* f_eC = nullptr;
+  int64_t* f_eB = nullptr;
+  int32_t* f_dB = nullptr;
+  double* f_sB = nullptr;
 };
+
+__device__ __forceinline__ double to_double(long long x) { return (double)x; }
+__device__ __forceinline__ double to_double(i128 x) {
+  const long long hi = (long long)(x >> 64);
+  const unsigned long long lo = (unsigned long long)x;
+  return (double)hi * 18446744073709551616.0 + (double)lo;
+}
 
 __device__ __forceinline__ int32_t guard_choice(int32_t C, int32_t D, const int32_t* size) {
   // singleton-swap guard (minimum-label rule)
@@ -81,6 +95,16 @@ __global__ void __launch_bounds__(256) lm_warp(LV<W> g, const int32_t* __restric
     }
     warp_argmax(S, D);
     if (lane == 0) prop[i] = (D != INT_MAX && S > 0) ? guard_choice(C, D, g.size) : C;
+    if (g.f_eC) {
+      const unsigned bm = __ballot_sync(0xffffffffu, valid && leader && lab == D);
+      const int64_t eBx = __shfl_sync(0xffffffffu, e, bm ? __ffs(bm) - 1 : 0);
+      if (lane == 0) {
+        g.f_eC[i] = eC;
+        g.f_eB[i] = bm ? eBx : 0;
+        g.f_dB[i] = D == INT_MAX ? -1 : D;
+        g.f_sB[i] = D == INT_MAX ? 0.0 : to_double(S);
+      }
+    }
     v = vn;
     b = bn;
     bend = bendn;
@@ -137,7 +161,15 @@ __global__ void __launch_bounds__(256) lm_warp_tbl(LV<W> g, const int32_t* __res
       }
     }
     warp_argmax(S, D);
-    if (lane == 0) prop[i] = (D != INT_MAX && S > 0) ? guard_choice(C, D, g.size) : C;
+    if (lane == 0) {
+      prop[i] = (D != INT_MAX && S > 0) ? guard_choice(C, D, g.size) : C;
+      if (g.f_eC) {
+        g.f_eC[i] = eC;
+        g.f_eB[i] = D == INT_MAX ? 0 : tbl_get(keys, vals, mask, D);
+        g.f_dB[i] = D == INT_MAX ? -1 : D;
+        g.f_sB[i] = D == INT_MAX ? 0.0 : to_double(S);
+      }
+    }
     __syncwarp();
   }
 }
@@ -209,7 +241,15 @@ __global__ void __launch_bounds__(THREADS) lm_block(LV<W> g, const int32_t* __re
       S = lane < NW ? redS[lane] : gain_lowest<ST>();
       D = lane < NW ? redD[lane] : INT_MAX;
       warp_argmax(S, D);
-      if (lane == 0) prop[i] = (D != INT_MAX && S > 0) ? guard_choice(C, D, g.size) : C;
+      if (lane == 0) {
+        prop[i] = (D != INT_MAX && S > 0) ? guard_choice(C, D, g.size) : C;
+        if (g.f_eC) {
+          g.f_eC[i] = eC;
+          g.f_eB[i] = D == INT_MAX ? 0 : tbl_get(keys, vals, mask, D);
+          g.f_dB[i] = D == INT_MAX ? -1 : D;
+          g.f_sB[i] = D == INT_MAX ? 0.0 : to_double(S);
+        }
+      }
     }
     __syncthreads();
   }
@@ -681,6 +721,104 @@ struct LevelRun {
   float ms_lm = 0.f, ms_apply = 0.f;
 };
 
+// Degree bins of the active vertices of one level and the hub tables.
+struct Bins {
+  Buf<int32_t> list;
+  int64_t cnt[4] = {0, 0, 0, 0};
+  int64_t total = 0, act_deg = 0, n_active = 0;
+  size_t large_smem = 0;
+  Buf<int32_t> hkeys;
+  Buf<unsigned long long> hvals;
+  int64_t hub_cap = 0, hub_ctas = 0;
+};
+
+template <typename W>
+int make_bins(dcd_ctx* c, const Csr<W>& g, const uint8_t* active, Bins* b) {
+  cudaStream_t s = c->stream;
+  DevScalars* d = c->dsc.get();
+  const int64_t nv = g.n;
+  const int T = 256;
+  DCD_TRY_CUDA(cudaMemsetAsync(&d->bin_cnt[0], 0, sizeof(int64_t) * 7, s));  // bins, maxdeg, act_deg, ncomm
+  DCD_TRY_CUDA(cudaMemsetAsync(&d->bin2_maxdeg, 0, sizeof(int64_t), s));
+  ::dcd::count_launch(), bin_count<<<grid_for(nv, T), T, 0, s>>>(g.rp, nv, active, d);
+  DCD_LAUNCH_CHECK();
+  DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+  DCD_TRY_CUDA(cudaStreamSynchronize(s));
+  for (int x = 0; x < 4; x++) b->cnt[x] = c->hsc->bin_cnt[x];
+  b->total = b->cnt[0] + b->cnt[1] + b->cnt[2] + b->cnt[3];
+  const int64_t hub_max = c->hsc->bin_maxdeg;
+  b->large_smem = (size_t)table_cap(c->hsc->bin2_maxdeg > 0 ? c->hsc->bin2_maxdeg : 1) * 12;
+  b->act_deg = c->hsc->act_deg;
+  b->n_active = c->hsc->ncomm;  // bin_count leaves the active count here
+  Buf<int32_t> cursor;
+  DCD_TRY(b->list.alloc(&c->mem, b->total));
+  DCD_TRY(cursor.alloc(&c->mem, 4));
+  DCD_TRY_CUDA(cudaMemsetAsync(cursor.get(), 0, 4 * sizeof(int32_t), s));
+  if (b->total > 0) {
+    ::dcd::count_launch(), bin_scatter<<<grid_for(nv, T), T, 0, s>>>(g.rp, nv, active, d, cursor.get(),
+                                                                       b->list.get());
+    DCD_LAUNCH_CHECK();
+  }
+  // hub tables in global memory: one region per CTA, sized for the largest hub
+  if (b->cnt[3]) {
+    b->hub_cap = table_cap(hub_max);
+    const int64_t budget = (int64_t)1 << 30;  // bytes for hub tables
+    int64_t hc = budget / (b->hub_cap * 12);
+    if (hc < 1) hc = 1;
+    if (hc > b->cnt[3]) hc = b->cnt[3];
+    if (hc > 4 * (int64_t)c->sms) hc = 4 * (int64_t)c->sms;
+    b->hub_ctas = hc;
+    DCD_TRY(b->hkeys.alloc(&c->mem, hc * b->hub_cap));
+    DCD_TRY(b->hvals.alloc(&c->mem, hc * b->hub_cap));
+  }
+  return DCD_OK;
+}
+
+// One local-move evaluation of every binned vertex (proposals in prop[]).
+template <typename W, typename ST>
+int launch_lm_st(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop) {
+  cudaStream_t s = c->stream;
+  const int T = 256;
+  const size_t mid_smem = (size_t)8 * kMidCap * 12;
+  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_warp_tbl<W, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mid_smem));
+  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_block<W, ST, kLargeThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)((size_t)kLargeCap * 12)));
+  const int32_t* lst = b.list.get();
+  const int64_t* cnt = b.cnt;
+  LV<W> g1 = lv, g2 = lv, g3 = lv;  // feature outputs shifted to each bin's list offset
+  auto shift = [](LV<W>& x, int64_t o) {
+    if (x.f_eC) {
+      x.f_eC += o;
+      x.f_eB += o;
+      x.f_dB += o;
+      x.f_sB += o;
+    }
+  };
+  shift(g1, cnt[0]);
+  shift(g2, cnt[0] + cnt[1]);
+  shift(g3, cnt[0] + cnt[1] + cnt[2]);
+  if (cnt[0]) count_launch(), lm_warp<W, ST><<<grid_for(cnt[0] * 32, T, 16), T, 0, s>>>(lv, lst, cnt[0], prop);
+  if (cnt[1])
+    count_launch(), lm_warp_tbl<W, ST><<<grid_for(cnt[1] * 32, T, 8), T, mid_smem, s>>>(g1, lst + cnt[0], cnt[1],
+                                                                                         prop + cnt[0]);
+  if (cnt[2])
+    count_launch(), lm_block<W, ST, kLargeThreads>
+        <<<(unsigned)(cnt[2] < 8 * c->sms ? cnt[2] : 8 * c->sms), kLargeThreads, b.large_smem, s>>>(
+            g2, lst + cnt[0] + cnt[1], cnt[2], prop + cnt[0] + cnt[1], nullptr, nullptr, 0);
+  if (cnt[3])
+    count_launch(), lm_block<W, ST, kHubThreads><<<(unsigned)b.hub_ctas, kHubThreads, 0, s>>>(
+        g3, lst + cnt[0] + cnt[1] + cnt[2], cnt[3], prop + cnt[0] + cnt[1] + cnt[2], b.hkeys.get(), b.hvals.get(),
+        b.hub_cap);
+  DCD_LAUNCH_CHECK();
+  return DCD_OK;
+}
+
+template <typename W>
+int launch_lm(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop) {
+  if (lv.m2 >= ((int64_t)1 << 31)) return launch_lm_st<W, i128>(c, lv, b, prop);
+  return launch_lm_st<W, long long>(c, lv, b, prop);
+}
+
 template <typename W>
 int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<int64_t>& a, Buf<int32_t>& size,
               const uint8_t* active, LevelRun* out) {
@@ -689,25 +827,12 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
   const int64_t nv = g.n;
   const int T = 256;
 
-  // ---- bins of the active vertices ----
-  DCD_TRY_CUDA(cudaMemsetAsync(&d->bin_cnt[0], 0, sizeof(int64_t) * 7, s));  // bins, maxdeg, act_deg, ncomm
-  DCD_TRY_CUDA(cudaMemsetAsync(&d->bin2_maxdeg, 0, sizeof(int64_t), s));
-  ::dcd::count_launch(), bin_count<<<grid_for(nv, T), T, 0, s>>>(g.rp, nv, active, d);
-  DCD_LAUNCH_CHECK();
-  DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
-  DCD_TRY_CUDA(cudaStreamSynchronize(s));
-  int64_t cnt[4];
-  for (int b = 0; b < 4; b++) cnt[b] = c->hsc->bin_cnt[b];
-  const int64_t total = cnt[0] + cnt[1] + cnt[2] + cnt[3];
-  const int64_t hub_max = c->hsc->bin_maxdeg;
-  const size_t large_smem_used = (size_t)table_cap(c->hsc->bin2_maxdeg > 0 ? c->hsc->bin2_maxdeg : 1) * 12;
-  const int64_t act_deg = c->hsc->act_deg;
-  const int64_t n_active = c->hsc->ncomm;  // bin_count leaves the active count here
+  Bins bins;
+  DCD_TRY(make_bins<W>(c, g, active, &bins));
   trace("level: binned");
-
-  Buf<int32_t> list, cursor, prop, Lprev, mvit, moved, moved_cnt, moved_big, moved_big_cnt;
-  DCD_TRY(list.alloc(&c->mem, total));
-  DCD_TRY(cursor.alloc(&c->mem, 4));
+  const int64_t* cnt = bins.cnt;
+  const int64_t total = bins.total;
+  Buf<int32_t> prop, Lprev, mvit, moved, moved_cnt, moved_big, moved_big_cnt;
   DCD_TRY(prop.alloc(&c->mem, total));
   DCD_TRY(Lprev.alloc(&c->mem, nv));
   DCD_TRY(mvit.alloc(&c->mem, nv));
@@ -715,68 +840,16 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
   DCD_TRY(moved_cnt.alloc(&c->mem, 1));
   DCD_TRY(moved_big.alloc(&c->mem, cnt[2] + cnt[3]));
   DCD_TRY(moved_big_cnt.alloc(&c->mem, 1));
-  DCD_TRY_CUDA(cudaMemsetAsync(cursor.get(), 0, 4 * sizeof(int32_t), s));
-  if (total > 0) {
-    ::dcd::count_launch(), bin_scatter<<<grid_for(nv, T), T, 0, s>>>(g.rp, nv, active, d, cursor.get(), list.get());
-    DCD_LAUNCH_CHECK();
-  }
   ::dcd::count_launch(), fill_i32<<<grid_for(nv, T), T, 0, s>>>(mvit.get(), nv, -1);
   DCD_LAUNCH_CHECK();
-
-  // hub tables in global memory: one region per CTA, sized for the largest hub
-  const int64_t hub_cap = cnt[3] ? (int64_t)table_cap(hub_max) : 0;
-  int64_t hub_ctas = 0;
-  Buf<int32_t> hkeys;
-  Buf<unsigned long long> hvals;
-  if (cnt[3]) {
-    const int64_t budget = (int64_t)1 << 30;  // bytes for hub tables
-    hub_ctas = budget / (hub_cap * 12);
-    if (hub_ctas < 1) hub_ctas = 1;
-    if (hub_ctas > cnt[3]) hub_ctas = cnt[3];
-    if (hub_ctas > 4 * (int64_t)c->sms) hub_ctas = 4 * (int64_t)c->sms;
-    DCD_TRY(hkeys.alloc(&c->mem, hub_ctas * hub_cap));
-    DCD_TRY(hvals.alloc(&c->mem, hub_ctas * hub_cap));
-  }
-
   const int sq_ctas = grid_for(nv, T, 4);
-
-  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_warp_tbl<W, long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)((size_t)8 * kMidCap * 12)));
-  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_warp_tbl<W, i128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)((size_t)8 * kMidCap * 12)));
-  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_block<W, long long, kLargeThreads>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((size_t)kLargeCap * 12)));
-  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_block<W, i128, kLargeThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)((size_t)kLargeCap * 12)));
-  LV<W> lv{g.rp, g.col, g.w, kbuf.get(), L, a.get(), size.get(), 0};
-  lv.m2 = c->hsc->m2;
-  const bool wide = lv.m2 >= ((int64_t)1 << 31);
-  const int32_t* lst = list.get();
-  const size_t mid_smem = (size_t)8 * kMidCap * 12, large_smem = (size_t)kLargeCap * 12;
+  LV<W> lv{g.rp, g.col, g.w, kbuf.get(), L, a.get(), size.get(), c->hsc->m2};
+  const int32_t* lst = bins.list.get();
 
   for (;;) {
     const int32_t iter = (int32_t)out->passes;
     DCD_TRY_CUDA(cudaEventRecord(c->ev[2], s));
-#define DCD_LM_LAUNCH(ST)                                                                                          \
-  do {                                                                                                             \
-    if (cnt[0])                                                                                                    \
-      ::dcd::count_launch(), lm_warp<W, ST><<<grid_for(cnt[0] * 32, T, 16), T, 0, s>>>(lv, lst, cnt[0], prop.get());                      \
-    if (cnt[1])                                                                                                    \
-      ::dcd::count_launch(), lm_warp_tbl<W, ST><<<grid_for(cnt[1] * 32, T, 8), T, mid_smem, s>>>(                  \
-          lv, lst + cnt[0], cnt[1], prop.get() + cnt[0]);                                                          \
-    if (cnt[2])                                                                                                    \
-      ::dcd::count_launch(), lm_block<W, ST, kLargeThreads><<<(unsigned)(cnt[2] < 8 * c->sms ? cnt[2] : 8 * c->sms), kLargeThreads,      \
-                                       large_smem_used, s>>>(lv, lst + cnt[0] + cnt[1], cnt[2],                         \
-                                                        prop.get() + cnt[0] + cnt[1], nullptr, nullptr, 0);       \
-    if (cnt[3])                                                                                                    \
-      ::dcd::count_launch(), lm_block<W, ST, kHubThreads><<<(unsigned)hub_ctas, kHubThreads, 0, s>>>(                                     \
-          lv, lst + cnt[0] + cnt[1] + cnt[2], cnt[3], prop.get() + cnt[0] + cnt[1] + cnt[2], hkeys.get(),         \
-          hvals.get(), hub_cap);                                                                                   \
-  } while (0)
-    if (wide) DCD_LM_LAUNCH(i128);
-    else DCD_LM_LAUNCH(long long);
-#undef DCD_LM_LAUNCH
-    DCD_LAUNCH_CHECK();
+    DCD_TRY(launch_lm<W>(c, lv, bins, prop.get()));
     DCD_TRY_CUDA(cudaEventRecord(c->ev[3], s));
     DCD_TRY_CUDA(cudaMemsetAsync(moved_cnt.get(), 0, sizeof(int32_t), s));
     DCD_TRY_CUDA(cudaMemsetAsync(moved_big_cnt.get(), 0, sizeof(int32_t), s));
@@ -806,8 +879,8 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
     out->ms_lm += t1;
     out->ms_apply += t2;
     out->passes++;
-    out->edges += act_deg;
-    out->verts += n_active;
+    out->edges += bins.act_deg;
+    out->verts += bins.n_active;
     out->moves += c->hsc->moves;
     if (c->hsc->stop) break;
   }
@@ -907,6 +980,33 @@ int coarsen(dcd_ctx* c, const Csr<W>& g, const int32_t* L, const int32_t* cid, i
 
 }  // namespace
 
+int pool_stats(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* L, const int64_t* k, const int64_t* a,
+               const int32_t* size, const uint8_t* mask, PoolStats* out) {
+  Bins bins;
+  DCD_TRY(make_bins<int32_t>(c, g, mask, &bins));
+  const int64_t m = bins.total;
+  out->count = m;
+  DCD_TRY(out->eC.alloc(&c->mem, m));
+  DCD_TRY(out->eB.alloc(&c->mem, m));
+  DCD_TRY(out->dB.alloc(&c->mem, m));
+  DCD_TRY(out->sB.alloc(&c->mem, m));
+  Buf<int32_t> prop;
+  DCD_TRY(prop.alloc(&c->mem, m));
+  LV<int32_t> lv{g.rp, g.col, g.w, k, L, a, size, c->hsc->m2};
+  lv.f_eC = out->eC.get();
+  lv.f_eB = out->eB.get();
+  lv.f_dB = out->dB.get();
+  lv.f_sB = out->sB.get();
+  if (m) DCD_TRY(launch_lm<int32_t>(c, lv, bins, prop.get()));
+  out->list.reset();
+  out->list.p = bins.list.p;
+  out->list.n = bins.list.n;
+  out->list.mem = bins.list.mem;
+  bins.list.p = nullptr;
+  bins.list.n = 0;
+  return DCD_OK;
+}
+
 int community_sums(dcd_ctx* c, int64_t n, const int32_t* labels, const int64_t* k, int64_t* a, int32_t* size) {
   cudaStream_t s = c->stream;
   DCD_TRY_CUDA(cudaMemsetAsync(a, 0, n * sizeof(int64_t), s));
@@ -917,7 +1017,7 @@ int community_sums(dcd_ctx* c, int64_t n, const int32_t* labels, const int64_t* 
 }
 
 int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint8_t* active0, Buf<int64_t>& k0,
-                int32_t* out_labels, dcd_step_stats* st) {
+                int32_t* out_labels, dcd_step_stats* st, int32_t* level0_out) {
   cudaStream_t s = c->stream;
   DevScalars* d = c->dsc.get();
   const int T = 256;
@@ -958,6 +1058,8 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
     LevelRun lr;
     if (level == 0) {
       DCD_TRY(run_level<int32_t>(c, *g_l0, L, *kcur, a, size, active, &lr));
+      if (level0_out)
+        DCD_TRY_CUDA(cudaMemcpyAsync(level0_out, L, n0 * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     } else {
       DCD_TRY(run_level<int64_t>(c, *g_lc, L, *kcur, a, size, nullptr, &lr));
     }

@@ -447,6 +447,17 @@ uint64_t splitmix(uint64_t& s) {
 
 }  // namespace
 
+namespace dcd {
+int mlp_forward_on(dcd_mlp* m, const float* X, int64_t n, float* p, cudaStream_t s) {
+  if (n <= 0) return DCD_OK;
+  const int64_t tiles = cdiv(n, 16);
+  const int64_t ctas = cdiv(tiles, 4) < 8 * (int64_t)num_sms() ? cdiv(tiles, 4) : 8 * (int64_t)num_sms();
+  count_launch(), mlp_infer<<<(unsigned)ctas, 128, 0, s>>>(weights_of(m), X, n, p);
+  DCD_LAUNCH_CHECK();
+  return DCD_OK;
+}
+}  // namespace dcd
+
 extern "C" {
 
 int dcd_mlp_create(uint64_t seed, void* cuda_stream, dcd_mlp** out) {

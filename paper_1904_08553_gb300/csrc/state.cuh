@@ -94,6 +94,18 @@ struct dcd_ctx {
 
   dcd::Buf<int32_t> iota;  // 0..n-1 (singleton labels)
 
+  // learned screen (DCD_MODE_LEARNED) and training-data collection
+  struct dcd_mlp* mlp = nullptr;
+  float theta_keep = 0.5f, theta_add = 0.5f;
+  int32_t judge = 0;
+  int32_t collect = 0;
+  dcd::Buf<float> feat_X;     // pool rows x 12
+  dcd::Buf<float> feat_y;     // pool rows (move labels)
+  dcd::Buf<int32_t> feat_v;   // vertex of each pool row
+  dcd::Buf<int32_t> level0;   // level-0 labels of the last collected update
+  int64_t feat_n = 0;
+  bool feat_has_y = false;
+
   cudaEvent_t ev[16] = {};
 };
 
@@ -119,7 +131,33 @@ int screen_batch(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* labels0, cons
 // level-0 result), level-0 active flags (NULL = all), k and m2 of G_t.
 // Writes canonical labels to out_labels and fills stats.
 int run_louvain(dcd_ctx* c, const Csr<int32_t>& g, int32_t* labels0, const uint8_t* active0,
-                Buf<int64_t>& k, int32_t* out_labels, dcd_step_stats* st);
+                Buf<int64_t>& k, int32_t* out_labels, dcd_step_stats* st, int32_t* level0_out = nullptr);
+
+// louvain.cu: statistics of the learned screen's pool (mask over vertices):
+// the local-move evaluation of every pool vertex of positive degree, without
+// moving, in degree-bin order.  list[i] is the vertex of row i.
+struct PoolStats {
+  Buf<int32_t> list;
+  Buf<int64_t> eC, eB;  // e_{v->C\v}, e_{v->D*}
+  Buf<int32_t> dB;      // D* (-1: no other community)
+  Buf<double> sB;       // S(v -> D*)
+  int64_t count = 0;
+};
+int pool_stats(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* L, const int64_t* k, const int64_t* a,
+               const int32_t* size, const uint8_t* mask, PoolStats* out);
+
+// features.cu: the learned screen's pool, features, R'_t and move labels.
+struct LearnedPool {
+  PoolStats st;
+};
+int screen_features(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* L0, const int64_t* k, const int64_t* a,
+                    const int32_t* size, const MergeOut& mo, const uint8_t* rds, LearnedPool* out);
+int learned_rset_build(dcd_ctx* c, const LearnedPool& lp, const uint8_t* rds, const float* p, uint8_t* r,
+                       int64_t* r_size);
+int screen_labels(dcd_ctx* c, const int32_t* before, const int32_t* after);
+
+// mlp.cu: forward pass of the network on a given stream (no synchronisation).
+int mlp_forward_on(struct dcd_mlp* m, const float* X, int64_t n, float* p, cudaStream_t s);
 
 // louvain.cu: community sums a (by label) and sizes from k and labels.
 int community_sums(dcd_ctx* c, int64_t n, const int32_t* labels, const int64_t* k, int64_t* a,

@@ -19,7 +19,7 @@ _PKG = Path(__file__).resolve().parent
 LIB_PATH = _PKG / "libdcd.so"
 
 DCD_OK, DCD_EINVAL, DCD_ENOMEM, DCD_ECUDA, DCD_ESTATE, DCD_EOVERFLOW, DCD_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
-MODE_STATIC, MODE_BASE, MODE_DELTA, MODE_GIVEN_R = 0, 1, 2, 3
+MODE_STATIC, MODE_BASE, MODE_DELTA, MODE_GIVEN_R, MODE_LEARNED = 0, 1, 2, 3, 4
 
 EXPORTED = [
     "dcd_config_default", "dcd_create", "dcd_destroy", "dcd_apply_batch", "dcd_apply_batch_device",
@@ -27,6 +27,7 @@ EXPORTED = [
     "dcd_get_graph", "dcd_kernel_launches", "dcd_strerror", "dcd_last_cuda_error",
     "dcd_modularity_noalloc", "dcd_mlp_create", "dcd_mlp_destroy", "dcd_mlp_set_params",
     "dcd_mlp_get_params", "dcd_mlp_forward", "dcd_mlp_grad", "dcd_mlp_train",
+    "dcd_set_screen", "dcd_set_collect", "dcd_get_screen_data",
 ]
 MLP_FEATURES, MLP_HIDDEN, MLP_PARAMS = 12, 64, 5057
 NOALLOC_MAX_N = 1048056
@@ -58,7 +59,8 @@ _STAT_F32 = ["ms_total", "ms_merge", "ms_screen", "ms_local_move", "ms_apply", "
 class StepStats(ctypes.Structure):
     _fields_ = ([(k, ctypes.c_int64) for k in _STAT_I64] + [("q", ctypes.c_double)] +
                 [("ins_records", ctypes.c_int64), ("del_records", ctypes.c_int64),
-                 ("launches", ctypes.c_int64)] +
+                 ("launches", ctypes.c_int64), ("r_screen", ctypes.c_int64), ("pool", ctypes.c_int64),
+                 ("fallback", ctypes.c_int64), ("q_screen", ctypes.c_double)] +
                 [(k, ctypes.c_float) for k in _STAT_F32] + [("reserved_f", ctypes.c_float * 9)])
 
     @property
@@ -110,6 +112,9 @@ def lib():
             "dcd_mlp_forward": (INT, [P, P, I64, P]),
             "dcd_mlp_grad": (INT, [P, P, P, I64, P, P]),
             "dcd_mlp_train": (INT, [P, P, P, I64, I64, I32, ctypes.c_float, P]),
+            "dcd_set_screen": (INT, [P, P, ctypes.c_float, ctypes.c_float, I32]),
+            "dcd_set_collect": (INT, [P, I32]),
+            "dcd_get_screen_data": (INT, [P, P, P, P, I64, P]),
             "dcd_strerror": (ctypes.c_char_p, [INT]),
             "dcd_last_cuda_error": (ctypes.c_char_p, []),
         }
@@ -232,6 +237,22 @@ def dcd_kernel_launches() -> int:
     return int(lib().dcd_kernel_launches())
 
 
+def dcd_set_screen(h, mlp_handle, theta_keep: float = 0.5, theta_add: float = 0.5, judge: bool = True) -> None:
+    _check(lib().dcd_set_screen(h, mlp_handle, float(theta_keep), float(theta_add), int(bool(judge))),
+           "dcd_set_screen")
+
+
+def dcd_set_collect(h, on: bool = True) -> None:
+    _check(lib().dcd_set_collect(h, int(bool(on))), "dcd_set_collect")
+
+
+def dcd_get_screen_data(h, X_out=None, y_out=None, vertex_out=None, cap: int = 0) -> int:
+    n = ctypes.c_int64()
+    _check(lib().dcd_get_screen_data(h, _ptr(X_out), _ptr(y_out), _ptr(vertex_out), int(cap), ctypes.byref(n)),
+           "dcd_get_screen_data")
+    return n.value
+
+
 def dcd_strerror(code: int) -> str:
     return lib().dcd_strerror(int(code)).decode()
 
@@ -309,6 +330,21 @@ class Context:
 
     def graph(self):
         return dcd_get_graph(self._h, self.n)
+
+    def set_screen(self, mlp, theta_keep=0.5, theta_add=0.5, judge=True):
+        dcd_set_screen(self._h, None if mlp is None else mlp.handle, theta_keep, theta_add, judge)
+
+    def set_collect(self, on=True):
+        dcd_set_collect(self._h, on)
+
+    def screen_data(self, with_labels=True):
+        """(X, y or None, vertices) of the last update's pool, as numpy arrays."""
+        n = dcd_get_screen_data(self._h)
+        X = np.zeros((n, MLP_FEATURES), np.float32)
+        y = np.zeros(n, np.float32) if with_labels else None
+        v = np.zeros(n, np.int32)
+        dcd_get_screen_data(self._h, X, y, v, n)
+        return X, y, v
 
 
 # ---- learned screen network -------------------------------------------------
