@@ -338,6 +338,103 @@ def gpu_arm(args):
         dist.destroy_process_group()
 
 
+
+# ------------------------------------------------------------------ learned screen
+
+def learned_arm(args):
+    """Learned screen vs plain Delta-screening on the LFR stream: train the
+    network on move labels of full re-evaluation (BASE) runs of the same
+    generator at n = 200,000, then run the evaluation stream three times:
+    plain Delta-screening, the learned screen, and the learned screen with the
+    judge (plain Delta-screening from the same state; a step more than 1e-3
+    below it is redone)."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1904_08553_gb300 import dcd, synth
+
+    torch.cuda.set_device(0)
+    T = 1 + args.warmup + args.steps
+    Xs, ys = [], []
+    t0 = time.time()
+    for r in range(args.train_seeds):
+        n_tr = 200_000
+        s = synth.lfr(synth.seed_for(4, r), n_tr, int(31.5 * n_tr), 12, kmax=5000.0, smax=12_500.0)
+        ctx = dcd.Context(n_tr, mode=dcd.MODE_BASE)
+        ctx.set_collect(True)
+        for t, (ins, dels) in enumerate(s.steps):
+            ctx.apply_batch(ins, dels)
+            ctx.update(labels_out=None)
+            if t > 0:
+                X, y, _ = ctx.screen_data()
+                Xs.append(X)
+                ys.append(y)
+        ctx.close()
+    X = np.concatenate(Xs)
+    y = np.concatenate(ys)
+    perm = np.random.default_rng(0).permutation(len(X))
+    dX = torch.from_numpy(X[perm]).cuda()
+    dy = torch.from_numpy(y[perm]).cuda()
+    mlp = dcd.Mlp(seed=11)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    loss = mlp.train(dX, dy, len(X), batch=8192, epochs=args.epochs, lr=2e-3)
+    ev1.record()
+    torch.cuda.synchronize()
+    train_ms = ev0.elapsed_time(ev1)
+    gen_s = time.time() - t0
+
+    stream = make_stream(args.n, T, replica=9)
+    n = stream.n
+    d_ins = [torch.from_numpy(np.ascontiguousarray(i)).cuda() for i, _ in stream.steps]
+    d_del = []
+    for _, dels in stream.steps:
+        dd = np.zeros((len(dels), 3), np.int32)
+        dd[:, :2] = dels
+        d_del.append(torch.from_numpy(dd).cuda())
+
+    def run(mode, judge):
+        ctx = dcd.Context(n, mode=mode)
+        if mode == dcd.MODE_LEARNED:
+            ctx.set_screen(mlp, theta_keep=args.theta_keep, theta_add=args.theta_add, judge=judge)
+        out = []
+        for t in range(T):
+            ctx.apply_batch_device(d_ins[t], len(stream.steps[t][0]), d_del[t], len(stream.steps[t][1]))
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            _, q, st = ctx.update(labels_out=None)
+            ms = (time.perf_counter() - a) * 1e3
+            if t >= 1 + args.warmup:
+                out.append((ms, q, st.r_size, st.r_screen, st.fallback, st.q_screen, st.pool))
+        ctx.close()
+        return out
+
+    plain = run(dcd.MODE_DELTA, False)
+    learned = run(dcd.MODE_LEARNED, False)
+    judged = run(dcd.MODE_LEARNED, True)
+    gap = [p[1] - l[1] for p, l in zip(plain, learned)]
+    line = {
+        "metric": "learned screen vs Delta-screening: |R_t|, ms per step, modularity gap",
+        "workload": workload_desc(T).replace("lfr_2m", f"lfr n={n:,}"),
+        "training": {"runs": args.train_seeds, "n": 200_000, "steps": 12, "rows": int(len(X)),
+                     "positive_fraction": float(y.mean()), "epochs": args.epochs, "final_loss": loss,
+                     "train_ms_gpu": train_ms, "data_s": gen_s},
+        "thresholds": {"keep": args.theta_keep, "add": args.theta_add},
+        "r_fraction_delta": float(np.mean([p[2] for p in plain]) / n),
+        "r_fraction_learned": float(np.mean([l[2] for l in learned]) / n),
+        "ms_per_step_delta": float(np.mean([p[0] for p in plain])),
+        "ms_per_step_learned": float(np.mean([l[0] for l in learned])),
+        "ms_per_step_learned_judged": float(np.mean([j[0] for j in judged])),
+        "q_gap_max": float(max(gap)), "q_gap_mean": float(np.mean(gap)),
+        "steps_within_1e-3": int(sum(g <= 1e-3 for g in gap)), "steps": len(gap),
+        "judged_fallbacks": int(sum(j[4] for j in judged)),
+        "pool_fraction": float(np.mean([l[6] for l in learned]) / n),
+    }
+    print(json.dumps(line), flush=True)
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -347,11 +444,18 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--n", type=int, default=LFR_N, help="vertex count (smaller cases for profiling)")
+    ap.add_argument("--workload", default="lfr_2m", choices=["lfr_2m", "learned"])
+    ap.add_argument("--train-seeds", type=int, default=8)
+    ap.add_argument("--epochs", type=int, default=4)
+    ap.add_argument("--theta-keep", type=float, default=0.3)
+    ap.add_argument("--theta-add", type=float, default=0.9)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload == "learned":
+        learned_arm(args)
     else:
         gpu_arm(args)
 
