@@ -95,7 +95,10 @@ typedef struct {
   float ms_apply;        /* move apply + modularity tracking                        */
   float ms_coarsen;      /* graph compaction (all levels)                           */
   float ms_finish;       /* label composition, canonical labels                     */
-  float reserved_f[9];
+  float ms_bin[4];       /* local-move time per degree bin: <=32, 33..256, 257..4096, more */
+  float reserved_f[5];
+  int64_t edges_bin[4];  /* entries scanned per degree bin (all passes)              */
+  int64_t verts_bin[4];  /* vertices evaluated per degree bin (all passes)           */
 } dcd_step_stats;
 
 typedef struct dcd_ctx dcd_ctx;

@@ -456,10 +456,13 @@ __global__ void lm_decide(DevScalars* d, int mode, const int32_t* __restrict__ m
 
 __global__ void bin_count(const int64_t* __restrict__ rp, int64_t n, const uint8_t* __restrict__ active,
                           DevScalars* d) {
-  __shared__ unsigned long long sc[4];
+  __shared__ unsigned long long sc[4], sdb[4];
   __shared__ unsigned long long sdeg, sact;
   __shared__ long long smax, smax2;
-  if (threadIdx.x < 4) sc[threadIdx.x] = 0;
+  if (threadIdx.x < 4) {
+    sc[threadIdx.x] = 0;
+    sdb[threadIdx.x] = 0;
+  }
   if (threadIdx.x == 0) {
     sdeg = 0;
     sact = 0;
@@ -475,11 +478,15 @@ __global__ void bin_count(const int64_t* __restrict__ rp, int64_t n, const uint8
     if (deg == 0) continue;
     const int bin = deg <= kBinWarpMax ? 0 : deg <= kBinMidMax ? 1 : deg <= kBinLargeMax ? 2 : 3;
     atomicAdd(&sc[bin], 1ull);
+    atomicAdd(&sdb[bin], (unsigned long long)deg);
     if (bin == 3) atomicMax(&smax, (long long)deg);
     if (bin == 2) atomicMax(&smax2, (long long)deg);
   }
   __syncthreads();
-  if (threadIdx.x < 4 && sc[threadIdx.x]) atomicAdd((unsigned long long*)&d->bin_cnt[threadIdx.x], sc[threadIdx.x]);
+  if (threadIdx.x < 4 && sc[threadIdx.x]) {
+    atomicAdd((unsigned long long*)&d->bin_cnt[threadIdx.x], sc[threadIdx.x]);
+    atomicAdd((unsigned long long*)&d->bin_deg[threadIdx.x], sdb[threadIdx.x]);
+  }
   if (threadIdx.x == 0) {
     atomicAdd((unsigned long long*)&d->act_deg, sdeg);
     atomicAdd((unsigned long long*)&d->ncomm, sact);
@@ -719,6 +726,8 @@ inline bool h_below_tau(i128 gain, i128 base, int64_t tau_inv) {
 struct LevelRun {
   int64_t passes = 0, moves = 0, edges = 0, verts = 0;
   float ms_lm = 0.f, ms_apply = 0.f;
+  float ms_bin[4] = {0.f, 0.f, 0.f, 0.f};
+  int64_t edges_bin[4] = {0, 0, 0, 0}, verts_bin[4] = {0, 0, 0, 0};
 };
 
 // Degree bins of the active vertices of one level and the hub tables.
@@ -726,6 +735,7 @@ struct Bins {
   Buf<int32_t> list;
   int64_t cnt[4] = {0, 0, 0, 0};
   int64_t total = 0, act_deg = 0, n_active = 0;
+  int64_t deg[4] = {0, 0, 0, 0};
   size_t large_smem = 0;
   Buf<int32_t> hkeys;
   Buf<unsigned long long> hvals;
@@ -739,12 +749,15 @@ int make_bins(dcd_ctx* c, const Csr<W>& g, const uint8_t* active, Bins* b) {
   const int64_t nv = g.n;
   const int T = 256;
   DCD_TRY_CUDA(cudaMemsetAsync(&d->bin_cnt[0], 0, sizeof(int64_t) * 7, s));  // bins, maxdeg, act_deg, ncomm
-  DCD_TRY_CUDA(cudaMemsetAsync(&d->bin2_maxdeg, 0, sizeof(int64_t), s));
+  DCD_TRY_CUDA(cudaMemsetAsync(&d->bin2_maxdeg, 0, 5 * sizeof(int64_t), s));  // bin2_maxdeg, bin_deg[4]
   ::dcd::count_launch(), bin_count<<<grid_for(nv, T), T, 0, s>>>(g.rp, nv, active, d);
   DCD_LAUNCH_CHECK();
   DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
   DCD_TRY_CUDA(cudaStreamSynchronize(s));
-  for (int x = 0; x < 4; x++) b->cnt[x] = c->hsc->bin_cnt[x];
+  for (int x = 0; x < 4; x++) {
+    b->cnt[x] = c->hsc->bin_cnt[x];
+    b->deg[x] = c->hsc->bin_deg[x];
+  }
   b->total = b->cnt[0] + b->cnt[1] + b->cnt[2] + b->cnt[3];
   const int64_t hub_max = c->hsc->bin_maxdeg;
   b->large_smem = (size_t)table_cap(c->hsc->bin2_maxdeg > 0 ? c->hsc->bin2_maxdeg : 1) * 12;
@@ -776,7 +789,7 @@ int make_bins(dcd_ctx* c, const Csr<W>& g, const uint8_t* active, Bins* b) {
 
 // One local-move evaluation of every binned vertex (proposals in prop[]).
 template <typename W, typename ST>
-int launch_lm_st(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop) {
+int launch_lm_st(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEvent_t* bin_ev) {
   cudaStream_t s = c->stream;
   const int T = 256;
   const size_t mid_smem = (size_t)8 * kMidCap * 12;
@@ -798,13 +811,16 @@ int launch_lm_st(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop) {
   shift(g2, cnt[0] + cnt[1]);
   shift(g3, cnt[0] + cnt[1] + cnt[2]);
   if (cnt[0]) count_launch(), lm_warp<W, ST><<<grid_for(cnt[0] * 32, T, 16), T, 0, s>>>(lv, lst, cnt[0], prop);
+  if (bin_ev) DCD_TRY_CUDA(cudaEventRecord(bin_ev[0], s));
   if (cnt[1])
     count_launch(), lm_warp_tbl<W, ST><<<grid_for(cnt[1] * 32, T, 8), T, mid_smem, s>>>(g1, lst + cnt[0], cnt[1],
                                                                                          prop + cnt[0]);
+  if (bin_ev) DCD_TRY_CUDA(cudaEventRecord(bin_ev[1], s));
   if (cnt[2])
     count_launch(), lm_block<W, ST, kLargeThreads>
         <<<(unsigned)(cnt[2] < 8 * c->sms ? cnt[2] : 8 * c->sms), kLargeThreads, b.large_smem, s>>>(
             g2, lst + cnt[0] + cnt[1], cnt[2], prop + cnt[0] + cnt[1], nullptr, nullptr, 0);
+  if (bin_ev) DCD_TRY_CUDA(cudaEventRecord(bin_ev[2], s));
   if (cnt[3])
     count_launch(), lm_block<W, ST, kHubThreads><<<(unsigned)b.hub_ctas, kHubThreads, 0, s>>>(
         g3, lst + cnt[0] + cnt[1] + cnt[2], cnt[3], prop + cnt[0] + cnt[1] + cnt[2], b.hkeys.get(), b.hvals.get(),
@@ -814,9 +830,9 @@ int launch_lm_st(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop) {
 }
 
 template <typename W>
-int launch_lm(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop) {
-  if (lv.m2 >= ((int64_t)1 << 31)) return launch_lm_st<W, i128>(c, lv, b, prop);
-  return launch_lm_st<W, long long>(c, lv, b, prop);
+int launch_lm(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEvent_t* bin_ev = nullptr) {
+  if (lv.m2 >= ((int64_t)1 << 31)) return launch_lm_st<W, i128>(c, lv, b, prop, bin_ev);
+  return launch_lm_st<W, long long>(c, lv, b, prop, bin_ev);
 }
 
 template <typename W>
@@ -849,7 +865,7 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
   for (;;) {
     const int32_t iter = (int32_t)out->passes;
     DCD_TRY_CUDA(cudaEventRecord(c->ev[2], s));
-    DCD_TRY(launch_lm<W>(c, lv, bins, prop.get()));
+    DCD_TRY(launch_lm<W>(c, lv, bins, prop.get(), &c->ev[12]));
     DCD_TRY_CUDA(cudaEventRecord(c->ev[3], s));
     DCD_TRY_CUDA(cudaMemsetAsync(moved_cnt.get(), 0, sizeof(int32_t), s));
     DCD_TRY_CUDA(cudaMemsetAsync(moved_big_cnt.get(), 0, sizeof(int32_t), s));
@@ -878,6 +894,18 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
     cudaEventElapsedTime(&t2, c->ev[3], c->ev[4]);
     out->ms_lm += t1;
     out->ms_apply += t2;
+    {
+      float tb[4] = {0.f, 0.f, 0.f, 0.f};
+      cudaEventElapsedTime(&tb[0], c->ev[2], c->ev[12]);
+      cudaEventElapsedTime(&tb[1], c->ev[12], c->ev[13]);
+      cudaEventElapsedTime(&tb[2], c->ev[13], c->ev[14]);
+      cudaEventElapsedTime(&tb[3], c->ev[14], c->ev[3]);
+      for (int x = 0; x < 4; x++) {
+        out->ms_bin[x] += tb[x];
+        out->edges_bin[x] += bins.deg[x];
+        out->verts_bin[x] += bins.cnt[x];
+      }
+    }
     out->passes++;
     out->edges += bins.act_deg;
     out->verts += bins.n_active;
@@ -1039,6 +1067,8 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
   DCD_TRY_CUDA(cudaStreamSynchronize(s));
 
   int64_t level = 0, passes_total = 0, passes0 = 0, moves_total = 0, edges_total = 0, verts_total = 0;
+  float ms_bin[4] = {0.f, 0.f, 0.f, 0.f};
+  int64_t edges_bin[4] = {0, 0, 0, 0}, verts_bin[4] = {0, 0, 0, 0};
   float ms_lm = 0.f, ms_apply = 0.f, ms_coarsen = 0.f;
   i128 N_start = h128(c->hsc->n_start_lo, c->hsc->n_start_hi);
 
@@ -1068,6 +1098,11 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
     moves_total += lr.moves;
     edges_total += lr.edges;
     verts_total += lr.verts;
+    for (int x = 0; x < 4; x++) {
+      ms_bin[x] += lr.ms_bin[x];
+      edges_bin[x] += lr.edges_bin[x];
+      verts_bin[x] += lr.verts_bin[x];
+    }
     ms_lm += lr.ms_lm;
     ms_apply += lr.ms_apply;
     const i128 N_end = h128(c->hsc->n_cur_lo, c->hsc->n_cur_hi);
@@ -1149,6 +1184,11 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
     st->moves_total = moves_total;
     st->edges_scanned = edges_total;
     st->verts_scanned = verts_total;
+    for (int x = 0; x < 4; x++) {
+      st->ms_bin[x] = ms_bin[x];
+      st->edges_bin[x] = edges_bin[x];
+      st->verts_bin[x] = verts_bin[x];
+    }
     st->communities = c->hsc->ncomm;
     st->n_lo = (int64_t)(unsigned long long)N;
     st->n_hi = (int64_t)(unsigned long long)((unsigned __int128)N >> 64);

@@ -43,6 +43,7 @@ struct DevScalars {
   uint32_t err;      // kErr* bits
   uint32_t pad1;
   int64_t bin2_maxdeg;  // largest degree in the 129..4096 bin
+  int64_t bin_deg[4];   // sum of the degrees in each bin
 };
 
 // Degree bins of the local-move kernels.

@@ -61,7 +61,10 @@ class StepStats(ctypes.Structure):
                 [("ins_records", ctypes.c_int64), ("del_records", ctypes.c_int64),
                  ("launches", ctypes.c_int64), ("r_screen", ctypes.c_int64), ("pool", ctypes.c_int64),
                  ("fallback", ctypes.c_int64), ("q_screen", ctypes.c_double)] +
-                [(k, ctypes.c_float) for k in _STAT_F32] + [("reserved_f", ctypes.c_float * 9)])
+                [(k, ctypes.c_float) for k in _STAT_F32] + [("ms_bin", ctypes.c_float * 4),
+                                                            ("reserved_f", ctypes.c_float * 5),
+                                                            ("edges_bin", ctypes.c_int64 * 4),
+                                                            ("verts_bin", ctypes.c_int64 * 4)])
 
     @property
     def N(self) -> int:
@@ -69,6 +72,8 @@ class StepStats(ctypes.Structure):
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved_f"}
+        for k in ("ms_bin", "edges_bin", "verts_bin"):
+            d[k] = list(d[k])
         d["N"] = self.N
         return d
 
