@@ -5,6 +5,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "prims.cuh"
 #include "state.cuh"
@@ -211,6 +212,15 @@ int dcd_create(int64_t n, const dcd_config* cfg, void* cuda_stream, dcd_ctx** ou
       if (cudaEventCreate(&e) != cudaSuccess) { rc = DCD_ECUDA; break; }
     if (rc) break;
     if ((rc = c->dsc.alloc(&c->mem, 1))) break;
+    if ((rc = c->gs.alloc(&c->mem, 1))) break;
+    if ((rc = c->goff_d.alloc(&c->mem, 2))) break;
+    if (cudaMallocHost(&c->hgs, sizeof(GraphState)) != cudaSuccess) { rc = DCD_ENOMEM; break; }
+    c->goff = new (std::nothrow) int64_t[2];
+    if (!c->goff) { rc = DCD_ENOMEM; break; }
+    c->goff[0] = 0;
+    c->goff[1] = n;
+    if (cudaMemcpyAsync(c->goff_d.get(), c->goff, 2 * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream) !=
+        cudaSuccess) { rc = DCD_ECUDA; break; }
     if ((rc = c->labels.alloc(&c->mem, n))) break;
     if ((rc = c->iota.alloc(&c->mem, n))) break;
     if ((rc = c->rset.alloc(&c->mem, n))) break;
@@ -244,6 +254,7 @@ int dcd_destroy(dcd_ctx* c) {
     c->labels.reset(); c->labels_nx.reset(); c->rset.reset(); c->rgiven.reset();
     c->ins.reset(); c->del.reset(); c->dsc.reset(); c->iota.reset(); c->rset_nx.reset();
     c->feat_X.reset(); c->feat_y.reset(); c->feat_v.reset(); c->level0.reset();
+    c->gs.reset(); c->goff_d.reset(); c->gid.reset();
     if (c->mem.arena) cudaFreeAsync(c->mem.arena, c->stream);
     c->mem.arena = nullptr;
     cudaStreamSynchronize(c->stream);
@@ -251,6 +262,8 @@ int dcd_destroy(dcd_ctx* c) {
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   if (c->hsc) cudaFreeHost(c->hsc);
+  if (c->hgs) cudaFreeHost(c->hgs);
+  delete[] c->goff;
   if (c->hscratch) cudaFreeHost(c->hscratch);
   if (c->mem.pool) cudaMemPoolDestroy(c->mem.pool);
   delete c;
@@ -322,8 +335,13 @@ static int update_impl(dcd_ctx* c, dcd_step_stats* st) {
   trace("update: merge done");
   if (c->hsc->err & kErrBadRecord) return DCD_EINVAL;
   if (c->hsc->err & kErrOverflow) return DCD_EOVERFLOW;
-  const int64_t m2 = c->hsc->m2;
-  if (m2 < 0 || m2 >= ((int64_t)1 << 62)) return DCD_EOVERFLOW;
+  DCD_TRY_CUDA(cudaMemcpyAsync(c->hgs, c->gs.get(), c->G * sizeof(GraphState), cudaMemcpyDeviceToHost, s));
+  DCD_TRY_CUDA(cudaStreamSynchronize(s));
+  for (int x = 0; x < c->G; x++)
+    if (c->hgs[x].m2 < 0 || c->hgs[x].m2 >= ((int64_t)1 << 62)) return DCD_EOVERFLOW;
+  // per-graph state after the merge (2m, sum e_{i->C(i)} under C_{t-1}): a
+  // second run from the same state starts from this copy
+  std::vector<GraphState> gs0(c->hgs, c->hgs + c->G);
   const int64_t nnz_new = c->hscratch[8];
   Csr<int32_t> g{n, nnz_new, c->rp[nxt].get(), c->col[nxt].get(), c->w[nxt].get()};
 
@@ -379,7 +397,6 @@ static int update_impl(dcd_ctx* c, dcd_step_stats* st) {
   trace("update: R_t done");
 
   // ---- Algorithm 1 with R_t at level 0 ----
-  const int64_t in0 = c->hsc->in_cur;  // sum e_{i->C(i)} under C_{t-1}, for a second run
   DCD_TRY(c->labels_nx.ensure(&c->mem, n));
   if (collect) DCD_TRY(c->level0.ensure(&c->mem, n));
   DCD_TRY(run_louvain(c, g, L0.get(), active, mo.k, c->labels_nx.get(), st, collect ? c->level0.get() : nullptr));
@@ -393,7 +410,8 @@ static int update_impl(dcd_ctx* c, dcd_step_stats* st) {
     DCD_TRY(L0b.alloc(&c->mem, n));
     DCD_TRY(lab2.alloc(&c->mem, n));
     DCD_TRY_CUDA(cudaMemcpyAsync(L0b.get(), src_labels, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-    DCD_TRY_CUDA(cudaMemcpyAsync(&d->in_cur, &in0, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    memcpy(c->hgs, gs0.data(), c->G * sizeof(GraphState));
+    DCD_TRY_CUDA(cudaMemcpyAsync(c->gs.get(), c->hgs, c->G * sizeof(GraphState), cudaMemcpyHostToDevice, s));
     DCD_TRY(run_louvain(c, g, L0b.get(), rds.get(), mo.k, lab2.get(), &st2));
     st->q_screen = st2.q;
     if (st->q < st2.q - 1e-3) {

@@ -114,7 +114,7 @@ int screen_features(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* L0, const 
   if (m > 0) {
     count_launch(), assemble<<<grid_for(m, T), T, 0, s>>>(
         m, out->st.list.get(), g.rp, k, L0, a, size, mo.pair_ptr.get(), mo.pflag.get(), mo.pw.get(),
-        out->st.eC.get(), out->st.eB.get(), out->st.dB.get(), out->st.sB.get(), rds, c->hsc->m2, c->feat_X.get());
+        out->st.eC.get(), out->st.eB.get(), out->st.dB.get(), out->st.sB.get(), rds, c->hgs[0].m2, c->feat_X.get());
     DCD_LAUNCH_CHECK();
     DCD_TRY_CUDA(cudaMemcpyAsync(c->feat_v.get(), out->st.list.get(), m * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   }

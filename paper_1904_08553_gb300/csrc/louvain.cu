@@ -35,7 +35,10 @@ struct LV {
   const int32_t* L;
   const int64_t* a;
   const int32_t* size;
-  int64_t m2;
+  int64_t m2;                   // 2m when the context holds one graph
+  const int32_t* gid = nullptr;  // graph of each vertex (several graphs)
+  const GraphState* gs = nullptr;
+  __device__ __forceinline__ int64_t m2_of(int64_t v) const { return gid ? gs[gid[v]].m2 : m2; }
   // optional per-list-position statistics for the learned screen's features:
   // e_{v->C\v}, e_{v->D*}, D* (-1: none) and S(v -> D*) of the best other
   // community D* (the greedy choice before the S > 0 test and the guard)
@@ -90,7 +93,7 @@ __global__ void __launch_bounds__(256) lm_warp(LV<W> g, const int32_t* __restric
     ST S = gain_lowest<ST>();
     int32_t D = INT_MAX;
     if (valid && leader && lab != C) {
-      S = gain<ST>(g.m2, g.k[v], e, eC, g.a[lab], g.a[C]);
+      S = gain<ST>(g.m2_of(v), g.k[v], e, eC, g.a[lab], g.a[C]);
       D = lab;
     }
     warp_argmax(S, D);
@@ -147,13 +150,13 @@ __global__ void __launch_bounds__(256) lm_warp_tbl(LV<W> g, const int32_t* __res
     __syncwarp();
     long long eC = lane == 0 ? tbl_get(keys, vals, mask, C) : 0;
     eC = __shfl_sync(0xffffffffu, eC, 0);
-    const int64_t kv = g.k[v], aC = g.a[C];
+    const int64_t kv = g.k[v], aC = g.a[C], m2v = g.m2_of(v);
     ST S = gain_lowest<ST>();
     int32_t D = INT_MAX;
     for (uint32_t s = lane; s < cap; s += 32) {
       const int32_t key = keys[s];
       if (key >= 0 && key != C) {
-        const ST x = gain<ST>(g.m2, kv, (int64_t)vals[s], eC, g.a[key], aC);
+        const ST x = gain<ST>(m2v, kv, (int64_t)vals[s], eC, g.a[key], aC);
         if (better(x, key, S, D)) {
           S = x;
           D = key;
@@ -218,13 +221,13 @@ __global__ void __launch_bounds__(THREADS) lm_block(LV<W> g, const int32_t* __re
     __syncthreads();
     if (tid == 0) s_eC = tbl_get(keys, vals, mask, C);
     __syncthreads();
-    const int64_t eC = s_eC, kv = g.k[v], aC = g.a[C];
+    const int64_t eC = s_eC, kv = g.k[v], aC = g.a[C], m2v = g.m2_of(v);
     ST S = gain_lowest<ST>();
     int32_t D = INT_MAX;
     for (uint32_t s = tid; s < cap; s += THREADS) {
       const int32_t key = keys[s];
       if (key >= 0 && key != C) {
-        ST x = gain<ST>(g.m2, kv, (int64_t)vals[s], eC, g.a[key], aC);
+        ST x = gain<ST>(m2v, kv, (int64_t)vals[s], eC, g.a[key], aC);
         if (better(x, key, S, D)) {
           S = x;
           D = key;
@@ -257,27 +260,31 @@ __global__ void __launch_bounds__(THREADS) lm_block(LV<W> g, const int32_t* __re
 
 // ---------------------------------------------------------------- apply + N
 
-// Moves of one pass.  Community sums change by warp-aggregated atomics (one
-// per distinct community of the warp); movers of long rows (list positions
-// from big_from on) go to a separate list for block-per-row processing.
+// Moves of one pass (proposals of graphs whose pass loop has stopped are
+// dropped).  Community sums change by warp-aggregated atomics (one per distinct
+// community of the warp); movers of long rows (list positions from big_from
+// on) go to a separate list for block-per-row processing; per-graph mover
+// counts feed the stop rule.
 __global__ void lm_apply(const int32_t* __restrict__ list, int64_t cnt, int64_t big_from,
                          const int32_t* __restrict__ prop, int32_t* __restrict__ L, const int64_t* __restrict__ k,
                          unsigned long long* __restrict__ a, int32_t* __restrict__ size, int32_t* __restrict__ Lprev,
                          int32_t* __restrict__ mvit, int32_t iter, int32_t* __restrict__ moved,
                          int32_t* __restrict__ moved_cnt, int32_t* __restrict__ moved_big,
-                         int32_t* __restrict__ moved_big_cnt) {
+                         int32_t* __restrict__ moved_big_cnt, const int32_t* __restrict__ gid,
+                         GraphState* __restrict__ gs) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t base0 = (blockIdx.x * (int64_t)blockDim.x) & ~31ll;
   for (int64_t base = base0 + (threadIdx.x & ~31); base < cnt; base += stride) {
     const int64_t i = base + lane_id();
     bool mv = false;
-    int32_t v = 0, c = -1, p = -1;
+    int32_t v = 0, c = -1, p = -1, gv = -1;
     int64_t kv = 0;
     if (i < cnt) {
       v = list[i];
       p = prop[i];
       c = L[v];
-      if (p != c) {
+      gv = graph_of(gid, v);
+      if (p != c && gs[gv].running) {
         mv = true;
         Lprev[v] = c;
         L[v] = p;
@@ -303,6 +310,10 @@ __global__ void lm_apply(const int32_t* __restrict__ list, int64_t cnt, int64_t 
         atomicAdd(&size[p], __popc(peers));
       }
     }
+    {  // movers per graph
+      const unsigned peers = __match_any_sync(0xffffffffu, mv ? gv : -1);
+      if (mv && (int)(__ffs(peers) - 1) == (int)lane_id()) atomicAdd(&gs[gv].moves, __popc(peers));
+    }
     const bool big = mv && i >= big_from;
     const bool small = mv && !big;
     unsigned bal = __ballot_sync(0xffffffffu, small);
@@ -321,30 +332,34 @@ __global__ void lm_apply(const int32_t* __restrict__ list, int64_t cnt, int64_t 
 // Change of sum_i e_{i->C(i)} from the rows of the moved vertices: an entry
 // (x, y) with y unmoved also stands for its mirror (y, x), hence weight 2.
 template <typename W>
+__device__ __forceinline__ int64_t moved_row_delta(const LV<W>& g, int32_t x, const int32_t* __restrict__ Lprev,
+                                                   const int32_t* __restrict__ mvit, int32_t iter, int tid, int nt) {
+  const int32_t ox = Lprev[x], nx = g.L[x];
+  const int64_t e1 = g.rp[x + 1];
+  int64_t acc = 0;
+  for (int64_t e = g.rp[x] + tid; e < e1; e += nt) {
+    const int32_t y = g.col[e];
+    const int64_t wt = (int64_t)g.w[e];
+    const bool ym = mvit[y] == iter;
+    const int32_t ny = g.L[y];
+    const int32_t oy = ym ? Lprev[y] : ny;
+    acc += ((int)(nx == ny) - (int)(ox == oy)) * wt * (ym ? 1 : 2);
+  }
+  return acc;
+}
+
+template <typename W>
 __global__ void __launch_bounds__(256) lm_delta_in(LV<W> g, const int32_t* __restrict__ moved,
                                                    const int32_t* __restrict__ moved_cnt,
                                                    const int32_t* __restrict__ Lprev, const int32_t* __restrict__ mvit,
-                                                   int32_t iter, unsigned long long* __restrict__ in_delta) {
+                                                   int32_t iter, GraphState* __restrict__ gs) {
   const int64_t cnt = *moved_cnt;
-  const int lane = lane_id();
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  int64_t acc = 0;
   for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < cnt; i += nw) {
     const int32_t x = moved[i];
-    const int32_t ox = Lprev[x], nx = g.L[x];
-    const int64_t b = g.rp[x], e1 = g.rp[x + 1];
-    for (int64_t e = b + lane; e < e1; e += 32) {
-      const int32_t y = g.col[e];
-      const int64_t wt = (int64_t)g.w[e];
-      const bool ym = mvit[y] == iter;
-      const int32_t ny = g.L[y];
-      const int32_t oy = ym ? Lprev[y] : ny;
-      const int dlt = (int)(nx == ny) - (int)(ox == oy);
-      acc += dlt * wt * (ym ? 1 : 2);
-    }
+    const int64_t acc = (int64_t)warp_sum((long long)moved_row_delta(g, x, Lprev, mvit, iter, lane_id(), 32));
+    if (lane_id() == 0 && acc != 0) atomicAdd((unsigned long long*)&gs[graph_of(g.gid, x)].in_delta, (unsigned long long)acc);
   }
-  acc = (int64_t)warp_sum((long long)acc);
-  if (lane == 0 && acc != 0) atomicAdd(in_delta, (unsigned long long)acc);
 }
 
 // As lm_delta_in with one CTA per moved vertex (rows above 256 entries).
@@ -353,31 +368,39 @@ __global__ void __launch_bounds__(256) lm_delta_in_block(LV<W> g, const int32_t*
                                                          const int32_t* __restrict__ moved_cnt,
                                                          const int32_t* __restrict__ Lprev,
                                                          const int32_t* __restrict__ mvit, int32_t iter,
-                                                         unsigned long long* __restrict__ in_delta) {
+                                                         GraphState* __restrict__ gs) {
   const int64_t cnt = *moved_cnt;
-  int64_t acc = 0;
   for (int64_t i = blockIdx.x; i < cnt; i += gridDim.x) {
     const int32_t x = moved[i];
-    const int32_t ox = Lprev[x], nx = g.L[x];
-    const int64_t e1 = g.rp[x + 1];
-    for (int64_t e = g.rp[x] + threadIdx.x; e < e1; e += blockDim.x) {
-      const int32_t y = g.col[e];
-      const int64_t wt = (int64_t)g.w[e];
-      const bool ym = mvit[y] == iter;
-      const int32_t ny = g.L[y];
-      const int32_t oy = ym ? Lprev[y] : ny;
-      acc += ((int)(nx == ny) - (int)(ox == oy)) * wt * (ym ? 1 : 2);
-    }
+    const int64_t acc = (int64_t)warp_sum((long long)moved_row_delta(g, x, Lprev, mvit, iter, threadIdx.x, blockDim.x));
+    if (lane_id() == 0 && acc != 0) atomicAdd((unsigned long long*)&gs[graph_of(g.gid, x)].in_delta, (unsigned long long)acc);
   }
-  acc = (int64_t)warp_sum((long long)acc);
-  if (lane_id() == 0 && acc != 0) atomicAdd(in_delta, (unsigned long long)acc);
 }
 
-// sum over labels of a^2 as an unsigned 128-bit value, added into acc[0..1]
-// (low, high word): every CTA adds its part with a carry into the high word,
-// so the final pair is exact whatever the order.
+__device__ __forceinline__ void add128(unsigned long long* lo, unsigned long long* hi, unsigned __int128 v) {
+  const unsigned long long vlo = (unsigned long long)v, vhi = (unsigned long long)(v >> 64);
+  if (!(vlo | vhi)) return;
+  const unsigned long long old = atomicAdd(lo, vlo);
+  const unsigned long long carry = (old + vlo < old) ? 1ull : 0ull;
+  if (vhi + carry) atomicAdd(hi, vhi + carry);
+}
+
+// sum over labels of a^2 per graph, unsigned 128-bit: every contribution is
+// added with a carry into the high word, so the total is exact in any order.
+// One graph: a CTA reduction then one addition per CTA; several graphs: one
+// addition per community in use.
 __global__ void __launch_bounds__(256) sumsq_acc(const int64_t* __restrict__ a, int64_t n,
-                                                 unsigned long long* __restrict__ acc) {
+                                                 const int32_t* __restrict__ gid, GraphState* __restrict__ gs) {
+  if (gid) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+      const unsigned long long x = (unsigned long long)a[c];
+      if (x) {
+        GraphState& G = gs[gid[c]];
+        add128(&G.sq_lo, &G.sq_hi, (unsigned __int128)x * x);
+      }
+    }
+    return;
+  }
   __shared__ unsigned long long slo[8], shi[8];
   unsigned __int128 s = 0;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
@@ -400,12 +423,7 @@ __global__ void __launch_bounds__(256) sumsq_acc(const int64_t* __restrict__ a, 
   if (threadIdx.x == 0) {
     unsigned __int128 t = 0;
     for (int w = 0; w < 8; w++) t += ((unsigned __int128)shi[w] << 64) | slo[w];
-    const unsigned long long tlo = (unsigned long long)t, thi = (unsigned long long)(t >> 64);
-    if (tlo | thi) {
-      const unsigned long long old = atomicAdd(&acc[0], tlo);
-      const unsigned long long carry = (old + tlo < old) ? 1ull : 0ull;
-      if (thi + carry) atomicAdd(&acc[1], thi + carry);
-    }
+    add128(&gs[0].sq_lo, &gs[0].sq_hi, t);
   }
 }
 
@@ -422,40 +440,53 @@ __device__ __forceinline__ void st128(int64_t* lo, i128 x) {
   lo[1] = (int64_t)(unsigned long long)((unsigned __int128)x >> 64);
 }
 
-// The pass decision (one thread); sum a^2 is already in d->sq.
-// mode 0: level start (N_start = N_cur = m2 in - sq); mode 1: after a pass.
-__global__ void lm_decide(DevScalars* d, int mode, const int32_t* __restrict__ moved_cnt,
-                          const int32_t* __restrict__ moved_big_cnt, int32_t passes_done, int32_t max_iters,
-                          int64_t tau_inv) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const unsigned __int128 sq =
-      ((unsigned __int128)(unsigned long long)d->sq_hi << 64) | (unsigned long long)d->sq_lo;
-  if (mode == 0) {
-    const i128 N = (i128)d->m2 * (i128)d->in_cur - (i128)sq;
-    st128(&d->n_cur_lo, N);
-    st128(&d->n_start_lo, N);
-    d->stop = 0;
-    d->moves = 0;
-    return;
+// Per-pass accumulators back to zero (one thread per graph).
+__global__ void gs_reset_pass(GraphState* __restrict__ gs, int G) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+    gs[g].in_delta = 0;
+    gs[g].sq_lo = gs[g].sq_hi = 0;
+    gs[g].moves = 0;
   }
-  const int32_t moves = *moved_cnt + *moved_big_cnt;
-  d->moves = moves;
-  if (moves == 0) {
-    d->stop = 1;
-    return;
+}
+
+// The pass decision per graph (one thread per graph).  mode 0: level start
+// (N_start = N_cur = m2 in - sq; graphs whose levels are over do not run);
+// mode 1: after a pass.  any_running <- some graph goes on.
+__global__ void lm_decide(GraphState* __restrict__ gs, int G, int mode, int32_t max_iters, int64_t tau_inv,
+                          int32_t* __restrict__ any_running) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+    GraphState& X = gs[g];
+    const unsigned __int128 sq = ((unsigned __int128)X.sq_hi << 64) | X.sq_lo;
+    if (mode == 0) {
+      const i128 N = (i128)X.m2 * (i128)X.in_cur - (i128)sq;
+      st128(&X.n_cur_lo, N);
+      st128(&X.n_start_lo, N);
+      X.running = X.done ? 0 : 1;
+      X.passes = 0;
+      X.moves = 0;
+      if (X.running) atomicOr(any_running, 1);
+      continue;
+    }
+    if (!X.running) continue;
+    X.passes++;
+    if (X.moves == 0) {
+      X.running = 0;
+      continue;
+    }
+    const int64_t in_new = X.in_cur + X.in_delta;
+    const i128 N_new = (i128)X.m2 * (i128)in_new - (i128)sq;
+    const i128 N_old = ld128(&X.n_cur_lo);
+    X.in_cur = in_new;
+    st128(&X.n_cur_lo, N_new);
+    if (below_tau(N_new - N_old, N_old, tau_inv) || X.passes >= max_iters) X.running = 0;
+    if (X.running) atomicOr(any_running, 1);
   }
-  const int64_t in_new = d->in_cur + d->in_delta;
-  const i128 N_new = (i128)d->m2 * (i128)in_new - (i128)sq;
-  const i128 N_old = ld128(&d->n_cur_lo);
-  d->in_cur = in_new;
-  st128(&d->n_cur_lo, N_new);
-  d->stop = (below_tau(N_new - N_old, N_old, tau_inv) || passes_done >= max_iters) ? 1 : 0;
 }
 
 // ---------------------------------------------------------------- binning
 
 __global__ void bin_count(const int64_t* __restrict__ rp, int64_t n, const uint8_t* __restrict__ active,
-                          DevScalars* d) {
+                          DevScalars* d, const int32_t* __restrict__ gid, const GraphState* __restrict__ gs) {
   __shared__ unsigned long long sc[4], sdb[4];
   __shared__ unsigned long long sdeg, sact;
   __shared__ long long smax, smax2;
@@ -472,6 +503,7 @@ __global__ void bin_count(const int64_t* __restrict__ rp, int64_t n, const uint8
   __syncthreads();
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     if (active && !active[v]) continue;
+    if (gid && !gs[gid[v]].running) continue;
     const int64_t deg = rp[v + 1] - rp[v];
     atomicAdd(&sdeg, (unsigned long long)deg);
     atomicAdd(&sact, 1ull);
@@ -497,7 +529,8 @@ __global__ void bin_count(const int64_t* __restrict__ rp, int64_t n, const uint8
 
 __global__ void bin_scatter(const int64_t* __restrict__ rp, int64_t n, const uint8_t* __restrict__ active,
                             const DevScalars* __restrict__ d, int32_t* __restrict__ cursor,
-                            int32_t* __restrict__ list) {
+                            int32_t* __restrict__ list, const int32_t* __restrict__ gid,
+                            const GraphState* __restrict__ gs) {
   __shared__ int32_t off[4];
   if (threadIdx.x == 0) {
     int64_t o = 0;
@@ -512,7 +545,7 @@ __global__ void bin_scatter(const int64_t* __restrict__ rp, int64_t n, const uin
   for (int64_t base = base0; base < n; base += stride) {
     const int64_t v = base + lane_id();
     int bin = -1;
-    if (v < n && (!active || active[v])) {
+    if (v < n && (!active || active[v]) && (!gid || gs[gid[v]].running)) {
       const int64_t deg = rp[v + 1] - rp[v];
       if (deg > 0) bin = deg <= kBinWarpMax ? 0 : deg <= kBinMidMax ? 1 : deg <= kBinLargeMax ? 2 : 3;
     }
@@ -671,6 +704,29 @@ __global__ void reduce_runs(const uint64_t* __restrict__ keys, const uint64_t* _
   if (cur >= 0) atomicAdd(&cw[cur], acc);
 }
 
+__global__ void gs_reset_nc(GraphState* __restrict__ gs, int G) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+    gs[g].nc = 0;
+    gs[g].ncomm = 0;
+  }
+}
+
+// Labels in use per graph (after the used-label scan: c is used when
+// cid[c + 1] != cid[c]) and the graph of every coarse vertex.
+__global__ void count_used(int64_t n, const int32_t* __restrict__ cid, const int32_t* __restrict__ gid,
+                           GraphState* __restrict__ gs, int32_t* __restrict__ gid_next) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (blockIdx.x * (int64_t)blockDim.x) + (threadIdx.x & ~31); base < n; base += stride) {
+    const int64_t c = base + lane_id();
+    const bool used = c < n && cid[c + 1] != cid[c];
+    const int g = used ? graph_of(gid, c) : -1;
+    if (used && gid_next) gid_next[cid[c]] = g;
+    const unsigned peers = __match_any_sync(0xffffffffu, g);
+    if (used && (int)(__ffs(peers) - 1) == (int)lane_id())
+      atomicAdd((unsigned long long*)&gs[g].nc, (unsigned long long)__popc(peers));
+  }
+}
+
 // k of a coarse vertex = a of its community; compose the original vertices.
 __global__ void coarse_k(int64_t n, const int32_t* __restrict__ cid, const int64_t* __restrict__ a,
                          int64_t* __restrict__ kc) {
@@ -698,17 +754,26 @@ __global__ void final_min(int64_t n0, const int32_t* __restrict__ comp, const in
   }
 }
 
+// Canonical labels (smallest member id, a vertex id of the context) and the
+// number of communities per graph.
 __global__ void final_labels(int64_t n0, const int32_t* __restrict__ comp, const int32_t* __restrict__ L,
                              const int32_t* __restrict__ minid, int32_t* __restrict__ out,
-                             unsigned long long* __restrict__ ncomm) {
-  unsigned long long c = 0;
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n0; v += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t x = minid[L[comp[v]]];
-    out[v] = x;
-    c += (x == (int32_t)v);
+                             const int32_t* __restrict__ gid, GraphState* __restrict__ gs) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (blockIdx.x * (int64_t)blockDim.x) + (threadIdx.x & ~31); base < n0; base += stride) {
+    const int64_t v = base + lane_id();
+    int g = -1;
+    bool head = false;
+    if (v < n0) {
+      const int32_t x = minid[L[comp[v]]];
+      head = x == (int32_t)v;
+      g = graph_of(gid, v);
+      out[v] = x;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, head ? g : -1);
+    if (head && (int)(__ffs(peers) - 1) == (int)lane_id())
+      atomicAdd((unsigned long long*)&gs[g].ncomm, (unsigned long long)__popc(peers));
   }
-  c = warp_sum(c);
-  if (lane_id() == 0 && c) atomicAdd(ncomm, c);
 }
 
 // ---------------------------------------------------------------- host side
@@ -743,14 +808,14 @@ struct Bins {
 };
 
 template <typename W>
-int make_bins(dcd_ctx* c, const Csr<W>& g, const uint8_t* active, Bins* b) {
+int make_bins(dcd_ctx* c, const Csr<W>& g, const uint8_t* active, Bins* b, const int32_t* gid = nullptr) {
   cudaStream_t s = c->stream;
   DevScalars* d = c->dsc.get();
   const int64_t nv = g.n;
   const int T = 256;
   DCD_TRY_CUDA(cudaMemsetAsync(&d->bin_cnt[0], 0, sizeof(int64_t) * 7, s));  // bins, maxdeg, act_deg, ncomm
   DCD_TRY_CUDA(cudaMemsetAsync(&d->bin2_maxdeg, 0, 5 * sizeof(int64_t), s));  // bin2_maxdeg, bin_deg[4]
-  ::dcd::count_launch(), bin_count<<<grid_for(nv, T), T, 0, s>>>(g.rp, nv, active, d);
+  ::dcd::count_launch(), bin_count<<<grid_for(nv, T), T, 0, s>>>(g.rp, nv, active, d, gid, c->gs.get());
   DCD_LAUNCH_CHECK();
   DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
   DCD_TRY_CUDA(cudaStreamSynchronize(s));
@@ -769,7 +834,7 @@ int make_bins(dcd_ctx* c, const Csr<W>& g, const uint8_t* active, Bins* b) {
   DCD_TRY_CUDA(cudaMemsetAsync(cursor.get(), 0, 4 * sizeof(int32_t), s));
   if (b->total > 0) {
     ::dcd::count_launch(), bin_scatter<<<grid_for(nv, T), T, 0, s>>>(g.rp, nv, active, d, cursor.get(),
-                                                                       b->list.get());
+                                                                       b->list.get(), gid, c->gs.get());
     DCD_LAUNCH_CHECK();
   }
   // hub tables in global memory: one region per CTA, sized for the largest hub
@@ -835,16 +900,29 @@ int launch_lm(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEvent_t* 
   return launch_lm_st<W, long long>(c, lv, b, prop, bin_ev);
 }
 
+// Per-graph counters of one update (host).
+struct GraphTally {
+  std::vector<int64_t> passes, passes0, moves, levels;
+  explicit GraphTally(int G) : passes(G, 0), passes0(G, 0), moves(G, 0), levels(G, 0) {}
+};
+
 template <typename W>
 int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<int64_t>& a, Buf<int32_t>& size,
-              const uint8_t* active, LevelRun* out) {
+              const uint8_t* active, const int32_t* gid, int level, LevelRun* out, GraphTally* tally) {
   cudaStream_t s = c->stream;
   DevScalars* d = c->dsc.get();
+  GraphState* gs = c->gs.get();
+  const int G = c->G;
   const int64_t nv = g.n;
   const int T = 256;
 
+  // level start: N_start = N_cur per graph, running = not done
+  DCD_TRY_CUDA(cudaMemsetAsync(&d->any_running, 0, sizeof(int32_t), s));
+  ::dcd::count_launch(), lm_decide<<<cdiv(G, 128), 128, 0, s>>>(gs, G, 0, c->cfg.max_iters, c->cfg.tau_inv,
+                                                                 &d->any_running);
+  DCD_LAUNCH_CHECK();
   Bins bins;
-  DCD_TRY(make_bins<W>(c, g, active, &bins));
+  DCD_TRY(make_bins<W>(c, g, active, &bins, gid));
   trace("level: binned");
   const int64_t* cnt = bins.cnt;
   const int64_t total = bins.total;
@@ -859,35 +937,46 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
   ::dcd::count_launch(), fill_i32<<<grid_for(nv, T), T, 0, s>>>(mvit.get(), nv, -1);
   DCD_LAUNCH_CHECK();
   const int sq_ctas = grid_for(nv, T, 4);
-  LV<W> lv{g.rp, g.col, g.w, kbuf.get(), L, a.get(), size.get(), c->hsc->m2};
+  LV<W> lv{g.rp, g.col, g.w, kbuf.get(), L, a.get(), size.get(), G == 1 ? c->hgs[0].m2 : 0};
+  lv.gid = gid;
+  lv.gs = gid ? gs : nullptr;
+  int64_t m2max = 0;
+  for (int x = 0; x < G; x++) m2max = c->hgs[x].m2 > m2max ? c->hgs[x].m2 : m2max;
+  LV<W> lvl = lv;
+  lvl.m2 = G == 1 ? lv.m2 : m2max;  // gain width chosen by the largest graph
   const int32_t* lst = bins.list.get();
-
+  bool any = total > 0;
+  // a level with nothing to evaluate still runs one (empty) pass, as the
+  // sequential definition does
   for (;;) {
     const int32_t iter = (int32_t)out->passes;
-    DCD_TRY_CUDA(cudaEventRecord(c->ev[2], s));
-    DCD_TRY(launch_lm<W>(c, lv, bins, prop.get(), &c->ev[12]));
-    DCD_TRY_CUDA(cudaEventRecord(c->ev[3], s));
+    ::dcd::count_launch(), gs_reset_pass<<<cdiv(G, 128), 128, 0, s>>>(gs, G);
     DCD_TRY_CUDA(cudaMemsetAsync(moved_cnt.get(), 0, sizeof(int32_t), s));
     DCD_TRY_CUDA(cudaMemsetAsync(moved_big_cnt.get(), 0, sizeof(int32_t), s));
-    DCD_TRY_CUDA(cudaMemsetAsync(&d->in_delta, 0, 3 * sizeof(int64_t), s));  // in_delta, sq_lo, sq_hi
+    DCD_TRY_CUDA(cudaMemsetAsync(&d->any_running, 0, sizeof(int32_t), s));
+    DCD_TRY_CUDA(cudaEventRecord(c->ev[2], s));
+    if (any) DCD_TRY(launch_lm<W>(c, lvl, bins, prop.get(), &c->ev[12]));
+    else
+      for (int x = 12; x < 15; x++) DCD_TRY_CUDA(cudaEventRecord(c->ev[x], s));
+    DCD_TRY_CUDA(cudaEventRecord(c->ev[3], s));
     if (total) {
       ::dcd::count_launch(), lm_apply<<<grid_for(total, T), T, 0, s>>>(
           lst, total, cnt[0] + cnt[1], prop.get(), L, kbuf.get(), (unsigned long long*)a.get(), size.get(),
-          Lprev.get(), mvit.get(), iter, moved.get(), moved_cnt.get(), moved_big.get(), moved_big_cnt.get());
+          Lprev.get(), mvit.get(), iter, moved.get(), moved_cnt.get(), moved_big.get(), moved_big_cnt.get(), gid, gs);
       if (cnt[0] + cnt[1])
         ::dcd::count_launch(), lm_delta_in<W><<<grid_for((cnt[0] + cnt[1]) * 32, T, 16), T, 0, s>>>(
-            lv, moved.get(), moved_cnt.get(), Lprev.get(), mvit.get(), iter, (unsigned long long*)&d->in_delta);
+            lv, moved.get(), moved_cnt.get(), Lprev.get(), mvit.get(), iter, gs);
       if (cnt[2] + cnt[3])
         ::dcd::count_launch(), lm_delta_in_block<W><<<grid_for((cnt[2] + cnt[3]) * T, T, 4), T, 0, s>>>(
-            lv, moved_big.get(), moved_big_cnt.get(), Lprev.get(), mvit.get(), iter,
-            (unsigned long long*)&d->in_delta);
+            lv, moved_big.get(), moved_big_cnt.get(), Lprev.get(), mvit.get(), iter, gs);
     }
-    ::dcd::count_launch(), sumsq_acc<<<sq_ctas, T, 0, s>>>(a.get(), nv, (unsigned long long*)&d->sq_lo);
-    ::dcd::count_launch(), lm_decide<<<1, 32, 0, s>>>(d, 1, moved_cnt.get(), moved_big_cnt.get(), iter + 1,
-                                                       c->cfg.max_iters, c->cfg.tau_inv);
+    ::dcd::count_launch(), sumsq_acc<<<sq_ctas, T, 0, s>>>(a.get(), nv, gid, gs);
+    ::dcd::count_launch(), lm_decide<<<cdiv(G, 128), 128, 0, s>>>(gs, G, 1, c->cfg.max_iters, c->cfg.tau_inv,
+                                                                   &d->any_running);
     DCD_LAUNCH_CHECK();
     DCD_TRY_CUDA(cudaEventRecord(c->ev[4], s));
     DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+    DCD_TRY_CUDA(cudaMemcpyAsync(c->hgs, gs, G * sizeof(GraphState), cudaMemcpyDeviceToHost, s));
     DCD_TRY_CUDA(cudaStreamSynchronize(s));
     float t1 = 0.f, t2 = 0.f;
     cudaEventElapsedTime(&t1, c->ev[2], c->ev[3]);
@@ -909,8 +998,12 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
     out->passes++;
     out->edges += bins.act_deg;
     out->verts += bins.n_active;
-    out->moves += c->hsc->moves;
-    if (c->hsc->stop) break;
+    for (int x = 0; x < G; x++) tally->moves[x] += c->hgs[x].moves;
+    if (!c->hsc->any_running) break;
+  }
+  for (int x = 0; x < G; x++) {
+    tally->passes[x] += c->hgs[x].passes;
+    if (level == 0) tally->passes0[x] = c->hgs[x].passes;
   }
   trace("level: passes done");
   return DCD_OK;
@@ -918,7 +1011,8 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
 
 // Compaction of one level: returns nc; fills the coarse graph when nc < n.
 template <typename W>
-int used_labels(dcd_ctx* c, const Csr<W>& g, const int32_t* L, Buf<int32_t>& cid, int64_t* nc) {
+int used_labels(dcd_ctx* c, const Csr<W>& g, const int32_t* L, Buf<int32_t>& cid, int64_t* nc,
+                const int32_t* gid, Buf<int32_t>* gid_next) {
   cudaStream_t s = c->stream;
   const int T = 256;
   const int64_t nv = g.n;
@@ -929,9 +1023,16 @@ int used_labels(dcd_ctx* c, const Csr<W>& g, const int32_t* L, Buf<int32_t>& cid
   ::dcd::count_launch(), mark_used<<<grid_for(nv, T), T, 0, s>>>(nv, L, cid.get());
   DCD_LAUNCH_CHECK();
   DCD_TRY(exclusive_scan<int32_t>(cid.get(), cid.get(), nv + 1, nullptr, tmp.get(), s));
+  ::dcd::count_launch(), gs_reset_nc<<<cdiv(c->G, 128), 128, 0, s>>>(c->gs.get(), c->G);
   DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch, cid.get() + nv, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   DCD_TRY_CUDA(cudaStreamSynchronize(s));
   *nc = *reinterpret_cast<int32_t*>(c->hscratch);
+  if (gid_next) DCD_TRY(gid_next->alloc(&c->mem, *nc > 0 ? *nc : 1));
+  ::dcd::count_launch(), count_used<<<grid_for(nv, T), T, 0, s>>>(nv, cid.get(), gid, c->gs.get(),
+                                                                   gid_next ? gid_next->get() : nullptr);
+  DCD_LAUNCH_CHECK();
+  DCD_TRY_CUDA(cudaMemcpyAsync(c->hgs, c->gs.get(), c->G * sizeof(GraphState), cudaMemcpyDeviceToHost, s));
+  DCD_TRY_CUDA(cudaStreamSynchronize(s));
   return DCD_OK;
 }
 
@@ -1020,7 +1121,7 @@ int pool_stats(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* L, const int64_
   DCD_TRY(out->sB.alloc(&c->mem, m));
   Buf<int32_t> prop;
   DCD_TRY(prop.alloc(&c->mem, m));
-  LV<int32_t> lv{g.rp, g.col, g.w, k, L, a, size, c->hsc->m2};
+  LV<int32_t> lv{g.rp, g.col, g.w, k, L, a, size, c->hgs[0].m2};
   lv.f_eC = out->eC.get();
   lv.f_eB = out->eB.get();
   lv.f_dB = out->dB.get();
@@ -1045,12 +1146,14 @@ int community_sums(dcd_ctx* c, int64_t n, const int32_t* labels, const int64_t* 
 }
 
 int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint8_t* active0, Buf<int64_t>& k0,
-                int32_t* out_labels, dcd_step_stats* st, int32_t* level0_out) {
+                int32_t* out_labels, dcd_step_stats* st, int32_t* level0_out, dcd_step_stats* per_graph) {
   cudaStream_t s = c->stream;
-  DevScalars* d = c->dsc.get();
+  GraphState* gs = c->gs.get();
+  const int G = c->G;
   const int T = 256;
   const int64_t n0 = g0.n;
   const int64_t tau = c->cfg.tau_inv;
+  const int32_t* gid0 = G > 1 ? c->gid.get() : nullptr;
 
   Buf<int64_t> a;
   Buf<int32_t> size, comp;
@@ -1059,43 +1162,50 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
   DCD_TRY(comp.alloc(&c->mem, n0));
   DCD_TRY(community_sums(c, n0, labels0, k0.get(), a.get(), size.get()));
   ::dcd::count_launch(), fill_iota<<<grid_for(n0, T), T, 0, s>>>(comp.get(), n0);
-  DCD_TRY_CUDA(cudaMemsetAsync(&d->sq_lo, 0, 2 * sizeof(int64_t), s));
-  ::dcd::count_launch(), sumsq_acc<<<grid_for(n0, T, 4), T, 0, s>>>(a.get(), n0, (unsigned long long*)&d->sq_lo);
-  ::dcd::count_launch(), lm_decide<<<1, 32, 0, s>>>(d, 0, nullptr, nullptr, 0, 0, tau);
+  ::dcd::count_launch(), gs_reset_pass<<<cdiv(G, 128), 128, 0, s>>>(gs, G);
+  ::dcd::count_launch(), sumsq_acc<<<grid_for(n0, T, 4), T, 0, s>>>(a.get(), n0, gid0, gs);
   DCD_LAUNCH_CHECK();
-  DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
-  DCD_TRY_CUDA(cudaStreamSynchronize(s));
 
-  int64_t level = 0, passes_total = 0, passes0 = 0, moves_total = 0, edges_total = 0, verts_total = 0;
+  // per-graph host state of the level loop
+  std::vector<int64_t> nv(G);
+  std::vector<i128> N_start(G);
+  for (int x = 0; x < G; x++) nv[x] = c->goff[x + 1] - c->goff[x];
+  GraphTally tally(G);
+
+  int64_t level = 0, passes_total = 0, passes0 = 0, edges_total = 0, verts_total = 0;
   float ms_bin[4] = {0.f, 0.f, 0.f, 0.f};
   int64_t edges_bin[4] = {0, 0, 0, 0}, verts_bin[4] = {0, 0, 0, 0};
   float ms_lm = 0.f, ms_apply = 0.f, ms_coarsen = 0.f;
-  i128 N_start = h128(c->hsc->n_start_lo, c->hsc->n_start_hi);
+  bool first_level = true;
 
   // current level: level 0 uses g0 / labels0 / k0; later levels own their data
   CoarseGraph cg[2];
   Buf<int64_t> kc[2];
-  Buf<int32_t> Lc[2];
+  Buf<int32_t> Lc[2], gidc[2];
   int which = 0;
   const Csr<int32_t>* g_l0 = &g0;
   const Csr<int64_t>* g_lc = nullptr;
   int32_t* L = labels0;
   Buf<int64_t>* kcur = &k0;
   const uint8_t* active = active0;
-  int64_t nv = n0;
+  const int32_t* gid = gid0;
+  int64_t nvu = n0;  // vertices of the union at this level
 
   for (;;) {
     LevelRun lr;
     if (level == 0) {
-      DCD_TRY(run_level<int32_t>(c, *g_l0, L, *kcur, a, size, active, &lr));
+      DCD_TRY(run_level<int32_t>(c, *g_l0, L, *kcur, a, size, active, gid, (int)level, &lr, &tally));
       if (level0_out)
         DCD_TRY_CUDA(cudaMemcpyAsync(level0_out, L, n0 * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     } else {
-      DCD_TRY(run_level<int64_t>(c, *g_lc, L, *kcur, a, size, nullptr, &lr));
+      DCD_TRY(run_level<int64_t>(c, *g_lc, L, *kcur, a, size, nullptr, gid, (int)level, &lr, &tally));
+    }
+    if (first_level) {
+      for (int x = 0; x < G; x++) N_start[x] = h128(c->hgs[x].n_start_lo, c->hgs[x].n_start_hi);
+      first_level = false;
     }
     passes_total += lr.passes;
     if (level == 0) passes0 = lr.passes;
-    moves_total += lr.moves;
     edges_total += lr.edges;
     verts_total += lr.verts;
     for (int x = 0; x < 4; x++) {
@@ -1105,17 +1215,33 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
     }
     ms_lm += lr.ms_lm;
     ms_apply += lr.ms_apply;
-    const i128 N_end = h128(c->hsc->n_cur_lo, c->hsc->n_cur_hi);
 
     DCD_TRY_CUDA(cudaEventRecord(c->ev[5], s));
     Buf<int32_t> cid;
     int64_t nc = 0;
-    if (level == 0) DCD_TRY(used_labels<int32_t>(c, *g_l0, L, cid, &nc));
-    else DCD_TRY(used_labels<int64_t>(c, *g_lc, L, cid, &nc));
+    const int nx = which ^ 1;
+    Buf<int32_t>* gnext = G > 1 ? &gidc[nx] : nullptr;
+    if (level == 0) DCD_TRY(used_labels<int32_t>(c, *g_l0, L, cid, &nc, gid, gnext));
+    else DCD_TRY(used_labels<int64_t>(c, *g_lc, L, cid, &nc, gid, gnext));
     trace("level: labels counted");
     level++;
-    bool stop = nc == nv || (level >= 2 && h_below_tau(N_end - N_start, N_start, tau)) || level >= c->cfg.max_levels;
-    if (stop) {
+    // level stop per graph: nothing merged, or (from the second level on) a
+    // gain of at most |N_start| / tau_inv, or the level cap
+    bool all_done = true;
+    for (int x = 0; x < G; x++) {
+      GraphState& X = c->hgs[x];
+      if (X.done) continue;
+      tally.levels[x] = level;
+      const i128 N_end = h128(X.n_cur_lo, X.n_cur_hi);
+      if (X.nc == nv[x] || (level >= 2 && h_below_tau(N_end - N_start[x], N_start[x], tau)) ||
+          level >= c->cfg.max_levels)
+        X.done = 1;
+      else
+        all_done = false;
+      N_start[x] = N_end;
+      nv[x] = X.nc;
+    }
+    if (all_done) {
       DCD_TRY_CUDA(cudaEventRecord(c->ev[6], s));
       DCD_TRY_CUDA(cudaEventSynchronize(c->ev[6]));
       float tc = 0.f;
@@ -1123,13 +1249,14 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
       ms_coarsen += tc;
       break;
     }
-    // ---- compact: next level ----
-    const int nx = which ^ 1;
+    DCD_TRY_CUDA(cudaMemcpyAsync(gs, c->hgs, G * sizeof(GraphState), cudaMemcpyHostToDevice, s));
+    // ---- compact: next level (all graphs together; finished graphs only
+    // carry their labels along) ----
     if (level == 1) DCD_TRY(coarsen<int32_t>(c, *g_l0, L, cid.get(), nc, &cg[nx]));
     else DCD_TRY(coarsen<int64_t>(c, *g_lc, L, cid.get(), nc, &cg[nx]));
     DCD_TRY(kc[nx].alloc(&c->mem, nc));
     DCD_TRY(Lc[nx].alloc(&c->mem, nc));
-    ::dcd::count_launch(), coarse_k<<<grid_for(nv, T), T, 0, s>>>(nv, cid.get(), a.get(), kc[nx].get());
+    ::dcd::count_launch(), coarse_k<<<grid_for(nvu, T), T, 0, s>>>(nvu, cid.get(), a.get(), kc[nx].get());
     ::dcd::count_launch(), compose<<<grid_for(n0, T), T, 0, s>>>(n0, comp.get(), L, cid.get());
     ::dcd::count_launch(), fill_iota<<<grid_for(nc, T), T, 0, s>>>(Lc[nx].get(), nc);
     DCD_LAUNCH_CHECK();
@@ -1149,39 +1276,65 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
     cg[which].w.reset();
     kc[which].reset();
     Lc[which].reset();
+    gidc[which].reset();
     which = nx;
     g_lc = &cg[which].view;
     L = Lc[which].get();
     kcur = &kc[which];
-    nv = nc;
+    gid = G > 1 ? gidc[which].get() : nullptr;
+    nvu = nc;
     active = nullptr;
-    N_start = N_end;
   }
 
   // ---- compose + canonical labels (smallest member id) ----
   DCD_TRY_CUDA(cudaEventRecord(c->ev[7], s));
   {
     Buf<int32_t> minid;
-    DCD_TRY(minid.alloc(&c->mem, nv));
-    ::dcd::count_launch(), fill_i32<<<grid_for(nv, T), T, 0, s>>>(minid.get(), nv, INT32_MAX);
+    DCD_TRY(minid.alloc(&c->mem, nvu));
+    ::dcd::count_launch(), fill_i32<<<grid_for(nvu, T), T, 0, s>>>(minid.get(), nvu, INT32_MAX);
     ::dcd::count_launch(), final_min<<<grid_for(n0, T), T, 0, s>>>(n0, comp.get(), L, minid.get());
-    DCD_TRY_CUDA(cudaMemsetAsync(&d->ncomm, 0, sizeof(int64_t), s));
+    ::dcd::count_launch(), gs_reset_nc<<<cdiv(G, 128), 128, 0, s>>>(gs, G);
     ::dcd::count_launch(), final_labels<<<grid_for(n0, T), T, 0, s>>>(n0, comp.get(), L, minid.get(), out_labels,
-                                                (unsigned long long*)&d->ncomm);
+                                                                       gid0, gs);
     DCD_LAUNCH_CHECK();
     DCD_TRY_CUDA(cudaEventRecord(c->ev[8], s));
-    DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+    DCD_TRY_CUDA(cudaMemcpyAsync(c->hgs, gs, G * sizeof(GraphState), cudaMemcpyDeviceToHost, s));
     DCD_TRY_CUDA(cudaStreamSynchronize(s));
   }
   float tf = 0.f;
   cudaEventElapsedTime(&tf, c->ev[7], c->ev[8]);
+  auto fill = [&](dcd_step_stats* o, int x) {
+    const GraphState& X = c->hgs[x];
+    const i128 N = h128(X.n_cur_lo, X.n_cur_hi);
+    o->levels = tally.levels[x];
+    o->iters_total = tally.passes[x];
+    o->iters_level0 = tally.passes0[x];
+    o->moves_total = tally.moves[x];
+    o->communities = X.ncomm;
+    o->n_lo = (int64_t)(unsigned long long)N;
+    o->n_hi = (int64_t)(unsigned long long)((unsigned __int128)N >> 64);
+    o->m2 = X.m2;
+    o->q = X.m2 == 0 ? 0.0 : (double)N / ((double)X.m2 * (double)X.m2);
+  };
+  if (per_graph)
+    for (int x = 0; x < G; x++) fill(&per_graph[x], x);
   if (st) {
-    const i128 N = h128(c->hsc->n_cur_lo, c->hsc->n_cur_hi);
-    const int64_t m2 = c->hsc->m2;
-    st->levels = level;
-    st->iters_total = passes_total;
-    st->iters_level0 = passes0;
-    st->moves_total = moves_total;
+    if (G == 1) {
+      fill(st, 0);
+      st->iters_total = passes_total;
+      st->iters_level0 = passes0;
+    } else {
+      st->levels = level;
+      st->iters_total = passes_total;
+      st->iters_level0 = passes0;
+      int64_t mv = 0, nc = 0;
+      for (int x = 0; x < G; x++) {
+        mv += tally.moves[x];
+        nc += c->hgs[x].ncomm;
+      }
+      st->moves_total = mv;
+      st->communities = nc;
+    }
     st->edges_scanned = edges_total;
     st->verts_scanned = verts_total;
     for (int x = 0; x < 4; x++) {
@@ -1189,11 +1342,6 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
       st->edges_bin[x] = edges_bin[x];
       st->verts_bin[x] = verts_bin[x];
     }
-    st->communities = c->hsc->ncomm;
-    st->n_lo = (int64_t)(unsigned long long)N;
-    st->n_hi = (int64_t)(unsigned long long)((unsigned __int128)N >> 64);
-    st->m2 = m2;
-    st->q = m2 == 0 ? 0.0 : (double)N / ((double)m2 * (double)m2);
     st->ms_local_move = ms_lm;
     st->ms_apply = ms_apply;
     st->ms_coarsen = ms_coarsen;

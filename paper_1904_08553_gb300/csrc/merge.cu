@@ -146,13 +146,16 @@ __global__ void __launch_bounds__(256) merge_rows(
     const int64_t* __restrict__ rp_n, int32_t* __restrict__ col_n, int32_t* __restrict__ w_n,
     const int64_t* __restrict__ pair_ptr, const uint64_t* __restrict__ pkey, const int64_t* __restrict__ pw,
     const uint8_t* __restrict__ pflag, const int32_t* __restrict__ pA, const int32_t* __restrict__ pR,
-    const int32_t* __restrict__ lab, int64_t* __restrict__ kdeg, unsigned long long* __restrict__ m2_acc,
-    unsigned long long* __restrict__ in_acc) {
+    const int32_t* __restrict__ lab, int64_t* __restrict__ kdeg, const int32_t* __restrict__ gid,
+    GraphState* __restrict__ gs) {
   const int g = threadIdx.x % G;
   // warp-uniform loop: every lane reaches the group shuffles
   const int64_t gid0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * (32 / G);
   const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
+  // 2m and sum_i e_{i->C(i)} per graph: accumulated while consecutive rows of
+  // a group stay in one graph, flushed by the group leader when it changes
   int64_t m2_loc = 0, in_loc = 0;
+  int cur_g = -1;
   for (int64_t ubase = gid0; ubase < n; ubase += ngroups) {
     const int64_t u = ubase + (int64_t)(lane_id() / G);
     int64_t ks = 0, is = 0;
@@ -203,20 +206,24 @@ __global__ void __launch_bounds__(256) merge_rows(
     }
     ks = group_sum<G>(ks);
     is = group_sum<G>(is);
-    if (g == 0 && u < n) kdeg[u] = ks;
-    m2_loc += ks;
-    in_loc += is;
+    if (g == 0 && u < n) {
+      kdeg[u] = ks;
+      const int gu = graph_of(gid, u);
+      if (gu != cur_g) {
+        if (cur_g >= 0 && (m2_loc | in_loc)) {
+          atomicAdd((unsigned long long*)&gs[cur_g].m2, (unsigned long long)m2_loc);
+          atomicAdd((unsigned long long*)&gs[cur_g].in_cur, (unsigned long long)in_loc);
+        }
+        cur_g = gu;
+        m2_loc = in_loc = 0;
+      }
+      m2_loc += ks;
+      in_loc += is;
+    }
   }
-  // one atomic per warp (each group leader holds its group's totals)
-  int64_t m = (g == 0) ? m2_loc : 0, i = (g == 0) ? in_loc : 0;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    m += __shfl_xor_sync(0xffffffffu, m, o);
-    i += __shfl_xor_sync(0xffffffffu, i, o);
-  }
-  if (lane_id() == 0) {
-    atomicAdd(m2_acc, (unsigned long long)m);
-    atomicAdd(in_acc, (unsigned long long)i);
+  if (g == 0 && cur_g >= 0 && (m2_loc | in_loc)) {
+    atomicAdd((unsigned long long*)&gs[cur_g].m2, (unsigned long long)m2_loc);
+    atomicAdd((unsigned long long*)&gs[cur_g].in_cur, (unsigned long long)in_loc);
   }
 }
 
@@ -318,16 +325,15 @@ int merge_batch(dcd_ctx* c, const int32_t* labels0, MergeOut* out) {
 
   // ---- merge rows, degrees, m2, in ----
   DCD_TRY(out->k.alloc(&c->mem, n));
-  DCD_TRY_CUDA(cudaMemsetAsync(&d->m2, 0, sizeof(int64_t), s));
-  DCD_TRY_CUDA(cudaMemsetAsync(&d->in_cur, 0, sizeof(int64_t), s));
+  DCD_TRY_CUDA(cudaMemsetAsync(c->gs.get(), 0, c->G * sizeof(GraphState), s));
   const int64_t avg = (cap + n - 1) / n;
   const int64_t* pp = out->pair_ptr.get();
 #define DCD_MERGE(Gs)                                                                                       \
   ::dcd::count_launch(), merge_rows<Gs><<<grid_for(n * Gs, T), T, 0, s>>>(n, rp_o, col_o, w_o, rp_n, c->col[nxt].get(),            \
                                                    c->w[nxt].get(), pp, out->pkey.get(), out->pw.get(),     \
                                                    out->pflag.get(), added.get(), removed.get(), labels0,  \
-                                                   out->k.get(), (unsigned long long*)&d->m2,               \
-                                                   (unsigned long long*)&d->in_cur)
+                                                   out->k.get(), c->G > 1 ? c->gid.get() : nullptr,         \
+                                                   c->gs.get())
   if (avg <= 6) DCD_MERGE(4);
   else if (avg <= 12) DCD_MERGE(8);
   else if (avg <= 24) DCD_MERGE(16);

@@ -39,7 +39,10 @@ struct SV {
   const uint64_t* pkey;
   const uint8_t* pflag;
   const int64_t* pair_ptr;
-  int64_t m2;
+  int64_t m2;                   // 2m when the context holds one graph
+  const int32_t* gid;           // graph of each vertex (several graphs)
+  const GraphState* gs;
+  __device__ __forceinline__ int64_t m2_of(int64_t v) const { return gid ? gs[gid[v]].m2 : m2; }
   uint8_t* mark;
   uint8_t* cflag;
   // phase A outputs / phase C inputs, indexed by position in the source list
@@ -203,7 +206,7 @@ __global__ void __launch_bounds__(256) scr_a_warp(SV g, int64_t off, int64_t cnt
         const int32_t Dj = sink ? g.L[j] : -2;
         const int64_t eD = lane_get(r, Dj);
         if (sink) {
-          const ST x = (Dj == C) ? ST(0) : gain<ST>(g.m2, ku, eD, eC, g.a[Dj], aC);
+          const ST x = (Dj == C) ? ST(0) : gain<ST>(g.m2_of(u), ku, eD, eC, g.a[Dj], aC);
           if (better3(x, Dj, j, S, D, J)) {
             S = x;
             D = Dj;
@@ -255,7 +258,7 @@ __global__ void __launch_bounds__(256) scr_a_wtbl(SV g, int64_t off, int64_t cnt
         if (!(g.pflag[q] & kPairIns)) continue;
         const int32_t j = (int32_t)(g.pkey[q] & 0xffffffffu);
         const int32_t Dj = g.L[j];
-        const ST x = (Dj == C) ? ST(0) : gain<ST>(g.m2, ku, tbl_get(keys, vals, mask, Dj), eC, g.a[Dj], aC);
+        const ST x = (Dj == C) ? ST(0) : gain<ST>(g.m2_of(u), ku, tbl_get(keys, vals, mask, Dj), eC, g.a[Dj], aC);
         if (better3(x, Dj, j, S, D, J)) {
           S = x;
           D = Dj;
@@ -322,7 +325,7 @@ __global__ void __launch_bounds__(THREADS) scr_a_block(SV g, int64_t off, int64_
         if (!(g.pflag[q] & kPairIns)) continue;
         const int32_t j = (int32_t)(g.pkey[q] & 0xffffffffu);
         const int32_t Dj = g.L[j];
-        const ST x = (Dj == C) ? ST(0) : gain<ST>(g.m2, ku, tbl_get(keys, vals, mask, Dj), eC, g.a[Dj], aC);
+        const ST x = (Dj == C) ? ST(0) : gain<ST>(g.m2_of(u), ku, tbl_get(keys, vals, mask, Dj), eC, g.a[Dj], aC);
         if (better3(x, Dj, j, S, D, J)) {
           S = x;
           D = Dj;
@@ -424,7 +427,7 @@ template <typename ST>
 __device__ __forceinline__ void decide(const SV& g, int64_t idx, int32_t j, int64_t e1, int64_t e2) {
   const int32_t i = g.src[idx];
   const int32_t Ci = g.L[i], Cj = g.L[j];
-  const ST g2 = (Cj == Ci) ? ST(0) : gain<ST>(g.m2, g.k[j], e1, e2, g.a[Ci], g.a[Cj]);
+  const ST g2 = (Cj == Ci) ? ST(0) : gain<ST>(g.m2_of(j), g.k[j], e1, e2, g.a[Ci], g.a[Cj]);
   if (ld_gain<ST>(&g.g1[2 * idx]) >= g2) g.flags[idx] |= 2;
 }
 
@@ -740,9 +743,12 @@ int screen_batch(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* labels0, cons
     DCD_TRY(jstar.alloc(&c->mem, nsrc));
     DCD_TRY(g1.alloc(&c->mem, 2 * nsrc));
     DCD_TRY(flags.alloc(&c->mem, nsrc));
-    SV sv{g.rp, g.col, g.w, k, labels0, a, mo.pkey.get(), mo.pflag.get(), mo.pair_ptr.get(), c->hsc->m2,
-          mark.get(), cflag.get(), src.get(), jstar.get(), g1.get(), flags.get()};
-    if (sv.m2 >= ((int64_t)1 << 31)) DCD_TRY(screen_impl<i128>(c, sv, g, cnt, hub_max, nsrc));
+    int64_t m2max = 0;
+    for (int x = 0; x < c->G; x++) m2max = c->hgs[x].m2 > m2max ? c->hgs[x].m2 : m2max;
+    SV sv{g.rp, g.col, g.w, k, labels0, a, mo.pkey.get(), mo.pflag.get(), mo.pair_ptr.get(), c->hgs[0].m2,
+          c->G > 1 ? c->gid.get() : nullptr, c->gs.get(), mark.get(), cflag.get(), src.get(), jstar.get(),
+          g1.get(), flags.get()};
+    if (m2max >= ((int64_t)1 << 31)) DCD_TRY(screen_impl<i128>(c, sv, g, cnt, hub_max, nsrc));
     else DCD_TRY(screen_impl<long long>(c, sv, g, cnt, hub_max, nsrc));
   }
   DCD_TRY_CUDA(cudaMemsetAsync(&d->r_size, 0, sizeof(int64_t), s));

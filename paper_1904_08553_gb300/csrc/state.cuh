@@ -19,17 +19,9 @@ struct Csr {
 
 // Per-step scalars kept on the device (one struct, copied back in one go).
 struct DevScalars {
-  int64_t m2;        // 2m of the current level (equal on every level)
-  int64_t in_cur;    // sum_i e_{i->C(i)} of the current labels
-  int64_t in_delta;  // change of in_cur produced by the last pass
-  int64_t sq_lo;     // sum_C a_C^2 (two words of an unsigned 128-bit value)
-  int64_t sq_hi;
-  int64_t n_cur_lo;  // N of the current labels
-  int64_t n_cur_hi;
-  int64_t n_start_lo;  // N at the start of the level
-  int64_t n_start_hi;
-  int32_t moves;     // movers of the last pass
-  int32_t stop;      // 1 = the level's pass loop stops
+  int64_t pad_[9];
+  int32_t any_running;  // some graph's pass loop goes on
+  int32_t stop_unused;
   int32_t nc;        // labels in use (coarsening)
   int32_t pad0;
   int64_t uniq;      // distinct coarse entries (coarsening)
@@ -45,6 +37,27 @@ struct DevScalars {
   int64_t bin2_maxdeg;  // largest degree in the 129..4096 bin
   int64_t bin_deg[4];   // sum of the degrees in each bin
 };
+
+// Per-graph state of one update.  A context holds G graphs on disjoint vertex
+// ranges (G = 1 for dcd_create, G > 1 for a dcd_group); every level-wide
+// quantity of Algorithm 1 that the paper defines per graph lives here.
+struct GraphState {
+  int64_t m2;          // 2m of the graph (equal on every level)
+  int64_t in_cur;      // sum_i e_{i->C(i)} of the current labels
+  int64_t in_delta;    // change of in_cur produced by the last pass
+  unsigned long long sq_lo, sq_hi;  // sum_C a_C^2 (unsigned 128-bit)
+  int64_t n_cur_lo, n_cur_hi;       // N of the current labels
+  int64_t n_start_lo, n_start_hi;   // N at the start of the level
+  int64_t nc;          // labels in use at the end of the level
+  int64_t nv;          // vertices of the graph at this level
+  int64_t ncomm;       // communities at the end of the update
+  int32_t moves;       // movers of the last pass
+  int32_t running;     // the graph's pass loop at this level goes on
+  int32_t passes;      // passes at this level
+  int32_t done;        // the graph's levels are over
+};
+
+__device__ __forceinline__ int graph_of(const int32_t* gid, int64_t v) { return gid ? gid[v] : 0; }
 
 // Degree bins of the local-move kernels.
 constexpr int kBinWarpMax = 32;     // 1..32: one warp, lanes hold the row
@@ -91,6 +104,15 @@ struct dcd_ctx {
   // device scalars + pinned host mirror
   dcd::Buf<dcd::DevScalars> dsc;
   dcd::DevScalars* hsc = nullptr;
+
+  // graphs of the context: G vertex ranges starting at goff[g] (goff[G] = n);
+  // gid[v] = graph of vertex v (absent when G = 1)
+  int32_t G = 1;
+  dcd::Buf<int32_t> gid;
+  dcd::Buf<int64_t> goff_d;
+  int64_t* goff = nullptr;            // host, G + 1
+  dcd::Buf<dcd::GraphState> gs;       // device, G
+  dcd::GraphState* hgs = nullptr;     // pinned host mirror, G
   int64_t* hscratch = nullptr;  // pinned, 64 words
 
   dcd::Buf<int32_t> iota;  // 0..n-1 (singleton labels)
@@ -132,7 +154,8 @@ int screen_batch(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* labels0, cons
 // level-0 result), level-0 active flags (NULL = all), k and m2 of G_t.
 // Writes canonical labels to out_labels and fills stats.
 int run_louvain(dcd_ctx* c, const Csr<int32_t>& g, int32_t* labels0, const uint8_t* active0,
-                Buf<int64_t>& k, int32_t* out_labels, dcd_step_stats* st, int32_t* level0_out = nullptr);
+                Buf<int64_t>& k, int32_t* out_labels, dcd_step_stats* st, int32_t* level0_out = nullptr,
+                dcd_step_stats* per_graph = nullptr);
 
 // louvain.cu: statistics of the learned screen's pool (mask over vertices):
 // the local-move evaluation of every pool vertex of positive degree, without
