@@ -447,6 +447,70 @@ def learned_arm(args):
     }
     print(json.dumps(line), flush=True)
 
+
+# ------------------------------------------------------------------ batched form
+
+def batched_arm(args):
+    """512 independent temporal SBMs (n log-uniform in 500..200,000, blocks of
+    20..2,000, mean degree 8..32, 3 % inserts and 1 % deletes per step) advanced
+    together by one group update per step, against the same graphs updated one
+    context at a time (both on the GPU, Delta-screening mode)."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1904_08553_gb300 import dcd, synth
+
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    streams = synth.batched_sbm(G=args.graphs, steps=7)
+    gen_s = time.time() - t0
+    sizes = [s.n for s in streams]
+    T = len(streams[0].steps)
+    grp = dcd.Group(sizes, mode=dcd.MODE_DELTA)
+    group_ms = []
+    for t in range(T):
+        for g, s in enumerate(streams):
+            grp.apply_batch(g, *s.steps[t])
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        _, q, st = grp.update(labels_out=None)
+        torch.cuda.synchronize()
+        if t >= 1:
+            group_ms.append((time.perf_counter() - a) * 1e3)
+    launches_group = st[0].launches
+    q_group = q.copy()
+    grp.close()
+    ctxs = [dcd.Context(n, mode=dcd.MODE_DELTA) for n in sizes]
+    seq_ms = []
+    q_seq = np.zeros(len(sizes))
+    launches_seq = 0
+    for t in range(T):
+        for g, s in enumerate(streams):
+            ctxs[g].apply_batch(*s.steps[t])
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        for g in range(len(sizes)):
+            _, q_seq[g], stg = ctxs[g].update(labels_out=None)
+            if t == T - 1:
+                launches_seq += stg.launches
+        torch.cuda.synchronize()
+        if t >= 1:
+            seq_ms.append((time.perf_counter() - a) * 1e3)
+    for c_ in ctxs:
+        c_.close()
+    line = {
+        "metric": "batched form: ms per time step for all graphs (group update vs one context per graph)",
+        "workload": (f"{len(sizes)} temporal SBMs, n log-uniform 500..200,000 (total {sum(sizes):,} vertices), "
+                     f"initial load + {T - 1} steps of 3% inserts / 1% deletes"),
+        "ms_per_step_group": float(np.mean(group_ms)), "ms_per_step_one_at_a_time": float(np.mean(seq_ms)),
+        "speedup": float(np.mean(seq_ms) / np.mean(group_ms)),
+        "kernel_launches_per_step": {"group": int(launches_group), "one_at_a_time": int(launches_seq)},
+        "identical_modularity": bool(np.array_equal(q_group, q_seq)), "generation_s": gen_s,
+    }
+    print(json.dumps(line), flush=True)
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -456,7 +520,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--n", type=int, default=LFR_N, help="vertex count (smaller cases for profiling)")
-    ap.add_argument("--workload", default="lfr_2m", choices=["lfr_2m", "learned"])
+    ap.add_argument("--workload", default="lfr_2m", choices=["lfr_2m", "learned", "batched"])
+    ap.add_argument("--graphs", type=int, default=512)
     ap.add_argument("--train-seeds", type=int, default=8)
     ap.add_argument("--epochs", type=int, default=4)
     ap.add_argument("--theta-keep", type=float, default=0.3)
@@ -468,6 +533,8 @@ def main():
         reference_arm(args)
     elif args.workload == "learned":
         learned_arm(args)
+    elif args.workload == "batched":
+        batched_arm(args)
     else:
         gpu_arm(args)
 

@@ -223,6 +223,25 @@ int dcd_set_collect(dcd_ctx* ctx, int32_t on);
 int dcd_get_screen_data(dcd_ctx* ctx, float* X_out, float* y_out, int32_t* vertex_out, int64_t cap,
                         int64_t* n_out);
 
+/* ---- batched form: many independent dynamic graphs in one context ----
+ * G graphs of n[g] vertices each (sum <= 2^31 - 1) advance together: one
+ * update runs every kernel once for all graphs (they occupy disjoint vertex
+ * ranges of one union graph), while 2m, the tracked modularity and the pass
+ * and level stop rules of Algorithm 1 stay per graph, so every graph's result
+ * is the one its own context would give.  Modes STATIC, BASE, DELTA only.
+ * dcd_group_apply_batch stages a batch of graph g (local ids in [0, n[g]),
+ * host arrays); dcd_group_update advances every graph one step.
+ * labels_out: sum(n) int32 (graph after graph, local canonical labels), host
+ * or device, may be NULL; q_out: G doubles (host, may be NULL); stats_out: G
+ * dcd_step_stats (host, may be NULL).  Errors as dcd_create / dcd_update;
+ * DCD_EINVAL also for g out of range. */
+typedef struct dcd_group dcd_group;
+int dcd_group_create(int32_t G, const int64_t* n, const dcd_config* cfg, void* cuda_stream, dcd_group** out);
+int dcd_group_destroy(dcd_group* grp);
+int dcd_group_apply_batch(dcd_group* grp, int32_t g, const dcd_edge* ins, int64_t n_ins, const dcd_edge* del,
+                          int64_t n_del);
+int dcd_group_update(dcd_group* grp, int32_t* labels_out, double* q_out, dcd_step_stats* stats_out);
+
 /* ---- allocation-free evaluation ----
  * No counterpart in the paper: a service for callers that cannot allocate
  * device memory when they need the answer (their device memory is held by

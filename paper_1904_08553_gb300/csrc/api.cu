@@ -308,7 +308,13 @@ int dcd_apply_batch_device(dcd_ctx* c, const dcd_edge* ins, int64_t n_ins, const
   return DCD_OK;
 }
 
-static int update_impl(dcd_ctx* c, dcd_step_stats* st) {
+}  // extern "C"
+
+namespace dcd {
+int update_impl(dcd_ctx* c, dcd_step_stats* st, dcd_step_stats* per_graph);
+}
+
+int dcd::update_impl(dcd_ctx* c, dcd_step_stats* st, dcd_step_stats* per_graph) {
   cudaStream_t s = c->stream;
   const int64_t n = c->n;
   DevScalars* d = c->dsc.get();
@@ -399,7 +405,8 @@ static int update_impl(dcd_ctx* c, dcd_step_stats* st) {
   // ---- Algorithm 1 with R_t at level 0 ----
   DCD_TRY(c->labels_nx.ensure(&c->mem, n));
   if (collect) DCD_TRY(c->level0.ensure(&c->mem, n));
-  DCD_TRY(run_louvain(c, g, L0.get(), active, mo.k, c->labels_nx.get(), st, collect ? c->level0.get() : nullptr));
+  DCD_TRY(run_louvain(c, g, L0.get(), active, mo.k, c->labels_nx.get(), st, collect ? c->level0.get() : nullptr,
+                      per_graph));
   if (collect) DCD_TRY(screen_labels(c, src_labels, c->level0.get()));
   if (learned && c->judge && st) {
     // the judge: plain Delta-screening from the same state; keep it when the
@@ -458,6 +465,8 @@ static int update_impl(dcd_ctx* c, dcd_step_stats* st) {
   return DCD_OK;
 }
 
+extern "C" {
+
 int dcd_update(dcd_ctx* c, int32_t* labels_out, double* q_out, dcd_step_stats* stats) {
   if (!c) return DCD_EINVAL;
   DCD_SCOPE(c);
@@ -469,7 +478,7 @@ int dcd_update(dcd_ctx* c, int32_t* labels_out, double* q_out, dcd_step_stats* s
     const int64_t nnz_cap = c->nnz + 2 * c->n_ins;
     DCD_TRY(c->mem.begin_step((size_t)(40 * nnz_cap + 64 * c->n + 48 * R) + ((size_t)64 << 20)));
   }
-  const int rc = update_impl(c, &st);
+  const int rc = update_impl(c, &st, nullptr);
   c->mem.end_step();
   st.launches = dcd::g_launches.load() - launches0;
   // the staged batch is consumed by the attempt, successful or not

@@ -28,6 +28,7 @@ EXPORTED = [
     "dcd_modularity_noalloc", "dcd_mlp_create", "dcd_mlp_destroy", "dcd_mlp_set_params",
     "dcd_mlp_get_params", "dcd_mlp_forward", "dcd_mlp_grad", "dcd_mlp_train",
     "dcd_set_screen", "dcd_set_collect", "dcd_get_screen_data",
+    "dcd_group_create", "dcd_group_destroy", "dcd_group_apply_batch", "dcd_group_update",
 ]
 MLP_FEATURES, MLP_HIDDEN, MLP_PARAMS = 12, 64, 5057
 NOALLOC_MAX_N = 1048056
@@ -120,6 +121,10 @@ def lib():
             "dcd_set_screen": (INT, [P, P, ctypes.c_float, ctypes.c_float, I32]),
             "dcd_set_collect": (INT, [P, I32]),
             "dcd_get_screen_data": (INT, [P, P, P, P, I64, P]),
+            "dcd_group_create": (INT, [I32, P, P, P, P]),
+            "dcd_group_destroy": (INT, [P]),
+            "dcd_group_apply_batch": (INT, [P, I32, P, I64, P, I64]),
+            "dcd_group_update": (INT, [P, P, P, P]),
             "dcd_strerror": (ctypes.c_char_p, [INT]),
             "dcd_last_cuda_error": (ctypes.c_char_p, []),
         }
@@ -428,3 +433,61 @@ class Mlp:
 
     def train(self, d_X, d_y, n, batch=4096, epochs=1, lr=1e-3):
         return dcd_mlp_train(self._h, d_X, d_y, n, batch, epochs, lr)
+
+
+# ---- batched form ---------------------------------------------------------------
+
+def dcd_group_create(sizes, cfg: Config | None = None, stream=None):
+    n = np.ascontiguousarray(sizes, dtype=np.int64)
+    h = ctypes.c_void_p()
+    _check(lib().dcd_group_create(len(n), _ptr(n), ctypes.byref(cfg) if cfg is not None else None,
+                                  _stream_ptr(stream), ctypes.byref(h)), "dcd_group_create")
+    return h
+
+
+def dcd_group_destroy(h) -> None:
+    _check(lib().dcd_group_destroy(h), "dcd_group_destroy")
+
+
+def dcd_group_apply_batch(h, g: int, ins=None, dels=None) -> None:
+    i3, d3 = _edges(ins, "ins"), _edges(dels, "dels")
+    _check(lib().dcd_group_apply_batch(h, int(g), _ptr(i3), len(i3), _ptr(d3), len(d3)), "dcd_group_apply_batch")
+
+
+def dcd_group_update(h, G: int, labels_out=None):
+    q = np.zeros(G, np.float64)
+    st = (StepStats * G)()
+    _check(lib().dcd_group_update(h, _ptr(labels_out), _ptr(q), ctypes.cast(st, ctypes.c_void_p).value),
+           "dcd_group_update")
+    return q, list(st)
+
+
+class Group:
+    """Many independent dynamic graphs advanced together (dcd_group)."""
+
+    def __init__(self, sizes, mode: int = MODE_DELTA, stream=None):
+        cfg = dcd_config_default()
+        cfg.mode = mode
+        self.sizes = np.asarray(sizes, dtype=np.int64)
+        self.G = len(self.sizes)
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)])
+        self._h = dcd_group_create(self.sizes, cfg, stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            dcd_group_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply_batch(self, g, ins=None, dels=None):
+        dcd_group_apply_batch(self._h, g, ins, dels)
+
+    def update(self, labels_out="host"):
+        out = np.empty(int(self.offsets[-1]), np.int32) if isinstance(labels_out, str) else labels_out
+        q, st = dcd_group_update(self._h, self.G, out)
+        return out, q, st
