@@ -197,19 +197,37 @@ int dcd_create(int64_t n, const dcd_config* cfg, void* cuda_stream, dcd_ctx** ou
   c->mem.stream = c->stream;
   int rc = DCD_OK;
   do {
-    if (cudaGetDevice(&c->device) != cudaSuccess) { rc = DCD_ECUDA; break; }
+    {
+      const cudaError_t ee = cudaGetDevice(&c->device);
+      if (ee != cudaSuccess) {
+        note_cuda_error(ee, "cudaGetDevice", __FILE__, __LINE__);
+        rc = DCD_ECUDA;
+        break;
+      }
+    }
     c->sms = num_sms();
     cudaMemPoolProps props{};
     props.allocType = cudaMemAllocationTypePinned;
     props.location.type = cudaMemLocationTypeDevice;
     props.location.id = c->device;
-    if (cudaMemPoolCreate(&c->mem.pool, &props) != cudaSuccess) { rc = DCD_ECUDA; break; }
-    uint64_t thr = UINT64_MAX;
-    cudaMemPoolSetAttribute(c->mem.pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    if (cudaMemPoolCreate(&c->mem.pool, &props) != cudaSuccess) {
+      // many contexts in one process: share the device's default pool
+      cudaGetLastError();
+      c->mem.pool = nullptr;
+    } else {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(c->mem.pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
     if (cudaMallocHost(&c->hsc, sizeof(DevScalars)) != cudaSuccess) { rc = DCD_ENOMEM; break; }
     if (cudaMallocHost(&c->hscratch, 64 * sizeof(int64_t)) != cudaSuccess) { rc = DCD_ENOMEM; break; }
-    for (auto& e : c->ev)
-      if (cudaEventCreate(&e) != cudaSuccess) { rc = DCD_ECUDA; break; }
+    for (auto& e : c->ev) {
+      const cudaError_t ee = cudaEventCreate(&e);
+      if (ee != cudaSuccess) {
+        note_cuda_error(ee, "cudaEventCreate", __FILE__, __LINE__);
+        rc = DCD_ECUDA;
+        break;
+      }
+    }
     if (rc) break;
     if ((rc = c->dsc.alloc(&c->mem, 1))) break;
     if ((rc = c->gs.alloc(&c->mem, 1))) break;
