@@ -482,24 +482,24 @@ def batched_arm(args):
     launches_group = st[0].launches
     q_group = q.copy()
     grp.close()
-    ctxs = [dcd.Context(n, mode=dcd.MODE_DELTA) for n in sizes]
-    seq_ms = []
+    # one context per graph, one graph after the other (a context lives for its
+    # graph's whole stream); the per-step time is summed over the graphs
+    seq_ms = np.zeros(T - 1)
     q_seq = np.zeros(len(sizes))
     launches_seq = 0
-    for t in range(T):
-        for g, s in enumerate(streams):
-            ctxs[g].apply_batch(*s.steps[t])
-        torch.cuda.synchronize()
-        a = time.perf_counter()
-        for g in range(len(sizes)):
-            _, q_seq[g], stg = ctxs[g].update(labels_out=None)
+    for g, s_ in enumerate(streams):
+        ctx = dcd.Context(sizes[g], mode=dcd.MODE_DELTA)
+        for t in range(T):
+            ctx.apply_batch(*s_.steps[t])
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            _, q_seq[g], stg = ctx.update(labels_out=None)
+            torch.cuda.synchronize()
+            if t >= 1:
+                seq_ms[t - 1] += (time.perf_counter() - a) * 1e3
             if t == T - 1:
                 launches_seq += stg.launches
-        torch.cuda.synchronize()
-        if t >= 1:
-            seq_ms.append((time.perf_counter() - a) * 1e3)
-    for c_ in ctxs:
-        c_.close()
+        ctx.close()
     line = {
         "metric": "batched form: ms per time step for all graphs (group update vs one context per graph)",
         "workload": (f"{len(sizes)} temporal SBMs, n log-uniform 500..200,000 (total {sum(sizes):,} vertices), "
