@@ -128,6 +128,30 @@ __device__ __forceinline__ void tbl_add(int32_t* keys, unsigned long long* vals,
   }
 }
 
+// tbl_add that also appends each newly claimed slot to slots[] (counter *ns),
+// so the distinct keys can be visited, and the table emptied again, without a
+// scan over the whole capacity.
+__device__ __forceinline__ void tbl_add_list(int32_t* keys, unsigned long long* vals, uint16_t* slots, int32_t* ns,
+                                             uint32_t mask, int32_t lab, unsigned long long x) {
+  uint32_t s = hash_label(lab, mask);
+  for (;;) {
+    int32_t k = keys[s];
+    if (k == lab) {
+      atomicAdd(&vals[s], x);
+      return;
+    }
+    if (k == -1) {
+      const int32_t old = atomicCAS(&keys[s], -1, lab);
+      if (old == -1) slots[atomicAdd(ns, 1)] = (uint16_t)s;
+      if (old == -1 || old == lab) {
+        atomicAdd(&vals[s], x);
+        return;
+      }
+    }
+    s = (s + 1) & mask;
+  }
+}
+
 __device__ __forceinline__ int64_t tbl_get(const int32_t* keys, const unsigned long long* vals, uint32_t mask,
                                            int32_t lab) {
   uint32_t s = hash_label(lab, mask);

@@ -1,6 +1,7 @@
 // api.cu -- the extern "C" entry points of dcd.h and the per-step driver
 // (Sec. III-D: G_t <- G_{t-1} + Delta_t; R_t; multi-level run; C_t, Q_t).
 #include <chrono>
+#include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -58,6 +59,21 @@ void trace(const char* what) {
   const clk::time_point now = clk::now();
   fprintf(stderr, "[dcd] %-28s %9.3f ms\n", what, std::chrono::duration<double, std::milli>(now - last).count());
   last = now;
+}
+
+bool trace_on() {
+  static const bool on = getenv("DCD_TRACE") != nullptr;
+  return on;
+}
+
+void tracef(const char* fmt, ...) {
+  if (!trace_on()) return;
+  va_list ap;
+  va_start(ap, fmt);
+  fprintf(stderr, "[dcd] ");
+  vfprintf(stderr, fmt, ap);
+  fprintf(stderr, "\n");
+  va_end(ap);
 }
 
 void note_cuda_error(cudaError_t e, const char* what, const char* file, int line) {

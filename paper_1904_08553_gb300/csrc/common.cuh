@@ -22,6 +22,8 @@ inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed);
 // Host-side phase trace: with the environment variable DCD_TRACE set, prints
 // the host time since the previous trace point (a debugging aid; off by default).
 void trace(const char* what);
+bool trace_on();
+void tracef(const char* fmt, ...);
 
 // Records the failing CUDA call for dcd_last_cuda_error().
 void note_cuda_error(cudaError_t e, const char* what, const char* file, int line);

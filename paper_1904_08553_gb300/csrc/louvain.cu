@@ -16,6 +16,7 @@
 //             grouped with match_any and summed with redux.sync
 //   lm_block  33..4096 entries: one CTA per vertex, shared-memory table
 //             > 4096 entries: one CTA per vertex, table in global memory
+#include <cstdio>
 #include <vector>
 
 #include "agg.cuh"
@@ -114,48 +115,86 @@ __global__ void __launch_bounds__(256) lm_warp(LV<W> g, const int32_t* __restric
   }
 }
 
-// One warp per vertex of 33..256 entries: a warp-private shared-memory table
-// (capacity 2 x degree rounded up to a power of two, at most kMidCap).
-template <typename W, typename ST>
+// One warp per vertex of up to 32 Q entries, with a warp-private shared-memory
+// table of CAP = 64 Q slots (the table of a row of d entries uses the first
+// 2 d rounded up to a power of two).  The row is loaded into registers first
+// (Q entries a lane, all loads in flight together, then all label gathers),
+// each 32-entry chunk is grouped by label with match_any, and the group
+// leaders add into the table.  New keys are listed as they are claimed, so
+// the gain step visits only the distinct communities and then empties
+// exactly the slots it used: the table is cleared once per kernel, not once
+// per vertex.
+template <int CAP>
+__host__ __device__ constexpr size_t warp_tbl_bytes() {
+  return (size_t)CAP * 12 + (size_t)CAP + 16;  // values, keys, slot list (CAP / 2 entries of 2 bytes), count
+}
+
+template <typename W, typename ST, int CAP, int Q>
 __global__ void __launch_bounds__(256) lm_warp_tbl(LV<W> g, const int32_t* __restrict__ list, int64_t cnt,
                                                    int32_t* __restrict__ prop) {
+  static_assert(CAP == 64 * Q, "table of twice the largest row");
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = lane_id(), wib = threadIdx.x >> 5;
-  unsigned long long* vals = reinterpret_cast<unsigned long long*>(smem) + (size_t)wib * kMidCap;
-  int32_t* keys = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned long long*>(smem) + 8 * kMidCap) +
-                  (size_t)wib * kMidCap;
+  unsigned char* base = smem + (size_t)wib * warp_tbl_bytes<CAP>();
+  unsigned long long* vals = reinterpret_cast<unsigned long long*>(base);
+  int32_t* keys = reinterpret_cast<int32_t*>(base + (size_t)CAP * 8);
+  uint16_t* slots = reinterpret_cast<uint16_t*>(base + (size_t)CAP * 12);
+  int32_t* nslot = reinterpret_cast<int32_t*>(base + (size_t)CAP * 13);
+  for (int s = lane; s < CAP; s += 32) {
+    keys[s] = -1;
+    vals[s] = 0;
+  }
+  if (lane == 0) *nslot = 0;
+  __syncwarp();
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < cnt; i += nw) {
     const int32_t v = list[i];
     const int64_t b = g.rp[v];
-    const int64_t d = g.rp[v + 1] - b;
+    const int d = (int)(g.rp[v + 1] - b);
     const int32_t C = g.L[v];
-    const uint32_t cap = table_cap(d), mask = cap - 1;
-    for (uint32_t s = lane; s < cap; s += 32) {
-      keys[s] = -1;
-      vals[s] = 0;
+    int32_t lab[Q];
+    W wt[Q];
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      const int e = q * 32 + lane;
+      lab[q] = -1;
+      wt[q] = W(0);
+      if (e < d) {
+        lab[q] = g.col[b + e];
+        wt[q] = g.w[b + e];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      const int32_t u = lab[q];
+      lab[q] = (u >= 0 && u != v) ? g.L[u] : -1;
+    }
+    const uint32_t mask = table_cap(d) - 1;
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      if (q * 32 < d) {
+        const unsigned peers = __match_any_sync(0xffffffffu, lab[q]);
+        const int64_t sum = group_sum_exact(peers, lab[q] >= 0 ? wt[q] : W(0));
+        if (lab[q] >= 0 && (int)(__ffs(peers) - 1) == lane)
+          tbl_add_list(keys, vals, slots, nslot, mask, lab[q], (unsigned long long)sum);
+      }
     }
     __syncwarp();
-    for (int64_t e0 = 0; e0 < d; e0 += 32) {
-      const int64_t e = e0 + lane;
-      bool valid = e < d;
-      const int32_t u = valid ? g.col[b + e] : -1;
-      valid = valid && u != v;
-      const int32_t lab = valid ? g.L[u] : -1;
-      const W wt = valid ? g.w[b + e] : W(0);
-      const unsigned peers = __match_any_sync(0xffffffffu, lab);
-      const int64_t sum = group_sum_exact(peers, wt);
-      if (valid && (int)(__ffs(peers) - 1) == lane) tbl_add(keys, vals, mask, lab, (unsigned long long)sum);
+    const int nd = *nslot;
+    long long eC = 0;
+    for (int j0 = 0; j0 < nd; j0 += 32) {
+      const int j = j0 + lane;
+      const int32_t key = j < nd ? keys[slots[j]] : -1;
+      const unsigned cm = __ballot_sync(0xffffffffu, key == C);
+      if (cm) eC = (long long)vals[slots[j0 + __ffs(cm) - 1]];
     }
-    __syncwarp();
-    long long eC = lane == 0 ? tbl_get(keys, vals, mask, C) : 0;
-    eC = __shfl_sync(0xffffffffu, eC, 0);
     const int64_t kv = g.k[v], aC = g.a[C], m2v = g.m2_of(v);
     ST S = gain_lowest<ST>();
     int32_t D = INT_MAX;
-    for (uint32_t s = lane; s < cap; s += 32) {
+    for (int j = lane; j < nd; j += 32) {
+      const uint32_t s = slots[j];
       const int32_t key = keys[s];
-      if (key >= 0 && key != C) {
+      if (key != C) {
         const ST x = gain<ST>(m2v, kv, (int64_t)vals[s], eC, g.a[key], aC);
         if (better(x, key, S, D)) {
           S = x;
@@ -174,6 +213,123 @@ __global__ void __launch_bounds__(256) lm_warp_tbl(LV<W> g, const int32_t* __res
       }
     }
     __syncwarp();
+    for (int j = lane; j < nd; j += 32) {
+      const uint32_t s = slots[j];
+      keys[s] = -1;
+      vals[s] = 0;
+    }
+    if (lane == 0) *nslot = 0;
+    __syncwarp();
+  }
+}
+
+// One CTA per vertex of up to THREADS x Q entries (the large bin), with the
+// same scheme at block scope: registers hold the row, the shared table lists
+// its claimed slots, and only those are visited and emptied.
+template <typename W, typename ST, int THREADS, int Q>
+__global__ void __launch_bounds__(THREADS) lm_large(LV<W> g, const int32_t* __restrict__ list, int64_t cnt,
+                                                    int32_t* __restrict__ prop, int32_t tcap) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int NW = THREADS / 32;
+  __shared__ ST redS[NW];
+  __shared__ int32_t redD[NW];
+  __shared__ long long s_eC;
+  __shared__ int32_t s_n;
+  unsigned long long* vals = reinterpret_cast<unsigned long long*>(smem);
+  int32_t* keys = reinterpret_cast<int32_t*>(smem + (size_t)tcap * 8);
+  uint16_t* slots = reinterpret_cast<uint16_t*>(smem + (size_t)tcap * 12);
+  const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5;
+  for (int s = tid; s < tcap; s += THREADS) {
+    keys[s] = -1;
+    vals[s] = 0;
+  }
+  if (tid == 0) {
+    s_n = 0;
+    s_eC = 0;
+  }
+  __syncthreads();
+  for (int64_t i = blockIdx.x; i < cnt; i += gridDim.x) {
+    const int32_t v = list[i];
+    const int64_t b = g.rp[v];
+    const int d = (int)(g.rp[v + 1] - b);
+    const int32_t C = g.L[v];
+    int32_t lab[Q];
+    W wt[Q];
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      const int e = q * THREADS + tid;
+      lab[q] = -1;
+      wt[q] = W(0);
+      if (e < d) {
+        lab[q] = g.col[b + e];
+        wt[q] = g.w[b + e];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      const int32_t u = lab[q];
+      lab[q] = (u >= 0 && u != v) ? g.L[u] : -1;
+    }
+    const uint32_t mask = table_cap(d) - 1;
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      if (q * THREADS < d) {
+        const unsigned peers = __match_any_sync(0xffffffffu, lab[q]);
+        const int64_t sum = group_sum_exact(peers, lab[q] >= 0 ? wt[q] : W(0));
+        if (lab[q] >= 0 && (int)(__ffs(peers) - 1) == lane)
+          tbl_add_list(keys, vals, slots, &s_n, mask, lab[q], (unsigned long long)sum);
+      }
+    }
+    __syncthreads();
+    const int nd = s_n;
+    for (int j = tid; j < nd; j += THREADS)
+      if (keys[slots[j]] == C) s_eC = (long long)vals[slots[j]];
+    __syncthreads();
+    const int64_t eC = s_eC, kv = g.k[v], aC = g.a[C], m2v = g.m2_of(v);
+    ST S = gain_lowest<ST>();
+    int32_t D = INT_MAX;
+    for (int j = tid; j < nd; j += THREADS) {
+      const uint32_t s = slots[j];
+      const int32_t key = keys[s];
+      if (key != C) {
+        const ST x = gain<ST>(m2v, kv, (int64_t)vals[s], eC, g.a[key], aC);
+        if (better(x, key, S, D)) {
+          S = x;
+          D = key;
+        }
+      }
+    }
+    warp_argmax(S, D);
+    if (lane == 0) {
+      redS[wid] = S;
+      redD[wid] = D;
+    }
+    __syncthreads();
+    if (wid == 0) {
+      S = lane < NW ? redS[lane] : gain_lowest<ST>();
+      D = lane < NW ? redD[lane] : INT_MAX;
+      warp_argmax(S, D);
+      if (lane == 0) {
+        prop[i] = (D != INT_MAX && S > 0) ? guard_choice(C, D, g.size) : C;
+        if (g.f_eC) {
+          g.f_eC[i] = eC;
+          g.f_eB[i] = D == INT_MAX ? 0 : tbl_get(keys, vals, mask, D);
+          g.f_dB[i] = D == INT_MAX ? -1 : D;
+          g.f_sB[i] = D == INT_MAX ? 0.0 : to_double(S);
+        }
+      }
+    }
+    __syncthreads();
+    for (int j = tid; j < nd; j += THREADS) {
+      const uint32_t s = slots[j];
+      keys[s] = -1;
+      vals[s] = 0;
+    }
+    if (tid == 0) {
+      s_n = 0;
+      s_eC = 0;
+    }
+    __syncthreads();
   }
 }
 
@@ -486,19 +642,19 @@ __global__ void lm_decide(GraphState* __restrict__ gs, int G, int mode, int32_t 
 // ---------------------------------------------------------------- binning
 
 __global__ void bin_count(const int64_t* __restrict__ rp, int64_t n, const uint8_t* __restrict__ active,
-                          DevScalars* d, const int32_t* __restrict__ gid, const GraphState* __restrict__ gs) {
-  __shared__ unsigned long long sc[4], sdb[4];
+                          DevScalars* d, const int32_t* __restrict__ gid, const GraphState* __restrict__ gs,
+                          BinPlan plan) {
+  __shared__ unsigned long long sc[kMaxBins], sdb[kMaxBins];
+  __shared__ long long smax[kMaxBins];
   __shared__ unsigned long long sdeg, sact;
-  __shared__ long long smax, smax2;
-  if (threadIdx.x < 4) {
+  if (threadIdx.x < kMaxBins) {
     sc[threadIdx.x] = 0;
     sdb[threadIdx.x] = 0;
+    smax[threadIdx.x] = 0;
   }
   if (threadIdx.x == 0) {
     sdeg = 0;
     sact = 0;
-    smax = 0;
-    smax2 = 0;
   }
   __syncthreads();
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
@@ -508,35 +664,33 @@ __global__ void bin_count(const int64_t* __restrict__ rp, int64_t n, const uint8
     atomicAdd(&sdeg, (unsigned long long)deg);
     atomicAdd(&sact, 1ull);
     if (deg == 0) continue;
-    const int bin = deg <= kBinWarpMax ? 0 : deg <= kBinMidMax ? 1 : deg <= kBinLargeMax ? 2 : 3;
+    const int bin = bin_of(plan, deg);
     atomicAdd(&sc[bin], 1ull);
     atomicAdd(&sdb[bin], (unsigned long long)deg);
-    if (bin == 3) atomicMax(&smax, (long long)deg);
-    if (bin == 2) atomicMax(&smax2, (long long)deg);
+    atomicMax(&smax[bin], (long long)deg);
   }
   __syncthreads();
-  if (threadIdx.x < 4 && sc[threadIdx.x]) {
-    atomicAdd((unsigned long long*)&d->bin_cnt[threadIdx.x], sc[threadIdx.x]);
-    atomicAdd((unsigned long long*)&d->bin_deg[threadIdx.x], sdb[threadIdx.x]);
+  if (threadIdx.x < plan.nb && sc[threadIdx.x]) {
+    atomicAdd((unsigned long long*)&d->bcnt[threadIdx.x], sc[threadIdx.x]);
+    atomicAdd((unsigned long long*)&d->bdeg[threadIdx.x], sdb[threadIdx.x]);
+    atomicMax((long long*)&d->bmax[threadIdx.x], smax[threadIdx.x]);
   }
   if (threadIdx.x == 0) {
     atomicAdd((unsigned long long*)&d->act_deg, sdeg);
     atomicAdd((unsigned long long*)&d->ncomm, sact);
-    atomicMax((long long*)&d->bin_maxdeg, smax);
-    atomicMax((long long*)&d->bin2_maxdeg, smax2);
   }
 }
 
 __global__ void bin_scatter(const int64_t* __restrict__ rp, int64_t n, const uint8_t* __restrict__ active,
                             const DevScalars* __restrict__ d, int32_t* __restrict__ cursor,
                             int32_t* __restrict__ list, const int32_t* __restrict__ gid,
-                            const GraphState* __restrict__ gs) {
-  __shared__ int32_t off[4];
+                            const GraphState* __restrict__ gs, BinPlan plan) {
+  __shared__ int32_t off[kMaxBins];
   if (threadIdx.x == 0) {
     int64_t o = 0;
-    for (int b = 0; b < 4; b++) {
+    for (int b = 0; b < plan.nb; b++) {
       off[b] = (int32_t)o;
-      o += d->bin_cnt[b];
+      o += d->bcnt[b];
     }
   }
   __syncthreads();
@@ -547,10 +701,9 @@ __global__ void bin_scatter(const int64_t* __restrict__ rp, int64_t n, const uin
     int bin = -1;
     if (v < n && (!active || active[v]) && (!gid || gs[gid[v]].running)) {
       const int64_t deg = rp[v + 1] - rp[v];
-      if (deg > 0) bin = deg <= kBinWarpMax ? 0 : deg <= kBinMidMax ? 1 : deg <= kBinLargeMax ? 2 : 3;
+      if (deg > 0) bin = bin_of(plan, deg);
     }
-#pragma unroll
-    for (int b = 0; b < 4; b++) {
+    for (int b = 0; b < plan.nb; b++) {
       const unsigned bal = __ballot_sync(0xffffffffu, bin == b);
       if (!bal) continue;
       int32_t slot = 0;
@@ -797,11 +950,10 @@ struct LevelRun {
 
 // Degree bins of the active vertices of one level and the hub tables.
 struct Bins {
+  BinPlan plan;
   Buf<int32_t> list;
-  int64_t cnt[4] = {0, 0, 0, 0};
+  int64_t cnt[kMaxBins] = {}, deg[kMaxBins] = {}, maxd[kMaxBins] = {}, off[kMaxBins + 1] = {};
   int64_t total = 0, act_deg = 0, n_active = 0;
-  int64_t deg[4] = {0, 0, 0, 0};
-  size_t large_smem = 0;
   Buf<int32_t> hkeys;
   Buf<unsigned long long> hvals;
   int64_t hub_cap = 0, hub_ctas = 0;
@@ -813,37 +965,47 @@ int make_bins(dcd_ctx* c, const Csr<W>& g, const uint8_t* active, Bins* b, const
   DevScalars* d = c->dsc.get();
   const int64_t nv = g.n;
   const int T = 256;
-  DCD_TRY_CUDA(cudaMemsetAsync(&d->bin_cnt[0], 0, sizeof(int64_t) * 7, s));  // bins, maxdeg, act_deg, ncomm
-  DCD_TRY_CUDA(cudaMemsetAsync(&d->bin2_maxdeg, 0, 5 * sizeof(int64_t), s));  // bin2_maxdeg, bin_deg[4]
-  ::dcd::count_launch(), bin_count<<<grid_for(nv, T), T, 0, s>>>(g.rp, nv, active, d, gid, c->gs.get());
+  b->plan = c->bin_plan;
+  const BinPlan& plan = b->plan;
+  DCD_TRY_CUDA(cudaMemsetAsync(&d->act_deg, 0, 2 * sizeof(int64_t), s));  // act_deg, ncomm
+  DCD_TRY_CUDA(cudaMemsetAsync(&d->bcnt[0], 0, 3 * kMaxBins * sizeof(int64_t), s));  // bcnt, bdeg, bmax
+  ::dcd::count_launch(), bin_count<<<grid_for(nv, T), T, 0, s>>>(g.rp, nv, active, d, gid, c->gs.get(), plan);
   DCD_LAUNCH_CHECK();
   DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
   DCD_TRY_CUDA(cudaStreamSynchronize(s));
-  for (int x = 0; x < 4; x++) {
-    b->cnt[x] = c->hsc->bin_cnt[x];
-    b->deg[x] = c->hsc->bin_deg[x];
+  b->total = 0;
+  for (int x = 0; x < plan.nb; x++) {
+    b->cnt[x] = c->hsc->bcnt[x];
+    b->deg[x] = c->hsc->bdeg[x];
+    b->maxd[x] = c->hsc->bmax[x];
+    b->off[x] = b->total;
+    b->total += b->cnt[x];
   }
-  b->total = b->cnt[0] + b->cnt[1] + b->cnt[2] + b->cnt[3];
-  const int64_t hub_max = c->hsc->bin_maxdeg;
-  b->large_smem = (size_t)table_cap(c->hsc->bin2_maxdeg > 0 ? c->hsc->bin2_maxdeg : 1) * 12;
+  b->off[plan.nb] = b->total;
   b->act_deg = c->hsc->act_deg;
   b->n_active = c->hsc->ncomm;  // bin_count leaves the active count here
   Buf<int32_t> cursor;
   DCD_TRY(b->list.alloc(&c->mem, b->total));
-  DCD_TRY(cursor.alloc(&c->mem, 4));
-  DCD_TRY_CUDA(cudaMemsetAsync(cursor.get(), 0, 4 * sizeof(int32_t), s));
+  DCD_TRY(cursor.alloc(&c->mem, kMaxBins));
+  DCD_TRY_CUDA(cudaMemsetAsync(cursor.get(), 0, kMaxBins * sizeof(int32_t), s));
   if (b->total > 0) {
     ::dcd::count_launch(), bin_scatter<<<grid_for(nv, T), T, 0, s>>>(g.rp, nv, active, d, cursor.get(),
-                                                                       b->list.get(), gid, c->gs.get());
+                                                                       b->list.get(), gid, c->gs.get(), plan);
     DCD_LAUNCH_CHECK();
   }
   // hub tables in global memory: one region per CTA, sized for the largest hub
-  if (b->cnt[3]) {
+  int64_t hub_cnt = 0, hub_max = 0;
+  for (int x = 0; x < plan.nb; x++)
+    if (plan.var[x] == kLmHub) {
+      hub_cnt += b->cnt[x];
+      hub_max = b->maxd[x] > hub_max ? b->maxd[x] : hub_max;
+    }
+  if (hub_cnt) {
     b->hub_cap = table_cap(hub_max);
     const int64_t budget = (int64_t)1 << 30;  // bytes for hub tables
     int64_t hc = budget / (b->hub_cap * 12);
     if (hc < 1) hc = 1;
-    if (hc > b->cnt[3]) hc = b->cnt[3];
+    if (hc > hub_cnt) hc = hub_cnt;
     if (hc > 4 * (int64_t)c->sms) hc = 4 * (int64_t)c->sms;
     b->hub_ctas = hc;
     DCD_TRY(b->hkeys.alloc(&c->mem, hc * b->hub_cap));
@@ -852,45 +1014,65 @@ int make_bins(dcd_ctx* c, const Csr<W>& g, const uint8_t* active, Bins* b, const
   return DCD_OK;
 }
 
-// One local-move evaluation of every binned vertex (proposals in prop[]).
+template <typename W, typename ST, int CAP, int Q>
+int launch_warp_tbl(dcd_ctx* c, const LV<W>& g, const int32_t* lst, int64_t cnt, int32_t* prop) {
+  constexpr int T = 256;
+  constexpr size_t smem = (size_t)(T / 32) * warp_tbl_bytes<CAP>();
+  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_warp_tbl<W, ST, CAP, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  count_launch(), lm_warp_tbl<W, ST, CAP, Q><<<grid_for(cnt * 32, T, 8), T, smem, c->stream>>>(g, lst, cnt, prop);
+  return DCD_OK;
+}
+
+template <typename W, typename ST, int THREADS, int Q>
+int launch_large(dcd_ctx* c, const LV<W>& g, const int32_t* lst, int64_t cnt, int64_t maxd, int32_t* prop) {
+  const int32_t tcap = (int32_t)table_cap(maxd);
+  const size_t smem = (size_t)tcap * 14;  // values, keys, claimed-slot list
+  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_large<W, ST, THREADS, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)((size_t)table_cap((int64_t)THREADS * Q) * 14)));
+  const int64_t ctas = cnt < 16 * (int64_t)c->sms ? cnt : 16 * (int64_t)c->sms;
+  count_launch(), lm_large<W, ST, THREADS, Q><<<(unsigned)ctas, THREADS, smem, c->stream>>>(g, lst, cnt, prop, tcap);
+  return DCD_OK;
+}
+
+// One local-move evaluation of every binned vertex (proposals in prop[]);
+// bin_ev[x] is recorded after bin x.
 template <typename W, typename ST>
 int launch_lm_st(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEvent_t* bin_ev) {
   cudaStream_t s = c->stream;
   const int T = 256;
-  const size_t mid_smem = (size_t)8 * kMidCap * 12;
-  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_warp_tbl<W, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mid_smem));
-  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_block<W, ST, kLargeThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)((size_t)kLargeCap * 12)));
-  const int32_t* lst = b.list.get();
-  const int64_t* cnt = b.cnt;
-  LV<W> g1 = lv, g2 = lv, g3 = lv;  // feature outputs shifted to each bin's list offset
-  auto shift = [](LV<W>& x, int64_t o) {
-    if (x.f_eC) {
-      x.f_eC += o;
-      x.f_eB += o;
-      x.f_dB += o;
-      x.f_sB += o;
+  const int32_t* lst0 = b.list.get();
+  for (int x = 0; x < b.plan.nb; x++) {
+    const int64_t cnt = b.cnt[x], o = b.off[x];
+    if (cnt) {
+      LV<W> g = lv;  // feature outputs shifted to the bin's list offset
+      if (g.f_eC) {
+        g.f_eC += o;
+        g.f_eB += o;
+        g.f_dB += o;
+        g.f_sB += o;
+      }
+      const int32_t* lst = lst0 + o;
+      int32_t* pr = prop + o;
+      switch (b.plan.var[x]) {
+        case kLmWarp:
+          count_launch(), lm_warp<W, ST><<<grid_for(cnt * 32, T, 16), T, 0, s>>>(g, lst, cnt, pr);
+          break;
+        case kLmWarp128: DCD_TRY((launch_warp_tbl<W, ST, 256, 4>(c, g, lst, cnt, pr))); break;
+        case kLmWarp256: DCD_TRY((launch_warp_tbl<W, ST, 512, 8>(c, g, lst, cnt, pr))); break;
+        case kLmBlk512: DCD_TRY((launch_large<W, ST, 256, 2>(c, g, lst, cnt, b.maxd[x], pr))); break;
+        case kLmBlk1k: DCD_TRY((launch_large<W, ST, 256, 4>(c, g, lst, cnt, b.maxd[x], pr))); break;
+        case kLmBlk2k: DCD_TRY((launch_large<W, ST, 256, 8>(c, g, lst, cnt, b.maxd[x], pr))); break;
+        case kLmBlk4k: DCD_TRY((launch_large<W, ST, 512, 8>(c, g, lst, cnt, b.maxd[x], pr))); break;
+        default:
+          count_launch(), lm_block<W, ST, kHubThreads><<<(unsigned)b.hub_ctas, kHubThreads, 0, s>>>(
+              g, lst, cnt, pr, b.hkeys.get(), b.hvals.get(), b.hub_cap);
+          break;
+      }
+      DCD_LAUNCH_CHECK();
     }
-  };
-  shift(g1, cnt[0]);
-  shift(g2, cnt[0] + cnt[1]);
-  shift(g3, cnt[0] + cnt[1] + cnt[2]);
-  if (cnt[0]) count_launch(), lm_warp<W, ST><<<grid_for(cnt[0] * 32, T, 16), T, 0, s>>>(lv, lst, cnt[0], prop);
-  if (bin_ev) DCD_TRY_CUDA(cudaEventRecord(bin_ev[0], s));
-  if (cnt[1])
-    count_launch(), lm_warp_tbl<W, ST><<<grid_for(cnt[1] * 32, T, 8), T, mid_smem, s>>>(g1, lst + cnt[0], cnt[1],
-                                                                                         prop + cnt[0]);
-  if (bin_ev) DCD_TRY_CUDA(cudaEventRecord(bin_ev[1], s));
-  if (cnt[2])
-    count_launch(), lm_block<W, ST, kLargeThreads>
-        <<<(unsigned)(cnt[2] < 8 * c->sms ? cnt[2] : 8 * c->sms), kLargeThreads, b.large_smem, s>>>(
-            g2, lst + cnt[0] + cnt[1], cnt[2], prop + cnt[0] + cnt[1], nullptr, nullptr, 0);
-  if (bin_ev) DCD_TRY_CUDA(cudaEventRecord(bin_ev[2], s));
-  if (cnt[3])
-    count_launch(), lm_block<W, ST, kHubThreads><<<(unsigned)b.hub_ctas, kHubThreads, 0, s>>>(
-        g3, lst + cnt[0] + cnt[1] + cnt[2], cnt[3], prop + cnt[0] + cnt[1] + cnt[2], b.hkeys.get(), b.hvals.get(),
-        b.hub_cap);
-  DCD_LAUNCH_CHECK();
+    if (bin_ev) DCD_TRY_CUDA(cudaEventRecord(bin_ev[x], s));
+  }
   return DCD_OK;
 }
 
@@ -924,15 +1106,20 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
   Bins bins;
   DCD_TRY(make_bins<W>(c, g, active, &bins, gid));
   trace("level: binned");
-  const int64_t* cnt = bins.cnt;
   const int64_t total = bins.total;
+  // list positions from big_from on hold rows longer than 256 entries: their
+  // movers' delta of sum_i e_{i->C(i)} is taken by a CTA each
+  int64_t big_from = 0;
+  for (int x = 0; x < bins.plan.nb; x++)
+    if (bins.plan.var[x] <= kLmWarp256) big_from += bins.cnt[x];
+  const int64_t n_big = total - big_from;
   Buf<int32_t> prop, Lprev, mvit, moved, moved_cnt, moved_big, moved_big_cnt;
   DCD_TRY(prop.alloc(&c->mem, total));
   DCD_TRY(Lprev.alloc(&c->mem, nv));
   DCD_TRY(mvit.alloc(&c->mem, nv));
   DCD_TRY(moved.alloc(&c->mem, total));
   DCD_TRY(moved_cnt.alloc(&c->mem, 1));
-  DCD_TRY(moved_big.alloc(&c->mem, cnt[2] + cnt[3]));
+  DCD_TRY(moved_big.alloc(&c->mem, n_big));
   DCD_TRY(moved_big_cnt.alloc(&c->mem, 1));
   ::dcd::count_launch(), fill_i32<<<grid_for(nv, T), T, 0, s>>>(mvit.get(), nv, -1);
   DCD_LAUNCH_CHECK();
@@ -957,17 +1144,17 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
     DCD_TRY_CUDA(cudaEventRecord(c->ev[2], s));
     if (any) DCD_TRY(launch_lm<W>(c, lvl, bins, prop.get(), &c->ev[12]));
     else
-      for (int x = 12; x < 15; x++) DCD_TRY_CUDA(cudaEventRecord(c->ev[x], s));
+      for (int x = 0; x < bins.plan.nb; x++) DCD_TRY_CUDA(cudaEventRecord(c->ev[12 + x], s));
     DCD_TRY_CUDA(cudaEventRecord(c->ev[3], s));
     if (total) {
       ::dcd::count_launch(), lm_apply<<<grid_for(total, T), T, 0, s>>>(
-          lst, total, cnt[0] + cnt[1], prop.get(), L, kbuf.get(), (unsigned long long*)a.get(), size.get(),
+          lst, total, big_from, prop.get(), L, kbuf.get(), (unsigned long long*)a.get(), size.get(),
           Lprev.get(), mvit.get(), iter, moved.get(), moved_cnt.get(), moved_big.get(), moved_big_cnt.get(), gid, gs);
-      if (cnt[0] + cnt[1])
-        ::dcd::count_launch(), lm_delta_in<W><<<grid_for((cnt[0] + cnt[1]) * 32, T, 16), T, 0, s>>>(
+      if (big_from)
+        ::dcd::count_launch(), lm_delta_in<W><<<grid_for(big_from * 32, T, 16), T, 0, s>>>(
             lv, moved.get(), moved_cnt.get(), Lprev.get(), mvit.get(), iter, gs);
-      if (cnt[2] + cnt[3])
-        ::dcd::count_launch(), lm_delta_in_block<W><<<grid_for((cnt[2] + cnt[3]) * T, T, 4), T, 0, s>>>(
+      if (n_big)
+        ::dcd::count_launch(), lm_delta_in_block<W><<<grid_for(n_big * T, T, 4), T, 0, s>>>(
             lv, moved_big.get(), moved_big_cnt.get(), Lprev.get(), mvit.get(), iter, gs);
     }
     ::dcd::count_launch(), sumsq_acc<<<sq_ctas, T, 0, s>>>(a.get(), nv, gid, gs);
@@ -984,15 +1171,22 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
     out->ms_lm += t1;
     out->ms_apply += t2;
     {
-      float tb[4] = {0.f, 0.f, 0.f, 0.f};
-      cudaEventElapsedTime(&tb[0], c->ev[2], c->ev[12]);
-      cudaEventElapsedTime(&tb[1], c->ev[12], c->ev[13]);
-      cudaEventElapsedTime(&tb[2], c->ev[13], c->ev[14]);
-      cudaEventElapsedTime(&tb[3], c->ev[14], c->ev[3]);
-      for (int x = 0; x < 4; x++) {
-        out->ms_bin[x] += tb[x];
-        out->edges_bin[x] += bins.deg[x];
-        out->verts_bin[x] += bins.cnt[x];
+      float tb[kMaxBins] = {};
+      for (int x = 0; x < bins.plan.nb; x++) {
+        cudaEventElapsedTime(&tb[x], x ? c->ev[11 + x] : c->ev[2], c->ev[12 + x]);
+        const int k = lm_variant_class(bins.plan.var[x]);
+        out->ms_bin[k] += tb[x];
+        out->edges_bin[k] += bins.deg[x];
+        out->verts_bin[k] += bins.cnt[x];
+      }
+      if (trace_on()) {
+        char buf[512];
+        int o = 0;
+        for (int x = 0; x < bins.plan.nb && o < 400; x++)
+          o += snprintf(buf + o, sizeof(buf) - o, " [<=%lld: %lld v %lld e %.3f ms]",
+                        bins.plan.hi[x] == INT64_MAX ? -1LL : (long long)bins.plan.hi[x], (long long)bins.cnt[x],
+                        (long long)bins.deg[x], tb[x]);
+        tracef("pass %d level %d:%s apply %.3f", (int)out->passes, level, buf, t2);
       }
     }
     out->passes++;

@@ -25,8 +25,6 @@ struct DevScalars {
   int32_t nc;        // labels in use (coarsening)
   int32_t pad0;
   int64_t uniq;      // distinct coarse entries (coarsening)
-  int64_t bin_cnt[4];
-  int64_t bin_maxdeg;
   int64_t act_deg;   // sum of the active vertices' degrees
   int64_t ncomm;     // communities at the end
   int64_t nsrc;      // screening: distinct sources
@@ -34,8 +32,9 @@ struct DevScalars {
   int64_t r_size;    // |R_t|
   uint32_t err;      // kErr* bits
   uint32_t pad1;
-  int64_t bin2_maxdeg;  // largest degree in the 129..4096 bin
-  int64_t bin_deg[4];   // sum of the degrees in each bin
+  int64_t bcnt[8];   // active vertices in each degree bin
+  int64_t bdeg[8];   // sum of their degrees
+  int64_t bmax[8];   // largest degree in the bin
 };
 
 // Per-graph state of one update.  A context holds G graphs on disjoint vertex
@@ -59,16 +58,70 @@ struct GraphState {
 
 __device__ __forceinline__ int graph_of(const int32_t* gid, int64_t v) { return gid ? gid[v] : 0; }
 
-// Degree bins of the local-move kernels.
-constexpr int kBinWarpMax = 32;     // 1..32: one warp, lanes hold the row
-constexpr int kBinMidMax = 256;     // 33..256: one warp, warp-private shared table
-constexpr int kBinLargeMax = 4096;  // 257..4096: 256-thread CTA, shared table
-                                    // >4096: 512-thread CTA, table in global memory
-constexpr int kMidThreads = 64;
+// Degree bins of the local-move kernels.  A bin holds the active vertices
+// whose degree lies in (hi of the previous bin, hi]; each bin runs one kernel
+// variant, which bounds the degree it accepts:
+//   kLmWarp      1..32     one warp a vertex, lanes hold the row (no table)
+//   kLmWarp128   ..128     one warp a vertex, warp-private shared table of 256
+//   kLmWarp256   ..256     one warp a vertex, warp-private shared table of 512
+//   kLmBlk512    ..512     one CTA a vertex, shared table (256 threads)
+//   kLmBlk1k     ..1024    one CTA a vertex, shared table (256 threads)
+//   kLmBlk2k     ..2048    one CTA a vertex, shared table (256 threads)
+//   kLmBlk4k     ..4096    one CTA a vertex, shared table (512 threads)
+//   kLmHub       any       one CTA a vertex, table in global memory
+constexpr int kMaxBins = 8;
+enum LmVariant : int32_t {
+  kLmWarp = 0,
+  kLmWarp128,
+  kLmWarp256,
+  kLmBlk512,
+  kLmBlk1k,
+  kLmBlk2k,
+  kLmBlk4k,
+  kLmHub,
+  kLmVariants
+};
+__host__ __device__ __forceinline__ int64_t lm_variant_max(int v) {
+  return v == kLmWarp ? 32 : v == kLmWarp128 ? 128 : v == kLmWarp256 ? 256 : v == kLmBlk512 ? 512
+       : v == kLmBlk1k ? 1024 : v == kLmBlk2k ? 2048 : v == kLmBlk4k ? 4096 : INT64_MAX;
+}
+// The four classes the step statistics report (warp, warp + table, CTA, hub).
+__host__ __device__ __forceinline__ int lm_variant_class(int v) {
+  return v == kLmWarp ? 0 : v <= kLmWarp256 ? 1 : v <= kLmBlk4k ? 2 : 3;
+}
+
+struct BinPlan {
+  int32_t nb = 0;
+  int32_t var[kMaxBins] = {};
+  int64_t hi[kMaxBins] = {};  // the last bin's is INT64_MAX
+};
+
+__host__ __device__ __forceinline__ int bin_of(const BinPlan& p, int64_t deg) {
+  int b = 0;
+  while (b < p.nb - 1 && deg > p.hi[b]) b++;
+  return b;
+}
+
+// Every variant in degree order, each bin as wide as its kernel allows.
+inline BinPlan default_bin_plan() {
+  BinPlan p;
+  p.nb = kLmVariants;
+  for (int v = 0; v < kLmVariants; v++) {
+    p.var[v] = v;
+    p.hi[v] = lm_variant_max(v);
+  }
+  return p;
+}
+
+// The screening kernels' three source bins (1..32 warp, 33..256 warp with a
+// shared table, 257..4096 CTA with a shared table, larger: global table).
+constexpr int kBinWarpMax = 32;
+constexpr int kBinMidMax = 256;
+constexpr int kBinLargeMax = 4096;
 constexpr int kLargeThreads = 256;
 constexpr int kHubThreads = 512;
-constexpr int kMidCap = 512;  // table_cap(kBinMidMax)
-constexpr int kLargeCap = 8192;
+constexpr int kMidCap = 512;     // table_cap(kBinMidMax)
+constexpr int kLargeCap = 8192;  // table_cap(kBinLargeMax)
 
 }  // namespace dcd
 
@@ -129,7 +182,8 @@ struct dcd_ctx {
   int64_t feat_n = 0;
   bool feat_has_y = false;
 
-  cudaEvent_t ev[16] = {};
+  cudaEvent_t ev[24] = {};
+  dcd::BinPlan bin_plan = dcd::default_bin_plan();  // degree bins of the local-move kernels
 };
 
 namespace dcd {
