@@ -65,23 +65,18 @@ __device__ __forceinline__ void warp_argmax(i128& S, int32_t& D) {
   }
 }
 
-// Whole-warp argmax of (S, D) for 64-bit gains with redux.sync: the maximum
-// of the high words, then of the low words among those lanes, then the
-// smallest label among the lanes holding the maximum (labels are >= 0, the
-// sentinel INT_MAX).  Same result as warp_argmax, fewer instructions.
+// Whole-warp argmax of (S, D) for 64-bit gains with redux.sync over the full
+// warp: the maximum of the high words, then of the low words among the lanes
+// holding that high word, then the smallest label among the lanes holding
+// the maximum (labels are >= 0, the sentinel INT_MAX).  Lanes outside each
+// step contribute the neutral value, so no lane diverges.
 __device__ __forceinline__ void warp_argmax(long long& S, int32_t& D) {
   const unsigned long long u = (unsigned long long)S ^ 0x8000000000000000ull;
   const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
   const unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
-  const unsigned m1 = __ballot_sync(0xffffffffu, hi == mhi);
-  unsigned mlo = 0;
-  if (hi == mhi) mlo = __reduce_max_sync(m1, lo);
-  mlo = __shfl_sync(0xffffffffu, mlo, __ffs(m1) - 1);
+  const unsigned mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
   const bool top = hi == mhi && lo == mlo;
-  const unsigned m2 = __ballot_sync(0xffffffffu, top);
-  unsigned dmin = 0;
-  if (top) dmin = __reduce_min_sync(m2, (unsigned)D);
-  dmin = __shfl_sync(0xffffffffu, dmin, __ffs(m2) - 1);
+  const unsigned dmin = __reduce_min_sync(0xffffffffu, top ? (unsigned)D : 0xffffffffu);
   S = (long long)((((unsigned long long)mhi << 32) | mlo) ^ 0x8000000000000000ull);
   D = (int32_t)dmin;
 }
@@ -104,6 +99,29 @@ __device__ __forceinline__ int64_t group_sum_exact(unsigned peers, int64_t w) {
     s += (int64_t)__reduce_add_sync(peers, part) << (16 * q);
   }
   return s;
+}
+
+// Sum of weights over the lanes of `peers` as the gain arithmetic needs it:
+// with 64-bit gains 2m < 2^31, so every sum of a vertex's weights is below
+// 2^31 and one 32-bit reduction is exact; with 128-bit gains the sum is
+// taken exactly from 16-bit slices.
+template <typename ST, typename W>
+__device__ __forceinline__ int64_t group_sum(unsigned peers, W w);
+template <>
+__device__ __forceinline__ int64_t group_sum<long long, int32_t>(unsigned peers, int32_t w) {
+  return (int64_t)__reduce_add_sync(peers, (unsigned)w);
+}
+template <>
+__device__ __forceinline__ int64_t group_sum<long long, int64_t>(unsigned peers, int64_t w) {
+  return (int64_t)__reduce_add_sync(peers, (unsigned)w);
+}
+template <>
+__device__ __forceinline__ int64_t group_sum<i128, int32_t>(unsigned peers, int32_t w) {
+  return group_sum_exact(peers, w);
+}
+template <>
+__device__ __forceinline__ int64_t group_sum<i128, int64_t>(unsigned peers, int64_t w) {
+  return group_sum_exact(peers, w);
 }
 
 // ---- open-addressing table: key -1 = empty; capacity a power of two that is

@@ -64,14 +64,19 @@ __device__ __forceinline__ int32_t guard_choice(int32_t C, int32_t D, const int3
 
 // ---------------------------------------------------------------- local move
 
+// One warp per vertex of at most 32 entries: lanes hold the row, labels are
+// grouped with match_any and their weights summed with redux.sync, and the
+// best community is a warp argmax over the group leaders.  The code has no
+// divergent branch: the kernel is bound by the issue rate of the warp-wide
+// instructions, so every reduction runs over the full warp with neutral
+// values, and the next vertex's row bounds load while the current row is
+// aggregated.
 template <typename W, typename ST>
 __global__ void __launch_bounds__(256) lm_warp(LV<W> g, const int32_t* __restrict__ list, int64_t cnt,
                                                int32_t* __restrict__ prop) {
   const int lane = lane_id();
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  // software pipeline: the next vertex's id and row bounds load while the
-  // current row is aggregated
   int32_t v = i < cnt ? list[i] : 0;
   int64_t b = g.rp[v], bend = g.rp[v + 1];
   for (; i < cnt; i += nw) {
@@ -79,32 +84,29 @@ __global__ void __launch_bounds__(256) lm_warp(LV<W> g, const int32_t* __restric
     const int32_t vn = in < cnt ? list[in] : v;
     const int d = (int)(bend - b);
     const int32_t C = g.L[v];
+    const int64_t kv = g.k[v], m2v = g.m2_of(v);
+    const int64_t aC = g.a[C];
     bool valid = lane < d;
-    int32_t u = valid ? g.col[b + lane] : -1;
+    const int32_t u = valid ? g.col[b + lane] : -1;
     valid = valid && u != v;
     const int32_t lab = valid ? g.L[u] : -1;
     const W wt = valid ? g.w[b + lane] : W(0);
+    const int64_t aD = valid ? g.a[lab] : 0;
     const int64_t bn = g.rp[vn], bendn = g.rp[vn + 1];
     const unsigned peers = __match_any_sync(0xffffffffu, lab);
-    const int64_t e = group_sum_exact(peers, wt);
-    const bool leader = (int)(__ffs(peers) - 1) == lane;
-    const unsigned cm = __ballot_sync(0xffffffffu, valid && leader && lab == C);
-    const int64_t eCx = __shfl_sync(0xffffffffu, e, cm ? __ffs(cm) - 1 : 0);
-    const int64_t eC = cm ? eCx : 0;
-    ST S = gain_lowest<ST>();
-    int32_t D = INT_MAX;
-    if (valid && leader && lab != C) {
-      S = gain<ST>(g.m2_of(v), g.k[v], e, eC, g.a[lab], g.a[C]);
-      D = lab;
-    }
+    const int64_t e = group_sum<ST>(peers, wt);
+    const int64_t eC = group_sum<ST>(0xffffffffu, lab == C ? wt : W(0));
+    const bool cand = valid && (int)(__ffs(peers) - 1) == lane && lab != C;
+    const ST x = gain<ST>(m2v, kv, e, eC, aD, aC);
+    ST S = cand ? x : gain_lowest<ST>();
+    int32_t D = cand ? lab : INT_MAX;
     warp_argmax(S, D);
     if (lane == 0) prop[i] = (D != INT_MAX && S > 0) ? guard_choice(C, D, g.size) : C;
     if (g.f_eC) {
-      const unsigned bm = __ballot_sync(0xffffffffu, valid && leader && lab == D);
-      const int64_t eBx = __shfl_sync(0xffffffffu, e, bm ? __ffs(bm) - 1 : 0);
+      const int64_t eB = group_sum<ST>(0xffffffffu, (valid && lab == D) ? wt : W(0));
       if (lane == 0) {
         g.f_eC[i] = eC;
-        g.f_eB[i] = bm ? eBx : 0;
+        g.f_eB[i] = eB;
         g.f_dB[i] = D == INT_MAX ? -1 : D;
         g.f_sB[i] = D == INT_MAX ? 0.0 : to_double(S);
       }
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(256) lm_warp_tbl(LV<W> g, const int32_t* __res
     for (int q = 0; q < Q; q++) {
       if (q * 32 < d) {
         const unsigned peers = __match_any_sync(0xffffffffu, lab[q]);
-        const int64_t sum = group_sum_exact(peers, lab[q] >= 0 ? wt[q] : W(0));
+        const int64_t sum = group_sum<ST>(peers, lab[q] >= 0 ? wt[q] : W(0));
         if (lab[q] >= 0 && (int)(__ffs(peers) - 1) == lane)
           tbl_add_list(keys, vals, slots, nslot, mask, lab[q], (unsigned long long)sum);
       }
@@ -275,7 +277,7 @@ __global__ void __launch_bounds__(THREADS) lm_large(LV<W> g, const int32_t* __re
     for (int q = 0; q < Q; q++) {
       if (q * THREADS < d) {
         const unsigned peers = __match_any_sync(0xffffffffu, lab[q]);
-        const int64_t sum = group_sum_exact(peers, lab[q] >= 0 ? wt[q] : W(0));
+        const int64_t sum = group_sum<ST>(peers, lab[q] >= 0 ? wt[q] : W(0));
         if (lab[q] >= 0 && (int)(__ffs(peers) - 1) == lane)
           tbl_add_list(keys, vals, slots, &s_n, mask, lab[q], (unsigned long long)sum);
       }
@@ -371,7 +373,7 @@ __global__ void __launch_bounds__(THREADS) lm_block(LV<W> g, const int32_t* __re
       const int32_t lab = valid ? g.L[u] : -1;
       const W wt = valid ? g.w[b + e] : W(0);
       const unsigned peers = __match_any_sync(0xffffffffu, lab);
-      const int64_t sum = group_sum_exact(peers, wt);
+      const int64_t sum = group_sum<ST>(peers, wt);
       if (valid && (int)(__ffs(peers) - 1) == lane) tbl_add(keys, vals, mask, lab, (unsigned long long)sum);
     }
     __syncthreads();
