@@ -81,6 +81,32 @@ __device__ __forceinline__ void warp_argmax(long long& S, int32_t& D) {
   D = (int32_t)dmin;
 }
 
+// Argmax of (S, D) over the SEG-lane segment of the calling lane (mask: that
+// segment's lanes); SEG = 32 is the whole warp.
+template <int SEG>
+__device__ __forceinline__ void seg_argmax(long long& S, int32_t& D, unsigned mask) {
+  const unsigned long long u = (unsigned long long)S ^ 0x8000000000000000ull;
+  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+  const unsigned mhi = __reduce_max_sync(mask, hi);
+  const unsigned mlo = __reduce_max_sync(mask, hi == mhi ? lo : 0u);
+  const bool top = hi == mhi && lo == mlo;
+  const unsigned dmin = __reduce_min_sync(mask, top ? (unsigned)D : 0xffffffffu);
+  S = (long long)((((unsigned long long)mhi << 32) | mlo) ^ 0x8000000000000000ull);
+  D = (int32_t)dmin;
+}
+template <int SEG>
+__device__ __forceinline__ void seg_argmax(i128& S, int32_t& D, unsigned) {
+#pragma unroll
+  for (int o = SEG / 2; o > 0; o >>= 1) {
+    const i128 s2 = shfl_xor_st(S, o);
+    const int32_t d2 = __shfl_xor_sync(0xffffffffu, D, o);
+    if (better(s2, d2, S, D)) {
+      S = s2;
+      D = d2;
+    }
+  }
+}
+
 // Exact sum of non-negative weights over the lanes of `peers` (a match_any
 // group), from 16-bit slices reduced with redux.sync: no slice sum can carry
 // out of 32 bits, so the result is exact for any int32/int64 weight.

@@ -62,49 +62,83 @@ __device__ __forceinline__ int32_t guard_choice(int32_t C, int32_t D, const int3
   return D;
 }
 
+// The proposal of a vertex from its best (S, D): move on S > 0, subject to
+// the guard.  Evaluated by every lane of the (uniform) argmax result, so the
+// caller stores it with a predicated write instead of a divergent branch.
+__device__ __forceinline__ int32_t proposal(long long S, int32_t D, int32_t C, const int32_t* size) {
+  const bool mv = D != INT_MAX && S > 0;
+  const int32_t Dm = mv ? D : C;
+  const int32_t sC = size[C], sD = size[Dm];
+  return (mv && sC == 1 && sD == 1 && Dm > C) ? C : Dm;
+}
+__device__ __forceinline__ int32_t proposal(i128 S, int32_t D, int32_t C, const int32_t* size) {
+  const bool mv = D != INT_MAX && S > 0;
+  const int32_t Dm = mv ? D : C;
+  const int32_t sC = size[C], sD = size[Dm];
+  return (mv && sC == 1 && sD == 1 && Dm > C) ? C : Dm;
+}
+
 // ---------------------------------------------------------------- local move
 
-// One warp per vertex of at most 32 entries: lanes hold the row, labels are
-// grouped with match_any and their weights summed with redux.sync, and the
-// best community is a warp argmax over the group leaders.  The code has no
-// divergent branch: the kernel is bound by the issue rate of the warp-wide
-// instructions, so every reduction runs over the full warp with neutral
-// values, and the next vertex's row bounds load while the current row is
-// aggregated.
-template <typename W, typename ST>
+// SEG lanes per vertex (SEG = 32: one warp; SEG = 16: two vertices a warp)
+// for rows of at most SEG entries: lanes hold the row, labels are grouped
+// with match_any (the key carries the segment, so segments never mix) and
+// their weights summed with redux.sync, and the best community is a segment
+// argmax over the group leaders.  The code has no divergent branch: the
+// kernel is bound by the issue rate of the warp-wide instructions, so every
+// reduction runs over whole segments with neutral values, and the next
+// vertex's row bounds load while the current row is aggregated.
+template <typename W, typename ST, int SEG>
 __global__ void __launch_bounds__(256) lm_warp(LV<W> g, const int32_t* __restrict__ list, int64_t cnt,
                                                int32_t* __restrict__ prop) {
-  const int lane = lane_id();
+  static_assert(SEG == 32 || SEG == 16, "one or two vertices a warp");
+  constexpr int P = 32 / SEG;
+  const int lane = lane_id(), sub = lane / SEG, sl = lane % SEG;
+  const unsigned smask = SEG == 32 ? 0xffffffffu : (((1u << SEG) - 1u) << (sub * SEG));
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  int32_t v = i < cnt ? list[i] : 0;
-  int64_t b = g.rp[v], bend = g.rp[v + 1];
-  for (; i < cnt; i += nw) {
-    const int64_t in = i + nw;
-    const int32_t vn = in < cnt ? list[in] : v;
+  const int64_t stride = nw * P;
+  int64_t base = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * P;
+  int32_t v = base + sub < cnt ? list[base + sub] : -1;
+  int64_t b = 0, bend = 0;
+  if (v >= 0) {
+    b = g.rp[v];
+    bend = g.rp[v + 1];
+  }
+  for (; base < cnt; base += stride) {
+    const int64_t i = base + sub, in = i + stride;
+    const int32_t vn = in < cnt ? list[in] : -1;
+    const bool has = v >= 0;
+    const int32_t vv = has ? v : 0;
     const int d = (int)(bend - b);
-    const int32_t C = g.L[v];
-    const int64_t kv = g.k[v], m2v = g.m2_of(v);
+    const int32_t C = g.L[vv];
+    const int64_t kv = g.k[vv], m2v = g.m2_of(vv);
     const int64_t aC = g.a[C];
-    bool valid = lane < d;
-    const int32_t u = valid ? g.col[b + lane] : -1;
+    bool valid = sl < d;
+    const int32_t u = valid ? g.col[b + sl] : -1;
     valid = valid && u != v;
     const int32_t lab = valid ? g.L[u] : -1;
-    const W wt = valid ? g.w[b + lane] : W(0);
+    const W wt = valid ? g.w[b + sl] : W(0);
     const int64_t aD = valid ? g.a[lab] : 0;
-    const int64_t bn = g.rp[vn], bendn = g.rp[vn + 1];
-    const unsigned peers = __match_any_sync(0xffffffffu, lab);
+    int64_t bn = 0, bendn = 0;
+    if (vn >= 0) {
+      bn = g.rp[vn];
+      bendn = g.rp[vn + 1];
+    }
+    // labels are < 2^31 - 1, so bit 31 is free for the segment
+    const unsigned key = valid ? ((unsigned)lab | ((unsigned)sub << 31)) : 0xffffffffu;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
     const int64_t e = group_sum<ST>(peers, wt);
-    const int64_t eC = group_sum<ST>(0xffffffffu, lab == C ? wt : W(0));
+    const int64_t eC = group_sum<ST>(smask, lab == C ? wt : W(0));
     const bool cand = valid && (int)(__ffs(peers) - 1) == lane && lab != C;
     const ST x = gain<ST>(m2v, kv, e, eC, aD, aC);
     ST S = cand ? x : gain_lowest<ST>();
     int32_t D = cand ? lab : INT_MAX;
-    warp_argmax(S, D);
-    if (lane == 0) prop[i] = (D != INT_MAX && S > 0) ? guard_choice(C, D, g.size) : C;
+    seg_argmax<SEG>(S, D, smask);
+    const int32_t pv = proposal(S, D, C, g.size);
+    if (sl == 0 && has) prop[i] = pv;
     if (g.f_eC) {
-      const int64_t eB = group_sum<ST>(0xffffffffu, (valid && lab == D) ? wt : W(0));
-      if (lane == 0) {
+      const int64_t eB = group_sum<ST>(smask, (valid && lab == D) ? wt : W(0));
+      if (sl == 0 && has) {
         g.f_eC[i] = eC;
         g.f_eB[i] = eB;
         g.f_dB[i] = D == INT_MAX ? -1 : D;
@@ -205,8 +239,9 @@ __global__ void __launch_bounds__(256) lm_warp_tbl(LV<W> g, const int32_t* __res
       }
     }
     warp_argmax(S, D);
+    const int32_t pv = proposal(S, D, C, g.size);
+    if (lane == 0) prop[i] = pv;
     if (lane == 0) {
-      prop[i] = (D != INT_MAX && S > 0) ? guard_choice(C, D, g.size) : C;
       if (g.f_eC) {
         g.f_eC[i] = eC;
         g.f_eB[i] = D == INT_MAX ? 0 : tbl_get(keys, vals, mask, D);
@@ -758,6 +793,57 @@ __global__ void mark_used(int64_t n, const int32_t* __restrict__ L, int32_t* __r
 // of the chunk with match_any + redux before one emit per distinct key.
 constexpr int64_t kSegEntries = 1024;
 
+// Row of entry e for the entry-linear walks below: every warp takes a
+// segment of kSegEntries consecutive entries, finds the row of its first
+// entry by binary search, then advances 32 entries at a time with the row
+// ends of the next 32 rows in its lanes.
+struct RowWalk {
+  int64_t r;  // row of the chunk's first entry
+  __device__ __forceinline__ void start(const int64_t* __restrict__ rp, int64_t n, int64_t E0) {
+    int64_t x = 0;
+    if (lane_id() == 0) {  // last row whose start is <= E0
+      int64_t lo = 0, hi = n - 1;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (rp[mid] <= E0) lo = mid; else hi = mid - 1;
+      }
+      x = lo;
+    }
+    r = __shfl_sync(0xffffffffu, x, 0);
+  }
+  // row of entry c0 + lane (entries past the segment get the last row)
+  __device__ __forceinline__ int64_t row(const int64_t* __restrict__ rp, int64_t n, int64_t c0, bool valid) {
+    const int lane = lane_id();
+    const int64_t e = c0 + lane;
+    const int64_t bk = (r + 1 + lane <= n) ? rp[r + 1 + lane] : INT64_MAX;  // end of row r + lane
+    const int64_t last = __shfl_sync(0xffffffffu, bk, 31);
+    int64_t rw;
+    if (last <= c0 + 31) {
+      // more than 31 rows end inside this chunk (empty rows): search per lane
+      int64_t lo = r, hi = n - 1, x = valid ? e : c0;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (rp[mid] <= x) lo = mid; else hi = mid - 1;
+      }
+      rw = lo;
+    } else {
+      int cntv = 0;
+      const int64_t x = valid ? e : c0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int64_t v = __shfl_sync(0xffffffffu, bk, cntv + step - 1);
+        if (v <= x) cntv += step;
+      }
+      rw = r + cntv;
+    }
+    r = __shfl_sync(0xffffffffu, rw, 31);
+    return rw;
+  }
+};
+
+// Coarse entries of one level (sort path): every entry (u, v, w) becomes the
+// key cid(L(u)) * nc + cid(L(v)) with weight w; equal keys of a 32-entry
+// chunk are summed before they are written.
 template <typename W>
 __global__ void __launch_bounds__(256) emit_coarse(int64_t n, int64_t m, const int64_t* __restrict__ rp,
                                                    const int32_t* __restrict__ col, const W* __restrict__ w,
@@ -769,40 +855,12 @@ __global__ void __launch_bounds__(256) emit_coarse(int64_t n, int64_t m, const i
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t sg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sg < nseg; sg += nw) {
     const int64_t E0 = sg * kSegEntries, E1 = E0 + kSegEntries < m ? E0 + kSegEntries : m;
-    int64_t r = 0;
-    if (lane == 0) {  // last row whose start is <= E0
-      int64_t lo = 0, hi = n - 1;
-      while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) >> 1;
-        if (rp[mid] <= E0) lo = mid; else hi = mid - 1;
-      }
-      r = lo;
-    }
-    r = __shfl_sync(0xffffffffu, r, 0);
+    RowWalk rw;
+    rw.start(rp, n, E0);
     for (int64_t c0 = E0; c0 < E1; c0 += 32) {
       const int64_t e = c0 + lane;
       const bool valid = e < E1;
-      const int64_t bk = (r + 1 + lane <= n) ? rp[r + 1 + lane] : INT64_MAX;  // end of row r + lane
-      const int64_t last = __shfl_sync(0xffffffffu, bk, 31);
-      int64_t row;
-      if (last <= c0 + 31) {
-        // more than 31 rows end inside this chunk (empty rows): search per lane
-        int64_t lo = r, hi = n - 1, x = valid ? e : c0;
-        while (lo < hi) {
-          const int64_t mid = (lo + hi + 1) >> 1;
-          if (rp[mid] <= x) lo = mid; else hi = mid - 1;
-        }
-        row = lo;
-      } else {
-        int cntv = 0;
-        const int64_t x = valid ? e : c0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-          const int64_t v = __shfl_sync(0xffffffffu, bk, cntv + step - 1);
-          if (v <= x) cntv += step;
-        }
-        row = r + cntv;
-      }
+      const int64_t row = rw.row(rp, n, c0, valid);
       const int32_t cy = valid ? cid[L[col[e]]] : 0;
       const uint64_t cu = valid ? (uint64_t)cid[L[row]] : 0;
       const uint64_t key = valid ? cu * nc + (uint64_t)cy : ~0ull;
@@ -819,7 +877,6 @@ __global__ void __launch_bounds__(256) emit_coarse(int64_t n, int64_t m, const i
         keys[pos] = key;
         vals[pos] = (uint64_t)sum;
       }
-      r = __shfl_sync(0xffffffffu, row, 31);
     }
   }
 }
@@ -1057,8 +1114,11 @@ int launch_lm_st(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEvent_
       const int32_t* lst = lst0 + o;
       int32_t* pr = prop + o;
       switch (b.plan.var[x]) {
+        case kLmHalf:
+          count_launch(), lm_warp<W, ST, 16><<<grid_for(cnt * 16, T, 16), T, 0, s>>>(g, lst, cnt, pr);
+          break;
         case kLmWarp:
-          count_launch(), lm_warp<W, ST><<<grid_for(cnt * 32, T, 16), T, 0, s>>>(g, lst, cnt, pr);
+          count_launch(), lm_warp<W, ST, 32><<<grid_for(cnt * 32, T, 16), T, 0, s>>>(g, lst, cnt, pr);
           break;
         case kLmWarp128: DCD_TRY((launch_warp_tbl<W, ST, 256, 4>(c, g, lst, cnt, pr))); break;
         case kLmWarp256: DCD_TRY((launch_warp_tbl<W, ST, 512, 8>(c, g, lst, cnt, pr))); break;
@@ -1182,9 +1242,9 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
         out->verts_bin[k] += bins.cnt[x];
       }
       if (trace_on()) {
-        char buf[512];
+        char buf[1024];
         int o = 0;
-        for (int x = 0; x < bins.plan.nb && o < 400; x++)
+        for (int x = 0; x < bins.plan.nb && o < 900; x++)
           o += snprintf(buf + o, sizeof(buf) - o, " [<=%lld: %lld v %lld e %.3f ms]",
                         bins.plan.hi[x] == INT64_MAX ? -1LL : (long long)bins.plan.hi[x], (long long)bins.cnt[x],
                         (long long)bins.deg[x], tb[x]);

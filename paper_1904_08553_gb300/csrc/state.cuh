@@ -32,9 +32,9 @@ struct DevScalars {
   int64_t r_size;    // |R_t|
   uint32_t err;      // kErr* bits
   uint32_t pad1;
-  int64_t bcnt[8];   // active vertices in each degree bin
-  int64_t bdeg[8];   // sum of their degrees
-  int64_t bmax[8];   // largest degree in the bin
+  int64_t bcnt[12];  // active vertices in each degree bin
+  int64_t bdeg[12];  // sum of their degrees
+  int64_t bmax[12];  // largest degree in the bin
 };
 
 // Per-graph state of one update.  A context holds G graphs on disjoint vertex
@@ -61,7 +61,8 @@ __device__ __forceinline__ int graph_of(const int32_t* gid, int64_t v) { return 
 // Degree bins of the local-move kernels.  A bin holds the active vertices
 // whose degree lies in (hi of the previous bin, hi]; each bin runs one kernel
 // variant, which bounds the degree it accepts:
-//   kLmWarp      1..32     one warp a vertex, lanes hold the row (no table)
+//   kLmHalf      1..16     half a warp a vertex, lanes hold the row (no table)
+//   kLmWarp      ..32      one warp a vertex, lanes hold the row (no table)
 //   kLmWarp128   ..128     one warp a vertex, warp-private shared table of 256
 //   kLmWarp256   ..256     one warp a vertex, warp-private shared table of 512
 //   kLmBlk512    ..512     one CTA a vertex, shared table (256 threads)
@@ -69,9 +70,10 @@ __device__ __forceinline__ int graph_of(const int32_t* gid, int64_t v) { return 
 //   kLmBlk2k     ..2048    one CTA a vertex, shared table (256 threads)
 //   kLmBlk4k     ..4096    one CTA a vertex, shared table (512 threads)
 //   kLmHub       any       one CTA a vertex, table in global memory
-constexpr int kMaxBins = 8;
+constexpr int kMaxBins = 12;
 enum LmVariant : int32_t {
-  kLmWarp = 0,
+  kLmHalf = 0,
+  kLmWarp,
   kLmWarp128,
   kLmWarp256,
   kLmBlk512,
@@ -82,13 +84,15 @@ enum LmVariant : int32_t {
   kLmVariants
 };
 __host__ __device__ __forceinline__ int64_t lm_variant_max(int v) {
-  return v == kLmWarp ? 32 : v == kLmWarp128 ? 128 : v == kLmWarp256 ? 256 : v == kLmBlk512 ? 512
+  return v == kLmHalf ? 16 : v == kLmWarp ? 32 : v == kLmWarp128 ? 128 : v == kLmWarp256 ? 256 : v == kLmBlk512 ? 512
        : v == kLmBlk1k ? 1024 : v == kLmBlk2k ? 2048 : v == kLmBlk4k ? 4096 : INT64_MAX;
 }
 // The four classes the step statistics report (warp, warp + table, CTA, hub).
 __host__ __device__ __forceinline__ int lm_variant_class(int v) {
-  return v == kLmWarp ? 0 : v <= kLmWarp256 ? 1 : v <= kLmBlk4k ? 2 : 3;
+  return v <= kLmWarp ? 0 : v <= kLmWarp256 ? 1 : v <= kLmBlk4k ? 2 : 3;
 }
+
+static_assert(sizeof(DevScalars::bcnt) == kMaxBins * sizeof(int64_t), "one counter a bin");
 
 struct BinPlan {
   int32_t nb = 0;
@@ -102,13 +106,16 @@ __host__ __device__ __forceinline__ int bin_of(const BinPlan& p, int64_t deg) {
   return b;
 }
 
-// Every variant in degree order, each bin as wide as its kernel allows.
+// Every variant from kLmWarp on in degree order, each bin as wide as its
+// kernel allows (the half-warp variant measured no faster than a warp per
+// vertex on rows of up to 16 entries).
 inline BinPlan default_bin_plan() {
   BinPlan p;
-  p.nb = kLmVariants;
-  for (int v = 0; v < kLmVariants; v++) {
-    p.var[v] = v;
-    p.hi[v] = lm_variant_max(v);
+  p.nb = 0;
+  for (int v = kLmWarp; v < kLmVariants; v++) {
+    p.var[p.nb] = v;
+    p.hi[p.nb] = lm_variant_max(v);
+    p.nb++;
   }
   return p;
 }
