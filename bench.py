@@ -208,7 +208,7 @@ def gpu_arm(args):
         __graft_entry__.build()
     if world > 1:
         dist.barrier()
-    from paper_1904_08553_gb300 import dcd
+    from paper_1904_08553_gb300 import dcd, shard
 
     T = 1 + args.warmup + args.steps
     stream = make_stream(args.n, T, replica=rank)
@@ -250,11 +250,7 @@ def gpu_arm(args):
         e1.record(ts)
         torch.cuda.synchronize()
     launches = dcd.dcd_kernel_launches() - launches0
-    total_ms = e0.elapsed_time(e1)
-    if world > 1:
-        x = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(x, op=dist.ReduceOp.MAX)
-        total_ms = float(x.item())
+    total_ms = shard.max_over_ranks(e0.elapsed_time(e1), device=dev)
     clocks = clk.summary()
     nnz_by_step = {1 + args.warmup + i + 1: st.nnz for i, st in enumerate(stats)}
     ctx.close()
@@ -279,7 +275,7 @@ def gpu_arm(args):
             run(ctx, t, host=True, lab_host=lab_host)
             h2d += pinned[t][0].nbytes + len(pinned[t][1]) * 12
         torch.cuda.synchronize()
-        e2e_ms = (time.perf_counter() - a) * 1e3 / args.steps
+        e2e_ms = shard.max_over_ranks((time.perf_counter() - a) * 1e3 / args.steps, device=dev)
         ctx.close()
         e2e = {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(h2d / args.steps),
                "d2h_bytes_per_step": int(n * 4)}
@@ -300,7 +296,7 @@ def gpu_arm(args):
     lm_bytes = BYTES_PER_ENTRY * edges + BYTES_PER_VERTEX * verts
     pass_gbs = lm_bytes / (lm_ms * 1e-3) / 1e9 if lm_ms > 0 else None
     # per degree-bin kernel: time, algorithmic bytes, achieved GB/s
-    names = ["lm_warp (degree <= 32)", "lm_warp_tbl (33..256)", "lm_block (257..4096)", "lm_block hub (> 4096)"]
+    names = ["lm_warp (degree <= 32)", "lm_warp_tbl (33..256)", "lm_large (257..4096)", "lm_block hub (> 4096)"]
     bins = []
     for b in range(4):
         ms_b = sum(st.ms_bin[b] for st in stats)
@@ -454,17 +450,32 @@ def batched_arm(args):
     """512 independent temporal SBMs (n log-uniform in 500..200,000, blocks of
     20..2,000, mean degree 8..32, 3 % inserts and 1 % deletes per step) advanced
     together by one group update per step, against the same graphs updated one
-    context at a time (both on the GPU, Delta-screening mode)."""
+    context at a time (both on the GPU, Delta-screening mode).  Under torchrun
+    every rank takes its share of the graphs (no data crosses ranks); the
+    job's time per step is the slowest rank's."""
     import torch
+    import torch.distributed as dist
 
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
     import __graft_entry__
 
-    __graft_entry__.build()
-    from paper_1904_08553_gb300 import dcd, synth
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1904_08553_gb300 import dcd, shard, synth
 
-    torch.cuda.set_device(0)
+    params = synth.batched_params(synth.seed_for(3, 0), args.graphs)
+    cost = [int(n * deg) for n, deg, _ in params]
+    mine = shard.partition_graphs(cost, world)[rank]
     t0 = time.time()
-    streams = synth.batched_sbm(G=args.graphs, steps=7)
+    streams = synth.batched_sbm(G=args.graphs, steps=7, graphs=set(mine))
     gen_s = time.time() - t0
     sizes = [s.n for s in streams]
     T = len(streams[0].steps)
@@ -474,11 +485,14 @@ def batched_arm(args):
         for g, s in enumerate(streams):
             grp.apply_batch(g, *s.steps[t])
         torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
         a = time.perf_counter()
         _, q, st = grp.update(labels_out=None)
         torch.cuda.synchronize()
+        ms = shard.max_over_ranks((time.perf_counter() - a) * 1e3, device=dev)
         if t >= 1:
-            group_ms.append((time.perf_counter() - a) * 1e3)
+            group_ms.append(ms)
     launches_group = st[0].launches
     q_group = q.copy()
     grp.close()
@@ -500,16 +514,26 @@ def batched_arm(args):
             if t == T - 1:
                 launches_seq += stg.launches
         ctx.close()
+    seq_mean = shard.max_over_ranks(float(np.mean(seq_ms)), device=dev)
+    same = shard.sum_over_ranks(float(not np.array_equal(q_group, q_seq)), device=dev) == 0
+    n_all = int(shard.sum_over_ranks(float(sum(sizes)), device=dev))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return
     line = {
         "metric": "batched form: ms per time step for all graphs (group update vs one context per graph)",
-        "workload": (f"{len(sizes)} temporal SBMs, n log-uniform 500..200,000 (total {sum(sizes):,} vertices), "
+        "workload": (f"{args.graphs} temporal SBMs, n log-uniform 500..200,000 (total {n_all:,} vertices), "
                      f"initial load + {T - 1} steps of 3% inserts / 1% deletes"),
-        "ms_per_step_group": float(np.mean(group_ms)), "ms_per_step_one_at_a_time": float(np.mean(seq_ms)),
-        "speedup": float(np.mean(seq_ms) / np.mean(group_ms)),
+        "n_gpus": world, "scaling": "strong" if world > 1 else None,
+        "ms_per_step_group": float(np.mean(group_ms)), "ms_per_step_one_at_a_time": seq_mean,
+        "speedup": float(seq_mean / np.mean(group_ms)),
         "kernel_launches_per_step": {"group": int(launches_group), "one_at_a_time": int(launches_seq)},
-        "identical_modularity": bool(np.array_equal(q_group, q_seq)), "generation_s": gen_s,
+        "identical_modularity": bool(same), "generation_s": gen_s,
     }
     print(json.dumps(line), flush=True)
+
 
 def main():
     ap = argparse.ArgumentParser()

@@ -174,11 +174,15 @@ def batched_params(seed: int, G: int = 512, nmin: float = 500, nmax: float = 200
 
 
 def batched_sbm(replica: int = 0, G: int = 512, steps: int = 7, nmax: float = 200_000,
-                intra_frac: float = 0.8) -> list:
-    """Independent temporal SBMs of uneven sizes (initial load + steps-1 updates)."""
+                intra_frac: float = 0.8, graphs=None) -> list:
+    """Independent temporal SBMs of uneven sizes (initial load + steps-1 updates).
+    ``graphs`` (indices into the G graphs) generates a subset; graph g is the
+    same whichever subset it is generated in."""
     params = batched_params(seed_for(3, replica), G, nmax=nmax)
     streams = []
     for g, (n, deg, sizes) in enumerate(params):
+        if graphs is not None and g not in graphs:
+            continue
         m = int(round(n * deg / 2))
         m_intra = int(round(intra_frac * m))
         streams.append(sbm(seed_for(3, replica) * 7919 + g, sizes, m_intra, m - m_intra, steps,
