@@ -234,6 +234,8 @@ def gpu_arm(args):
     # ---- device-resident inputs ----
     ctx = dcd.Context(n, mode=dcd.MODE_DELTA, stream=ts)
     run(ctx, 0)
+    ctx.autotune(reps=3)  # degree-bin plan for this graph (untimed)
+    plan = ctx.bins()
     for t in range(1, 1 + args.warmup):
         run(ctx, t)
     if world > 1:
@@ -265,6 +267,7 @@ def gpu_arm(args):
             pinned.append((pi, pd))
         lab_host = torch.empty(n, dtype=torch.int32).pin_memory().numpy()
         ctx = dcd.Context(n, mode=dcd.MODE_DELTA, stream=ts)
+        ctx.set_bins(*plan)
         run(ctx, 0, host=True, lab_host=lab_host)
         for t in range(1, 1 + args.warmup):
             run(ctx, t, host=True, lab_host=lab_host)
@@ -312,7 +315,8 @@ def gpu_arm(args):
         "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded LFR-style generator)",
         "config": {"workload": workload_desc(T), "mode": "delta", "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": "inputs larger than L2 (G_t holds ~100M directed entries, ~0.8 GB)",
-                   "timed_steps": f"t={2 + args.warmup}..{T}"},
+                   "timed_steps": f"t={2 + args.warmup}..{T}",
+                   "bin_plan": {"variants": plan[0], "max_degree": plan[1]}},
         "local_move_gteps": gteps,
         "steps_detail": {
             "r_fraction": float(np.mean([s.r_size / s.n for s in stats])),
@@ -493,6 +497,9 @@ def batched_arm(args):
         ms = shard.max_over_ranks((time.perf_counter() - a) * 1e3, device=dev)
         if t >= 1:
             group_ms.append(ms)
+        else:
+            grp.autotune(reps=3)  # degree-bin plan of the union graph (untimed)
+    plan = grp.bins()
     launches_group = st[0].launches
     q_group = q.copy()
     grp.close()
@@ -531,6 +538,7 @@ def batched_arm(args):
         "speedup": float(seq_mean / np.mean(group_ms)),
         "kernel_launches_per_step": {"group": int(launches_group), "one_at_a_time": int(launches_seq)},
         "identical_modularity": bool(same), "generation_s": gen_s,
+        "bin_plan": {"variants": plan[0], "max_degree": plan[1]},
     }
     print(json.dumps(line), flush=True)
 

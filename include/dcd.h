@@ -161,6 +161,35 @@ int dcd_set_rset(dcd_ctx* ctx, const uint8_t* r);
 /* Change the mode for the following updates (DCD_MODE_*). */
 int dcd_set_mode(dcd_ctx* ctx, int32_t mode);
 
+/* ---- degree bins of the local-move kernels (no counterpart in the paper) ----
+ * The local-move evaluation (Algorithm 1, the loop over vertices) splits the
+ * active vertices into bins by degree (CSR entries of the row); each bin runs
+ * one kernel variant DCD_LM_*, which accepts rows up to its limit.  A plan is
+ * nb bins in increasing degree: bin b holds the degrees in (hi[b-1], hi[b]];
+ * the last bin has hi = -1 (no limit) and variant DCD_LM_HUB.  Every plan
+ * gives the same labels and modularity; only the time differs.
+ * dcd_set_bins: errors DCD_EINVAL (nb outside 1..DCD_MAX_BINS, unknown
+ * variant, hi not increasing or above the variant's limit, last bin not an
+ * unbounded DCD_LM_HUB).  dcd_get_bins: *nb, and nb entries of variant / hi
+ * (host, each may be NULL).  dcd_autotune: times one local-move evaluation of
+ * every vertex of G_t under C_t (no move applied), reps times for each
+ * candidate plan, and keeps the fastest; *best_ms (host, may be NULL)
+ * receives its time per evaluation.  Errors: DCD_ESTATE before the first
+ * update or for reps < 1, DCD_ENOMEM, DCD_ECUDA. */
+#define DCD_MAX_BINS 12
+#define DCD_LM_HALF 0    /* <= 16 entries: half a warp per vertex, no table        */
+#define DCD_LM_WARP 1    /* <= 32: a warp per vertex, no table                     */
+#define DCD_LM_WARP128 2 /* <= 128: a warp per vertex, warp-private shared table   */
+#define DCD_LM_WARP256 3 /* <= 256: a warp per vertex, warp-private shared table   */
+#define DCD_LM_BLK512 4  /* <= 512: a CTA per vertex, shared table                  */
+#define DCD_LM_BLK1K 5   /* <= 1024: a CTA per vertex, shared table                 */
+#define DCD_LM_BLK2K 6   /* <= 2048: a CTA per vertex, shared table                 */
+#define DCD_LM_BLK4K 7   /* <= 4096: a CTA per vertex, shared table                 */
+#define DCD_LM_HUB 8     /* any degree: a CTA per vertex, table in global memory   */
+int dcd_set_bins(dcd_ctx* ctx, int32_t nb, const int32_t* variant, const int64_t* hi);
+int dcd_get_bins(const dcd_ctx* ctx, int32_t* nb, int32_t* variant, int64_t* hi);
+int dcd_autotune(dcd_ctx* ctx, int32_t reps, float* best_ms);
+
 /* The CSR of G_t: *nnz_out receives the entry count; when row_ptr/col/w are
  * non-NULL they receive n+1 int64, nnz int32 and nnz int32 (host memory). */
 int dcd_get_graph(dcd_ctx* ctx, int64_t* nnz_out, int64_t* row_ptr, int32_t* col, int32_t* w);
@@ -169,7 +198,7 @@ int dcd_get_graph(dcd_ctx* ctx, int64_t* nnz_out, int64_t* row_ptr, int32_t* col
  * contexts, all devices): lets a caller count the device work of a region. */
 int64_t dcd_kernel_launches(void);
 
-/* ---- learned screen: the network (BASELINE north star, pattern "learned parts") ----
+/* ---- learned screen: the network ----
  * A multilayer perceptron 12 -> 64 -> 64 -> 1 (ReLU, ReLU, sigmoid) that
  * scores a vertex's chance of changing community at level 0.  Not in the
  * paper: it widens or prunes the Delta-screening set R_t (DCD_MODE_LEARNED).
@@ -241,6 +270,11 @@ int dcd_group_destroy(dcd_group* grp);
 int dcd_group_apply_batch(dcd_group* grp, int32_t g, const dcd_edge* ins, int64_t n_ins, const dcd_edge* del,
                           int64_t n_del);
 int dcd_group_update(dcd_group* grp, int32_t* labels_out, double* q_out, dcd_step_stats* stats_out);
+/* The degree bins of the group's local-move kernels, as dcd_set_bins /
+ * dcd_get_bins / dcd_autotune for a context (the union of the G graphs). */
+int dcd_group_set_bins(dcd_group* grp, int32_t nb, const int32_t* variant, const int64_t* hi);
+int dcd_group_get_bins(const dcd_group* grp, int32_t* nb, int32_t* variant, int64_t* hi);
+int dcd_group_autotune(dcd_group* grp, int32_t reps, float* best_ms);
 
 /* ---- allocation-free evaluation ----
  * No counterpart in the paper: a service for callers that cannot allocate

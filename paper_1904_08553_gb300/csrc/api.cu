@@ -346,7 +346,55 @@ int dcd_apply_batch_device(dcd_ctx* c, const dcd_edge* ins, int64_t n_ins, const
 
 namespace dcd {
 int update_impl(dcd_ctx* c, dcd_step_stats* st, dcd_step_stats* per_graph);
+
+// Candidate bin plans of the autotuner: the default (every variant from a warp
+// per vertex on), with the half-warp variant in front, and coarser layouts
+// that drop variants (fewer launches, larger tables).
+static std::vector<BinPlan> candidate_plans() {
+  const int32_t lists[][kMaxBins] = {
+      {kLmWarp, kLmWarp128, kLmWarp256, kLmBlk512, kLmBlk1k, kLmBlk2k, kLmBlk4k, kLmHub},
+      {kLmHalf, kLmWarp, kLmWarp128, kLmWarp256, kLmBlk512, kLmBlk1k, kLmBlk2k, kLmBlk4k, kLmHub},
+      {kLmWarp, kLmWarp256, kLmBlk512, kLmBlk1k, kLmBlk2k, kLmBlk4k, kLmHub},
+      {kLmWarp, kLmWarp128, kLmWarp256, kLmBlk1k, kLmBlk4k, kLmHub},
+      {kLmWarp, kLmWarp128, kLmWarp256, kLmBlk512, kLmBlk1k, kLmBlk2k, kLmHub},
+      {kLmWarp, kLmWarp256, kLmBlk4k, kLmHub},
+      {kLmWarp, kLmWarp128, kLmWarp256, kLmHub},
+  };
+  const int lens[] = {8, 9, 7, 6, 7, 4, 4};
+  std::vector<BinPlan> out;
+  for (int x = 0; x < (int)(sizeof(lens) / sizeof(lens[0])); x++) {
+    BinPlan p;
+    p.nb = lens[x];
+    for (int b = 0; b < p.nb; b++) {
+      p.var[b] = lists[x][b];
+      p.hi[b] = b == p.nb - 1 ? INT64_MAX : lm_variant_max(lists[x][b]);
+    }
+    out.push_back(p);
+  }
+  return out;
 }
+
+// Times one local-move evaluation of every vertex of the current graph under
+// the current labels for each candidate plan and keeps the fastest.  Every
+// plan gives the same proposals; only the time differs.
+int autotune_impl(dcd_ctx* c, int32_t reps, float* best_ms) {
+  if (c->t == 0 || reps < 1) return DCD_ESTATE;
+  const std::vector<BinPlan> cands = candidate_plans();
+  std::vector<float> ms(cands.size(), 0.f);
+  int best = -1;
+  DCD_TRY(c->mem.begin_step((size_t)(32 * c->n) + ((size_t)64 << 20)));
+  const int k = c->cur;
+  const Csr<int32_t> g{c->n, c->nnz, c->rp[k].get(), c->col[k].get(), c->w[k].get()};
+  const int rc = tune_bins(c, g, c->labels.get(), cands.data(), (int)cands.size(), reps, ms.data(), &best);
+  c->mem.end_step();
+  if (rc) return rc;
+  if (trace_on())
+    for (size_t x = 0; x < cands.size(); x++)
+      tracef("autotune plan %d: %.3f ms%s", (int)x, ms[x], (int)x == best ? " *" : "");
+  if (best_ms) *best_ms = best >= 0 ? ms[best] : 0.f;
+  return DCD_OK;
+}
+}  // namespace dcd
 
 int dcd::update_impl(dcd_ctx* c, dcd_step_stats* st, dcd_step_stats* per_graph) {
   cudaStream_t s = c->stream;
@@ -573,6 +621,46 @@ int dcd_set_mode(dcd_ctx* c, int32_t mode) {
   if (!c || mode < DCD_MODE_STATIC || mode > DCD_MODE_LEARNED) return DCD_EINVAL;
   c->mode = mode;
   return DCD_OK;
+}
+
+static_assert(DCD_MAX_BINS == kMaxBins && DCD_LM_HALF == kLmHalf && DCD_LM_WARP == kLmWarp &&
+                  DCD_LM_WARP128 == kLmWarp128 && DCD_LM_WARP256 == kLmWarp256 && DCD_LM_BLK512 == kLmBlk512 &&
+                  DCD_LM_BLK1K == kLmBlk1k && DCD_LM_BLK2K == kLmBlk2k && DCD_LM_BLK4K == kLmBlk4k &&
+                  DCD_LM_HUB == kLmHub,
+              "header constants name the kernel variants");
+
+int dcd_set_bins(dcd_ctx* c, int32_t nb, const int32_t* variant, const int64_t* hi) {
+  if (!c || nb < 1 || nb > kMaxBins || !variant || !hi) return DCD_EINVAL;
+  BinPlan p;
+  p.nb = nb;
+  for (int b = 0; b < nb; b++) {
+    const bool last = b == nb - 1;
+    const int64_t h = last ? INT64_MAX : hi[b];
+    if (variant[b] < 0 || variant[b] >= kLmVariants) return DCD_EINVAL;
+    if (last ? (hi[b] != -1 || variant[b] != kLmHub) : (h < 1 || h > lm_variant_max(variant[b])))
+      return DCD_EINVAL;
+    if (b > 0 && h <= p.hi[b - 1]) return DCD_EINVAL;
+    p.var[b] = variant[b];
+    p.hi[b] = h;
+  }
+  c->bin_plan = p;
+  return DCD_OK;
+}
+
+int dcd_get_bins(const dcd_ctx* c, int32_t* nb, int32_t* variant, int64_t* hi) {
+  if (!c || !nb) return DCD_EINVAL;
+  *nb = c->bin_plan.nb;
+  for (int b = 0; b < c->bin_plan.nb; b++) {
+    if (variant) variant[b] = c->bin_plan.var[b];
+    if (hi) hi[b] = c->bin_plan.hi[b] == INT64_MAX ? -1 : c->bin_plan.hi[b];
+  }
+  return DCD_OK;
+}
+
+int dcd_autotune(dcd_ctx* c, int32_t reps, float* best_ms) {
+  if (!c) return DCD_EINVAL;
+  DCD_SCOPE(c);
+  return autotune_impl(c, reps, best_ms);
 }
 
 int dcd_set_screen(dcd_ctx* c, dcd_mlp* mlp, float theta_keep, float theta_add, int32_t judge) {

@@ -51,6 +51,7 @@ __global__ void per_graph_counts(int G, const int64_t* __restrict__ off, const i
 }  // namespace
 
 int update_impl(dcd_ctx* c, dcd_step_stats* st, dcd_step_stats* per_graph);
+int autotune_impl(dcd_ctx* c, int32_t reps, float* best_ms);
 
 }  // namespace dcd
 
@@ -133,6 +134,20 @@ int dcd_group_apply_batch(dcd_group* grp, int32_t g, const dcd_edge* ins, int64_
     grp->ins.push_back(dcd_edge{(int32_t)(ins[i].u + o), (int32_t)(ins[i].v + o), ins[i].w});
   for (int64_t i = 0; i < n_del; i++) grp->del.push_back(dcd_edge{(int32_t)(del[i].u + o), (int32_t)(del[i].v + o), 0});
   return DCD_OK;
+}
+
+int dcd_group_autotune(dcd_group* grp, int32_t reps, float* best_ms) {
+  if (!grp) return DCD_EINVAL;
+  DCD_TRY_CUDA(cudaSetDevice(grp->ctx->device));
+  return autotune_impl(grp->ctx, reps, best_ms);
+}
+
+int dcd_group_set_bins(dcd_group* grp, int32_t nb, const int32_t* variant, const int64_t* hi) {
+  return grp ? dcd_set_bins(grp->ctx, nb, variant, hi) : DCD_EINVAL;
+}
+
+int dcd_group_get_bins(const dcd_group* grp, int32_t* nb, int32_t* variant, int64_t* hi) {
+  return grp ? dcd_get_bins(grp->ctx, nb, variant, hi) : DCD_EINVAL;
 }
 
 int dcd_group_update(dcd_group* grp, int32_t* labels_out, double* q_out, dcd_step_stats* stats_out) {

@@ -1392,6 +1392,64 @@ int pool_stats(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* L, const int64_
   return DCD_OK;
 }
 
+namespace {
+__global__ void row_sums(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ w,
+                         int64_t* __restrict__ k) {
+  const int lane = lane_id();
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; v < n; v += nw) {
+    int64_t x = 0;
+    for (int64_t e = rp[v] + lane; e < rp[v + 1]; e += 32) x += w[e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) k[v] = x;
+  }
+}
+}  // namespace
+
+int tune_bins(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* L, const BinPlan* cands, int ncand, int reps,
+              float* ms, int* best) {
+  cudaStream_t s = c->stream;
+  const int T = 256;
+  const int64_t n = g.n;
+  const int G = c->G;
+  Buf<int64_t> k, a;
+  Buf<int32_t> size, prop;
+  DCD_TRY(k.alloc(&c->mem, n));
+  DCD_TRY(a.alloc(&c->mem, n));
+  DCD_TRY(size.alloc(&c->mem, n));
+  DCD_TRY(prop.alloc(&c->mem, n));
+  ::dcd::count_launch(), row_sums<<<grid_for(n * 32, T), T, 0, s>>>(n, g.rp, g.w, k.get());
+  DCD_LAUNCH_CHECK();
+  DCD_TRY(community_sums(c, n, L, k.get(), a.get(), size.get()));
+  int64_t m2max = 0;
+  for (int x = 0; x < G; x++) m2max = c->hgs[x].m2 > m2max ? c->hgs[x].m2 : m2max;
+  LV<int32_t> lv{g.rp, g.col, g.w, k.get(), L, a.get(), size.get(), m2max};
+  if (G > 1) {
+    lv.gid = c->gid.get();
+    lv.gs = c->gs.get();
+  }
+  const BinPlan keep = c->bin_plan;
+  *best = -1;
+  for (int x = 0; x < ncand; x++) {
+    c->bin_plan = cands[x];
+    Bins bins;
+    DCD_TRY(make_bins<int32_t>(c, g, nullptr, &bins));
+    if (bins.total) DCD_TRY(launch_lm<int32_t>(c, lv, bins, prop.get()));  // warm-up
+    DCD_TRY_CUDA(cudaEventRecord(c->ev[20], s));
+    for (int r = 0; r < reps; r++)
+      if (bins.total) DCD_TRY(launch_lm<int32_t>(c, lv, bins, prop.get()));
+    DCD_TRY_CUDA(cudaEventRecord(c->ev[21], s));
+    DCD_TRY_CUDA(cudaEventSynchronize(c->ev[21]));
+    float t = 0.f;
+    DCD_TRY_CUDA(cudaEventElapsedTime(&t, c->ev[20], c->ev[21]));
+    ms[x] = t / (reps > 0 ? reps : 1);
+    if (*best < 0 || ms[x] < ms[*best]) *best = x;
+  }
+  c->bin_plan = *best >= 0 ? cands[*best] : keep;
+  return DCD_OK;
+}
+
 int community_sums(dcd_ctx* c, int64_t n, const int32_t* labels, const int64_t* k, int64_t* a, int32_t* size) {
   cudaStream_t s = c->stream;
   DCD_TRY_CUDA(cudaMemsetAsync(a, 0, n * sizeof(int64_t), s));

@@ -244,6 +244,12 @@ int screen_labels(dcd_ctx* c, const int32_t* before, const int32_t* after);
 // mlp.cu: forward pass of the network on a given stream (no synchronisation).
 int mlp_forward_on(struct dcd_mlp* m, const float* X, int64_t n, float* p, cudaStream_t s);
 
+// louvain.cu: one local-move evaluation of every vertex of g under labels L
+// (no move applied) timed for each candidate bin plan; the fastest becomes the
+// context's plan.  ms[x] receives candidate x's time per evaluation.
+int tune_bins(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* L, const BinPlan* cands, int ncand, int reps,
+              float* ms, int* best);
+
 // louvain.cu: community sums a (by label) and sizes from k and labels.
 int community_sums(dcd_ctx* c, int64_t n, const int32_t* labels, const int64_t* k, int64_t* a,
                    int32_t* size);

@@ -29,7 +29,12 @@ EXPORTED = [
     "dcd_mlp_get_params", "dcd_mlp_forward", "dcd_mlp_grad", "dcd_mlp_train",
     "dcd_set_screen", "dcd_set_collect", "dcd_get_screen_data",
     "dcd_group_create", "dcd_group_destroy", "dcd_group_apply_batch", "dcd_group_update",
+    "dcd_set_bins", "dcd_get_bins", "dcd_autotune", "dcd_group_set_bins", "dcd_group_get_bins",
+    "dcd_group_autotune",
 ]
+MAX_BINS = 12
+LM_HALF, LM_WARP, LM_WARP128, LM_WARP256, LM_BLK512, LM_BLK1K, LM_BLK2K, LM_BLK4K, LM_HUB = range(9)
+LM_LIMIT = [16, 32, 128, 256, 512, 1024, 2048, 4096, -1]
 MLP_FEATURES, MLP_HIDDEN, MLP_PARAMS = 12, 64, 5057
 NOALLOC_MAX_N = 1048056
 
@@ -125,6 +130,12 @@ def lib():
             "dcd_group_destroy": (INT, [P]),
             "dcd_group_apply_batch": (INT, [P, I32, P, I64, P, I64]),
             "dcd_group_update": (INT, [P, P, P, P]),
+            "dcd_set_bins": (INT, [P, I32, P, P]),
+            "dcd_get_bins": (INT, [P, P, P, P]),
+            "dcd_autotune": (INT, [P, I32, P]),
+            "dcd_group_set_bins": (INT, [P, I32, P, P]),
+            "dcd_group_get_bins": (INT, [P, P, P, P]),
+            "dcd_group_autotune": (INT, [P, I32, P]),
             "dcd_strerror": (ctypes.c_char_p, [INT]),
             "dcd_last_cuda_error": (ctypes.c_char_p, []),
         }
@@ -279,7 +290,71 @@ def _stream_ptr(stream):
     return getattr(stream, "cuda_stream", None)
 
 
-class Context:
+def _set_bins(fn, h, variants, his):
+    v = np.ascontiguousarray(variants, dtype=np.int32)
+    hi = np.ascontiguousarray(his, dtype=np.int64)
+    if v.shape != hi.shape or v.ndim != 1:
+        raise ValueError("variants and his must be 1-D of the same length")
+    _check(fn(h, len(v), v.ctypes.data, hi.ctypes.data), "set_bins")
+
+
+def _get_bins(fn, h):
+    nb = ctypes.c_int32(0)
+    v = np.zeros(MAX_BINS, np.int32)
+    hi = np.zeros(MAX_BINS, np.int64)
+    _check(fn(h, ctypes.byref(nb), v.ctypes.data, hi.ctypes.data), "get_bins")
+    return v[:nb.value].tolist(), hi[:nb.value].tolist()
+
+
+def _autotune(fn, h, reps):
+    ms = ctypes.c_float(0.0)
+    _check(fn(h, int(reps), ctypes.byref(ms)), "autotune")
+    return ms.value
+
+
+def dcd_set_bins(h, variants, his) -> None:
+    _set_bins(lib().dcd_set_bins, h, variants, his)
+
+
+def dcd_get_bins(h):
+    return _get_bins(lib().dcd_get_bins, h)
+
+
+def dcd_autotune(h, reps: int = 3) -> float:
+    return _autotune(lib().dcd_autotune, h, reps)
+
+
+def dcd_group_set_bins(h, variants, his) -> None:
+    _set_bins(lib().dcd_group_set_bins, h, variants, his)
+
+
+def dcd_group_get_bins(h):
+    return _get_bins(lib().dcd_group_get_bins, h)
+
+
+def dcd_group_autotune(h, reps: int = 3) -> float:
+    return _autotune(lib().dcd_group_autotune, h, reps)
+
+
+class _Bins:
+    """Degree bins of the local-move kernels (dcd_set_bins / dcd_get_bins /
+    dcd_autotune, or their group forms)."""
+
+    _prefix = "dcd_"
+
+    def set_bins(self, variants, his):
+        _set_bins(getattr(lib(), self._prefix + "set_bins"), self._h, variants, his)
+
+    def bins(self):
+        return _get_bins(getattr(lib(), self._prefix + "get_bins"), self._h)
+
+    def autotune(self, reps: int = 3) -> float:
+        """Time each candidate bin plan on the current graph and keep the fastest;
+        returns its time (ms) per local-move evaluation."""
+        return _autotune(getattr(lib(), self._prefix + "autotune"), self._h, reps)
+
+
+class Context(_Bins):
     """One dynamic graph on vertices [0, n) (dcd_ctx)."""
 
     def __init__(self, n: int, mode: int = MODE_DELTA, stream=None, max_iters: int = 500,
@@ -462,7 +537,7 @@ def dcd_group_update(h, G: int, labels_out=None):
     return q, list(st)
 
 
-class Group:
+class Group(_Bins):
     """Many independent dynamic graphs advanced together (dcd_group)."""
 
     def __init__(self, sizes, mode: int = MODE_DELTA, stream=None):
@@ -471,6 +546,7 @@ class Group:
         self.sizes = np.asarray(sizes, dtype=np.int64)
         self.G = len(self.sizes)
         self.offsets = np.concatenate([[0], np.cumsum(self.sizes)])
+        self._prefix = "dcd_group_"
         self._h = dcd_group_create(self.sizes, cfg, stream)
 
     def close(self):
