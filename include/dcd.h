@@ -108,7 +108,10 @@ void dcd_config_default(dcd_config* cfg);
 
 /* Create a dynamic graph on vertices [0, n) with no edges (Sec. III-A:
  * G(V, E) as a sequence G_1..G_T).  cfg may be NULL (defaults);
- * cuda_stream is a cudaStream_t or NULL.  *out receives the context.
+ * cuda_stream is the cudaStream_t the context's work runs on; with NULL the
+ * context creates a stream of its own that is ordered with the legacy default
+ * stream (the local-move passes run as CUDA graphs, which the legacy stream
+ * cannot capture).  *out receives the context.
  * Errors: DCD_EINVAL (n <= 0 or n > 2^31 - 1, out NULL), DCD_ENOMEM, DCD_ECUDA. */
 int dcd_create(int64_t n, const dcd_config* cfg, void* cuda_stream, dcd_ctx** out);
 

@@ -222,6 +222,21 @@ int dcd_create(int64_t n, const dcd_config* cfg, void* cuda_stream, dcd_ctx** ou
       }
     }
     c->sms = num_sms();
+    if (!c->stream) {
+      // the local-move passes are replayed as CUDA graphs, which cannot be
+      // captured on the legacy default stream: use a stream of our own that
+      // is ordered with it (blocking), so device batches written there first
+      // are still seen
+      const cudaError_t es = cudaStreamCreate(&c->stream);
+      if (es != cudaSuccess) {
+        note_cuda_error(es, "cudaStreamCreate", __FILE__, __LINE__);
+        c->stream = nullptr;
+        rc = DCD_ECUDA;
+        break;
+      }
+      c->own_stream = true;
+      c->mem.stream = c->stream;
+    }
     cudaMemPoolProps props{};
     props.allocType = cudaMemAllocationTypePinned;
     props.location.type = cudaMemLocationTypeDevice;
@@ -300,6 +315,7 @@ int dcd_destroy(dcd_ctx* c) {
   delete[] c->goff;
   if (c->hscratch) cudaFreeHost(c->hscratch);
   if (c->mem.pool) cudaMemPoolDestroy(c->mem.pool);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return DCD_OK;
 }

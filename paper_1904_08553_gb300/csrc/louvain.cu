@@ -461,10 +461,11 @@ __global__ void __launch_bounds__(THREADS) lm_block(LV<W> g, const int32_t* __re
 __global__ void lm_apply(const int32_t* __restrict__ list, int64_t cnt, int64_t big_from,
                          const int32_t* __restrict__ prop, int32_t* __restrict__ L, const int64_t* __restrict__ k,
                          unsigned long long* __restrict__ a, int32_t* __restrict__ size, int32_t* __restrict__ Lprev,
-                         int32_t* __restrict__ mvit, int32_t iter, int32_t* __restrict__ moved,
-                         int32_t* __restrict__ moved_cnt, int32_t* __restrict__ moved_big,
-                         int32_t* __restrict__ moved_big_cnt, const int32_t* __restrict__ gid,
-                         GraphState* __restrict__ gs) {
+                         int32_t* __restrict__ mvit, const int32_t* __restrict__ pass_id,
+                         int32_t* __restrict__ moved, int32_t* __restrict__ moved_cnt,
+                         int32_t* __restrict__ moved_big, int32_t* __restrict__ moved_big_cnt,
+                         const int32_t* __restrict__ gid, GraphState* __restrict__ gs) {
+  const int32_t iter = *pass_id;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t base0 = (blockIdx.x * (int64_t)blockDim.x) & ~31ll;
   for (int64_t base = base0 + (threadIdx.x & ~31); base < cnt; base += stride) {
@@ -545,8 +546,9 @@ template <typename W>
 __global__ void __launch_bounds__(256) lm_delta_in(LV<W> g, const int32_t* __restrict__ moved,
                                                    const int32_t* __restrict__ moved_cnt,
                                                    const int32_t* __restrict__ Lprev, const int32_t* __restrict__ mvit,
-                                                   int32_t iter, GraphState* __restrict__ gs) {
+                                                   const int32_t* __restrict__ pass_id, GraphState* __restrict__ gs) {
   const int64_t cnt = *moved_cnt;
+  const int32_t iter = *pass_id;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < cnt; i += nw) {
     const int32_t x = moved[i];
@@ -560,9 +562,11 @@ template <typename W>
 __global__ void __launch_bounds__(256) lm_delta_in_block(LV<W> g, const int32_t* __restrict__ moved,
                                                          const int32_t* __restrict__ moved_cnt,
                                                          const int32_t* __restrict__ Lprev,
-                                                         const int32_t* __restrict__ mvit, int32_t iter,
+                                                         const int32_t* __restrict__ mvit,
+                                                         const int32_t* __restrict__ pass_id,
                                                          GraphState* __restrict__ gs) {
   const int64_t cnt = *moved_cnt;
+  const int32_t iter = *pass_id;
   for (int64_t i = blockIdx.x; i < cnt; i += gridDim.x) {
     const int32_t x = moved[i];
     const int64_t acc = (int64_t)warp_sum((long long)moved_row_delta(g, x, Lprev, mvit, iter, threadIdx.x, blockDim.x));
@@ -634,7 +638,8 @@ __device__ __forceinline__ void st128(int64_t* lo, i128 x) {
 }
 
 // Per-pass accumulators back to zero (one thread per graph).
-__global__ void gs_reset_pass(GraphState* __restrict__ gs, int G) {
+__global__ void gs_reset_pass(GraphState* __restrict__ gs, int G, int32_t* __restrict__ pass_id) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *pass_id += 1;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
     gs[g].in_delta = 0;
     gs[g].sq_lo = gs[g].sq_hi = 0;
@@ -1077,8 +1082,6 @@ template <typename W, typename ST, int CAP, int Q>
 int launch_warp_tbl(dcd_ctx* c, const LV<W>& g, const int32_t* lst, int64_t cnt, int32_t* prop) {
   constexpr int T = 256;
   constexpr size_t smem = (size_t)(T / 32) * warp_tbl_bytes<CAP>();
-  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_warp_tbl<W, ST, CAP, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
   count_launch(), lm_warp_tbl<W, ST, CAP, Q><<<grid_for(cnt * 32, T, 8), T, smem, c->stream>>>(g, lst, cnt, prop);
   return DCD_OK;
 }
@@ -1087,17 +1090,36 @@ template <typename W, typename ST, int THREADS, int Q>
 int launch_large(dcd_ctx* c, const LV<W>& g, const int32_t* lst, int64_t cnt, int64_t maxd, int32_t* prop) {
   const int32_t tcap = (int32_t)table_cap(maxd);
   const size_t smem = (size_t)tcap * 14;  // values, keys, claimed-slot list
-  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_large<W, ST, THREADS, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)((size_t)table_cap((int64_t)THREADS * Q) * 14)));
   const int64_t ctas = cnt < 16 * (int64_t)c->sms ? cnt : 16 * (int64_t)c->sms;
   count_launch(), lm_large<W, ST, THREADS, Q><<<(unsigned)ctas, THREADS, smem, c->stream>>>(g, lst, cnt, prop, tcap);
   return DCD_OK;
 }
 
-// One local-move evaluation of every binned vertex (proposals in prop[]);
-// bin_ev[x] is recorded after bin x.
+// Shared-memory limits of the table kernels (host calls, made before any
+// launch and outside stream capture).
 template <typename W, typename ST>
-int launch_lm_st(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEvent_t* bin_ev) {
+int prepare_lm_st() {
+  constexpr int T = 256;
+  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_warp_tbl<W, ST, 256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)((T / 32) * warp_tbl_bytes<256>())));
+  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_warp_tbl<W, ST, 512, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)((T / 32) * warp_tbl_bytes<512>())));
+  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_large<W, ST, 256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(table_cap(512) * 14)));
+  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_large<W, ST, 256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(table_cap(1024) * 14)));
+  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_large<W, ST, 256, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(table_cap(2048) * 14)));
+  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_large<W, ST, 512, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(table_cap(4096) * 14)));
+  return DCD_OK;
+}
+
+// One local-move evaluation of every binned vertex (proposals in prop[]);
+// bin_ev[x] is recorded after bin x (with ev_flags: external records inside
+// stream capture).
+template <typename W, typename ST>
+int launch_lm_st(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEvent_t* bin_ev, unsigned ev_flags) {
   cudaStream_t s = c->stream;
   const int T = 256;
   const int32_t* lst0 = b.list.get();
@@ -1133,15 +1155,29 @@ int launch_lm_st(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEvent_
       }
       DCD_LAUNCH_CHECK();
     }
-    if (bin_ev) DCD_TRY_CUDA(cudaEventRecord(bin_ev[x], s));
+    if (bin_ev) DCD_TRY_CUDA(cudaEventRecordWithFlags(bin_ev[x], s, ev_flags));
   }
   return DCD_OK;
 }
 
 template <typename W>
-int launch_lm(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEvent_t* bin_ev = nullptr) {
-  if (lv.m2 >= ((int64_t)1 << 31)) return launch_lm_st<W, i128>(c, lv, b, prop, bin_ev);
-  return launch_lm_st<W, long long>(c, lv, b, prop, bin_ev);
+int prepare_lm(const LV<W>& lv) {
+  if (lv.m2 >= ((int64_t)1 << 31)) return prepare_lm_st<W, i128>();
+  return prepare_lm_st<W, long long>();
+}
+
+template <typename W>
+int launch_lm(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEvent_t* bin_ev = nullptr,
+              unsigned ev_flags = 0) {
+  DCD_TRY(prepare_lm<W>(lv));
+  if (lv.m2 >= ((int64_t)1 << 31)) return launch_lm_st<W, i128>(c, lv, b, prop, bin_ev, ev_flags);
+  return launch_lm_st<W, long long>(c, lv, b, prop, bin_ev, ev_flags);
+}
+
+template <typename W>
+int launch_lm_nocfg(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEvent_t* bin_ev, unsigned ev_flags) {
+  if (lv.m2 >= ((int64_t)1 << 31)) return launch_lm_st<W, i128>(c, lv, b, prop, bin_ev, ev_flags);
+  return launch_lm_st<W, long long>(c, lv, b, prop, bin_ev, ev_flags);
 }
 
 // Per-graph counters of one update (host).
@@ -1195,37 +1231,71 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
   lvl.m2 = G == 1 ? lv.m2 : m2max;  // gain width chosen by the largest graph
   const int32_t* lst = bins.list.get();
   bool any = total > 0;
-  // a level with nothing to evaluate still runs one (empty) pass, as the
-  // sequential definition does
-  for (;;) {
-    const int32_t iter = (int32_t)out->passes;
-    ::dcd::count_launch(), gs_reset_pass<<<cdiv(G, 128), 128, 0, s>>>(gs, G);
+  // One pass: evaluate, apply, tracked N, stop rule, scalars to the host.
+  // Every pass of a level enqueues the same work (the pass number lives on
+  // the device), so the body is captured once into a CUDA graph and each pass
+  // is one graph launch.
+  auto enqueue_pass = [&](unsigned evf) -> int {
+    ::dcd::count_launch(), gs_reset_pass<<<cdiv(G, 128), 128, 0, s>>>(gs, G, &d->pass_id);
     DCD_TRY_CUDA(cudaMemsetAsync(moved_cnt.get(), 0, sizeof(int32_t), s));
     DCD_TRY_CUDA(cudaMemsetAsync(moved_big_cnt.get(), 0, sizeof(int32_t), s));
     DCD_TRY_CUDA(cudaMemsetAsync(&d->any_running, 0, sizeof(int32_t), s));
-    DCD_TRY_CUDA(cudaEventRecord(c->ev[2], s));
-    if (any) DCD_TRY(launch_lm<W>(c, lvl, bins, prop.get(), &c->ev[12]));
+    DCD_TRY_CUDA(cudaEventRecordWithFlags(c->ev[2], s, evf));
+    if (any) DCD_TRY(launch_lm_nocfg<W>(c, lvl, bins, prop.get(), &c->ev[12], evf));
     else
-      for (int x = 0; x < bins.plan.nb; x++) DCD_TRY_CUDA(cudaEventRecord(c->ev[12 + x], s));
-    DCD_TRY_CUDA(cudaEventRecord(c->ev[3], s));
+      for (int x = 0; x < bins.plan.nb; x++) DCD_TRY_CUDA(cudaEventRecordWithFlags(c->ev[12 + x], s, evf));
+    DCD_TRY_CUDA(cudaEventRecordWithFlags(c->ev[3], s, evf));
     if (total) {
       ::dcd::count_launch(), lm_apply<<<grid_for(total, T), T, 0, s>>>(
           lst, total, big_from, prop.get(), L, kbuf.get(), (unsigned long long*)a.get(), size.get(),
-          Lprev.get(), mvit.get(), iter, moved.get(), moved_cnt.get(), moved_big.get(), moved_big_cnt.get(), gid, gs);
+          Lprev.get(), mvit.get(), &d->pass_id, moved.get(), moved_cnt.get(), moved_big.get(), moved_big_cnt.get(),
+          gid, gs);
       if (big_from)
         ::dcd::count_launch(), lm_delta_in<W><<<grid_for(big_from * 32, T, 16), T, 0, s>>>(
-            lv, moved.get(), moved_cnt.get(), Lprev.get(), mvit.get(), iter, gs);
+            lv, moved.get(), moved_cnt.get(), Lprev.get(), mvit.get(), &d->pass_id, gs);
       if (n_big)
         ::dcd::count_launch(), lm_delta_in_block<W><<<grid_for(n_big * T, T, 4), T, 0, s>>>(
-            lv, moved_big.get(), moved_big_cnt.get(), Lprev.get(), mvit.get(), iter, gs);
+            lv, moved_big.get(), moved_big_cnt.get(), Lprev.get(), mvit.get(), &d->pass_id, gs);
     }
     ::dcd::count_launch(), sumsq_acc<<<sq_ctas, T, 0, s>>>(a.get(), nv, gid, gs);
     ::dcd::count_launch(), lm_decide<<<cdiv(G, 128), 128, 0, s>>>(gs, G, 1, c->cfg.max_iters, c->cfg.tau_inv,
                                                                    &d->any_running);
     DCD_LAUNCH_CHECK();
-    DCD_TRY_CUDA(cudaEventRecord(c->ev[4], s));
+    DCD_TRY_CUDA(cudaEventRecordWithFlags(c->ev[4], s, evf));
     DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
     DCD_TRY_CUDA(cudaMemcpyAsync(c->hgs, gs, G * sizeof(GraphState), cudaMemcpyDeviceToHost, s));
+    return DCD_OK;
+  };
+  if (any) DCD_TRY(prepare_lm<W>(lvl));
+  struct ExecGuard {
+    cudaGraphExec_t x = nullptr;
+    ~ExecGuard() {
+      if (x) cudaGraphExecDestroy(x);
+    }
+  } exec;
+  int64_t body_launches = 0;
+  // a level with nothing to evaluate still runs one (empty) pass, as the
+  // sequential definition does
+  for (;;) {
+    if (!exec.x) {
+      DCD_TRY_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      const int64_t l0 = g_launches.load();
+      const int rc = enqueue_pass(cudaEventRecordExternal);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(s, &graph);
+      body_launches = g_launches.load() - l0;
+      if (rc != DCD_OK || ec != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        if (rc != DCD_OK) return rc;
+        DCD_TRY_CUDA(ec);
+      }
+      const cudaError_t ei = cudaGraphInstantiate(&exec.x, graph, 0);
+      cudaGraphDestroy(graph);
+      DCD_TRY_CUDA(ei);
+    } else {
+      g_launches += body_launches;
+    }
+    DCD_TRY_CUDA(cudaGraphLaunch(exec.x, s));
     DCD_TRY_CUDA(cudaStreamSynchronize(s));
     float t1 = 0.f, t2 = 0.f;
     cudaEventElapsedTime(&t1, c->ev[2], c->ev[3]);
@@ -1476,7 +1546,7 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
   DCD_TRY(comp.alloc(&c->mem, n0));
   DCD_TRY(community_sums(c, n0, labels0, k0.get(), a.get(), size.get()));
   ::dcd::count_launch(), fill_iota<<<grid_for(n0, T), T, 0, s>>>(comp.get(), n0);
-  ::dcd::count_launch(), gs_reset_pass<<<cdiv(G, 128), 128, 0, s>>>(gs, G);
+  ::dcd::count_launch(), gs_reset_pass<<<cdiv(G, 128), 128, 0, s>>>(gs, G, &c->dsc.get()->pass_id);
   ::dcd::count_launch(), sumsq_acc<<<grid_for(n0, T, 4), T, 0, s>>>(a.get(), n0, gid0, gs);
   DCD_LAUNCH_CHECK();
 

@@ -35,6 +35,8 @@ struct DevScalars {
   int64_t bcnt[12];  // active vertices in each degree bin
   int64_t bdeg[12];  // sum of their degrees
   int64_t bmax[12];  // largest degree in the bin
+  int32_t pass_id;   // local-move passes started in this update (moved-in-pass marks)
+  int32_t pad2;
 };
 
 // Per-graph state of one update.  A context holds G graphs on disjoint vertex
@@ -137,6 +139,7 @@ struct dcd_ctx {
   dcd_config cfg{};
   int32_t mode = DCD_MODE_DELTA;
   cudaStream_t stream = nullptr;
+  bool own_stream = false;  // created by dcd_create (the caller passed none)
   int device = 0;
   int sms = 0;
   dcd::DevMem mem;
