@@ -172,6 +172,60 @@ __global__ void __launch_bounds__(256) merge_rows(
         ks += wv;
         if (lab[c] == Lu) is += wv;
       }
+    } else if (pair_ptr[u + 1] - pair_ptr[u] < G) {
+      // few pairs: the group's lanes hold them (lane q: pair p0 + q, and the
+      // prefix counts up to it), so an entry finds its place among them with
+      // shuffles instead of a binary search in global memory
+      const int64_t ob = rp_o[u], oe = rp_o[u + 1], nb = rp_n[u];
+      const int64_t p0 = pair_ptr[u];
+      const int np = (int)(pair_ptr[u + 1] - p0);
+      const int32_t Lu = lab[u];
+      const int32_t rA0 = pA[p0], rR0 = pR[p0];
+      const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane_id() & ~(G - 1)));
+      int32_t pc = INT_MAX, pa = 0, pr = 0;
+      uint32_t pf = 0;
+      long long pwv = 0;
+      if (g <= np) {
+        pa = pA[p0 + g] - rA0;
+        pr = pR[p0 + g] - rR0;
+        if (g < np) {
+          pc = (int32_t)(pkey[p0 + g] & 0xffffffffu);
+          pf = pflag[p0 + g];
+          pwv = pw[p0 + g];
+        }
+      }
+      for (int64_t e0 = ob; e0 < oe; e0 += G) {
+        const int64_t e = e0 + g;
+        const bool valid = e < oe;
+        const int32_t c = valid ? col_o[e] : INT_MAX;
+        int q = 0;  // pairs of the row with a smaller column (pairs are sorted)
+        for (int t = 0; t < np; t++) q += __shfl_sync(gmask, pc, t, G) < c ? 1 : 0;
+        const int32_t kq = __shfl_sync(gmask, pc, q, G);
+        const uint32_t fq = __shfl_sync(gmask, pf, q, G);
+        const long long wq = __shfl_sync(gmask, pwv, q, G);
+        const int32_t aq = __shfl_sync(gmask, pa, q, G), rq = __shfl_sync(gmask, pr, q, G);
+        const bool match = valid && kq == c;
+        const uint32_t f = match ? fq : 0u;
+        if (!valid || (f & kPairRemoved)) continue;
+        int64_t wv = w_o[e];
+        if (match && (f & kPairIns)) wv = (f & kPairDel) ? (int64_t)wq : wv + (int64_t)wq;
+        const int64_t pos = nb + (e - ob) - rq + aq;
+        col_n[pos] = c;
+        w_n[pos] = (int32_t)wv;
+        ks += wv;
+        if (lab[c] == Lu) is += wv;
+      }
+      for (int64_t q = p0 + g; q < p0 + np; q += G) {
+        if (!(pflag[q] & kPairAdded)) continue;
+        const int32_t c = (int32_t)(pkey[q] & 0xffffffffu);
+        const int64_t o = lower_bound_i32(col_o, ob, oe, c) - ob;
+        const int64_t pos = nb + o - (pR[q] - rR0) + (pA[q] - rA0);
+        const int64_t wv = pw[q];
+        col_n[pos] = c;
+        w_n[pos] = (int32_t)wv;
+        ks += wv;
+        if (lab[c] == Lu) is += wv;
+      }
     } else {
       int64_t ob = rp_o[u], oe = rp_o[u + 1], nb = rp_n[u];
       int64_t p0 = pair_ptr[u], p1 = pair_ptr[u + 1];

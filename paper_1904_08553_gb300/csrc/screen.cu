@@ -58,11 +58,10 @@ __device__ __forceinline__ bool better3(ST s1, int32_t d1, int32_t j1, ST s2, in
   return s1 > s2 || (s1 == s2 && (d1 < d2 || (d1 == d2 && j1 < j2)));
 }
 
-template <typename ST>
-__device__ __forceinline__ void warp_argmax3(ST& S, int32_t& D, int32_t& J) {
+__device__ __forceinline__ void warp_argmax3(i128& S, int32_t& D, int32_t& J) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    ST s2 = shfl_xor_st(S, o);
+    i128 s2 = shfl_xor_st(S, o);
     int32_t d2 = __shfl_xor_sync(0xffffffffu, D, o);
     int32_t j2 = __shfl_xor_sync(0xffffffffu, J, o);
     if (better3(s2, d2, j2, S, D, J)) {
@@ -71,6 +70,24 @@ __device__ __forceinline__ void warp_argmax3(ST& S, int32_t& D, int32_t& J) {
       J = j2;
     }
   }
+}
+
+// 64-bit gains: full-warp redux.sync steps with neutral values (no
+// divergence): the largest gain (high word, then low word), then the
+// smallest C(j) among the lanes holding it, then the smallest j (D and J are
+// >= 0 where a lane has a candidate; the sentinel is INT_MAX).
+__device__ __forceinline__ void warp_argmax3(long long& S, int32_t& D, int32_t& J) {
+  const unsigned long long u = (unsigned long long)S ^ 0x8000000000000000ull;
+  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+  const unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
+  const unsigned mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
+  const bool top = hi == mhi && lo == mlo;
+  const unsigned dmin = __reduce_min_sync(0xffffffffu, top ? (unsigned)D : 0xffffffffu);
+  const bool top2 = top && (unsigned)D == dmin;
+  const unsigned jmin = __reduce_min_sync(0xffffffffu, top2 ? (unsigned)J : 0xffffffffu);
+  S = (long long)((((unsigned long long)mhi << 32) | mlo) ^ 0x8000000000000000ull);
+  D = (int32_t)dmin;
+  J = (int32_t)jmin;
 }
 
 __device__ __forceinline__ void st_gain(long long* p, long long x) {
@@ -94,11 +111,11 @@ __device__ __forceinline__ i128 ld_gain<i128>(const long long* p) {
 
 // ---- row aggregation helpers ----
 
-// Lanes of one warp hold row v (degree <= 32), grouped by community.
+// Lanes of one warp hold row v (degree <= 32): neighbour label (-1: none or a
+// self loop) and weight.
 struct LaneRow {
   int32_t lab;
-  int64_t e;
-  unsigned leaders;
+  int32_t wt;
 };
 
 __device__ __forceinline__ LaneRow lane_row(const SV& g, int32_t v) {
@@ -110,21 +127,29 @@ __device__ __forceinline__ LaneRow lane_row(const SV& g, int32_t v) {
   valid = valid && y != v;
   LaneRow r;
   r.lab = valid ? g.L[y] : -1;
-  const int32_t wt = valid ? g.w[b + lane] : 0;
-  const unsigned peers = __match_any_sync(0xffffffffu, r.lab);
-  r.e = group_sum_exact(peers, wt);
-  r.leaders = __ballot_sync(0xffffffffu, valid && (int)(__ffs(peers) - 1) == lane);
+  r.wt = valid ? g.w[b + lane] : 0;
   return r;
 }
 
-// Weight from the row into community D (whole warp calls; D may differ per lane).
+// Weight from the row into community D (D the same in every lane): one
+// reduction over the warp.
+template <typename ST>
 __device__ __forceinline__ int64_t lane_get(const LaneRow& r, int32_t D) {
+  return group_sum<ST>(0xffffffffu, r.lab == D ? r.wt : 0);
+}
+
+// Weight from the row into each lane's own community D (lanes with want):
+// one reduction per distinct D among them.
+template <typename ST>
+__device__ __forceinline__ int64_t lane_get_each(const LaneRow& r, int32_t D, bool want) {
   int64_t out = 0;
-  for (unsigned lm = r.leaders; lm; lm &= lm - 1) {
-    const int l = __ffs(lm) - 1;
-    const int32_t ll = __shfl_sync(0xffffffffu, r.lab, l);
-    const int64_t el = __shfl_sync(0xffffffffu, r.e, l);
-    if (ll == D) out = el;
+  unsigned todo = __ballot_sync(0xffffffffu, want);
+  while (todo) {
+    const int32_t Dl = __shfl_sync(0xffffffffu, D, __ffs(todo) - 1);
+    const int64_t el = group_sum<ST>(0xffffffffu, r.lab == Dl ? r.wt : 0);
+    const bool hit = want && D == Dl;
+    if (hit) out = el;
+    todo &= ~__ballot_sync(0xffffffffu, hit);
   }
   return out;
 }
@@ -194,7 +219,7 @@ __global__ void __launch_bounds__(256) scr_a_warp(SV g, int64_t off, int64_t cnt
     ST S = 0;
     if (has_ins) {
       const LaneRow r = lane_row(g, u);
-      const int64_t eC = lane_get(r, C);
+      const int64_t eC = lane_get<ST>(r, C);
       const int64_t ku = g.k[u], aC = g.a[C];
       int32_t D = INT_MAX;
       J = INT_MAX;
@@ -204,7 +229,7 @@ __global__ void __launch_bounds__(256) scr_a_warp(SV g, int64_t off, int64_t cnt
         const bool sink = q < p1 && (g.pflag[q] & kPairIns);
         const int32_t j = sink ? (int32_t)(g.pkey[q] & 0xffffffffu) : -1;
         const int32_t Dj = sink ? g.L[j] : -2;
-        const int64_t eD = lane_get(r, Dj);
+        const int64_t eD = lane_get_each<ST>(r, Dj, sink);
         if (sink) {
           const ST x = (Dj == C) ? ST(0) : gain<ST>(g.m2_of(u), ku, eD, eC, g.a[Dj], aC);
           if (better3(x, Dj, j, S, D, J)) {
@@ -440,12 +465,12 @@ __global__ void __launch_bounds__(256) scr_c_warp(SV g, GroupView gv, int64_t cn
     const int64_t m0 = gv.gstart[gi], m1 = gv.gstart[gi + 1];
     const int32_t j = (int32_t)gv.keys[m0];
     const LaneRow r = lane_row(g, j);
-    const int64_t e2 = lane_get(r, g.L[j]);
+    const int64_t e2 = lane_get<ST>(r, g.L[j]);
     for (int64_t q0 = m0; q0 < m1; q0 += 32) {
       const int64_t q = q0 + lane;
       const int64_t idx = q < m1 ? (int64_t)gv.vals[q] : -1;
       const int32_t Ci = idx >= 0 ? g.L[g.src[idx]] : -2;
-      const int64_t e1 = lane_get(r, Ci);
+      const int64_t e1 = lane_get_each<ST>(r, Ci, idx >= 0);
       if (idx >= 0) decide<ST>(g, idx, j, e1, e2);
     }
   }
