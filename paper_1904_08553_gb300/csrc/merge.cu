@@ -120,12 +120,136 @@ __global__ void pair_status(const uint64_t* __restrict__ pkey, const int64_t* __
   }
 }
 
+// Rows longer than kLongRow entries (old or new) are merged by a CTA each
+// (merge_long) instead of by G lanes: a hub row would otherwise hold its
+// group for thousands of iterations and set the kernel's length.
+constexpr int64_t kLongRow = 512;
+
 __global__ void new_degrees(const int64_t* __restrict__ rp, const int64_t* __restrict__ pair_ptr,
                             const int32_t* __restrict__ pA, const int32_t* __restrict__ pR, int64_t n,
-                            int64_t* __restrict__ deg) {
-  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
-    int64_t p0 = pair_ptr[u], p1 = pair_ptr[u + 1];
-    deg[u] = rp[u + 1] - rp[u] + (pA[p1] - pA[p0]) - (pR[p1] - pR[p0]);
+                            int64_t* __restrict__ deg, int32_t* __restrict__ long_rows,
+                            int32_t* __restrict__ long_cnt) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (blockIdx.x * (int64_t)blockDim.x) + (threadIdx.x & ~31); base < n; base += stride) {
+    const int64_t u = base + lane_id();
+    bool lng = false;
+    if (u < n) {
+      const int64_t p0 = pair_ptr[u], p1 = pair_ptr[u + 1];
+      const int64_t od = rp[u + 1] - rp[u];
+      const int64_t nd = od + (pA[p1] - pA[p0]) - (pR[p1] - pR[p0]);
+      deg[u] = nd;
+      lng = od > kLongRow || nd > kLongRow;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, lng);
+    if (bal) {
+      int32_t slot = 0;
+      if (lane_id() == 0) slot = atomicAdd(long_cnt, __popc(bal));
+      slot = __shfl_sync(0xffffffffu, slot, 0);
+      if (lng) long_rows[slot + __popc(bal & lanemask_lt())] = (int32_t)u;
+    }
+  }
+}
+
+// One CTA per long row (the list from new_degrees): the row's pairs are staged
+// in shared memory when they fit, the entries are placed as in merge_rows, and
+// k_u, 2m and sum_i e_{i->C(i)} are reduced over the CTA.
+constexpr int kLongPairs = 1024;
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) merge_long(
+    const int32_t* __restrict__ long_rows, const int32_t* __restrict__ long_cnt, const int64_t* __restrict__ rp_o,
+    const int32_t* __restrict__ col_o, const int32_t* __restrict__ w_o, const int64_t* __restrict__ rp_n,
+    int32_t* __restrict__ col_n, int32_t* __restrict__ w_n, const int64_t* __restrict__ pair_ptr,
+    const uint64_t* __restrict__ pkey, const int64_t* __restrict__ pw, const uint8_t* __restrict__ pflag,
+    const int32_t* __restrict__ pA, const int32_t* __restrict__ pR, const int32_t* __restrict__ lab,
+    int64_t* __restrict__ kdeg, const int32_t* __restrict__ gid, GraphState* __restrict__ gs) {
+  __shared__ int32_t s_pc[kLongPairs];
+  __shared__ int32_t s_pa[kLongPairs + 1], s_pr[kLongPairs + 1];
+  __shared__ long long red_k[THREADS / 32], red_i[THREADS / 32];
+  const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5;
+  const int64_t cnt = *long_cnt;
+  for (int64_t i = blockIdx.x; i < cnt; i += gridDim.x) {
+    const int32_t u = long_rows[i];
+    const int64_t ob = rp_o[u], oe = rp_o[u + 1], nb = rp_n[u];
+    const int64_t p0 = pair_ptr[u], p1 = pair_ptr[u + 1];
+    const int64_t np = p1 - p0;
+    const int32_t Lu = lab[u];
+    const int32_t rA0 = pA[p0], rR0 = pR[p0];  // prefix arrays hold P + 1 entries
+    const bool staged = np <= kLongPairs;
+    if (staged) {
+      for (int64_t q = tid; q <= np; q += THREADS) {
+        s_pa[q] = pA[p0 + q] - rA0;
+        s_pr[q] = pR[p0 + q] - rR0;
+        if (q < np) s_pc[q] = (int32_t)(pkey[p0 + q] & 0xffffffffu);
+      }
+    }
+    __syncthreads();
+    int64_t ks = 0, is = 0;
+    const uint64_t hi = (uint64_t)(uint32_t)u << 32;
+    for (int64_t e = ob + tid; e < oe; e += THREADS) {
+      const int32_t c = col_o[e];
+      int64_t q;
+      bool match;
+      int32_t aq, rq;
+      if (staged) {
+        int64_t lo = 0, hi2 = np;
+        while (lo < hi2) {
+          const int64_t mid = (lo + hi2) >> 1;
+          if (s_pc[mid] < c) lo = mid + 1; else hi2 = mid;
+        }
+        q = p0 + lo;
+        match = lo < np && s_pc[lo] == c;
+        aq = s_pa[lo];
+        rq = s_pr[lo];
+      } else {
+        q = lower_bound_u64(pkey, p0, p1, hi | (uint32_t)c);
+        match = q < p1 && pkey[q] == (hi | (uint32_t)c);
+        aq = pA[q] - rA0;
+        rq = pR[q] - rR0;
+      }
+      const uint8_t f = match ? pflag[q] : 0;
+      if (f & kPairRemoved) continue;
+      int64_t wv = w_o[e];
+      if (match && (f & kPairIns)) wv = (f & kPairDel) ? pw[q] : wv + pw[q];
+      const int64_t pos = nb + (e - ob) - rq + aq;
+      col_n[pos] = c;
+      w_n[pos] = (int32_t)wv;
+      ks += wv;
+      if (lab[c] == Lu) is += wv;
+    }
+    for (int64_t q = p0 + tid; q < p1; q += THREADS) {
+      if (!(pflag[q] & kPairAdded)) continue;
+      const int32_t c = (int32_t)(pkey[q] & 0xffffffffu);
+      const int64_t o = lower_bound_i32(col_o, ob, oe, c) - ob;
+      const int64_t pos = nb + o - (pR[q] - rR0) + (pA[q] - rA0);
+      const int64_t wv = pw[q];
+      col_n[pos] = c;
+      w_n[pos] = (int32_t)wv;
+      ks += wv;
+      if (lab[c] == Lu) is += wv;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ks += __shfl_xor_sync(0xffffffffu, ks, o);
+      is += __shfl_xor_sync(0xffffffffu, is, o);
+    }
+    if (lane == 0) {
+      red_k[wid] = ks;
+      red_i[wid] = is;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      long long tk = 0, ti = 0;
+      for (int x = 0; x < THREADS / 32; x++) {
+        tk += red_k[x];
+        ti += red_i[x];
+      }
+      kdeg[u] = tk;
+      const int gu = graph_of(gid, u);
+      atomicAdd((unsigned long long*)&gs[gu].m2, (unsigned long long)tk);
+      atomicAdd((unsigned long long*)&gs[gu].in_cur, (unsigned long long)ti);
+    }
+    __syncthreads();
   }
 }
 
@@ -159,8 +283,9 @@ __global__ void __launch_bounds__(256) merge_rows(
   for (int64_t ubase = gid0; ubase < n; ubase += ngroups) {
     const int64_t u = ubase + (int64_t)(lane_id() / G);
     int64_t ks = 0, is = 0;
-    if (u >= n) {
-      // idle group in the warp's last round
+    const bool lng = u < n && (rp_o[u + 1] - rp_o[u] > kLongRow || rp_n[u + 1] - rp_n[u] > kLongRow);
+    if (u >= n || lng) {
+      // idle group in the warp's last round, or a long row (merge_long)
     } else if (pair_ptr[u] == pair_ptr[u + 1]) {
       int64_t ob = rp_o[u], oe = rp_o[u + 1], nb = rp_n[u];
       int32_t Lu = lab[u];
@@ -260,7 +385,7 @@ __global__ void __launch_bounds__(256) merge_rows(
     }
     ks = group_sum<G>(ks);
     is = group_sum<G>(is);
-    if (g == 0 && u < n) {
+    if (g == 0 && u < n && !lng) {
       kdeg[u] = ks;
       const int gu = graph_of(gid, u);
       if (gu != cur_g) {
@@ -373,7 +498,12 @@ int merge_batch(dcd_ctx* c, const int32_t* labels0, MergeOut* out) {
   DCD_TRY(c->col[nxt].ensure(&c->mem, cap));
   DCD_TRY(c->w[nxt].ensure(&c->mem, cap));
   int64_t* rp_n = c->rp[nxt].get();
-  ::dcd::count_launch(), new_degrees<<<grid_for(n, T), T, 0, s>>>(rp_o, out->pair_ptr.get(), added.get(), removed.get(), n, rp_n);
+  Buf<int32_t> long_rows, long_cnt;
+  DCD_TRY(long_rows.alloc(&c->mem, n));
+  DCD_TRY(long_cnt.alloc(&c->mem, 1));
+  DCD_TRY_CUDA(cudaMemsetAsync(long_cnt.get(), 0, sizeof(int32_t), s));
+  ::dcd::count_launch(), new_degrees<<<grid_for(n, T), T, 0, s>>>(rp_o, out->pair_ptr.get(), added.get(), removed.get(),
+                                                                   n, rp_n, long_rows.get(), long_cnt.get());
   DCD_LAUNCH_CHECK();
   DCD_TRY(exclusive_scan<int64_t>(rp_n, rp_n, n + 1, nullptr, stmp64, s));
 
@@ -393,6 +523,10 @@ int merge_batch(dcd_ctx* c, const int32_t* labels0, MergeOut* out) {
   else if (avg <= 24) DCD_MERGE(16);
   else DCD_MERGE(32);
 #undef DCD_MERGE
+  ::dcd::count_launch(), merge_long<256><<<4 * c->sms, 256, 0, s>>>(
+      long_rows.get(), long_cnt.get(), rp_o, col_o, w_o, rp_n, c->col[nxt].get(), c->w[nxt].get(), pp,
+      out->pkey.get(), out->pw.get(), out->pflag.get(), added.get(), removed.get(), labels0, out->k.get(),
+      c->G > 1 ? c->gid.get() : nullptr, c->gs.get());
   DCD_LAUNCH_CHECK();
   return DCD_OK;
 }
