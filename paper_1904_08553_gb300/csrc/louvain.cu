@@ -849,10 +849,10 @@ struct RowWalk {
 // Coarse entries of one level (sort path): every entry (u, v, w) becomes the
 // key cid(L(u)) * nc + cid(L(v)) with weight w; equal keys of a 32-entry
 // chunk are summed before they are written.
-template <typename W>
+template <typename W, bool NARROW>
 __global__ void __launch_bounds__(256) emit_coarse(int64_t n, int64_t m, const int64_t* __restrict__ rp,
                                                    const int32_t* __restrict__ col, const W* __restrict__ w,
-                                                   const int32_t* __restrict__ L, const int32_t* __restrict__ cid,
+                                                   const int32_t* __restrict__ ccid,
                                                    uint64_t nc, uint64_t* __restrict__ keys,
                                                    uint64_t* __restrict__ vals, unsigned long long* __restrict__ count) {
   const int lane = lane_id();
@@ -866,12 +866,13 @@ __global__ void __launch_bounds__(256) emit_coarse(int64_t n, int64_t m, const i
       const int64_t e = c0 + lane;
       const bool valid = e < E1;
       const int64_t row = rw.row(rp, n, c0, valid);
-      const int32_t cy = valid ? cid[L[col[e]]] : 0;
-      const uint64_t cu = valid ? (uint64_t)cid[L[row]] : 0;
+      const int32_t cy = valid ? ccid[col[e]] : 0;
+      const uint64_t cu = valid ? (uint64_t)ccid[row] : 0;
       const uint64_t key = valid ? cu * nc + (uint64_t)cy : ~0ull;
       const W wt = valid ? w[e] : W(0);
       const unsigned peers = __match_any_sync(0xffffffffu, key);
-      const int64_t sum = group_sum_exact(peers, wt);
+      // NARROW: 2m < 2^31 bounds every sum of weights, so 32 bits are exact
+      const int64_t sum = NARROW ? (int64_t)__reduce_add_sync(peers, (unsigned)wt) : group_sum_exact(peers, wt);
       const bool lead = valid && (int)(__ffs(peers) - 1) == lane;
       const unsigned bal = __ballot_sync(0xffffffffu, lead);
       unsigned long long slot = 0;
@@ -884,6 +885,14 @@ __global__ void __launch_bounds__(256) emit_coarse(int64_t n, int64_t m, const i
       }
     }
   }
+}
+
+// coarse vertex of every vertex: cid of its label (one gather per entry in the
+// emit instead of two dependent ones)
+__global__ void coarse_of(int64_t n, const int32_t* __restrict__ L, const int32_t* __restrict__ cid,
+                          int32_t* __restrict__ ccid) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    ccid[v] = cid[L[v]];
 }
 
 __global__ void key_heads(const uint64_t* __restrict__ keys, int64_t m, int32_t* __restrict__ head) {
@@ -1389,8 +1398,17 @@ int coarsen(dcd_ctx* c, const Csr<W>& g, const int32_t* L, const int32_t* cid, i
   DCD_TRY(cnt.alloc(&c->mem, 1));
   DCD_TRY_CUDA(cudaMemsetAsync(cnt.get(), 0, sizeof(unsigned long long), s));
   if (m0 > 0) {
-    ::dcd::count_launch(), emit_coarse<W><<<grid_for(cdiv(m0, kSegEntries) * 32, T, 16), T, 0, s>>>(
-        g.n, m0, g.rp, g.col, g.w, L, cid, (uint64_t)nc, k0.get(), v0.get(), cnt.get());
+    Buf<int32_t> ccid;
+    DCD_TRY(ccid.alloc(&c->mem, g.n));
+    ::dcd::count_launch(), coarse_of<<<grid_for(g.n, T), T, 0, s>>>(g.n, L, cid, ccid.get());
+    int64_t m2max = 0;
+    for (int x = 0; x < c->G; x++) m2max = c->hgs[x].m2 > m2max ? c->hgs[x].m2 : m2max;
+    if (m2max < ((int64_t)1 << 31))
+      ::dcd::count_launch(), emit_coarse<W, true><<<grid_for(cdiv(m0, kSegEntries) * 32, T, 16), T, 0, s>>>(
+          g.n, m0, g.rp, g.col, g.w, ccid.get(), (uint64_t)nc, k0.get(), v0.get(), cnt.get());
+    else
+      ::dcd::count_launch(), emit_coarse<W, false><<<grid_for(cdiv(m0, kSegEntries) * 32, T, 16), T, 0, s>>>(
+          g.n, m0, g.rp, g.col, g.w, ccid.get(), (uint64_t)nc, k0.get(), v0.get(), cnt.get());
     DCD_LAUNCH_CHECK();
   }
   DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch, cnt.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, s));
