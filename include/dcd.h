@@ -172,9 +172,9 @@ int dcd_set_mode(dcd_ctx* ctx, int32_t mode);
  * the last bin has hi = -1 (no limit) and variant DCD_LM_HUB.  Every plan
  * gives the same labels and modularity; only the time differs.
  * dcd_set_bins: errors DCD_EINVAL (nb outside 1..DCD_MAX_BINS, unknown
- * variant, hi not increasing or above the variant's limit, last bin not an
- * unbounded DCD_LM_HUB).  dcd_get_bins: *nb, and nb entries of variant / hi
- * (host, each may be NULL).  dcd_autotune: times one local-move evaluation of
+ * variant, hi not increasing or above the variant's limit, DCD_LM_HUB
+ * anywhere but in the last bin, last bin not an unbounded DCD_LM_HUB).
+ * dcd_get_bins: *nb, and nb entries of variant / hi (host, each may be NULL).  dcd_autotune: times one local-move evaluation of
  * every vertex of G_t under C_t (no move applied), reps times for each
  * candidate plan, and keeps the fastest; *best_ms (host, may be NULL)
  * receives its time per evaluation.  Errors: DCD_ESTATE before the first
@@ -188,7 +188,7 @@ int dcd_set_mode(dcd_ctx* ctx, int32_t mode);
 #define DCD_LM_BLK1K 5   /* <= 1024: a CTA per vertex, shared table                 */
 #define DCD_LM_BLK2K 6   /* <= 2048: a CTA per vertex, shared table                 */
 #define DCD_LM_BLK4K 7   /* <= 4096: a CTA per vertex, shared table                 */
-#define DCD_LM_HUB 8     /* any degree: a CTA per vertex, table in global memory   */
+#define DCD_LM_HUB 8     /* any degree: a row split over many CTAs, global tables  */
 int dcd_set_bins(dcd_ctx* ctx, int32_t nb, const int32_t* variant, const int64_t* hi);
 int dcd_get_bins(const dcd_ctx* ctx, int32_t* nb, int32_t* variant, int64_t* hi);
 int dcd_autotune(dcd_ctx* ctx, int32_t reps, float* best_ms);

@@ -653,7 +653,7 @@ int dcd_set_bins(dcd_ctx* c, int32_t nb, const int32_t* variant, const int64_t* 
     const bool last = b == nb - 1;
     const int64_t h = last ? INT64_MAX : hi[b];
     if (variant[b] < 0 || variant[b] >= kLmVariants) return DCD_EINVAL;
-    if (last ? (hi[b] != -1 || variant[b] != kLmHub) : (h < 1 || h > lm_variant_max(variant[b])))
+    if (last ? (hi[b] != -1 || variant[b] != kLmHub) : (h < 1 || h > lm_variant_max(variant[b]) || variant[b] == kLmHub))
       return DCD_EINVAL;
     if (b > 0 && h <= p.hi[b - 1]) return DCD_EINVAL;
     p.var[b] = variant[b];

@@ -11,11 +11,15 @@
 // after max_iters passes.  N = m2^2 Q is tracked exactly: the moved rows give
 // the change of sum_i e_{i->C(i)}, a full reduction gives sum_C a_C^2.
 //
-// Kernels (degree-binned; a bin is a list of active vertex ids):
-//   lm_warp   1..32 entries:  one warp per vertex, lanes hold the row, labels
-//             grouped with match_any and summed with redux.sync
-//   lm_block  33..4096 entries: one CTA per vertex, shared-memory table
-//             > 4096 entries: one CTA per vertex, table in global memory
+// Kernels (degree-binned; a bin is a list of active vertex ids, see BinPlan):
+//   lm_warp      rows of at most 32 (or 16) entries: a warp (half warp) per
+//                vertex, labels grouped with match_any, summed with redux.sync
+//   lm_warp_tbl  rows of at most 128 / 256 entries: a warp per vertex with a
+//                warp-private shared table
+//   lm_large     rows of at most 512 .. 4096 entries: a CTA per vertex with a
+//                shared table
+//   hub_*        longer rows: split into chunks over many CTAs, per-hub tables
+//                in global memory
 #include <cstdio>
 #include <vector>
 
@@ -370,57 +374,138 @@ __global__ void __launch_bounds__(THREADS) lm_large(LV<W> g, const int32_t* __re
   }
 }
 
-template <typename W, typename ST, int THREADS>
-__global__ void __launch_bounds__(THREADS) lm_block(LV<W> g, const int32_t* __restrict__ list, int64_t cnt,
-                                                    int32_t* __restrict__ prop, int32_t* __restrict__ gkeys,
-                                                    unsigned long long* __restrict__ gvals, int64_t gcap) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int NW = THREADS / 32;
-  __shared__ ST redS[NW];
-  __shared__ int32_t redD[NW];
-  __shared__ long long s_eC;
-  const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5;
-  for (int64_t i = blockIdx.x; i < cnt; i += gridDim.x) {
-    const int32_t v = list[i];
-    const int64_t b = g.rp[v];
-    const int64_t d = g.rp[v + 1] - b;
-    const int32_t C = g.L[v];
-    const uint32_t cap = table_cap(d), mask = cap - 1;
-    int32_t* keys;
-    unsigned long long* vals;
-    if (gcap == 0) {
-      vals = reinterpret_cast<unsigned long long*>(smem);
-      keys = reinterpret_cast<int32_t*>(smem + (size_t)cap * sizeof(unsigned long long));
-    } else {
-      keys = gkeys + (int64_t)blockIdx.x * gcap;
-      vals = gvals + (int64_t)blockIdx.x * gcap;
-    }
-    for (uint32_t s = tid; s < cap; s += THREADS) {
-      keys[s] = -1;
-      vals[s] = 0;
-    }
-    __syncthreads();
-    for (int64_t e0 = 0; e0 < d; e0 += THREADS) {
-      const int64_t e = e0 + tid;
-      bool valid = e < d;
+// ---------------------------------------------------------------- hub rows
+//
+// Rows of the hub bin are split into chunks of kHubChunk entries so that many
+// CTAs work on one hub at once (one CTA per hub leaves the largest hub setting
+// the kernel's length).  Each hub owns a region of a global open-addressing
+// table (capacity: 2 x degree, rounded up to a power of two) and of a list of
+// claimed slots:
+//   hub_agg     chunk c of hub h: group the chunk's labels by warp (match_any),
+//               add the group sums into h's table, list new keys;
+//   hub_gain    chunk c of hub h: the gains of h's claimed slots in slice c
+//               (the distinct labels are at most the degree), CTA argmax into
+//               a partial per chunk;
+//   hub_pick    warp per hub: argmax of the partials, the proposal;
+//   hub_clear   chunk c: empty the slots listed in slice c (the table is
+//               clean again for the next pass).
+constexpr int64_t kHubChunk = 4096;
+
+struct HubTables {
+  const int32_t* list = nullptr;  // hub vertices (the bin's list segment)
+  int64_t H = 0;                  // hubs
+  const int64_t* toff = nullptr;  // table offset of hub h (H + 1)
+  const int64_t* soff = nullptr;  // claimed-slot list offset of hub h (H + 1)
+  const int64_t* coff = nullptr;  // first chunk of hub h (H + 1)
+  int32_t* keys = nullptr;        // all tables (-1: empty)
+  unsigned long long* vals = nullptr;
+  int32_t* slots = nullptr;       // claimed-slot lists (table-relative slot)
+  int32_t* nslot = nullptr;       // claimed slots of hub h (this pass)
+  int32_t* nprev = nullptr;       // the same, kept for hub_clear
+  long long* part = nullptr;      // per chunk: gain (2 words), label
+};
+
+__device__ __forceinline__ int64_t hub_of_chunk(const HubTables& t, int64_t c) {
+  int64_t lo = 0, hi = t.H - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (t.coff[mid] <= c) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename W, typename ST>
+__global__ void __launch_bounds__(256) hub_agg(LV<W> g, HubTables t) {
+  const int lane = lane_id(), wib = threadIdx.x >> 5;
+  const int64_t nch = t.coff[t.H];
+  for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
+    const int64_t h = hub_of_chunk(t, c);
+    const int32_t v = t.list[h];
+    const int64_t b = g.rp[v], d = g.rp[v + 1] - b;
+    const int64_t e0 = (c - t.coff[h]) * kHubChunk, e1 = e0 + kHubChunk < d ? e0 + kHubChunk : d;
+    const uint32_t mask = (uint32_t)(t.toff[h + 1] - t.toff[h]) - 1;
+    int32_t* keys = t.keys + t.toff[h];
+    unsigned long long* vals = t.vals + t.toff[h];
+    int32_t* slots = t.slots + t.soff[h];
+    for (int64_t q0 = e0 + wib * 32; q0 < e1; q0 += blockDim.x) {
+      const int64_t e = q0 + lane;
+      bool valid = e < e1;
       const int32_t u = valid ? g.col[b + e] : -1;
       valid = valid && u != v;
       const int32_t lab = valid ? g.L[u] : -1;
       const W wt = valid ? g.w[b + e] : W(0);
       const unsigned peers = __match_any_sync(0xffffffffu, lab);
       const int64_t sum = group_sum<ST>(peers, wt);
-      if (valid && (int)(__ffs(peers) - 1) == lane) tbl_add(keys, vals, mask, lab, (unsigned long long)sum);
+      if (valid && (int)(__ffs(peers) - 1) == lane) {
+        uint32_t sl = hash_label(lab, mask);
+        for (;;) {
+          const int32_t k = keys[sl];
+          if (k == lab) {
+            atomicAdd(&vals[sl], (unsigned long long)sum);
+            break;
+          }
+          if (k == -1) {
+            const int32_t old = atomicCAS(&keys[sl], -1, lab);
+            if (old == -1) slots[atomicAdd(&t.nslot[h], 1)] = (int32_t)sl;
+            if (old == -1 || old == lab) {
+              atomicAdd(&vals[sl], (unsigned long long)sum);
+              break;
+            }
+          }
+          sl = (sl + 1) & mask;
+        }
+      }
     }
-    __syncthreads();
-    if (tid == 0) s_eC = tbl_get(keys, vals, mask, C);
-    __syncthreads();
-    const int64_t eC = s_eC, kv = g.k[v], aC = g.a[C], m2v = g.m2_of(v);
+  }
+}
+
+__device__ __forceinline__ void st_part(long long* p, long long S, int32_t D) {
+  p[0] = S;
+  p[1] = S < 0 ? -1 : 0;
+  p[2] = D;
+}
+__device__ __forceinline__ void st_part(long long* p, i128 S, int32_t D) {
+  p[0] = (long long)(unsigned long long)S;
+  p[1] = (long long)(unsigned long long)((unsigned __int128)S >> 64);
+  p[2] = D;
+}
+template <typename ST>
+__device__ __forceinline__ ST ld_part(const long long* p);
+template <>
+__device__ __forceinline__ long long ld_part<long long>(const long long* p) {
+  return p[0];
+}
+template <>
+__device__ __forceinline__ i128 ld_part<i128>(const long long* p) {
+  return (i128)(((unsigned __int128)(unsigned long long)p[1] << 64) | (unsigned long long)p[0]);
+}
+
+template <typename W, typename ST>
+__global__ void __launch_bounds__(256) hub_gain(LV<W> g, HubTables t) {
+  constexpr int NW = 256 / 32;
+  __shared__ ST redS[NW];
+  __shared__ int32_t redD[NW];
+  const int lane = lane_id(), wid = threadIdx.x >> 5;
+  const int64_t nch = t.coff[t.H];
+  for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
+    const int64_t h = hub_of_chunk(t, c);
+    const int32_t v = t.list[h];
+    const int32_t C = g.L[v];
+    const uint32_t mask = (uint32_t)(t.toff[h + 1] - t.toff[h]) - 1;
+    const int32_t* keys = t.keys + t.toff[h];
+    const unsigned long long* vals = t.vals + t.toff[h];
+    const int32_t* slots = t.slots + t.soff[h];
+    const int64_t nd = t.nslot[h];
+    const int64_t s0 = (c - t.coff[h]) * kHubChunk, s1 = s0 + kHubChunk < nd ? s0 + kHubChunk : nd;
+    const int64_t eC = tbl_get(keys, vals, mask, C);
+    const int64_t kv = g.k[v], aC = g.a[C], m2v = g.m2_of(v);
     ST S = gain_lowest<ST>();
     int32_t D = INT_MAX;
-    for (uint32_t s = tid; s < cap; s += THREADS) {
-      const int32_t key = keys[s];
-      if (key >= 0 && key != C) {
-        ST x = gain<ST>(m2v, kv, (int64_t)vals[s], eC, g.a[key], aC);
+    for (int64_t j = s0 + threadIdx.x; j < s1; j += blockDim.x) {
+      const uint32_t sl = (uint32_t)slots[j];
+      const int32_t key = keys[sl];
+      if (key != C) {
+        const ST x = gain<ST>(m2v, kv, (int64_t)vals[sl], eC, g.a[key], aC);
         if (better(x, key, S, D)) {
           S = x;
           D = key;
@@ -437,17 +522,75 @@ __global__ void __launch_bounds__(THREADS) lm_block(LV<W> g, const int32_t* __re
       S = lane < NW ? redS[lane] : gain_lowest<ST>();
       D = lane < NW ? redD[lane] : INT_MAX;
       warp_argmax(S, D);
-      if (lane == 0) {
-        prop[i] = (D != INT_MAX && S > 0) ? guard_choice(C, D, g.size) : C;
-        if (g.f_eC) {
-          g.f_eC[i] = eC;
-          g.f_eB[i] = D == INT_MAX ? 0 : tbl_get(keys, vals, mask, D);
-          g.f_dB[i] = D == INT_MAX ? -1 : D;
-          g.f_sB[i] = D == INT_MAX ? 0.0 : to_double(S);
-        }
-      }
+      if (lane == 0) st_part(t.part + 3 * c, S, D);
     }
     __syncthreads();
+  }
+}
+
+template <typename W, typename ST>
+__global__ void __launch_bounds__(256) hub_pick(LV<W> g, HubTables t, int32_t* __restrict__ prop) {
+  const int lane = lane_id();
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t h = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; h < t.H; h += nw) {
+    const int32_t v = t.list[h];
+    const int32_t C = g.L[v];
+    ST S = gain_lowest<ST>();
+    int32_t D = INT_MAX;
+    for (int64_t c = t.coff[h] + lane; c < t.coff[h + 1]; c += 32) {
+      const ST x = ld_part<ST>(t.part + 3 * c);
+      const int32_t y = (int32_t)t.part[3 * c + 2];
+      if (better(x, y, S, D)) {
+        S = x;
+        D = y;
+      }
+    }
+    warp_argmax(S, D);
+    const int32_t pv = proposal(S, D, C, g.size);
+    if (lane == 0) {
+      prop[h] = pv;
+      if (g.f_eC) {
+        const uint32_t mask = (uint32_t)(t.toff[h + 1] - t.toff[h]) - 1;
+        const int32_t* keys = t.keys + t.toff[h];
+        const unsigned long long* vals = t.vals + t.toff[h];
+        g.f_eC[h] = tbl_get(keys, vals, mask, C);
+        g.f_eB[h] = D == INT_MAX ? 0 : tbl_get(keys, vals, mask, D);
+        g.f_dB[h] = D == INT_MAX ? -1 : D;
+        g.f_sB[h] = D == INT_MAX ? 0.0 : to_double(S);
+      }
+      t.nprev[h] = t.nslot[h];
+      t.nslot[h] = 0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) hub_clear(HubTables t) {
+  const int64_t nch = t.coff[t.H];
+  for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
+    const int64_t h = hub_of_chunk(t, c);
+    int32_t* keys = t.keys + t.toff[h];
+    unsigned long long* vals = t.vals + t.toff[h];
+    const int32_t* slots = t.slots + t.soff[h];
+    const int64_t nd = t.nprev[h];
+    const int64_t s0 = (c - t.coff[h]) * kHubChunk, s1 = s0 + kHubChunk < nd ? s0 + kHubChunk : nd;
+    for (int64_t j = s0 + threadIdx.x; j < s1; j += blockDim.x) {
+      const uint32_t sl = (uint32_t)slots[j];
+      keys[sl] = -1;
+      vals[sl] = 0;
+    }
+  }
+}
+
+// sizes of the hub tables (hub h: table 2 x degree rounded up to a power of
+// two, slot list = degree, chunks = degree / kHubChunk rounded up)
+__global__ void hub_sizes(const int32_t* __restrict__ list, int64_t H, const int64_t* __restrict__ rp,
+                          int64_t* __restrict__ cap, int64_t* __restrict__ deg, int64_t* __restrict__ nch) {
+  for (int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h < H; h += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = list[h];
+    const int64_t d = rp[v + 1] - rp[v];
+    cap[h] = table_cap(d);
+    deg[h] = d;
+    nch[h] = cdiv(d, kHubChunk);
   }
 }
 
@@ -1027,9 +1170,13 @@ struct Bins {
   Buf<int32_t> list;
   int64_t cnt[kMaxBins] = {}, deg[kMaxBins] = {}, maxd[kMaxBins] = {}, off[kMaxBins + 1] = {};
   int64_t total = 0, act_deg = 0, n_active = 0;
-  Buf<int32_t> hkeys;
+  // tables of the hub bin (see hub_agg)
+  Buf<int64_t> htoff, hsoff, hcoff;
+  Buf<int32_t> hkeys, hslots, hnslot, hnprev;
   Buf<unsigned long long> hvals;
-  int64_t hub_cap = 0, hub_ctas = 0;
+  Buf<long long> hpart;
+  int64_t hub_chunks = 0;
+  HubTables ht;
 };
 
 template <typename W>
@@ -1066,23 +1213,55 @@ int make_bins(dcd_ctx* c, const Csr<W>& g, const uint8_t* active, Bins* b, const
                                                                        b->list.get(), gid, c->gs.get(), plan);
     DCD_LAUNCH_CHECK();
   }
-  // hub tables in global memory: one region per CTA, sized for the largest hub
-  int64_t hub_cnt = 0, hub_max = 0;
+  // tables of the hub bin: a region per hub, sized by its degree
+  int hub_bin = -1;
   for (int x = 0; x < plan.nb; x++)
-    if (plan.var[x] == kLmHub) {
-      hub_cnt += b->cnt[x];
-      hub_max = b->maxd[x] > hub_max ? b->maxd[x] : hub_max;
-    }
-  if (hub_cnt) {
-    b->hub_cap = table_cap(hub_max);
-    const int64_t budget = (int64_t)1 << 30;  // bytes for hub tables
-    int64_t hc = budget / (b->hub_cap * 12);
-    if (hc < 1) hc = 1;
-    if (hc > hub_cnt) hc = hub_cnt;
-    if (hc > 4 * (int64_t)c->sms) hc = 4 * (int64_t)c->sms;
-    b->hub_ctas = hc;
-    DCD_TRY(b->hkeys.alloc(&c->mem, hc * b->hub_cap));
-    DCD_TRY(b->hvals.alloc(&c->mem, hc * b->hub_cap));
+    if (plan.var[x] == kLmHub && b->cnt[x]) hub_bin = x;
+  if (hub_bin >= 0) {
+    const int64_t H = b->cnt[hub_bin];
+    const int32_t* hl = b->list.get() + b->off[hub_bin];
+    Buf<int64_t> deg, tmp;
+    DCD_TRY(b->htoff.alloc(&c->mem, H + 1));
+    DCD_TRY(b->hsoff.alloc(&c->mem, H + 1));
+    DCD_TRY(b->hcoff.alloc(&c->mem, H + 1));
+    DCD_TRY(deg.alloc(&c->mem, H + 1));
+    DCD_TRY(tmp.alloc(&c->mem, scan_tmp_count(H + 1) + 1));
+    DCD_TRY_CUDA(cudaMemsetAsync(b->htoff.get() + H, 0, sizeof(int64_t), s));
+    DCD_TRY_CUDA(cudaMemsetAsync(b->hcoff.get() + H, 0, sizeof(int64_t), s));
+    DCD_TRY_CUDA(cudaMemsetAsync(deg.get() + H, 0, sizeof(int64_t), s));
+    ::dcd::count_launch(), hub_sizes<<<grid_for(H, T), T, 0, s>>>(hl, H, g.rp, b->htoff.get(), deg.get(),
+                                                                  b->hcoff.get());
+    DCD_LAUNCH_CHECK();
+    DCD_TRY(exclusive_scan<int64_t>(b->htoff.get(), b->htoff.get(), H + 1, nullptr, tmp.get(), s));
+    DCD_TRY(exclusive_scan<int64_t>(deg.get(), b->hsoff.get(), H + 1, nullptr, tmp.get(), s));
+    DCD_TRY(exclusive_scan<int64_t>(b->hcoff.get(), b->hcoff.get(), H + 1, nullptr, tmp.get(), s));
+    DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch, b->htoff.get() + H, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch + 1, b->hsoff.get() + H, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch + 2, b->hcoff.get() + H, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    DCD_TRY_CUDA(cudaStreamSynchronize(s));
+    const int64_t tcap = c->hscratch[0], scap = c->hscratch[1];
+    b->hub_chunks = c->hscratch[2];
+    DCD_TRY(b->hkeys.alloc(&c->mem, tcap));
+    DCD_TRY(b->hvals.alloc(&c->mem, tcap));
+    DCD_TRY(b->hslots.alloc(&c->mem, scap));
+    DCD_TRY(b->hnslot.alloc(&c->mem, H));
+    DCD_TRY(b->hnprev.alloc(&c->mem, H));
+    DCD_TRY(b->hpart.alloc(&c->mem, 3 * b->hub_chunks));
+    DCD_TRY_CUDA(cudaMemsetAsync(b->hkeys.get(), 0xff, tcap * sizeof(int32_t), s));
+    DCD_TRY_CUDA(cudaMemsetAsync(b->hvals.get(), 0, tcap * sizeof(unsigned long long), s));
+    DCD_TRY_CUDA(cudaMemsetAsync(b->hnslot.get(), 0, H * sizeof(int32_t), s));
+    HubTables& t = b->ht;
+    t.list = hl;
+    t.H = H;
+    t.toff = b->htoff.get();
+    t.soff = b->hsoff.get();
+    t.coff = b->hcoff.get();
+    t.keys = b->hkeys.get();
+    t.vals = b->hvals.get();
+    t.slots = b->hslots.get();
+    t.nslot = b->hnslot.get();
+    t.nprev = b->hnprev.get();
+    t.part = b->hpart.get();
   }
   return DCD_OK;
 }
@@ -1157,10 +1336,14 @@ int launch_lm_st(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEvent_
         case kLmBlk1k: DCD_TRY((launch_large<W, ST, 256, 4>(c, g, lst, cnt, b.maxd[x], pr))); break;
         case kLmBlk2k: DCD_TRY((launch_large<W, ST, 256, 8>(c, g, lst, cnt, b.maxd[x], pr))); break;
         case kLmBlk4k: DCD_TRY((launch_large<W, ST, 512, 8>(c, g, lst, cnt, b.maxd[x], pr))); break;
-        default:
-          count_launch(), lm_block<W, ST, kHubThreads><<<(unsigned)b.hub_ctas, kHubThreads, 0, s>>>(
-              g, lst, cnt, pr, b.hkeys.get(), b.hvals.get(), b.hub_cap);
+        default: {
+          const unsigned ch = (unsigned)(b.hub_chunks < 16 * (int64_t)c->sms ? b.hub_chunks : 16 * (int64_t)c->sms);
+          count_launch(), hub_agg<W, ST><<<ch, 256, 0, s>>>(g, b.ht);
+          count_launch(), hub_gain<W, ST><<<ch, 256, 0, s>>>(g, b.ht);
+          count_launch(), hub_pick<W, ST><<<grid_for(cnt * 32, T), T, 0, s>>>(g, b.ht, pr);
+          count_launch(), hub_clear<<<ch, 256, 0, s>>>(b.ht);
           break;
+        }
       }
       DCD_LAUNCH_CHECK();
     }

@@ -535,10 +535,11 @@ __global__ void __launch_bounds__(THREADS) scr_c_block(SV g, GroupView gv, int64
 }
 
 // ---- phase D: marks ----
-__global__ void __launch_bounds__(256) scr_mark(SV g, int64_t nsrc) {
+// Sources [lo, hi) of the list, a warp each.
+__global__ void __launch_bounds__(256) scr_mark(SV g, int64_t lo, int64_t hi) {
   const int lane = lane_id();
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t idx = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; idx < nsrc; idx += nw) {
+  for (int64_t idx = lo + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); idx < hi; idx += nw) {
     const uint8_t f = g.flags[idx];
     if (!f) continue;
     const int32_t u = g.src[idx];
@@ -552,6 +553,30 @@ __global__ void __launch_bounds__(256) scr_mark(SV g, int64_t nsrc) {
     }
     const int64_t e1 = g.rp[u + 1];
     for (int64_t e = g.rp[u] + lane; e < e1; e += 32) g.mark[g.col[e]] = 1;
+  }
+}
+
+// Hub sources [lo, hi) of the list (rows above 4096 entries): kMarkSlices
+// CTAs per source, each marking one slice of the row.
+constexpr int kMarkSlices = 16;
+__global__ void __launch_bounds__(256) scr_mark_hub(SV g, int64_t lo, int64_t hi) {
+  for (int64_t b = blockIdx.x; b < (hi - lo) * kMarkSlices; b += gridDim.x) {
+    const int64_t idx = lo + b / kMarkSlices;
+    const int sl = (int)(b % kMarkSlices);
+    const uint8_t f = g.flags[idx];
+    if (!f) continue;
+    const int32_t u = g.src[idx];
+    if (sl == 0 && threadIdx.x == 0) {
+      g.mark[u] = 1;
+      if (f & 2) {
+        const int32_t j = g.jstar[idx];
+        g.mark[j] = 1;
+        g.cflag[g.L[j]] = 1;
+      }
+    }
+    const int64_t r0 = g.rp[u], d = g.rp[u + 1] - r0;
+    const int64_t e0 = r0 + d * sl / kMarkSlices, e1 = r0 + d * (sl + 1) / kMarkSlices;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) g.mark[g.col[e]] = 1;
   }
 }
 
@@ -722,7 +747,8 @@ int screen_impl(dcd_ctx* c, SV& sv, const Csr<int32_t>& g, const int64_t* cnt, i
   }
   trace("screen: phases B, C");
   // ---- D ----
-  count_launch(), scr_mark<<<grid_for(nsrc * 32, T, 16), T, 0, s>>>(sv, nsrc);
+  if (off3) count_launch(), scr_mark<<<grid_for(off3 * 32, T, 16), T, 0, s>>>(sv, 0, off3);
+  if (cnt[3]) count_launch(), scr_mark_hub<<<grid_for(cnt[3] * kMarkSlices * T, T, 8), T, 0, s>>>(sv, off3, nsrc);
   DCD_LAUNCH_CHECK();
   return DCD_OK;
 }
