@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "agg.cuh"
+#include "hub.cuh"
 #include "prims.cuh"
 #include "state.cuh"
 
@@ -376,88 +377,14 @@ __global__ void __launch_bounds__(THREADS) lm_large(LV<W> g, const int32_t* __re
 
 // ---------------------------------------------------------------- hub rows
 //
-// Rows of the hub bin are split into chunks of kHubChunk entries so that many
-// CTAs work on one hub at once (one CTA per hub leaves the largest hub setting
-// the kernel's length).  Each hub owns a region of a global open-addressing
-// table (capacity: 2 x degree, rounded up to a power of two) and of a list of
-// claimed slots:
-//   hub_agg     chunk c of hub h: group the chunk's labels by warp (match_any),
-//               add the group sums into h's table, list new keys;
+// Rows of the hub bin (hub.cuh): hub_agg sums each row into its hub's global
+// table, chunk by chunk over many CTAs; then
 //   hub_gain    chunk c of hub h: the gains of h's claimed slots in slice c
 //               (the distinct labels are at most the degree), CTA argmax into
 //               a partial per chunk;
 //   hub_pick    warp per hub: argmax of the partials, the proposal;
 //   hub_clear   chunk c: empty the slots listed in slice c (the table is
 //               clean again for the next pass).
-constexpr int64_t kHubChunk = 4096;
-
-struct HubTables {
-  const int32_t* list = nullptr;  // hub vertices (the bin's list segment)
-  int64_t H = 0;                  // hubs
-  const int64_t* toff = nullptr;  // table offset of hub h (H + 1)
-  const int64_t* soff = nullptr;  // claimed-slot list offset of hub h (H + 1)
-  const int64_t* coff = nullptr;  // first chunk of hub h (H + 1)
-  int32_t* keys = nullptr;        // all tables (-1: empty)
-  unsigned long long* vals = nullptr;
-  int32_t* slots = nullptr;       // claimed-slot lists (table-relative slot)
-  int32_t* nslot = nullptr;       // claimed slots of hub h (this pass)
-  int32_t* nprev = nullptr;       // the same, kept for hub_clear
-  long long* part = nullptr;      // per chunk: gain (2 words), label
-};
-
-__device__ __forceinline__ int64_t hub_of_chunk(const HubTables& t, int64_t c) {
-  int64_t lo = 0, hi = t.H - 1;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi + 1) >> 1;
-    if (t.coff[mid] <= c) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-template <typename W, typename ST>
-__global__ void __launch_bounds__(256) hub_agg(LV<W> g, HubTables t) {
-  const int lane = lane_id(), wib = threadIdx.x >> 5;
-  const int64_t nch = t.coff[t.H];
-  for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
-    const int64_t h = hub_of_chunk(t, c);
-    const int32_t v = t.list[h];
-    const int64_t b = g.rp[v], d = g.rp[v + 1] - b;
-    const int64_t e0 = (c - t.coff[h]) * kHubChunk, e1 = e0 + kHubChunk < d ? e0 + kHubChunk : d;
-    const uint32_t mask = (uint32_t)(t.toff[h + 1] - t.toff[h]) - 1;
-    int32_t* keys = t.keys + t.toff[h];
-    unsigned long long* vals = t.vals + t.toff[h];
-    int32_t* slots = t.slots + t.soff[h];
-    for (int64_t q0 = e0 + wib * 32; q0 < e1; q0 += blockDim.x) {
-      const int64_t e = q0 + lane;
-      bool valid = e < e1;
-      const int32_t u = valid ? g.col[b + e] : -1;
-      valid = valid && u != v;
-      const int32_t lab = valid ? g.L[u] : -1;
-      const W wt = valid ? g.w[b + e] : W(0);
-      const unsigned peers = __match_any_sync(0xffffffffu, lab);
-      const int64_t sum = group_sum<ST>(peers, wt);
-      if (valid && (int)(__ffs(peers) - 1) == lane) {
-        uint32_t sl = hash_label(lab, mask);
-        for (;;) {
-          const int32_t k = keys[sl];
-          if (k == lab) {
-            atomicAdd(&vals[sl], (unsigned long long)sum);
-            break;
-          }
-          if (k == -1) {
-            const int32_t old = atomicCAS(&keys[sl], -1, lab);
-            if (old == -1) slots[atomicAdd(&t.nslot[h], 1)] = (int32_t)sl;
-            if (old == -1 || old == lab) {
-              atomicAdd(&vals[sl], (unsigned long long)sum);
-              break;
-            }
-          }
-          sl = (sl + 1) & mask;
-        }
-      }
-    }
-  }
-}
 
 __device__ __forceinline__ void st_part(long long* p, long long S, int32_t D) {
   p[0] = S;
@@ -578,19 +505,6 @@ __global__ void __launch_bounds__(256) hub_clear(HubTables t) {
       keys[sl] = -1;
       vals[sl] = 0;
     }
-  }
-}
-
-// sizes of the hub tables (hub h: table 2 x degree rounded up to a power of
-// two, slot list = degree, chunks = degree / kHubChunk rounded up)
-__global__ void hub_sizes(const int32_t* __restrict__ list, int64_t H, const int64_t* __restrict__ rp,
-                          int64_t* __restrict__ cap, int64_t* __restrict__ deg, int64_t* __restrict__ nch) {
-  for (int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h < H; h += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t v = list[h];
-    const int64_t d = rp[v + 1] - rp[v];
-    cap[h] = table_cap(d);
-    deg[h] = d;
-    nch[h] = cdiv(d, kHubChunk);
   }
 }
 
@@ -1170,13 +1084,7 @@ struct Bins {
   Buf<int32_t> list;
   int64_t cnt[kMaxBins] = {}, deg[kMaxBins] = {}, maxd[kMaxBins] = {}, off[kMaxBins + 1] = {};
   int64_t total = 0, act_deg = 0, n_active = 0;
-  // tables of the hub bin (see hub_agg)
-  Buf<int64_t> htoff, hsoff, hcoff;
-  Buf<int32_t> hkeys, hslots, hnslot, hnprev;
-  Buf<unsigned long long> hvals;
-  Buf<long long> hpart;
-  int64_t hub_chunks = 0;
-  HubTables ht;
+  HubBufs hub;  // tables of the hub bin (hub.cuh)
 };
 
 template <typename W>
@@ -1214,55 +1122,9 @@ int make_bins(dcd_ctx* c, const Csr<W>& g, const uint8_t* active, Bins* b, const
     DCD_LAUNCH_CHECK();
   }
   // tables of the hub bin: a region per hub, sized by its degree
-  int hub_bin = -1;
   for (int x = 0; x < plan.nb; x++)
-    if (plan.var[x] == kLmHub && b->cnt[x]) hub_bin = x;
-  if (hub_bin >= 0) {
-    const int64_t H = b->cnt[hub_bin];
-    const int32_t* hl = b->list.get() + b->off[hub_bin];
-    Buf<int64_t> deg, tmp;
-    DCD_TRY(b->htoff.alloc(&c->mem, H + 1));
-    DCD_TRY(b->hsoff.alloc(&c->mem, H + 1));
-    DCD_TRY(b->hcoff.alloc(&c->mem, H + 1));
-    DCD_TRY(deg.alloc(&c->mem, H + 1));
-    DCD_TRY(tmp.alloc(&c->mem, scan_tmp_count(H + 1) + 1));
-    DCD_TRY_CUDA(cudaMemsetAsync(b->htoff.get() + H, 0, sizeof(int64_t), s));
-    DCD_TRY_CUDA(cudaMemsetAsync(b->hcoff.get() + H, 0, sizeof(int64_t), s));
-    DCD_TRY_CUDA(cudaMemsetAsync(deg.get() + H, 0, sizeof(int64_t), s));
-    ::dcd::count_launch(), hub_sizes<<<grid_for(H, T), T, 0, s>>>(hl, H, g.rp, b->htoff.get(), deg.get(),
-                                                                  b->hcoff.get());
-    DCD_LAUNCH_CHECK();
-    DCD_TRY(exclusive_scan<int64_t>(b->htoff.get(), b->htoff.get(), H + 1, nullptr, tmp.get(), s));
-    DCD_TRY(exclusive_scan<int64_t>(deg.get(), b->hsoff.get(), H + 1, nullptr, tmp.get(), s));
-    DCD_TRY(exclusive_scan<int64_t>(b->hcoff.get(), b->hcoff.get(), H + 1, nullptr, tmp.get(), s));
-    DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch, b->htoff.get() + H, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch + 1, b->hsoff.get() + H, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch + 2, b->hcoff.get() + H, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    DCD_TRY_CUDA(cudaStreamSynchronize(s));
-    const int64_t tcap = c->hscratch[0], scap = c->hscratch[1];
-    b->hub_chunks = c->hscratch[2];
-    DCD_TRY(b->hkeys.alloc(&c->mem, tcap));
-    DCD_TRY(b->hvals.alloc(&c->mem, tcap));
-    DCD_TRY(b->hslots.alloc(&c->mem, scap));
-    DCD_TRY(b->hnslot.alloc(&c->mem, H));
-    DCD_TRY(b->hnprev.alloc(&c->mem, H));
-    DCD_TRY(b->hpart.alloc(&c->mem, 3 * b->hub_chunks));
-    DCD_TRY_CUDA(cudaMemsetAsync(b->hkeys.get(), 0xff, tcap * sizeof(int32_t), s));
-    DCD_TRY_CUDA(cudaMemsetAsync(b->hvals.get(), 0, tcap * sizeof(unsigned long long), s));
-    DCD_TRY_CUDA(cudaMemsetAsync(b->hnslot.get(), 0, H * sizeof(int32_t), s));
-    HubTables& t = b->ht;
-    t.list = hl;
-    t.H = H;
-    t.toff = b->htoff.get();
-    t.soff = b->hsoff.get();
-    t.coff = b->hcoff.get();
-    t.keys = b->hkeys.get();
-    t.vals = b->hvals.get();
-    t.slots = b->hslots.get();
-    t.nslot = b->hnslot.get();
-    t.nprev = b->hnprev.get();
-    t.part = b->hpart.get();
-  }
+    if (plan.var[x] == kLmHub && b->cnt[x])
+      DCD_TRY(hub_setup(c, b->list.get() + b->off[x], b->cnt[x], g.rp, &b->hub));
   return DCD_OK;
 }
 
@@ -1337,11 +1199,11 @@ int launch_lm_st(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEvent_
         case kLmBlk2k: DCD_TRY((launch_large<W, ST, 256, 8>(c, g, lst, cnt, b.maxd[x], pr))); break;
         case kLmBlk4k: DCD_TRY((launch_large<W, ST, 512, 8>(c, g, lst, cnt, b.maxd[x], pr))); break;
         default: {
-          const unsigned ch = (unsigned)(b.hub_chunks < 16 * (int64_t)c->sms ? b.hub_chunks : 16 * (int64_t)c->sms);
-          count_launch(), hub_agg<W, ST><<<ch, 256, 0, s>>>(g, b.ht);
-          count_launch(), hub_gain<W, ST><<<ch, 256, 0, s>>>(g, b.ht);
-          count_launch(), hub_pick<W, ST><<<grid_for(cnt * 32, T), T, 0, s>>>(g, b.ht, pr);
-          count_launch(), hub_clear<<<ch, 256, 0, s>>>(b.ht);
+          const unsigned ch = hub_grid(c, b.hub);
+          count_launch(), hub_agg<W, ST><<<ch, 256, 0, s>>>(g, b.hub.t);
+          count_launch(), hub_gain<W, ST><<<ch, 256, 0, s>>>(g, b.hub.t);
+          count_launch(), hub_pick<W, ST><<<grid_for(cnt * 32, T), T, 0, s>>>(g, b.hub.t, pr);
+          count_launch(), hub_clear<<<ch, 256, 0, s>>>(b.hub.t);
           break;
         }
       }
@@ -1635,6 +1497,59 @@ int coarsen(dcd_ctx* c, const Csr<W>& g, const int32_t* L, const int32_t* cid, i
 }
 
 }  // namespace
+
+int hub_setup(dcd_ctx* c, const int32_t* list, int64_t H, const int64_t* rp, HubBufs* b) {
+  cudaStream_t s = c->stream;
+  const int T = 256;
+  Buf<int64_t> deg, tmp;
+  DCD_TRY(b->toff.alloc(&c->mem, H + 1));
+  DCD_TRY(b->soff.alloc(&c->mem, H + 1));
+  DCD_TRY(b->coff.alloc(&c->mem, H + 1));
+  DCD_TRY(deg.alloc(&c->mem, H + 1));
+  DCD_TRY(tmp.alloc(&c->mem, scan_tmp_count(H + 1) + 1));
+  DCD_TRY_CUDA(cudaMemsetAsync(b->toff.get() + H, 0, sizeof(int64_t), s));
+  DCD_TRY_CUDA(cudaMemsetAsync(b->coff.get() + H, 0, sizeof(int64_t), s));
+  DCD_TRY_CUDA(cudaMemsetAsync(deg.get() + H, 0, sizeof(int64_t), s));
+  ::dcd::count_launch(), hub_sizes<0><<<grid_for(H, T), T, 0, s>>>(list, H, rp, b->toff.get(), deg.get(),
+                                                                    b->coff.get());
+  DCD_LAUNCH_CHECK();
+  DCD_TRY(exclusive_scan<int64_t>(b->toff.get(), b->toff.get(), H + 1, nullptr, tmp.get(), s));
+  DCD_TRY(exclusive_scan<int64_t>(deg.get(), b->soff.get(), H + 1, nullptr, tmp.get(), s));
+  DCD_TRY(exclusive_scan<int64_t>(b->coff.get(), b->coff.get(), H + 1, nullptr, tmp.get(), s));
+  DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch, b->toff.get() + H, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch + 1, b->soff.get() + H, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch + 2, b->coff.get() + H, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  DCD_TRY_CUDA(cudaStreamSynchronize(s));
+  const int64_t tcap = c->hscratch[0], scap = c->hscratch[1];
+  b->chunks = c->hscratch[2];
+  DCD_TRY(b->keys.alloc(&c->mem, tcap));
+  DCD_TRY(b->vals.alloc(&c->mem, tcap));
+  DCD_TRY(b->slots.alloc(&c->mem, scap));
+  DCD_TRY(b->nslot.alloc(&c->mem, H));
+  DCD_TRY(b->nprev.alloc(&c->mem, H));
+  DCD_TRY(b->part.alloc(&c->mem, 3 * b->chunks));
+  DCD_TRY_CUDA(cudaMemsetAsync(b->keys.get(), 0xff, tcap * sizeof(int32_t), s));
+  DCD_TRY_CUDA(cudaMemsetAsync(b->vals.get(), 0, tcap * sizeof(unsigned long long), s));
+  DCD_TRY_CUDA(cudaMemsetAsync(b->nslot.get(), 0, H * sizeof(int32_t), s));
+  HubTables& t = b->t;
+  t.list = list;
+  t.H = H;
+  t.toff = b->toff.get();
+  t.soff = b->soff.get();
+  t.coff = b->coff.get();
+  t.keys = b->keys.get();
+  t.vals = b->vals.get();
+  t.slots = b->slots.get();
+  t.nslot = b->nslot.get();
+  t.nprev = b->nprev.get();
+  t.part = b->part.get();
+  return DCD_OK;
+}
+
+unsigned hub_grid(dcd_ctx* c, const HubBufs& b) {
+  const int64_t cap = 16 * (int64_t)c->sms;
+  return (unsigned)(b.chunks < cap ? (b.chunks > 0 ? b.chunks : 1) : cap);
+}
 
 int pool_stats(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* L, const int64_t* k, const int64_t* a,
                const int32_t* size, const uint8_t* mask, PoolStats* out) {

@@ -20,6 +20,7 @@
 //      per source).
 //   D  per source: mark Gamma(i), i, j*, flag C(j*).
 #include "agg.cuh"
+#include "hub.cuh"
 #include "prims.cuh"
 #include "state.cuh"
 
@@ -378,6 +379,71 @@ __global__ void __launch_bounds__(THREADS) scr_a_block(SV g, int64_t off, int64_
   }
 }
 
+// Hub sources (rows above 4096 entries): the rows were summed into per-hub
+// global tables by hub_agg (many CTAs per row); one CTA per source then
+// reads its deletes and evaluates its insert sinks by table lookups.
+template <typename ST, int THREADS>
+__global__ void __launch_bounds__(THREADS) scr_a_hub(SV g, int64_t off, int64_t cnt, HubTables t) {
+  constexpr int NW = THREADS / 32;
+  __shared__ ST redS[NW];
+  __shared__ int32_t redD[NW], redJ[NW];
+  __shared__ int s_flags;
+  const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5;
+  for (int64_t h = blockIdx.x; h < cnt; h += gridDim.x) {
+    const int64_t idx = off + h;
+    const int32_t u = g.src[idx];
+    const int32_t C = g.L[u];
+    const int64_t p0 = g.pair_ptr[u], p1 = g.pair_ptr[u + 1];
+    if (tid == 0) s_flags = 0;
+    __syncthreads();
+    bool has_ins;
+    const bool intra = scan_deletes(g, u, p0, p1, tid, THREADS, &has_ins);
+    if (intra || has_ins) atomicOr(&s_flags, (intra ? 1 : 0) | (has_ins ? 2 : 0));
+    __syncthreads();
+    const int flags = s_flags;
+    int32_t J = -1;
+    ST S = 0;
+    if (flags & 2) {
+      const uint32_t mask = (uint32_t)(t.toff[h + 1] - t.toff[h]) - 1;
+      const int32_t* keys = t.keys + t.toff[h];
+      const unsigned long long* vals = t.vals + t.toff[h];
+      const int64_t eC = tbl_get(keys, vals, mask, C);
+      const int64_t ku = g.k[u], aC = g.a[C];
+      int32_t D = INT_MAX;
+      J = INT_MAX;
+      S = gain_lowest<ST>();
+      for (int64_t q = p0 + tid; q < p1; q += THREADS) {
+        if (!(g.pflag[q] & kPairIns)) continue;
+        const int32_t j = (int32_t)(g.pkey[q] & 0xffffffffu);
+        const int32_t Dj = g.L[j];
+        const ST x = (Dj == C) ? ST(0) : gain<ST>(g.m2_of(u), ku, tbl_get(keys, vals, mask, Dj), eC, g.a[Dj], aC);
+        if (better3(x, Dj, j, S, D, J)) {
+          S = x;
+          D = Dj;
+          J = j;
+        }
+      }
+      warp_argmax3(S, D, J);
+      if (lane == 0) {
+        redS[wid] = S;
+        redD[wid] = D;
+        redJ[wid] = J;
+      }
+      __syncthreads();
+      S = lane < NW ? redS[lane] : gain_lowest<ST>();
+      D = lane < NW ? redD[lane] : INT_MAX;
+      J = lane < NW ? redJ[lane] : INT_MAX;
+      warp_argmax3(S, D, J);
+    }
+    if (tid == 0) {
+      g.jstar[idx] = J;
+      st_gain(&g.g1[2 * idx], S);
+      g.flags[idx] = (flags & 1) ? 1 : 0;
+    }
+    __syncthreads();
+  }
+}
+
 // ---- phase B: group the sources with gain1 > 0 by j* ----
 
 template <typename ST>
@@ -416,7 +482,7 @@ __global__ void close_groups(const uint64_t* __restrict__ keys, int64_t m, int64
 // groups binned by the degree of their j*
 __global__ void group_bins(const uint64_t* __restrict__ keys, const int32_t* __restrict__ gstart, int64_t ng,
                            const int64_t* __restrict__ rp, int32_t* __restrict__ cursor, int32_t* __restrict__ lists,
-                           int64_t cap_per_bin, unsigned long long* __restrict__ hub_max) {
+                           int64_t cap_per_bin) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (blockIdx.x * (int64_t)blockDim.x) + (threadIdx.x & ~31); base < ng; base += stride) {
     const int64_t gi = base + lane_id();
@@ -425,7 +491,6 @@ __global__ void group_bins(const uint64_t* __restrict__ keys, const int32_t* __r
       const int64_t j = (int64_t)keys[gstart[gi]];
       const int64_t deg = rp[j + 1] - rp[j];
       bin = deg <= kBinWarpMax ? 0 : deg <= kBinMidMax ? 1 : deg <= kBinLargeMax ? 2 : 3;
-      if (bin == 3) atomicMax(hub_max, (unsigned long long)deg);
     }
 #pragma unroll
     for (int b = 0; b < 4; b++) {
@@ -534,6 +599,32 @@ __global__ void __launch_bounds__(THREADS) scr_c_block(SV g, GroupView gv, int64
   }
 }
 
+// j* of each hub group (the vertex whose row hub_agg sums).
+__global__ void group_vertices(const uint64_t* __restrict__ keys, const int32_t* __restrict__ gstart,
+                               const int32_t* __restrict__ glist, int64_t cnt, int32_t* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (int32_t)keys[gstart[glist[i]]];
+}
+
+// Hub j* (rows above 4096 entries) summed into per-hub tables by hub_agg; one
+// CTA per group evaluates gain2 for its sources by lookups.
+template <typename ST, int THREADS>
+__global__ void __launch_bounds__(THREADS) scr_c_hub(SV g, GroupView gv, int64_t cnt, HubTables t) {
+  for (int64_t h = blockIdx.x; h < cnt; h += gridDim.x) {
+    const int32_t gi = gv.glist[h];
+    const int64_t m0 = gv.gstart[gi], m1 = gv.gstart[gi + 1];
+    const int32_t j = t.list[h];
+    const uint32_t mask = (uint32_t)(t.toff[h + 1] - t.toff[h]) - 1;
+    const int32_t* keys = t.keys + t.toff[h];
+    const unsigned long long* vals = t.vals + t.toff[h];
+    const int64_t e2 = tbl_get(keys, vals, mask, g.L[j]);
+    for (int64_t q = m0 + threadIdx.x; q < m1; q += THREADS) {
+      const int64_t idx = gv.vals[q];
+      decide<ST>(g, idx, j, tbl_get(keys, vals, mask, g.L[g.src[idx]]), e2);
+    }
+  }
+}
+
 // ---- phase D: marks ----
 // Sources [lo, hi) of the list, a warp each.
 __global__ void __launch_bounds__(256) scr_mark(SV g, int64_t lo, int64_t hi) {
@@ -582,8 +673,7 @@ __global__ void __launch_bounds__(256) scr_mark_hub(SV g, int64_t lo, int64_t hi
 
 // Sources (vertices with at least one pair) binned by their degree in G_t.
 __global__ void src_bins(int64_t n, const int64_t* __restrict__ pair_ptr, const int64_t* __restrict__ rp,
-                         int32_t* __restrict__ cursor, int32_t* __restrict__ lists, int64_t cap_per_bin,
-                         unsigned long long* __restrict__ hub_max) {
+                         int32_t* __restrict__ cursor, int32_t* __restrict__ lists, int64_t cap_per_bin) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (blockIdx.x * (int64_t)blockDim.x) + (threadIdx.x & ~31); base < n; base += stride) {
     const int64_t v = base + lane_id();
@@ -591,7 +681,6 @@ __global__ void src_bins(int64_t n, const int64_t* __restrict__ pair_ptr, const 
     if (v < n && pair_ptr[v + 1] > pair_ptr[v]) {
       const int64_t deg = rp[v + 1] - rp[v];
       bin = deg <= kBinWarpMax ? 0 : deg <= kBinMidMax ? 1 : deg <= kBinLargeMax ? 2 : 3;
-      if (bin == 3) atomicMax(hub_max, (unsigned long long)deg);
     }
 #pragma unroll
     for (int b = 0; b < 4; b++) {
@@ -632,24 +721,9 @@ __global__ void build_rset(int64_t n, const uint8_t* __restrict__ mark, const ui
   if (lane_id() == 0 && c) atomicAdd(count, c);
 }
 
-int hub_tables(dcd_ctx* c, int64_t count, int64_t maxdeg, Buf<int32_t>& k, Buf<unsigned long long>& v,
-               int64_t* cap, int64_t* ctas) {
-  *cap = 0;
-  *ctas = 0;
-  if (!count) return DCD_OK;
-  *cap = table_cap(maxdeg);
-  int64_t n = ((int64_t)1 << 30) / (*cap * 12);
-  if (n < 1) n = 1;
-  if (n > count) n = count;
-  if (n > 4 * (int64_t)c->sms) n = 4 * (int64_t)c->sms;
-  *ctas = n;
-  DCD_TRY(k.alloc(&c->mem, n * *cap));
-  DCD_TRY(v.alloc(&c->mem, n * *cap));
-  return DCD_OK;
-}
 
 template <typename ST>
-int screen_impl(dcd_ctx* c, SV& sv, const Csr<int32_t>& g, const int64_t* cnt, int64_t hub_max, int64_t nsrc) {
+int screen_impl(dcd_ctx* c, SV& sv, const Csr<int32_t>& g, const int64_t* cnt, int64_t nsrc) {
   cudaStream_t s = c->stream;
   const int T = 256;
   const int64_t n = g.n;
@@ -662,17 +736,18 @@ int screen_impl(dcd_ctx* c, SV& sv, const Csr<int32_t>& g, const int64_t* cnt, i
   const int sm2 = 2 * c->sms;
 
   // ---- A ----
-  Buf<int32_t> hk;
-  Buf<unsigned long long> hv;
-  int64_t hcap, hctas;
-  DCD_TRY(hub_tables(c, cnt[3], hub_max, hk, hv, &hcap, &hctas));
   if (cnt[0]) count_launch(), scr_a_warp<ST><<<grid_for(cnt[0] * 32, T, 16), T, 0, s>>>(sv, 0, cnt[0]);
   if (cnt[1]) count_launch(), scr_a_wtbl<ST><<<grid_for(cnt[1] * 32, T, 8), T, wsmem, s>>>(sv, off1, cnt[1]);
   if (cnt[2])
     count_launch(), scr_a_block<ST, 256><<<(unsigned)(cnt[2] < sm2 ? cnt[2] : sm2), 256, bsmem, s>>>(
                         sv, off2, cnt[2], nullptr, nullptr, 0);
-  if (cnt[3])
-    count_launch(), scr_a_block<ST, 512><<<(unsigned)hctas, 512, 0, s>>>(sv, off3, cnt[3], hk.get(), hv.get(), hcap);
+  if (cnt[3]) {
+    HubBufs hb;
+    DCD_TRY(hub_setup(c, sv.src + off3, cnt[3], g.rp, &hb));
+    count_launch(), hub_agg<int32_t, ST><<<hub_grid(c, hb), 256, 0, s>>>(sv, hb.t);
+    count_launch(), scr_a_hub<ST, 512><<<(unsigned)(cnt[3] < 4 * c->sms ? cnt[3] : 4 * c->sms), 512, 0, s>>>(
+                        sv, off3, cnt[3], hb.t);
+  }
   DCD_LAUNCH_CHECK();
 
   trace("screen: phase A");
@@ -709,29 +784,19 @@ int screen_impl(dcd_ctx* c, SV& sv, const Csr<int32_t>& g, const int64_t* cnt, i
     DCD_LAUNCH_CHECK();
     // end of the last group: number of candidate keys (< n)
     Buf<int32_t> gl, gcur;
-    Buf<unsigned long long> ghub;
     DCD_TRY(gl.alloc(&c->mem, 4 * ng));
     DCD_TRY(gcur.alloc(&c->mem, 4));
-    DCD_TRY(ghub.alloc(&c->mem, 1));
     DCD_TRY_CUDA(cudaMemsetAsync(gcur.get(), 0, 4 * sizeof(int32_t), s));
-    DCD_TRY_CUDA(cudaMemsetAsync(ghub.get(), 0, sizeof(unsigned long long), s));
-    count_launch(), group_bins<<<grid_for(ng, T), T, 0, s>>>(keys, gstart.get(), ng, g.rp, gcur.get(), gl.get(), ng,
-                                                             ghub.get());
+    count_launch(), group_bins<<<grid_for(ng, T), T, 0, s>>>(keys, gstart.get(), ng, g.rp, gcur.get(), gl.get(), ng);
     DCD_LAUNCH_CHECK();
     DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch, gcur.get(), 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch + 2, ghub.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     DCD_TRY_CUDA(cudaStreamSynchronize(s));
     const int32_t* gc = reinterpret_cast<const int32_t*>(c->hscratch);
     const int64_t gcnt[4] = {gc[0], gc[1], gc[2], gc[3]};
-    const int64_t ghubmax = c->hscratch[2];
     // gstart[ng] = number of candidates = lower bound of the sentinel key
     count_launch(), close_groups<<<1, 32, 0, s>>>(keys, nsrc, n, gstart.get() + ng);
     DCD_LAUNCH_CHECK();
     // ---- C ----
-    Buf<int32_t> ck;
-    Buf<unsigned long long> cv;
-    int64_t ccap, cctas;
-    DCD_TRY(hub_tables(c, gcnt[3], ghubmax, ck, cv, &ccap, &cctas));
     GroupView gv{keys, vals, gstart.get(), gl.get()};
     if (gcnt[0]) count_launch(), scr_c_warp<ST><<<grid_for(gcnt[0] * 32, T, 16), T, 0, s>>>(sv, gv, gcnt[0]);
     gv.glist = gl.get() + ng;
@@ -741,8 +806,17 @@ int screen_impl(dcd_ctx* c, SV& sv, const Csr<int32_t>& g, const int64_t* cnt, i
       count_launch(), scr_c_block<ST, 256><<<(unsigned)(gcnt[2] < sm2 ? gcnt[2] : sm2), 256, bsmem, s>>>(
                           sv, gv, gcnt[2], nullptr, nullptr, 0);
     gv.glist = gl.get() + 3 * ng;
-    if (gcnt[3])
-      count_launch(), scr_c_block<ST, 512><<<(unsigned)cctas, 512, 0, s>>>(sv, gv, gcnt[3], ck.get(), cv.get(), ccap);
+    if (gcnt[3]) {
+      Buf<int32_t> jl;
+      DCD_TRY(jl.alloc(&c->mem, gcnt[3]));
+      count_launch(), group_vertices<<<grid_for(gcnt[3], T), T, 0, s>>>(keys, gstart.get(), gv.glist, gcnt[3],
+                                                                        jl.get());
+      HubBufs hb;
+      DCD_TRY(hub_setup(c, jl.get(), gcnt[3], g.rp, &hb));
+      count_launch(), hub_agg<int32_t, ST><<<hub_grid(c, hb), 256, 0, s>>>(sv, hb.t);
+      count_launch(), scr_c_hub<ST, 512><<<(unsigned)(gcnt[3] < 4 * c->sms ? gcnt[3] : 4 * c->sms), 512, 0, s>>>(
+                          sv, gv, gcnt[3], hb.t);
+    }
     DCD_LAUNCH_CHECK();
   }
   trace("screen: phases B, C");
@@ -768,21 +842,15 @@ int screen_batch(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* labels0, cons
   DCD_TRY_CUDA(cudaMemsetAsync(cflag.get(), 0, n, s));
   if (mo.npairs > 0) {
     Buf<int32_t> lists, cursor, src;
-    Buf<unsigned long long> hubmax;
     DCD_TRY(lists.alloc(&c->mem, 4 * n));
     DCD_TRY(cursor.alloc(&c->mem, 4));
-    DCD_TRY(hubmax.alloc(&c->mem, 1));
     DCD_TRY_CUDA(cudaMemsetAsync(cursor.get(), 0, 4 * sizeof(int32_t), s));
-    DCD_TRY_CUDA(cudaMemsetAsync(hubmax.get(), 0, sizeof(unsigned long long), s));
-    count_launch(), src_bins<<<grid_for(n, T), T, 0, s>>>(n, mo.pair_ptr.get(), g.rp, cursor.get(), lists.get(), n,
-                                                          hubmax.get());
+    count_launch(), src_bins<<<grid_for(n, T), T, 0, s>>>(n, mo.pair_ptr.get(), g.rp, cursor.get(), lists.get(), n);
     DCD_LAUNCH_CHECK();
     DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch, cursor.get(), 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch + 2, hubmax.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     DCD_TRY_CUDA(cudaStreamSynchronize(s));
     const int32_t* cn = reinterpret_cast<const int32_t*>(c->hscratch);
     const int64_t cnt[4] = {cn[0], cn[1], cn[2], cn[3]};
-    const int64_t hub_max = c->hscratch[2];
     const int64_t nsrc = cnt[0] + cnt[1] + cnt[2] + cnt[3];
     DCD_TRY(src.alloc(&c->mem, nsrc));
     count_launch(), pack_bins<<<grid_for(nsrc, T), T, 0, s>>>(lists.get(), n, cnt[0], cnt[1], cnt[2], cnt[3], src.get());
@@ -799,8 +867,8 @@ int screen_batch(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* labels0, cons
     SV sv{g.rp, g.col, g.w, k, labels0, a, mo.pkey.get(), mo.pflag.get(), mo.pair_ptr.get(), c->hgs[0].m2,
           c->G > 1 ? c->gid.get() : nullptr, c->gs.get(), mark.get(), cflag.get(), src.get(), jstar.get(),
           g1.get(), flags.get()};
-    if (m2max >= ((int64_t)1 << 31)) DCD_TRY(screen_impl<i128>(c, sv, g, cnt, hub_max, nsrc));
-    else DCD_TRY(screen_impl<long long>(c, sv, g, cnt, hub_max, nsrc));
+    if (m2max >= ((int64_t)1 << 31)) DCD_TRY(screen_impl<i128>(c, sv, g, cnt, nsrc));
+    else DCD_TRY(screen_impl<long long>(c, sv, g, cnt, nsrc));
   }
   DCD_TRY_CUDA(cudaMemsetAsync(&d->r_size, 0, sizeof(int64_t), s));
   count_launch(), build_rset<<<grid_for(n, T), T, 0, s>>>(n, mark.get(), cflag.get(), labels0, rset,

@@ -174,6 +174,36 @@ def test_hub_vertex_uses_global_table(dcd, orc):
     run_stream(dcd, orc, s, dcd.MODE_DELTA, orc.DELTA)
 
 
+def test_several_hubs_over_steps(dcd, orc):
+    # three hubs of 6,000..21,000 entries (rows split over several CTAs) that
+    # are screening sources, j* of other sources and local-move vertices, over
+    # steps that insert at and delete from them
+    rng = np.random.default_rng(31)
+    n = 40_000
+    hubs = [7, 19_000, 33_333]
+    degs = [21_000, 12_000, 6_000]
+    ins = []
+    for h, d in zip(hubs, degs):
+        nb = rng.choice(n, size=d, replace=False)
+        ins += [(h, int(v), int(rng.integers(1, 5))) for v in nb if v != h]
+    ins += [(int(a), int(b), 1) for a, b in rng.integers(0, n, (60_000, 2)) if a != b]
+    ins += [(v, v + 1, 2) for v in range(0, n - 1, 3)]
+    ins = np.array(ins, np.int32)
+    steps = [(ins, np.zeros((0, 2), np.int32))]
+    for t in range(3):
+        add = [(hubs[t % 3], int(v), 1) for v in rng.integers(0, n, 2_500) if v != hubs[t % 3]]
+        add += [(int(a), int(b), 1) for a, b in rng.integers(0, n, (5_000, 2)) if a != b]
+        dels = ins[rng.choice(len(ins), size=1_500, replace=False), :2]
+        steps.append((np.array(add, np.int32), dels.copy()))
+
+    class S:
+        pass
+
+    s = S()
+    s.n, s.steps = n, steps
+    run_stream(dcd, orc, s, dcd.MODE_DELTA, orc.DELTA)
+
+
 def test_wide_gain_path(dcd, orc, synth):
     # weights near 2^20 push 2m above 2^31: the 128-bit gain path
     s = synth.sbm_10k(n=2000, blocks=20, steps=3)
