@@ -299,7 +299,7 @@ def gpu_arm(args):
     lm_bytes = BYTES_PER_ENTRY * edges + BYTES_PER_VERTEX * verts
     pass_gbs = lm_bytes / (lm_ms * 1e-3) / 1e9 if lm_ms > 0 else None
     # per degree-bin kernel: time, algorithmic bytes, achieved GB/s
-    names = ["lm_warp (degree <= 32)", "lm_warp_tbl (33..256)", "lm_large (257..4096)", "lm_block hub (> 4096)"]
+    names = ["lm_warp (degree <= 32)", "lm_warp_tbl (33..256)", "lm_large (257..4096)", "hub_agg + hub_gain + hub_pick (> 4096)"]
     bins = []
     for b in range(4):
         ms_b = sum(st.ms_bin[b] for st in stats)
