@@ -175,8 +175,9 @@ __device__ __forceinline__ void tbl_add(int32_t* keys, unsigned long long* vals,
 // tbl_add that also appends each newly claimed slot to slots[] (counter *ns),
 // so the distinct keys can be visited, and the table emptied again, without a
 // scan over the whole capacity.
-__device__ __forceinline__ void tbl_add_list(int32_t* keys, unsigned long long* vals, uint16_t* slots, int32_t* ns,
-                                             uint32_t mask, int32_t lab, unsigned long long x) {
+template <typename VT>
+__device__ __forceinline__ void tbl_add_list(int32_t* keys, VT* vals, uint16_t* slots, int32_t* ns, uint32_t mask,
+                                             int32_t lab, VT x) {
   uint32_t s = hash_label(lab, mask);
   for (;;) {
     int32_t k = keys[s];
@@ -196,8 +197,8 @@ __device__ __forceinline__ void tbl_add_list(int32_t* keys, unsigned long long* 
   }
 }
 
-__device__ __forceinline__ int64_t tbl_get(const int32_t* keys, const unsigned long long* vals, uint32_t mask,
-                                           int32_t lab) {
+template <typename VT>
+__device__ __forceinline__ int64_t tbl_get(const int32_t* keys, const VT* vals, uint32_t mask, int32_t lab) {
   uint32_t s = hash_label(lab, mask);
   for (;;) {
     int32_t k = keys[s];
@@ -206,6 +207,18 @@ __device__ __forceinline__ int64_t tbl_get(const int32_t* keys, const unsigned l
     s = (s + 1) & mask;
   }
 }
+
+// Width of the shared-table sums: with 64-bit gains 2m < 2^31 bounds every
+// sum of a vertex's weights, so 32 bits hold them exactly (smaller tables,
+// more warps per SM); with 128-bit gains the sums are 64-bit.
+template <typename ST>
+struct TblVal {
+  using type = unsigned long long;
+};
+template <>
+struct TblVal<long long> {
+  using type = unsigned;
+};
 
 __host__ __device__ __forceinline__ uint32_t table_cap(int64_t deg) {
   uint32_t c = 64;

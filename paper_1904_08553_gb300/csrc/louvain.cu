@@ -165,9 +165,10 @@ __global__ void __launch_bounds__(256) lm_warp(LV<W> g, const int32_t* __restric
 // the gain step visits only the distinct communities and then empties
 // exactly the slots it used: the table is cleared once per kernel, not once
 // per vertex.
-template <int CAP>
+template <int CAP, typename VT>
 __host__ __device__ constexpr size_t warp_tbl_bytes() {
-  return (size_t)CAP * 12 + (size_t)CAP + 16;  // values, keys, slot list (CAP / 2 entries of 2 bytes), count
+  // values, keys, slot list (CAP / 2 entries of 2 bytes), count; 8-byte aligned
+  return ((size_t)CAP * (sizeof(VT) + 4) + (size_t)CAP + 16 + 7) / 8 * 8;
 }
 
 template <typename W, typename ST, int CAP, int Q>
@@ -176,11 +177,12 @@ __global__ void __launch_bounds__(256) lm_warp_tbl(LV<W> g, const int32_t* __res
   static_assert(CAP == 64 * Q, "table of twice the largest row");
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = lane_id(), wib = threadIdx.x >> 5;
-  unsigned char* base = smem + (size_t)wib * warp_tbl_bytes<CAP>();
-  unsigned long long* vals = reinterpret_cast<unsigned long long*>(base);
-  int32_t* keys = reinterpret_cast<int32_t*>(base + (size_t)CAP * 8);
-  uint16_t* slots = reinterpret_cast<uint16_t*>(base + (size_t)CAP * 12);
-  int32_t* nslot = reinterpret_cast<int32_t*>(base + (size_t)CAP * 13);
+  using VT = typename TblVal<ST>::type;
+  unsigned char* base = smem + (size_t)wib * warp_tbl_bytes<CAP, VT>();
+  VT* vals = reinterpret_cast<VT*>(base);
+  int32_t* keys = reinterpret_cast<int32_t*>(base + (size_t)CAP * sizeof(VT));
+  uint16_t* slots = reinterpret_cast<uint16_t*>(base + (size_t)CAP * (sizeof(VT) + 4));
+  int32_t* nslot = reinterpret_cast<int32_t*>(base + (size_t)CAP * (sizeof(VT) + 5));
   for (int s = lane; s < CAP; s += 32) {
     keys[s] = -1;
     vals[s] = 0;
@@ -217,7 +219,7 @@ __global__ void __launch_bounds__(256) lm_warp_tbl(LV<W> g, const int32_t* __res
         const unsigned peers = __match_any_sync(0xffffffffu, lab[q]);
         const int64_t sum = group_sum<ST>(peers, lab[q] >= 0 ? wt[q] : W(0));
         if (lab[q] >= 0 && (int)(__ffs(peers) - 1) == lane)
-          tbl_add_list(keys, vals, slots, nslot, mask, lab[q], (unsigned long long)sum);
+          tbl_add_list<VT>(keys, vals, slots, nslot, mask, lab[q], (VT)sum);
       }
     }
     __syncwarp();
@@ -277,9 +279,10 @@ __global__ void __launch_bounds__(THREADS) lm_large(LV<W> g, const int32_t* __re
   __shared__ int32_t redD[NW];
   __shared__ long long s_eC;
   __shared__ int32_t s_n;
-  unsigned long long* vals = reinterpret_cast<unsigned long long*>(smem);
-  int32_t* keys = reinterpret_cast<int32_t*>(smem + (size_t)tcap * 8);
-  uint16_t* slots = reinterpret_cast<uint16_t*>(smem + (size_t)tcap * 12);
+  using VT = typename TblVal<ST>::type;
+  VT* vals = reinterpret_cast<VT*>(smem);
+  int32_t* keys = reinterpret_cast<int32_t*>(smem + (size_t)tcap * sizeof(VT));
+  uint16_t* slots = reinterpret_cast<uint16_t*>(smem + (size_t)tcap * (sizeof(VT) + 4));
   const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5;
   for (int s = tid; s < tcap; s += THREADS) {
     keys[s] = -1;
@@ -319,7 +322,7 @@ __global__ void __launch_bounds__(THREADS) lm_large(LV<W> g, const int32_t* __re
         const unsigned peers = __match_any_sync(0xffffffffu, lab[q]);
         const int64_t sum = group_sum<ST>(peers, lab[q] >= 0 ? wt[q] : W(0));
         if (lab[q] >= 0 && (int)(__ffs(peers) - 1) == lane)
-          tbl_add_list(keys, vals, slots, &s_n, mask, lab[q], (unsigned long long)sum);
+          tbl_add_list<VT>(keys, vals, slots, &s_n, mask, lab[q], (VT)sum);
       }
     }
     __syncthreads();
@@ -1131,7 +1134,7 @@ int make_bins(dcd_ctx* c, const Csr<W>& g, const uint8_t* active, Bins* b, const
 template <typename W, typename ST, int CAP, int Q>
 int launch_warp_tbl(dcd_ctx* c, const LV<W>& g, const int32_t* lst, int64_t cnt, int32_t* prop) {
   constexpr int T = 256;
-  constexpr size_t smem = (size_t)(T / 32) * warp_tbl_bytes<CAP>();
+  constexpr size_t smem = (size_t)(T / 32) * warp_tbl_bytes<CAP, typename TblVal<ST>::type>();
   count_launch(), lm_warp_tbl<W, ST, CAP, Q><<<grid_for(cnt * 32, T, 8), T, smem, c->stream>>>(g, lst, cnt, prop);
   return DCD_OK;
 }
@@ -1139,7 +1142,7 @@ int launch_warp_tbl(dcd_ctx* c, const LV<W>& g, const int32_t* lst, int64_t cnt,
 template <typename W, typename ST, int THREADS, int Q>
 int launch_large(dcd_ctx* c, const LV<W>& g, const int32_t* lst, int64_t cnt, int64_t maxd, int32_t* prop) {
   const int32_t tcap = (int32_t)table_cap(maxd);
-  const size_t smem = (size_t)tcap * 14;  // values, keys, claimed-slot list
+  const size_t smem = (size_t)tcap * (sizeof(typename TblVal<ST>::type) + 6);  // values, keys, claimed-slot list
   const int64_t ctas = cnt < 16 * (int64_t)c->sms ? cnt : 16 * (int64_t)c->sms;
   count_launch(), lm_large<W, ST, THREADS, Q><<<(unsigned)ctas, THREADS, smem, c->stream>>>(g, lst, cnt, prop, tcap);
   return DCD_OK;
@@ -1151,17 +1154,17 @@ template <typename W, typename ST>
 int prepare_lm_st() {
   constexpr int T = 256;
   DCD_TRY_CUDA(cudaFuncSetAttribute(lm_warp_tbl<W, ST, 256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)((T / 32) * warp_tbl_bytes<256>())));
+                                    (int)((T / 32) * warp_tbl_bytes<256, typename TblVal<ST>::type>())));
   DCD_TRY_CUDA(cudaFuncSetAttribute(lm_warp_tbl<W, ST, 512, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)((T / 32) * warp_tbl_bytes<512>())));
+                                    (int)((T / 32) * warp_tbl_bytes<512, typename TblVal<ST>::type>())));
   DCD_TRY_CUDA(cudaFuncSetAttribute(lm_large<W, ST, 256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(table_cap(512) * 14)));
+                                    (int)(table_cap(512) * (sizeof(typename TblVal<ST>::type) + 6))));
   DCD_TRY_CUDA(cudaFuncSetAttribute(lm_large<W, ST, 256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(table_cap(1024) * 14)));
+                                    (int)(table_cap(1024) * (sizeof(typename TblVal<ST>::type) + 6))));
   DCD_TRY_CUDA(cudaFuncSetAttribute(lm_large<W, ST, 256, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(table_cap(2048) * 14)));
+                                    (int)(table_cap(2048) * (sizeof(typename TblVal<ST>::type) + 6))));
   DCD_TRY_CUDA(cudaFuncSetAttribute(lm_large<W, ST, 512, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(table_cap(4096) * 14)));
+                                    (int)(table_cap(4096) * (sizeof(typename TblVal<ST>::type) + 6))));
   return DCD_OK;
 }
 
