@@ -503,8 +503,9 @@ int dcd::update_impl(dcd_ctx* c, dcd_step_stats* st, dcd_step_stats* per_graph) 
   // ---- Algorithm 1 with R_t at level 0 ----
   DCD_TRY(c->labels_nx.ensure(&c->mem, n));
   if (collect) DCD_TRY(c->level0.ensure(&c->mem, n));
+  // the screening's community sums are those of C_{t-1} on G_t, the start of level 0
   DCD_TRY(run_louvain(c, g, L0.get(), active, mo.k, c->labels_nx.get(), st, collect ? c->level0.get() : nullptr,
-                      per_graph));
+                      per_graph, a.n ? a.get() : nullptr, size.n ? size.get() : nullptr));
   if (collect) DCD_TRY(screen_labels(c, src_labels, c->level0.get()));
   if (learned && c->judge && st) {
     // the judge: plain Delta-screening from the same state; keep it when the

@@ -818,8 +818,26 @@ __global__ void bin_scatter(const int64_t* __restrict__ rp, int64_t n, const uin
 
 // ---------------------------------------------------------------- sums
 
-__global__ void comm_sums(int64_t n, const int32_t* __restrict__ L, const int64_t* __restrict__ k,
-                          unsigned long long* __restrict__ a, int32_t* __restrict__ size) {
+// a_C and |C| of every label: each warp groups its 32 vertices by label,
+// each CTA adds the group sums into a shared table (labels of a CTA repeat
+// heavily when communities are large), and the table goes to global memory
+// once per CTA; labels that find no slot within a few probes go there
+// directly.
+constexpr int kCsSlots = 2048;
+constexpr int kCsThreads = 1024;
+
+__global__ void __launch_bounds__(kCsThreads) comm_sums(int64_t n, const int32_t* __restrict__ L,
+                                                        const int64_t* __restrict__ k,
+                                                        unsigned long long* __restrict__ a, int32_t* __restrict__ size) {
+  __shared__ int32_t tk[kCsSlots];
+  __shared__ int32_t tc[kCsSlots];
+  __shared__ unsigned long long tv[kCsSlots];
+  for (int x = threadIdx.x; x < kCsSlots; x += blockDim.x) {
+    tk[x] = -1;
+    tc[x] = 0;
+    tv[x] = 0;
+  }
+  __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (blockIdx.x * (int64_t)blockDim.x) + (threadIdx.x & ~31); base < n; base += stride) {
     const int64_t v = base + lane_id();
@@ -828,10 +846,34 @@ __global__ void comm_sums(int64_t n, const int32_t* __restrict__ L, const int64_
     const unsigned peers = __match_any_sync(0xffffffffu, c);
     const int64_t sk = group_sum_exact(peers, kv);
     if (c >= 0 && (int)(__ffs(peers) - 1) == (int)lane_id()) {
-      atomicAdd(&a[c], (unsigned long long)sk);
-      atomicAdd(&size[c], __popc(peers));
+      uint32_t sl = hash_label(c, kCsSlots - 1);
+      bool done = false;
+      for (int probe = 0; probe < 8 && !done; probe++) {
+        const int32_t key = tk[sl];
+        if (key == c) {
+          done = true;
+        } else if (key == -1) {
+          const int32_t old = atomicCAS(&tk[sl], -1, c);
+          done = old == -1 || old == c;
+        }
+        if (done) {
+          atomicAdd(&tv[sl], (unsigned long long)sk);
+          atomicAdd(&tc[sl], __popc(peers));
+        }
+        sl = (sl + 1) & (kCsSlots - 1);
+      }
+      if (!done) {
+        atomicAdd(&a[c], (unsigned long long)sk);
+        atomicAdd(&size[c], __popc(peers));
+      }
     }
   }
+  __syncthreads();
+  for (int x = threadIdx.x; x < kCsSlots; x += blockDim.x)
+    if (tk[x] >= 0) {
+      atomicAdd(&a[tk[x]], tv[x]);
+      atomicAdd(&size[tk[x]], tc[x]);
+    }
 }
 
 __global__ void fill_iota(int32_t* __restrict__ x, int64_t n) {
@@ -1643,13 +1685,15 @@ int community_sums(dcd_ctx* c, int64_t n, const int32_t* labels, const int64_t* 
   cudaStream_t s = c->stream;
   DCD_TRY_CUDA(cudaMemsetAsync(a, 0, n * sizeof(int64_t), s));
   DCD_TRY_CUDA(cudaMemsetAsync(size, 0, n * sizeof(int32_t), s));
-  ::dcd::count_launch(), comm_sums<<<grid_for(n, 256), 256, 0, s>>>(n, labels, k, (unsigned long long*)a, size);
+  ::dcd::count_launch(), comm_sums<<<grid_for(n, kCsThreads, 2), kCsThreads, 0, s>>>(n, labels, k,
+                                                                                   (unsigned long long*)a, size);
   DCD_LAUNCH_CHECK();
   return DCD_OK;
 }
 
 int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint8_t* active0, Buf<int64_t>& k0,
-                int32_t* out_labels, dcd_step_stats* st, int32_t* level0_out, dcd_step_stats* per_graph) {
+                int32_t* out_labels, dcd_step_stats* st, int32_t* level0_out, dcd_step_stats* per_graph,
+                const int64_t* a0, const int32_t* size0) {
   cudaStream_t s = c->stream;
   GraphState* gs = c->gs.get();
   const int G = c->G;
@@ -1663,7 +1707,12 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
   DCD_TRY(a.alloc(&c->mem, n0));
   DCD_TRY(size.alloc(&c->mem, n0));
   DCD_TRY(comp.alloc(&c->mem, n0));
-  DCD_TRY(community_sums(c, n0, labels0, k0.get(), a.get(), size.get()));
+  if (a0 && size0) {
+    DCD_TRY_CUDA(cudaMemcpyAsync(a.get(), a0, n0 * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    DCD_TRY_CUDA(cudaMemcpyAsync(size.get(), size0, n0 * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  } else {
+    DCD_TRY(community_sums(c, n0, labels0, k0.get(), a.get(), size.get()));
+  }
   ::dcd::count_launch(), fill_iota<<<grid_for(n0, T), T, 0, s>>>(comp.get(), n0);
   ::dcd::count_launch(), gs_reset_pass<<<cdiv(G, 128), 128, 0, s>>>(gs, G, &c->dsc.get()->pass_id);
   ::dcd::count_launch(), sumsq_acc<<<grid_for(n0, T, 4), T, 0, s>>>(a.get(), n0, gid0, gs);

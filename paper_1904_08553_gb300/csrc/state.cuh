@@ -217,9 +217,10 @@ int screen_batch(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* labels0, cons
 // louvain.cu: Algorithm 1 from level-0 labels (modified in place into the
 // level-0 result), level-0 active flags (NULL = all), k and m2 of G_t.
 // Writes canonical labels to out_labels and fills stats.
+// a0 / size0 (may be NULL): community sums of labels0, when the caller has them.
 int run_louvain(dcd_ctx* c, const Csr<int32_t>& g, int32_t* labels0, const uint8_t* active0,
                 Buf<int64_t>& k, int32_t* out_labels, dcd_step_stats* st, int32_t* level0_out = nullptr,
-                dcd_step_stats* per_graph = nullptr);
+                dcd_step_stats* per_graph = nullptr, const int64_t* a0 = nullptr, const int32_t* size0 = nullptr);
 
 // louvain.cu: statistics of the learned screen's pool (mask over vertices):
 // the local-move evaluation of every pool vertex of positive degree, without
