@@ -890,7 +890,7 @@ __global__ void fill_i32(int32_t* __restrict__ x, int64_t n, int32_t val) {
 
 __global__ void mark_used(int64_t n, const int32_t* __restrict__ L, int32_t* __restrict__ used) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-    used[L[v]] = 1;
+    if (!used[L[v]]) used[L[v]] = 1;  // a read first: most labels are already marked
 }
 
 // Coarse entries, aggregated on the fly.  Warps walk the fine CSR entry by
@@ -1078,7 +1078,10 @@ __global__ void final_min(int64_t n0, const int32_t* __restrict__ comp, const in
     const int32_t c = v < n0 ? L[comp[v]] : -1;
     const unsigned peers = __match_any_sync(0xffffffffu, c);
     const unsigned mn = __reduce_min_sync(peers, v < n0 ? (unsigned)v : 0xffffffffu);
-    if (c >= 0 && (int)(__ffs(peers) - 1) == (int)lane_id()) atomicMin(&minid[c], (int32_t)mn);
+    // labels of large communities repeat across the grid: read first, and
+    // only a smaller id pays for the atomic
+    if (c >= 0 && (int)(__ffs(peers) - 1) == (int)lane_id() && (int32_t)mn < minid[c])
+      atomicMin(&minid[c], (int32_t)mn);
   }
 }
 

@@ -265,7 +265,7 @@ __device__ __forceinline__ int64_t group_sum(int64_t x) {
 // plus the added pairs that sort before it; an added pair lands after the old
 // entries below it, corrected the same way.
 template <int G>
-__global__ void __launch_bounds__(256) merge_rows(
+__global__ void __launch_bounds__(256, 5) merge_rows(
     int64_t n, const int64_t* __restrict__ rp_o, const int32_t* __restrict__ col_o, const int32_t* __restrict__ w_o,
     const int64_t* __restrict__ rp_n, int32_t* __restrict__ col_n, int32_t* __restrict__ w_n,
     const int64_t* __restrict__ pair_ptr, const uint64_t* __restrict__ pkey, const int64_t* __restrict__ pw,
