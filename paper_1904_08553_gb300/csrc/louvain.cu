@@ -905,7 +905,14 @@ constexpr int64_t kSegEntries = 1024;
 // entry by binary search, then advances 32 entries at a time with the row
 // ends of the next 32 rows in its lanes.
 struct RowWalk {
-  int64_t r;  // row of the chunk's first entry
+  int64_t r;     // row of the chunk's first entry
+  int64_t rb;    // lane i holds the end of row rb + i (valid while chunks stay below `last`)
+  int64_t bk, last;
+  __device__ __forceinline__ void load(const int64_t* __restrict__ rp, int64_t n, int64_t r0) {
+    rb = r0;
+    bk = (r0 + 1 + lane_id() <= n) ? rp[r0 + 1 + lane_id()] : INT64_MAX;
+    last = __shfl_sync(0xffffffffu, bk, 31);
+  }
   __device__ __forceinline__ void start(const int64_t* __restrict__ rp, int64_t n, int64_t E0) {
     int64_t x = 0;
     if (lane_id() == 0) {  // last row whose start is <= E0
@@ -917,13 +924,15 @@ struct RowWalk {
       x = lo;
     }
     r = __shfl_sync(0xffffffffu, x, 0);
+    load(rp, n, r);
   }
-  // row of entry c0 + lane (entries past the segment get the last row)
+  // row of entry c0 + lane (entries past the segment get the last row); the
+  // ends of 32 rows stay in the lanes across chunks and are reloaded only when
+  // a chunk runs past them
   __device__ __forceinline__ int64_t row(const int64_t* __restrict__ rp, int64_t n, int64_t c0, bool valid) {
     const int lane = lane_id();
     const int64_t e = c0 + lane;
-    const int64_t bk = (r + 1 + lane <= n) ? rp[r + 1 + lane] : INT64_MAX;  // end of row r + lane
-    const int64_t last = __shfl_sync(0xffffffffu, bk, 31);
+    if (last <= c0 + 31) load(rp, n, r);
     int64_t rw;
     if (last <= c0 + 31) {
       // more than 31 rows end inside this chunk (empty rows): search per lane
@@ -941,7 +950,7 @@ struct RowWalk {
         const int64_t v = __shfl_sync(0xffffffffu, bk, cntv + step - 1);
         if (v <= x) cntv += step;
       }
-      rw = r + cntv;
+      rw = rb + cntv;
     }
     r = __shfl_sync(0xffffffffu, rw, 31);
     return rw;
@@ -957,7 +966,28 @@ __global__ void __launch_bounds__(256) emit_coarse(int64_t n, int64_t m, const i
                                                    const int32_t* __restrict__ ccid,
                                                    uint64_t nc, uint64_t* __restrict__ keys,
                                                    uint64_t* __restrict__ vals, unsigned long long* __restrict__ count) {
-  const int lane = lane_id();
+  // each warp stages its (key, sum) pairs in shared memory and reserves room
+  // in the output once per kEmitBuf - 32 pairs, not once per chunk (the one
+  // output counter is otherwise hit by every chunk of the graph)
+  constexpr int kEmitBuf = 256;
+  __shared__ uint64_t sbk[8][kEmitBuf];
+  __shared__ uint64_t sbv[8][kEmitBuf];
+  const int lane = lane_id(), wib = threadIdx.x >> 5;
+  uint64_t* bk = sbk[wib];
+  uint64_t* bv = sbv[wib];
+  int nb = 0;
+  auto flush = [&]() {
+    __syncwarp();
+    unsigned long long slot = 0;
+    if (lane == 0 && nb) slot = atomicAdd(count, (unsigned long long)nb);
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    for (int x = lane; x < nb; x += 32) {
+      keys[slot + x] = bk[x];
+      vals[slot + x] = bv[x];
+    }
+    __syncwarp();
+    nb = 0;
+  };
   const int64_t nseg = cdiv(m, kSegEntries);
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t sg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sg < nseg; sg += nw) {
@@ -977,16 +1007,16 @@ __global__ void __launch_bounds__(256) emit_coarse(int64_t n, int64_t m, const i
       const int64_t sum = NARROW ? (int64_t)__reduce_add_sync(peers, (unsigned)wt) : group_sum_exact(peers, wt);
       const bool lead = valid && (int)(__ffs(peers) - 1) == lane;
       const unsigned bal = __ballot_sync(0xffffffffu, lead);
-      unsigned long long slot = 0;
-      if (lane == 0 && bal) slot = atomicAdd(count, (unsigned long long)__popc(bal));
-      slot = __shfl_sync(0xffffffffu, slot, 0);
       if (lead) {
-        const unsigned long long pos = slot + __popc(bal & lanemask_lt());
-        keys[pos] = key;
-        vals[pos] = (uint64_t)sum;
+        const int pos = nb + __popc(bal & lanemask_lt());
+        bk[pos] = key;
+        bv[pos] = (uint64_t)sum;
       }
+      nb += __popc(bal);
+      if (nb > kEmitBuf - 32) flush();
     }
   }
+  flush();
 }
 
 // coarse vertex of every vertex: cid of its label (one gather per entry in the
