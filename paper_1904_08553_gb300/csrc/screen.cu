@@ -155,17 +155,47 @@ __device__ __forceinline__ int64_t lane_get_each(const LaneRow& r, int32_t D, bo
   return out;
 }
 
-// Row v aggregated into a table by NT cooperating threads (tid in [0, NT)).
-// The caller synchronises (warp or CTA) before and after.
-__device__ __forceinline__ void table_clear(int32_t* keys, unsigned long long* vals, uint32_t cap, int tid, int NT) {
-  for (uint32_t s = tid; s < cap; s += NT) {
-    keys[s] = -1;
-    vals[s] = 0;
-  }
+// A shared table (keys, sums) with the list of the slots it claimed; empty
+// between uses: it is cleared once when a kernel starts and afterwards only
+// the listed slots are emptied, so a row costs its own entries, not the
+// table's capacity.  VT: 32-bit sums on the 64-bit gain path (2m < 2^31).
+template <typename VT>
+struct SlotTable {
+  int32_t* keys;
+  VT* vals;
+  uint16_t* slots;
+  int32_t* ns;
+};
+
+template <typename VT>
+__device__ __forceinline__ SlotTable<VT> slot_table(unsigned char* base, int cap) {
+  SlotTable<VT> t;
+  t.vals = reinterpret_cast<VT*>(base);
+  t.keys = reinterpret_cast<int32_t*>(base + (size_t)cap * sizeof(VT));
+  t.slots = reinterpret_cast<uint16_t*>(base + (size_t)cap * (sizeof(VT) + 4));
+  t.ns = reinterpret_cast<int32_t*>(base + (size_t)cap * (sizeof(VT) + 6));
+  return t;
+}
+template <typename VT>
+__host__ __device__ constexpr size_t slot_table_bytes(int cap) {
+  return ((size_t)cap * (sizeof(VT) + 6) + 16 + 7) / 8 * 8;
 }
 
-__device__ __forceinline__ void table_fill(const SV& g, int32_t v, int32_t* keys, unsigned long long* vals,
-                                           uint32_t mask, int tid, int NT) {
+// The whole table empty (NT threads, tid in [0, NT)); the caller synchronises.
+template <typename VT>
+__device__ __forceinline__ void slot_table_init(const SlotTable<VT>& t, int cap, int tid, int NT) {
+  for (int x = tid; x < cap; x += NT) {
+    t.keys[x] = -1;
+    t.vals[x] = 0;
+  }
+  if (tid == 0) *t.ns = 0;
+}
+
+// Row v added into t by NT cooperating threads (whole warps); the caller
+// synchronises before and after.
+template <typename ST, typename VT>
+__device__ __forceinline__ void slot_table_fill(const SV& g, int32_t v, const SlotTable<VT>& t, uint32_t mask, int tid,
+                                                int NT) {
   const int64_t b = g.rp[v];
   const int64_t d = g.rp[v + 1] - b;
   for (int64_t e0 = 0; e0 < d; e0 += NT) {
@@ -176,8 +206,21 @@ __device__ __forceinline__ void table_fill(const SV& g, int32_t v, int32_t* keys
     const int32_t lab = valid ? g.L[y] : -1;
     const int32_t wt = valid ? g.w[b + e] : 0;
     const unsigned peers = __match_any_sync(0xffffffffu, lab);
-    const int64_t sum = group_sum_exact(peers, wt);
-    if (valid && (int)(__ffs(peers) - 1) == (int)lane_id()) tbl_add(keys, vals, mask, lab, (unsigned long long)sum);
+    const int64_t sum = group_sum<ST>(peers, wt);
+    if (valid && (int)(__ffs(peers) - 1) == (int)lane_id())
+      tbl_add_list<VT>(t.keys, t.vals, t.slots, t.ns, mask, lab, (VT)sum);
+  }
+}
+
+// Empty the listed slots (after a synchronisation that ends the table's reads);
+// the count is reset by thread 0 after the next synchronisation.
+template <typename VT>
+__device__ __forceinline__ void slot_table_clear(const SlotTable<VT>& t, int tid, int NT) {
+  const int nd = *t.ns;
+  for (int x = tid; x < nd; x += NT) {
+    const uint32_t sl = t.slots[x];
+    t.keys[sl] = -1;
+    t.vals[sl] = 0;
   }
 }
 
@@ -253,11 +296,12 @@ __global__ void __launch_bounds__(256) scr_a_warp(SV g, int64_t off, int64_t cnt
 // Sources of degree 33..256: one warp with a warp-private shared table.
 template <typename ST>
 __global__ void __launch_bounds__(256) scr_a_wtbl(SV g, int64_t off, int64_t cnt) {
+  using VT = typename TblVal<ST>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = lane_id(), wib = threadIdx.x >> 5;
-  unsigned long long* vals = reinterpret_cast<unsigned long long*>(smem) + (size_t)wib * kMidCap;
-  int32_t* keys = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned long long*>(smem) + 8 * kMidCap) +
-                  (size_t)wib * kMidCap;
+  const SlotTable<VT> t = slot_table<VT>(smem + (size_t)wib * slot_table_bytes<VT>(kMidCap), kMidCap);
+  slot_table_init(t, kMidCap, lane, 32);
+  __syncwarp();
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < cnt; i += nw) {
     const int64_t idx = off + i;
@@ -270,12 +314,10 @@ __global__ void __launch_bounds__(256) scr_a_wtbl(SV g, int64_t off, int64_t cnt
     int32_t J = -1;
     ST S = 0;
     if (has_ins) {
-      const uint32_t cap = table_cap(g.rp[u + 1] - g.rp[u]), mask = cap - 1;
-      table_clear(keys, vals, cap, lane, 32);
+      const uint32_t mask = table_cap(g.rp[u + 1] - g.rp[u]) - 1;
+      slot_table_fill<ST, VT>(g, u, t, mask, lane, 32);
       __syncwarp();
-      table_fill(g, u, keys, vals, mask, lane, 32);
-      __syncwarp();
-      const int64_t eC = tbl_get(keys, vals, mask, C);
+      const int64_t eC = tbl_get(t.keys, t.vals, mask, C);
       const int64_t ku = g.k[u], aC = g.a[C];
       int32_t D = INT_MAX;
       J = INT_MAX;
@@ -284,7 +326,7 @@ __global__ void __launch_bounds__(256) scr_a_wtbl(SV g, int64_t off, int64_t cnt
         if (!(g.pflag[q] & kPairIns)) continue;
         const int32_t j = (int32_t)(g.pkey[q] & 0xffffffffu);
         const int32_t Dj = g.L[j];
-        const ST x = (Dj == C) ? ST(0) : gain<ST>(g.m2_of(u), ku, tbl_get(keys, vals, mask, Dj), eC, g.a[Dj], aC);
+        const ST x = (Dj == C) ? ST(0) : gain<ST>(g.m2_of(u), ku, tbl_get(t.keys, t.vals, mask, Dj), eC, g.a[Dj], aC);
         if (better3(x, Dj, j, S, D, J)) {
           S = x;
           D = Dj;
@@ -292,6 +334,10 @@ __global__ void __launch_bounds__(256) scr_a_wtbl(SV g, int64_t off, int64_t cnt
         }
       }
       warp_argmax3(S, D, J);
+      __syncwarp();
+      slot_table_clear(t, lane, 32);
+      __syncwarp();
+      if (lane == 0) *t.ns = 0;
       __syncwarp();
     }
     if (lane == 0) {
@@ -305,14 +351,17 @@ __global__ void __launch_bounds__(256) scr_a_wtbl(SV g, int64_t off, int64_t cnt
 // Sources above 256 entries: one CTA, table in shared memory (<= 4096
 // entries) or in a per-CTA region of global memory.
 template <typename ST, int THREADS>
-__global__ void __launch_bounds__(THREADS) scr_a_block(SV g, int64_t off, int64_t cnt, int32_t* __restrict__ gkeys,
-                                                       unsigned long long* __restrict__ gvals, int64_t gcap) {
+__global__ void __launch_bounds__(THREADS) scr_a_block(SV g, int64_t off, int64_t cnt, int cap) {
+  using VT = typename TblVal<ST>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NW = THREADS / 32;
   __shared__ ST redS[NW];
   __shared__ int32_t redD[NW], redJ[NW];
   __shared__ int s_flags;
   const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5;
+  const SlotTable<VT> t = slot_table<VT>(smem, cap);
+  slot_table_init(t, cap, tid, THREADS);
+  __syncthreads();
   for (int64_t i = blockIdx.x; i < cnt; i += gridDim.x) {
     const int64_t idx = off + i;
     const int32_t u = g.src[idx];
@@ -328,21 +377,10 @@ __global__ void __launch_bounds__(THREADS) scr_a_block(SV g, int64_t off, int64_
     int32_t J = -1;
     ST S = 0;
     if (flags & 2) {
-      const uint32_t cap = table_cap(g.rp[u + 1] - g.rp[u]), mask = cap - 1;
-      int32_t* keys;
-      unsigned long long* vals;
-      if (gcap == 0) {
-        vals = reinterpret_cast<unsigned long long*>(smem);
-        keys = reinterpret_cast<int32_t*>(smem + (size_t)cap * sizeof(unsigned long long));
-      } else {
-        keys = gkeys + (int64_t)blockIdx.x * gcap;
-        vals = gvals + (int64_t)blockIdx.x * gcap;
-      }
-      table_clear(keys, vals, cap, tid, THREADS);
+      const uint32_t mask = table_cap(g.rp[u + 1] - g.rp[u]) - 1;
+      slot_table_fill<ST, VT>(g, u, t, mask, tid, THREADS);
       __syncthreads();
-      table_fill(g, u, keys, vals, mask, tid, THREADS);
-      __syncthreads();
-      const int64_t eC = tbl_get(keys, vals, mask, C);
+      const int64_t eC = tbl_get(t.keys, t.vals, mask, C);
       const int64_t ku = g.k[u], aC = g.a[C];
       int32_t D = INT_MAX;
       J = INT_MAX;
@@ -351,7 +389,7 @@ __global__ void __launch_bounds__(THREADS) scr_a_block(SV g, int64_t off, int64_
         if (!(g.pflag[q] & kPairIns)) continue;
         const int32_t j = (int32_t)(g.pkey[q] & 0xffffffffu);
         const int32_t Dj = g.L[j];
-        const ST x = (Dj == C) ? ST(0) : gain<ST>(g.m2_of(u), ku, tbl_get(keys, vals, mask, Dj), eC, g.a[Dj], aC);
+        const ST x = (Dj == C) ? ST(0) : gain<ST>(g.m2_of(u), ku, tbl_get(t.keys, t.vals, mask, Dj), eC, g.a[Dj], aC);
         if (better3(x, Dj, j, S, D, J)) {
           S = x;
           D = Dj;
@@ -369,6 +407,9 @@ __global__ void __launch_bounds__(THREADS) scr_a_block(SV g, int64_t off, int64_
       D = lane < NW ? redD[lane] : INT_MAX;
       J = lane < NW ? redJ[lane] : INT_MAX;
       warp_argmax3(S, D, J);
+      slot_table_clear(t, tid, THREADS);
+      __syncthreads();
+      if (tid == 0) *t.ns = 0;
     }
     if (tid == 0) {
       g.jstar[idx] = J;
@@ -543,58 +584,57 @@ __global__ void __launch_bounds__(256) scr_c_warp(SV g, GroupView gv, int64_t cn
 
 template <typename ST>
 __global__ void __launch_bounds__(256) scr_c_wtbl(SV g, GroupView gv, int64_t cnt) {
+  using VT = typename TblVal<ST>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = lane_id(), wib = threadIdx.x >> 5;
-  unsigned long long* vals = reinterpret_cast<unsigned long long*>(smem) + (size_t)wib * kMidCap;
-  int32_t* keys = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned long long*>(smem) + 8 * kMidCap) +
-                  (size_t)wib * kMidCap;
+  const SlotTable<VT> t = slot_table<VT>(smem + (size_t)wib * slot_table_bytes<VT>(kMidCap), kMidCap);
+  slot_table_init(t, kMidCap, lane, 32);
+  __syncwarp();
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < cnt; i += nw) {
     const int32_t gi = gv.glist[i];
     const int64_t m0 = gv.gstart[gi], m1 = gv.gstart[gi + 1];
     const int32_t j = (int32_t)gv.keys[m0];
-    const uint32_t cap = table_cap(g.rp[j + 1] - g.rp[j]), mask = cap - 1;
-    table_clear(keys, vals, cap, lane, 32);
+    const uint32_t mask = table_cap(g.rp[j + 1] - g.rp[j]) - 1;
+    slot_table_fill<ST, VT>(g, j, t, mask, lane, 32);
     __syncwarp();
-    table_fill(g, j, keys, vals, mask, lane, 32);
-    __syncwarp();
-    const int64_t e2 = tbl_get(keys, vals, mask, g.L[j]);
+    const int64_t e2 = tbl_get(t.keys, t.vals, mask, g.L[j]);
     for (int64_t q = m0 + lane; q < m1; q += 32) {
       const int64_t idx = gv.vals[q];
-      decide<ST>(g, idx, j, tbl_get(keys, vals, mask, g.L[g.src[idx]]), e2);
+      decide<ST>(g, idx, j, tbl_get(t.keys, t.vals, mask, g.L[g.src[idx]]), e2);
     }
+    __syncwarp();
+    slot_table_clear(t, lane, 32);
+    __syncwarp();
+    if (lane == 0) *t.ns = 0;
     __syncwarp();
   }
 }
 
 template <typename ST, int THREADS>
-__global__ void __launch_bounds__(THREADS) scr_c_block(SV g, GroupView gv, int64_t cnt, int32_t* __restrict__ gkeys,
-                                                       unsigned long long* __restrict__ gvals, int64_t gcap) {
+__global__ void __launch_bounds__(THREADS) scr_c_block(SV g, GroupView gv, int64_t cnt, int cap) {
+  using VT = typename TblVal<ST>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x;
+  const SlotTable<VT> t = slot_table<VT>(smem, cap);
+  slot_table_init(t, cap, tid, THREADS);
+  __syncthreads();
   for (int64_t i = blockIdx.x; i < cnt; i += gridDim.x) {
     const int32_t gi = gv.glist[i];
     const int64_t m0 = gv.gstart[gi], m1 = gv.gstart[gi + 1];
     const int32_t j = (int32_t)gv.keys[m0];
-    const uint32_t cap = table_cap(g.rp[j + 1] - g.rp[j]), mask = cap - 1;
-    int32_t* keys;
-    unsigned long long* vals;
-    if (gcap == 0) {
-      vals = reinterpret_cast<unsigned long long*>(smem);
-      keys = reinterpret_cast<int32_t*>(smem + (size_t)cap * sizeof(unsigned long long));
-    } else {
-      keys = gkeys + (int64_t)blockIdx.x * gcap;
-      vals = gvals + (int64_t)blockIdx.x * gcap;
-    }
-    table_clear(keys, vals, cap, tid, THREADS);
+    const uint32_t mask = table_cap(g.rp[j + 1] - g.rp[j]) - 1;
+    slot_table_fill<ST, VT>(g, j, t, mask, tid, THREADS);
     __syncthreads();
-    table_fill(g, j, keys, vals, mask, tid, THREADS);
-    __syncthreads();
-    const int64_t e2 = tbl_get(keys, vals, mask, g.L[j]);
+    const int64_t e2 = tbl_get(t.keys, t.vals, mask, g.L[j]);
     for (int64_t q = m0 + tid; q < m1; q += THREADS) {
       const int64_t idx = gv.vals[q];
-      decide<ST>(g, idx, j, tbl_get(keys, vals, mask, g.L[g.src[idx]]), e2);
+      decide<ST>(g, idx, j, tbl_get(t.keys, t.vals, mask, g.L[g.src[idx]]), e2);
     }
+    __syncthreads();
+    slot_table_clear(t, tid, THREADS);
+    __syncthreads();
+    if (tid == 0) *t.ns = 0;
     __syncthreads();
   }
 }
@@ -727,7 +767,8 @@ int screen_impl(dcd_ctx* c, SV& sv, const Csr<int32_t>& g, const int64_t* cnt, i
   cudaStream_t s = c->stream;
   const int T = 256;
   const int64_t n = g.n;
-  const size_t wsmem = (size_t)8 * kMidCap * 12, bsmem = (size_t)kLargeCap * 12;
+  using VT = typename TblVal<ST>::type;
+  const size_t wsmem = (size_t)8 * slot_table_bytes<VT>(kMidCap), bsmem = slot_table_bytes<VT>(kLargeCap);
   DCD_TRY_CUDA(cudaFuncSetAttribute(scr_a_wtbl<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem));
   DCD_TRY_CUDA(cudaFuncSetAttribute(scr_c_wtbl<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem));
   DCD_TRY_CUDA(cudaFuncSetAttribute(scr_a_block<ST, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem));
@@ -740,7 +781,7 @@ int screen_impl(dcd_ctx* c, SV& sv, const Csr<int32_t>& g, const int64_t* cnt, i
   if (cnt[1]) count_launch(), scr_a_wtbl<ST><<<grid_for(cnt[1] * 32, T, 8), T, wsmem, s>>>(sv, off1, cnt[1]);
   if (cnt[2])
     count_launch(), scr_a_block<ST, 256><<<(unsigned)(cnt[2] < sm2 ? cnt[2] : sm2), 256, bsmem, s>>>(
-                        sv, off2, cnt[2], nullptr, nullptr, 0);
+                        sv, off2, cnt[2], kLargeCap);
   if (cnt[3]) {
     HubBufs hb;
     DCD_TRY(hub_setup(c, sv.src + off3, cnt[3], g.rp, &hb));
@@ -804,7 +845,7 @@ int screen_impl(dcd_ctx* c, SV& sv, const Csr<int32_t>& g, const int64_t* cnt, i
     gv.glist = gl.get() + 2 * ng;
     if (gcnt[2])
       count_launch(), scr_c_block<ST, 256><<<(unsigned)(gcnt[2] < sm2 ? gcnt[2] : sm2), 256, bsmem, s>>>(
-                          sv, gv, gcnt[2], nullptr, nullptr, 0);
+                          sv, gv, gcnt[2], kLargeCap);
     gv.glist = gl.get() + 3 * ng;
     if (gcnt[3]) {
       Buf<int32_t> jl;
