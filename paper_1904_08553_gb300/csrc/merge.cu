@@ -45,6 +45,63 @@ __global__ void make_records(const dcd_edge* __restrict__ ins, int64_t n_ins, co
   }
 }
 
+// Records sorted by source with a counting sort, then each source's segment
+// by sink with a rank sort (a record's place = the records of its segment
+// with a smaller key, or an equal key and a smaller index).  Used when no
+// source holds more than kRankSortMax records (the rank sort costs the square
+// of a segment); otherwise the batch takes the LSD radix sort.
+constexpr int64_t kRankSortMax = 4096;
+
+__global__ void rec_count(const dcd_edge* __restrict__ ins, int64_t n_ins, const dcd_edge* __restrict__ del,
+                          int64_t n_del, int32_t* __restrict__ cnt) {
+  const int64_t tot = n_ins + n_del;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
+    const dcd_edge e = i < n_ins ? ins[i] : del[i - n_ins];
+    atomicAdd(&cnt[e.u], 1);
+    atomicAdd(&cnt[e.v], 1);
+  }
+}
+
+__global__ void rec_maxseg(const int32_t* __restrict__ cnt, int64_t n, int32_t* __restrict__ mx) {
+  int32_t m = 0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    m = cnt[v] > m ? cnt[v] : m;
+  m = (int32_t)__reduce_max_sync(0xffffffffu, (unsigned)m);
+  if (lane_id() == 0 && m) atomicMax(mx, m);
+}
+
+__global__ void rec_scatter(const dcd_edge* __restrict__ ins, int64_t n_ins, const dcd_edge* __restrict__ del,
+                            int64_t n_del, const int32_t* __restrict__ off, int32_t* __restrict__ cur,
+                            uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  const int64_t tot = n_ins + n_del;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
+    const dcd_edge e = i < n_ins ? ins[i] : del[i - n_ins];
+    const uint64_t a = (uint64_t)(uint32_t)e.u, b = (uint64_t)(uint32_t)e.v;
+    const int32_t pa = off[e.u] + atomicAdd(&cur[e.u], 1);
+    keys[pa] = a << 32 | b;
+    vals[pa] = (uint32_t)(2 * i);
+    const int32_t pb = off[e.v] + atomicAdd(&cur[e.v], 1);
+    keys[pb] = b << 32 | a;
+    vals[pb] = (uint32_t)(2 * i + 1);
+  }
+}
+
+__global__ void rec_rank(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, int64_t R,
+                         const int32_t* __restrict__ off, uint64_t* __restrict__ kout, uint32_t* __restrict__ vout) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < R; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = kin[i];
+    const int32_t src = (int32_t)(k >> 32);
+    const int64_t a = off[src], b = off[src + 1];
+    int64_t r = 0;
+    for (int64_t j = a; j < b; j++) {
+      const uint64_t kj = kin[j];
+      r += (kj < k || (kj == k && j < i)) ? 1 : 0;
+    }
+    kout[a + r] = k;
+    vout[a + r] = vin[i];
+  }
+}
+
 __global__ void run_heads(const uint64_t* __restrict__ keys, int64_t R, int32_t* __restrict__ head) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < R; e += (int64_t)gridDim.x * blockDim.x)
     head[e] = (e == 0 || keys[e] != keys[e - 1]) ? 1 : 0;
@@ -446,15 +503,39 @@ int merge_batch(dcd_ctx* c, const int32_t* labels0, MergeOut* out) {
   uint32_t* vals = v0.get();
   int64_t P = 0;
   if (R > 0) {
-    ::dcd::count_launch(), make_records<<<grid_for(R / 2, T), T, 0, s>>>(c->ins.get(), n_ins, c->del.get(), n_del, k0.get(), v0.get());
+    // counting sort by source: per-source counts, offsets, the longest segment
+    Buf<int32_t> cnt, cur;
+    DCD_TRY(cnt.alloc(&c->mem, n + 1));
+    DCD_TRY(cur.alloc(&c->mem, n + 1));
+    DCD_TRY_CUDA(cudaMemsetAsync(cnt.get(), 0, (n + 1) * sizeof(int32_t), s));
+    DCD_TRY_CUDA(cudaMemsetAsync(cur.get(), 0, (n + 1) * sizeof(int32_t), s));
+    ::dcd::count_launch(), rec_count<<<grid_for(R / 2, T), T, 0, s>>>(c->ins.get(), n_ins, c->del.get(), n_del,
+                                                                       cnt.get());
+    ::dcd::count_launch(), rec_maxseg<<<grid_for(n, T), T, 0, s>>>(cnt.get(), n, cur.get() + n);
     DCD_LAUNCH_CHECK();
-    int b = bits_for(n - 1);
-    int ranges[4] = {0, b, 32, 32 + b};
-    bool in1 = false;
-    DCD_TRY(sort_pairs<uint32_t>(k0.get(), v0.get(), k1.get(), v1.get(), R, ranges, 2, stmp.get(), &in1, s));
-    if (in1) {
-      keys = k1.get();
-      vals = v1.get();
+    DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch, cur.get() + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    DCD_TRY(exclusive_scan<int32_t>(cnt.get(), cnt.get(), n + 1, nullptr, reinterpret_cast<int32_t*>(stmp.get()), s));
+    DCD_TRY_CUDA(cudaStreamSynchronize(s));
+    const int64_t maxseg = *reinterpret_cast<int32_t*>(c->hscratch);
+    if (maxseg <= kRankSortMax && R < (int64_t)INT32_MAX) {
+      DCD_TRY_CUDA(cudaMemsetAsync(cur.get() + n, 0, sizeof(int32_t), s));
+      ::dcd::count_launch(), rec_scatter<<<grid_for(R / 2, T), T, 0, s>>>(c->ins.get(), n_ins, c->del.get(), n_del,
+                                                                           cnt.get(), cur.get(), k1.get(), v1.get());
+      ::dcd::count_launch(), rec_rank<<<grid_for(R, T), T, 0, s>>>(k1.get(), v1.get(), R, cnt.get(), k0.get(),
+                                                                    v0.get());
+      DCD_LAUNCH_CHECK();
+    } else {
+      ::dcd::count_launch(), make_records<<<grid_for(R / 2, T), T, 0, s>>>(c->ins.get(), n_ins, c->del.get(), n_del,
+                                                                          k0.get(), v0.get());
+      DCD_LAUNCH_CHECK();
+      int b = bits_for(n - 1);
+      int ranges[4] = {0, b, 32, 32 + b};
+      bool in1 = false;
+      DCD_TRY(sort_pairs<uint32_t>(k0.get(), v0.get(), k1.get(), v1.get(), R, ranges, 2, stmp.get(), &in1, s));
+      if (in1) {
+        keys = k1.get();
+        vals = v1.get();
+      }
     }
     ::dcd::count_launch(), run_heads<<<grid_for(R, T), T, 0, s>>>(keys, R, head.get());
     DCD_TRY(exclusive_scan<int32_t>(head.get(), pid.get(), R, pid.get() + R, reinterpret_cast<int32_t*>(stmp.get()), s));
