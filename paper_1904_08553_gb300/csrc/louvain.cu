@@ -93,7 +93,7 @@ __device__ __forceinline__ int32_t proposal(i128 S, int32_t D, int32_t C, const 
 // kernel is bound by the issue rate of the warp-wide instructions, so every
 // reduction runs over whole segments with neutral values, and the next
 // vertex's row bounds load while the current row is aggregated.
-template <typename W, typename ST, int SEG>
+template <typename W, typename ST, int SEG, bool FEAT>
 __global__ void __launch_bounds__(256) lm_warp(LV<W> g, const int32_t* __restrict__ list, int64_t cnt,
                                                int32_t* __restrict__ prop) {
   static_assert(SEG == 32 || SEG == 16, "one or two vertices a warp");
@@ -138,10 +138,25 @@ __global__ void __launch_bounds__(256) lm_warp(LV<W> g, const int32_t* __restric
     const ST x = gain<ST>(m2v, kv, e, eC, aD, aC);
     ST S = cand ? x : gain_lowest<ST>();
     int32_t D = cand ? lab : INT_MAX;
-    seg_argmax<SEG>(S, D, smask);
+    if (SEG == 32) {
+      // most rows reach at most one other community: then the candidate is
+      // the answer and the three reductions of the argmax are skipped
+      const unsigned cb = __ballot_sync(0xffffffffu, cand);
+      if ((cb & (cb - 1)) == 0) {
+        const int l = cb ? __ffs(cb) - 1 : 0;
+        const ST xl = shfl_st(x, l);
+        const int32_t dl = __shfl_sync(0xffffffffu, lab, l);
+        S = cb ? xl : gain_lowest<ST>();
+        D = cb ? dl : INT_MAX;
+      } else {
+        seg_argmax<SEG>(S, D, smask);
+      }
+    } else {
+      seg_argmax<SEG>(S, D, smask);
+    }
     const int32_t pv = proposal(S, D, C, g.size);
     if (sl == 0 && has) prop[i] = pv;
-    if (g.f_eC) {
+    if (FEAT) {
       const int64_t eB = group_sum<ST>(smask, (valid && lab == D) ? wt : W(0));
       if (sl == 0 && has) {
         g.f_eC[i] = eC;
@@ -1265,10 +1280,12 @@ int launch_lm_st(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEvent_
       int32_t* pr = prop + o;
       switch (b.plan.var[x]) {
         case kLmHalf:
-          count_launch(), lm_warp<W, ST, 16><<<grid_for(cnt * 16, T, 16), T, 0, s>>>(g, lst, cnt, pr);
+          if (g.f_eC) count_launch(), lm_warp<W, ST, 16, true><<<grid_for(cnt * 16, T, 16), T, 0, s>>>(g, lst, cnt, pr);
+          else count_launch(), lm_warp<W, ST, 16, false><<<grid_for(cnt * 16, T, 16), T, 0, s>>>(g, lst, cnt, pr);
           break;
         case kLmWarp:
-          count_launch(), lm_warp<W, ST, 32><<<grid_for(cnt * 32, T, 16), T, 0, s>>>(g, lst, cnt, pr);
+          if (g.f_eC) count_launch(), lm_warp<W, ST, 32, true><<<grid_for(cnt * 32, T, 16), T, 0, s>>>(g, lst, cnt, pr);
+          else count_launch(), lm_warp<W, ST, 32, false><<<grid_for(cnt * 32, T, 16), T, 0, s>>>(g, lst, cnt, pr);
           break;
         case kLmWarp128: DCD_TRY((launch_warp_tbl<W, ST, 256, 4>(c, g, lst, cnt, pr))); break;
         case kLmWarp256: DCD_TRY((launch_warp_tbl<W, ST, 512, 8>(c, g, lst, cnt, pr))); break;
