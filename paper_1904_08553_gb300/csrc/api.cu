@@ -40,15 +40,6 @@ int grow_keep(DevMem* mem, Buf<T>& b, size_t need, size_t keep, cudaStream_t s) 
   return DCD_OK;
 }
 
-bool host_records_ok(const dcd_edge* e, int64_t m, int64_t n, bool is_insert) {
-  for (int64_t i = 0; i < m; i++) {
-    const dcd_edge x = e[i];
-    if (x.u < 0 || x.v < 0 || x.u >= n || x.v >= n || x.u == x.v) return false;
-    if (is_insert && x.w <= 0) return false;
-  }
-  return true;
-}
-
 }  // namespace
 
 void trace(const char* what) {
@@ -322,8 +313,6 @@ int dcd_destroy(dcd_ctx* c) {
 
 int dcd_apply_batch(dcd_ctx* c, const dcd_edge* ins, int64_t n_ins, const dcd_edge* del, int64_t n_del) {
   if (!c || n_ins < 0 || n_del < 0 || (n_ins && !ins) || (n_del && !del)) return DCD_EINVAL;
-  if (n_ins && !host_records_ok(ins, n_ins, c->n, true)) return DCD_EINVAL;
-  if (n_del && !host_records_ok(del, n_del, c->n, false)) return DCD_EINVAL;
   if ((c->n_ins + n_ins + c->n_del + n_del) * 2 >= (int64_t)INT32_MAX) return DCD_EINVAL;
   DCD_SCOPE(c);
   DCD_TRY(grow_keep(&c->mem, c->ins, c->n_ins + n_ins, c->n_ins, c->stream));
@@ -334,7 +323,11 @@ int dcd_apply_batch(dcd_ctx* c, const dcd_edge* ins, int64_t n_ins, const dcd_ed
   if (n_del)
     DCD_TRY_CUDA(cudaMemcpyAsync(c->del.get() + c->n_del, del, n_del * sizeof(dcd_edge), cudaMemcpyHostToDevice,
                                  c->stream));
-  DCD_TRY_CUDA(cudaStreamSynchronize(c->stream));
+  // the new records are checked on the device (one pass, then a
+  // synchronisation); a bad batch is not counted, so the staged state stays
+  bool ok = true;
+  DCD_TRY(validate_batch(c, c->ins.get() + c->n_ins, n_ins, c->del.get() + c->n_del, n_del, &ok));
+  if (!ok) return DCD_EINVAL;
   c->n_ins += n_ins;
   c->n_del += n_del;
   return DCD_OK;

@@ -465,6 +465,21 @@ __global__ void __launch_bounds__(256, 5) merge_rows(
 
 }  // namespace
 
+int validate_batch(dcd_ctx* c, const dcd_edge* ins, int64_t n_ins, const dcd_edge* del, int64_t n_del, bool* ok) {
+  cudaStream_t s = c->stream;
+  uint32_t* err = &c->dsc.get()->err;
+  *ok = true;
+  if (n_ins + n_del == 0) return DCD_OK;
+  DCD_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
+  ::dcd::count_launch(), validate_records<<<grid_for(n_ins + n_del, 256), 256, 0, s>>>(ins, n_ins, del, n_del, c->n,
+                                                                                       err);
+  DCD_LAUNCH_CHECK();
+  DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  DCD_TRY_CUDA(cudaStreamSynchronize(s));
+  *ok = !(*reinterpret_cast<uint32_t*>(c->hscratch) & kErrBadRecord);
+  return DCD_OK;
+}
+
 int merge_batch(dcd_ctx* c, const int32_t* labels0, MergeOut* out) {
   cudaStream_t s = c->stream;
   const int64_t n = c->n;

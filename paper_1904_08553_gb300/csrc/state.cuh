@@ -200,6 +200,10 @@ namespace dcd {
 
 // merge.cu: sort the staged batch, merge it into G_t (new buffers of ctx at
 // index 1 - cur), compute k (weighted degrees), m2 and in under labels0.
+// merge.cu: check staged records on the device (ids in [0, n), no self
+// loop, positive insert weight); *ok false when one fails.  Synchronises.
+int validate_batch(dcd_ctx* c, const dcd_edge* ins, int64_t n_ins, const dcd_edge* del, int64_t n_del, bool* ok);
+
 struct MergeOut {
   Buf<int64_t> k;          // n weighted degrees of G_t
   Buf<uint64_t> pkey;      // distinct (src << 32 | dst) pairs, sorted
