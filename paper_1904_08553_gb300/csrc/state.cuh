@@ -122,13 +122,12 @@ inline BinPlan default_bin_plan() {
   return p;
 }
 
-// The screening kernels' three source bins (1..32 warp, 33..256 warp with a
-// shared table, 257..4096 CTA with a shared table, larger: global table).
+// The screening kernels' source bins: 1..32 a warp, 33..256 a warp with a
+// shared table, 257..4096 a CTA with a shared table, larger: hub tables in
+// global memory (hub.cuh).
 constexpr int kBinWarpMax = 32;
 constexpr int kBinMidMax = 256;
 constexpr int kBinLargeMax = 4096;
-constexpr int kLargeThreads = 256;
-constexpr int kHubThreads = 512;
 constexpr int kMidCap = 512;     // table_cap(kBinMidMax)
 constexpr int kLargeCap = 8192;  // table_cap(kBinLargeMax)
 
