@@ -86,12 +86,17 @@ __global__ void rec_scatter(const dcd_edge* __restrict__ ins, int64_t n_ins, con
   }
 }
 
+// Segments longer than kRankSmall are sorted by rec_bitonic instead (a CTA
+// each, a bitonic network in shared memory).
+constexpr int kRankSmall = 64;
+
 __global__ void rec_rank(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, int64_t R,
                          const int32_t* __restrict__ off, uint64_t* __restrict__ kout, uint32_t* __restrict__ vout) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < R; i += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t k = kin[i];
     const int32_t src = (int32_t)(k >> 32);
     const int64_t a = off[src], b = off[src + 1];
+    if (b - a > kRankSmall) continue;
     int64_t r = 0;
     for (int64_t j = a; j < b; j++) {
       const uint64_t kj = kin[j];
@@ -99,6 +104,68 @@ __global__ void rec_rank(const uint64_t* __restrict__ kin, const uint32_t* __res
     }
     kout[a + r] = k;
     vout[a + r] = vin[i];
+  }
+}
+
+// sources whose segment is longer than kRankSmall
+__global__ void rec_big_list(const int32_t* __restrict__ off, int64_t n, int32_t* __restrict__ list,
+                             int32_t* __restrict__ cnt) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (blockIdx.x * (int64_t)blockDim.x) + (threadIdx.x & ~31); base < n; base += stride) {
+    const int64_t v = base + lane_id();
+    const bool big = v < n && off[v + 1] - off[v] > kRankSmall;
+    const unsigned bal = __ballot_sync(0xffffffffu, big);
+    if (!bal) continue;
+    int32_t slot = 0;
+    if (lane_id() == 0) slot = atomicAdd(cnt, __popc(bal));
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    if (big) list[slot + __popc(bal & lanemask_lt())] = (int32_t)v;
+  }
+}
+
+// One CTA per long segment (at most kRankSortMax records): a bitonic sort in
+// shared memory, padded to a power of two with the largest key.
+__global__ void __launch_bounds__(1024) rec_bitonic(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                    const int32_t* __restrict__ off, const int32_t* __restrict__ list,
+                                                    const int32_t* __restrict__ cnt, uint64_t* __restrict__ kout,
+                                                    uint32_t* __restrict__ vout) {
+  __shared__ uint64_t sk[kRankSortMax];
+  __shared__ uint32_t sv[kRankSortMax];
+  const int64_t nl = *cnt;
+  for (int64_t i = blockIdx.x; i < nl; i += gridDim.x) {
+    const int32_t v = list[i];
+    const int64_t a = off[v];
+    const int len = (int)(off[v + 1] - a);
+    int P = 1;
+    while (P < len) P <<= 1;
+    for (int x = threadIdx.x; x < P; x += blockDim.x) {
+      sk[x] = x < len ? kin[a + x] : ~0ull;
+      sv[x] = x < len ? vin[a + x] : 0u;
+    }
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int x = threadIdx.x; x < P; x += blockDim.x) {
+          const int y = x ^ j;
+          if (y > x) {
+            const bool up = (x & k) == 0;
+            const uint64_t kx = sk[x], ky = sk[y];
+            if ((kx > ky) == up) {
+              sk[x] = ky;
+              sk[y] = kx;
+              const uint32_t t = sv[x];
+              sv[x] = sv[y];
+              sv[y] = t;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    for (int x = threadIdx.x; x < len; x += blockDim.x) {
+      kout[a + x] = sk[x];
+      vout[a + x] = sv[x];
+    }
+    __syncthreads();
   }
 }
 
@@ -538,6 +605,14 @@ int merge_batch(dcd_ctx* c, const int32_t* labels0, MergeOut* out) {
                                                                            cnt.get(), cur.get(), k1.get(), v1.get());
       ::dcd::count_launch(), rec_rank<<<grid_for(R, T), T, 0, s>>>(k1.get(), v1.get(), R, cnt.get(), k0.get(),
                                                                     v0.get());
+      if (maxseg > kRankSmall) {
+        Buf<int32_t> big;
+        DCD_TRY(big.alloc(&c->mem, n));
+        DCD_TRY_CUDA(cudaMemsetAsync(cur.get() + n, 0, sizeof(int32_t), s));
+        ::dcd::count_launch(), rec_big_list<<<grid_for(n, T), T, 0, s>>>(cnt.get(), n, big.get(), cur.get() + n);
+        ::dcd::count_launch(), rec_bitonic<<<2 * c->sms, 1024, 0, s>>>(k1.get(), v1.get(), cnt.get(), big.get(),
+                                                                        cur.get() + n, k0.get(), v0.get());
+      }
       DCD_LAUNCH_CHECK();
     } else {
       ::dcd::count_launch(), make_records<<<grid_for(R / 2, T), T, 0, s>>>(c->ins.get(), n_ins, c->del.get(), n_del,
