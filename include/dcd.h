@@ -123,9 +123,10 @@ int dcd_destroy(dcd_ctx* ctx);
  * ins: n_ins host dcd_edge (u, v, w > 0); del: n_del host dcd_edge (u, v).
  * Deletes of the step act before its inserts; deleting an absent edge is a
  * no-op.  Several calls before one dcd_update concatenate.  The arrays are
- * validated whole before anything is staged and copied to the device; the
- * caller keeps ownership.  Errors: DCD_EINVAL (any bad record: nothing is
- * staged), DCD_ENOMEM, DCD_ECUDA. */
+ * copied to the device and checked there (ids in [0, n), u != v, w > 0 for
+ * inserts) before the call returns; a batch with a bad record is not staged.
+ * The caller keeps ownership.  Errors: DCD_EINVAL (any bad record: nothing
+ * is staged), DCD_ENOMEM, DCD_ECUDA. */
 int dcd_apply_batch(dcd_ctx* ctx, const dcd_edge* ins, int64_t n_ins, const dcd_edge* del,
                     int64_t n_del);
 
