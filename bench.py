@@ -263,7 +263,11 @@ def gpu_arm(args):
         pinned = []
         for ins, dels in stream.steps:
             pi = torch.from_numpy(np.ascontiguousarray(ins)).pin_memory().numpy()
-            pd = torch.from_numpy(np.ascontiguousarray(dels)).pin_memory().numpy()
+            # deletes as full dcd_edge records (w unused), so the binding passes
+            # the pinned buffer through without a conversion copy
+            d3 = np.zeros((len(dels), 3), np.int32)
+            d3[:, :2] = dels
+            pd = torch.from_numpy(d3).pin_memory().numpy()
             pinned.append((pi, pd))
         lab_host = torch.empty(n, dtype=torch.int32).pin_memory().numpy()
         ctx = dcd.Context(n, mode=dcd.MODE_DELTA, stream=ts)
