@@ -447,8 +447,13 @@ __global__ void __launch_bounds__(256, 5) merge_rows(
         const int64_t e = e0 + g;
         const bool valid = e < oe;
         const int32_t c = valid ? col_o[e] : INT_MAX;
-        int q = 0;  // pairs of the row with a smaller column (pairs are sorted)
-        for (int t = 0; t < np; t++) q += __shfl_sync(gmask, pc, t, G) < c ? 1 : 0;
+        // pairs of the row with a smaller column: the lanes hold the pair
+        // columns in ascending order (INT_MAX past the last), so a branch-free
+        // binary search over the G lanes counts them
+        int q = 0;
+#pragma unroll
+        for (int stp = G / 2; stp > 0; stp >>= 1)
+          if (__shfl_sync(gmask, pc, q + stp - 1, G) < c) q += stp;
         const int32_t kq = __shfl_sync(gmask, pc, q, G);
         const uint32_t fq = __shfl_sync(gmask, pf, q, G);
         const long long wq = __shfl_sync(gmask, pwv, q, G);
