@@ -45,6 +45,7 @@ extern "C" {
 #define DCD_ESTATE (-4)    /* call not valid in the current state                           */
 #define DCD_EOVERFLOW (-5) /* an edge weight above INT32_MAX, or 2m >= 2^62                  */
 #define DCD_ETIMEOUT (-6)  /* a bounded device-side wait gave up                            */
+#define DCD_EIO (-7)       /* a file could not be opened, written or renamed                 */
 
 /* ---- modes (Sec. III-C, III-D) ---- */
 #define DCD_MODE_STATIC 0  /* Static(G_t) from singletons every step (the naive approach)   */
@@ -198,6 +199,38 @@ int dcd_autotune(dcd_ctx* ctx, int32_t reps, float* best_ms);
  * non-NULL they receive n+1 int64, nnz int32 and nnz int32 (host memory). */
 int dcd_get_graph(dcd_ctx* ctx, int64_t* nnz_out, int64_t* row_ptr, int32_t* col, int32_t* w);
 
+/* ---- checkpoint / resume (no counterpart in the paper) ----
+ * dcd_save writes to the file at path (host string) what the next step of
+ * Sec. III-D reads from a context -- G_t as a CSR, C_t, the step counter t --
+ * and its mode, configuration, degree-bin plan and last R_t.  A context that
+ * dcd_load creates from the file (on cuda_stream, as dcd_create) continues
+ * the stream exactly as the saved one would: the same labels, modularity,
+ * R_t and step statistics for the same batches.  Not saved: a staged batch
+ * (dcd_save refuses while one is staged), the learned screen (attach the
+ * network again with dcd_set_screen; DCD_MODE_LEARNED updates fail with
+ * DCD_ESTATE until then), training-data collection and a pending
+ * dcd_set_rset.  The file is written under path + ".tmp" and renamed over
+ * path at the end, so a failed save leaves an existing file as it was.
+ * Format: little-endian; a 256-byte header (magic "DCDCKPT1", version 1,
+ * flags, n, nnz, t, mode, plan size, dcd_config, plan), then row_ptr (n + 1
+ * int64), col and w (nnz int32 each), labels (n int32) and R_t (n bytes,
+ * when flag bit 0 is set), each padded with zeros to a multiple of 8 bytes,
+ * then a 64-bit FNV-1a checksum over the 8-byte words before it.  dcd_load
+ * checks every field and entry on the host before it reaches the device
+ * (row_ptr from 0 to nnz without decreasing, columns in [0, n) increasing
+ * along each row with no self-loop, weights > 0, labels in [0, n), R_t bytes
+ * 0 or 1, the checksum, no trailing bytes).
+ * Errors: DCD_EINVAL (NULL or empty argument; a file that is not a valid
+ * checkpoint), DCD_ESTATE (dcd_save with a batch staged), DCD_EIO (the file
+ * cannot be opened, written or renamed), DCD_ENOMEM, DCD_ECUDA. */
+int dcd_save(dcd_ctx* ctx, const char* path);
+int dcd_load(const char* path, void* cuda_stream, dcd_ctx** out);
+
+/* The context's vertex count n, time steps computed t (the next update is
+ * step t + 1) and mode; each output is host memory and may be NULL.
+ * Errors: DCD_EINVAL (ctx NULL). */
+int dcd_get_state(const dcd_ctx* ctx, int64_t* n_out, int64_t* t_out, int32_t* mode_out);
+
 /* Kernel launches issued by the library in this process so far (all
  * contexts, all devices): lets a caller count the device work of a region. */
 int64_t dcd_kernel_launches(void);
@@ -233,6 +266,17 @@ int dcd_mlp_grad(dcd_mlp* mlp, const float* d_X, const float* d_y, int64_t n, fl
  * `batch` rows (the caller shuffles); *loss_out = last minibatch loss. */
 int dcd_mlp_train(dcd_mlp* mlp, const float* d_X, const float* d_y, int64_t n, int64_t batch, int32_t epochs,
                   float lr, double* loss_out);
+
+/* The network's parameters to / from a file (host path): magic "DCDMLP01",
+ * version 1 and DCD_MLP_PARAMS (uint32 each), the parameters as float32 in
+ * the layout above plus one zero float, then a 64-bit FNV-1a checksum over
+ * the 8-byte words before it.  The optimiser state is not saved.
+ * dcd_mlp_load creates the network on cuda_stream (as dcd_mlp_create) and
+ * rejects a file whose header, size, checksum or values (NaN, infinity) are
+ * wrong.  Errors: DCD_EINVAL, DCD_EIO (open, write or rename failed),
+ * DCD_ENOMEM, DCD_ECUDA. */
+int dcd_mlp_save(dcd_mlp* mlp, const char* path);
+int dcd_mlp_load(const char* path, void* cuda_stream, dcd_mlp** out);
 
 /* Learned screen for DCD_MODE_LEARNED: every update also runs
  * Delta-screening (R_t), scores the pool (R_t, the vertices the batch touches
@@ -303,6 +347,18 @@ int dcd_group_autotune(dcd_group* grp, int32_t reps, float* best_ms);
 #define DCD_NOALLOC_MAX_N 1048056
 int dcd_modularity_noalloc(int64_t n, const int64_t* d_row_ptr, const int32_t* d_col, const int32_t* d_w,
                            const int32_t* d_labels, void* cuda_stream, double* q_out, int64_t* m2_out);
+
+/* ---- fault injection (no counterpart in the paper) ----
+ * Makes the library's own error paths testable without a GPU fault: spec
+ * "alloc:N" makes the N-th device allocation from now on fail (DCD_ENOMEM),
+ * "cuda:N" the N-th checked CUDA runtime call (DCD_ECUDA, with
+ * dcd_last_cuda_error naming the call); "alloc:N,cuda:M" arms both.  The
+ * failing call is not made -- the library takes the error path a real
+ * failure of that call would take -- and each armed kind fires once.  NULL
+ * or "" disarms.  The environment variable DCD_FAULT, read when the library
+ * loads, takes the same spec.  Process-wide; counts from every thread and
+ * context.  Errors: DCD_EINVAL (a malformed spec: the armed state is kept). */
+int dcd_set_fault(const char* spec);
 
 /* Text of a status code (static storage). */
 const char* dcd_strerror(int code);

@@ -19,7 +19,7 @@ INCLUDE = ROOT / "include"
 BUILD = PKG / "_build"
 LIB = PKG / "libdcd.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "merge.cu", "screen.cu", "louvain.cu", "noalloc.cu", "mlp.cu", "features.cu", "group.cu"]
+SOURCES = ["api.cu", "merge.cu", "screen.cu", "louvain.cu", "noalloc.cu", "mlp.cu", "features.cu", "group.cu", "ckpt.cu"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
               "--expt-relaxed-constexpr", "-I", str(INCLUDE), "-I", str(CSRC)]
 

@@ -1,6 +1,7 @@
 // api.cu -- the extern "C" entry points of dcd.h and the per-step driver
 // (Sec. III-D: G_t <- G_{t-1} + Delta_t; R_t; multi-level run; C_t, Q_t).
 #include <chrono>
+#include <cerrno>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -14,6 +15,49 @@
 namespace dcd {
 
 std::atomic<int64_t> g_launches{0};
+std::atomic<int64_t> g_fault_left[kFaultKinds];
+
+bool fault_fire(int kind) {
+  int64_t v = g_fault_left[kind].load(std::memory_order_relaxed);
+  while (v > 0)
+    if (g_fault_left[kind].compare_exchange_weak(v, v - 1, std::memory_order_relaxed)) return v == 1;
+  return false;
+}
+
+namespace {
+// "alloc:N,cuda:M" (either, both, or empty = disarmed); N, M >= 1
+int parse_fault(const char* spec, int64_t left[kFaultKinds]) {
+  for (int k = 0; k < kFaultKinds; k++) left[k] = 0;
+  if (!spec) return DCD_OK;
+  const char* p = spec;
+  while (*p) {
+    const char* colon = strchr(p, ':');
+    if (!colon) return DCD_EINVAL;
+    const size_t len = (size_t)(colon - p);
+    const int kind = (len == 5 && !strncmp(p, "alloc", 5)) ? kFaultAlloc
+                     : (len == 4 && !strncmp(p, "cuda", 4)) ? kFaultCuda
+                                                             : -1;
+    if (kind < 0) return DCD_EINVAL;
+    char* end = nullptr;
+    errno = 0;
+    const long long v = strtoll(colon + 1, &end, 10);
+    if (end == colon + 1 || errno || v < 1) return DCD_EINVAL;
+    left[kind] = v;
+    if (*end == ',') p = end + 1;
+    else if (*end == '\0') p = end;
+    else return DCD_EINVAL;
+  }
+  return DCD_OK;
+}
+
+// DCD_FAULT arms the injector when the library loads
+const int g_fault_from_env = [] {
+  int64_t left[kFaultKinds];
+  if (parse_fault(getenv("DCD_FAULT"), left) == DCD_OK)
+    for (int k = 0; k < kFaultKinds; k++) g_fault_left[k].store(left[k]);
+  return 0;
+}();
+}  // namespace
 
 namespace {
 thread_local char g_last_cuda[512] = "no CUDA error";
@@ -81,6 +125,27 @@ int num_sms() {
   return g_sms_cache;
 }
 
+int resident_blocks(const void* kernel, int threads, size_t smem) {
+  struct Entry {
+    const void* k;
+    int threads, dev;
+    size_t smem;
+    int blocks;
+  };
+  static thread_local std::vector<Entry> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  for (const Entry& e : cache)
+    if (e.k == kernel && e.threads == threads && e.smem == smem && e.dev == dev) return e.blocks;
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, smem) != cudaSuccess || b < 1) {
+    cudaGetLastError();
+    b = 1;  // the launch itself reports what is wrong
+  }
+  cache.push_back(Entry{kernel, threads, dev, smem, b});
+  return b;
+}
+
 int grid_for(int64_t items, int threads, int per_sm) {
   int64_t b = cdiv(items > 0 ? items : 1, threads);
   int64_t cap = (int64_t)num_sms() * per_sm;
@@ -89,6 +154,10 @@ int grid_for(int64_t items, int threads, int per_sm) {
 }
 
 int DevMem::alloc_persistent(void** p, size_t bytes) {
+  if (fault_hit(kFaultAlloc)) {
+    *p = nullptr;
+    return DCD_ENOMEM;
+  }
   cudaError_t e = pool ? cudaMallocFromPoolAsync(p, bytes, pool, stream) : cudaMallocAsync(p, bytes, stream);
   if (e != cudaSuccess) {
     note_cuda_error(e, "cudaMallocAsync", __FILE__, __LINE__);
@@ -102,6 +171,10 @@ int DevMem::alloc_persistent(void** p, size_t bytes) {
 int DevMem::alloc(void** p, size_t bytes) {
   const size_t b = (bytes + 255) & ~(size_t)255;
   if (in_step && arena && arena_off + b <= arena_size) {
+    if (fault_hit(kFaultAlloc)) {
+      *p = nullptr;
+      return DCD_ENOMEM;
+    }
     *p = arena + arena_off;
     arena_off += b;
     return DCD_OK;
@@ -178,11 +251,19 @@ const char* dcd_strerror(int code) {
     case DCD_ESTATE: return "invalid state";
     case DCD_EOVERFLOW: return "integer overflow (weight above INT32_MAX or 2m >= 2^62)";
     case DCD_ETIMEOUT: return "device wait timed out";
+    case DCD_EIO: return "file could not be opened, written or renamed";
     default: return "unknown error";
   }
 }
 
 const char* dcd_last_cuda_error(void) { return dcd::g_last_cuda; }
+
+int dcd_set_fault(const char* spec) {
+  int64_t left[dcd::kFaultKinds];
+  DCD_TRY(dcd::parse_fault(spec, left));
+  for (int k = 0; k < dcd::kFaultKinds; k++) dcd::g_fault_left[k].store(left[k]);
+  return DCD_OK;
+}
 
 int64_t dcd_kernel_launches(void) { return dcd::g_launches.load(std::memory_order_relaxed); }
 
@@ -354,7 +435,6 @@ int dcd_apply_batch_device(dcd_ctx* c, const dcd_edge* ins, int64_t n_ins, const
 }  // extern "C"
 
 namespace dcd {
-int update_impl(dcd_ctx* c, dcd_step_stats* st, dcd_step_stats* per_graph);
 
 // Candidate bin plans of the autotuner: the default (every variant from a warp
 // per vertex on), with the half-warp variant in front, and coarser layouts
@@ -405,7 +485,7 @@ int autotune_impl(dcd_ctx* c, int32_t reps, float* best_ms) {
 }
 }  // namespace dcd
 
-int dcd::update_impl(dcd_ctx* c, dcd_step_stats* st, dcd_step_stats* per_graph) {
+int dcd::update_impl(dcd_ctx* c, dcd_step_stats* st, dcd_step_stats* per_graph, UpdateFinish finish, void* user) {
   cudaStream_t s = c->stream;
   const int64_t n = c->n;
   DevScalars* d = c->dsc.get();
@@ -427,13 +507,12 @@ int dcd::update_impl(dcd_ctx* c, dcd_step_stats* st, dcd_step_stats* per_graph) 
   const int nxt = 1 - c->cur;
   DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch + 8, c->rp[nxt].get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+  DCD_TRY_CUDA(cudaMemcpyAsync(c->hgs, c->gs.get(), c->G * sizeof(GraphState), cudaMemcpyDeviceToHost, s));
   DCD_TRY_CUDA(cudaEventRecord(c->ev[1], s));
   DCD_TRY_CUDA(cudaStreamSynchronize(s));
   trace("update: merge done");
   if (c->hsc->err & kErrBadRecord) return DCD_EINVAL;
   if (c->hsc->err & kErrOverflow) return DCD_EOVERFLOW;
-  DCD_TRY_CUDA(cudaMemcpyAsync(c->hgs, c->gs.get(), c->G * sizeof(GraphState), cudaMemcpyDeviceToHost, s));
-  DCD_TRY_CUDA(cudaStreamSynchronize(s));
   for (int x = 0; x < c->G; x++)
     if (c->hgs[x].m2 < 0 || c->hgs[x].m2 >= ((int64_t)1 << 62)) return DCD_EOVERFLOW;
   // per-graph state after the merge (2m, sum e_{i->C(i)} under C_{t-1}): a
@@ -531,6 +610,8 @@ int dcd::update_impl(dcd_ctx* c, dcd_step_stats* st, dcd_step_stats* per_graph) 
     st->pool = (learned || collect) ? c->feat_n : 0;
   }
 
+  if (finish) DCD_TRY(finish(c, user));
+
   // ---- commit ----
   c->cur = nxt;
   c->nnz = nnz_new;
@@ -565,13 +646,22 @@ int dcd_update(dcd_ctx* c, int32_t* labels_out, double* q_out, dcd_step_stats* s
   dcd_step_stats st;
   memset(&st, 0, sizeof(st));
   const int64_t launches0 = dcd::g_launches.load();
-  {
-    const int64_t R = 2 * (c->n_ins + c->n_del);
-    const int64_t nnz_cap = c->nnz + 2 * c->n_ins;
-    DCD_TRY(c->mem.begin_step((size_t)(40 * nnz_cap + 64 * c->n + 48 * R) + ((size_t)64 << 20)));
+  const int64_t R = 2 * (c->n_ins + c->n_del);
+  const int64_t nnz_cap = c->nnz + 2 * c->n_ins;
+  int rc = c->mem.begin_step((size_t)(40 * nnz_cap + 64 * c->n + 48 * R) + ((size_t)64 << 20));
+  if (rc == DCD_OK) {
+    // labels_out is written before the commit: a failed copy fails the step
+    const UpdateFinish copy_labels = [](dcd_ctx* cc, void* out) -> int {
+      if (out) {
+        DCD_TRY_CUDA(cudaMemcpyAsync(out, cc->labels_nx.get(), cc->n * sizeof(int32_t), cudaMemcpyDefault,
+                                     cc->stream));
+        DCD_TRY_CUDA(cudaStreamSynchronize(cc->stream));
+      }
+      return DCD_OK;
+    };
+    rc = update_impl(c, &st, nullptr, copy_labels, labels_out);
+    c->mem.end_step();
   }
-  const int rc = update_impl(c, &st, nullptr);
-  c->mem.end_step();
   st.launches = dcd::g_launches.load() - launches0;
   // the staged batch is consumed by the attempt, successful or not
   c->n_ins = c->n_del = 0;
@@ -580,10 +670,6 @@ int dcd_update(dcd_ctx* c, int32_t* labels_out, double* q_out, dcd_step_stats* s
     cudaStreamSynchronize(c->stream);
     cudaGetLastError();
     return rc;
-  }
-  if (labels_out) {
-    DCD_TRY_CUDA(cudaMemcpyAsync(labels_out, c->labels.get(), c->n * sizeof(int32_t), cudaMemcpyDefault, c->stream));
-    DCD_TRY_CUDA(cudaStreamSynchronize(c->stream));
   }
   if (q_out) *q_out = st.q;
   if (stats) *stats = st;

@@ -28,13 +28,25 @@ void tracef(const char* fmt, ...);
 // Records the failing CUDA call for dcd_last_cuda_error().
 void note_cuda_error(cudaError_t e, const char* what, const char* file, int line);
 
-#define DCD_TRY_CUDA(expr)                                   \
-  do {                                                       \
-    cudaError_t e_ = (expr);                                 \
-    if (e_ != cudaSuccess) {                                 \
-      ::dcd::note_cuda_error(e_, #expr, __FILE__, __LINE__); \
-      return DCD_ECUDA;                                      \
-    }                                                        \
+// Host-side fault injection (dcd_set_fault, environment variable DCD_FAULT),
+// for tests of the error paths: an armed kind counts its events -- device
+// allocations, checked CUDA calls -- and the N-th one reports failure instead
+// of being made.  Disarmed, the cost is one relaxed load per event.
+enum FaultKind : int { kFaultAlloc = 0, kFaultCuda = 1, kFaultKinds = 2 };
+extern std::atomic<int64_t> g_fault_left[kFaultKinds];
+bool fault_fire(int kind);
+inline bool fault_hit(int kind) {
+  return g_fault_left[kind].load(std::memory_order_relaxed) > 0 && fault_fire(kind);
+}
+
+#define DCD_TRY_CUDA(expr)                                                                          \
+  do {                                                                                              \
+    const bool f_ = ::dcd::fault_hit(::dcd::kFaultCuda);                                            \
+    cudaError_t e_ = f_ ? cudaErrorUnknown : (expr);                                                \
+    if (e_ != cudaSuccess) {                                                                        \
+      ::dcd::note_cuda_error(e_, f_ ? "injected fault instead of: " #expr : #expr, __FILE__, __LINE__); \
+      return DCD_ECUDA;                                                                             \
+    }                                                                                               \
   } while (0)
 
 #define DCD_TRY(expr)        \
@@ -53,6 +65,23 @@ __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 
 // times over, never more than the work needs.
 int grid_for(int64_t items, int threads, int per_sm = 8);
 int num_sms();
+
+// Blocks of a kernel resident on one SM at `threads` threads and `smem`
+// bytes of dynamic shared memory (the occupancy query, cached per thread and
+// device).  At least 1.
+int resident_blocks(const void* kernel, int threads, size_t smem);
+
+// Grid of a grid-stride kernel whose CTAs all do the same share of the work:
+// exactly one wave (resident blocks x SMs), never more CTAs than the items
+// need.  A grid above one wave that is not a whole number of waves leaves a
+// partial last wave at low occupancy, which a grid-stride loop cannot
+// rebalance.
+template <typename K>
+inline int wave_grid(K* kernel, int64_t items, int threads, size_t smem = 0) {
+  const int64_t need = cdiv(items > 0 ? items : 1, threads);
+  const int64_t wave = (int64_t)resident_blocks(reinterpret_cast<const void*>(kernel), threads, smem) * num_sms();
+  return (int)(need < wave ? need : wave);
+}
 
 // Device-side error word bits (ctx->d_err).
 enum : uint32_t {

@@ -48,9 +48,43 @@ __global__ void per_graph_counts(int G, const int64_t* __restrict__ off, const i
   }
 }
 
+// The group's outputs, written before the step is committed (update_impl's
+// finish): per-graph entry counts and |R_t|, and the local labels.
+struct GroupOut {
+  int G;
+  int32_t* labels_out;
+  long long* hn;
+  unsigned long long* hr;
+};
+
+int group_finish(dcd_ctx* c, void* user) {
+  const GroupOut* o = static_cast<const GroupOut*>(user);
+  cudaStream_t s = c->stream;
+  const int G = o->G;
+  Buf<long long> nnz;
+  Buf<unsigned long long> rsz;
+  DCD_TRY(nnz.alloc(&c->mem, G));
+  DCD_TRY(rsz.alloc(&c->mem, G));
+  DCD_TRY_CUDA(cudaMemsetAsync(rsz.get(), 0, G * sizeof(unsigned long long), s));
+  count_launch(), per_graph_counts<<<G < 4096 ? G : 4096, 256, 0, s>>>(G, c->goff_d.get(), c->rp[1 - c->cur].get(),
+                                                                      c->rset_nx.get(), nnz.get(), rsz.get());
+  DCD_LAUNCH_CHECK();
+  DCD_TRY_CUDA(cudaMemcpyAsync(o->hn, nnz.get(), G * sizeof(long long), cudaMemcpyDeviceToHost, s));
+  DCD_TRY_CUDA(cudaMemcpyAsync(o->hr, rsz.get(), G * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  if (o->labels_out) {
+    Buf<int32_t> loc;
+    DCD_TRY(loc.alloc(&c->mem, c->n));
+    count_launch(), to_local<<<grid_for(c->n, 256), 256, 0, s>>>(c->n, c->labels_nx.get(), c->gid.get(),
+                                                                 c->goff_d.get(), loc.get());
+    DCD_LAUNCH_CHECK();
+    DCD_TRY_CUDA(cudaMemcpyAsync(o->labels_out, loc.get(), c->n * sizeof(int32_t), cudaMemcpyDefault, s));
+  }
+  DCD_TRY_CUDA(cudaStreamSynchronize(s));
+  return DCD_OK;
+}
+
 }  // namespace
 
-int update_impl(dcd_ctx* c, dcd_step_stats* st, dcd_step_stats* per_graph);
 int autotune_impl(dcd_ctx* c, int32_t reps, float* best_ms);
 
 }  // namespace dcd
@@ -167,9 +201,17 @@ int dcd_group_update(dcd_group* grp, int32_t* labels_out, double* q_out, dcd_ste
   {
     const int64_t R = 2 * (c->n_ins + c->n_del);
     const int64_t nnz_cap = c->nnz + 2 * c->n_ins;
-    DCD_TRY(c->mem.begin_step((size_t)(40 * nnz_cap + 64 * c->n + 48 * R) + ((size_t)64 << 20)));
+    rc = c->mem.begin_step((size_t)(40 * nnz_cap + 64 * c->n + 48 * R) + ((size_t)64 << 20));
+    if (rc) {
+      c->n_ins = c->n_del = 0;  // the attempt consumes the staged batches, as a failed update does
+      c->staged_on_device = false;
+      return rc;
+    }
   }
-  rc = update_impl(c, &st, pg.data());
+  std::vector<long long> hn(G);
+  std::vector<unsigned long long> hr(G);
+  GroupOut go{G, labels_out, hn.data(), hr.data()};
+  rc = update_impl(c, &st, pg.data(), group_finish, &go);
   c->mem.end_step();
   c->n_ins = c->n_del = 0;
   c->staged_on_device = false;
@@ -178,28 +220,6 @@ int dcd_group_update(dcd_group* grp, int32_t* labels_out, double* q_out, dcd_ste
     cudaGetLastError();
     return rc;
   }
-  cudaStream_t s = c->stream;
-  Buf<long long> nnz;
-  Buf<unsigned long long> rsz;
-  DCD_TRY(nnz.alloc(&c->mem, G));
-  DCD_TRY(rsz.alloc(&c->mem, G));
-  DCD_TRY_CUDA(cudaMemsetAsync(rsz.get(), 0, G * sizeof(unsigned long long), s));
-  count_launch(), per_graph_counts<<<G < 4096 ? G : 4096, 256, 0, s>>>(G, c->goff_d.get(), c->rp[c->cur].get(),
-                                                                      c->rset.get(), nnz.get(), rsz.get());
-  DCD_LAUNCH_CHECK();
-  std::vector<long long> hn(G);
-  std::vector<unsigned long long> hr(G);
-  DCD_TRY_CUDA(cudaMemcpyAsync(hn.data(), nnz.get(), G * sizeof(long long), cudaMemcpyDeviceToHost, s));
-  DCD_TRY_CUDA(cudaMemcpyAsync(hr.data(), rsz.get(), G * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-  if (labels_out) {
-    Buf<int32_t> loc;
-    DCD_TRY(loc.alloc(&c->mem, c->n));
-    count_launch(), to_local<<<grid_for(c->n, 256), 256, 0, s>>>(c->n, c->labels.get(), c->gid.get(),
-                                                                 c->goff_d.get(), loc.get());
-    DCD_LAUNCH_CHECK();
-    DCD_TRY_CUDA(cudaMemcpyAsync(labels_out, loc.get(), c->n * sizeof(int32_t), cudaMemcpyDefault, s));
-  }
-  DCD_TRY_CUDA(cudaStreamSynchronize(s));
   const int64_t launches = g_launches.load() - launches0;
   for (int g = 0; g < G; g++) {
     dcd_step_stats& o = pg[g];

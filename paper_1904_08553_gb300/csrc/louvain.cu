@@ -1225,7 +1225,8 @@ template <typename W, typename ST, int CAP, int Q>
 int launch_warp_tbl(dcd_ctx* c, const LV<W>& g, const int32_t* lst, int64_t cnt, int32_t* prop) {
   constexpr int T = 256;
   constexpr size_t smem = (size_t)(T / 32) * warp_tbl_bytes<CAP, typename TblVal<ST>::type>();
-  count_launch(), lm_warp_tbl<W, ST, CAP, Q><<<grid_for(cnt * 32, T, 8), T, smem, c->stream>>>(g, lst, cnt, prop);
+  count_launch(), lm_warp_tbl<W, ST, CAP, Q><<<wave_grid(lm_warp_tbl<W, ST, CAP, Q>, cnt * 32, T, smem), T, smem,
+                                                 c->stream>>>(g, lst, cnt, prop);
   return DCD_OK;
 }
 
@@ -1255,6 +1256,12 @@ int prepare_lm_st() {
                                     (int)(table_cap(2048) * (sizeof(typename TblVal<ST>::type) + 6))));
   DCD_TRY_CUDA(cudaFuncSetAttribute(lm_large<W, ST, 512, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)(table_cap(4096) * (sizeof(typename TblVal<ST>::type) + 6))));
+  // occupancy of the grid-stride variants, looked up here so that no query
+  // runs while a pass is being captured
+  resident_blocks(reinterpret_cast<const void*>(lm_warp_tbl<W, ST, 256, 4>), T,
+                  (T / 32) * warp_tbl_bytes<256, typename TblVal<ST>::type>());
+  resident_blocks(reinterpret_cast<const void*>(lm_warp_tbl<W, ST, 512, 8>), T,
+                  (T / 32) * warp_tbl_bytes<512, typename TblVal<ST>::type>());
   return DCD_OK;
 }
 
@@ -1280,12 +1287,20 @@ int launch_lm_st(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEvent_
       int32_t* pr = prop + o;
       switch (b.plan.var[x]) {
         case kLmHalf:
-          if (g.f_eC) count_launch(), lm_warp<W, ST, 16, true><<<grid_for(cnt * 16, T, 16), T, 0, s>>>(g, lst, cnt, pr);
-          else count_launch(), lm_warp<W, ST, 16, false><<<grid_for(cnt * 16, T, 16), T, 0, s>>>(g, lst, cnt, pr);
+          if (g.f_eC)
+            count_launch(), lm_warp<W, ST, 16, true><<<grid_for(cnt * 16, T, 16), T, 0, s>>>(
+                                g, lst, cnt, pr);
+          else
+            count_launch(), lm_warp<W, ST, 16, false><<<grid_for(cnt * 16, T, 16), T, 0, s>>>(
+                                g, lst, cnt, pr);
           break;
         case kLmWarp:
-          if (g.f_eC) count_launch(), lm_warp<W, ST, 32, true><<<grid_for(cnt * 32, T, 16), T, 0, s>>>(g, lst, cnt, pr);
-          else count_launch(), lm_warp<W, ST, 32, false><<<grid_for(cnt * 32, T, 16), T, 0, s>>>(g, lst, cnt, pr);
+          if (g.f_eC)
+            count_launch(), lm_warp<W, ST, 32, true><<<grid_for(cnt * 32, T, 16), T, 0, s>>>(
+                                g, lst, cnt, pr);
+          else
+            count_launch(), lm_warp<W, ST, 32, false><<<grid_for(cnt * 32, T, 16), T, 0, s>>>(
+                                g, lst, cnt, pr);
           break;
         case kLmWarp128: DCD_TRY((launch_warp_tbl<W, ST, 256, 4>(c, g, lst, cnt, pr))); break;
         case kLmWarp256: DCD_TRY((launch_warp_tbl<W, ST, 512, 8>(c, g, lst, cnt, pr))); break;
@@ -1418,10 +1433,15 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
   if (any) DCD_TRY(prepare_lm<W>(lvl));
   struct ExecGuard {
     cudaGraphExec_t x = nullptr;
+    cudaStream_t s = nullptr;
     ~ExecGuard() {
-      if (x) cudaGraphExecDestroy(x);
+      if (x) {
+        cudaStreamSynchronize(s);  // an error path may leave a launch of it in flight
+        cudaGraphExecDestroy(x);
+      }
     }
   } exec;
+  exec.s = s;
   int64_t body_launches = 0;
   // a level with nothing to evaluate still runs one (empty) pass, as the
   // sequential definition does
@@ -1544,10 +1564,12 @@ int coarsen(dcd_ctx* c, const Csr<W>& g, const int32_t* L, const int32_t* cid, i
     int64_t m2max = 0;
     for (int x = 0; x < c->G; x++) m2max = c->hgs[x].m2 > m2max ? c->hgs[x].m2 : m2max;
     if (m2max < ((int64_t)1 << 31))
-      ::dcd::count_launch(), emit_coarse<W, true><<<grid_for(cdiv(m0, kSegEntries) * 32, T, 16), T, 0, s>>>(
+      ::dcd::count_launch(), emit_coarse<W, true><<<wave_grid(emit_coarse<W, true>, cdiv(m0, kSegEntries) * 32, T), T,
+                                                    0, s>>>(
           g.n, m0, g.rp, g.col, g.w, ccid.get(), (uint64_t)nc, k0.get(), v0.get(), cnt.get());
     else
-      ::dcd::count_launch(), emit_coarse<W, false><<<grid_for(cdiv(m0, kSegEntries) * 32, T, 16), T, 0, s>>>(
+      ::dcd::count_launch(), emit_coarse<W, false><<<wave_grid(emit_coarse<W, false>, cdiv(m0, kSegEntries) * 32, T),
+                                                     T, 0, s>>>(
           g.n, m0, g.rp, g.col, g.w, ccid.get(), (uint64_t)nc, k0.get(), v0.get(), cnt.get());
     DCD_LAUNCH_CHECK();
   }

@@ -689,7 +689,7 @@ int merge_batch(dcd_ctx* c, const int32_t* labels0, MergeOut* out) {
   const int64_t avg = (cap + n - 1) / n;
   const int64_t* pp = out->pair_ptr.get();
 #define DCD_MERGE(Gs)                                                                                       \
-  ::dcd::count_launch(), merge_rows<Gs><<<grid_for(n * Gs, T), T, 0, s>>>(n, rp_o, col_o, w_o, rp_n, c->col[nxt].get(),            \
+  ::dcd::count_launch(), merge_rows<Gs><<<wave_grid(merge_rows<Gs>, n * Gs, T), T, 0, s>>>(n, rp_o, col_o, w_o, rp_n, c->col[nxt].get(),            \
                                                    c->w[nxt].get(), pp, out->pkey.get(), out->pw.get(),     \
                                                    out->pflag.get(), added.get(), removed.get(), labels0,  \
                                                    out->k.get(), c->G > 1 ? c->gid.get() : nullptr,         \

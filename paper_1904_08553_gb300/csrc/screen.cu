@@ -777,8 +777,9 @@ int screen_impl(dcd_ctx* c, SV& sv, const Csr<int32_t>& g, const int64_t* cnt, i
   const int sm2 = 2 * c->sms;
 
   // ---- A ----
-  if (cnt[0]) count_launch(), scr_a_warp<ST><<<grid_for(cnt[0] * 32, T, 16), T, 0, s>>>(sv, 0, cnt[0]);
-  if (cnt[1]) count_launch(), scr_a_wtbl<ST><<<grid_for(cnt[1] * 32, T, 8), T, wsmem, s>>>(sv, off1, cnt[1]);
+  if (cnt[0]) count_launch(), scr_a_warp<ST><<<wave_grid(scr_a_warp<ST>, cnt[0] * 32, T), T, 0, s>>>(sv, 0, cnt[0]);
+  if (cnt[1])
+    count_launch(), scr_a_wtbl<ST><<<wave_grid(scr_a_wtbl<ST>, cnt[1] * 32, T, wsmem), T, wsmem, s>>>(sv, off1, cnt[1]);
   if (cnt[2])
     count_launch(), scr_a_block<ST, 256><<<(unsigned)(cnt[2] < sm2 ? cnt[2] : sm2), 256, bsmem, s>>>(
                         sv, off2, cnt[2], kLargeCap);
@@ -839,9 +840,12 @@ int screen_impl(dcd_ctx* c, SV& sv, const Csr<int32_t>& g, const int64_t* cnt, i
     DCD_LAUNCH_CHECK();
     // ---- C ----
     GroupView gv{keys, vals, gstart.get(), gl.get()};
-    if (gcnt[0]) count_launch(), scr_c_warp<ST><<<grid_for(gcnt[0] * 32, T, 16), T, 0, s>>>(sv, gv, gcnt[0]);
+    if (gcnt[0])
+      count_launch(), scr_c_warp<ST><<<wave_grid(scr_c_warp<ST>, gcnt[0] * 32, T), T, 0, s>>>(sv, gv, gcnt[0]);
     gv.glist = gl.get() + ng;
-    if (gcnt[1]) count_launch(), scr_c_wtbl<ST><<<grid_for(gcnt[1] * 32, T, 8), T, wsmem, s>>>(sv, gv, gcnt[1]);
+    if (gcnt[1])
+      count_launch(), scr_c_wtbl<ST><<<wave_grid(scr_c_wtbl<ST>, gcnt[1] * 32, T, wsmem), T, wsmem, s>>>(sv, gv,
+                                                                                                      gcnt[1]);
     gv.glist = gl.get() + 2 * ng;
     if (gcnt[2])
       count_launch(), scr_c_block<ST, 256><<<(unsigned)(gcnt[2] < sm2 ? gcnt[2] : sm2), 256, bsmem, s>>>(
@@ -862,7 +866,7 @@ int screen_impl(dcd_ctx* c, SV& sv, const Csr<int32_t>& g, const int64_t* cnt, i
   }
   trace("screen: phases B, C");
   // ---- D ----
-  if (off3) count_launch(), scr_mark<<<grid_for(off3 * 32, T, 16), T, 0, s>>>(sv, 0, off3);
+  if (off3) count_launch(), scr_mark<<<wave_grid(scr_mark, off3 * 32, T), T, 0, s>>>(sv, 0, off3);
   if (cnt[3]) count_launch(), scr_mark_hub<<<grid_for(cnt[3] * kMarkSlices * T, T, 8), T, 0, s>>>(sv, off3, nsrc);
   DCD_LAUNCH_CHECK();
   return DCD_OK;

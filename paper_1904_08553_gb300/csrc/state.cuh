@@ -203,6 +203,14 @@ namespace dcd {
 // loop, positive insert weight); *ok false when one fails.  Synchronises.
 int validate_batch(dcd_ctx* c, const dcd_edge* ins, int64_t n_ins, const dcd_edge* del, int64_t n_del, bool* ok);
 
+// api.cu: one time step of a context (or of a group's union graph).  Before
+// the step is committed (G_t, C_t, R_t and t replaced), finish(c, user) runs
+// when given: it reads the step's results in c->labels_nx, c->rset_nx and
+// c->rp/col/w[1 - c->cur] and writes the caller's outputs, so that a failure
+// there still leaves the context as it was.
+using UpdateFinish = int (*)(dcd_ctx* c, void* user);
+int update_impl(dcd_ctx* c, dcd_step_stats* st, dcd_step_stats* per_graph, UpdateFinish finish, void* user);
+
 struct MergeOut {
   Buf<int64_t> k;          // n weighted degrees of G_t
   Buf<uint64_t> pkey;      // distinct (src << 32 | dst) pairs, sorted

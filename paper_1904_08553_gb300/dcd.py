@@ -11,6 +11,7 @@ dcd_update, ...).  ``Context`` bundles them for one dynamic graph.
 from __future__ import annotations
 
 import ctypes
+import os
 from pathlib import Path
 
 import numpy as np
@@ -18,7 +19,8 @@ import numpy as np
 _PKG = Path(__file__).resolve().parent
 LIB_PATH = _PKG / "libdcd.so"
 
-DCD_OK, DCD_EINVAL, DCD_ENOMEM, DCD_ECUDA, DCD_ESTATE, DCD_EOVERFLOW, DCD_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+DCD_OK, DCD_EINVAL, DCD_ENOMEM, DCD_ECUDA, DCD_ESTATE, DCD_EOVERFLOW, DCD_ETIMEOUT, DCD_EIO = (
+    0, -1, -2, -3, -4, -5, -6, -7)
 MODE_STATIC, MODE_BASE, MODE_DELTA, MODE_GIVEN_R, MODE_LEARNED = 0, 1, 2, 3, 4
 
 EXPORTED = [
@@ -30,7 +32,8 @@ EXPORTED = [
     "dcd_set_screen", "dcd_set_collect", "dcd_get_screen_data",
     "dcd_group_create", "dcd_group_destroy", "dcd_group_apply_batch", "dcd_group_update",
     "dcd_set_bins", "dcd_get_bins", "dcd_autotune", "dcd_group_set_bins", "dcd_group_get_bins",
-    "dcd_group_autotune",
+    "dcd_group_autotune", "dcd_save", "dcd_load", "dcd_get_state", "dcd_mlp_save",
+    "dcd_mlp_load", "dcd_set_fault",
 ]
 MAX_BINS = 12
 LM_HALF, LM_WARP, LM_WARP128, LM_WARP256, LM_BLK512, LM_BLK1K, LM_BLK2K, LM_BLK4K, LM_HUB = range(9)
@@ -136,6 +139,12 @@ def lib():
             "dcd_group_set_bins": (INT, [P, I32, P, P]),
             "dcd_group_get_bins": (INT, [P, P, P, P]),
             "dcd_group_autotune": (INT, [P, I32, P]),
+            "dcd_save": (INT, [P, ctypes.c_char_p]),
+            "dcd_load": (INT, [ctypes.c_char_p, P, P]),
+            "dcd_get_state": (INT, [P, P, P, P]),
+            "dcd_set_fault": (INT, [ctypes.c_char_p]),
+            "dcd_mlp_save": (INT, [P, ctypes.c_char_p]),
+            "dcd_mlp_load": (INT, [ctypes.c_char_p, P, P]),
             "dcd_strerror": (ctypes.c_char_p, [INT]),
             "dcd_last_cuda_error": (ctypes.c_char_p, []),
         }
@@ -274,6 +283,11 @@ def dcd_get_screen_data(h, X_out=None, y_out=None, vertex_out=None, cap: int = 0
     return n.value
 
 
+def dcd_set_fault(spec: str | None) -> None:
+    """Arm host-side fault injection ("alloc:N", "cuda:N", both comma-separated; None or "" disarms)."""
+    _check(lib().dcd_set_fault(None if spec is None else spec.encode()), "dcd_set_fault")
+
+
 def dcd_strerror(code: int) -> str:
     return lib().dcd_strerror(int(code)).decode()
 
@@ -354,6 +368,27 @@ class _Bins:
         return _autotune(getattr(lib(), self._prefix + "autotune"), self._h, reps)
 
 
+def _path(path) -> bytes:
+    return os.fsencode(os.fspath(path))
+
+
+def dcd_save(h, path) -> None:
+    _check(lib().dcd_save(h, _path(path)), "dcd_save")
+
+
+def dcd_load(path, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().dcd_load(_path(path), _stream_ptr(stream), ctypes.byref(h)), "dcd_load")
+    return h
+
+
+def dcd_get_state(h):
+    """(n, t, mode) of a context."""
+    n, t, mode = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+    _check(lib().dcd_get_state(h, ctypes.byref(n), ctypes.byref(t), ctypes.byref(mode)), "dcd_get_state")
+    return n.value, t.value, mode.value
+
+
 class Context(_Bins):
     """One dynamic graph on vertices [0, n) (dcd_ctx)."""
 
@@ -363,6 +398,23 @@ class Context(_Bins):
         cfg.mode, cfg.max_iters, cfg.max_levels, cfg.tau_inv = mode, max_iters, max_levels, tau_inv
         self.n = int(n)
         self._h = dcd_create(self.n, cfg, stream)
+
+    @classmethod
+    def load(cls, path, stream=None) -> "Context":
+        """A context resumed from a dcd_save checkpoint."""
+        h = dcd_load(path, stream)
+        self = cls.__new__(cls)
+        self._h = h
+        self.n = dcd_get_state(h)[0]
+        return self
+
+    @property
+    def t(self) -> int:
+        """Time steps computed so far (the next update is step t + 1)."""
+        return dcd_get_state(self._h)[1]
+
+    def save(self, path) -> None:
+        dcd_save(self._h, path)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -508,6 +560,26 @@ class Mlp:
 
     def train(self, d_X, d_y, n, batch=4096, epochs=1, lr=1e-3):
         return dcd_mlp_train(self._h, d_X, d_y, n, batch, epochs, lr)
+
+    def save(self, path) -> None:
+        dcd_mlp_save(self._h, path)
+
+    @classmethod
+    def load(cls, path, stream=None) -> "Mlp":
+        """A network with the parameters of a dcd_mlp_save file."""
+        self = cls.__new__(cls)
+        self._h = dcd_mlp_load(path, stream)
+        return self
+
+
+def dcd_mlp_save(h, path) -> None:
+    _check(lib().dcd_mlp_save(h, _path(path)), "dcd_mlp_save")
+
+
+def dcd_mlp_load(path, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().dcd_mlp_load(_path(path), _stream_ptr(stream), ctypes.byref(h)), "dcd_mlp_load")
+    return h
 
 
 # ---- batched form ---------------------------------------------------------------
