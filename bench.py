@@ -302,7 +302,10 @@ def gpu_arm(args):
     peak, peak_kind = peaks()
     lm_bytes = BYTES_PER_ENTRY * edges + BYTES_PER_VERTEX * verts
     pass_gbs = lm_bytes / (lm_ms * 1e-3) / 1e9 if lm_ms > 0 else None
-    # per degree-bin kernel: time, algorithmic bytes, achieved GB/s
+    # per degree-bin kernel class: time from fork to join, algorithmic bytes.
+    # The bins of a pass run side by side, so these intervals overlap: the
+    # roofline is taken over the whole evaluation (every bin of a pass, the
+    # pass's own events on the context stream)
     names = ["lm_warp (degree <= 32)", "lm_warp_tbl (33..256)", "lm_large (257..4096)", "hub_agg + hub_gain + hub_pick (> 4096)"]
     bins = []
     for b in range(4):
@@ -310,8 +313,7 @@ def gpu_arm(args):
         by_b = sum(BYTES_PER_ENTRY * st.edges_bin[b] + BYTES_PER_VERTEX * st.verts_bin[b] for st in stats)
         bins.append({"kernel": names[b], "ms": ms_b, "bytes": by_b,
                      "gbs": by_b / (ms_b * 1e-3) / 1e9 if ms_b > 0 else None})
-    dom = max(bins, key=lambda x: x["ms"])
-    achieved = dom["gbs"]
+    achieved = pass_gbs
     cpu = cpu_baseline(T, nnz_by_step) if (world == 1 and not args.no_cpu) else None
     line = {
         "metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps,
@@ -335,13 +337,16 @@ def gpu_arm(args):
             "levels": float(np.mean([s.levels for s in stats])),
         },
         "roofline": {
-            "kernel": dom["kernel"],
+            "kernel": "local-move evaluation: the degree-bin kernels of a pass (lm_warp, lm_warp_tbl, lm_large, "
+                      "hub_*), run side by side",
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": None,
             "peak_kind": peak_kind,
             "algorithmic_bytes": f"{BYTES_PER_ENTRY} B x entries scanned + {BYTES_PER_VERTEX} B x vertices evaluated",
             "local_move_pass_gbs": pass_gbs,
             "bins": bins,
+            "bins_note": "each bin's ms runs from its fork to its join; the bins of a pass overlap, so the intervals "
+                         "add up to more than the pass and their GB/s understate the kernels",
         },
         "gpu_launches": int(launches),
         "clocks": clocks,

@@ -125,6 +125,18 @@ int num_sms() {
   return g_sms_cache;
 }
 
+int side_streams(dcd_ctx* c) {
+  if (c->have_side) return DCD_OK;
+  for (int x = 0; x < kMaxBins; x++) {
+    if (!c->side[x]) DCD_TRY_CUDA(cudaStreamCreateWithFlags(&c->side[x], cudaStreamNonBlocking));
+    if (!c->bin_start[x]) DCD_TRY_CUDA(cudaEventCreate(&c->bin_start[x]));
+    if (!c->join_ev[x]) DCD_TRY_CUDA(cudaEventCreateWithFlags(&c->join_ev[x], cudaEventDisableTiming));
+  }
+  if (!c->fork_ev) DCD_TRY_CUDA(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+  c->have_side = true;
+  return DCD_OK;
+}
+
 int resident_blocks(const void* kernel, int threads, size_t smem) {
   struct Entry {
     const void* k;
@@ -382,6 +394,12 @@ int dcd_destroy(dcd_ctx* c) {
   }
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
+  for (int x = 0; x < kMaxBins; x++) {
+    if (c->side[x]) cudaStreamDestroy(c->side[x]);
+    if (c->bin_start[x]) cudaEventDestroy(c->bin_start[x]);
+    if (c->join_ev[x]) cudaEventDestroy(c->join_ev[x]);
+  }
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   if (c->hsc) cudaFreeHost(c->hsc);
   if (c->hgs) cudaFreeHost(c->hgs);
   delete[] c->goff;

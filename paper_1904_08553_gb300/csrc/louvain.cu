@@ -1222,20 +1222,21 @@ int make_bins(dcd_ctx* c, const Csr<W>& g, const uint8_t* active, Bins* b, const
 }
 
 template <typename W, typename ST, int CAP, int Q>
-int launch_warp_tbl(dcd_ctx* c, const LV<W>& g, const int32_t* lst, int64_t cnt, int32_t* prop) {
+int launch_warp_tbl(cudaStream_t s, const LV<W>& g, const int32_t* lst, int64_t cnt, int32_t* prop) {
   constexpr int T = 256;
   constexpr size_t smem = (size_t)(T / 32) * warp_tbl_bytes<CAP, typename TblVal<ST>::type>();
   count_launch(), lm_warp_tbl<W, ST, CAP, Q><<<wave_grid(lm_warp_tbl<W, ST, CAP, Q>, cnt * 32, T, smem), T, smem,
-                                                 c->stream>>>(g, lst, cnt, prop);
+                                                 s>>>(g, lst, cnt, prop);
   return DCD_OK;
 }
 
 template <typename W, typename ST, int THREADS, int Q>
-int launch_large(dcd_ctx* c, const LV<W>& g, const int32_t* lst, int64_t cnt, int64_t maxd, int32_t* prop) {
+int launch_large(dcd_ctx* c, cudaStream_t s, const LV<W>& g, const int32_t* lst, int64_t cnt, int64_t maxd,
+                 int32_t* prop) {
   const int32_t tcap = (int32_t)table_cap(maxd);
   const size_t smem = (size_t)tcap * (sizeof(typename TblVal<ST>::type) + 6);  // values, keys, claimed-slot list
   const int64_t ctas = cnt < 16 * (int64_t)c->sms ? cnt : 16 * (int64_t)c->sms;
-  count_launch(), lm_large<W, ST, THREADS, Q><<<(unsigned)ctas, THREADS, smem, c->stream>>>(g, lst, cnt, prop, tcap);
+  count_launch(), lm_large<W, ST, THREADS, Q><<<(unsigned)ctas, THREADS, smem, s>>>(g, lst, cnt, prop, tcap);
   return DCD_OK;
 }
 
@@ -1267,14 +1268,29 @@ int prepare_lm_st() {
 
 // One local-move evaluation of every binned vertex (proposals in prop[]);
 // bin_ev[x] is recorded after bin x (with ev_flags: external records inside
-// stream capture).
+// stream capture).  With fork, the bins run side by side: they read the same
+// labels and sums and write disjoint slices of prop[], so each non-empty bin
+// runs on a side stream of its own between a fork from and a join to the
+// context stream, between c->bin_start[x] and bin_ev[x] (the ramp-up and tail
+// of one bin's kernels overlap the others'; a small bin fills SMs a large one
+// leaves idle).
 template <typename W, typename ST>
-int launch_lm_st(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEvent_t* bin_ev, unsigned ev_flags) {
-  cudaStream_t s = c->stream;
+int launch_lm_bins(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEvent_t* bin_ev, unsigned ev_flags,
+                   bool fork, unsigned* forked) {
+  const cudaStream_t s0 = c->stream;
   const int T = 256;
   const int32_t* lst0 = b.list.get();
+  if (fork) DCD_TRY_CUDA(cudaEventRecord(c->fork_ev, s0));
   for (int x = 0; x < b.plan.nb; x++) {
     const int64_t cnt = b.cnt[x], o = b.off[x];
+    const cudaStream_t s = fork && cnt ? c->side[x] : s0;
+    if (fork) {
+      if (cnt) {
+        DCD_TRY_CUDA(cudaStreamWaitEvent(s, c->fork_ev, 0));
+        *forked |= 1u << x;
+      }
+      DCD_TRY_CUDA(cudaEventRecordWithFlags(c->bin_start[x], s, ev_flags));
+    }
     if (cnt) {
       LV<W> g = lv;  // feature outputs shifted to the bin's list offset
       if (g.f_eC) {
@@ -1302,12 +1318,12 @@ int launch_lm_st(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEvent_
             count_launch(), lm_warp<W, ST, 32, false><<<grid_for(cnt * 32, T, 16), T, 0, s>>>(
                                 g, lst, cnt, pr);
           break;
-        case kLmWarp128: DCD_TRY((launch_warp_tbl<W, ST, 256, 4>(c, g, lst, cnt, pr))); break;
-        case kLmWarp256: DCD_TRY((launch_warp_tbl<W, ST, 512, 8>(c, g, lst, cnt, pr))); break;
-        case kLmBlk512: DCD_TRY((launch_large<W, ST, 256, 2>(c, g, lst, cnt, b.maxd[x], pr))); break;
-        case kLmBlk1k: DCD_TRY((launch_large<W, ST, 256, 4>(c, g, lst, cnt, b.maxd[x], pr))); break;
-        case kLmBlk2k: DCD_TRY((launch_large<W, ST, 256, 8>(c, g, lst, cnt, b.maxd[x], pr))); break;
-        case kLmBlk4k: DCD_TRY((launch_large<W, ST, 512, 8>(c, g, lst, cnt, b.maxd[x], pr))); break;
+        case kLmWarp128: DCD_TRY((launch_warp_tbl<W, ST, 256, 4>(s, g, lst, cnt, pr))); break;
+        case kLmWarp256: DCD_TRY((launch_warp_tbl<W, ST, 512, 8>(s, g, lst, cnt, pr))); break;
+        case kLmBlk512: DCD_TRY((launch_large<W, ST, 256, 2>(c, s, g, lst, cnt, b.maxd[x], pr))); break;
+        case kLmBlk1k: DCD_TRY((launch_large<W, ST, 256, 4>(c, s, g, lst, cnt, b.maxd[x], pr))); break;
+        case kLmBlk2k: DCD_TRY((launch_large<W, ST, 256, 8>(c, s, g, lst, cnt, b.maxd[x], pr))); break;
+        case kLmBlk4k: DCD_TRY((launch_large<W, ST, 512, 8>(c, s, g, lst, cnt, b.maxd[x], pr))); break;
         default: {
           const unsigned ch = hub_grid(c, b.hub);
           count_launch(), hub_agg<W, ST><<<ch, 256, 0, s>>>(g, b.hub.t);
@@ -1320,8 +1336,28 @@ int launch_lm_st(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEvent_
       DCD_LAUNCH_CHECK();
     }
     if (bin_ev) DCD_TRY_CUDA(cudaEventRecordWithFlags(bin_ev[x], s, ev_flags));
+    if (fork && cnt) {
+      DCD_TRY_CUDA(cudaEventRecord(c->join_ev[x], s));
+      DCD_TRY_CUDA(cudaStreamWaitEvent(s0, c->join_ev[x], 0));
+      *forked &= ~(1u << x);
+    }
   }
   return DCD_OK;
+}
+
+template <typename W, typename ST>
+int launch_lm_st(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEvent_t* bin_ev, unsigned ev_flags,
+                 bool fork = false) {
+  unsigned forked = 0;
+  const int rc = launch_lm_bins<W, ST>(c, lv, b, prop, bin_ev, ev_flags, fork, &forked);
+  // an error between a fork and its join: join the side streams all the same,
+  // so that a stream capture in progress ends with every stream back home
+  for (int x = 0; x < kMaxBins; x++)
+    if (forked & (1u << x)) {
+      cudaEventRecord(c->join_ev[x], c->side[x]);
+      cudaStreamWaitEvent(c->stream, c->join_ev[x], 0);
+    }
+  return rc;
 }
 
 template <typename W>
@@ -1339,9 +1375,10 @@ int launch_lm(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEvent_t* 
 }
 
 template <typename W>
-int launch_lm_nocfg(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEvent_t* bin_ev, unsigned ev_flags) {
-  if (lv.m2 >= ((int64_t)1 << 31)) return launch_lm_st<W, i128>(c, lv, b, prop, bin_ev, ev_flags);
-  return launch_lm_st<W, long long>(c, lv, b, prop, bin_ev, ev_flags);
+int launch_lm_nocfg(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEvent_t* bin_ev, unsigned ev_flags,
+                    bool fork) {
+  if (lv.m2 >= ((int64_t)1 << 31)) return launch_lm_st<W, i128>(c, lv, b, prop, bin_ev, ev_flags, fork);
+  return launch_lm_st<W, long long>(c, lv, b, prop, bin_ev, ev_flags, fork);
 }
 
 // Per-graph counters of one update (host).
@@ -1405,9 +1442,12 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
     DCD_TRY_CUDA(cudaMemsetAsync(moved_big_cnt.get(), 0, sizeof(int32_t), s));
     DCD_TRY_CUDA(cudaMemsetAsync(&d->any_running, 0, sizeof(int32_t), s));
     DCD_TRY_CUDA(cudaEventRecordWithFlags(c->ev[2], s, evf));
-    if (any) DCD_TRY(launch_lm_nocfg<W>(c, lvl, bins, prop.get(), &c->ev[12], evf));
+    if (any) DCD_TRY(launch_lm_nocfg<W>(c, lvl, bins, prop.get(), &c->ev[12], evf, true));
     else
-      for (int x = 0; x < bins.plan.nb; x++) DCD_TRY_CUDA(cudaEventRecordWithFlags(c->ev[12 + x], s, evf));
+      for (int x = 0; x < bins.plan.nb; x++) {
+        DCD_TRY_CUDA(cudaEventRecordWithFlags(c->bin_start[x], s, evf));
+        DCD_TRY_CUDA(cudaEventRecordWithFlags(c->ev[12 + x], s, evf));
+      }
     DCD_TRY_CUDA(cudaEventRecordWithFlags(c->ev[3], s, evf));
     if (total) {
       ::dcd::count_launch(), lm_apply<<<grid_for(total, T), T, 0, s>>>(
@@ -1431,6 +1471,7 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
     return DCD_OK;
   };
   if (any) DCD_TRY(prepare_lm<W>(lvl));
+  DCD_TRY(side_streams(c));
   struct ExecGuard {
     cudaGraphExec_t x = nullptr;
     cudaStream_t s = nullptr;
@@ -1474,7 +1515,7 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
     {
       float tb[kMaxBins] = {};
       for (int x = 0; x < bins.plan.nb; x++) {
-        cudaEventElapsedTime(&tb[x], x ? c->ev[11 + x] : c->ev[2], c->ev[12 + x]);
+        cudaEventElapsedTime(&tb[x], c->bin_start[x], c->ev[12 + x]);
         const int k = lm_variant_class(bins.plan.var[x]);
         out->ms_bin[k] += tb[x];
         out->edges_bin[k] += bins.deg[x];

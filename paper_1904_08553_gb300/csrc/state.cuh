@@ -192,6 +192,12 @@ struct dcd_ctx {
   bool feat_has_y = false;
 
   cudaEvent_t ev[24] = {};
+  // the local-move bins of a captured pass run on side streams (fork / join)
+  bool have_side = false;
+  cudaStream_t side[dcd::kMaxBins] = {};
+  cudaEvent_t bin_start[dcd::kMaxBins] = {};
+  cudaEvent_t join_ev[dcd::kMaxBins] = {};
+  cudaEvent_t fork_ev = nullptr;
   dcd::BinPlan bin_plan = dcd::default_bin_plan();  // degree bins of the local-move kernels
 };
 
@@ -202,6 +208,10 @@ namespace dcd {
 // merge.cu: check staged records on the device (ids in [0, n), no self
 // loop, positive insert weight); *ok false when one fails.  Synchronises.
 int validate_batch(dcd_ctx* c, const dcd_edge* ins, int64_t n_ins, const dcd_edge* del, int64_t n_del, bool* ok);
+
+// api.cu: create the context's side streams and their events once (outside
+// stream capture); dcd_destroy releases them.
+int side_streams(dcd_ctx* c);
 
 // api.cu: one time step of a context (or of a group's union graph).  Before
 // the step is committed (G_t, C_t, R_t and t replaced), finish(c, user) runs
