@@ -688,6 +688,17 @@ int merge_batch(dcd_ctx* c, const int32_t* labels0, MergeOut* out) {
   DCD_TRY_CUDA(cudaMemsetAsync(c->gs.get(), 0, c->G * sizeof(GraphState), s));
   const int64_t avg = (cap + n - 1) / n;
   const int64_t* pp = out->pair_ptr.get();
+  // merge_rows skips the rows above kLongRow entries, which merge_long takes:
+  // the two write disjoint rows (and add into 2m and sum e_{i->C(i)} with
+  // atomics), so they run side by side
+  SideBySide par(c);
+  DCD_TRY(par.fork());
+  cudaStream_t s_long;
+  DCD_TRY(par.on(0, &s_long));
+  ::dcd::count_launch(), merge_long<256><<<4 * c->sms, 256, 0, s_long>>>(
+      long_rows.get(), long_cnt.get(), rp_o, col_o, w_o, rp_n, c->col[nxt].get(), c->w[nxt].get(), pp,
+      out->pkey.get(), out->pw.get(), out->pflag.get(), added.get(), removed.get(), labels0, out->k.get(),
+      c->G > 1 ? c->gid.get() : nullptr, c->gs.get());
 #define DCD_MERGE(Gs)                                                                                       \
   ::dcd::count_launch(), merge_rows<Gs><<<wave_grid(merge_rows<Gs>, n * Gs, T), T, 0, s>>>(n, rp_o, col_o, w_o, rp_n, c->col[nxt].get(),            \
                                                    c->w[nxt].get(), pp, out->pkey.get(), out->pw.get(),     \
@@ -699,11 +710,8 @@ int merge_batch(dcd_ctx* c, const int32_t* labels0, MergeOut* out) {
   else if (avg <= 24) DCD_MERGE(16);
   else DCD_MERGE(32);
 #undef DCD_MERGE
-  ::dcd::count_launch(), merge_long<256><<<4 * c->sms, 256, 0, s>>>(
-      long_rows.get(), long_cnt.get(), rp_o, col_o, w_o, rp_n, c->col[nxt].get(), c->w[nxt].get(), pp,
-      out->pkey.get(), out->pw.get(), out->pflag.get(), added.get(), removed.get(), labels0, out->k.get(),
-      c->G > 1 ? c->gid.get() : nullptr, c->gs.get());
   DCD_LAUNCH_CHECK();
+  DCD_TRY(par.join());
   return DCD_OK;
 }
 

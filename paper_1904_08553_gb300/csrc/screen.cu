@@ -777,20 +777,37 @@ int screen_impl(dcd_ctx* c, SV& sv, const Csr<int32_t>& g, const int64_t* cnt, i
   const int sm2 = 2 * c->sms;
 
   // ---- A ----
-  if (cnt[0]) count_launch(), scr_a_warp<ST><<<wave_grid(scr_a_warp<ST>, cnt[0] * 32, T), T, 0, s>>>(sv, 0, cnt[0]);
-  if (cnt[1])
-    count_launch(), scr_a_wtbl<ST><<<wave_grid(scr_a_wtbl<ST>, cnt[1] * 32, T, wsmem), T, wsmem, s>>>(sv, off1, cnt[1]);
-  if (cnt[2])
-    count_launch(), scr_a_block<ST, 256><<<(unsigned)(cnt[2] < sm2 ? cnt[2] : sm2), 256, bsmem, s>>>(
-                        sv, off2, cnt[2], kLargeCap);
-  if (cnt[3]) {
+  // the four source classes write disjoint slices of the per-source outputs:
+  // they run side by side (the hub tables are set up before the fork)
+  {
     HubBufs hb;
-    DCD_TRY(hub_setup(c, sv.src + off3, cnt[3], g.rp, &hb));
-    count_launch(), hub_agg<int32_t, ST><<<hub_grid(c, hb), 256, 0, s>>>(sv, hb.t);
-    count_launch(), scr_a_hub<ST, 512><<<(unsigned)(cnt[3] < 4 * c->sms ? cnt[3] : 4 * c->sms), 512, 0, s>>>(
-                        sv, off3, cnt[3], hb.t);
+    if (cnt[3]) DCD_TRY(hub_setup(c, sv.src + off3, cnt[3], g.rp, &hb));
+    SideBySide par(c);
+    DCD_TRY(par.fork());
+    cudaStream_t sx;
+    if (cnt[0]) {
+      DCD_TRY(par.on(0, &sx));
+      count_launch(), scr_a_warp<ST><<<wave_grid(scr_a_warp<ST>, cnt[0] * 32, T), T, 0, sx>>>(sv, 0, cnt[0]);
+    }
+    if (cnt[1]) {
+      DCD_TRY(par.on(1, &sx));
+      count_launch(), scr_a_wtbl<ST><<<wave_grid(scr_a_wtbl<ST>, cnt[1] * 32, T, wsmem), T, wsmem, sx>>>(sv, off1,
+                                                                                                       cnt[1]);
+    }
+    if (cnt[2]) {
+      DCD_TRY(par.on(2, &sx));
+      count_launch(), scr_a_block<ST, 256><<<(unsigned)(cnt[2] < sm2 ? cnt[2] : sm2), 256, bsmem, sx>>>(
+                          sv, off2, cnt[2], kLargeCap);
+    }
+    if (cnt[3]) {
+      DCD_TRY(par.on(3, &sx));
+      count_launch(), hub_agg<int32_t, ST><<<hub_grid(c, hb), 256, 0, sx>>>(sv, hb.t);
+      count_launch(), scr_a_hub<ST, 512><<<(unsigned)(cnt[3] < 4 * c->sms ? cnt[3] : 4 * c->sms), 512, 0, sx>>>(
+                          sv, off3, cnt[3], hb.t);
+    }
+    DCD_LAUNCH_CHECK();
+    DCD_TRY(par.join());
   }
-  DCD_LAUNCH_CHECK();
 
   trace("screen: phase A");
   // ---- B ----
@@ -839,30 +856,45 @@ int screen_impl(dcd_ctx* c, SV& sv, const Csr<int32_t>& g, const int64_t* cnt, i
     count_launch(), close_groups<<<1, 32, 0, s>>>(keys, nsrc, n, gstart.get() + ng);
     DCD_LAUNCH_CHECK();
     // ---- C ----
+    // each candidate group is in one class and a source in one group, so the
+    // classes write disjoint flags: side by side, as in phase A
     GroupView gv{keys, vals, gstart.get(), gl.get()};
-    if (gcnt[0])
-      count_launch(), scr_c_warp<ST><<<wave_grid(scr_c_warp<ST>, gcnt[0] * 32, T), T, 0, s>>>(sv, gv, gcnt[0]);
+    Buf<int32_t> jl;
+    HubBufs hb;
+    if (gcnt[3]) {
+      DCD_TRY(jl.alloc(&c->mem, gcnt[3]));
+      count_launch(), group_vertices<<<grid_for(gcnt[3], T), T, 0, s>>>(keys, gstart.get(), gl.get() + 3 * ng,
+                                                                        gcnt[3], jl.get());
+      DCD_TRY(hub_setup(c, jl.get(), gcnt[3], g.rp, &hb));
+    }
+    SideBySide par(c);
+    DCD_TRY(par.fork());
+    cudaStream_t sx;
+    if (gcnt[0]) {
+      DCD_TRY(par.on(0, &sx));
+      count_launch(), scr_c_warp<ST><<<wave_grid(scr_c_warp<ST>, gcnt[0] * 32, T), T, 0, sx>>>(sv, gv, gcnt[0]);
+    }
     gv.glist = gl.get() + ng;
-    if (gcnt[1])
-      count_launch(), scr_c_wtbl<ST><<<wave_grid(scr_c_wtbl<ST>, gcnt[1] * 32, T, wsmem), T, wsmem, s>>>(sv, gv,
-                                                                                                      gcnt[1]);
+    if (gcnt[1]) {
+      DCD_TRY(par.on(1, &sx));
+      count_launch(), scr_c_wtbl<ST><<<wave_grid(scr_c_wtbl<ST>, gcnt[1] * 32, T, wsmem), T, wsmem, sx>>>(sv, gv,
+                                                                                                       gcnt[1]);
+    }
     gv.glist = gl.get() + 2 * ng;
-    if (gcnt[2])
-      count_launch(), scr_c_block<ST, 256><<<(unsigned)(gcnt[2] < sm2 ? gcnt[2] : sm2), 256, bsmem, s>>>(
+    if (gcnt[2]) {
+      DCD_TRY(par.on(2, &sx));
+      count_launch(), scr_c_block<ST, 256><<<(unsigned)(gcnt[2] < sm2 ? gcnt[2] : sm2), 256, bsmem, sx>>>(
                           sv, gv, gcnt[2], kLargeCap);
+    }
     gv.glist = gl.get() + 3 * ng;
     if (gcnt[3]) {
-      Buf<int32_t> jl;
-      DCD_TRY(jl.alloc(&c->mem, gcnt[3]));
-      count_launch(), group_vertices<<<grid_for(gcnt[3], T), T, 0, s>>>(keys, gstart.get(), gv.glist, gcnt[3],
-                                                                        jl.get());
-      HubBufs hb;
-      DCD_TRY(hub_setup(c, jl.get(), gcnt[3], g.rp, &hb));
-      count_launch(), hub_agg<int32_t, ST><<<hub_grid(c, hb), 256, 0, s>>>(sv, hb.t);
-      count_launch(), scr_c_hub<ST, 512><<<(unsigned)(gcnt[3] < 4 * c->sms ? gcnt[3] : 4 * c->sms), 512, 0, s>>>(
+      DCD_TRY(par.on(3, &sx));
+      count_launch(), hub_agg<int32_t, ST><<<hub_grid(c, hb), 256, 0, sx>>>(sv, hb.t);
+      count_launch(), scr_c_hub<ST, 512><<<(unsigned)(gcnt[3] < 4 * c->sms ? gcnt[3] : 4 * c->sms), 512, 0, sx>>>(
                           sv, gv, gcnt[3], hb.t);
     }
     DCD_LAUNCH_CHECK();
+    DCD_TRY(par.join());
   }
   trace("screen: phases B, C");
   // ---- D ----

@@ -213,6 +213,50 @@ int validate_batch(dcd_ctx* c, const dcd_edge* ins, int64_t n_ins, const dcd_edg
 // stream capture); dcd_destroy releases them.
 int side_streams(dcd_ctx* c);
 
+// Kernels with disjoint outputs, run side by side on the context's side
+// streams.  fork() marks the point of the context stream every side stream
+// starts from; on(x) gives side stream x, made to wait for that point once;
+// join() brings every side stream used back into the context stream.  The
+// destructor joins whatever is left, so an error return never leaves side
+// work unjoined; declare it after the buffers the side work uses, so that
+// they are released (stream-ordered, on the context stream) after the join.
+struct SideBySide {
+  dcd_ctx* c;
+  unsigned used = 0;
+  explicit SideBySide(dcd_ctx* cc) : c(cc) {}
+  SideBySide(const SideBySide&) = delete;
+  SideBySide& operator=(const SideBySide&) = delete;
+  int fork() {
+    DCD_TRY(side_streams(c));
+    DCD_TRY_CUDA(cudaEventRecord(c->fork_ev, c->stream));
+    return DCD_OK;
+  }
+  int on(int x, cudaStream_t* out) {
+    if (!(used & (1u << x))) {
+      DCD_TRY_CUDA(cudaStreamWaitEvent(c->side[x], c->fork_ev, 0));
+      used |= 1u << x;
+    }
+    *out = c->side[x];
+    return DCD_OK;
+  }
+  int join() {
+    for (int x = 0; x < kMaxBins; x++)
+      if (used & (1u << x)) {
+        DCD_TRY_CUDA(cudaEventRecord(c->join_ev[x], c->side[x]));
+        DCD_TRY_CUDA(cudaStreamWaitEvent(c->stream, c->join_ev[x], 0));
+        used &= ~(1u << x);
+      }
+    return DCD_OK;
+  }
+  ~SideBySide() {
+    for (int x = 0; x < kMaxBins; x++)
+      if (used & (1u << x)) {
+        cudaEventRecord(c->join_ev[x], c->side[x]);
+        cudaStreamWaitEvent(c->stream, c->join_ev[x], 0);
+      }
+  }
+};
+
 // api.cu: one time step of a context (or of a group's union graph).  Before
 // the step is committed (G_t, C_t, R_t and t replaced), finish(c, user) runs
 // when given: it reads the step's results in c->labels_nx, c->rset_nx and
