@@ -36,6 +36,21 @@ MAX_ITERS = 500
 MAX_LEVELS = 64
 
 
+SANITIZE_FLAGS = ["-O1", "-g", "-fno-omit-frame-pointer", "-fsanitize=address,undefined",
+                  "-fno-sanitize-recover=undefined"]
+
+
+def build_sanitized(out: Path) -> Path:
+    """The same sources with AddressSanitizer and UndefinedBehaviorSanitizer,
+    for a process that preloads the sanitizer runtime and points DCD_ORACLE_LIB
+    at `out` (the sanitizer test does both)."""
+    subprocess.check_call(
+        ["gcc", *SANITIZE_FLAGS, "-std=gnu11", "-fPIC", "-shared", "-Wall", "-Wextra",
+         "-Wno-unused-parameter", str(_SRC), str(_SRC_MLP), "-o", str(out), "-lm"]
+    )
+    return Path(out)
+
+
 def build(force: bool = False) -> Path:
     """Compile the oracle with gcc (portable C: no target-specific flags)."""
     if force or not _LIB.exists() or _LIB.stat().st_mtime < max(
@@ -71,8 +86,11 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        build()
-        L = ctypes.CDLL(str(_LIB))
+        # DCD_ORACLE_LIB: another build of these sources (the sanitizer build)
+        alt = os.environ.get("DCD_ORACLE_LIB")
+        if not alt:
+            build()
+        L = ctypes.CDLL(alt or str(_LIB))
         P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
         sig = {
             "orc_graph_new": (P, [I64, P, P, P]),
