@@ -15,6 +15,8 @@ Parity status per function (pins in ``tests/test_oracle_pins.py``):
                                   m2 preserved, brute-force optimum bound, mode identities)
   screening inserts (Alg. 2)      pinned: hand-built cases
   deletion rule                   parity unpinned (the paper has no deletion rule)
+  smart local moving (dSLM)       pinned: closed forms (split of a disconnected community),
+                                  invariants (nesting, no improving move, coarse Q = fine Q)
   batch apply                     pinned: dictionary re-implementation of the edge set
 """
 from __future__ import annotations
@@ -32,6 +34,7 @@ _SRC_MLP = _HERE / "mlp_oracle.c"
 _LIB = _HERE / "libdcd_oracle.so"
 
 STATIC, BASE, DELTA, GIVEN_R = 0, 1, 2, 3
+LOUVAIN, SLM = 0, 1  # host method of the multi-level run
 MAX_ITERS = 500
 MAX_LEVELS = 64
 
@@ -68,7 +71,8 @@ def build(force: bool = False) -> Path:
 class Stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "t", "n", "nnz", "m2", "r_size", "levels", "iters_total", "iters_level0",
-        "moves_total", "edges_scanned", "communities", "n_lo", "n_hi")] + [("q", ctypes.c_double)]
+        "moves_total", "edges_scanned", "communities", "n_lo", "n_hi")] + [("q", ctypes.c_double)] + [
+        (name, ctypes.c_int64) for name in ("refine_iters", "refine_moves")]
 
     @property
     def N(self) -> int:
@@ -110,6 +114,10 @@ def lib():
             "orc_destroy": (None, [P]),
             "orc_apply_batch": (ctypes.c_int, [P, P, I64, P, I64]),
             "orc_update": (ctypes.c_int, [P, ctypes.c_int, P, P, P, P]),
+            "orc_update_alg": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, P, P, P, P]),
+            "orc_slm": (ctypes.c_int, [P, P, P, P, P]),
+            "orc_slm_refine": (I64, [P, P, P, P]),
+            "orc_slm_level": (I64, [P, P, P, P]),
             "orc_get_rset": (ctypes.c_int, [P, P]),
             "orc_ctx_graph": (P, [P]),
             "orc_set_labels": (ctypes.c_int, [P, P]),
@@ -250,6 +258,34 @@ class Graph:
         g = Graph(lib().orc_coarsen(self._h, _p(lab), _p(cid)))
         return g, cid
 
+    def slm(self, init=None, active=None):
+        """Multi-level smart local moving (the dSLM-Delta-s host method)."""
+        n = self.n
+        ini = np.arange(n, dtype=np.int32) if init is None else np.ascontiguousarray(init, np.int32)
+        act = None if active is None else np.ascontiguousarray(active, dtype=np.uint8)
+        out = np.zeros(n, np.int32)
+        st = Stats()
+        rc = lib().orc_slm(self._h, _p(ini), _p(act), _p(out), ctypes.byref(st))
+        if rc != 0:
+            raise RuntimeError(f"orc_slm failed: {rc}")
+        return out, st
+
+    def slm_refine(self, parent):
+        """Sub-communities of each parent community (canonical), passes, moves."""
+        par = np.ascontiguousarray(parent, dtype=np.int32)
+        sub = np.zeros(self.n, np.int32)
+        moves = ctypes.c_int64()
+        it = lib().orc_slm_refine(self._h, _p(par), _p(sub), ctypes.byref(moves))
+        return sub, int(it), moves.value
+
+    def slm_level(self, labels, active=None):
+        """SLM local moving of one level: (canonical labels, passes, moves)."""
+        lab = np.array(labels, dtype=np.int32, copy=True)
+        act = None if active is None else np.ascontiguousarray(active, dtype=np.uint8)
+        moves = ctypes.c_int64()
+        it = lib().orc_slm_level(self._h, _p(lab), _p(act), ctypes.byref(moves))
+        return lab, int(it), moves.value
+
     def louvain(self, init=None, active=None):
         n = self.n
         ini = np.arange(n, dtype=np.int32) if init is None else np.ascontiguousarray(init, np.int32)
@@ -308,13 +344,13 @@ class Context:
         del2 = _edges2(dels)
         return int(lib().orc_apply_batch(self._h, _p(ins3), len(ins3), _p(del2), len(del2)))
 
-    def update(self, mode: int = DELTA, r_given=None):
+    def update(self, mode: int = DELTA, r_given=None, alg: int = LOUVAIN):
         labels = np.zeros(self.n, np.int32)
         q = ctypes.c_double()
         st = Stats()
         r = None if r_given is None else np.ascontiguousarray(r_given, dtype=np.uint8)
-        rc = lib().orc_update(self._h, int(mode), _p(r), _p(labels), ctypes.byref(q),
-                              ctypes.byref(st))
+        rc = lib().orc_update_alg(self._h, int(alg), int(mode), _p(r), _p(labels), ctypes.byref(q),
+                                  ctypes.byref(st))
         if rc != 0:
             raise RuntimeError(f"orc_update failed: {rc}")
         return labels, q.value, st

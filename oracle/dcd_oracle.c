@@ -591,6 +591,237 @@ int orc_louvain(const orc_graph* g0, const int32_t* init, const uint8_t* active0
 }
 
 /* ------------------------------------------------------------------ */
+/* Smart local moving (the paper's second host method, dSLM-Delta-s)   */
+/* ------------------------------------------------------------------ */
+
+/* The paper applies Delta-screening to SLM (Waltman and van Eck's smart
+ * local moving) as well as to Louvain and defers to SLM's own definition.
+ * Restated here in the synchronous, exact-integer form of the Louvain code
+ * above, with these readings:
+ *   - a local-move pass also offers every vertex an empty community (SLM's
+ *     local moving does); vertex v's empty community is label n + v, chosen
+ *     only when its gain is larger than every neighbouring community's; after
+ *     each pass every community is renamed to its smallest member id;
+ *   - passes alternate direction: an even pass moves vertices only to
+ *     smaller labels, an odd pass only to larger ones (the empty community
+ *     counts as larger).  SLM's coarse levels start from whole communities,
+ *     and two communities that both prefer each other would otherwise swap
+ *     their members in every synchronous pass; one direction per pass lets
+ *     them merge, and replaces the singleton-swap guard of the Louvain code;
+ *   - a level stops after a down-and-up cycle of two passes that moved
+ *     nothing or gained at most 1e-6 of |Q|, or after 500 passes;
+ *   - refinement: each community is split by local moving from singletons
+ *     restricted to the edges inside it, with the gains of the whole graph
+ *     (k_v and 2m of the graph, a over the sub-communities), so it optimises
+ *     the same modularity; it moves nothing between communities and runs over
+ *     every vertex;
+ *   - aggregation: sub-communities become vertices (rank of the sub label),
+ *     each starting in the community that holds it (named by its smallest
+ *     coarse member); the run stops when every sub-community is a single
+ *     vertex, when a level >= 1 gained at most 1e-6 of |Q|, or at 64 levels;
+ *   - Delta-screening: R_t restricts the local moving of level 0 only. */
+
+/* The SLM choice for one vertex from a snapshot.  parent (NULL = none)
+ * restricts the candidates to neighbours in v's parent community; up (0 or 1)
+ * is the pass direction: only labels below C, or only above (empty included). */
+static int32_t slm_best_move(const orc_graph* g, const int32_t* labels, const int32_t* parent,
+                             const int64_t* k, const int64_t* a, const int64_t* size, int64_t m2,
+                             int32_t v, int up, lw* buf) {
+  int32_t C = labels[v];
+  int64_t cnt = 0;
+  for (int64_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; e++) {
+    int32_t u = g->col[e];
+    if (u == v || (parent && parent[u] != parent[v])) continue;
+    buf[cnt].label = labels[u];
+    buf[cnt].w = g->w[e];
+    cnt++;
+  }
+  qsort(buf, (size_t)cnt, sizeof(lw), cmp_lw);
+  int64_t eC = 0;
+  for (int64_t i = 0; i < cnt; i++) if (buf[i].label == C) eC += buf[i].w;
+  int32_t best = C;
+  i128 bestS = 0;
+  for (int64_t i = 0; i < cnt;) {
+    int32_t D = buf[i].label;
+    int64_t eD = 0;
+    int64_t j = i;
+    while (j < cnt && buf[j].label == D) eD += buf[j++].w;
+    i = j;
+    if (D == C || (up ? D < C : D > C)) continue;
+    i128 S = gain_S(m2, k[v], eD, eC, a[D], a[C]);
+    if (S > bestS) { bestS = S; best = D; }
+  }
+  if (up && size[C] > 1) {
+    i128 S0 = gain_S(m2, k[v], 0, eC, 0, a[C]);  /* into an empty community */
+    if (S0 > bestS) return (int32_t)(g->n + v);
+  }
+  return best;
+}
+
+/* Every community named by its smallest member (labels in [0, 2n) in, [0, n) out). */
+static void canonical(int64_t n, int32_t* labels, int32_t* minid /* 2n scratch */) {
+  for (int64_t c = 0; c < 2 * n; c++) minid[c] = INT32_MAX;
+  for (int64_t v = 0; v < n; v++)
+    if ((int32_t)v < minid[labels[v]]) minid[labels[v]] = (int32_t)v;
+  for (int64_t v = 0; v < n; v++) labels[v] = minid[labels[v]];
+}
+
+/* One synchronous SLM pass; labels canonical on entry and exit.  Returns movers. */
+static int64_t slm_pass(const orc_graph* g, int32_t* labels, const int32_t* parent,
+                        const uint8_t* active, int up, const int64_t* k, int64_t m2, lw* buf,
+                        int32_t* next, int32_t* scratch) {
+  int64_t n = g->n, moves = 0;
+  int64_t* a = (int64_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+  int64_t* size = (int64_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+  community_sums(n, labels, k, a, size);
+  for (int64_t v = 0; v < n; v++) {
+    next[v] = labels[v];
+    if (active && !active[v]) continue;
+    next[v] = slm_best_move(g, labels, parent, k, a, size, m2, (int32_t)v, up, buf);
+    if (next[v] != labels[v]) moves++;
+  }
+  memcpy(labels, next, (size_t)n * sizeof(int32_t));
+  canonical(n, labels, scratch);
+  free(a); free(size);
+  return moves;
+}
+
+/* Passes to convergence: down-and-up cycles until a cycle moves nothing or
+ * gains at most 1e-6 of |Q| of the partition being moved, or 500 passes.
+ * Returns the number of passes. */
+static int64_t slm_level(const orc_graph* g, int32_t* labels, const int32_t* parent,
+                         const uint8_t* active, int64_t* moves_out, int64_t* edges_out) {
+  int64_t n = g->n, m2, iters = 0, moves = 0, edges = 0, act_deg = 0, maxdeg = 1;
+  int64_t* k = (int64_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+  int32_t* next = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+  int32_t* scratch = (int32_t*)malloc((size_t)(n > 0 ? 2 * n : 2) * sizeof(int32_t));
+  weighted_degrees(g, k, &m2);
+  for (int64_t v = 0; v < n; v++) {
+    int64_t d = g->row_ptr[v + 1] - g->row_ptr[v];
+    if (d > maxdeg) maxdeg = d;
+    if (!active || active[v]) act_deg += d;
+  }
+  lw* buf = (lw*)malloc((size_t)maxdeg * sizeof(lw));
+  i128 N_old = modularity_N(g, labels, &m2);
+  int64_t cycle_moves = 0;
+  while (iters < ORC_MAX_ITERS) {
+    const int up = (int)(iters & 1);
+    int64_t mv = slm_pass(g, labels, parent, active, up, k, m2, buf, next, scratch);
+    iters++;
+    edges += act_deg;
+    moves += mv;
+    cycle_moves += mv;
+    if (!up) continue;
+    if (cycle_moves == 0) break;
+    cycle_moves = 0;
+    i128 N_new = modularity_N(g, labels, &m2);
+    if (below_tau(N_new - N_old, N_old)) break;
+    N_old = N_new;
+  }
+  free(buf); free(k); free(next); free(scratch);
+  if (moves_out) *moves_out = moves;
+  if (edges_out) *edges_out = edges;
+  return iters;
+}
+
+int64_t orc_slm_refine(const orc_graph* g, const int32_t* parent, int32_t* sub, int64_t* moves) {
+  for (int64_t v = 0; v < g->n; v++) sub[v] = (int32_t)v;
+  return slm_level(g, sub, parent, NULL, moves, NULL);
+}
+
+int64_t orc_slm_level(const orc_graph* g, int32_t* labels, const uint8_t* active, int64_t* moves) {
+  int32_t* scratch = (int32_t*)malloc((size_t)(g->n > 0 ? 2 * g->n : 2) * sizeof(int32_t));
+  canonical(g->n, labels, scratch);
+  free(scratch);
+  return slm_level(g, labels, NULL, active, moves, NULL);
+}
+
+int orc_slm(const orc_graph* g0, const int32_t* init, const uint8_t* active0, int32_t* out,
+            orc_stats* st) {
+  int64_t n0 = g0->n;
+  int32_t* comp = (int32_t*)malloc((size_t)(n0 > 0 ? n0 : 1) * sizeof(int32_t));
+  int32_t* L = (int32_t*)malloc((size_t)(n0 > 0 ? n0 : 1) * sizeof(int32_t));
+  int32_t* scratch = (int32_t*)malloc((size_t)(n0 > 0 ? 2 * n0 : 2) * sizeof(int32_t));
+  for (int64_t v = 0; v < n0; v++) { comp[v] = (int32_t)v; L[v] = init[v]; }
+  canonical(n0, L, scratch);
+  free(scratch);
+  const orc_graph* g = g0;
+  orc_graph* owned = NULL;
+  const uint8_t* active = active0;
+  int64_t m2;
+  i128 N_start = modularity_N(g, L, &m2);
+  int64_t level = 0, iters_total = 0, iters0 = 0, moves_total = 0, edges_total = 0;
+  int64_t refine_iters = 0, refine_moves = 0;
+  for (;;) {
+    int64_t moves = 0, edges = 0;
+    int64_t it = slm_level(g, L, NULL, active, &moves, &edges);
+    iters_total += it;
+    if (level == 0) iters0 = it;
+    moves_total += moves;
+    edges_total += edges;
+    i128 N_end = modularity_N(g, L, &m2);
+    int64_t nv = g->n;
+    int32_t* sub = (int32_t*)malloc((size_t)(nv > 0 ? nv : 1) * sizeof(int32_t));
+    int64_t rmoves = 0;
+    refine_iters += orc_slm_refine(g, L, sub, &rmoves);
+    refine_moves += rmoves;
+    int64_t ns = 0;
+    for (int64_t v = 0; v < nv; v++) if (sub[v] == (int32_t)v) ns++;  /* canonical: one min member each */
+    level++;
+    int stop = ns == nv || (level >= 2 && below_tau(N_end - N_start, N_start)) || level >= ORC_MAX_LEVELS;
+    if (stop) { free(sub); break; }
+    int32_t* cid = (int32_t*)malloc((size_t)(nv > 0 ? nv : 1) * sizeof(int32_t));
+    orc_graph* cg = orc_coarsen(g, sub, cid);
+    for (int64_t v = 0; v < n0; v++) comp[v] = cid[comp[v]];
+    /* coarse start: the community holding the sub-community, named by its
+     * smallest coarse member (the sub-community of the community's smallest
+     * fine member, since coarse ids rank the sub labels) */
+    int32_t* Lc = (int32_t*)malloc((size_t)(cg->n > 0 ? cg->n : 1) * sizeof(int32_t));
+    for (int64_t v = 0; v < nv; v++) Lc[cid[v]] = cid[L[v]];
+    free(cid); free(sub);
+    if (owned) orc_graph_free(owned);
+    owned = cg;
+    g = cg;
+    free(L);
+    L = Lc;
+    active = NULL;
+    N_start = N_end;
+  }
+  int64_t nf = g->n;
+  int32_t* minid = (int32_t*)malloc((size_t)(nf > 0 ? nf : 1) * sizeof(int32_t));
+  for (int64_t c = 0; c < nf; c++) minid[c] = INT32_MAX;
+  for (int64_t v = 0; v < n0; v++) {
+    int32_t c = L[comp[v]];
+    if ((int32_t)v < minid[c]) minid[c] = (int32_t)v;
+  }
+  int64_t ncomm = 0;
+  for (int64_t v = 0; v < n0; v++) {
+    out[v] = minid[L[comp[v]]];
+    if (out[v] == (int32_t)v) ncomm++;
+  }
+  if (st) {
+    i128 N = modularity_N(g0, out, &m2);
+    st->n = n0;
+    st->nnz = g0->row_ptr[n0];
+    st->m2 = m2;
+    st->levels = level;
+    st->iters_total = iters_total;
+    st->iters_level0 = iters0;
+    st->moves_total = moves_total;
+    st->edges_scanned = edges_total;
+    st->communities = ncomm;
+    st->n_lo = (int64_t)(uint64_t)N;
+    st->n_hi = (int64_t)(N >> 64);
+    st->q = q_from(N, m2);
+    st->refine_iters = refine_iters;
+    st->refine_moves = refine_moves;
+  }
+  free(minid); free(comp); free(L);
+  if (owned) orc_graph_free(owned);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
 /* Incremental driver (Sec. III-D)                                     */
 /* ------------------------------------------------------------------ */
 
@@ -657,6 +888,12 @@ int orc_apply_batch(orc_ctx* c, const int32_t* ins, int64_t n_ins, const int32_t
  * Static(G_t) from scratch (the naive approach, Sec. III-C). */
 int orc_update(orc_ctx* c, int mode, const uint8_t* r_given, int32_t* labels_out,
                double* q_out, orc_stats* st) {
+  return orc_update_alg(c, ORC_LOUVAIN, mode, r_given, labels_out, q_out, st);
+}
+
+int orc_update_alg(orc_ctx* c, int alg, int mode, const uint8_t* r_given, int32_t* labels_out,
+                   double* q_out, orc_stats* st) {
+  if (alg != ORC_LOUVAIN && alg != ORC_SLM) return ORC_EINVAL;
   int err;
   int64_t n = c->n;
   orc_graph* gt = orc_apply(c->g, c->ins, c->n_ins, c->del, c->n_del, NULL, &err);
@@ -673,7 +910,8 @@ int orc_update(orc_ctx* c, int mode, const uint8_t* r_given, int32_t* labels_out
   }
   orc_stats s;
   memset(&s, 0, sizeof(s));
-  orc_louvain(gt, init, c->rset, c->labels, &s);
+  if (alg == ORC_SLM) orc_slm(gt, init, c->rset, c->labels, &s);
+  else orc_louvain(gt, init, c->rset, c->labels, &s);
   free(init);
   int64_t r = 0;
   for (int64_t v = 0; v < n; v++) r += c->rset[v];

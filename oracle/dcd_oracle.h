@@ -24,6 +24,7 @@ extern "C" {
 #endif
 
 enum { ORC_STATIC = 0, ORC_BASE = 1, ORC_DELTA = 2, ORC_GIVEN_R = 3 };
+enum { ORC_LOUVAIN = 0, ORC_SLM = 1 }; /* the host method of the multi-level run */
 
 enum {
   ORC_OK = 0,
@@ -53,6 +54,8 @@ typedef struct {
   int64_t communities;    /* |C_t|                                        */
   int64_t n_lo, n_hi;     /* N as a 128-bit integer (two's complement)    */
   double q;               /* modularity Q_t                               */
+  int64_t refine_iters;   /* SLM: refinement passes over all levels       */
+  int64_t refine_moves;   /* SLM: moves applied by the refinements        */
 } orc_stats;
 
 /* ---- graphs (CSR: int64 row_ptr[n+1], int32 col[nnz] sorted, int64 w) ---- */
@@ -102,6 +105,17 @@ int orc_screen(const orc_graph* g_prev, const orc_graph* g_t, const int32_t* lab
 int orc_louvain(const orc_graph* g, const int32_t* init, const uint8_t* active,
                 int32_t* out, orc_stats* st);
 
+/* Smart local moving, the paper's second host method (dSLM-Delta-s), with the
+ * readings stated in dcd_oracle.c.  orc_slm: multi-level SLM from init with
+ * the level-0 active set (NULL = all); out = canonical labels.
+ * orc_slm_refine: the refinement of one level (sub-communities of each
+ * parent community, canonical).  orc_slm_level: SLM local moving of one level
+ * (labels made canonical first, updated in place).  Both return passes. */
+int orc_slm(const orc_graph* g, const int32_t* init, const uint8_t* active, int32_t* out,
+            orc_stats* st);
+int64_t orc_slm_refine(const orc_graph* g, const int32_t* parent, int32_t* sub, int64_t* moves);
+int64_t orc_slm_level(const orc_graph* g, int32_t* labels, const uint8_t* active, int64_t* moves);
+
 /* Learned-screen pool and features (not in the paper): see dcd_oracle.c. */
 int orc_screen_features(const orc_graph* g_prev, const orc_graph* g_t, const int32_t* labels, const int32_t* ins,
                         int64_t n_ins, const int32_t* del, int64_t n_del, const uint8_t* rds, uint8_t* pool_out,
@@ -116,6 +130,9 @@ int orc_apply_batch(orc_ctx* c, const int32_t* ins, int64_t n_ins, const int32_t
  * The first update of a context is always static (step 1 of Sec. III-D). */
 int orc_update(orc_ctx* c, int mode, const uint8_t* r_given, int32_t* labels_out,
                double* q_out, orc_stats* st);
+/* As orc_update with the host method alg (ORC_LOUVAIN or ORC_SLM). */
+int orc_update_alg(orc_ctx* c, int alg, int mode, const uint8_t* r_given, int32_t* labels_out,
+                   double* q_out, orc_stats* st);
 int orc_get_rset(const orc_ctx* c, uint8_t* r_out);
 const orc_graph* orc_ctx_graph(const orc_ctx* c);
 int orc_set_labels(orc_ctx* c, const int32_t* labels);

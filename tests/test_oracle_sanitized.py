@@ -18,14 +18,15 @@ from paper_1904_08553_gb300 import synth
 
 synth.lib()
 s = synth.lfr(synth.seed_for(1, 21), n=3000, n_events=40_000, steps=4, kmin=4, kmax=500, smin=20, smax=500)
-for mode in (orc.STATIC, orc.BASE, orc.DELTA):
-    c = orc.Context(s.n)
-    for ins, dels in s.steps:
-        c.apply_batch(ins, dels)
-        lab, q, st = c.update(mode)
-        c.rset()
-    c.graph_csr()
-    c.set_labels(lab)
+for alg in (orc.LOUVAIN, orc.SLM):
+    for mode in (orc.STATIC, orc.BASE, orc.DELTA):
+        c = orc.Context(s.n)
+        for ins, dels in s.steps:
+            c.apply_batch(ins, dels)
+            lab, q, st = c.update(mode, alg=alg)
+            c.rset()
+        c.graph_csr()
+        c.set_labels(lab)
 g_prev = orc.Graph.empty(s.n)
 lab = np.arange(s.n, dtype=np.int32)
 for ins, dels in s.steps:
@@ -39,6 +40,9 @@ for ins, dels in s.steps:
     g_t.run_level(lab2.copy())
     g_t.local_move_pass(lab2.copy())
     g_t.gain(lab2, 0, int(lab2[1]))
+    g_t.slm(lab, r)
+    g_t.slm_refine(lab2)
+    g_t.slm_level(lab2, r)
     g_prev, lab = g_t, lab2
 P = np.random.default_rng(0).normal(0, 0.2, orc.mlp_nparams()).astype(np.float32)
 X = np.random.default_rng(1).normal(0, 1, (257, 12)).astype(np.float32)
