@@ -23,8 +23,11 @@
  *     "device" are CUDA device memory of the context's device; "host or
  *     device" pointers are told apart with cudaPointerGetAttributes.
  *     The library never takes ownership of caller memory.
- *   - All device work runs on the CUDA stream given to dcd_create (NULL =
- *     the legacy default stream); every call returns with that work complete
+ *   - All device work is ordered on the CUDA stream given to dcd_create
+ *     (NULL: a stream the context creates, see dcd_create).  Kernels with
+ *     disjoint outputs may run on side streams the context owns, forked from
+ *     that stream and joined back into it within the same call, so the caller
+ *     sees one stream's order.  Every call returns with its work complete
  *     unless the call says otherwise.
  *   - Not thread-safe per context: one context, one host thread at a time.
  */
