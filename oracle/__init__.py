@@ -18,7 +18,8 @@ Parity status per function (pins in ``tests/test_oracle_pins.py``):
   smart local moving (dSLM)       pinned: closed forms (split of a disconnected community),
                                   invariants (nesting, no improving move, coarse Q = fine Q)
   batch apply                     pinned: dictionary re-implementation of the edge set
-  learned-screen pool, features   pinned: re-implementation from the feature definitions
+  learned-screen pool, features   parity unpinned (not in the paper); cross-checked against a
+                                  second implementation of the feature definitions
 """
 from __future__ import annotations
 
