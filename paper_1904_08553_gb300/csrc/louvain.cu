@@ -1284,13 +1284,13 @@ int launch_lm_bins(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEven
   for (int x = 0; x < b.plan.nb; x++) {
     const int64_t cnt = b.cnt[x], o = b.off[x];
     const cudaStream_t s = fork && cnt ? c->side[x] : s0;
-    if (fork) {
-      if (cnt) {
-        DCD_TRY_CUDA(cudaStreamWaitEvent(s, c->fork_ev, 0));
-        *forked |= 1u << x;
-      }
-      DCD_TRY_CUDA(cudaEventRecordWithFlags(c->bin_start[x], s, ev_flags));
+    if (fork && cnt) {
+      DCD_TRY_CUDA(cudaStreamWaitEvent(s, c->fork_ev, 0));
+      *forked |= 1u << x;
     }
+    // a bin's interval starts on its own stream (forked or not), so every
+    // interval the caller times has both its events recorded
+    if (bin_ev) DCD_TRY_CUDA(cudaEventRecordWithFlags(c->bin_start[x], s, ev_flags));
     if (cnt) {
       LV<W> g = lv;  // feature outputs shifted to the bin's list offset
       if (g.f_eC) {
@@ -1442,7 +1442,7 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
     DCD_TRY_CUDA(cudaMemsetAsync(moved_big_cnt.get(), 0, sizeof(int32_t), s));
     DCD_TRY_CUDA(cudaMemsetAsync(&d->any_running, 0, sizeof(int32_t), s));
     DCD_TRY_CUDA(cudaEventRecordWithFlags(c->ev[2], s, evf));
-    if (any) DCD_TRY(launch_lm_nocfg<W>(c, lvl, bins, prop.get(), &c->ev[12], evf, true));
+    if (any) DCD_TRY(launch_lm_nocfg<W>(c, lvl, bins, prop.get(), &c->ev[12], evf, total >= kForkMin));
     else
       for (int x = 0; x < bins.plan.nb; x++) {
         DCD_TRY_CUDA(cudaEventRecordWithFlags(c->bin_start[x], s, evf));

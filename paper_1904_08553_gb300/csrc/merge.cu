@@ -691,7 +691,7 @@ int merge_batch(dcd_ctx* c, const int32_t* labels0, MergeOut* out) {
   // merge_rows skips the rows above kLongRow entries, which merge_long takes:
   // the two write disjoint rows (and add into 2m and sum e_{i->C(i)} with
   // atomics), so they run side by side
-  SideBySide par(c);
+  SideBySide par(c, n);
   DCD_TRY(par.fork());
   cudaStream_t s_long;
   DCD_TRY(par.on(0, &s_long));

@@ -782,7 +782,7 @@ int screen_impl(dcd_ctx* c, SV& sv, const Csr<int32_t>& g, const int64_t* cnt, i
   {
     HubBufs hb;
     if (cnt[3]) DCD_TRY(hub_setup(c, sv.src + off3, cnt[3], g.rp, &hb));
-    SideBySide par(c);
+    SideBySide par(c, nsrc);
     DCD_TRY(par.fork());
     cudaStream_t sx;
     if (cnt[0]) {
@@ -867,7 +867,7 @@ int screen_impl(dcd_ctx* c, SV& sv, const Csr<int32_t>& g, const int64_t* cnt, i
                                                                         gcnt[3], jl.get());
       DCD_TRY(hub_setup(c, jl.get(), gcnt[3], g.rp, &hb));
     }
-    SideBySide par(c);
+    SideBySide par(c, nsrc);
     DCD_TRY(par.fork());
     cudaStream_t sx;
     if (gcnt[0]) {

@@ -220,18 +220,29 @@ int side_streams(dcd_ctx* c);
 // destructor joins whatever is left, so an error return never leaves side
 // work unjoined; declare it after the buffers the side work uses, so that
 // they are released (stream-ordered, on the context stream) after the join.
+// Below kForkMin items the kernels are too small to gain from running side
+// by side and the fork would only add its events: everything then stays on
+// the context stream.
+constexpr int64_t kForkMin = (int64_t)1 << 16;
+
 struct SideBySide {
   dcd_ctx* c;
+  bool enabled;
   unsigned used = 0;
-  explicit SideBySide(dcd_ctx* cc) : c(cc) {}
+  SideBySide(dcd_ctx* cc, int64_t items) : c(cc), enabled(items >= kForkMin) {}
   SideBySide(const SideBySide&) = delete;
   SideBySide& operator=(const SideBySide&) = delete;
   int fork() {
+    if (!enabled) return DCD_OK;
     DCD_TRY(side_streams(c));
     DCD_TRY_CUDA(cudaEventRecord(c->fork_ev, c->stream));
     return DCD_OK;
   }
   int on(int x, cudaStream_t* out) {
+    if (!enabled) {
+      *out = c->stream;
+      return DCD_OK;
+    }
     if (!(used & (1u << x))) {
       DCD_TRY_CUDA(cudaStreamWaitEvent(c->side[x], c->fork_ev, 0));
       used |= 1u << x;
