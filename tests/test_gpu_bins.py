@@ -5,7 +5,7 @@ plans are refused without changing the context."""
 import numpy as np
 import pytest
 
-from test_gpu_parity import dcd, run_stream  # noqa: F401  (fixture + helper)
+from test_gpu_parity import dcd  # noqa: F401  (fixture)
 
 pytestmark = pytest.mark.gpu
 
