@@ -573,6 +573,89 @@ def batched_arm(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ temporal resolution
+
+RES_FINE_STEPS = 28
+RES_BINS = (2, 4, 8, 12, 16, 20, 24, 28)
+
+
+def resolution_stream(n: int, replica: int = 0):
+    """An insert-only LFR-style interaction stream of 28 fine steps (no drift,
+    no deletes: the shape of a temporal interaction log), LFR_EVENTS scaled by
+    n / LFR_N."""
+    from paper_1904_08553_gb300 import synth
+
+    synth.build()
+    events = int(round(LFR_EVENTS * n / LFR_N))
+    return synth.lfr(synth.seed_for(5, replica), n, events, RES_FINE_STEPS, kmax=min(20_000.0, n / 2),
+                     smax=min(50_000.0, n / 4), drift=0.0, del_frac=0.0)
+
+
+def resolution_sweep(make_ctx, fine, ks, modes):
+    """The temporal-resolution experiment of Sec. IV-C on one insert-only
+    stream: for every binning k of it and every mode, a fresh context runs the
+    k steps.  make_ctx(n, mode) returns an object with step(ins, dels) ->
+    (Q, ms, |R_t|) and close().  Rows: k, mode, total ms, mean Q over the
+    steps, mean |R_t| / n."""
+    from paper_1904_08553_gb300 import synth
+
+    rows = []
+    for k in ks:
+        s = synth.rebin(fine, k)
+        for mode in modes:
+            ctx = make_ctx(s.n, mode)
+            qs, ms, rs = [], [], []
+            for ins, dels in s.steps:
+                q, t_ms, r = ctx.step(ins, dels)
+                qs.append(q)
+                ms.append(t_ms)
+                rs.append(r / s.n)
+            ctx.close()
+            rows.append({"steps": k, "mode": mode, "total_ms": float(sum(ms)), "mean_q": float(np.mean(qs)),
+                         "mean_r_fraction": float(np.mean(rs))})
+    return rows
+
+
+def resolution_arm(args):
+    """Sweep on the GPU: Delta-screening against dLouvain-base at every
+    binning; reports the savings and mean modularity per number of steps."""
+    import torch
+
+    from paper_1904_08553_gb300 import dcd
+
+    dcd.lib()
+    torch.cuda.set_device(0)
+    fine = resolution_stream(args.n)
+
+    class Ctx:
+        def __init__(self, n, mode):
+            self.c = dcd.Context(n, mode={"base": dcd.MODE_BASE, "delta": dcd.MODE_DELTA}[mode])
+
+        def step(self, ins, dels):
+            self.c.apply_batch(ins, dels)
+            _, q, st = self.c.update(labels_out=None)
+            return q, st.ms_total, st.r_size
+
+        def close(self):
+            self.c.close()
+
+    rows = resolution_sweep(Ctx, fine, RES_BINS, ("base", "delta"))
+    table = []
+    for k in RES_BINS:
+        b = next(r for r in rows if r["steps"] == k and r["mode"] == "base")
+        d = next(r for r in rows if r["steps"] == k and r["mode"] == "delta")
+        table.append({"steps": k, "ms_base": b["total_ms"], "ms_delta": d["total_ms"],
+                      "savings_pct": 100.0 * (1.0 - d["total_ms"] / b["total_ms"]) if b["total_ms"] > 0 else None,
+                      "mean_q_base": b["mean_q"], "mean_q_delta": d["mean_q"],
+                      "mean_r_fraction_delta": d["mean_r_fraction"]})
+    print(json.dumps({
+        "metric": "temporal-resolution sweep: Delta-screening savings and mean modularity per number of steps",
+        "workload": (f"insert-only LFR-style stream, n={args.n:,}, {sum(len(i) for i, _ in fine.steps):,} "
+                     f"events in {RES_FINE_STEPS} fine steps, rebinned into k steps"),
+        "n_gpus": 1, "unit": "ms (device time of the updates, all steps)", "rows": table,
+    }), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -582,7 +665,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--n", type=int, default=LFR_N, help="vertex count (smaller cases for profiling)")
-    ap.add_argument("--workload", default="lfr_2m", choices=["lfr_2m", "learned", "batched"])
+    ap.add_argument("--workload", default="lfr_2m", choices=["lfr_2m", "learned", "batched", "resolution"])
     ap.add_argument("--graphs", type=int, default=512)
     ap.add_argument("--train-seeds", type=int, default=40)
     ap.add_argument("--eval", default="lfr,rmat", help="learned workload: evaluation streams (lfr, rmat)")
@@ -599,6 +682,8 @@ def main():
         learned_arm(args)
     elif args.workload == "batched":
         batched_arm(args)
+    elif args.workload == "resolution":
+        resolution_arm(args)
     else:
         gpu_arm(args)
 

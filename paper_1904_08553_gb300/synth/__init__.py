@@ -116,6 +116,24 @@ def _collect(h) -> Stream:
         L.dcdsyn_free(h)
 
 
+def rebin(stream: Stream, k: int) -> Stream:
+    """The same insert-only stream at a coarser temporal resolution: its steps
+    merged into k consecutive groups (group g holds steps [g T / k, (g+1) T / k)
+    rounded down).  Inserts commute, so every binning ends in the same graph;
+    a stream with deletes is refused (a delete and an insert of one edge do not
+    commute)."""
+    T = len(stream.steps)
+    if not 1 <= k <= T:
+        raise ValueError(f"k must be in [1, {T}]")
+    if any(len(d) for _, d in stream.steps):
+        raise ValueError("rebinning needs an insert-only stream")
+    bounds = [(g * T) // k for g in range(k + 1)]
+    empty = np.zeros((0, 2), np.int32)
+    steps = [(np.concatenate([stream.steps[t][0] for t in range(bounds[g], bounds[g + 1])]), empty)
+             for g in range(k)]
+    return Stream(stream.n, steps, stream.planted)
+
+
 def sbm(seed: int, sizes, m_intra: int, m_inter: int, steps: int, ins_count: int = 0,
         ins_frac: float = 0.0, del_count: int = 0, del_frac: float = 0.0,
         intra_frac: float = 0.8) -> Stream:
