@@ -198,6 +198,17 @@ int dcd_set_bins(dcd_ctx* ctx, int32_t nb, const int32_t* variant, const int64_t
 int dcd_get_bins(const dcd_ctx* ctx, int32_t* nb, int32_t* variant, int64_t* hi);
 int dcd_autotune(dcd_ctx* ctx, int32_t reps, float* best_ms);
 
+/* Level 0 of the last update's local move (Algorithm 1 over R_t), as run:
+ * *nb bins of the plan in force; count[b] the active vertices of bin b;
+ * per_sweep[b] the vertices one sweep of bin b's kernel grid covers (a bin
+ * holding more runs its grid-stride loop more than once; for the hub bin it
+ * equals the count); *side_by_side 1 when the bins ran concurrently on side
+ * streams.  Outputs are host memory; count, per_sweep and side_by_side may
+ * be NULL.  Before the first update *nb is 0.  Errors: DCD_EINVAL (ctx or nb
+ * NULL). */
+int dcd_get_level0_bins(const dcd_ctx* ctx, int32_t* nb, int64_t* count, int64_t* per_sweep,
+                        int32_t* side_by_side);
+
 /* The CSR of G_t: *nnz_out receives the entry count; when row_ptr/col/w are
  * non-NULL they receive n+1 int64, nnz int32 and nnz int32 (host memory). */
 int dcd_get_graph(dcd_ctx* ctx, int64_t* nnz_out, int64_t* row_ptr, int32_t* col, int32_t* w);
@@ -333,16 +344,17 @@ int dcd_group_autotune(dcd_group* grp, int32_t reps, float* best_ms);
  * another allocator, such as a framework's caching allocator, or they run
  * where cudaMalloc/cudaFree must not be called or must not synchronise).
  *
- * Modularity Q (Eq. 1) of the partition d_labels of the graph given as a
- * device CSR: d_row_ptr (n+1 int64), d_col and d_w (row_ptr[n] int32 each;
+ * Modularity Q of the partition d_labels of the graph given as a device
+ * CSR: d_row_ptr (n+1 int64), d_col and d_w (row_ptr[n] int32 each;
  * every undirected edge stored in both rows, positive weights), d_labels
  * (n int32 in [0, n)).  *q_out (host) receives Q, *m2_out (host, may be NULL)
  * 2m.  Work runs on cuda_stream (NULL = legacy default stream) and the call
  * returns when it is done.  No device memory is allocated: the scratch is a
  * fixed 8 MiB array that the library reserves on every GPU where it is loaded
- * and keeps until the process exits.  The first call on a device looks up
- * that array's device address; make that first call before any stream
- * capture.  Every call overwrites the array (each call clears what it needs),
+ * and keeps until the process exits.  Every call looks up that array's
+ * device address on the current device (the first lookup on a device loads
+ * the library's device code there); make the first call on a device before
+ * any stream capture.  Every call overwrites the array (each call clears what it needs),
  * so calls whose device work overlaps -- other streams, other host threads --
  * race and return wrong values.
  * Errors: DCD_EINVAL (n <= 0, n > DCD_NOALLOC_MAX_N, NULL pointer, a label or

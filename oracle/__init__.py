@@ -123,6 +123,7 @@ def lib():
             "orc_get_rset": (ctypes.c_int, [P, P]),
             "orc_ctx_graph": (P, [P]),
             "orc_set_labels": (ctypes.c_int, [P, P]),
+            "orc_clone": (P, [P]),
             "orc_mlp_nparams": (ctypes.c_int, []),
             "orc_bf16": (ctypes.c_float, [ctypes.c_float]),
             "orc_mlp_forward": (D, [P, P, P, I64, P]),
@@ -375,6 +376,17 @@ class Context:
     def set_labels(self, labels) -> int:
         lab = np.ascontiguousarray(labels, dtype=np.int32)
         return int(lib().orc_set_labels(self._h, _p(lab)))
+
+    def clone(self) -> "Context":
+        """A deep copy (G_t, C_t, R_t, t, staged batch): the next update of
+        either copy gives the same result."""
+        h = lib().orc_clone(self._h)
+        if not h:
+            raise MemoryError("oracle context copy failed")
+        c = Context.__new__(Context)
+        c._h = h
+        c.n = self.n
+        return c
 
 
 # ---------------------------------------------------------------- learned screen (MLP)

@@ -934,6 +934,37 @@ int orc_get_rset(const orc_ctx* c, uint8_t* r_out) {
 
 const orc_graph* orc_ctx_graph(const orc_ctx* c) { return c->g; }
 
+/* A deep copy of the whole context: G_t, C_t, R_t, t and any staged batch.
+ * Test and timing infrastructure only (a timed step can start again from one
+ * saved state); it computes nothing. */
+orc_ctx* orc_clone(const orc_ctx* c) {
+  if (!c) return NULL;
+  orc_ctx* d = (orc_ctx*)calloc(1, sizeof(orc_ctx));
+  if (!d) return NULL;
+  d->n = c->n;
+  d->t = c->t;
+  d->g = orc_graph_new(c->n, c->g->row_ptr, c->g->col, c->g->w);
+  d->labels = (int32_t*)malloc((size_t)c->n * sizeof(int32_t));
+  d->rset = (uint8_t*)malloc((size_t)c->n);
+  if (!d->g || !d->labels || !d->rset) {
+    orc_destroy(d);
+    return NULL;
+  }
+  memcpy(d->labels, c->labels, (size_t)c->n * sizeof(int32_t));
+  memcpy(d->rset, c->rset, (size_t)c->n);
+  if (c->n_ins) {
+    d->ins = (int32_t*)malloc((size_t)c->n_ins * 3 * sizeof(int32_t));
+    memcpy(d->ins, c->ins, (size_t)c->n_ins * 3 * sizeof(int32_t));
+    d->n_ins = d->cap_ins = c->n_ins;
+  }
+  if (c->n_del) {
+    d->del = (int32_t*)malloc((size_t)c->n_del * 2 * sizeof(int32_t));
+    memcpy(d->del, c->del, (size_t)c->n_del * 2 * sizeof(int32_t));
+    d->n_del = d->cap_del = c->n_del;
+  }
+  return d;
+}
+
 int orc_set_labels(orc_ctx* c, const int32_t* labels) {
   for (int64_t v = 0; v < c->n; v++)
     if (labels[v] < 0 || labels[v] >= c->n) return ORC_EINVAL;

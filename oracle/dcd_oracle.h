@@ -136,6 +136,9 @@ int orc_update_alg(orc_ctx* c, int alg, int mode, const uint8_t* r_given, int32_
 int orc_get_rset(const orc_ctx* c, uint8_t* r_out);
 const orc_graph* orc_ctx_graph(const orc_ctx* c);
 int orc_set_labels(orc_ctx* c, const int32_t* labels);
+/* Deep copy of a context (G_t, C_t, R_t, t, staged batch): test and timing
+ * infrastructure, no arithmetic. */
+orc_ctx* orc_clone(const orc_ctx* c);
 
 #ifdef __cplusplus
 }

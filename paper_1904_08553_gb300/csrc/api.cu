@@ -771,6 +771,17 @@ int dcd_get_bins(const dcd_ctx* c, int32_t* nb, int32_t* variant, int64_t* hi) {
   return DCD_OK;
 }
 
+int dcd_get_level0_bins(const dcd_ctx* c, int32_t* nb, int64_t* count, int64_t* per_sweep, int32_t* side_by_side) {
+  if (!c || !nb) return DCD_EINVAL;
+  *nb = c->l0_nb;
+  for (int b = 0; b < c->l0_nb; b++) {
+    if (count) count[b] = c->l0_cnt[b];
+    if (per_sweep) per_sweep[b] = c->l0_sweep[b];
+  }
+  if (side_by_side) *side_by_side = c->l0_side;
+  return DCD_OK;
+}
+
 int dcd_autotune(dcd_ctx* c, int32_t reps, float* best_ms) {
   if (!c) return DCD_EINVAL;
   DCD_SCOPE(c);

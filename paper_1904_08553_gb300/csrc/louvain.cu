@@ -1222,20 +1222,23 @@ int make_bins(dcd_ctx* c, const Csr<W>& g, const uint8_t* active, Bins* b, const
 }
 
 template <typename W, typename ST, int CAP, int Q>
-int launch_warp_tbl(cudaStream_t s, const LV<W>& g, const int32_t* lst, int64_t cnt, int32_t* prop) {
+int launch_warp_tbl(cudaStream_t s, const LV<W>& g, const int32_t* lst, int64_t cnt, int32_t* prop,
+                    int64_t* sweep) {
   constexpr int T = 256;
   constexpr size_t smem = (size_t)(T / 32) * warp_tbl_bytes<CAP, typename TblVal<ST>::type>();
-  count_launch(), lm_warp_tbl<W, ST, CAP, Q><<<wave_grid(lm_warp_tbl<W, ST, CAP, Q>, cnt * 32, T, smem), T, smem,
-                                                 s>>>(g, lst, cnt, prop);
+  const int grid = wave_grid(lm_warp_tbl<W, ST, CAP, Q>, cnt * 32, T, smem);
+  *sweep = (int64_t)grid * (T / 32);
+  count_launch(), lm_warp_tbl<W, ST, CAP, Q><<<grid, T, smem, s>>>(g, lst, cnt, prop);
   return DCD_OK;
 }
 
 template <typename W, typename ST, int THREADS, int Q>
 int launch_large(dcd_ctx* c, cudaStream_t s, const LV<W>& g, const int32_t* lst, int64_t cnt, int64_t maxd,
-                 int32_t* prop) {
+                 int32_t* prop, int64_t* sweep) {
   const int32_t tcap = (int32_t)table_cap(maxd);
   const size_t smem = (size_t)tcap * (sizeof(typename TblVal<ST>::type) + 6);  // values, keys, claimed-slot list
   const int64_t ctas = cnt < 16 * (int64_t)c->sms ? cnt : 16 * (int64_t)c->sms;
+  *sweep = ctas;
   count_launch(), lm_large<W, ST, THREADS, Q><<<(unsigned)ctas, THREADS, smem, s>>>(g, lst, cnt, prop, tcap);
   return DCD_OK;
 }
@@ -1276,7 +1279,9 @@ int prepare_lm_st() {
 // leaves idle).
 template <typename W, typename ST>
 int launch_lm_bins(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEvent_t* bin_ev, unsigned ev_flags,
-                   bool fork, unsigned* forked) {
+                   bool fork, unsigned* forked, int64_t* sweep_out) {
+  int64_t sweep_tmp[kMaxBins];
+  int64_t* sweep = sweep_out ? sweep_out : sweep_tmp;
   const cudaStream_t s0 = c->stream;
   const int T = 256;
   const int32_t* lst0 = b.list.get();
@@ -1302,29 +1307,32 @@ int launch_lm_bins(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEven
       const int32_t* lst = lst0 + o;
       int32_t* pr = prop + o;
       switch (b.plan.var[x]) {
-        case kLmHalf:
+        case kLmHalf: {
+          const int grid = grid_for(cnt * 16, T, 16);
+          sweep[x] = (int64_t)grid * (T / 16);
           if (g.f_eC)
-            count_launch(), lm_warp<W, ST, 16, true><<<grid_for(cnt * 16, T, 16), T, 0, s>>>(
-                                g, lst, cnt, pr);
+            count_launch(), lm_warp<W, ST, 16, true><<<grid, T, 0, s>>>(g, lst, cnt, pr);
           else
-            count_launch(), lm_warp<W, ST, 16, false><<<grid_for(cnt * 16, T, 16), T, 0, s>>>(
-                                g, lst, cnt, pr);
+            count_launch(), lm_warp<W, ST, 16, false><<<grid, T, 0, s>>>(g, lst, cnt, pr);
           break;
-        case kLmWarp:
+        }
+        case kLmWarp: {
+          const int grid = grid_for(cnt * 32, T, 16);
+          sweep[x] = (int64_t)grid * (T / 32);
           if (g.f_eC)
-            count_launch(), lm_warp<W, ST, 32, true><<<grid_for(cnt * 32, T, 16), T, 0, s>>>(
-                                g, lst, cnt, pr);
+            count_launch(), lm_warp<W, ST, 32, true><<<grid, T, 0, s>>>(g, lst, cnt, pr);
           else
-            count_launch(), lm_warp<W, ST, 32, false><<<grid_for(cnt * 32, T, 16), T, 0, s>>>(
-                                g, lst, cnt, pr);
+            count_launch(), lm_warp<W, ST, 32, false><<<grid, T, 0, s>>>(g, lst, cnt, pr);
           break;
-        case kLmWarp128: DCD_TRY((launch_warp_tbl<W, ST, 256, 4>(s, g, lst, cnt, pr))); break;
-        case kLmWarp256: DCD_TRY((launch_warp_tbl<W, ST, 512, 8>(s, g, lst, cnt, pr))); break;
-        case kLmBlk512: DCD_TRY((launch_large<W, ST, 256, 2>(c, s, g, lst, cnt, b.maxd[x], pr))); break;
-        case kLmBlk1k: DCD_TRY((launch_large<W, ST, 256, 4>(c, s, g, lst, cnt, b.maxd[x], pr))); break;
-        case kLmBlk2k: DCD_TRY((launch_large<W, ST, 256, 8>(c, s, g, lst, cnt, b.maxd[x], pr))); break;
-        case kLmBlk4k: DCD_TRY((launch_large<W, ST, 512, 8>(c, s, g, lst, cnt, b.maxd[x], pr))); break;
+        }
+        case kLmWarp128: DCD_TRY((launch_warp_tbl<W, ST, 256, 4>(s, g, lst, cnt, pr, &sweep[x]))); break;
+        case kLmWarp256: DCD_TRY((launch_warp_tbl<W, ST, 512, 8>(s, g, lst, cnt, pr, &sweep[x]))); break;
+        case kLmBlk512: DCD_TRY((launch_large<W, ST, 256, 2>(c, s, g, lst, cnt, b.maxd[x], pr, &sweep[x]))); break;
+        case kLmBlk1k: DCD_TRY((launch_large<W, ST, 256, 4>(c, s, g, lst, cnt, b.maxd[x], pr, &sweep[x]))); break;
+        case kLmBlk2k: DCD_TRY((launch_large<W, ST, 256, 8>(c, s, g, lst, cnt, b.maxd[x], pr, &sweep[x]))); break;
+        case kLmBlk4k: DCD_TRY((launch_large<W, ST, 512, 8>(c, s, g, lst, cnt, b.maxd[x], pr, &sweep[x]))); break;
         default: {
+          sweep[x] = cnt;
           const unsigned ch = hub_grid(c, b.hub);
           count_launch(), hub_agg<W, ST><<<ch, 256, 0, s>>>(g, b.hub.t);
           count_launch(), hub_gain<W, ST><<<ch, 256, 0, s>>>(g, b.hub.t);
@@ -1347,9 +1355,9 @@ int launch_lm_bins(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEven
 
 template <typename W, typename ST>
 int launch_lm_st(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEvent_t* bin_ev, unsigned ev_flags,
-                 bool fork = false) {
+                 bool fork = false, int64_t* sweep = nullptr) {
   unsigned forked = 0;
-  const int rc = launch_lm_bins<W, ST>(c, lv, b, prop, bin_ev, ev_flags, fork, &forked);
+  const int rc = launch_lm_bins<W, ST>(c, lv, b, prop, bin_ev, ev_flags, fork, &forked, sweep);
   // an error between a fork and its join: join the side streams all the same,
   // so that a stream capture in progress ends with every stream back home
   for (int x = 0; x < kMaxBins; x++)
@@ -1376,9 +1384,9 @@ int launch_lm(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEvent_t* 
 
 template <typename W>
 int launch_lm_nocfg(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEvent_t* bin_ev, unsigned ev_flags,
-                    bool fork) {
-  if (lv.m2 >= ((int64_t)1 << 31)) return launch_lm_st<W, i128>(c, lv, b, prop, bin_ev, ev_flags, fork);
-  return launch_lm_st<W, long long>(c, lv, b, prop, bin_ev, ev_flags, fork);
+                    bool fork, int64_t* sweep) {
+  if (lv.m2 >= ((int64_t)1 << 31)) return launch_lm_st<W, i128>(c, lv, b, prop, bin_ev, ev_flags, fork, sweep);
+  return launch_lm_st<W, long long>(c, lv, b, prop, bin_ev, ev_flags, fork, sweep);
 }
 
 // Per-graph counters of one update (host).
@@ -1432,6 +1440,7 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
   lvl.m2 = G == 1 ? lv.m2 : m2max;  // gain width chosen by the largest graph
   const int32_t* lst = bins.list.get();
   bool any = total > 0;
+  int64_t sweep[kMaxBins] = {};
   // One pass: evaluate, apply, tracked N, stop rule, scalars to the host.
   // Every pass of a level enqueues the same work (the pass number lives on
   // the device), so the body is captured once into a CUDA graph and each pass
@@ -1442,7 +1451,8 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
     DCD_TRY_CUDA(cudaMemsetAsync(moved_big_cnt.get(), 0, sizeof(int32_t), s));
     DCD_TRY_CUDA(cudaMemsetAsync(&d->any_running, 0, sizeof(int32_t), s));
     DCD_TRY_CUDA(cudaEventRecordWithFlags(c->ev[2], s, evf));
-    if (any) DCD_TRY(launch_lm_nocfg<W>(c, lvl, bins, prop.get(), &c->ev[12], evf, total >= kForkMin));
+    if (any)
+      DCD_TRY(launch_lm_nocfg<W>(c, lvl, bins, prop.get(), &c->ev[12], evf, total >= kForkMin, sweep));
     else
       for (int x = 0; x < bins.plan.nb; x++) {
         DCD_TRY_CUDA(cudaEventRecordWithFlags(c->bin_start[x], s, evf));
@@ -1502,6 +1512,14 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
       const cudaError_t ei = cudaGraphInstantiate(&exec.x, graph, 0);
       cudaGraphDestroy(graph);
       DCD_TRY_CUDA(ei);
+      if (level == 0) {  // the level-0 bin record (dcd_get_level0_bins)
+        c->l0_nb = bins.plan.nb;
+        c->l0_side = any && total >= kForkMin;
+        for (int x = 0; x < kMaxBins; x++) {
+          c->l0_cnt[x] = x < bins.plan.nb ? bins.cnt[x] : 0;
+          c->l0_sweep[x] = x < bins.plan.nb ? sweep[x] : 0;
+        }
+      }
     } else {
       g_launches += body_launches;
     }

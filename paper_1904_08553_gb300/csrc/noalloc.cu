@@ -104,20 +104,14 @@ __global__ void na_final(int64_t n, unsigned long long* s) {
   tail[3] = (unsigned long long)((unsigned __int128)N >> 64);
 }
 
-// Device address of the scratch array, looked up once per device.
-constexpr int kMaxDevices = 64;
-unsigned long long* g_scratch_addr[kMaxDevices] = {};
-
+// Device address of the scratch array on the current device.  Looked up on
+// every call (the lookup allocates nothing and is cheap): a cached address
+// would be shared by host threads without synchronisation and would outlive
+// a device reset.  The first lookup on a device loads the module there.
 int scratch_for_current_device(unsigned long long** out) {
-  int dev = 0;
-  DCD_TRY_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return DCD_EINVAL;
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    DCD_TRY_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_scratch_addr[dev] = static_cast<unsigned long long*>(p);
-  }
-  *out = g_scratch_addr[dev];
+  void* p = nullptr;
+  DCD_TRY_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+  *out = static_cast<unsigned long long*>(p);
   return DCD_OK;
 }
 
@@ -130,7 +124,7 @@ extern "C" int dcd_modularity_noalloc(int64_t n, const int64_t* d_row_ptr, const
                                       const int32_t* d_w, const int32_t* d_labels, void* cuda_stream,
                                       double* q_out, int64_t* m2_out) {
   using namespace dcd;
-  if (n <= 0 || n > kNoAllocMaxN || !d_row_ptr || !d_labels || !q_out) return DCD_EINVAL;
+  if (n <= 0 || n > kNoAllocMaxN || !d_row_ptr || !d_col || !d_w || !d_labels || !q_out) return DCD_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   unsigned long long* sc = nullptr;
   DCD_TRY(scratch_for_current_device(&sc));

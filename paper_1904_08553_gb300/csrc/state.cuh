@@ -199,6 +199,11 @@ struct dcd_ctx {
   cudaEvent_t join_ev[dcd::kMaxBins] = {};
   cudaEvent_t fork_ev = nullptr;
   dcd::BinPlan bin_plan = dcd::default_bin_plan();  // degree bins of the local-move kernels
+  // level 0 of the last update's local move (dcd_get_level0_bins): active
+  // vertices per bin, vertices one sweep of each bin's grid covers, and
+  // whether the bins ran side by side
+  int32_t l0_nb = 0, l0_side = 0;
+  int64_t l0_cnt[dcd::kMaxBins] = {}, l0_sweep[dcd::kMaxBins] = {};
 };
 
 namespace dcd {

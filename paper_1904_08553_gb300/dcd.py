@@ -33,7 +33,7 @@ EXPORTED = [
     "dcd_group_create", "dcd_group_destroy", "dcd_group_apply_batch", "dcd_group_update",
     "dcd_set_bins", "dcd_get_bins", "dcd_autotune", "dcd_group_set_bins", "dcd_group_get_bins",
     "dcd_group_autotune", "dcd_save", "dcd_load", "dcd_get_state", "dcd_mlp_save",
-    "dcd_mlp_load", "dcd_set_fault",
+    "dcd_mlp_load", "dcd_set_fault", "dcd_get_level0_bins",
 ]
 MAX_BINS = 12
 LM_HALF, LM_WARP, LM_WARP128, LM_WARP256, LM_BLK512, LM_BLK1K, LM_BLK2K, LM_BLK4K, LM_HUB = range(9)
@@ -136,6 +136,7 @@ def lib():
             "dcd_set_bins": (INT, [P, I32, P, P]),
             "dcd_get_bins": (INT, [P, P, P, P]),
             "dcd_autotune": (INT, [P, I32, P]),
+            "dcd_get_level0_bins": (INT, [P, P, P, P, P]),
             "dcd_group_set_bins": (INT, [P, I32, P, P]),
             "dcd_group_get_bins": (INT, [P, P, P, P]),
             "dcd_group_autotune": (INT, [P, I32, P]),
@@ -338,6 +339,18 @@ def dcd_autotune(h, reps: int = 3) -> float:
     return _autotune(lib().dcd_autotune, h, reps)
 
 
+def dcd_get_level0_bins(h):
+    """Level 0 of the last update's local move: (count per bin, vertices one
+    sweep of each bin's grid covers, whether the bins ran side by side)."""
+    nb = ctypes.c_int32(0)
+    cnt = np.zeros(MAX_BINS, np.int64)
+    sw = np.zeros(MAX_BINS, np.int64)
+    side = ctypes.c_int32(0)
+    _check(lib().dcd_get_level0_bins(h, ctypes.byref(nb), cnt.ctypes.data, sw.ctypes.data, ctypes.byref(side)),
+           "dcd_get_level0_bins")
+    return cnt[:nb.value].tolist(), sw[:nb.value].tolist(), bool(side.value)
+
+
 def dcd_group_set_bins(h, variants, his) -> None:
     _set_bins(lib().dcd_group_set_bins, h, variants, his)
 
@@ -415,6 +428,11 @@ class Context(_Bins):
 
     def save(self, path) -> None:
         dcd_save(self._h, path)
+
+    def level0_bins(self):
+        """(count per bin, vertices per grid sweep, side by side) of the last
+        update's level-0 local move."""
+        return dcd_get_level0_bins(self._h)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -12,7 +12,7 @@ ROOT = Path(__file__).resolve().parent.parent
 def declared_functions():
     text = (ROOT / "include" / "dcd.h").read_text()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(dcd_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(dcd_[a-z0-9_]+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")
