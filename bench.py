@@ -6,10 +6,11 @@ multi-level local moving over R_t + compaction), with local-move GTEPS beside
 it.  Workload: the LFR-style power-law temporal graph shaped like the paper's
 largest run (2,000,000 vertices, 63M temporal edges over 12 time steps,
 degree exponent 2.5, community-size exponent 1.5, mixing 0.3, 5 % community
-drift and 2 % deletions per step), generated from a fixed seed.  Step 1 is
-the static start (untimed); W warm-up steps follow, then K timed steps.  The
-stream has 1 + W + K steps at the configuration's rate of 63M / 12 events per
-step (W = 3, K = 8 reproduce the 12-step configuration exactly).
+drift and 2 % deletions per step), generated from a fixed seed: exactly the
+configuration's 12 steps.  Step 1 is the static start (untimed); W warm-up
+steps follow (t = 2..W+1), then K timed steps: t = W+2..12, and when K is
+larger than that, the same steps again from a checkpoint of the state after
+the warm-up (dcd_save / dcd_load, untimed) until K steps are timed.
 
 Prints one JSON line.  ``--impl reference`` times the CPU oracle instead.
 """
@@ -33,19 +34,21 @@ sys.path.insert(0, str(ROOT))
 LFR_N = 2_000_000
 LFR_EVENTS = 63_000_000
 LFR_STEPS = 12
-CPU_SAMPLE_N = 100_000
 METRIC = "ms per time-step update"
 BYTES_PER_ENTRY = 12   # int32 col + int32 weight + int32 neighbour label, per directed entry visited
 BYTES_PER_VERTEX = 40  # row_ptr pair, k, label, a_C, |C|, proposal, list entry per active vertex
 
 
-def workload_desc(T: int) -> str:
-    return (f"lfr_2m: LFR-style temporal graph, n=2,000,000, {LFR_EVENTS // LFR_STEPS * T:,} edge events "
-            f"over {T} steps (63M over 12 in the configuration), degree exp 2.5 on [20,20000], "
-            f"community-size exp 1.5 on [100,50000], mu=0.3, 5% drift and 2% deletes per step")
+def workload_desc(n: int = LFR_N) -> str:
+    return (f"lfr_2m: LFR-style temporal graph, n={n:,}, {int(round(LFR_EVENTS * n / LFR_N)):,} edge events over "
+            f"12 time steps by uniform timestamps, degree exponent 2.5 on [20,20000], community-size exponent "
+            f"1.5 on [100,50000], mixing mu=0.3, 5% of vertices drift per step, repeated edges accumulate as "
+            f"int32 weights, 2% of the previous step's edges deleted")
 
 
-def make_stream(n: int, T: int, replica: int = 0):
+def make_stream(n: int, T: int = LFR_STEPS, replica: int = 0):
+    """The LFR-style stream of the configuration at n vertices (events scaled
+    by n / 2,000,000): T = 12 gives the configuration's 12 steps exactly."""
     from paper_1904_08553_gb300 import synth
 
     synth.build()
@@ -122,75 +125,101 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ CPU oracle
 
-def time_oracle(T: int, steps_timed: int, budget_s: float, n: int = CPU_SAMPLE_N, warm: int = 0):
-    """Oracle (single thread) on the same generator at n vertices; returns
-    per-step seconds and the sample's nnz per timed step."""
+def oracle_steps(stream, first: int, count: int):
+    """The oracle (single thread) on the configuration's own stream: step 1
+    (the static start, untimed) and the steps before `first` build the state;
+    each sample then copies that state (untimed) and times step `first + 1`
+    on the copy.  Returns the per-sample seconds, the graph size after the
+    timed step and the static step's seconds."""
     import oracle
 
     oracle.build()
-    s = make_stream(n, T, replica=0)
+    n = stream.n
     ctx = oracle.Context(n)
-    ins, dels = s.steps[0]
-    ctx.apply_batch(ins, dels)
+    a = time.perf_counter()
+    ctx.apply_batch(*stream.steps[0])
     ctx.update(oracle.DELTA)
-    for t in range(1, 1 + warm):
-        ctx.apply_batch(*s.steps[t])
+    s_static = time.perf_counter() - a
+    for t in range(1, first):
+        ctx.apply_batch(*stream.steps[t])
         ctx.update(oracle.DELTA)
-    secs, nnzs = [], []
-    t0 = time.perf_counter()
-    for t in range(1 + warm, min(T, 1 + warm + steps_timed)):
-        ins, dels = s.steps[t]
+    secs, nnz = [], 0
+    for _ in range(count):
+        c = ctx.clone()
         a = time.perf_counter()
-        ctx.apply_batch(ins, dels)
-        _, _, st = ctx.update(oracle.DELTA)
+        c.apply_batch(*stream.steps[first])
+        _, _, st = c.update(oracle.DELTA)
         secs.append(time.perf_counter() - a)
-        nnzs.append(st.nnz)
-        if time.perf_counter() - t0 > budget_s:
-            break
-    return secs, nnzs
+        nnz = st.nnz
+        del c
+    return secs, nnz, s_static
 
 
-def cpu_baseline(T: int, nnz_full_by_step: dict, budget_s: float = 20.0):
-    secs, nnzs = time_oracle(T, steps_timed=T, budget_s=budget_s)
-    # scale each sampled step to the full workload by its graph size (the
-    # oracle's work per step grows with nnz)
-    full = []
-    for i, (s_, z) in enumerate(zip(secs, nnzs)):
-        zf = nnz_full_by_step.get(2 + i)
-        full.append(s_ * 1e3 * (zf / z if zf else LFR_N / CPU_SAMPLE_N))
+def cpu_baseline(stream, gpu_nnz_mean: float):
+    """One measured oracle step of the configuration (step 2, its first
+    Delta-screening step, at the full n), beside an nnz-scaled estimate for
+    the steps the GPU arm times."""
+    secs, nnz, s_static = oracle_steps(stream, 1, 1)
+    ms = secs[0] * 1e3
+    est = ms * gpu_nnz_mean / max(nnz, 1)
     return {
-        "value": float(np.mean(full)), "unit": "ms", "cores": 1, "kind": "oracle",
-        "sample": (f"oracle (1 thread of {os.cpu_count()}) on the same LFR generator at n={CPU_SAMPLE_N:,} "
-                   f"(events scaled alike), steps 2..{1 + len(secs)}: {np.mean(secs) * 1e3:.1f} ms/step measured, "
-                   f"scaled to n=2M by the nnz ratio of each step"),
+        "value": ms, "unit": "ms", "cores": 1, "kind": "oracle",
+        "sample": (f"oracle (1 thread of {os.cpu_count()} host cores) on the configuration's own stream at "
+                   f"n={stream.n:,}: step 2 (the first Delta-screening step, {nnz:,} directed entries) measured "
+                   f"once after the static step 1 ({s_static:.1f} s, untimed); the GPU arm's timed steps hold "
+                   f"{gpu_nnz_mean:,.0f} entries on average, so scaled by size the oracle would need about "
+                   f"{est:,.0f} ms for one of them (an estimate, not measured)"),
+        "measured_step": 2, "measured_nnz": int(nnz), "static_step_s": s_static,
+        "nnz_scaled_estimate_ms": est,
     }
 
 
 def reference_arm(args):
+    """The oracle as the reference arm: every step is a measured oracle step 2
+    of the configuration's stream, started from a copy of the state after
+    step 1 (the copy is untimed); W untimed steps, then K timed."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    T = 1 + args.warmup + args.steps
-    secs, nnzs = time_oracle(T, steps_timed=args.steps, budget_s=240.0, warm=args.warmup)
-    # full-size nnz of the same steps, estimated from the sample by the vertex ratio
-    scale = LFR_N / CPU_SAMPLE_N
-    ms = [s_ * 1e3 * scale for s_ in secs]
-    v = float(np.mean(ms))
+    stream = make_stream(args.n, LFR_STEPS)
+    secs, nnz, s_static = oracle_steps(stream, 1, args.warmup + args.steps)
+    timed = secs[args.warmup:]
+    v = float(np.mean(timed)) * 1e3
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "higher_is_better": False,
-        "n_gpus": args.gpus, "steps": len(secs), "warmup": args.warmup, "ms_per_step": v,
-        "dtype": "int64", "data": "synthetic", "scaling": "weak", "vs_baseline": None,
-        "config": {"workload": workload_desc(T), "mode": "delta"},
+        "n_gpus": args.gpus, "steps": len(timed), "warmup": args.warmup, "ms_per_step": v,
+        "dtype": "int64", "data": "synthetic (seeded LFR-style generator)", "scaling": "weak", "vs_baseline": None,
+        "config": config_of(args.n),
         "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle",
-                         "sample": (f"oracle on the LFR generator at n={CPU_SAMPLE_N:,}, timed steps "
-                                    f"{2 + args.warmup}..{1 + args.warmup + len(secs)}, "
-                                    f"{np.mean(secs) * 1e3:.1f} ms/step measured x{scale:.0f} (vertex ratio)")},
+                         "sample": (f"oracle (1 thread of {os.cpu_count()} host cores) on the configuration's own "
+                                    f"stream at n={args.n:,}: each step is step 2 (the first Delta-screening step, "
+                                    f"{nnz:,} directed entries) from a copy of the state after the static step 1 "
+                                    f"({s_static:.1f} s, untimed)")},
         "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 # ------------------------------------------------------------------ GPU arm
+
+def config_of(n: int) -> dict:
+    return {"workload": workload_desc(n), "mode": "delta",
+            "l2": "inputs larger than L2 (G_t holds 50M-126M directed entries, 0.4-1.0 GB, at n=2,000,000)"}
+
+
+def timed_schedule(warmup: int, steps: int):
+    """Step indices (0-based) of the timed steps: the configuration's steps
+    after step 1 and the warm-up, replayed from a checkpoint of the state
+    after the warm-up until `steps` steps are timed."""
+    first = 1 + warmup
+    avail = LFR_STEPS - first
+    segs, done = [], 0
+    while done < steps:
+        k = min(avail, steps - done)
+        segs.append(list(range(first, first + k)))
+        done += k
+    return segs
+
 
 def gpu_arm(args):
     import torch
@@ -210,9 +239,9 @@ def gpu_arm(args):
         dist.barrier()
     from paper_1904_08553_gb300 import dcd, shard
 
-    T = 1 + args.warmup + args.steps
-    stream = make_stream(args.n, T, replica=rank)
+    stream = make_stream(args.n, LFR_STEPS, replica=rank)
     n = stream.n
+    segs = timed_schedule(args.warmup, args.steps)
     dev = torch.device("cuda", local)
     d_ins, d_del = [], []
     for ins, dels in stream.steps:
@@ -222,6 +251,8 @@ def gpu_arm(args):
         d_del.append(torch.from_numpy(dd).to(dev))
     torch.cuda.synchronize()
     ts = torch.cuda.current_stream(dev)
+    tmpdir = tempfile.mkdtemp(prefix="dcd_bench_")
+    ckpt = os.path.join(tmpdir, "after_warmup.ckpt")
 
     def run(ctx, t, host=False, lab_host=None):
         ins, dels = stream.steps[t]
@@ -238,23 +269,29 @@ def gpu_arm(args):
     plan = ctx.bins()
     for t in range(1, 1 + args.warmup):
         run(ctx, t)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    stats = []
-    launches0 = dcd.dcd_kernel_launches()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if len(segs) > 1:
+        ctx.save(ckpt)
+    stats, total_ms, launches = [], 0.0, 0
     with ClockSampler(local) as clk:
-        e0.record(ts)
-        for t in range(1 + args.warmup, T):
-            _, q, st = run(ctx, t)
-            stats.append(st)
-        e1.record(ts)
-        torch.cuda.synchronize()
-    launches = dcd.dcd_kernel_launches() - launches0
-    total_ms = shard.max_over_ranks(e0.elapsed_time(e1), device=dev)
+        for si, seg in enumerate(segs):
+            if si > 0:  # the state after the warm-up again (untimed)
+                ctx.close()
+                ctx = dcd.Context.load(ckpt, stream=ts)
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
+            l0 = dcd.dcd_kernel_launches()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(ts)
+            for t in seg:
+                _, q, st = run(ctx, t)
+                stats.append(st)
+            e1.record(ts)
+            torch.cuda.synchronize()
+            launches += dcd.dcd_kernel_launches() - l0
+            total_ms += e0.elapsed_time(e1)
+    total_ms = shard.max_over_ranks(total_ms, device=dev)
     clocks = clk.summary()
-    nnz_by_step = {1 + args.warmup + i + 1: st.nnz for i, st in enumerate(stats)}
     ctx.close()
 
     # ---- end to end through the public API with host buffers ----
@@ -272,20 +309,28 @@ def gpu_arm(args):
         lab_host = torch.empty(n, dtype=torch.int32).pin_memory().numpy()
         ctx = dcd.Context(n, mode=dcd.MODE_DELTA, stream=ts)
         ctx.set_bins(*plan)
-        run(ctx, 0, host=True, lab_host=lab_host)
-        for t in range(1, 1 + args.warmup):
+        for t in range(0, 1 + args.warmup):
             run(ctx, t, host=True, lab_host=lab_host)
         torch.cuda.synchronize()
-        h2d = 0
-        a = time.perf_counter()
-        for t in range(1 + args.warmup, T):
-            run(ctx, t, host=True, lab_host=lab_host)
-            h2d += pinned[t][0].nbytes + len(pinned[t][1]) * 12
-        torch.cuda.synchronize()
-        e2e_ms = shard.max_over_ranks((time.perf_counter() - a) * 1e3 / args.steps, device=dev)
+        h2d, e2e_ms = 0, 0.0
+        for si, seg in enumerate(segs):
+            if si > 0:  # same state as the device-resident leg after its warm-up
+                ctx.close()
+                ctx = dcd.Context.load(ckpt, stream=ts)
+                torch.cuda.synchronize()
+            a = time.perf_counter()
+            for t in seg:
+                run(ctx, t, host=True, lab_host=lab_host)
+                h2d += pinned[t][0].nbytes + pinned[t][1].nbytes
+            torch.cuda.synchronize()
+            e2e_ms += (time.perf_counter() - a) * 1e3
+        e2e_ms = shard.max_over_ranks(e2e_ms / args.steps, device=dev)
         ctx.close()
         e2e = {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(h2d / args.steps),
                "d2h_bytes_per_step": int(n * 4)}
+    if os.path.exists(ckpt):
+        os.unlink(ckpt)
+    os.rmdir(tmpdir)
 
     if rank != 0:
         if world > 1:
@@ -302,31 +347,44 @@ def gpu_arm(args):
     peak, peak_kind = peaks()
     lm_bytes = BYTES_PER_ENTRY * edges + BYTES_PER_VERTEX * verts
     pass_gbs = lm_bytes / (lm_ms * 1e-3) / 1e9 if lm_ms > 0 else None
+    # level 0 (the R_t level, where the graph is the full G_t) is the
+    # dominant part of the local move; the upper levels are graphs of a few
+    # hundred vertices whose passes are launch-bound
+    lm0_ms = sum(s.ms_local_move0 for s in stats)
+    lm0_bytes = sum(BYTES_PER_ENTRY * s.edges_level0 + BYTES_PER_VERTEX * s.verts_level0 for s in stats)
+    l0_gbs = lm0_bytes / (lm0_ms * 1e-3) / 1e9 if lm0_ms > 0 else None
+    passes0 = sum(s.iters_level0 for s in stats)
     # per degree-bin kernel class: time from fork to join, algorithmic bytes.
     # The bins of a pass run side by side, so these intervals overlap: the
     # roofline is taken over the whole evaluation (every bin of a pass, the
     # pass's own events on the context stream)
-    names = ["lm_warp (degree <= 32)", "lm_warp_tbl (33..256)", "lm_large (257..4096)", "hub_agg + hub_gain + hub_pick (> 4096)"]
+    names = ["lm_seg (degree <= 32)", "lm_seg (33..256)", "lm_cta (257..4096)",
+             "hub_agg + hub_gain + hub_pick (> 4096)"]
     bins = []
     for b in range(4):
         ms_b = sum(st.ms_bin[b] for st in stats)
         by_b = sum(BYTES_PER_ENTRY * st.edges_bin[b] + BYTES_PER_VERTEX * st.verts_bin[b] for st in stats)
         bins.append({"kernel": names[b], "ms": ms_b, "bytes": by_b,
                      "gbs": by_b / (ms_b * 1e-3) / 1e9 if ms_b > 0 else None})
-    achieved = pass_gbs
-    cpu = cpu_baseline(T, nnz_by_step) if (world == 1 and not args.no_cpu) else None
+    achieved = l0_gbs
+    nnz_mean = float(np.mean([s.nnz for s in stats]))
+    cpu = cpu_baseline(stream, nnz_mean) if (world == 1 and not args.no_cpu) else None
+    cfg = config_of(n)
+    cfg.update({"parallelism": "replicas" if world > 1 else "1 GPU",
+                "timed_steps": (f"t={segs[0][0] + 1}..{segs[0][-1] + 1} of 12"
+                                + (f", replayed {len(segs)} times from a checkpoint of the state after the warm-up "
+                                   f"(the reload is untimed)" if len(segs) > 1 else "")),
+                "bin_plan": {"variants": plan[0], "max_degree": plan[1]}})
     line = {
         "metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded LFR-style generator)",
-        "config": {"workload": workload_desc(T), "mode": "delta", "parallelism": "replicas" if world > 1 else "1 GPU",
-                   "l2": "inputs larger than L2 (G_t holds ~100M directed entries, ~0.8 GB)",
-                   "timed_steps": f"t={2 + args.warmup}..{T}",
-                   "bin_plan": {"variants": plan[0], "max_degree": plan[1]}},
+        "config": cfg,
         "local_move_gteps": gteps,
         "steps_detail": {
             "r_fraction": float(np.mean([s.r_size / s.n for s in stats])),
-            "q_last": stats[-1].q, "nnz_last": stats[-1].nnz, "communities_last": stats[-1].communities,
+            "q_last": stats[-1].q, "nnz_mean": nnz_mean, "nnz_last": stats[-1].nnz,
+            "communities_last": stats[-1].communities,
             "ms_merge": float(np.mean([s.ms_merge for s in stats])),
             "ms_screen": float(np.mean([s.ms_screen for s in stats])),
             "ms_local_move": float(np.mean([s.ms_local_move for s in stats])),
@@ -334,16 +392,20 @@ def gpu_arm(args):
             "ms_coarsen": float(np.mean([s.ms_coarsen for s in stats])),
             "ms_finish": float(np.mean([s.ms_finish for s in stats])),
             "passes_per_step": passes / len(stats),
+            "passes_level0_per_step": passes0 / len(stats),
+            "ms_local_move_level0": lm0_ms / len(stats),
             "levels": float(np.mean([s.levels for s in stats])),
         },
         "roofline": {
-            "kernel": "local-move evaluation: the degree-bin kernels of a pass (lm_warp, lm_warp_tbl, lm_large, "
-                      "hub_*), run side by side",
+            "kernel": "level-0 local-move evaluation: the degree-bin kernels of a pass (lm_seg, lm_cta, hub_*) over "
+                      "R_t on G_t, run side by side",
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": None,
             "peak_kind": peak_kind,
             "algorithmic_bytes": f"{BYTES_PER_ENTRY} B x entries scanned + {BYTES_PER_VERTEX} B x vertices evaluated",
-            "local_move_pass_gbs": pass_gbs,
+            "level0_bytes_per_pass": lm0_bytes / max(passes0, 1),
+            "all_levels_gbs": pass_gbs,
+            "all_levels_frac": (pass_gbs / peak) if pass_gbs else None,
             "bins": bins,
             "bins_note": "each bin's ms runs from its fork to its join; the bins of a pass overlap, so the intervals "
                          "add up to more than the pass and their GB/s understate the kernels",
@@ -357,7 +419,6 @@ def gpu_arm(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
-
 
 
 # ------------------------------------------------------------------ learned screen
@@ -460,7 +521,7 @@ def learned_arm(args):
     for name in args.eval.split(","):
         if name == "lfr":
             st_ = make_stream(args.n, T, replica=9)
-            evals.append(evaluate("lfr", st_, workload_desc(T).replace("lfr_2m", f"lfr n={st_.n:,}")))
+            evals.append(evaluate("lfr", st_, workload_desc(st_.n).replace("lfr_2m", f"lfr n={st_.n:,}")))
         elif name == "rmat":
             st_ = synth.rmat(synth.seed_for(2, 9), scale=args.rmat_scale, edge_factor=16, steps=T,
                              ins_frac=0.01, del_frac=0.005)
@@ -676,6 +737,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.workload == "lfr_2m" and args.warmup > LFR_STEPS - 2:
+        ap.error(f"--warmup must leave a timed step of the {LFR_STEPS}-step configuration (at most {LFR_STEPS - 2})")
     if args.impl == "reference":
         reference_arm(args)
     elif args.workload == "learned":

@@ -103,6 +103,10 @@ typedef struct {
   float reserved_f[5];
   int64_t edges_bin[4];  /* entries scanned per degree bin (all passes)              */
   int64_t verts_bin[4];  /* vertices evaluated per degree bin (all passes)           */
+  float ms_local_move0;  /* local-move kernels of level 0 only (the R_t level)        */
+  float reserved_g;
+  int64_t edges_level0;  /* entries scanned at level 0 (all its passes)             */
+  int64_t verts_level0;  /* vertices evaluated at level 0 (all its passes)          */
 } dcd_step_stats;
 
 typedef struct dcd_ctx dcd_ctx;
@@ -185,15 +189,16 @@ int dcd_set_mode(dcd_ctx* ctx, int32_t mode);
  * receives its time per evaluation.  Errors: DCD_ESTATE before the first
  * update or for reps < 1, DCD_ENOMEM, DCD_ECUDA. */
 #define DCD_MAX_BINS 12
-#define DCD_LM_HALF 0    /* <= 16 entries: half a warp per vertex, no table        */
-#define DCD_LM_WARP 1    /* <= 32: a warp per vertex, no table                     */
-#define DCD_LM_WARP128 2 /* <= 128: a warp per vertex, warp-private shared table   */
-#define DCD_LM_WARP256 3 /* <= 256: a warp per vertex, warp-private shared table   */
-#define DCD_LM_BLK512 4  /* <= 512: a CTA per vertex, shared table                  */
-#define DCD_LM_BLK1K 5   /* <= 1024: a CTA per vertex, shared table                 */
-#define DCD_LM_BLK2K 6   /* <= 2048: a CTA per vertex, shared table                 */
-#define DCD_LM_BLK4K 7   /* <= 4096: a CTA per vertex, shared table                 */
-#define DCD_LM_HUB 8     /* any degree: a row split over many CTAs, global tables  */
+#define DCD_LM_SEG16 0   /* <= 16 entries: 8 lanes per vertex, 4 vertices a warp   */
+#define DCD_LM_SEG32 1   /* <= 32: 16 lanes per vertex, 2 vertices a warp          */
+#define DCD_LM_SEG64 2   /* <= 64: 16 lanes per vertex, 2 vertices a warp          */
+#define DCD_LM_WARP128 3 /* <= 128: a warp per vertex                              */
+#define DCD_LM_WARP256 4 /* <= 256: a warp per vertex                              */
+#define DCD_LM_CTA512 5  /* <= 512: a CTA of 128 threads per vertex                */
+#define DCD_LM_CTA1K 6   /* <= 1024: a CTA of 256 threads per vertex               */
+#define DCD_LM_CTA2K 7   /* <= 2048: a CTA of 512 threads per vertex               */
+#define DCD_LM_CTA4K 8   /* <= 4096: a CTA of 512 threads per vertex               */
+#define DCD_LM_HUB 9     /* any degree: a row split over many CTAs, global tables  */
 int dcd_set_bins(dcd_ctx* ctx, int32_t nb, const int32_t* variant, const int64_t* hi);
 int dcd_get_bins(const dcd_ctx* ctx, int32_t* nb, int32_t* variant, int64_t* hi);
 int dcd_autotune(dcd_ctx* ctx, int32_t reps, float* best_ms);

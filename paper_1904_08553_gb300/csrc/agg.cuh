@@ -220,6 +220,39 @@ struct TblVal<long long> {
   using type = unsigned;
 };
 
+// The slot of `lab` in the table (claimed when absent); `claimed` is set when
+// this call took an empty slot for it.
+__device__ __forceinline__ uint32_t probe_claim(int32_t* keys, uint32_t mask, int32_t lab, bool& claimed) {
+  uint32_t s = hash_label(lab, mask);
+  for (;;) {
+    const int32_t k = keys[s];
+    if (k == lab) return s;
+    if (k == -1) {
+      const int32_t old = atomicCAS(&keys[s], -1, lab);
+      if (old == -1) {
+        claimed = true;
+        return s;
+      }
+      if (old == lab) return s;
+    }
+    s = (s + 1) & mask;
+  }
+}
+
+// Sum over the S lanes of the calling lane's segment: 32-bit sums are exact
+// with 64-bit gains (every sum of a vertex's weights is below 2m < 2^31),
+// 64-bit sums with 128-bit gains.
+template <int S>
+__device__ __forceinline__ int64_t seg_total(unsigned x, unsigned smask) {
+  return (int64_t)__reduce_add_sync(smask, x);
+}
+template <int S>
+__device__ __forceinline__ int64_t seg_total(unsigned long long x, unsigned) {
+#pragma unroll
+  for (int o = S / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return (int64_t)x;
+}
+
 __host__ __device__ __forceinline__ uint32_t table_cap(int64_t deg) {
   uint32_t c = 64;
   while ((int64_t)c < 2 * deg) c <<= 1;

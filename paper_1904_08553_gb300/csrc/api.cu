@@ -459,15 +459,15 @@ namespace dcd {
 // that drop variants (fewer launches, larger tables).
 static std::vector<BinPlan> candidate_plans() {
   const int32_t lists[][kMaxBins] = {
-      {kLmWarp, kLmWarp128, kLmWarp256, kLmBlk512, kLmBlk1k, kLmBlk2k, kLmBlk4k, kLmHub},
-      {kLmHalf, kLmWarp, kLmWarp128, kLmWarp256, kLmBlk512, kLmBlk1k, kLmBlk2k, kLmBlk4k, kLmHub},
-      {kLmWarp, kLmWarp256, kLmBlk512, kLmBlk1k, kLmBlk2k, kLmBlk4k, kLmHub},
-      {kLmWarp, kLmWarp128, kLmWarp256, kLmBlk1k, kLmBlk4k, kLmHub},
-      {kLmWarp, kLmWarp128, kLmWarp256, kLmBlk512, kLmBlk1k, kLmBlk2k, kLmHub},
-      {kLmWarp, kLmWarp256, kLmBlk4k, kLmHub},
-      {kLmWarp, kLmWarp128, kLmWarp256, kLmHub},
+      {kLmSeg16, kLmSeg32, kLmSeg64, kLmWarp128, kLmWarp256, kLmCta512, kLmCta1k, kLmCta2k, kLmCta4k, kLmHub},
+      {kLmSeg32, kLmSeg64, kLmWarp128, kLmWarp256, kLmCta512, kLmCta1k, kLmCta2k, kLmCta4k, kLmHub},
+      {kLmSeg16, kLmSeg32, kLmWarp128, kLmWarp256, kLmCta512, kLmCta1k, kLmCta2k, kLmCta4k, kLmHub},
+      {kLmSeg16, kLmSeg32, kLmSeg64, kLmWarp128, kLmWarp256, kLmCta1k, kLmCta4k, kLmHub},
+      {kLmSeg16, kLmSeg32, kLmSeg64, kLmWarp128, kLmWarp256, kLmCta512, kLmCta1k, kLmCta2k, kLmHub},
+      {kLmSeg32, kLmWarp256, kLmCta4k, kLmHub},
+      {kLmSeg16, kLmSeg32, kLmSeg64, kLmWarp128, kLmWarp256, kLmHub},
   };
-  const int lens[] = {8, 9, 7, 6, 7, 4, 4};
+  const int lens[] = {10, 9, 9, 8, 9, 4, 6};
   std::vector<BinPlan> out;
   for (int x = 0; x < (int)(sizeof(lens) / sizeof(lens[0])); x++) {
     BinPlan p;
@@ -737,11 +737,11 @@ int dcd_set_mode(dcd_ctx* c, int32_t mode) {
   return DCD_OK;
 }
 
-static_assert(DCD_MAX_BINS == kMaxBins && DCD_LM_HALF == kLmHalf && DCD_LM_WARP == kLmWarp &&
-                  DCD_LM_WARP128 == kLmWarp128 && DCD_LM_WARP256 == kLmWarp256 && DCD_LM_BLK512 == kLmBlk512 &&
-                  DCD_LM_BLK1K == kLmBlk1k && DCD_LM_BLK2K == kLmBlk2k && DCD_LM_BLK4K == kLmBlk4k &&
-                  DCD_LM_HUB == kLmHub,
-              "header constants name the kernel variants");
+static_assert(DCD_MAX_BINS == kMaxBins && DCD_LM_SEG16 == kLmSeg16 && DCD_LM_SEG32 == kLmSeg32 &&
+                  DCD_LM_SEG64 == kLmSeg64 && DCD_LM_WARP128 == kLmWarp128 && DCD_LM_WARP256 == kLmWarp256 &&
+                  DCD_LM_CTA512 == kLmCta512 && DCD_LM_CTA1K == kLmCta1k && DCD_LM_CTA2K == kLmCta2k &&
+                  DCD_LM_CTA4K == kLmCta4k && DCD_LM_HUB == kLmHub,
+              "variant ids of dcd.h and the kernels agree");
 
 int dcd_set_bins(dcd_ctx* c, int32_t nb, const int32_t* variant, const int64_t* hi) {
   if (!c || nb < 1 || nb > kMaxBins || !variant || !hi) return DCD_EINVAL;

@@ -61,12 +61,6 @@ __device__ __forceinline__ double to_double(i128 x) {
   return (double)hi * 18446744073709551616.0 + (double)lo;
 }
 
-__device__ __forceinline__ int32_t guard_choice(int32_t C, int32_t D, const int32_t* size) {
-  // singleton-swap guard (minimum-label rule)
-  if (D != C && size[C] == 1 && size[D] == 1 && D > C) return C;
-  return D;
-}
-
 // The proposal of a vertex from its best (S, D): move on S > 0, subject to
 // the guard.  Evaluated by every lane of the (uniform) argmax result, so the
 // caller stores it with a predicated write instead of a divergent branch.
@@ -84,137 +78,83 @@ __device__ __forceinline__ int32_t proposal(i128 S, int32_t D, int32_t C, const 
 }
 
 // ---------------------------------------------------------------- local move
+//
+// Rows up to 4096 entries: the neighbour communities of a row are summed in
+// an open-addressing table in shared memory (community label -> summed edge
+// weight), written by every lane for its own entries: a lane probes for its
+// entry's label, claims an empty slot with a CAS when the label is new, and
+// adds its weight with a shared-memory atomic.  The vertex's own community C
+// never enters the table: e_{v->C\v} is summed in registers and reduced once.
+// A lane that claims a slot appends it to the row's list of distinct labels
+// (one ballot per entry position), so the gain step visits only the distinct
+// communities and then empties exactly the slots it used.  No warp-wide
+// grouping instruction (match) runs per entry: round trips to the table are
+// ordinary shared-memory operations, which the SM issues at a far higher rate.
+//
+// The table of a row of at most R entries has seg_cap(R) >= 2R slots, so at
+// most half of it is ever in use and every probe sequence ends at the key or
+// at an empty slot.
 
-// SEG lanes per vertex (SEG = 32: one warp; SEG = 16: two vertices a warp)
-// for rows of at most SEG entries: lanes hold the row, labels are grouped
-// with match_any (the key carries the segment, so segments never mix) and
-// their weights summed with redux.sync, and the best community is a segment
-// argmax over the group leaders.  The code has no divergent branch: the
-// kernel is bound by the issue rate of the warp-wide instructions, so every
-// reduction runs over whole segments with neutral values, and the next
-// vertex's row bounds load while the current row is aggregated.
-template <typename W, typename ST, int SEG, bool FEAT>
-__global__ void __launch_bounds__(256) lm_warp(LV<W> g, const int32_t* __restrict__ list, int64_t cnt,
-                                               int32_t* __restrict__ prop) {
-  static_assert(SEG == 32 || SEG == 16, "one or two vertices a warp");
-  constexpr int P = 32 / SEG;
-  const int lane = lane_id(), sub = lane / SEG, sl = lane % SEG;
-  const unsigned smask = SEG == 32 ? 0xffffffffu : (((1u << SEG) - 1u) << (sub * SEG));
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t stride = nw * P;
-  int64_t base = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * P;
-  int32_t v = base + sub < cnt ? list[base + sub] : -1;
-  int64_t b = 0, bend = 0;
-  if (v >= 0) {
-    b = g.rp[v];
-    bend = g.rp[v + 1];
-  }
-  for (; base < cnt; base += stride) {
-    const int64_t i = base + sub, in = i + stride;
-    const int32_t vn = in < cnt ? list[in] : -1;
-    const bool has = v >= 0;
-    const int32_t vv = has ? v : 0;
-    const int d = (int)(bend - b);
-    const int32_t C = g.L[vv];
-    const int64_t kv = g.k[vv], m2v = g.m2_of(vv);
-    const int64_t aC = g.a[C];
-    bool valid = sl < d;
-    const int32_t u = valid ? g.col[b + sl] : -1;
-    valid = valid && u != v;
-    const int32_t lab = valid ? g.L[u] : -1;
-    const W wt = valid ? g.w[b + sl] : W(0);
-    const int64_t aD = valid ? g.a[lab] : 0;
-    int64_t bn = 0, bendn = 0;
-    if (vn >= 0) {
-      bn = g.rp[vn];
-      bendn = g.rp[vn + 1];
-    }
-    // labels are < 2^31 - 1, so bit 31 is free for the segment
-    const unsigned key = valid ? ((unsigned)lab | ((unsigned)sub << 31)) : 0xffffffffu;
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
-    const int64_t e = group_sum<ST>(peers, wt);
-    const int64_t eC = group_sum<ST>(smask, lab == C ? wt : W(0));
-    const bool cand = valid && (int)(__ffs(peers) - 1) == lane && lab != C;
-    const ST x = gain<ST>(m2v, kv, e, eC, aD, aC);
-    ST S = cand ? x : gain_lowest<ST>();
-    int32_t D = cand ? lab : INT_MAX;
-    if (SEG == 32) {
-      // most rows reach at most one other community: then the candidate is
-      // the answer and the three reductions of the argmax are skipped
-      const unsigned cb = __ballot_sync(0xffffffffu, cand);
-      if ((cb & (cb - 1)) == 0) {
-        const int l = cb ? __ffs(cb) - 1 : 0;
-        const ST xl = shfl_st(x, l);
-        const int32_t dl = __shfl_sync(0xffffffffu, lab, l);
-        S = cb ? xl : gain_lowest<ST>();
-        D = cb ? dl : INT_MAX;
-      } else {
-        seg_argmax<SEG>(S, D, smask);
-      }
-    } else {
-      seg_argmax<SEG>(S, D, smask);
-    }
-    const int32_t pv = proposal(S, D, C, g.size);
-    if (sl == 0 && has) prop[i] = pv;
-    if (FEAT) {
-      const int64_t eB = group_sum<ST>(smask, (valid && lab == D) ? wt : W(0));
-      if (sl == 0 && has) {
-        g.f_eC[i] = eC;
-        g.f_eB[i] = eB;
-        g.f_dB[i] = D == INT_MAX ? -1 : D;
-        g.f_sB[i] = D == INT_MAX ? 0.0 : to_double(S);
-      }
-    }
-    v = vn;
-    b = bn;
-    bend = bendn;
-  }
+__host__ __device__ constexpr int seg_cap(int row) {
+  int c = 32;
+  while (c < 2 * row) c <<= 1;
+  return c;
 }
 
-// One warp per vertex of up to 32 Q entries, with a warp-private shared-memory
-// table of CAP = 64 Q slots (the table of a row of d entries uses the first
-// 2 d rounded up to a power of two).  The row is loaded into registers first
-// (Q entries a lane, all loads in flight together, then all label gathers),
-// each 32-entry chunk is grouped by label with match_any, and the group
-// leaders add into the table.  New keys are listed as they are claimed, so
-// the gain step visits only the distinct communities and then empties
-// exactly the slots it used: the table is cleared once per kernel, not once
-// per vertex.
-template <int CAP, typename VT>
-__host__ __device__ constexpr size_t warp_tbl_bytes() {
-  // values, keys, slot list (CAP / 2 entries of 2 bytes), count; 8-byte aligned
-  return ((size_t)CAP * (sizeof(VT) + 4) + (size_t)CAP + 16 + 7) / 8 * 8;
+// Shared memory of one row table: keys (int32), sums (VT), the claimed-slot
+// list (one uint16 per row entry); a multiple of 16 bytes.
+template <int ROW, typename VT>
+__host__ __device__ constexpr size_t row_tbl_bytes() {
+  return ((size_t)seg_cap(ROW) * (4 + sizeof(VT)) + (size_t)ROW * 2 + 15) / 16 * 16;
 }
 
-template <typename W, typename ST, int CAP, int Q>
-__global__ void __launch_bounds__(256) lm_warp_tbl(LV<W> g, const int32_t* __restrict__ list, int64_t cnt,
-                                                   int32_t* __restrict__ prop) {
-  static_assert(CAP == 64 * Q, "table of twice the largest row");
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = lane_id(), wib = threadIdx.x >> 5;
+// The learned screen's per-row statistics (see LV).
+template <typename W, typename ST, typename VT>
+__device__ __forceinline__ void put_features(const LV<W>& g, int64_t i, int64_t eC, const int32_t* keys,
+                                             const VT* vals, uint32_t mask, ST S, int32_t D) {
+  g.f_eC[i] = eC;
+  g.f_eB[i] = D == INT_MAX ? 0 : tbl_get(keys, vals, mask, D);
+  g.f_dB[i] = D == INT_MAX ? -1 : D;
+  g.f_sB[i] = D == INT_MAX ? 0.0 : to_double(S);
+}
+
+// S lanes per vertex (32 / S vertices a warp), Q entries per lane: rows of at
+// most S x Q entries.  Each segment owns a table in shared memory; the
+// segments of a warp run in lockstep on their own rows.
+template <typename W, typename ST, int S, int Q>
+__global__ void __launch_bounds__(256) lm_seg(LV<W> g, const int32_t* __restrict__ list, int64_t cnt,
+                                              int32_t* __restrict__ prop) {
+  static_assert(S == 8 || S == 16 || S == 32, "segments of 8, 16 or 32 lanes");
   using VT = typename TblVal<ST>::type;
-  unsigned char* base = smem + (size_t)wib * warp_tbl_bytes<CAP, VT>();
-  VT* vals = reinterpret_cast<VT*>(base);
-  int32_t* keys = reinterpret_cast<int32_t*>(base + (size_t)CAP * sizeof(VT));
-  uint16_t* slots = reinterpret_cast<uint16_t*>(base + (size_t)CAP * (sizeof(VT) + 4));
-  int32_t* nslot = reinterpret_cast<int32_t*>(base + (size_t)CAP * (sizeof(VT) + 5));
-  for (int s = lane; s < CAP; s += 32) {
+  constexpr int P = 32 / S, ROW = S * Q, CAP = seg_cap(ROW);
+  constexpr size_t SB = row_tbl_bytes<ROW, VT>();
+  constexpr uint32_t mask = CAP - 1;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = lane_id(), sub = lane / S, sl = lane % S, wib = threadIdx.x >> 5;
+  const unsigned smask = S == 32 ? 0xffffffffu : (((1u << S) - 1u) << (sub * S));
+  unsigned char* base = smem + ((size_t)wib * P + sub) * SB;
+  int32_t* keys = reinterpret_cast<int32_t*>(base);
+  VT* vals = reinterpret_cast<VT*>(base + (size_t)CAP * 4);
+  uint16_t* slots = reinterpret_cast<uint16_t*>(base + (size_t)CAP * (4 + sizeof(VT)));
+  for (int s = sl; s < CAP; s += S) {
     keys[s] = -1;
     vals[s] = 0;
   }
-  if (lane == 0) *nslot = 0;
   __syncwarp();
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < cnt; i += nw) {
-    const int32_t v = list[i];
+  for (int64_t wb = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * P; wb < cnt; wb += nw * P) {
+    const int64_t i = wb + sub;
+    const bool has = i < cnt;
+    const int32_t v = has ? list[i] : 0;
     const int64_t b = g.rp[v];
-    const int d = (int)(g.rp[v + 1] - b);
+    const int d = has ? (int)(g.rp[v + 1] - b) : 0;
+    const int dmax = S == 32 ? d : (int)__reduce_max_sync(0xffffffffu, (unsigned)d);
     const int32_t C = g.L[v];
     int32_t lab[Q];
     W wt[Q];
 #pragma unroll
     for (int q = 0; q < Q; q++) {
-      const int e = q * 32 + lane;
+      const int e = q * S + sl;
       lab[q] = -1;
       wt[q] = W(0);
       if (e < d) {
@@ -225,88 +165,83 @@ __global__ void __launch_bounds__(256) lm_warp_tbl(LV<W> g, const int32_t* __res
 #pragma unroll
     for (int q = 0; q < Q; q++) {
       const int32_t u = lab[q];
-      lab[q] = (u >= 0 && u != v) ? g.L[u] : -1;
+      lab[q] = (u >= 0 && u != v) ? g.L[u] : -1;  // a coarse self-loop is no neighbour
     }
-    const uint32_t mask = table_cap(d) - 1;
+    VT eCl = 0;
+    int nd = 0;
 #pragma unroll
     for (int q = 0; q < Q; q++) {
-      if (q * 32 < d) {
-        const unsigned peers = __match_any_sync(0xffffffffu, lab[q]);
-        const int64_t sum = group_sum<ST>(peers, lab[q] >= 0 ? wt[q] : W(0));
-        if (lab[q] >= 0 && (int)(__ffs(peers) - 1) == lane)
-          tbl_add_list<VT>(keys, vals, slots, nslot, mask, lab[q], (VT)sum);
+      if (q * S < dmax) {
+        const bool isC = lab[q] == C;
+        eCl += isC ? (VT)wt[q] : VT(0);
+        bool claimed = false;
+        uint32_t s = 0;
+        if (lab[q] >= 0 && !isC) {
+          s = probe_claim(keys, mask, lab[q], claimed);
+          atomicAdd(&vals[s], (VT)wt[q]);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, claimed) & smask;
+        if (claimed) slots[nd + __popc(bal & lanemask_lt())] = (uint16_t)s;
+        nd += __popc(bal);
       }
     }
     __syncwarp();
-    const int nd = *nslot;
-    long long eC = 0;
-    for (int j0 = 0; j0 < nd; j0 += 32) {
-      const int j = j0 + lane;
-      const int32_t key = j < nd ? keys[slots[j]] : -1;
-      const unsigned cm = __ballot_sync(0xffffffffu, key == C);
-      if (cm) eC = (long long)vals[slots[j0 + __ffs(cm) - 1]];
-    }
+    const int64_t eC = seg_total<S>(eCl, smask);
     const int64_t kv = g.k[v], aC = g.a[C], m2v = g.m2_of(v);
-    ST S = gain_lowest<ST>();
+    ST Sb = gain_lowest<ST>();
     int32_t D = INT_MAX;
-    for (int j = lane; j < nd; j += 32) {
+    for (int j = sl; j < nd; j += S) {
       const uint32_t s = slots[j];
       const int32_t key = keys[s];
-      if (key != C) {
-        const ST x = gain<ST>(m2v, kv, (int64_t)vals[s], eC, g.a[key], aC);
-        if (better(x, key, S, D)) {
-          S = x;
-          D = key;
-        }
+      const ST x = gain<ST>(m2v, kv, (int64_t)vals[s], eC, g.a[key], aC);
+      if (better(x, key, Sb, D)) {
+        Sb = x;
+        D = key;
       }
     }
-    warp_argmax(S, D);
-    const int32_t pv = proposal(S, D, C, g.size);
-    if (lane == 0) prop[i] = pv;
-    if (lane == 0) {
-      if (g.f_eC) {
-        g.f_eC[i] = eC;
-        g.f_eB[i] = D == INT_MAX ? 0 : tbl_get(keys, vals, mask, D);
-        g.f_dB[i] = D == INT_MAX ? -1 : D;
-        g.f_sB[i] = D == INT_MAX ? 0.0 : to_double(S);
-      }
+    seg_argmax<S>(Sb, D, smask);
+    const int32_t pv = proposal(Sb, D, C, g.size);
+    if (sl == 0 && has) {
+      prop[i] = pv;
+      if (g.f_eC) put_features(g, i, eC, keys, vals, mask, Sb, D);
     }
     __syncwarp();
-    for (int j = lane; j < nd; j += 32) {
+    for (int j = sl; j < nd; j += S) {
       const uint32_t s = slots[j];
       keys[s] = -1;
       vals[s] = 0;
     }
-    if (lane == 0) *nslot = 0;
     __syncwarp();
   }
 }
 
-// One CTA per vertex of up to THREADS x Q entries (the large bin), with the
-// same scheme at block scope: registers hold the row, the shared table lists
-// its claimed slots, and only those are visited and emptied.
-template <typename W, typename ST, int THREADS, int Q>
-__global__ void __launch_bounds__(THREADS) lm_large(LV<W> g, const int32_t* __restrict__ list, int64_t cnt,
-                                                    int32_t* __restrict__ prop, int32_t tcap) {
+// One CTA of T threads per vertex, Q entries per thread: rows of at most
+// T x Q entries, one table of seg_cap(T x Q) slots in shared memory.
+template <int T, int Q, typename VT>
+__host__ __device__ constexpr size_t cta_tbl_bytes() {
+  return row_tbl_bytes<T * Q, VT>();
+}
+
+template <typename W, typename ST, int T, int Q>
+__global__ void __launch_bounds__(T) lm_cta(LV<W> g, const int32_t* __restrict__ list, int64_t cnt,
+                                            int32_t* __restrict__ prop) {
+  using VT = typename TblVal<ST>::type;
+  constexpr int NW = T / 32, ROW = T * Q, CAP = seg_cap(ROW);
+  constexpr uint32_t mask = CAP - 1;
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int NW = THREADS / 32;
   __shared__ ST redS[NW];
   __shared__ int32_t redD[NW];
-  __shared__ long long s_eC;
-  __shared__ int32_t s_n;
-  using VT = typename TblVal<ST>::type;
-  VT* vals = reinterpret_cast<VT*>(smem);
-  int32_t* keys = reinterpret_cast<int32_t*>(smem + (size_t)tcap * sizeof(VT));
-  uint16_t* slots = reinterpret_cast<uint16_t*>(smem + (size_t)tcap * (sizeof(VT) + 4));
+  __shared__ VT redC[NW];
+  __shared__ int32_t s_nd;
+  int32_t* keys = reinterpret_cast<int32_t*>(smem);
+  VT* vals = reinterpret_cast<VT*>(smem + (size_t)CAP * 4);
+  uint16_t* slots = reinterpret_cast<uint16_t*>(smem + (size_t)CAP * (4 + sizeof(VT)));
   const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5;
-  for (int s = tid; s < tcap; s += THREADS) {
+  for (int s = tid; s < CAP; s += T) {
     keys[s] = -1;
     vals[s] = 0;
   }
-  if (tid == 0) {
-    s_n = 0;
-    s_eC = 0;
-  }
+  if (tid == 0) s_nd = 0;
   __syncthreads();
   for (int64_t i = blockIdx.x; i < cnt; i += gridDim.x) {
     const int32_t v = list[i];
@@ -317,7 +252,7 @@ __global__ void __launch_bounds__(THREADS) lm_large(LV<W> g, const int32_t* __re
     W wt[Q];
 #pragma unroll
     for (int q = 0; q < Q; q++) {
-      const int e = q * THREADS + tid;
+      const int e = q * T + tid;
       lab[q] = -1;
       wt[q] = W(0);
       if (e < d) {
@@ -330,65 +265,66 @@ __global__ void __launch_bounds__(THREADS) lm_large(LV<W> g, const int32_t* __re
       const int32_t u = lab[q];
       lab[q] = (u >= 0 && u != v) ? g.L[u] : -1;
     }
-    const uint32_t mask = table_cap(d) - 1;
+    VT eCl = 0;
 #pragma unroll
     for (int q = 0; q < Q; q++) {
-      if (q * THREADS < d) {
-        const unsigned peers = __match_any_sync(0xffffffffu, lab[q]);
-        const int64_t sum = group_sum<ST>(peers, lab[q] >= 0 ? wt[q] : W(0));
-        if (lab[q] >= 0 && (int)(__ffs(peers) - 1) == lane)
-          tbl_add_list<VT>(keys, vals, slots, &s_n, mask, lab[q], (VT)sum);
+      if (q * T < d) {
+        const bool isC = lab[q] == C;
+        eCl += isC ? (VT)wt[q] : VT(0);
+        bool claimed = false;
+        uint32_t s = 0;
+        if (lab[q] >= 0 && !isC) {
+          s = probe_claim(keys, mask, lab[q], claimed);
+          atomicAdd(&vals[s], (VT)wt[q]);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, claimed);
+        int at = 0;
+        if (lane == 0 && bal) at = atomicAdd(&s_nd, __popc(bal));
+        at = __shfl_sync(0xffffffffu, at, 0);
+        if (claimed) slots[at + __popc(bal & lanemask_lt())] = (uint16_t)s;
       }
     }
+    const int64_t ew = seg_total<32>(eCl, 0xffffffffu);
+    if (lane == 0) redC[wid] = (VT)ew;
     __syncthreads();
-    const int nd = s_n;
-    for (int j = tid; j < nd; j += THREADS)
-      if (keys[slots[j]] == C) s_eC = (long long)vals[slots[j]];
-    __syncthreads();
-    const int64_t eC = s_eC, kv = g.k[v], aC = g.a[C], m2v = g.m2_of(v);
-    ST S = gain_lowest<ST>();
+    const int nd = s_nd;
+    int64_t eC = 0;
+#pragma unroll
+    for (int x = 0; x < NW; x++) eC += (int64_t)redC[x];
+    const int64_t kv = g.k[v], aC = g.a[C], m2v = g.m2_of(v);
+    ST Sb = gain_lowest<ST>();
     int32_t D = INT_MAX;
-    for (int j = tid; j < nd; j += THREADS) {
+    for (int j = tid; j < nd; j += T) {
       const uint32_t s = slots[j];
       const int32_t key = keys[s];
-      if (key != C) {
-        const ST x = gain<ST>(m2v, kv, (int64_t)vals[s], eC, g.a[key], aC);
-        if (better(x, key, S, D)) {
-          S = x;
-          D = key;
-        }
+      const ST x = gain<ST>(m2v, kv, (int64_t)vals[s], eC, g.a[key], aC);
+      if (better(x, key, Sb, D)) {
+        Sb = x;
+        D = key;
       }
     }
-    warp_argmax(S, D);
+    warp_argmax(Sb, D);
     if (lane == 0) {
-      redS[wid] = S;
+      redS[wid] = Sb;
       redD[wid] = D;
     }
     __syncthreads();
     if (wid == 0) {
-      S = lane < NW ? redS[lane] : gain_lowest<ST>();
+      Sb = lane < NW ? redS[lane] : gain_lowest<ST>();
       D = lane < NW ? redD[lane] : INT_MAX;
-      warp_argmax(S, D);
+      warp_argmax(Sb, D);
       if (lane == 0) {
-        prop[i] = (D != INT_MAX && S > 0) ? guard_choice(C, D, g.size) : C;
-        if (g.f_eC) {
-          g.f_eC[i] = eC;
-          g.f_eB[i] = D == INT_MAX ? 0 : tbl_get(keys, vals, mask, D);
-          g.f_dB[i] = D == INT_MAX ? -1 : D;
-          g.f_sB[i] = D == INT_MAX ? 0.0 : to_double(S);
-        }
+        prop[i] = proposal(Sb, D, C, g.size);
+        if (g.f_eC) put_features(g, i, eC, keys, vals, mask, Sb, D);
       }
     }
     __syncthreads();
-    for (int j = tid; j < nd; j += THREADS) {
+    for (int j = tid; j < nd; j += T) {
       const uint32_t s = slots[j];
       keys[s] = -1;
       vals[s] = 0;
     }
-    if (tid == 0) {
-      s_n = 0;
-      s_eC = 0;
-    }
+    if (tid == 0) s_nd = 0;
     __syncthreads();
   }
 }
@@ -758,43 +694,65 @@ __global__ void lm_decide(GraphState* __restrict__ gs, int G, int mode, int32_t 
 
 // ---------------------------------------------------------------- binning
 
-__global__ void bin_count(const int64_t* __restrict__ rp, int64_t n, const uint8_t* __restrict__ active,
-                          DevScalars* d, const int32_t* __restrict__ gid, const GraphState* __restrict__ gs,
-                          BinPlan plan) {
-  __shared__ unsigned long long sc[kMaxBins], sdb[kMaxBins];
-  __shared__ long long smax[kMaxBins];
-  __shared__ unsigned long long sdeg, sact;
-  if (threadIdx.x < kMaxBins) {
-    sc[threadIdx.x] = 0;
-    sdb[threadIdx.x] = 0;
-    smax[threadIdx.x] = 0;
+// Active vertices per degree bin, their degree sums and largest degree.  The
+// lanes of a warp are grouped by bin (match_any); each group's leader updates
+// the warp's own counters (leaders hold distinct bins, so no two update one
+// counter), and the warps' counters meet in shared memory, then in global
+// memory, once per CTA.
+__global__ void __launch_bounds__(256) bin_count(const int64_t* __restrict__ rp, int64_t n,
+                                                 const uint8_t* __restrict__ active, DevScalars* d,
+                                                 const int32_t* __restrict__ gid,
+                                                 const GraphState* __restrict__ gs, BinPlan plan) {
+  constexpr int NW = 256 / 32;
+  __shared__ unsigned long long wc[NW][kMaxBins], wdb[NW][kMaxBins];
+  __shared__ long long wmax[NW][kMaxBins];
+  const int lane = lane_id(), wid = threadIdx.x >> 5;
+  for (int b = lane; b < kMaxBins; b += 32) {
+    wc[wid][b] = 0;
+    wdb[wid][b] = 0;
+    wmax[wid][b] = 0;
   }
-  if (threadIdx.x == 0) {
-    sdeg = 0;
-    sact = 0;
+  __syncwarp();
+  unsigned long long deg_sum = 0, act = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (blockIdx.x * (int64_t)blockDim.x) + (threadIdx.x & ~31); base < n; base += stride) {
+    const int64_t v = base + lane;
+    bool ok = v < n && (!active || active[v]) && (!gid || gs[gid[v]].running);
+    const int64_t deg = ok ? rp[v + 1] - rp[v] : 0;
+    deg_sum += (unsigned long long)deg;
+    act += ok ? 1 : 0;
+    const int bin = (ok && deg > 0) ? bin_of(plan, deg) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, bin);
+    const int64_t ds = group_sum_exact(peers, deg);
+    const unsigned mx = __reduce_max_sync(peers, (unsigned)deg);
+    if (bin >= 0 && (int)(__ffs(peers) - 1) == lane) {
+      wc[wid][bin] += __popc(peers);
+      wdb[wid][bin] += (unsigned long long)ds;
+      if ((long long)mx > wmax[wid][bin]) wmax[wid][bin] = (long long)mx;
+    }
+    __syncwarp();
   }
+  deg_sum = warp_sum(deg_sum);
+  act = warp_sum(act);
   __syncthreads();
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-    if (active && !active[v]) continue;
-    if (gid && !gs[gid[v]].running) continue;
-    const int64_t deg = rp[v + 1] - rp[v];
-    atomicAdd(&sdeg, (unsigned long long)deg);
-    atomicAdd(&sact, 1ull);
-    if (deg == 0) continue;
-    const int bin = bin_of(plan, deg);
-    atomicAdd(&sc[bin], 1ull);
-    atomicAdd(&sdb[bin], (unsigned long long)deg);
-    atomicMax(&smax[bin], (long long)deg);
+  if (threadIdx.x < plan.nb) {
+    const int b = threadIdx.x;
+    unsigned long long c = 0, db = 0;
+    long long mx = 0;
+    for (int x = 0; x < NW; x++) {
+      c += wc[x][b];
+      db += wdb[x][b];
+      mx = wmax[x][b] > mx ? wmax[x][b] : mx;
+    }
+    if (c) {
+      atomicAdd((unsigned long long*)&d->bcnt[b], c);
+      atomicAdd((unsigned long long*)&d->bdeg[b], db);
+      atomicMax((long long*)&d->bmax[b], mx);
+    }
   }
-  __syncthreads();
-  if (threadIdx.x < plan.nb && sc[threadIdx.x]) {
-    atomicAdd((unsigned long long*)&d->bcnt[threadIdx.x], sc[threadIdx.x]);
-    atomicAdd((unsigned long long*)&d->bdeg[threadIdx.x], sdb[threadIdx.x]);
-    atomicMax((long long*)&d->bmax[threadIdx.x], smax[threadIdx.x]);
-  }
-  if (threadIdx.x == 0) {
-    atomicAdd((unsigned long long*)&d->act_deg, sdeg);
-    atomicAdd((unsigned long long*)&d->ncomm, sact);
+  if (lane == 0 && act) {
+    atomicAdd((unsigned long long*)&d->act_deg, deg_sum);
+    atomicAdd((unsigned long long*)&d->ncomm, act);
   }
 }
 
@@ -908,17 +866,10 @@ __global__ void mark_used(int64_t n, const int32_t* __restrict__ L, int32_t* __r
     if (!used[L[v]]) used[L[v]] = 1;  // a read first: most labels are already marked
 }
 
-// Coarse entries, aggregated on the fly.  Warps walk the fine CSR entry by
-// entry (1024-entry segments, so a hub row is shared by many warps); each
-// 32-entry chunk finds the row of every entry from the row boundaries held
-// one per lane, builds the key cid[L[u]] * nc + cid[L[y]] and sums equal keys
-// of the chunk with match_any + redux before one emit per distinct key.
-constexpr int64_t kSegEntries = 1024;
-
-// Row of entry e for the entry-linear walks below: every warp takes a
-// segment of kSegEntries consecutive entries, finds the row of its first
-// entry by binary search, then advances 32 entries at a time with the row
-// ends of the next 32 rows in its lanes.
+// Row of entry e for the entry-linear walks below: a warp walks a range of
+// consecutive entries, finds the row of its first entry by binary search,
+// then advances 32 entries at a time with the row ends of the next 32 rows
+// in its lanes.
 struct RowWalk {
   int64_t r;     // row of the chunk's first entry
   int64_t rb;    // lane i holds the end of row rb + i (valid while chunks stay below `last`)
@@ -972,63 +923,121 @@ struct RowWalk {
   }
 };
 
-// Coarse entries of one level (sort path): every entry (u, v, w) becomes the
-// key cid(L(u)) * nc + cid(L(v)) with weight w; equal keys of a 32-entry
-// chunk are summed before they are written.
-template <typename W, bool NARROW>
-__global__ void __launch_bounds__(256) emit_coarse(int64_t n, int64_t m, const int64_t* __restrict__ rp,
-                                                   const int32_t* __restrict__ col, const W* __restrict__ w,
-                                                   const int32_t* __restrict__ ccid,
-                                                   uint64_t nc, uint64_t* __restrict__ keys,
-                                                   uint64_t* __restrict__ vals, unsigned long long* __restrict__ count) {
-  // each warp stages its (key, sum) pairs in shared memory and reserves room
-  // in the output once per kEmitBuf - 32 pairs, not once per chunk (the one
-  // output counter is otherwise hit by every chunk of the graph)
-  constexpr int kEmitBuf = 256;
-  __shared__ uint64_t sbk[8][kEmitBuf];
-  __shared__ uint64_t sbv[8][kEmitBuf];
-  const int lane = lane_id(), wib = threadIdx.x >> 5;
-  uint64_t* bk = sbk[wib];
-  uint64_t* bv = sbv[wib];
-  int nb = 0;
+// Coarse entries of one level (sort path): every entry (u, y, w) becomes the
+// key cid(L(u)) * nc + cid(L(y)) with weight w.  Equal keys are summed twice
+// before they are written: within a warp's 32-entry chunk (match_any + redux),
+// then across the warp's whole range of entries in a warp-private hash table
+// in shared memory (the chunk's leaders hold distinct keys, so their updates
+// of the table never contend).  A warp writes its table out when it passes
+// half full, and at the end.  A level that collapses into few communities --
+// level 0 of a step that starts from the previous step's communities -- then
+// writes a few hundred pairs per warp instead of one per chunk, and the sort
+// that follows has little to do.
+constexpr int kEmitThreads = 256;
+
+// Warp table slots: 512 when key and sum are 32-bit (4 KB a warp), 256
+// otherwise, so a CTA's tables stay within 48 KB of static shared memory.
+template <typename KT, typename VT>
+__host__ __device__ constexpr int emit_slots() {
+  return sizeof(KT) + sizeof(VT) == 8 ? 512 : 256;
+}
+template <int BITS>
+__device__ __forceinline__ uint32_t emit_hash(uint32_t k) {
+  return (k * 0x9E3779B1u) >> (32 - BITS);
+}
+template <int BITS>
+__device__ __forceinline__ uint32_t emit_hash(unsigned long long k) {
+  return (uint32_t)((k * 0x9E3779B97F4A7C15ull) >> (64 - BITS));
+}
+
+template <typename W, typename KT, typename VT>
+__global__ void __launch_bounds__(kEmitThreads) emit_coarse(int64_t n, int64_t m, const int64_t* __restrict__ rp,
+                                                            const int32_t* __restrict__ col,
+                                                            const W* __restrict__ w,
+                                                            const int32_t* __restrict__ ccid, uint64_t nc,
+                                                            int64_t per_warp, uint64_t* __restrict__ keys,
+                                                            uint64_t* __restrict__ vals,
+                                                            unsigned long long* __restrict__ count) {
+  constexpr int NW = kEmitThreads / 32;
+  constexpr KT kEmpty = ~KT(0);
+  constexpr int kSlots = emit_slots<KT, VT>();
+  constexpr int kBits = kSlots == 512 ? 9 : 8;
+  static_assert(kSlots == (1 << kBits), "hash bits");
+  __shared__ KT stk[NW][kSlots];
+  __shared__ VT stv[NW][kSlots];
+  const int lane = lane_id(), wid = threadIdx.x >> 5;
+  KT* tk = stk[wid];
+  VT* tv = stv[wid];
+  for (int s = lane; s < kSlots; s += 32) {
+    tk[s] = kEmpty;
+    tv[s] = 0;
+  }
+  __syncwarp();
+  int used = 0;  // slots in use (warp-uniform)
+  // write the table's pairs out (one output reservation per 32 slots) and
+  // empty it
   auto flush = [&]() {
     __syncwarp();
-    unsigned long long slot = 0;
-    if (lane == 0 && nb) slot = atomicAdd(count, (unsigned long long)nb);
-    slot = __shfl_sync(0xffffffffu, slot, 0);
-    for (int x = lane; x < nb; x += 32) {
-      keys[slot + x] = bk[x];
-      vals[slot + x] = bv[x];
+    for (int s0 = 0; s0 < kSlots; s0 += 32) {
+      const int s = s0 + lane;
+      const KT k = tk[s];
+      const bool occ = k != kEmpty;
+      const unsigned bal = __ballot_sync(0xffffffffu, occ);
+      unsigned long long at = 0;
+      if (lane == 0 && bal) at = atomicAdd(count, (unsigned long long)__popc(bal));
+      at = __shfl_sync(0xffffffffu, at, 0);
+      if (occ) {
+        const unsigned long long pos = at + __popc(bal & lanemask_lt());
+        keys[pos] = (uint64_t)k;
+        vals[pos] = (uint64_t)tv[s];
+        tk[s] = kEmpty;
+        tv[s] = 0;
+      }
     }
     __syncwarp();
-    nb = 0;
+    used = 0;
   };
-  const int64_t nseg = cdiv(m, kSegEntries);
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t sg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; sg < nseg; sg += nw) {
-    const int64_t E0 = sg * kSegEntries, E1 = E0 + kSegEntries < m ? E0 + kSegEntries : m;
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t W0 = gw * per_warp, W1 = W0 + per_warp < m ? W0 + per_warp : m;
+  if (W0 < W1) {
     RowWalk rw;
-    rw.start(rp, n, E0);
-    for (int64_t c0 = E0; c0 < E1; c0 += 32) {
+    rw.start(rp, n, W0);
+    for (int64_t c0 = W0; c0 < W1; c0 += 32) {
       const int64_t e = c0 + lane;
-      const bool valid = e < E1;
+      const bool valid = e < W1;
       const int64_t row = rw.row(rp, n, c0, valid);
-      const int32_t cy = valid ? ccid[col[e]] : 0;
-      const uint64_t cu = valid ? (uint64_t)ccid[row] : 0;
-      const uint64_t key = valid ? cu * nc + (uint64_t)cy : ~0ull;
-      const W wt = valid ? w[e] : W(0);
-      const unsigned peers = __match_any_sync(0xffffffffu, key);
-      // NARROW: 2m < 2^31 bounds every sum of weights, so 32 bits are exact
-      const int64_t sum = NARROW ? (int64_t)__reduce_add_sync(peers, (unsigned)wt) : group_sum_exact(peers, wt);
-      const bool lead = valid && (int)(__ffs(peers) - 1) == lane;
-      const unsigned bal = __ballot_sync(0xffffffffu, lead);
-      if (lead) {
-        const int pos = nb + __popc(bal & lanemask_lt());
-        bk[pos] = key;
-        bv[pos] = (uint64_t)sum;
+      KT key = kEmpty;
+      W wt = W(0);
+      if (valid) {
+        key = (KT)((uint64_t)ccid[row] * nc + (uint64_t)ccid[col[e]]);
+        wt = w[e];
       }
-      nb += __popc(bal);
-      if (nb > kEmitBuf - 32) flush();
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      // VT = 32 bits: 2m < 2^31 bounds every sum of weights
+      const VT sum = sizeof(VT) == 4 ? (VT)__reduce_add_sync(peers, (unsigned)wt)
+                                     : (VT)group_sum_exact(peers, (int64_t)wt);
+      const bool lead = valid && (int)(__ffs(peers) - 1) == lane;
+      bool claimed = false;
+      if (lead) {
+        // leaders hold distinct keys, so a slot is claimed by at most one of
+        // them, and each adds to its own slot
+        uint32_t s = emit_hash<kBits>(key);
+        for (;;) {
+          const KT k = tk[s];
+          if (k == key) break;
+          if (k == kEmpty && atomicCAS(&tk[s], kEmpty, key) == kEmpty) {
+            claimed = true;
+            break;
+          }
+          s = (s + 1) & (kSlots - 1);
+        }
+        tv[s] += sum;
+      }
+      __syncwarp();
+      // at most 32 new keys a chunk: flushing above half minus one chunk keeps
+      // the table at most half full, so every probe ends
+      used += __popc(__ballot_sync(0xffffffffu, claimed));
+      if (used > kSlots / 2 - 32) flush();
     }
   }
   flush();
@@ -1221,51 +1230,55 @@ int make_bins(dcd_ctx* c, const Csr<W>& g, const uint8_t* active, Bins* b, const
   return DCD_OK;
 }
 
-template <typename W, typename ST, int CAP, int Q>
-int launch_warp_tbl(cudaStream_t s, const LV<W>& g, const int32_t* lst, int64_t cnt, int32_t* prop,
-                    int64_t* sweep) {
-  constexpr int T = 256;
-  constexpr size_t smem = (size_t)(T / 32) * warp_tbl_bytes<CAP, typename TblVal<ST>::type>();
-  const int grid = wave_grid(lm_warp_tbl<W, ST, CAP, Q>, cnt * 32, T, smem);
-  *sweep = (int64_t)grid * (T / 32);
-  count_launch(), lm_warp_tbl<W, ST, CAP, Q><<<grid, T, smem, s>>>(g, lst, cnt, prop);
+template <typename W, typename ST, int S, int Q>
+constexpr size_t seg_smem() {
+  return (size_t)8 * (32 / S) * row_tbl_bytes<S * Q, typename TblVal<ST>::type>();
+}
+
+template <typename W, typename ST, int S, int Q>
+int launch_seg(cudaStream_t s, const LV<W>& g, const int32_t* lst, int64_t cnt, int32_t* prop, int64_t* sweep) {
+  constexpr int T = 256, P = 32 / S;
+  constexpr size_t smem = seg_smem<W, ST, S, Q>();
+  const int grid = wave_grid(lm_seg<W, ST, S, Q>, cdiv(cnt, P) * 32, T, smem);
+  *sweep = (int64_t)grid * (T / 32) * P;
+  count_launch(), lm_seg<W, ST, S, Q><<<grid, T, smem, s>>>(g, lst, cnt, prop);
   return DCD_OK;
 }
 
-template <typename W, typename ST, int THREADS, int Q>
-int launch_large(dcd_ctx* c, cudaStream_t s, const LV<W>& g, const int32_t* lst, int64_t cnt, int64_t maxd,
-                 int32_t* prop, int64_t* sweep) {
-  const int32_t tcap = (int32_t)table_cap(maxd);
-  const size_t smem = (size_t)tcap * (sizeof(typename TblVal<ST>::type) + 6);  // values, keys, claimed-slot list
-  const int64_t ctas = cnt < 16 * (int64_t)c->sms ? cnt : 16 * (int64_t)c->sms;
-  *sweep = ctas;
-  count_launch(), lm_large<W, ST, THREADS, Q><<<(unsigned)ctas, THREADS, smem, s>>>(g, lst, cnt, prop, tcap);
+template <typename W, typename ST, int T, int Q>
+int launch_cta(cudaStream_t s, const LV<W>& g, const int32_t* lst, int64_t cnt, int32_t* prop, int64_t* sweep) {
+  constexpr size_t smem = cta_tbl_bytes<T, Q, typename TblVal<ST>::type>();
+  const int grid = wave_grid(lm_cta<W, ST, T, Q>, cnt * T, T, smem);
+  *sweep = grid;
+  count_launch(), lm_cta<W, ST, T, Q><<<grid, T, smem, s>>>(g, lst, cnt, prop);
   return DCD_OK;
 }
 
-// Shared-memory limits of the table kernels (host calls, made before any
-// launch and outside stream capture).
+template <typename K>
+int table_kernel_attrs(K* kernel, int threads, size_t smem) {
+  DCD_TRY_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  DCD_TRY_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                    (int)cudaSharedmemCarveoutMaxShared));
+  // occupancy of the grid-stride kernel, looked up here so that no query runs
+  // while a pass is being captured
+  resident_blocks(reinterpret_cast<const void*>(kernel), threads, smem);
+  return DCD_OK;
+}
+
+// Shared-memory limits and occupancy of the table kernels (host calls, made
+// before any launch and outside stream capture).
 template <typename W, typename ST>
 int prepare_lm_st() {
-  constexpr int T = 256;
-  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_warp_tbl<W, ST, 256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)((T / 32) * warp_tbl_bytes<256, typename TblVal<ST>::type>())));
-  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_warp_tbl<W, ST, 512, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)((T / 32) * warp_tbl_bytes<512, typename TblVal<ST>::type>())));
-  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_large<W, ST, 256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(table_cap(512) * (sizeof(typename TblVal<ST>::type) + 6))));
-  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_large<W, ST, 256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(table_cap(1024) * (sizeof(typename TblVal<ST>::type) + 6))));
-  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_large<W, ST, 256, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(table_cap(2048) * (sizeof(typename TblVal<ST>::type) + 6))));
-  DCD_TRY_CUDA(cudaFuncSetAttribute(lm_large<W, ST, 512, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(table_cap(4096) * (sizeof(typename TblVal<ST>::type) + 6))));
-  // occupancy of the grid-stride variants, looked up here so that no query
-  // runs while a pass is being captured
-  resident_blocks(reinterpret_cast<const void*>(lm_warp_tbl<W, ST, 256, 4>), T,
-                  (T / 32) * warp_tbl_bytes<256, typename TblVal<ST>::type>());
-  resident_blocks(reinterpret_cast<const void*>(lm_warp_tbl<W, ST, 512, 8>), T,
-                  (T / 32) * warp_tbl_bytes<512, typename TblVal<ST>::type>());
+  using VT = typename TblVal<ST>::type;
+  DCD_TRY(table_kernel_attrs(lm_seg<W, ST, 8, 2>, 256, seg_smem<W, ST, 8, 2>()));
+  DCD_TRY(table_kernel_attrs(lm_seg<W, ST, 16, 2>, 256, seg_smem<W, ST, 16, 2>()));
+  DCD_TRY(table_kernel_attrs(lm_seg<W, ST, 16, 4>, 256, seg_smem<W, ST, 16, 4>()));
+  DCD_TRY(table_kernel_attrs(lm_seg<W, ST, 32, 4>, 256, seg_smem<W, ST, 32, 4>()));
+  DCD_TRY(table_kernel_attrs(lm_seg<W, ST, 32, 8>, 256, seg_smem<W, ST, 32, 8>()));
+  DCD_TRY(table_kernel_attrs(lm_cta<W, ST, 128, 4>, 128, cta_tbl_bytes<128, 4, VT>()));
+  DCD_TRY(table_kernel_attrs(lm_cta<W, ST, 256, 4>, 256, cta_tbl_bytes<256, 4, VT>()));
+  DCD_TRY(table_kernel_attrs(lm_cta<W, ST, 512, 4>, 512, cta_tbl_bytes<512, 4, VT>()));
+  DCD_TRY(table_kernel_attrs(lm_cta<W, ST, 512, 8>, 512, cta_tbl_bytes<512, 8, VT>()));
   return DCD_OK;
 }
 
@@ -1307,30 +1320,15 @@ int launch_lm_bins(dcd_ctx* c, const LV<W>& lv, Bins& b, int32_t* prop, cudaEven
       const int32_t* lst = lst0 + o;
       int32_t* pr = prop + o;
       switch (b.plan.var[x]) {
-        case kLmHalf: {
-          const int grid = grid_for(cnt * 16, T, 16);
-          sweep[x] = (int64_t)grid * (T / 16);
-          if (g.f_eC)
-            count_launch(), lm_warp<W, ST, 16, true><<<grid, T, 0, s>>>(g, lst, cnt, pr);
-          else
-            count_launch(), lm_warp<W, ST, 16, false><<<grid, T, 0, s>>>(g, lst, cnt, pr);
-          break;
-        }
-        case kLmWarp: {
-          const int grid = grid_for(cnt * 32, T, 16);
-          sweep[x] = (int64_t)grid * (T / 32);
-          if (g.f_eC)
-            count_launch(), lm_warp<W, ST, 32, true><<<grid, T, 0, s>>>(g, lst, cnt, pr);
-          else
-            count_launch(), lm_warp<W, ST, 32, false><<<grid, T, 0, s>>>(g, lst, cnt, pr);
-          break;
-        }
-        case kLmWarp128: DCD_TRY((launch_warp_tbl<W, ST, 256, 4>(s, g, lst, cnt, pr, &sweep[x]))); break;
-        case kLmWarp256: DCD_TRY((launch_warp_tbl<W, ST, 512, 8>(s, g, lst, cnt, pr, &sweep[x]))); break;
-        case kLmBlk512: DCD_TRY((launch_large<W, ST, 256, 2>(c, s, g, lst, cnt, b.maxd[x], pr, &sweep[x]))); break;
-        case kLmBlk1k: DCD_TRY((launch_large<W, ST, 256, 4>(c, s, g, lst, cnt, b.maxd[x], pr, &sweep[x]))); break;
-        case kLmBlk2k: DCD_TRY((launch_large<W, ST, 256, 8>(c, s, g, lst, cnt, b.maxd[x], pr, &sweep[x]))); break;
-        case kLmBlk4k: DCD_TRY((launch_large<W, ST, 512, 8>(c, s, g, lst, cnt, b.maxd[x], pr, &sweep[x]))); break;
+        case kLmSeg16: DCD_TRY((launch_seg<W, ST, 8, 2>(s, g, lst, cnt, pr, &sweep[x]))); break;
+        case kLmSeg32: DCD_TRY((launch_seg<W, ST, 16, 2>(s, g, lst, cnt, pr, &sweep[x]))); break;
+        case kLmSeg64: DCD_TRY((launch_seg<W, ST, 16, 4>(s, g, lst, cnt, pr, &sweep[x]))); break;
+        case kLmWarp128: DCD_TRY((launch_seg<W, ST, 32, 4>(s, g, lst, cnt, pr, &sweep[x]))); break;
+        case kLmWarp256: DCD_TRY((launch_seg<W, ST, 32, 8>(s, g, lst, cnt, pr, &sweep[x]))); break;
+        case kLmCta512: DCD_TRY((launch_cta<W, ST, 128, 4>(s, g, lst, cnt, pr, &sweep[x]))); break;
+        case kLmCta1k: DCD_TRY((launch_cta<W, ST, 256, 4>(s, g, lst, cnt, pr, &sweep[x]))); break;
+        case kLmCta2k: DCD_TRY((launch_cta<W, ST, 512, 4>(s, g, lst, cnt, pr, &sweep[x]))); break;
+        case kLmCta4k: DCD_TRY((launch_cta<W, ST, 512, 8>(s, g, lst, cnt, pr, &sweep[x]))); break;
         default: {
           sweep[x] = cnt;
           const unsigned ch = hub_grid(c, b.hub);
@@ -1603,6 +1601,20 @@ struct CoarseGraph {
   Csr<int64_t> view;
 };
 
+// One wave of emit CTAs, every warp taking an equal contiguous range of
+// entries (a multiple of 32).
+template <typename W, typename KT, typename VT>
+int launch_emit(dcd_ctx* c, const Csr<W>& g, int64_t m0, const int32_t* ccid, int64_t nc, uint64_t* keys,
+                uint64_t* vals, unsigned long long* cnt) {
+  const int grid = wave_grid(emit_coarse<W, KT, VT>, cdiv(m0, 32) * 32, kEmitThreads);
+  const int64_t warps = (int64_t)grid * (kEmitThreads / 32);
+  const int64_t per_warp = cdiv(cdiv(m0, warps), 32) * 32;
+  ::dcd::count_launch(), emit_coarse<W, KT, VT><<<grid, kEmitThreads, 0, c->stream>>>(
+      g.n, m0, g.rp, g.col, g.w, ccid, (uint64_t)nc, per_warp, keys, vals, cnt);
+  DCD_LAUNCH_CHECK();
+  return DCD_OK;
+}
+
 template <typename W>
 int coarsen(dcd_ctx* c, const Csr<W>& g, const int32_t* L, const int32_t* cid, int64_t nc, CoarseGraph* out) {
   cudaStream_t s = c->stream;
@@ -1622,14 +1634,18 @@ int coarsen(dcd_ctx* c, const Csr<W>& g, const int32_t* L, const int32_t* cid, i
     ::dcd::count_launch(), coarse_of<<<grid_for(g.n, T), T, 0, s>>>(g.n, L, cid, ccid.get());
     int64_t m2max = 0;
     for (int x = 0; x < c->G; x++) m2max = c->hgs[x].m2 > m2max ? c->hgs[x].m2 : m2max;
-    if (m2max < ((int64_t)1 << 31))
-      ::dcd::count_launch(), emit_coarse<W, true><<<wave_grid(emit_coarse<W, true>, cdiv(m0, kSegEntries) * 32, T), T,
-                                                    0, s>>>(
-          g.n, m0, g.rp, g.col, g.w, ccid.get(), (uint64_t)nc, k0.get(), v0.get(), cnt.get());
+    const bool narrow = m2max < ((int64_t)1 << 31), small = nc < 65536;
+    if (narrow && small)
+      DCD_TRY((launch_emit<W, uint32_t, unsigned>(c, g, m0, ccid.get(), nc, k0.get(), v0.get(), cnt.get())));
+    else if (narrow)
+      DCD_TRY((launch_emit<W, unsigned long long, unsigned>(c, g, m0, ccid.get(), nc, k0.get(), v0.get(),
+                                                             cnt.get())));
+    else if (small)
+      DCD_TRY((launch_emit<W, uint32_t, unsigned long long>(c, g, m0, ccid.get(), nc, k0.get(), v0.get(),
+                                                             cnt.get())));
     else
-      ::dcd::count_launch(), emit_coarse<W, false><<<wave_grid(emit_coarse<W, false>, cdiv(m0, kSegEntries) * 32, T),
-                                                     T, 0, s>>>(
-          g.n, m0, g.rp, g.col, g.w, ccid.get(), (uint64_t)nc, k0.get(), v0.get(), cnt.get());
+      DCD_TRY((launch_emit<W, unsigned long long, unsigned long long>(c, g, m0, ccid.get(), nc, k0.get(),
+                                                                       v0.get(), cnt.get())));
     DCD_LAUNCH_CHECK();
   }
   DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch, cnt.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -1858,7 +1874,8 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
   int64_t level = 0, passes_total = 0, passes0 = 0, edges_total = 0, verts_total = 0;
   float ms_bin[4] = {0.f, 0.f, 0.f, 0.f};
   int64_t edges_bin[4] = {0, 0, 0, 0}, verts_bin[4] = {0, 0, 0, 0};
-  float ms_lm = 0.f, ms_apply = 0.f, ms_coarsen = 0.f;
+  float ms_lm = 0.f, ms_apply = 0.f, ms_coarsen = 0.f, ms_lm0 = 0.f;
+  int64_t edges0 = 0, verts0 = 0;
   bool first_level = true;
 
   // current level: level 0 uses g0 / labels0 / k0; later levels own their data
@@ -1888,7 +1905,12 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
       first_level = false;
     }
     passes_total += lr.passes;
-    if (level == 0) passes0 = lr.passes;
+    if (level == 0) {
+      passes0 = lr.passes;
+      ms_lm0 = lr.ms_lm;
+      edges0 = lr.edges;
+      verts0 = lr.verts;
+    }
     edges_total += lr.edges;
     verts_total += lr.verts;
     for (int x = 0; x < 4; x++) {
@@ -2026,6 +2048,9 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
       st->verts_bin[x] = verts_bin[x];
     }
     st->ms_local_move = ms_lm;
+    st->ms_local_move0 = ms_lm0;
+    st->edges_level0 = edges0;
+    st->verts_level0 = verts0;
     st->ms_apply = ms_apply;
     st->ms_coarsen = ms_coarsen;
     st->ms_finish = tf;

@@ -191,13 +191,19 @@ __device__ __forceinline__ void slot_table_init(const SlotTable<VT>& t, int cap,
   if (tid == 0) *t.ns = 0;
 }
 
-// Row v added into t by NT cooperating threads (whole warps); the caller
-// synchronises before and after.
+// Row v added into t by NT cooperating threads (whole warps): each thread
+// inserts its own entries -- a CAS claims the slot of a new label, a shared
+// atomic adds the weight, and the claimed slots are listed (one reservation
+// per warp and round) -- except the entries of label `skip` (the row vertex's
+// own community, most of a row), whose weight the thread sums in a register
+// and returns for the caller to reduce.  No warp-wide grouping runs per
+// entry.  The caller synchronises before and after.
 template <typename ST, typename VT>
-__device__ __forceinline__ void slot_table_fill(const SV& g, int32_t v, const SlotTable<VT>& t, uint32_t mask, int tid,
-                                                int NT) {
+__device__ __forceinline__ VT slot_table_fill(const SV& g, int32_t v, const SlotTable<VT>& t, uint32_t mask, int tid,
+                                              int NT, int32_t skip) {
   const int64_t b = g.rp[v];
   const int64_t d = g.rp[v + 1] - b;
+  VT acc = 0;
   for (int64_t e0 = 0; e0 < d; e0 += NT) {
     const int64_t e = e0 + tid;
     bool valid = e < d;
@@ -205,11 +211,37 @@ __device__ __forceinline__ void slot_table_fill(const SV& g, int32_t v, const Sl
     valid = valid && y != v;
     const int32_t lab = valid ? g.L[y] : -1;
     const int32_t wt = valid ? g.w[b + e] : 0;
-    const unsigned peers = __match_any_sync(0xffffffffu, lab);
-    const int64_t sum = group_sum<ST>(peers, wt);
-    if (valid && (int)(__ffs(peers) - 1) == (int)lane_id())
-      tbl_add_list<VT>(t.keys, t.vals, t.slots, t.ns, mask, lab, (VT)sum);
+    bool claimed = false;
+    uint32_t sl = 0;
+    if (valid) {
+      if (lab == skip) {
+        acc += (VT)wt;
+      } else {
+        sl = probe_claim(t.keys, mask, lab, claimed);
+        atomicAdd(&t.vals[sl], (VT)wt);
+      }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, claimed);
+    int at = 0;
+    if (lane_id() == 0 && bal) at = atomicAdd(t.ns, __popc(bal));
+    at = __shfl_sync(0xffffffffu, at, 0);
+    if (claimed) t.slots[at + __popc(bal & lanemask_lt())] = (uint16_t)sl;
   }
+  return acc;
+}
+
+// Sum over a CTA of one value per thread (red: NW words of shared memory);
+// every thread gets the total.  Synchronises twice.
+template <int NW, typename VT>
+__device__ __forceinline__ int64_t cta_total(VT x, VT* red) {
+  const int64_t w = seg_total<32>(x, 0xffffffffu);
+  if (lane_id() == 0) red[threadIdx.x >> 5] = (VT)w;
+  __syncthreads();
+  int64_t t = 0;
+#pragma unroll
+  for (int i = 0; i < NW; i++) t += (int64_t)red[i];
+  __syncthreads();
+  return t;
 }
 
 // Empty the listed slots (after a synchronisation that ends the table's reads);
@@ -315,9 +347,9 @@ __global__ void __launch_bounds__(256) scr_a_wtbl(SV g, int64_t off, int64_t cnt
     ST S = 0;
     if (has_ins) {
       const uint32_t mask = table_cap(g.rp[u + 1] - g.rp[u]) - 1;
-      slot_table_fill<ST, VT>(g, u, t, mask, lane, 32);
+      const VT own = slot_table_fill<ST, VT>(g, u, t, mask, lane, 32, C);
       __syncwarp();
-      const int64_t eC = tbl_get(t.keys, t.vals, mask, C);
+      const int64_t eC = seg_total<32>(own, 0xffffffffu);
       const int64_t ku = g.k[u], aC = g.a[C];
       int32_t D = INT_MAX;
       J = INT_MAX;
@@ -357,6 +389,7 @@ __global__ void __launch_bounds__(THREADS) scr_a_block(SV g, int64_t off, int64_
   constexpr int NW = THREADS / 32;
   __shared__ ST redS[NW];
   __shared__ int32_t redD[NW], redJ[NW];
+  __shared__ VT redE[NW];
   __shared__ int s_flags;
   const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5;
   const SlotTable<VT> t = slot_table<VT>(smem, cap);
@@ -378,9 +411,8 @@ __global__ void __launch_bounds__(THREADS) scr_a_block(SV g, int64_t off, int64_
     ST S = 0;
     if (flags & 2) {
       const uint32_t mask = table_cap(g.rp[u + 1] - g.rp[u]) - 1;
-      slot_table_fill<ST, VT>(g, u, t, mask, tid, THREADS);
-      __syncthreads();
-      const int64_t eC = tbl_get(t.keys, t.vals, mask, C);
+      const VT own = slot_table_fill<ST, VT>(g, u, t, mask, tid, THREADS, C);
+      const int64_t eC = cta_total<NW>(own, redE);
       const int64_t ku = g.k[u], aC = g.a[C];
       int32_t D = INT_MAX;
       J = INT_MAX;
@@ -595,13 +627,15 @@ __global__ void __launch_bounds__(256) scr_c_wtbl(SV g, GroupView gv, int64_t cn
     const int32_t gi = gv.glist[i];
     const int64_t m0 = gv.gstart[gi], m1 = gv.gstart[gi + 1];
     const int32_t j = (int32_t)gv.keys[m0];
+    const int32_t Cj = g.L[j];
     const uint32_t mask = table_cap(g.rp[j + 1] - g.rp[j]) - 1;
-    slot_table_fill<ST, VT>(g, j, t, mask, lane, 32);
+    const VT own = slot_table_fill<ST, VT>(g, j, t, mask, lane, 32, Cj);
     __syncwarp();
-    const int64_t e2 = tbl_get(t.keys, t.vals, mask, g.L[j]);
+    const int64_t e2 = seg_total<32>(own, 0xffffffffu);
     for (int64_t q = m0 + lane; q < m1; q += 32) {
       const int64_t idx = gv.vals[q];
-      decide<ST>(g, idx, j, tbl_get(t.keys, t.vals, mask, g.L[g.src[idx]]), e2);
+      const int32_t Ci = g.L[g.src[idx]];
+      decide<ST>(g, idx, j, Ci == Cj ? e2 : tbl_get(t.keys, t.vals, mask, Ci), e2);
     }
     __syncwarp();
     slot_table_clear(t, lane, 32);
@@ -614,7 +648,9 @@ __global__ void __launch_bounds__(256) scr_c_wtbl(SV g, GroupView gv, int64_t cn
 template <typename ST, int THREADS>
 __global__ void __launch_bounds__(THREADS) scr_c_block(SV g, GroupView gv, int64_t cnt, int cap) {
   using VT = typename TblVal<ST>::type;
+  constexpr int NW = THREADS / 32;
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ VT redE[NW];
   const int tid = threadIdx.x;
   const SlotTable<VT> t = slot_table<VT>(smem, cap);
   slot_table_init(t, cap, tid, THREADS);
@@ -623,13 +659,14 @@ __global__ void __launch_bounds__(THREADS) scr_c_block(SV g, GroupView gv, int64
     const int32_t gi = gv.glist[i];
     const int64_t m0 = gv.gstart[gi], m1 = gv.gstart[gi + 1];
     const int32_t j = (int32_t)gv.keys[m0];
+    const int32_t Cj = g.L[j];
     const uint32_t mask = table_cap(g.rp[j + 1] - g.rp[j]) - 1;
-    slot_table_fill<ST, VT>(g, j, t, mask, tid, THREADS);
-    __syncthreads();
-    const int64_t e2 = tbl_get(t.keys, t.vals, mask, g.L[j]);
+    const VT own = slot_table_fill<ST, VT>(g, j, t, mask, tid, THREADS, Cj);
+    const int64_t e2 = cta_total<NW>(own, redE);
     for (int64_t q = m0 + tid; q < m1; q += THREADS) {
       const int64_t idx = gv.vals[q];
-      decide<ST>(g, idx, j, tbl_get(t.keys, t.vals, mask, g.L[g.src[idx]]), e2);
+      const int32_t Ci = g.L[g.src[idx]];
+      decide<ST>(g, idx, j, Ci == Cj ? e2 : tbl_get(t.keys, t.vals, mask, Ci), e2);
     }
     __syncthreads();
     slot_table_clear(t, tid, THREADS);

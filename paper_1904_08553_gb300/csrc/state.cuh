@@ -62,36 +62,40 @@ __device__ __forceinline__ int graph_of(const int32_t* gid, int64_t v) { return 
 
 // Degree bins of the local-move kernels.  A bin holds the active vertices
 // whose degree lies in (hi of the previous bin, hi]; each bin runs one kernel
-// variant, which bounds the degree it accepts:
-//   kLmHalf      1..16     half a warp a vertex, lanes hold the row (no table)
-//   kLmWarp      ..32      one warp a vertex, lanes hold the row (no table)
-//   kLmWarp128   ..128     one warp a vertex, warp-private shared table of 256
-//   kLmWarp256   ..256     one warp a vertex, warp-private shared table of 512
-//   kLmBlk512    ..512     one CTA a vertex, shared table (256 threads)
-//   kLmBlk1k     ..1024    one CTA a vertex, shared table (256 threads)
-//   kLmBlk2k     ..2048    one CTA a vertex, shared table (256 threads)
-//   kLmBlk4k     ..4096    one CTA a vertex, shared table (512 threads)
-//   kLmHub       any       one CTA a vertex, table in global memory
+// variant, which bounds the degree it accepts.  Every variant sums the
+// neighbour communities of a row in a table in shared memory (louvain.cu):
+//   kLmSeg16     1..16     8 lanes a vertex (4 vertices a warp), 2 entries a lane
+//   kLmSeg32     ..32      16 lanes a vertex (2 vertices a warp), 2 entries a lane
+//   kLmSeg64     ..64      16 lanes a vertex (2 vertices a warp), 4 entries a lane
+//   kLmWarp128   ..128     one warp a vertex, 4 entries a lane
+//   kLmWarp256   ..256     one warp a vertex, 8 entries a lane
+//   kLmCta512    ..512     one CTA of 128 threads a vertex, 4 entries a thread
+//   kLmCta1k     ..1024    one CTA of 256 threads, 4 entries a thread
+//   kLmCta2k     ..2048    one CTA of 512 threads, 4 entries a thread
+//   kLmCta4k     ..4096    one CTA of 512 threads, 8 entries a thread
+//   kLmHub       any       a row split over many CTAs, table in global memory
 constexpr int kMaxBins = 12;
 enum LmVariant : int32_t {
-  kLmHalf = 0,
-  kLmWarp,
+  kLmSeg16 = 0,
+  kLmSeg32,
+  kLmSeg64,
   kLmWarp128,
   kLmWarp256,
-  kLmBlk512,
-  kLmBlk1k,
-  kLmBlk2k,
-  kLmBlk4k,
+  kLmCta512,
+  kLmCta1k,
+  kLmCta2k,
+  kLmCta4k,
   kLmHub,
   kLmVariants
 };
 __host__ __device__ __forceinline__ int64_t lm_variant_max(int v) {
-  return v == kLmHalf ? 16 : v == kLmWarp ? 32 : v == kLmWarp128 ? 128 : v == kLmWarp256 ? 256 : v == kLmBlk512 ? 512
-       : v == kLmBlk1k ? 1024 : v == kLmBlk2k ? 2048 : v == kLmBlk4k ? 4096 : INT64_MAX;
+  return v == kLmSeg16 ? 16 : v == kLmSeg32 ? 32 : v == kLmSeg64 ? 64 : v == kLmWarp128 ? 128
+       : v == kLmWarp256 ? 256 : v == kLmCta512 ? 512 : v == kLmCta1k ? 1024 : v == kLmCta2k ? 2048
+       : v == kLmCta4k ? 4096 : INT64_MAX;
 }
-// The four classes the step statistics report (warp, warp + table, CTA, hub).
+// The four classes the step statistics report (<= 32, 33..256, 257..4096, hub).
 __host__ __device__ __forceinline__ int lm_variant_class(int v) {
-  return v <= kLmWarp ? 0 : v <= kLmWarp256 ? 1 : v <= kLmBlk4k ? 2 : 3;
+  return v <= kLmSeg32 ? 0 : v <= kLmWarp256 ? 1 : v <= kLmCta4k ? 2 : 3;
 }
 
 static_assert(sizeof(DevScalars::bcnt) == kMaxBins * sizeof(int64_t), "one counter a bin");
@@ -108,13 +112,11 @@ __host__ __device__ __forceinline__ int bin_of(const BinPlan& p, int64_t deg) {
   return b;
 }
 
-// Every variant from kLmWarp on in degree order, each bin as wide as its
-// kernel allows (the half-warp variant measured no faster than a warp per
-// vertex on rows of up to 16 entries).
+// Every variant in degree order, each bin as wide as its kernel allows.
 inline BinPlan default_bin_plan() {
   BinPlan p;
   p.nb = 0;
-  for (int v = kLmWarp; v < kLmVariants; v++) {
+  for (int v = kLmSeg16; v < kLmVariants; v++) {
     p.var[p.nb] = v;
     p.hi[p.nb] = lm_variant_max(v);
     p.nb++;

@@ -36,8 +36,9 @@ EXPORTED = [
     "dcd_mlp_load", "dcd_set_fault", "dcd_get_level0_bins",
 ]
 MAX_BINS = 12
-LM_HALF, LM_WARP, LM_WARP128, LM_WARP256, LM_BLK512, LM_BLK1K, LM_BLK2K, LM_BLK4K, LM_HUB = range(9)
-LM_LIMIT = [16, 32, 128, 256, 512, 1024, 2048, 4096, -1]
+(LM_SEG16, LM_SEG32, LM_SEG64, LM_WARP128, LM_WARP256, LM_CTA512, LM_CTA1K, LM_CTA2K, LM_CTA4K,
+ LM_HUB) = range(10)
+LM_LIMIT = [16, 32, 64, 128, 256, 512, 1024, 2048, 4096, -1]
 MLP_FEATURES, MLP_HIDDEN, MLP_PARAMS = 12, 64, 5057
 NOALLOC_MAX_N = 1048056
 
@@ -73,14 +74,18 @@ class StepStats(ctypes.Structure):
                 [(k, ctypes.c_float) for k in _STAT_F32] + [("ms_bin", ctypes.c_float * 4),
                                                             ("reserved_f", ctypes.c_float * 5),
                                                             ("edges_bin", ctypes.c_int64 * 4),
-                                                            ("verts_bin", ctypes.c_int64 * 4)])
+                                                            ("verts_bin", ctypes.c_int64 * 4),
+                                                            ("ms_local_move0", ctypes.c_float),
+                                                            ("reserved_g", ctypes.c_float),
+                                                            ("edges_level0", ctypes.c_int64),
+                                                            ("verts_level0", ctypes.c_int64)])
 
     @property
     def N(self) -> int:
         return (self.n_hi << 64) + (self.n_lo & ((1 << 64) - 1))
 
     def as_dict(self) -> dict:
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved_f"}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("reserved_f", "reserved_g")}
         for k in ("ms_bin", "edges_bin", "verts_bin"):
             d[k] = list(d[k])
         d["N"] = self.N

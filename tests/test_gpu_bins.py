@@ -104,19 +104,21 @@ def test_group_autotune_keeps_results(dcd, orc, synth):
     grp.close()
 
 
+# variant ids of include/dcd.h: 1 = DCD_LM_SEG32, 3 = DCD_LM_WARP128,
+# 4 = DCD_LM_WARP256, 5 = DCD_LM_CTA512, 9 = DCD_LM_HUB
 @pytest.mark.parametrize("variants,his", [
     ([], []),                                         # no bin
     ([1], [32]),                                      # last bin not the unbounded hub
-    ([1, 8], [64, -1]),                               # above the warp variant's limit
-    ([4, 2, 8], [20, 100, -1]),                       # valid: a CTA variant below a warp one
-    ([3, 2, 8], [200, 100, -1]),                      # limits not increasing
-    ([9, 8], [10, -1]),                               # unknown variant
-    (list(range(9)) + [8, 8, 8, 8], [1] * 12 + [-1]),  # too many bins
+    ([1, 9], [64, -1]),                               # above the segment variant's limit
+    ([5, 3, 9], [20, 100, -1]),                       # valid: a CTA variant below a warp one
+    ([4, 3, 9], [200, 100, -1]),                      # limits not increasing
+    ([10, 9], [10, -1]),                              # unknown variant
+    (list(range(9)) + [9, 9, 9, 9], [1] * 12 + [-1]),  # too many bins
 ])
 def test_invalid_plans_are_refused(dcd, variants, his):
     ctx = dcd.Context(100)
     before = ctx.bins()
-    if variants == [4, 2, 8]:
+    if variants == [5, 3, 9]:
         ctx.set_bins(variants, his)  # increasing and within limits: accepted
         assert ctx.bins() == (variants, his)
         ctx.close()

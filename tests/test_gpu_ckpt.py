@@ -34,7 +34,7 @@ def test_resume_mid_stream_is_bit_identical(dcd, orc, synth, tmp_path):
         ref.apply_batch(ins, dels)
         a.update()
         ref.update(orc.DELTA)
-    a.set_bins([dcd.LM_WARP, dcd.LM_WARP256, dcd.LM_BLK4K, dcd.LM_HUB], [32, 256, 4096, -1])
+    a.set_bins([dcd.LM_SEG32, dcd.LM_WARP256, dcd.LM_CTA4K, dcd.LM_HUB], [32, 256, 4096, -1])
     path = tmp_path / "mid.ckpt"
     a.save(path)
     g_a, lab_a, r_a = a.graph(), a.labels(), a.rset()

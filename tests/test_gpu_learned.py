@@ -49,6 +49,66 @@ def test_features_and_labels_match_oracle(dcd, orc, synth):
         g_prev, labels = g_t, lab
 
 
+def test_learned_selection_matches_oracle(dcd, orc, synth):
+    """R'_t of the learned screen against the oracle's selection: the oracle's
+    pool and features, its FP64 network (BF16-rounded operands) and the same
+    thresholds; every pool vertex whose score is clear of its threshold by
+    more than the network tolerance (2e-2) must be selected alike, and no
+    vertex outside the pool may be selected."""
+    s = small_lfr(synth, 3, n=4000, steps=4)
+    rng = np.random.default_rng(5)
+    P = (rng.standard_normal(dcd.MLP_PARAMS) * 0.3).astype(np.float32)
+    # centre the network's output on the first screened step (the oracle's
+    # pool and scores): the output bias moves the median logit to 0, so both
+    # thresholds below cut through the scores
+    o = orc.Context(s.n)
+    o.apply_batch(*s.steps[0])
+    lab1, _, _ = o.update(orc.STATIC)
+    g0, _ = orc.Graph.empty(s.n).apply(*s.steps[0])
+    g1, _ = g0.apply(*s.steps[1])
+    r1 = orc.screen(g0, g1, lab1, *s.steps[1])
+    pool1, X1 = orc.screen_features(g0, g1, lab1, *s.steps[1], r1)
+    p1, _ = orc.mlp_forward(P, X1[np.nonzero(pool1)[0]])
+    p1 = np.clip(p1, 1e-6, 1 - 1e-6)
+    P[-1] -= np.float32(np.median(np.log(p1 / (1 - p1))))
+    mlp = dcd.Mlp(seed=1)
+    mlp.params = P
+    tk, ta = 0.4, 0.6
+    ctx = dcd.Context(s.n, mode=dcd.MODE_LEARNED)
+    ctx.set_screen(mlp, theta_keep=tk, theta_add=ta, judge=False)
+    g_prev = orc.Graph.empty(s.n)
+    labels = np.arange(s.n, dtype=np.int32)
+    clear_total, near_total, picked = 0, 0, 0
+    for t, (ins, dels) in enumerate(s.steps):
+        ctx.apply_batch(ins, dels)
+        lab, q, st = ctx.update()
+        g_t, err = g_prev.apply(ins, dels)
+        assert err == 0
+        if t > 0:
+            rds = orc.screen(g_prev, g_t, labels, ins, dels)
+            pool, X = orc.screen_features(g_prev, g_t, labels, ins, dels, rds)
+            v = np.nonzero(pool)[0]
+            p_ref, _ = orc.mlp_forward(P, X[v])
+            thr = np.where(rds[v] != 0, tk, ta)
+            want = p_ref >= thr
+            got = ctx.rset()
+            assert st.r_screen == int(rds.sum()) and st.pool == len(v)
+            clear = np.abs(p_ref - thr) > 2e-2
+            assert np.array_equal(got[v][clear] != 0, want[clear])
+            outside = np.ones(s.n, bool)
+            outside[v] = False
+            assert not got[outside].any()
+            clear_total += int(clear.sum())
+            near_total += int((~clear).sum())
+            picked += int(want.sum())
+        g_prev, labels = g_t, lab
+    ctx.close()
+    # the comparison is not vacuous: most pool vertices are clear of their
+    # threshold, and the selection keeps some vertices and drops others
+    assert clear_total > 10 * max(near_total, 1)
+    assert 0 < picked < clear_total + near_total
+
+
 def collect(dcd, synth, replicas, n):
     Xs, ys = [], []
     for r in replicas:

@@ -8,8 +8,8 @@ Labels, R_t, N, 2m, and the pass, move and level counts must be equal, bit
 for bit, at every step.  The test also shows that it reached the paths the
 small parity cases do not: at level 0 the active set holds at least 65,536
 vertices (the degree bins then run side by side on their own streams), and
-the warp-per-vertex bins hold more vertices than one sweep of their grid
-covers (the grid-stride loops run more than once per warp).
+the most populated segment-per-vertex bins hold more vertices than one sweep
+of their grid covers (the grid-stride loops run more than once per warp).
 """
 import numpy as np
 import pytest
@@ -51,8 +51,9 @@ def test_lfr_200k_label_exact(dcd, orc):
             if c > w:
                 multi_sweep.add(plan_var[b])
     assert side_steps == DELTA_STEPS
-    # the warp-per-vertex kernels (no table, and with a warp-private table)
-    # each ran more than one sweep of their grid in some step
-    assert dcd.LM_WARP in multi_sweep, multi_sweep
-    assert dcd.LM_WARP128 in multi_sweep, multi_sweep
+    # the segment kernels of the two most populated bins (rows of 17..32 and
+    # 33..64 entries, two vertices a warp) each ran more than one sweep of
+    # their grid in some step
+    assert dcd.LM_SEG32 in multi_sweep, multi_sweep
+    assert dcd.LM_SEG64 in multi_sweep, multi_sweep
     ctx.close()
