@@ -265,7 +265,8 @@ def gpu_arm(args):
     # ---- device-resident inputs ----
     ctx = dcd.Context(n, mode=dcd.MODE_DELTA, stream=ts)
     run(ctx, 0)
-    ctx.autotune(reps=3)  # degree-bin plan for this graph (untimed)
+    if not args.no_autotune:
+        ctx.autotune(reps=3)  # degree-bin plan for this graph (untimed)
     plan = ctx.bins()
     for t in range(1, 1 + args.warmup):
         run(ctx, t)
@@ -354,18 +355,15 @@ def gpu_arm(args):
     lm0_bytes = sum(BYTES_PER_ENTRY * s.edges_level0 + BYTES_PER_VERTEX * s.verts_level0 for s in stats)
     l0_gbs = lm0_bytes / (lm0_ms * 1e-3) / 1e9 if lm0_ms > 0 else None
     passes0 = sum(s.iters_level0 for s in stats)
-    # per degree-bin kernel class: time from fork to join, algorithmic bytes.
-    # The bins of a pass run side by side, so these intervals overlap: the
-    # roofline is taken over the whole evaluation (every bin of a pass, the
-    # pass's own events on the context stream)
+    # per degree-bin kernel class: its share of the algorithmic bytes (the
+    # bins of a pass run side by side inside one graph launch, so their times
+    # are not separated)
     names = ["lm_seg (degree <= 32)", "lm_seg (33..256)", "lm_cta (257..4096)",
              "hub_agg + hub_gain + hub_pick (> 4096)"]
     bins = []
     for b in range(4):
-        ms_b = sum(st.ms_bin[b] for st in stats)
         by_b = sum(BYTES_PER_ENTRY * st.edges_bin[b] + BYTES_PER_VERTEX * st.verts_bin[b] for st in stats)
-        bins.append({"kernel": names[b], "ms": ms_b, "bytes": by_b,
-                     "gbs": by_b / (ms_b * 1e-3) / 1e9 if ms_b > 0 else None})
+        bins.append({"kernel": names[b], "bytes": by_b, "share": by_b / lm_bytes if lm_bytes else None})
     achieved = l0_gbs
     nnz_mean = float(np.mean([s.nnz for s in stats]))
     cpu = cpu_baseline(stream, nnz_mean) if (world == 1 and not args.no_cpu) else None
@@ -407,23 +405,109 @@ def gpu_arm(args):
             "all_levels_gbs": pass_gbs,
             "all_levels_frac": (pass_gbs / peak) if pass_gbs else None,
             "bins": bins,
-            "bins_note": "each bin's ms runs from its fork to its join; the bins of a pass overlap, so the intervals "
-                         "add up to more than the pass and their GB/s understate the kernels",
         },
         "gpu_launches": int(launches),
         "clocks": clocks,
         "e2e": e2e,
         "cpu_baseline": cpu,
     }
+    if world == 1 and not args.no_extra:
+        del d_ins, d_del
+        torch.cuda.empty_cache()
+        line["extra"] = extra_legs(args)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
 
 
+def extra_legs(args) -> dict:
+    """The configuration's other workloads, each timed with CUDA events and
+    its own clock record, reported beside the main line: R-MAT scale 24, the
+    512-graph batched form, and the learned screen."""
+    out = {}
+    for name, leg in (("rmat24", rmat_leg), ("batched", batched_leg), ("learned", learned_leg)):
+        t0 = time.time()
+        try:
+            out[name] = leg(args)
+        except Exception as e:  # a failing leg is reported, the main line stands
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        out[name]["wall_s"] = time.time() - t0
+    return out
+
+
+# ------------------------------------------------------------------ R-MAT scale 24
+
+RMAT_SCALE = 24
+
+
+def rmat_leg(args):
+    """Plain dLouvain-Delta-s on R-MAT scale 24 (16.8M vertices, a=0.57,
+    b=c=0.19, edge factor 16, weights 1..8), 12 steps of 1% inserts and 0.5%
+    deletes: step 1 static (untimed), then W warm-up steps and the remaining
+    steps timed with CUDA events on the context stream (2m >= 2^31 here, so
+    the 128-bit gain path runs)."""
+    import torch
+
+    from paper_1904_08553_gb300 import dcd, synth
+
+    t0 = time.time()
+    stream = synth.rmat(synth.seed_for(2, 0), scale=args.rmat_scale, edge_factor=16, steps=LFR_STEPS,
+                        ins_frac=0.01, del_frac=0.005)
+    gen_s = time.time() - t0
+    n = stream.n
+    dev = torch.device("cuda", 0)
+    ts = torch.cuda.current_stream(dev)
+    ctx = dcd.Context(n, mode=dcd.MODE_DELTA, stream=ts)
+    first = 1 + min(args.warmup, LFR_STEPS - 2)
+    stats, ms = [], 0.0
+    with ClockSampler(0) as clk:
+        for t in range(LFR_STEPS):
+            ins, dels = stream.steps[t]
+            di = torch.from_numpy(np.ascontiguousarray(ins)).to(dev)
+            dd = np.zeros((len(dels), 3), np.int32)
+            dd[:, :2] = dels
+            dd = torch.from_numpy(dd).to(dev)
+            torch.cuda.synchronize()
+            ctx.apply_batch_device(di, len(ins), dd, len(dels))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(ts)
+            _, q, st = ctx.update(labels_out=None)
+            e1.record(ts)
+            torch.cuda.synchronize()
+            if t == 0:
+                ctx.autotune(reps=2)
+            if t >= first:
+                stats.append(st)
+                ms += e0.elapsed_time(e1)
+            del di, dd
+    ctx.close()
+    peak, peak_kind = peaks()
+    lm0_ms = sum(s.ms_local_move0 for s in stats)
+    lm0_bytes = sum(BYTES_PER_ENTRY * s.edges_level0 + BYTES_PER_VERTEX * s.verts_level0 for s in stats)
+    gbs = lm0_bytes / (lm0_ms * 1e-3) / 1e9 if lm0_ms > 0 else None
+    return {
+        "workload": (f"rmat{args.rmat_scale}: R-MAT scale {args.rmat_scale} ({n:,} vertices, a=0.57 b=c=0.19), "
+                     f"edge factor 16, weights 1..8, 12 steps of 1% inserts and 0.5% deletes"),
+        "ms_per_step": ms / len(stats), "timed_steps": f"t={first + 1}..12", "generation_s": gen_s,
+        "r_fraction": float(np.mean([s.r_size / s.n for s in stats])), "nnz_last": stats[-1].nnz,
+        "m2_last": stats[-1].m2, "q_last": stats[-1].q,
+        "ms_merge": float(np.mean([s.ms_merge for s in stats])),
+        "ms_screen": float(np.mean([s.ms_screen for s in stats])),
+        "ms_local_move": float(np.mean([s.ms_local_move for s in stats])),
+        "ms_coarsen": float(np.mean([s.ms_coarsen for s in stats])),
+        "level0_local_move_gbs": gbs, "level0_frac": (gbs / peak) if gbs else None, "peak_kind": peak_kind,
+        "timing": "CUDA events on the context stream around each update", "clocks": clk.summary(),
+    }
+
+
 # ------------------------------------------------------------------ learned screen
 
 def learned_arm(args):
+    print(json.dumps(learned_leg(args)), flush=True)
+
+
+def learned_leg(args):
     """Learned screen vs plain Delta-screening: train the network on move labels
     of full re-evaluation (BASE) runs of the LFR generator at n = 200,000
     (--train-seeds runs of 12 steps), then run each evaluation stream (fresh
@@ -439,7 +523,8 @@ def learned_arm(args):
     from paper_1904_08553_gb300 import dcd, synth
 
     torch.cuda.set_device(0)
-    T = 1 + args.warmup + args.steps
+    T = LFR_STEPS  # the evaluation streams are the 12-step configurations
+    warm = min(args.warmup, LFR_STEPS - 2)
     Xs, ys = [], []
     t0 = time.time()
     for r in range(args.train_seeds):
@@ -480,31 +565,38 @@ def learned_arm(args):
             dd[:, :2] = dels
             d_del.append(torch.from_numpy(dd).cuda())
 
+        ts = torch.cuda.current_stream()
+
         def run(mode, judge):
-            ctx = dcd.Context(n, mode=mode)
+            ctx = dcd.Context(n, mode=mode, stream=ts)
             if mode == dcd.MODE_LEARNED:
                 ctx.set_screen(mlp, theta_keep=args.theta_keep, theta_add=args.theta_add, judge=judge)
             out = []
             for t in range(T):
                 ctx.apply_batch_device(d_ins[t], len(stream.steps[t][0]), d_del[t], len(stream.steps[t][1]))
                 torch.cuda.synchronize()
-                a = time.perf_counter()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(ts)
                 _, q, st = ctx.update(labels_out=None)
-                ms = (time.perf_counter() - a) * 1e3
+                e1.record(ts)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
                 if t == 0:
                     ctx.autotune(reps=2)
-                if t >= 1 + args.warmup:
+                if t >= 1 + warm:
                     out.append((ms, q, st.r_size, st.r_screen, st.fallback, st.q_screen, st.pool))
             ctx.close()
             return out
 
-        plain = run(dcd.MODE_DELTA, False)
-        learned = run(dcd.MODE_LEARNED, False)
-        judged = run(dcd.MODE_LEARNED, True)
+        with ClockSampler(0) as clk:
+            plain = run(dcd.MODE_DELTA, False)
+            learned = run(dcd.MODE_LEARNED, False)
+            judged = run(dcd.MODE_LEARNED, True)
+        clocks = clk.summary()
         del d_ins, d_del
         gap = [p[1] - l[1] for p, l in zip(plain, learned)]
         return {
-            "workload": name, "description": desc, "timed_steps": f"t={2 + args.warmup}..{T}",
+            "workload": name, "description": desc, "timed_steps": f"t={2 + warm}..{T}",
             "r_fraction_delta": float(np.mean([p[2] for p in plain]) / n),
             "r_fraction_learned": float(np.mean([l[2] for l in learned]) / n),
             "pool_fraction": float(np.mean([l[6] for l in learned]) / n),
@@ -515,6 +607,8 @@ def learned_arm(args):
             "q_gap_max": float(max(gap)), "q_gap_mean": float(np.mean(gap)),
             "steps_within_1e-3": int(sum(g <= 1e-3 for g in gap)), "steps": len(gap),
             "judged_fallbacks": int(sum(j[4] for j in judged)),
+            "timing": "CUDA events on the work stream around each update",
+            "clocks": clocks,
         }
 
     evals = []
@@ -536,12 +630,18 @@ def learned_arm(args):
         "thresholds": {"keep": args.theta_keep, "add": args.theta_add},
         "evaluations": evals,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 # ------------------------------------------------------------------ batched form
 
 def batched_arm(args):
+    line = batched_leg(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+def batched_leg(args):
     """512 independent temporal SBMs (n log-uniform in 500..200,000, blocks of
     20..2,000, mean degree 8..32, 3 % inserts and 1 % deletes per step) advanced
     together by one group update per step, against the same graphs updated one
@@ -554,7 +654,7 @@ def batched_arm(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
+    if world > 1 and not dist.is_initialized():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -574,24 +674,37 @@ def batched_arm(args):
     gen_s = time.time() - t0
     sizes = [s.n for s in streams]
     T = len(streams[0].steps)
-    grp = dcd.Group(sizes, mode=dcd.MODE_DELTA)
+    ts = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        """CUDA-event time (ms) of fn on the work stream, synchronised on both sides."""
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ts)
+        r = fn()
+        e1.record(ts)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), r
+
+    grp = dcd.Group(sizes, mode=dcd.MODE_DELTA, stream=ts)
     group_ms = []
-    for t in range(T):
-        for g, s in enumerate(streams):
-            grp.apply_batch(g, *s.steps[t])
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-        a = time.perf_counter()
-        _, q, st = grp.update(labels_out=None)
-        torch.cuda.synchronize()
-        ms = shard.max_over_ranks((time.perf_counter() - a) * 1e3, device=dev)
-        if t >= 1:
-            group_ms.append(ms)
-        else:
-            grp.autotune(reps=3)  # degree-bin plan of the union graph (untimed)
+    launches_group = []
+    with ClockSampler(local) as clk:
+        for t in range(T):
+            for g, s in enumerate(streams):
+                grp.apply_batch(g, *s.steps[t])
+            if world > 1:
+                dist.barrier()
+            l0 = dcd.dcd_kernel_launches()
+            ms, (_, q, st) = timed(lambda: grp.update(labels_out=None))
+            ms = shard.max_over_ranks(ms, device=dev)
+            if t >= 1:
+                group_ms.append(ms)
+                launches_group.append(dcd.dcd_kernel_launches() - l0)
+            else:
+                grp.autotune(reps=3)  # degree-bin plan of the union graph (untimed)
+    clocks = clk.summary()
     plan = grp.bins()
-    launches_group = st[0].launches
     q_group = q.copy()
     grp.close()
     # one context per graph, one graph after the other (a context lives for its
@@ -600,26 +713,24 @@ def batched_arm(args):
     q_seq = np.zeros(len(sizes))
     launches_seq = 0
     for g, s_ in enumerate(streams):
-        ctx = dcd.Context(sizes[g], mode=dcd.MODE_DELTA)
+        ctx = dcd.Context(sizes[g], mode=dcd.MODE_DELTA, stream=ts)
         for t in range(T):
             ctx.apply_batch(*s_.steps[t])
-            torch.cuda.synchronize()
-            a = time.perf_counter()
-            _, q_seq[g], stg = ctx.update(labels_out=None)
-            torch.cuda.synchronize()
+            l0 = dcd.dcd_kernel_launches()
+            ms, (_, q_seq[g], stg) = timed(lambda: ctx.update(labels_out=None))
             if t >= 1:
-                seq_ms[t - 1] += (time.perf_counter() - a) * 1e3
+                seq_ms[t - 1] += ms
             if t == T - 1:
-                launches_seq += stg.launches
+                launches_seq += dcd.dcd_kernel_launches() - l0
         ctx.close()
     seq_mean = shard.max_over_ranks(float(np.mean(seq_ms)), device=dev)
     same = shard.sum_over_ranks(float(not np.array_equal(q_group, q_seq)), device=dev) == 0
     n_all = int(shard.sum_over_ranks(float(sum(sizes)), device=dev))
-    if world > 1:
+    if world > 1 and not args.keep_pg:
         dist.barrier()
         dist.destroy_process_group()
     if rank != 0:
-        return
+        return None
     line = {
         "metric": "batched form: ms per time step for all graphs (group update vs one context per graph)",
         "workload": (f"{args.graphs} temporal SBMs, n log-uniform 500..200,000 (total {n_all:,} vertices), "
@@ -627,11 +738,13 @@ def batched_arm(args):
         "n_gpus": world, "scaling": "strong" if world > 1 else None,
         "ms_per_step_group": float(np.mean(group_ms)), "ms_per_step_one_at_a_time": seq_mean,
         "speedup": float(seq_mean / np.mean(group_ms)),
-        "kernel_launches_per_step": {"group": int(launches_group), "one_at_a_time": int(launches_seq)},
+        "kernel_launches_per_step": {"group": float(np.mean(launches_group)), "one_at_a_time": int(launches_seq)},
+        "timing": "CUDA events on the work stream around each update, synchronised on both sides",
+        "clocks": clocks,
         "identical_modularity": bool(same), "generation_s": gen_s,
         "bin_plan": {"variants": plan[0], "max_degree": plan[1]},
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 # ------------------------------------------------------------ temporal resolution
@@ -725,6 +838,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="main line only: skip the R-MAT, batched and learned-screen legs")
+    ap.add_argument("--keep-pg", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default degree-bin plan (a fixed kernel sequence, for profiling)")
     ap.add_argument("--n", type=int, default=LFR_N, help="vertex count (smaller cases for profiling)")
     ap.add_argument("--workload", default="lfr_2m", choices=["lfr_2m", "learned", "batched", "resolution"])
     ap.add_argument("--graphs", type=int, default=512)

@@ -62,12 +62,18 @@ typedef struct {
   int32_t w;    /* weight > 0 for inserts; ignored for deletes     */
 } dcd_edge;
 
+/* ---- host methods of the multi-level run (Sec. III-D applies
+ * Delta-screening to both) ---- */
+#define DCD_ALG_LOUVAIN 0  /* Louvain: Algorithm 1                                    */
+#define DCD_ALG_SLM 1      /* smart local moving: dSLM (refinement of every community) */
+
 typedef struct {
   int32_t mode;       /* DCD_MODE_*; default DCD_MODE_DELTA                          */
   int32_t max_iters;  /* local-move passes per level; default 500 (tau reading)       */
   int32_t max_levels; /* default 64                                                   */
   int32_t tau_inv;    /* a pass (level) gaining at most |N| / tau_inv stops it; 1e6  */
-  int32_t reserved[12];
+  int32_t alg;        /* DCD_ALG_*; default DCD_ALG_LOUVAIN                           */
+  int32_t reserved[11];
 } dcd_config;
 
 typedef struct {
@@ -99,7 +105,8 @@ typedef struct {
   float ms_apply;        /* move apply + modularity tracking                        */
   float ms_coarsen;      /* graph compaction (all levels)                           */
   float ms_finish;       /* label composition, canonical labels                     */
-  float ms_bin[4];       /* local-move time per degree bin: <=32, 33..256, 257..4096, more */
+  float ms_bin[4];       /* 0: the degree bins of a pass run side by side in one graph launch, so their
+                            times are not separated (edges_bin / verts_bin give their work) */
   float reserved_f[5];
   int64_t edges_bin[4];  /* entries scanned per degree bin (all passes)              */
   int64_t verts_bin[4];  /* vertices evaluated per degree bin (all passes)           */
@@ -107,6 +114,8 @@ typedef struct {
   float reserved_g;
   int64_t edges_level0;  /* entries scanned at level 0 (all its passes)             */
   int64_t verts_level0;  /* vertices evaluated at level 0 (all its passes)          */
+  int64_t refine_iters;  /* DCD_ALG_SLM: local-move passes of the refinements       */
+  int64_t refine_moves;  /* DCD_ALG_SLM: moves of the refinements                   */
 } dcd_step_stats;
 
 typedef struct dcd_ctx dcd_ctx;
@@ -115,12 +124,17 @@ typedef struct dcd_ctx dcd_ctx;
 void dcd_config_default(dcd_config* cfg);
 
 /* Create a dynamic graph on vertices [0, n) with no edges (Sec. III-A:
- * G(V, E) as a sequence G_1..G_T).  cfg may be NULL (defaults);
+ * G(V, E) as a sequence G_1..G_T).  cfg may be NULL (defaults); with
+ * cfg->alg = DCD_ALG_SLM the multi-level run is smart local moving
+ * (dSLM-Delta-s in DCD_MODE_DELTA), which needs n < 2^30 (a pass may name
+ * n + v, the empty community of v) and does not take DCD_MODE_LEARNED or
+ * training-data collection (dcd_update: DCD_ESTATE);
  * cuda_stream is the cudaStream_t the context's work runs on; with NULL the
  * context creates a stream of its own that is ordered with the legacy default
  * stream (the local-move passes run as CUDA graphs, which the legacy stream
  * cannot capture).  *out receives the context.
- * Errors: DCD_EINVAL (n <= 0 or n > 2^31 - 1, out NULL), DCD_ENOMEM, DCD_ECUDA. */
+ * Errors: DCD_EINVAL (n <= 0 or n > 2^31 - 1, out NULL, an unknown alg, alg
+ * DCD_ALG_SLM with n >= 2^30), DCD_ENOMEM, DCD_ECUDA. */
 int dcd_create(int64_t n, const dcd_config* cfg, void* cuda_stream, dcd_ctx** out);
 
 /* Release every resource of the context.  NULL is accepted. */
@@ -324,7 +338,8 @@ int dcd_get_screen_data(dcd_ctx* ctx, float* X_out, float* y_out, int32_t* verte
  * update runs every kernel once for all graphs (they occupy disjoint vertex
  * ranges of one union graph), while 2m, the tracked modularity and the pass
  * and level stop rules of Algorithm 1 stay per graph, so every graph's result
- * is the one its own context would give.  Modes STATIC, BASE, DELTA only.
+ * is the one its own context would give.  Modes STATIC, BASE, DELTA only;
+ * Louvain only (DCD_ALG_SLM: DCD_EINVAL).
  * dcd_group_apply_batch stages a batch of graph g (local ids in [0, n[g]),
  * host arrays); dcd_group_update advances every graph one step.
  * labels_out: sum(n) int32 (graph after graph, local canonical labels), host

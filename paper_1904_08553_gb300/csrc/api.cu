@@ -286,8 +286,9 @@ int dcd_create(int64_t n, const dcd_config* cfg, void* cuda_stream, dcd_ctx** ou
   dcd_config_default(&cf);
   if (cfg) cf = *cfg;
   if (cf.mode < DCD_MODE_STATIC || cf.mode > DCD_MODE_LEARNED || cf.max_iters <= 0 || cf.max_levels <= 0 ||
-      cf.tau_inv <= 0)
+      cf.tau_inv <= 0 || (cf.alg != DCD_ALG_LOUVAIN && cf.alg != DCD_ALG_SLM))
     return DCD_EINVAL;
+  if (cf.alg == DCD_ALG_SLM && n >= ((int64_t)1 << 30)) return DCD_EINVAL;
   dcd_ctx* c = new (std::nothrow) dcd_ctx();
   if (!c) return DCD_ENOMEM;
   c->n = n;
@@ -510,6 +511,8 @@ int dcd::update_impl(dcd_ctx* c, dcd_step_stats* st, dcd_step_stats* per_graph, 
   const bool first = c->t == 0;
   const int mode = first ? DCD_MODE_STATIC : c->mode;
   if (mode == DCD_MODE_GIVEN_R && !c->has_rgiven) return DCD_ESTATE;
+  // the learned screen and its training data are defined on Louvain's level 0
+  if (c->cfg.alg == DCD_ALG_SLM && (mode == DCD_MODE_LEARNED || c->collect)) return DCD_ESTATE;
   trace("update: enter");
   DCD_TRY_CUDA(cudaEventRecord(c->ev[0], s));
   DCD_TRY_CUDA(cudaMemsetAsync(d, 0, sizeof(DevScalars), s));
@@ -594,8 +597,12 @@ int dcd::update_impl(dcd_ctx* c, dcd_step_stats* st, dcd_step_stats* per_graph, 
   DCD_TRY(c->labels_nx.ensure(&c->mem, n));
   if (collect) DCD_TRY(c->level0.ensure(&c->mem, n));
   // the screening's community sums are those of C_{t-1} on G_t, the start of level 0
-  DCD_TRY(run_louvain(c, g, L0.get(), active, mo.k, c->labels_nx.get(), st, collect ? c->level0.get() : nullptr,
-                      per_graph, a.n ? a.get() : nullptr, size.n ? size.get() : nullptr));
+  if (c->cfg.alg == DCD_ALG_SLM)
+    DCD_TRY(run_slm(c, g, L0.get(), active, mo.k, c->labels_nx.get(), st));
+  else
+    DCD_TRY(run_louvain(c, g, L0.get(), active, mo.k, c->labels_nx.get(), st,
+                        collect ? c->level0.get() : nullptr, per_graph, a.n ? a.get() : nullptr,
+                        size.n ? size.get() : nullptr));
   if (collect) DCD_TRY(screen_labels(c, src_labels, c->level0.get()));
   if (learned && c->judge && st) {
     // the judge: plain Delta-screening from the same state; keep it when the

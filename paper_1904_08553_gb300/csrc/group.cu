@@ -105,7 +105,7 @@ int dcd_group_create(int32_t G, const int64_t* n, const dcd_config* cfg, void* c
   dcd_config cf;
   dcd_config_default(&cf);
   if (cfg) cf = *cfg;
-  if (cf.mode == DCD_MODE_GIVEN_R || cf.mode == DCD_MODE_LEARNED) return DCD_EINVAL;
+  if (cf.mode == DCD_MODE_GIVEN_R || cf.mode == DCD_MODE_LEARNED || cf.alg != DCD_ALG_LOUVAIN) return DCD_EINVAL;
   dcd_group* grp = new (std::nothrow) dcd_group();
   if (!grp) return DCD_ENOMEM;
   grp->G = G;

@@ -673,11 +673,13 @@ __global__ void lm_decide(GraphState* __restrict__ gs, int G, int mode, int32_t 
       X.running = X.done ? 0 : 1;
       X.passes = 0;
       X.moves = 0;
+      X.moves_level = 0;
       if (X.running) atomicOr(any_running, 1);
       continue;
     }
     if (!X.running) continue;
     X.passes++;
+    X.moves_level += X.moves;
     if (X.moves == 0) {
       X.running = 0;
       continue;
@@ -690,6 +692,35 @@ __global__ void lm_decide(GraphState* __restrict__ gs, int G, int mode, int32_t 
     if (below_tau(N_new - N_old, N_old, tau_inv) || X.passes >= max_iters) X.running = 0;
     if (X.running) atomicOr(any_running, 1);
   }
+}
+
+// ---------------------------------------------------------------- device pass loop
+//
+// A level's passes run inside one CUDA graph: a 'while' conditional node
+// around the pass body.  The body's first and middle kernels stamp the
+// global timer; its last kernel adds the pass's evaluation and apply times,
+// counts the pass, and keeps the loop going while some graph's pass loop goes
+// on (the stop rule of lm_decide).  The stop rule ends every level within
+// max_iters passes; the cap here is a second bound that can only be reached
+// if that rule were broken, and it is reported.
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__global__ void pass_stamp(DevScalars* d, int k) { d->stamp[k] = global_ns(); }
+
+__global__ void pass_end(DevScalars* d, cudaGraphConditionalHandle h, int32_t cap) {
+  const unsigned long long t = global_ns();
+  d->t_eval_ns += d->stamp[1] - d->stamp[0];
+  d->t_apply_ns += t - d->stamp[1];
+  d->level_passes += 1;
+  const bool more = d->any_running != 0;
+  const bool capped = more && d->level_passes >= cap;
+  if (capped) d->loop_err = 1;
+  cudaGraphSetConditional(h, (more && !capped) ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------- binning
@@ -1041,6 +1072,80 @@ __global__ void __launch_bounds__(kEmitThreads) emit_coarse(int64_t n, int64_t m
     }
   }
   flush();
+}
+
+// Dense coarsening, for levels that collapse into at most kDenseNc
+// communities (level 0 of a Delta-screening step starts from the previous
+// step's communities): the coarse graph is an nc x nc matrix of sums that
+// stays in L2.  Warps walk the fine entries as emit_coarse does, sum equal
+// keys of a 32-entry chunk with match_any + redux, and the chunk's leaders
+// add straight into the matrix; two row-per-warp passes then count and write
+// the non-zero cells in column order.  No key list, no sort.
+constexpr int64_t kDenseNc = 4096;
+
+template <typename W, typename VT>
+__global__ void __launch_bounds__(kEmitThreads) emit_dense(int64_t n, int64_t m, const int64_t* __restrict__ rp,
+                                                           const int32_t* __restrict__ col,
+                                                           const W* __restrict__ w,
+                                                           const int32_t* __restrict__ ccid, uint32_t nc,
+                                                           int64_t per_warp, VT* __restrict__ dense) {
+  const int lane = lane_id();
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t W0 = gw * per_warp, W1 = W0 + per_warp < m ? W0 + per_warp : m;
+  if (W0 >= W1) return;
+  RowWalk rw;
+  rw.start(rp, n, W0);
+  for (int64_t c0 = W0; c0 < W1; c0 += 32) {
+    const int64_t e = c0 + lane;
+    const bool valid = e < W1;
+    const int64_t row = rw.row(rp, n, c0, valid);
+    uint32_t key = 0xffffffffu;
+    W wt = W(0);
+    if (valid) {
+      key = (uint32_t)ccid[row] * nc + (uint32_t)ccid[col[e]];
+      wt = w[e];
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    // VT = 32 bits: 2m < 2^31 bounds every sum of weights
+    const VT sum = sizeof(VT) == 4 ? (VT)__reduce_add_sync(peers, (unsigned)wt)
+                                   : (VT)group_sum_exact(peers, (int64_t)wt);
+    if (valid && (int)(__ffs(peers) - 1) == lane) atomicAdd(&dense[key], sum);
+  }
+}
+
+// Non-zero cells of each matrix row (a warp a row).
+template <typename VT>
+__global__ void dense_count(const VT* __restrict__ dense, int64_t nc, int64_t* __restrict__ rowcnt) {
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < nc; r += nw) {
+    int64_t cnt = 0;
+    for (int64_t c0 = 0; c0 < nc; c0 += 32) {
+      const int64_t cc = c0 + lane_id();
+      cnt += __popc(__ballot_sync(0xffffffffu, cc < nc && dense[r * nc + cc] != 0));
+    }
+    if (lane_id() == 0) rowcnt[r] = cnt;
+  }
+}
+
+// The non-zero cells written as the coarse CSR (columns ascending).
+template <typename VT>
+__global__ void dense_write(const VT* __restrict__ dense, int64_t nc, const int64_t* __restrict__ rp,
+                            int32_t* __restrict__ ccol, int64_t* __restrict__ cw) {
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < nc; r += nw) {
+    int64_t pos = rp[r];
+    for (int64_t c0 = 0; c0 < nc; c0 += 32) {
+      const int64_t cc = c0 + lane_id();
+      const VT x = cc < nc ? dense[r * nc + cc] : VT(0);
+      const unsigned bal = __ballot_sync(0xffffffffu, x != 0);
+      if (x != 0) {
+        const int64_t at = pos + __popc(bal & lanemask_lt());
+        ccol[at] = (int32_t)cc;
+        cw[at] = (int64_t)x;
+      }
+      pos += __popc(bal);
+    }
+  }
 }
 
 // coarse vertex of every vertex: cid of its label (one gather per entry in the
@@ -1439,24 +1544,19 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
   const int32_t* lst = bins.list.get();
   bool any = total > 0;
   int64_t sweep[kMaxBins] = {};
-  // One pass: evaluate, apply, tracked N, stop rule, scalars to the host.
+  // One pass: evaluate, apply, tracked N, stop rule, then the loop condition.
   // Every pass of a level enqueues the same work (the pass number lives on
-  // the device), so the body is captured once into a CUDA graph and each pass
-  // is one graph launch.
-  auto enqueue_pass = [&](unsigned evf) -> int {
+  // the device), so the body is captured once, into the body of a 'while'
+  // conditional node, and the whole pass loop of the level is one graph
+  // launch.
+  auto enqueue_pass = [&](cudaGraphConditionalHandle h) -> int {
     ::dcd::count_launch(), gs_reset_pass<<<cdiv(G, 128), 128, 0, s>>>(gs, G, &d->pass_id);
     DCD_TRY_CUDA(cudaMemsetAsync(moved_cnt.get(), 0, sizeof(int32_t), s));
     DCD_TRY_CUDA(cudaMemsetAsync(moved_big_cnt.get(), 0, sizeof(int32_t), s));
     DCD_TRY_CUDA(cudaMemsetAsync(&d->any_running, 0, sizeof(int32_t), s));
-    DCD_TRY_CUDA(cudaEventRecordWithFlags(c->ev[2], s, evf));
-    if (any)
-      DCD_TRY(launch_lm_nocfg<W>(c, lvl, bins, prop.get(), &c->ev[12], evf, total >= kForkMin, sweep));
-    else
-      for (int x = 0; x < bins.plan.nb; x++) {
-        DCD_TRY_CUDA(cudaEventRecordWithFlags(c->bin_start[x], s, evf));
-        DCD_TRY_CUDA(cudaEventRecordWithFlags(c->ev[12 + x], s, evf));
-      }
-    DCD_TRY_CUDA(cudaEventRecordWithFlags(c->ev[3], s, evf));
+    ::dcd::count_launch(), pass_stamp<<<1, 1, 0, s>>>(d, 0);
+    if (any) DCD_TRY(launch_lm_nocfg<W>(c, lvl, bins, prop.get(), nullptr, 0, total >= kForkMin, sweep));
+    ::dcd::count_launch(), pass_stamp<<<1, 1, 0, s>>>(d, 1);
     if (total) {
       ::dcd::count_launch(), lm_apply<<<grid_for(total, T), T, 0, s>>>(
           lst, total, big_from, prop.get(), L, kbuf.get(), (unsigned long long*)a.get(), size.get(),
@@ -1472,88 +1572,92 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
     ::dcd::count_launch(), sumsq_acc<<<sq_ctas, T, 0, s>>>(a.get(), nv, gid, gs);
     ::dcd::count_launch(), lm_decide<<<cdiv(G, 128), 128, 0, s>>>(gs, G, 1, c->cfg.max_iters, c->cfg.tau_inv,
                                                                    &d->any_running);
+    ::dcd::count_launch(), pass_end<<<1, 1, 0, s>>>(d, h, c->cfg.max_iters + 2);
     DCD_LAUNCH_CHECK();
-    DCD_TRY_CUDA(cudaEventRecordWithFlags(c->ev[4], s, evf));
-    DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
-    DCD_TRY_CUDA(cudaMemcpyAsync(c->hgs, gs, G * sizeof(GraphState), cudaMemcpyDeviceToHost, s));
     return DCD_OK;
   };
   if (any) DCD_TRY(prepare_lm<W>(lvl));
   DCD_TRY(side_streams(c));
-  struct ExecGuard {
+  struct GraphGuard {
+    cudaGraph_t g = nullptr;
     cudaGraphExec_t x = nullptr;
     cudaStream_t s = nullptr;
-    ~ExecGuard() {
+    ~GraphGuard() {
       if (x) {
         cudaStreamSynchronize(s);  // an error path may leave a launch of it in flight
         cudaGraphExecDestroy(x);
       }
+      if (g) cudaGraphDestroy(g);
     }
-  } exec;
-  exec.s = s;
-  int64_t body_launches = 0;
-  // a level with nothing to evaluate still runs one (empty) pass, as the
-  // sequential definition does
-  for (;;) {
-    if (!exec.x) {
-      DCD_TRY_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      const int64_t l0 = g_launches.load();
-      const int rc = enqueue_pass(cudaEventRecordExternal);
-      cudaGraph_t graph = nullptr;
-      const cudaError_t ec = cudaStreamEndCapture(s, &graph);
-      body_launches = g_launches.load() - l0;
-      if (rc != DCD_OK || ec != cudaSuccess) {
-        if (graph) cudaGraphDestroy(graph);
-        if (rc != DCD_OK) return rc;
-        DCD_TRY_CUDA(ec);
+  } gg;
+  gg.s = s;
+  {
+    DCD_TRY_CUDA(cudaGraphCreate(&gg.g, 0));
+    cudaGraphConditionalHandle h;
+    // the condition starts at 1 on every launch: a level runs at least one
+    // pass, even with nothing to evaluate, as the sequential definition does
+    DCD_TRY_CUDA(cudaGraphConditionalHandleCreate(&h, gg.g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    DCD_TRY_CUDA(cudaGraphAddNode(&node, gg.g, nullptr, nullptr, 0, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    DCD_TRY_CUDA(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const int64_t l0 = g_launches.load();
+    const int rc = enqueue_pass(h);
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(s, &captured);
+    const int64_t body_launches = g_launches.load() - l0;
+    g_launches -= body_launches;  // counted below, once per pass that ran
+    if (rc != DCD_OK) return rc;
+    DCD_TRY_CUDA(ec);
+    DCD_TRY_CUDA(cudaGraphInstantiate(&gg.x, gg.g, 0));
+    if (level == 0) {  // the level-0 bin record (dcd_get_level0_bins)
+      c->l0_nb = bins.plan.nb;
+      c->l0_side = any && total >= kForkMin;
+      for (int x = 0; x < kMaxBins; x++) {
+        c->l0_cnt[x] = x < bins.plan.nb ? bins.cnt[x] : 0;
+        c->l0_sweep[x] = x < bins.plan.nb ? sweep[x] : 0;
       }
-      const cudaError_t ei = cudaGraphInstantiate(&exec.x, graph, 0);
-      cudaGraphDestroy(graph);
-      DCD_TRY_CUDA(ei);
-      if (level == 0) {  // the level-0 bin record (dcd_get_level0_bins)
-        c->l0_nb = bins.plan.nb;
-        c->l0_side = any && total >= kForkMin;
-        for (int x = 0; x < kMaxBins; x++) {
-          c->l0_cnt[x] = x < bins.plan.nb ? bins.cnt[x] : 0;
-          c->l0_sweep[x] = x < bins.plan.nb ? sweep[x] : 0;
-        }
-      }
-    } else {
-      g_launches += body_launches;
     }
-    DCD_TRY_CUDA(cudaGraphLaunch(exec.x, s));
+    DCD_TRY_CUDA(cudaMemsetAsync(&d->level_passes, 0, sizeof(int32_t), s));
+    DCD_TRY_CUDA(cudaMemsetAsync(&d->t_eval_ns, 0, 2 * sizeof(unsigned long long), s));
+    DCD_TRY_CUDA(cudaGraphLaunch(gg.x, s));
+    DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+    DCD_TRY_CUDA(cudaMemcpyAsync(c->hgs, gs, G * sizeof(GraphState), cudaMemcpyDeviceToHost, s));
     DCD_TRY_CUDA(cudaStreamSynchronize(s));
-    float t1 = 0.f, t2 = 0.f;
-    cudaEventElapsedTime(&t1, c->ev[2], c->ev[3]);
-    cudaEventElapsedTime(&t2, c->ev[3], c->ev[4]);
-    out->ms_lm += t1;
-    out->ms_apply += t2;
-    {
-      float tb[kMaxBins] = {};
-      for (int x = 0; x < bins.plan.nb; x++) {
-        cudaEventElapsedTime(&tb[x], c->bin_start[x], c->ev[12 + x]);
-        const int k = lm_variant_class(bins.plan.var[x]);
-        out->ms_bin[k] += tb[x];
-        out->edges_bin[k] += bins.deg[x];
-        out->verts_bin[k] += bins.cnt[x];
-      }
-      if (trace_on()) {
-        char buf[1024];
-        int o = 0;
-        for (int x = 0; x < bins.plan.nb && o < 900; x++)
-          o += snprintf(buf + o, sizeof(buf) - o, " [<=%lld: %lld v %lld e %.3f ms]",
-                        bins.plan.hi[x] == INT64_MAX ? -1LL : (long long)bins.plan.hi[x], (long long)bins.cnt[x],
-                        (long long)bins.deg[x], tb[x]);
-        tracef("pass %d level %d:%s apply %.3f", (int)out->passes, level, buf, t2);
-      }
+    if (c->hsc->loop_err) {
+      note_cuda_error(cudaErrorUnknown, "local-move pass loop passed its cap", __FILE__, __LINE__);
+      return DCD_ETIMEOUT;
     }
-    out->passes++;
-    out->edges += bins.act_deg;
-    out->verts += bins.n_active;
-    for (int x = 0; x < G; x++) tally->moves[x] += c->hgs[x].moves;
-    if (!c->hsc->any_running) break;
+    const int64_t passes = c->hsc->level_passes;
+    g_launches += body_launches * passes;
+    out->passes = passes;
+    out->ms_lm = (float)(c->hsc->t_eval_ns * 1e-6);
+    out->ms_apply = (float)(c->hsc->t_apply_ns * 1e-6);
+    out->edges = bins.act_deg * passes;
+    out->verts = bins.n_active * passes;
+    for (int x = 0; x < bins.plan.nb; x++) {
+      const int k = lm_variant_class(bins.plan.var[x]);
+      out->edges_bin[k] += bins.deg[x] * passes;
+      out->verts_bin[k] += bins.cnt[x] * passes;
+    }
+    if (trace_on()) {
+      char buf[1024];
+      int o = 0;
+      for (int x = 0; x < bins.plan.nb && o < 900; x++)
+        o += snprintf(buf + o, sizeof(buf) - o, " [<=%lld: %lld v %lld e]",
+                      bins.plan.hi[x] == INT64_MAX ? -1LL : (long long)bins.plan.hi[x], (long long)bins.cnt[x],
+                      (long long)bins.deg[x]);
+      tracef("level %d: %lld passes, evaluation %.3f ms, apply %.3f ms:%s", level, (long long)passes, out->ms_lm,
+             out->ms_apply, buf);
+    }
   }
   for (int x = 0; x < G; x++) {
+    tally->moves[x] += c->hgs[x].moves_level;
     tally->passes[x] += c->hgs[x].passes;
     if (level == 0) tally->passes0[x] = c->hgs[x].passes;
   }
@@ -1615,11 +1719,58 @@ int launch_emit(dcd_ctx* c, const Csr<W>& g, int64_t m0, const int32_t* ccid, in
   return DCD_OK;
 }
 
+// Dense coarsening (nc <= kDenseNc): matrix, emit, count, scan, write.
+template <typename W, typename VT>
+int coarsen_dense(dcd_ctx* c, const Csr<W>& g, const int32_t* ccid, int64_t nc, CoarseGraph* out) {
+  cudaStream_t s = c->stream;
+  const int T = 256;
+  const int64_t m0 = g.nnz;
+  Buf<VT> dense;
+  Buf<int64_t> stmp;
+  DCD_TRY(dense.alloc(&c->mem, nc * nc));
+  DCD_TRY(stmp.alloc(&c->mem, scan_tmp_count(nc + 1) + 1));
+  DCD_TRY_CUDA(cudaMemsetAsync(dense.get(), 0, nc * nc * sizeof(VT), s));
+  if (m0 > 0) {
+    const int grid = wave_grid(emit_dense<W, VT>, cdiv(m0, 32) * 32, kEmitThreads);
+    const int64_t per_warp = cdiv(cdiv(m0, (int64_t)grid * (kEmitThreads / 32)), 32) * 32;
+    ::dcd::count_launch(), emit_dense<W, VT><<<grid, kEmitThreads, 0, s>>>(g.n, m0, g.rp, g.col, g.w, ccid,
+                                                                            (uint32_t)nc, per_warp, dense.get());
+    DCD_LAUNCH_CHECK();
+  }
+  DCD_TRY(out->rp.alloc(&c->mem, nc + 1));
+  DCD_TRY_CUDA(cudaMemsetAsync(out->rp.get(), 0, (nc + 1) * sizeof(int64_t), s));
+  ::dcd::count_launch(), dense_count<VT><<<grid_for(nc * 32, T), T, 0, s>>>(dense.get(), nc, out->rp.get());
+  DCD_LAUNCH_CHECK();
+  DCD_TRY(exclusive_scan<int64_t>(out->rp.get(), out->rp.get(), nc + 1, nullptr, stmp.get(), s));
+  DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch, out->rp.get() + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  DCD_TRY_CUDA(cudaStreamSynchronize(s));
+  const int64_t U = c->hscratch[0];
+  DCD_TRY(out->col.alloc(&c->mem, U));
+  DCD_TRY(out->w.alloc(&c->mem, U));
+  ::dcd::count_launch(), dense_write<VT><<<grid_for(nc * 32, T), T, 0, s>>>(dense.get(), nc, out->rp.get(),
+                                                                             out->col.get(), out->w.get());
+  DCD_LAUNCH_CHECK();
+  out->view = Csr<int64_t>{nc, U, out->rp.get(), out->col.get(), out->w.get()};
+  return DCD_OK;
+}
+
 template <typename W>
 int coarsen(dcd_ctx* c, const Csr<W>& g, const int32_t* L, const int32_t* cid, int64_t nc, CoarseGraph* out) {
   cudaStream_t s = c->stream;
   const int T = 256;
   const int64_t m0 = g.nnz;
+  if (nc <= kDenseNc) {
+    Buf<int32_t> ccid;
+    DCD_TRY(ccid.alloc(&c->mem, g.n > 0 ? g.n : 1));
+    if (g.n > 0) {
+      ::dcd::count_launch(), coarse_of<<<grid_for(g.n, T), T, 0, s>>>(g.n, L, cid, ccid.get());
+      DCD_LAUNCH_CHECK();
+    }
+    int64_t m2max = 0;
+    for (int x = 0; x < c->G; x++) m2max = c->hgs[x].m2 > m2max ? c->hgs[x].m2 : m2max;
+    if (m2max < ((int64_t)1 << 31)) return coarsen_dense<W, unsigned>(c, g, ccid.get(), nc, out);
+    return coarsen_dense<W, unsigned long long>(c, g, ccid.get(), nc, out);
+  }
   Buf<uint64_t> k0, k1, v0, v1;
   Buf<int32_t> head, uid;
   Buf<uint32_t> stmp;
@@ -2052,6 +2203,653 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
     st->edges_level0 = edges0;
     st->verts_level0 = verts0;
     st->ms_apply = ms_apply;
+    st->ms_coarsen = ms_coarsen;
+    st->ms_finish = tf;
+  }
+  return DCD_OK;
+}
+
+
+// ================================================================ dSLM-Delta-s
+//
+// Smart local moving, the paper's second host method (Sec. III-D applies
+// Delta-screening to it as to Louvain), in the synchronous exact-integer form
+// the oracle fixes:
+//   - a pass moves vertices in one direction only: even passes to smaller
+//     labels, odd passes to larger ones; in an odd pass a vertex of a
+//     community of two or more may also move into an empty community (label
+//     n + v) when that gains more than every neighbouring community; staying
+//     wins ties, the smaller label wins ties between communities; after the
+//     pass every community is renamed to its smallest member;
+//   - a level stops after a down-and-up cycle that moved nothing or gained at
+//     most |N| / tau_inv, or after max_iters passes;
+//   - refinement: every community is split by the same local moving from
+//     singletons, a vertex seeing only neighbours of its own community, with
+//     the whole graph's k_v and 2m;
+//   - aggregation: sub-communities become vertices, each starting in the
+//     community that holds it (named by the coarse vertex of the community's
+//     smallest member); the run stops when every sub-community is a single
+//     vertex, when a level >= 1 gained at most |N| / tau_inv, or at
+//     max_levels;
+//   - R_t restricts the local moving of level 0 only.
+
+namespace {
+
+// The SLM choice of v from its row's sums: the best neighbouring community
+// in the pass direction (S > 0 to move, ties to the smaller label), then, in
+// an upward pass, the empty community n + v when it gains more.
+template <typename ST>
+__device__ __forceinline__ int32_t slm_choice(ST S, int32_t D, int32_t C, int up, int64_t m2, int64_t kv, int64_t eC,
+                                              int64_t aC, int32_t sizeC, int64_t n, int32_t v) {
+  int32_t best = C;
+  ST bestS = 0;
+  if (D != INT_MAX && S > 0) {
+    best = D;
+    bestS = S;
+  }
+  if (up && sizeC > 1) {
+    const ST s0 = gain<ST>(m2, kv, 0, eC, 0, aC);  // into an empty community
+    if (s0 > bestS) best = (int32_t)(n + v);
+  }
+  return best;
+}
+
+// Rows of at most 32 x Q entries: one warp per vertex, the row's sums in a
+// warp-private shared table (the local move's scheme); parent (may be NULL)
+// limits the row to neighbours of v's parent community.
+template <typename W, typename ST, int Q>
+__global__ void __launch_bounds__(256) slm_warp(LV<W> g, const int32_t* __restrict__ parent, int up, int64_t n,
+                                                const int32_t* __restrict__ list, int64_t cnt,
+                                                int32_t* __restrict__ prop) {
+  using VT = typename TblVal<ST>::type;
+  constexpr int ROW = 32 * Q, CAP = seg_cap(ROW);
+  constexpr size_t SB = row_tbl_bytes<ROW, VT>();
+  constexpr uint32_t mask = CAP - 1;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = lane_id(), wib = threadIdx.x >> 5;
+  unsigned char* base = smem + (size_t)wib * SB;
+  int32_t* keys = reinterpret_cast<int32_t*>(base);
+  VT* vals = reinterpret_cast<VT*>(base + (size_t)CAP * 4);
+  uint16_t* slots = reinterpret_cast<uint16_t*>(base + (size_t)CAP * (4 + sizeof(VT)));
+  for (int s = lane; s < CAP; s += 32) {
+    keys[s] = -1;
+    vals[s] = 0;
+  }
+  __syncwarp();
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < cnt; i += nw) {
+    const int32_t v = list[i];
+    const int64_t b = g.rp[v];
+    const int d = (int)(g.rp[v + 1] - b);
+    const int32_t C = g.L[v], pv = parent ? parent[v] : 0;
+    int32_t lab[Q];
+    W wt[Q];
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      const int e = q * 32 + lane;
+      lab[q] = -1;
+      wt[q] = W(0);
+      if (e < d) {
+        lab[q] = g.col[b + e];
+        wt[q] = g.w[b + e];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      const int32_t u = lab[q];
+      lab[q] = (u >= 0 && u != v && (!parent || parent[u] == pv)) ? g.L[u] : -1;
+    }
+    VT eCl = 0;
+    int nd = 0;
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      if (q * 32 < d) {
+        const bool isC = lab[q] == C;
+        eCl += isC ? (VT)wt[q] : VT(0);
+        bool claimed = false;
+        uint32_t s = 0;
+        if (lab[q] >= 0 && !isC) {
+          s = probe_claim(keys, mask, lab[q], claimed);
+          atomicAdd(&vals[s], (VT)wt[q]);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, claimed);
+        if (claimed) slots[nd + __popc(bal & lanemask_lt())] = (uint16_t)s;
+        nd += __popc(bal);
+      }
+    }
+    __syncwarp();
+    const int64_t eC = seg_total<32>(eCl, 0xffffffffu);
+    const int64_t kv = g.k[v], aC = g.a[C], m2 = g.m2;
+    ST S = gain_lowest<ST>();
+    int32_t D = INT_MAX;
+    for (int j = lane; j < nd; j += 32) {
+      const uint32_t s = slots[j];
+      const int32_t key = keys[s];
+      if (up ? key > C : key < C) {
+        const ST x = gain<ST>(m2, kv, (int64_t)vals[s], eC, g.a[key], aC);
+        if (better(x, key, S, D)) {
+          S = x;
+          D = key;
+        }
+      }
+    }
+    warp_argmax(S, D);
+    if (lane == 0) prop[i] = slm_choice<ST>(S, D, C, up, m2, kv, eC, aC, g.size[C], n, v);
+    __syncwarp();
+    for (int j = lane; j < nd; j += 32) {
+      const uint32_t s = slots[j];
+      keys[s] = -1;
+      vals[s] = 0;
+    }
+    __syncwarp();
+  }
+}
+
+// Rows of any length: one CTA per vertex, the table in a region of global
+// memory private to the CTA (tcap slots, at least twice the longest row of
+// the bin).  Keys are read around L1 (__ldcg): the region is emptied and
+// reused vertex after vertex.
+template <typename W, typename ST>
+__global__ void __launch_bounds__(256) slm_cta(LV<W> g, const int32_t* __restrict__ parent, int up, int64_t n,
+                                               const int32_t* __restrict__ list, int64_t cnt,
+                                               int32_t* __restrict__ prop, int32_t* __restrict__ tkeys,
+                                               typename TblVal<ST>::type* __restrict__ tvals,
+                                               uint32_t* __restrict__ tslots, uint32_t tcap) {
+  using VT = typename TblVal<ST>::type;
+  constexpr int T = 256, NW = T / 32;
+  __shared__ ST redS[NW];
+  __shared__ int32_t redD[NW];
+  __shared__ VT redE[NW];
+  __shared__ int32_t s_nd;
+  const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5;
+  int32_t* keys = tkeys + (size_t)blockIdx.x * tcap;
+  VT* vals = tvals + (size_t)blockIdx.x * tcap;
+  uint32_t* slots = tslots + (size_t)blockIdx.x * tcap;
+  const uint32_t mask = tcap - 1;
+  for (uint32_t s = tid; s < tcap; s += T) {
+    keys[s] = -1;
+    vals[s] = 0;
+  }
+  if (tid == 0) s_nd = 0;
+  __syncthreads();
+  for (int64_t i = blockIdx.x; i < cnt; i += gridDim.x) {
+    const int32_t v = list[i];
+    const int64_t b = g.rp[v];
+    const int64_t d = g.rp[v + 1] - b;
+    const int32_t C = g.L[v], pv = parent ? parent[v] : 0;
+    VT eCl = 0;
+    for (int64_t e0 = 0; e0 < d; e0 += T) {
+      const int64_t e = e0 + tid;
+      bool valid = e < d;
+      const int32_t u = valid ? g.col[b + e] : -1;
+      valid = valid && u != v && (!parent || parent[u] == pv);
+      const int32_t lab = valid ? g.L[u] : -1;
+      const W wt = valid ? g.w[b + e] : W(0);
+      bool claimed = false;
+      uint32_t s = 0;
+      if (valid) {
+        if (lab == C) {
+          eCl += (VT)wt;
+        } else {
+          s = hash_label(lab, mask);
+          for (;;) {
+            const int32_t k = __ldcg(&keys[s]);
+            if (k == lab) break;
+            if (k == -1) {
+              const int32_t old = atomicCAS(&keys[s], -1, lab);
+              if (old == -1) {
+                claimed = true;
+                break;
+              }
+              if (old == lab) break;
+            }
+            s = (s + 1) & mask;
+          }
+          atomicAdd(&vals[s], (VT)wt);
+        }
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, claimed);
+      int at = 0;
+      if (lane == 0 && bal) at = atomicAdd(&s_nd, __popc(bal));
+      at = __shfl_sync(0xffffffffu, at, 0);
+      if (claimed) slots[at + __popc(bal & lanemask_lt())] = s;
+    }
+    const int64_t ew = seg_total<32>(eCl, 0xffffffffu);
+    if (lane == 0) redE[wid] = (VT)ew;
+    __syncthreads();
+    int64_t eC = 0;
+#pragma unroll
+    for (int x = 0; x < NW; x++) eC += (int64_t)redE[x];
+    const int nd = s_nd;
+    const int64_t kv = g.k[v], aC = g.a[C], m2 = g.m2;
+    ST S = gain_lowest<ST>();
+    int32_t D = INT_MAX;
+    for (int j = tid; j < nd; j += T) {
+      const uint32_t s = slots[j];
+      const int32_t key = __ldcg(&keys[s]);
+      if (up ? key > C : key < C) {
+        const ST x = gain<ST>(m2, kv, (int64_t)__ldcg(&vals[s]), eC, g.a[key], aC);
+        if (better(x, key, S, D)) {
+          S = x;
+          D = key;
+        }
+      }
+    }
+    warp_argmax(S, D);
+    if (lane == 0) {
+      redS[wid] = S;
+      redD[wid] = D;
+    }
+    __syncthreads();
+    if (wid == 0) {
+      S = lane < NW ? redS[lane] : gain_lowest<ST>();
+      D = lane < NW ? redD[lane] : INT_MAX;
+      warp_argmax(S, D);
+      if (lane == 0) prop[i] = slm_choice<ST>(S, D, C, up, m2, kv, eC, aC, g.size[C], n, v);
+    }
+    for (int j = tid; j < nd; j += T) {
+      const uint32_t s = slots[j];
+      keys[s] = -1;
+      vals[s] = 0;
+    }
+    __syncthreads();
+    if (tid == 0) s_nd = 0;
+    __syncthreads();
+  }
+}
+
+// next = L with the proposals of the listed vertices; movers counted.
+__global__ void slm_apply(const int32_t* __restrict__ list, int64_t cnt, const int32_t* __restrict__ prop,
+                          int32_t* __restrict__ next, const int32_t* __restrict__ L,
+                          unsigned long long* __restrict__ moves) {
+  unsigned long long mv = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = list[i], p = prop[i];
+    next[v] = p;
+    mv += p != L[v];
+  }
+  mv = warp_sum(mv);
+  if (lane_id() == 0 && mv) atomicAdd(moves, mv);
+}
+
+// Canonical labels: every community renamed to its smallest member
+// (labels in [0, 2n) in, [0, n) out).
+__global__ void canon_min(int64_t n, const int32_t* __restrict__ next, int32_t* __restrict__ minid) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    atomicMin(&minid[next[v]], (int32_t)v);
+}
+__global__ void canon_apply(int64_t n, const int32_t* __restrict__ next, const int32_t* __restrict__ minid,
+                            int32_t* __restrict__ L) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    L[v] = minid[next[v]];
+}
+
+// sum_i e_{i->C(i)} of labels L (self-loop entries included, as in Eq. 1's
+// double count), a warp per row.
+template <typename W>
+__global__ void slm_in_sum(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                           const W* __restrict__ w, const int32_t* __restrict__ L,
+                           unsigned long long* __restrict__ in) {
+  unsigned long long acc = 0;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < n; u += nw) {
+    const int32_t Lu = L[u];
+    for (int64_t e = rp[u] + lane_id(); e < rp[u + 1]; e += 32)
+      if (L[col[e]] == Lu) acc += (unsigned long long)w[e];
+  }
+  acc = warp_sum(acc);
+  if (lane_id() == 0 && acc) atomicAdd(in, acc);
+}
+
+// sum over labels of a^2 as an unsigned 128-bit integer (lo, hi).
+__global__ void slm_sumsq(const int64_t* __restrict__ a, int64_t n, unsigned long long* __restrict__ lohi) {
+  unsigned __int128 s = 0;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long x = (unsigned long long)a[c];
+    s += (unsigned __int128)x * x;
+  }
+  unsigned long long lo = (unsigned long long)s, hi = (unsigned long long)(s >> 64);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long lo2 = __shfl_xor_sync(0xffffffffu, lo, o), hi2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const unsigned long long nlo = lo + lo2;
+    hi = hi + hi2 + (nlo < lo ? 1ull : 0ull);
+    lo = nlo;
+  }
+  if (lane_id() == 0) add128(&lohi[0], &lohi[1], ((unsigned __int128)hi << 64) | lo);
+}
+
+// Start labels of the next level: the coarse vertex of sub-community s starts
+// in the community of its members, named by the coarse vertex of that
+// community's smallest member.
+__global__ void slm_parent_start(int64_t n, const int32_t* __restrict__ sub, const int32_t* __restrict__ L,
+                                 const int32_t* __restrict__ cid, int32_t* __restrict__ Lc) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    Lc[cid[sub[v]]] = cid[sub[L[v]]];
+}
+
+__global__ void count_heads(int64_t n, const int32_t* __restrict__ x, unsigned long long* __restrict__ out) {
+  unsigned long long c = 0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    c += x[v] == (int32_t)v;
+  c = warp_sum(c);
+  if (lane_id() == 0 && c) atomicAdd(out, c);
+}
+
+constexpr int kSlmQ = 8;            // slm_warp rows: at most 256 entries
+constexpr int64_t kSlmWarpMax = 32 * kSlmQ;
+constexpr int kSlmThreads = 256;
+
+// State and scratch of the SLM local moving on one graph.
+template <typename W>
+struct SlmLevel {
+  dcd_ctx* c;
+  Csr<W> g;
+  const int64_t* k;
+  int64_t m2;
+  Buf<int64_t> a;
+  Buf<int32_t> size, next, minid, prop;
+  Buf<unsigned long long> scal;  // [0] moves, [1] in, [2..3] sum a^2
+  int64_t passes = 0, moves = 0, edges = 0;
+
+  int init() {
+    DCD_TRY(a.alloc(&c->mem, g.n));
+    DCD_TRY(size.alloc(&c->mem, g.n));
+    DCD_TRY(next.alloc(&c->mem, g.n));
+    DCD_TRY(minid.alloc(&c->mem, 2 * g.n));
+    DCD_TRY(prop.alloc(&c->mem, g.n));
+    DCD_TRY(scal.alloc(&c->mem, 4));
+    return DCD_OK;
+  }
+
+  // a, size of labels L (in [0, n))
+  int sums(const int32_t* L) {
+    DCD_TRY_CUDA(cudaMemsetAsync(a.get(), 0, g.n * sizeof(int64_t), c->stream));
+    DCD_TRY_CUDA(cudaMemsetAsync(size.get(), 0, g.n * sizeof(int32_t), c->stream));
+    ::dcd::count_launch(), comm_sums<<<grid_for(g.n, kCsThreads, 2), kCsThreads, 0, c->stream>>>(
+        g.n, L, k, (unsigned long long*)a.get(), size.get());
+    DCD_LAUNCH_CHECK();
+    return DCD_OK;
+  }
+
+  // N = m2 * in - sum a^2 of labels L (Eq. 1 scaled by m2^2), exact
+  int modularity_N(const int32_t* L, i128* N) {
+    const int T = 256;
+    DCD_TRY(sums(L));
+    DCD_TRY_CUDA(cudaMemsetAsync(scal.get() + 1, 0, 3 * sizeof(unsigned long long), c->stream));
+    ::dcd::count_launch(), slm_in_sum<W><<<grid_for(g.n * 32, T), T, 0, c->stream>>>(g.n, g.rp, g.col, g.w, L,
+                                                                                      scal.get() + 1);
+    ::dcd::count_launch(), slm_sumsq<<<grid_for(g.n, T, 4), T, 0, c->stream>>>(a.get(), g.n, scal.get() + 2);
+    DCD_LAUNCH_CHECK();
+    DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch + 20, scal.get() + 1, 3 * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, c->stream));
+    DCD_TRY_CUDA(cudaStreamSynchronize(c->stream));
+    const unsigned long long in = (unsigned long long)c->hscratch[20];
+    const unsigned __int128 sq = ((unsigned __int128)(unsigned long long)c->hscratch[22] << 64) |
+                                 (unsigned long long)c->hscratch[21];
+    *N = (i128)m2 * (i128)in - (i128)sq;
+    return DCD_OK;
+  }
+
+  // The local moving of one level over the vertices of `active` (NULL: all)
+  // with positive degree, from canonical labels L (modified in place).
+  template <typename ST>
+  int run(int32_t* L, const int32_t* parent, const uint8_t* active) {
+    cudaStream_t s = c->stream;
+    DevScalars* d = c->dsc.get();
+    const int T = 256;
+    const int64_t n = g.n;
+    // the vertices to evaluate, split at kSlmWarpMax and kLargeRows entries
+    BinPlan plan;
+    plan.nb = 2;
+    plan.var[0] = kLmWarp256;
+    plan.hi[0] = kSlmWarpMax;
+    plan.var[1] = kLmHub;
+    plan.hi[1] = INT64_MAX;
+    DCD_TRY_CUDA(cudaMemsetAsync(&d->act_deg, 0, 2 * sizeof(int64_t), s));
+    DCD_TRY_CUDA(cudaMemsetAsync(&d->bcnt[0], 0, 3 * kMaxBins * sizeof(int64_t), s));
+    ::dcd::count_launch(), bin_count<<<grid_for(n, T), T, 0, s>>>(g.rp, n, active, d, nullptr, nullptr, plan);
+    DCD_LAUNCH_CHECK();
+    DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+    DCD_TRY_CUDA(cudaStreamSynchronize(s));
+    const int64_t cnt0 = c->hsc->bcnt[0], cnt1 = c->hsc->bcnt[1], maxd1 = c->hsc->bmax[1];
+    const int64_t act_deg = c->hsc->act_deg, total = cnt0 + cnt1;
+    Buf<int32_t> list, cursor;
+    DCD_TRY(list.alloc(&c->mem, total > 0 ? total : 1));
+    DCD_TRY(cursor.alloc(&c->mem, kMaxBins));
+    DCD_TRY_CUDA(cudaMemsetAsync(cursor.get(), 0, kMaxBins * sizeof(int32_t), s));
+    if (total)
+      ::dcd::count_launch(), bin_scatter<<<grid_for(n, T), T, 0, s>>>(g.rp, n, active, d, cursor.get(), list.get(),
+                                                                       nullptr, nullptr, plan);
+    // CTA tables in global memory for the long rows
+    using VT = typename TblVal<ST>::type;
+    const uint32_t tcap = cnt1 ? table_cap(maxd1) : 64;
+    const int64_t by_mem = ((int64_t)512 << 20) / ((int64_t)tcap * (4 + sizeof(VT) + 4));
+    int64_t ctas = cnt1 < 2 * (int64_t)c->sms ? cnt1 : 2 * (int64_t)c->sms;
+    if (ctas > by_mem) ctas = by_mem > 0 ? by_mem : 1;
+    Buf<int32_t> tk;
+    Buf<VT> tv;
+    Buf<uint32_t> tsl;
+    if (cnt1) {
+      DCD_TRY(tk.alloc(&c->mem, (size_t)ctas * tcap));
+      DCD_TRY(tv.alloc(&c->mem, (size_t)ctas * tcap));
+      DCD_TRY(tsl.alloc(&c->mem, (size_t)ctas * tcap));
+    }
+    constexpr size_t smem = (size_t)8 * row_tbl_bytes<kSlmWarpMax, VT>();
+    DCD_TRY_CUDA(cudaFuncSetAttribute(slm_warp<W, ST, kSlmQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LV<W> lv{g.rp, g.col, g.w, k, L, a.get(), size.get(), m2};
+    i128 N_old = 0;
+    DCD_TRY(modularity_N(L, &N_old));
+    int64_t cycle_moves = 0;
+    while (passes < c->cfg.max_iters) {
+      const int up = (int)(passes & 1);
+      DCD_TRY(sums(L));
+      if (cnt0)
+        ::dcd::count_launch(), slm_warp<W, ST, kSlmQ><<<grid_for(cnt0 * 32, T), T, smem, s>>>(
+            lv, parent, up, n, list.get(), cnt0, prop.get());
+      if (cnt1)
+        ::dcd::count_launch(), slm_cta<W, ST><<<(unsigned)ctas, kSlmThreads, 0, s>>>(
+            lv, parent, up, n, list.get() + cnt0, cnt1, prop.get() + cnt0, tk.get(), tv.get(), tsl.get(), tcap);
+      DCD_LAUNCH_CHECK();
+      DCD_TRY_CUDA(cudaMemcpyAsync(next.get(), L, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+      DCD_TRY_CUDA(cudaMemsetAsync(scal.get(), 0, sizeof(unsigned long long), s));
+      if (total)
+        ::dcd::count_launch(), slm_apply<<<grid_for(total, T), T, 0, s>>>(list.get(), total, prop.get(), next.get(), L,
+                                                                          scal.get());
+      ::dcd::count_launch(), fill_i32<<<grid_for(2 * n, T), T, 0, s>>>(minid.get(), 2 * n, INT32_MAX);
+      ::dcd::count_launch(), canon_min<<<grid_for(n, T), T, 0, s>>>(n, next.get(), minid.get());
+      ::dcd::count_launch(), canon_apply<<<grid_for(n, T), T, 0, s>>>(n, next.get(), minid.get(), L);
+      DCD_LAUNCH_CHECK();
+      DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch + 24, scal.get(), sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                   s));
+      DCD_TRY_CUDA(cudaStreamSynchronize(s));
+      const int64_t mv = c->hscratch[24];
+      passes++;
+      edges += act_deg;
+      moves += mv;
+      cycle_moves += mv;
+      if (!up) continue;
+      if (cycle_moves == 0) break;
+      cycle_moves = 0;
+      i128 N_new = 0;
+      DCD_TRY(modularity_N(L, &N_new));
+      if (h_below_tau(N_new - N_old, N_old, c->cfg.tau_inv)) break;
+      N_old = N_new;
+    }
+    return DCD_OK;
+  }
+};
+
+template <typename W>
+int slm_level(dcd_ctx* c, const Csr<W>& g, const int64_t* k, int64_t m2, int32_t* L, const int32_t* parent,
+              const uint8_t* active, int64_t* passes, int64_t* moves, int64_t* edges) {
+  SlmLevel<W> lv{c, g, k, m2};
+  DCD_TRY(lv.init());
+  if (m2 >= ((int64_t)1 << 31)) DCD_TRY(lv.template run<i128>(L, parent, active));
+  else DCD_TRY(lv.template run<long long>(L, parent, active));
+  *passes = lv.passes;
+  *moves = lv.moves;
+  if (edges) *edges = lv.edges;
+  return DCD_OK;
+}
+
+template <typename W>
+int slm_N(dcd_ctx* c, const Csr<W>& g, const int64_t* k, int64_t m2, const int32_t* L, i128* N) {
+  SlmLevel<W> lv{c, g, k, m2};
+  DCD_TRY(lv.init());
+  return lv.modularity_N(L, N);
+}
+
+}  // namespace
+
+// Multi-level SLM from level-0 labels (canonical or not), level-0 active
+// flags (NULL = all), k and 2m of G_t (one graph a context).  Canonical
+// labels to out_labels; stats as run_louvain's.
+int run_slm(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint8_t* active0, Buf<int64_t>& k0,
+            int32_t* out_labels, dcd_step_stats* st) {
+  cudaStream_t s = c->stream;
+  const int T = 256;
+  const int64_t n0 = g0.n;
+  const int64_t m2 = c->hgs[0].m2;
+  Buf<int32_t> comp, L, minid;
+  DCD_TRY(comp.alloc(&c->mem, n0));
+  DCD_TRY(L.alloc(&c->mem, n0));
+  DCD_TRY(minid.alloc(&c->mem, 2 * n0));
+  ::dcd::count_launch(), fill_iota<<<grid_for(n0, T), T, 0, s>>>(comp.get(), n0);
+  ::dcd::count_launch(), fill_i32<<<grid_for(2 * n0, T), T, 0, s>>>(minid.get(), 2 * n0, INT32_MAX);
+  ::dcd::count_launch(), canon_min<<<grid_for(n0, T), T, 0, s>>>(n0, labels0, minid.get());
+  ::dcd::count_launch(), canon_apply<<<grid_for(n0, T), T, 0, s>>>(n0, labels0, minid.get(), L.get());
+  DCD_LAUNCH_CHECK();
+  i128 N_start = 0, N_end = 0;
+  DCD_TRY(slm_N<int32_t>(c, g0, k0.get(), m2, L.get(), &N_start));
+  int64_t level = 0, iters_total = 0, iters0 = 0, moves_total = 0, edges_total = 0, refine_iters = 0,
+          refine_moves = 0;
+  float ms_lm = 0.f, ms_coarsen = 0.f;
+  CoarseGraph cg[2];
+  Buf<int64_t> kc[2];
+  Buf<int32_t> Lc[2];
+  int which = 0;
+  const Csr<int64_t>* gc = nullptr;
+  int32_t* Lcur = L.get();
+  const int64_t* kcur = k0.get();
+  const uint8_t* active = active0;
+  int64_t nv = n0;
+  for (;;) {
+    DCD_TRY_CUDA(cudaEventRecord(c->ev[2], s));
+    int64_t it = 0, mv = 0, ed = 0, rit = 0, rmv = 0;
+    Buf<int32_t> sub;
+    DCD_TRY(sub.alloc(&c->mem, nv));
+    if (level == 0) {
+      DCD_TRY(slm_level<int32_t>(c, g0, kcur, m2, Lcur, nullptr, active, &it, &mv, &ed));
+      DCD_TRY(slm_N<int32_t>(c, g0, kcur, m2, Lcur, &N_end));
+      ::dcd::count_launch(), fill_iota<<<grid_for(nv, T), T, 0, s>>>(sub.get(), nv);
+      DCD_TRY(slm_level<int32_t>(c, g0, kcur, m2, sub.get(), Lcur, nullptr, &rit, &rmv, nullptr));
+    } else {
+      DCD_TRY(slm_level<int64_t>(c, *gc, kcur, m2, Lcur, nullptr, nullptr, &it, &mv, &ed));
+      DCD_TRY(slm_N<int64_t>(c, *gc, kcur, m2, Lcur, &N_end));
+      ::dcd::count_launch(), fill_iota<<<grid_for(nv, T), T, 0, s>>>(sub.get(), nv);
+      DCD_TRY(slm_level<int64_t>(c, *gc, kcur, m2, sub.get(), Lcur, nullptr, &rit, &rmv, nullptr));
+    }
+    DCD_TRY_CUDA(cudaEventRecord(c->ev[3], s));
+    iters_total += it;
+    if (level == 0) iters0 = it;
+    moves_total += mv;
+    edges_total += ed;
+    refine_iters += rit;
+    refine_moves += rmv;
+    // sub-communities (canonical: one head each)
+    Buf<unsigned long long> heads;
+    DCD_TRY(heads.alloc(&c->mem, 1));
+    DCD_TRY_CUDA(cudaMemsetAsync(heads.get(), 0, sizeof(unsigned long long), s));
+    ::dcd::count_launch(), count_heads<<<grid_for(nv, T), T, 0, s>>>(nv, sub.get(), heads.get());
+    DCD_LAUNCH_CHECK();
+    DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch + 25, heads.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    DCD_TRY_CUDA(cudaStreamSynchronize(s));
+    float t1 = 0.f;
+    cudaEventElapsedTime(&t1, c->ev[2], c->ev[3]);
+    ms_lm += t1;
+    const int64_t ns = c->hscratch[25];
+    level++;
+    const bool stop = ns == nv || (level >= 2 && h_below_tau(N_end - N_start, N_start, c->cfg.tau_inv)) ||
+                      level >= c->cfg.max_levels;
+    if (stop) break;
+    // aggregation by the sub-communities
+    DCD_TRY_CUDA(cudaEventRecord(c->ev[5], s));
+    Buf<int32_t> cid;
+    int64_t nc = 0;
+    const int nx = which ^ 1;
+    if (level == 1) {
+      DCD_TRY(used_labels<int32_t>(c, g0, sub.get(), cid, &nc, nullptr, nullptr));
+      DCD_TRY(coarsen<int32_t>(c, g0, sub.get(), cid.get(), nc, &cg[nx]));
+    } else {
+      DCD_TRY(used_labels<int64_t>(c, *gc, sub.get(), cid, &nc, nullptr, nullptr));
+      DCD_TRY(coarsen<int64_t>(c, *gc, sub.get(), cid.get(), nc, &cg[nx]));
+    }
+    DCD_TRY(kc[nx].alloc(&c->mem, nc));
+    DCD_TRY(Lc[nx].alloc(&c->mem, nc));
+    {
+      // coarse k = sum of k over a sub-community
+      Buf<int64_t> asub;
+      Buf<int32_t> ssub;
+      DCD_TRY(asub.alloc(&c->mem, nv));
+      DCD_TRY(ssub.alloc(&c->mem, nv));
+      DCD_TRY(community_sums(c, nv, sub.get(), kcur, asub.get(), ssub.get()));
+      ::dcd::count_launch(), coarse_k<<<grid_for(nv, T), T, 0, s>>>(nv, cid.get(), asub.get(), kc[nx].get());
+    }
+    ::dcd::count_launch(), compose<<<grid_for(n0, T), T, 0, s>>>(n0, comp.get(), sub.get(), cid.get());
+    ::dcd::count_launch(), slm_parent_start<<<grid_for(nv, T), T, 0, s>>>(nv, sub.get(), Lcur, cid.get(),
+                                                                           Lc[nx].get());
+    DCD_LAUNCH_CHECK();
+    DCD_TRY_CUDA(cudaEventRecord(c->ev[6], s));
+    DCD_TRY_CUDA(cudaEventSynchronize(c->ev[6]));
+    float tc = 0.f;
+    cudaEventElapsedTime(&tc, c->ev[5], c->ev[6]);
+    ms_coarsen += tc;
+    cg[which].rp.reset();
+    cg[which].col.reset();
+    cg[which].w.reset();
+    kc[which].reset();
+    Lc[which].reset();
+    which = nx;
+    gc = &cg[which].view;
+    Lcur = Lc[which].get();
+    kcur = kc[which].get();
+    nv = nc;
+    active = nullptr;
+    N_start = N_end;
+  }
+  // compose + canonical labels (smallest member id)
+  DCD_TRY_CUDA(cudaEventRecord(c->ev[7], s));
+  {
+    Buf<int32_t> mid;
+    DCD_TRY(mid.alloc(&c->mem, nv));
+    ::dcd::count_launch(), fill_i32<<<grid_for(nv, T), T, 0, s>>>(mid.get(), nv, INT32_MAX);
+    ::dcd::count_launch(), final_min<<<grid_for(n0, T), T, 0, s>>>(n0, comp.get(), Lcur, mid.get());
+    ::dcd::count_launch(), gs_reset_nc<<<1, 128, 0, s>>>(c->gs.get(), 1);
+    ::dcd::count_launch(), final_labels<<<grid_for(n0, T), T, 0, s>>>(n0, comp.get(), Lcur, mid.get(), out_labels,
+                                                                       nullptr, c->gs.get());
+    DCD_LAUNCH_CHECK();
+    DCD_TRY_CUDA(cudaEventRecord(c->ev[8], s));
+    DCD_TRY_CUDA(cudaMemcpyAsync(c->hgs, c->gs.get(), sizeof(GraphState), cudaMemcpyDeviceToHost, s));
+    DCD_TRY_CUDA(cudaStreamSynchronize(s));
+  }
+  float tf = 0.f;
+  cudaEventElapsedTime(&tf, c->ev[7], c->ev[8]);
+  if (st) {
+    st->levels = level;
+    st->iters_total = iters_total;
+    st->iters_level0 = iters0;
+    st->moves_total = moves_total;
+    st->communities = c->hgs[0].ncomm;
+    st->n_lo = (int64_t)(unsigned long long)N_end;
+    st->n_hi = (int64_t)(unsigned long long)((unsigned __int128)N_end >> 64);
+    st->m2 = m2;
+    st->q = m2 == 0 ? 0.0 : (double)N_end / ((double)m2 * (double)m2);
+    st->edges_scanned = edges_total;
+    st->verts_scanned = 0;
+    st->refine_iters = refine_iters;
+    st->refine_moves = refine_moves;
+    st->ms_local_move = ms_lm;
     st->ms_coarsen = ms_coarsen;
     st->ms_finish = tf;
   }

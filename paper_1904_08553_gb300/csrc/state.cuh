@@ -36,7 +36,11 @@ struct DevScalars {
   int64_t bdeg[12];  // sum of their degrees
   int64_t bmax[12];  // largest degree in the bin
   int32_t pass_id;   // local-move passes started in this update (moved-in-pass marks)
-  int32_t pad2;
+  int32_t level_passes;  // passes of the level running on the device
+  unsigned long long stamp[2];  // globaltimer at the start of a pass and after its evaluation
+  unsigned long long t_eval_ns, t_apply_ns;  // a level's evaluation and apply time, summed over its passes
+  int32_t loop_err;  // the device pass loop hit its hard cap (cannot happen: the stop rule ends it first)
+  int32_t pad3;
 };
 
 // Per-graph state of one update.  A context holds G graphs on disjoint vertex
@@ -52,6 +56,7 @@ struct GraphState {
   int64_t nc;          // labels in use at the end of the level
   int64_t nv;          // vertices of the graph at this level
   int64_t ncomm;       // communities at the end of the update
+  int64_t moves_level; // movers summed over the passes of the level
   int32_t moves;       // movers of the last pass
   int32_t running;     // the graph's pass loop at this level goes on
   int32_t passes;      // passes at this level
@@ -304,6 +309,11 @@ int screen_batch(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* labels0, cons
 int run_louvain(dcd_ctx* c, const Csr<int32_t>& g, int32_t* labels0, const uint8_t* active0,
                 Buf<int64_t>& k, int32_t* out_labels, dcd_step_stats* st, int32_t* level0_out = nullptr,
                 dcd_step_stats* per_graph = nullptr, const int64_t* a0 = nullptr, const int32_t* size0 = nullptr);
+
+// louvain.cu: multi-level smart local moving (dSLM) from level-0 labels and
+// level-0 active flags (NULL = all), k and 2m of G_t (one graph a context).
+int run_slm(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint8_t* active0, Buf<int64_t>& k0,
+            int32_t* out_labels, dcd_step_stats* st);
 
 // louvain.cu: statistics of the learned screen's pool (mask over vertices):
 // the local-move evaluation of every pool vertex of positive degree, without

@@ -22,6 +22,7 @@ LIB_PATH = _PKG / "libdcd.so"
 DCD_OK, DCD_EINVAL, DCD_ENOMEM, DCD_ECUDA, DCD_ESTATE, DCD_EOVERFLOW, DCD_ETIMEOUT, DCD_EIO = (
     0, -1, -2, -3, -4, -5, -6, -7)
 MODE_STATIC, MODE_BASE, MODE_DELTA, MODE_GIVEN_R, MODE_LEARNED = 0, 1, 2, 3, 4
+ALG_LOUVAIN, ALG_SLM = 0, 1
 
 EXPORTED = [
     "dcd_config_default", "dcd_create", "dcd_destroy", "dcd_apply_batch", "dcd_apply_batch_device",
@@ -58,7 +59,7 @@ class Edge(ctypes.Structure):
 
 class Config(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("max_levels", ctypes.c_int32),
-                ("tau_inv", ctypes.c_int32), ("reserved", ctypes.c_int32 * 12)]
+                ("tau_inv", ctypes.c_int32), ("alg", ctypes.c_int32), ("reserved", ctypes.c_int32 * 11)]
 
 
 _STAT_I64 = ["t", "n", "nnz", "m2", "r_size", "levels", "iters_total", "iters_level0", "moves_total",
@@ -78,7 +79,9 @@ class StepStats(ctypes.Structure):
                                                             ("ms_local_move0", ctypes.c_float),
                                                             ("reserved_g", ctypes.c_float),
                                                             ("edges_level0", ctypes.c_int64),
-                                                            ("verts_level0", ctypes.c_int64)])
+                                                            ("verts_level0", ctypes.c_int64),
+                                                            ("refine_iters", ctypes.c_int64),
+                                                            ("refine_moves", ctypes.c_int64)])
 
     @property
     def N(self) -> int:
@@ -411,9 +414,10 @@ class Context(_Bins):
     """One dynamic graph on vertices [0, n) (dcd_ctx)."""
 
     def __init__(self, n: int, mode: int = MODE_DELTA, stream=None, max_iters: int = 500,
-                 max_levels: int = 64, tau_inv: int = 1_000_000):
+                 max_levels: int = 64, tau_inv: int = 1_000_000, alg: int = ALG_LOUVAIN):
         cfg = dcd_config_default()
         cfg.mode, cfg.max_iters, cfg.max_levels, cfg.tau_inv = mode, max_iters, max_levels, tau_inv
+        cfg.alg = alg
         self.n = int(n)
         self._h = dcd_create(self.n, cfg, stream)
 

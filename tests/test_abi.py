@@ -51,8 +51,8 @@ def test_status_text_and_defaults(libdcd):
 def test_struct_layouts_match_header(libdcd):
     assert ctypes.sizeof(libdcd.Edge) == 12
     assert ctypes.sizeof(libdcd.Config) == 64
-    # 14 int64 + double + 6 int64 + double + 16 float + 8 int64 + 2 float + 2 int64
-    assert ctypes.sizeof(libdcd.StepStats) == 14 * 8 + 8 + 6 * 8 + 8 + 16 * 4 + 8 * 8 + 2 * 4 + 2 * 8
+    # 14 int64 + double + 6 int64 + double + 16 float + 8 int64 + 2 float + 4 int64
+    assert ctypes.sizeof(libdcd.StepStats) == 14 * 8 + 8 + 6 * 8 + 8 + 16 * 4 + 8 * 8 + 2 * 4 + 4 * 8
 
 
 def test_create_rejects_bad_n_before_touching_the_device(libdcd):
@@ -62,3 +62,16 @@ def test_create_rejects_bad_n_before_touching_the_device(libdcd):
     assert L.dcd_create(-5, None, None, ctypes.byref(h)) == libdcd.DCD_EINVAL
     assert L.dcd_create(1 << 31, None, None, ctypes.byref(h)) == libdcd.DCD_EINVAL
     assert L.dcd_destroy(None) == 0
+
+
+def test_create_rejects_bad_configurations_before_touching_the_device(libdcd):
+    h = ctypes.c_void_p()
+    L = libdcd.lib()
+    cfg = libdcd.dcd_config_default()
+    cfg.alg = 7  # unknown host method
+    assert L.dcd_create(10, ctypes.byref(cfg), None, ctypes.byref(h)) == libdcd.DCD_EINVAL
+    cfg.alg = libdcd.ALG_SLM  # smart local moving names n + v: n must stay below 2^30
+    assert L.dcd_create(1 << 30, ctypes.byref(cfg), None, ctypes.byref(h)) == libdcd.DCD_EINVAL
+    sizes = (ctypes.c_int64 * 2)(10, 20)
+    g = ctypes.c_void_p()
+    assert L.dcd_group_create(2, sizes, ctypes.byref(cfg), None, ctypes.byref(g)) == libdcd.DCD_EINVAL
