@@ -389,6 +389,7 @@ int dcd_destroy(dcd_ctx* c) {
     c->ins.reset(); c->del.reset(); c->dsc.reset(); c->iota.reset(); c->rset_nx.reset();
     c->feat_X.reset(); c->feat_y.reset(); c->feat_v.reset(); c->level0.reset();
     c->gs.reset(); c->goff_d.reset(); c->gid.reset();
+    c->in_prev.reset(); c->in_next.reset();
     if (c->mem.arena) cudaFreeAsync(c->mem.arena, c->stream);
     c->mem.arena = nullptr;
     cudaStreamSynchronize(c->stream);
@@ -485,6 +486,10 @@ static std::vector<BinPlan> candidate_plans() {
 // Times one local-move evaluation of every vertex of the current graph under
 // the current labels for each candidate plan and keeps the fastest.  Every
 // plan gives the same proposals; only the time differs.
+__global__ void save_in(const GraphState* __restrict__ gs, int G, int64_t* __restrict__ out) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) out[g] = gs[g].in_cur;
+}
+
 int autotune_impl(dcd_ctx* c, int32_t reps, float* best_ms) {
   if (c->t == 0 || reps < 1) return DCD_ESTATE;
   const std::vector<BinPlan> cands = candidate_plans();
@@ -512,7 +517,7 @@ int dcd::update_impl(dcd_ctx* c, dcd_step_stats* st, dcd_step_stats* per_graph, 
   const int mode = first ? DCD_MODE_STATIC : c->mode;
   if (mode == DCD_MODE_GIVEN_R && !c->has_rgiven) return DCD_ESTATE;
   // the learned screen and its training data are defined on Louvain's level 0
-  if (c->cfg.alg == DCD_ALG_SLM && (mode == DCD_MODE_LEARNED || c->collect)) return DCD_ESTATE;
+  if (c->cfg.alg == DCD_ALG_SLM && (mode == DCD_MODE_LEARNED || (c->collect && !first))) return DCD_ESTATE;
   trace("update: enter");
   DCD_TRY_CUDA(cudaEventRecord(c->ev[0], s));
   DCD_TRY_CUDA(cudaMemsetAsync(d, 0, sizeof(DevScalars), s));
@@ -524,7 +529,7 @@ int dcd::update_impl(dcd_ctx* c, dcd_step_stats* st, dcd_step_stats* per_graph, 
   DCD_TRY_CUDA(cudaMemcpyAsync(L0.get(), src_labels, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
 
   MergeOut mo;
-  DCD_TRY(merge_batch(c, src_labels, &mo));
+  DCD_TRY(merge_batch(c, src_labels, mode == DCD_MODE_STATIC, &mo));
   const int nxt = 1 - c->cur;
   DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch + 8, c->rp[nxt].get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
@@ -635,9 +640,25 @@ int dcd::update_impl(dcd_ctx* c, dcd_step_stats* st, dcd_step_stats* per_graph, 
     st->pool = (learned || collect) ? c->feat_n : 0;
   }
 
+  // sum_i e_{i->C(i)} of C_t on G_t, kept for the next merge: Louvain's
+  // tracked value, except after a judged learned step (its device state then
+  // holds the second run) and after SLM (which does not track it)
+  const bool keep_in = c->cfg.alg == DCD_ALG_LOUVAIN && !(learned && c->judge);
+  if (keep_in) {
+    DCD_TRY(c->in_next.ensure(&c->mem, c->G));
+    ::dcd::count_launch(), save_in<<<cdiv(c->G, 128), 128, 0, s>>>(c->gs.get(), c->G, c->in_next.get());
+    DCD_LAUNCH_CHECK();
+  }
+
   if (finish) DCD_TRY(finish(c, user));
 
   // ---- commit ----
+  if (keep_in) {
+    std::swap(c->in_prev.p, c->in_next.p);
+    std::swap(c->in_prev.n, c->in_next.n);
+    std::swap(c->in_prev.mem, c->in_next.mem);
+  }
+  c->in_valid = keep_in;
   c->cur = nxt;
   c->nnz = nnz_new;
   std::swap(c->labels.p, c->labels_nx.p);
@@ -722,6 +743,7 @@ int dcd_set_labels(dcd_ctx* c, const int32_t* labels) {
   for (int64_t v = 0; v < c->n; v++)
     if (labels[v] < 0 || labels[v] >= c->n) return DCD_EINVAL;
   DCD_SCOPE(c);
+  c->in_valid = false;  // the kept sum_i e_{i->C(i)} belongs to the replaced labels
   DCD_TRY_CUDA(cudaMemcpyAsync(c->labels.get(), labels, c->n * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
   DCD_TRY_CUDA(cudaStreamSynchronize(c->stream));
   if (c->t == 0) c->t = 1;

@@ -1082,34 +1082,53 @@ __global__ void __launch_bounds__(kEmitThreads) emit_coarse(int64_t n, int64_t m
 // add straight into the matrix; two row-per-warp passes then count and write
 // the non-zero cells in column order.  No key list, no sort.
 constexpr int64_t kDenseNc = 4096;
+constexpr size_t kDenseSmem = 96 * 1024;  // the CTA copy of the matrix (emit_dense<..., true>)
 
-template <typename W, typename VT>
+// SMEM: the CTA first sums into its own copy of the matrix in shared memory
+// (nc x nc cells, for the smallest nc) and adds its non-zero cells into the
+// global matrix once at the end.  A level-0 matrix receives most of its
+// weight in the nc diagonal cells, and without the CTA copy every row's
+// chunks would queue on those few L2 lines.
+template <typename W, typename VT, bool SMEM>
 __global__ void __launch_bounds__(kEmitThreads) emit_dense(int64_t n, int64_t m, const int64_t* __restrict__ rp,
                                                            const int32_t* __restrict__ col,
                                                            const W* __restrict__ w,
                                                            const int32_t* __restrict__ ccid, uint32_t nc,
                                                            int64_t per_warp, VT* __restrict__ dense) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  VT* local = reinterpret_cast<VT*>(smem);
+  const uint32_t cells = nc * nc;
+  if (SMEM) {
+    for (uint32_t x = threadIdx.x; x < cells; x += blockDim.x) local[x] = 0;
+    __syncthreads();
+  }
   const int lane = lane_id();
   const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t W0 = gw * per_warp, W1 = W0 + per_warp < m ? W0 + per_warp : m;
-  if (W0 >= W1) return;
-  RowWalk rw;
-  rw.start(rp, n, W0);
-  for (int64_t c0 = W0; c0 < W1; c0 += 32) {
-    const int64_t e = c0 + lane;
-    const bool valid = e < W1;
-    const int64_t row = rw.row(rp, n, c0, valid);
-    uint32_t key = 0xffffffffu;
-    W wt = W(0);
-    if (valid) {
-      key = (uint32_t)ccid[row] * nc + (uint32_t)ccid[col[e]];
-      wt = w[e];
+  if (W0 < W1) {
+    RowWalk rw;
+    rw.start(rp, n, W0);
+    for (int64_t c0 = W0; c0 < W1; c0 += 32) {
+      const int64_t e = c0 + lane;
+      const bool valid = e < W1;
+      const int64_t row = rw.row(rp, n, c0, valid);
+      uint32_t key = 0xffffffffu;
+      W wt = W(0);
+      if (valid) {
+        key = (uint32_t)ccid[row] * nc + (uint32_t)ccid[col[e]];
+        wt = w[e];
+      }
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      // VT = 32 bits: 2m < 2^31 bounds every sum of weights
+      const VT sum = sizeof(VT) == 4 ? (VT)__reduce_add_sync(peers, (unsigned)wt)
+                                     : (VT)group_sum_exact(peers, (int64_t)wt);
+      if (valid && (int)(__ffs(peers) - 1) == lane) atomicAdd(SMEM ? &local[key] : &dense[key], sum);
     }
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
-    // VT = 32 bits: 2m < 2^31 bounds every sum of weights
-    const VT sum = sizeof(VT) == 4 ? (VT)__reduce_add_sync(peers, (unsigned)wt)
-                                   : (VT)group_sum_exact(peers, (int64_t)wt);
-    if (valid && (int)(__ffs(peers) - 1) == lane) atomicAdd(&dense[key], sum);
+  }
+  if (SMEM) {
+    __syncthreads();
+    for (uint32_t x = threadIdx.x; x < cells; x += blockDim.x)
+      if (local[x]) atomicAdd(&dense[x], local[x]);
   }
 }
 
@@ -1731,10 +1750,21 @@ int coarsen_dense(dcd_ctx* c, const Csr<W>& g, const int32_t* ccid, int64_t nc, 
   DCD_TRY(stmp.alloc(&c->mem, scan_tmp_count(nc + 1) + 1));
   DCD_TRY_CUDA(cudaMemsetAsync(dense.get(), 0, nc * nc * sizeof(VT), s));
   if (m0 > 0) {
-    const int grid = wave_grid(emit_dense<W, VT>, cdiv(m0, 32) * 32, kEmitThreads);
-    const int64_t per_warp = cdiv(cdiv(m0, (int64_t)grid * (kEmitThreads / 32)), 32) * 32;
-    ::dcd::count_launch(), emit_dense<W, VT><<<grid, kEmitThreads, 0, s>>>(g.n, m0, g.rp, g.col, g.w, ccid,
-                                                                            (uint32_t)nc, per_warp, dense.get());
+    // a CTA copy of the matrix when it fits in shared memory (two CTAs an SM)
+    const size_t msm = (size_t)nc * nc * sizeof(VT);
+    if (msm <= kDenseSmem) {
+      DCD_TRY_CUDA(cudaFuncSetAttribute(emit_dense<W, VT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kDenseSmem));
+      const int grid = wave_grid(emit_dense<W, VT, true>, cdiv(m0, 32) * 32, kEmitThreads, msm);
+      const int64_t per_warp = cdiv(cdiv(m0, (int64_t)grid * (kEmitThreads / 32)), 32) * 32;
+      ::dcd::count_launch(), emit_dense<W, VT, true><<<grid, kEmitThreads, msm, s>>>(
+          g.n, m0, g.rp, g.col, g.w, ccid, (uint32_t)nc, per_warp, dense.get());
+    } else {
+      const int grid = wave_grid(emit_dense<W, VT, false>, cdiv(m0, 32) * 32, kEmitThreads);
+      const int64_t per_warp = cdiv(cdiv(m0, (int64_t)grid * (kEmitThreads / 32)), 32) * 32;
+      ::dcd::count_launch(), emit_dense<W, VT, false><<<grid, kEmitThreads, 0, s>>>(
+          g.n, m0, g.rp, g.col, g.w, ccid, (uint32_t)nc, per_warp, dense.get());
+    }
     DCD_LAUNCH_CHECK();
   }
   DCD_TRY(out->rp.alloc(&c->mem, nc + 1));

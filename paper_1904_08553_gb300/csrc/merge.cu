@@ -217,31 +217,77 @@ __device__ __forceinline__ int64_t lower_bound_u64(const uint64_t* __restrict__ 
 }
 
 // Per pair: was the edge in G_{t-1}; does the merge add or remove a row entry.
+// With lab0 (C_{t-1}) given, also the change the pair makes to
+// sum_i e_{i->C(i)} under C_{t-1}: its new weight minus its old one when both
+// ends share a community, added into in_delta[graph].
 __global__ void pair_status(const uint64_t* __restrict__ pkey, const int64_t* __restrict__ pw,
                             uint8_t* __restrict__ pflag, int64_t P, const int64_t* __restrict__ rp,
                             const int32_t* __restrict__ col, const int32_t* __restrict__ w,
                             int32_t* __restrict__ added, int32_t* __restrict__ removed,
-                            int64_t* __restrict__ src_cnt, uint32_t* __restrict__ err) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
-    uint64_t k = pkey[p];
-    int32_t u = (int32_t)(k >> 32), v = (int32_t)(k & 0xffffffffu);
-    int64_t b = rp[u], e = rp[u + 1];
-    int64_t pos = lower_bound_i32(col, b, e, v);
-    bool present = pos < e && col[pos] == v;
-    uint8_t f = pflag[p];
-    bool isins = f & kPairIns, isdel = f & kPairDel;
-    bool add = isins && !present;
-    bool rem = !isins && isdel && present;
-    if (isins) {
-      int64_t nw = (present && !isdel) ? (int64_t)w[pos] + pw[p] : pw[p];
-      if (nw > INT32_MAX) atomicOr(err, kErrOverflow);
+                            int64_t* __restrict__ src_cnt, uint32_t* __restrict__ err,
+                            const int32_t* __restrict__ lab0, const int32_t* __restrict__ gid,
+                            int64_t* __restrict__ in_delta) {
+  // warp-uniform trip count: the lanes of a warp sum their in_delta changes
+  // per graph before one lane adds them (most pairs of a step add into the
+  // same word)
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31u); p0 < P; p0 += stride) {
+    const int64_t p = p0 + lane_id();
+    int64_t dlt = 0;
+    int32_t graph = 0, src = -1;
+    if (p < P) {
+      uint64_t k = pkey[p];
+      int32_t u = (int32_t)(k >> 32), v = (int32_t)(k & 0xffffffffu);
+      int64_t b = rp[u], e = rp[u + 1];
+      int64_t pos = lower_bound_i32(col, b, e, v);
+      bool present = pos < e && col[pos] == v;
+      uint8_t f = pflag[p];
+      bool isins = f & kPairIns, isdel = f & kPairDel;
+      bool add = isins && !present;
+      bool rem = !isins && isdel && present;
+      if (isins) {
+        int64_t nw = (present && !isdel) ? (int64_t)w[pos] + pw[p] : pw[p];
+        if (nw > INT32_MAX) atomicOr(err, kErrOverflow);
+      }
+      if (lab0 && lab0[u] == lab0[v]) {
+        // deletes remove the whole edge first, then inserts add their weight
+        const int64_t w_old = present ? (int64_t)w[pos] : 0;
+        const int64_t w_new = ((present && !isdel) ? w_old : 0) + (isins ? pw[p] : 0);
+        dlt = w_new - w_old;
+        graph = graph_of(gid, u);
+      }
+      f |= (present ? kPairPresent : 0) | (add ? kPairAdded : 0) | (rem ? kPairRemoved : 0);
+      pflag[p] = f;
+      added[p] = add;
+      removed[p] = rem;
+      src = u;
     }
-    f |= (present ? kPairPresent : 0) | (add ? kPairAdded : 0) | (rem ? kPairRemoved : 0);
-    pflag[p] = f;
-    added[p] = add;
-    removed[p] = rem;
-    atomicAdd((unsigned long long*)&src_cnt[u], 1ull);
+    {
+      // pairs are sorted by source: one add per run of equal sources
+      const unsigned same = __match_any_sync(0xffffffffu, src);
+      if (src >= 0 && (int)(__ffs(same) - 1) == (int)lane_id())
+        atomicAdd((unsigned long long*)&src_cnt[src], (unsigned long long)__popc(same));
+    }
+    if (lab0) {
+      const unsigned peers = __match_any_sync(0xffffffffu, graph);
+      // two's-complement sum of the peers' changes, 16 bits at a time
+      const unsigned long long x = (unsigned long long)dlt;
+      unsigned long long sum = 0;
+#pragma unroll
+      for (int q = 0; q < 4; q++)
+        sum += (unsigned long long)__reduce_add_sync(peers, (unsigned)(x >> (16 * q)) & 0xffffu) << (16 * q);
+      if (sum != 0 && (int)(__ffs(peers) - 1) == (int)lane_id())
+        atomicAdd((unsigned long long*)&in_delta[graph], sum);
+    }
   }
+}
+
+// sum_i e_{i->C(i)} under C_{t-1} on G_t from its value on G_{t-1} (kept by
+// the previous update) and the batch's change.
+__global__ void seed_in(GraphState* __restrict__ gs, int G, const int64_t* __restrict__ in_prev,
+                        const int64_t* __restrict__ in_delta) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x)
+    gs[g].in_cur += in_prev[g] + in_delta[g];
 }
 
 // Rows longer than kLongRow entries (old or new) are merged by a CTA each
@@ -297,7 +343,7 @@ __global__ void __launch_bounds__(THREADS) merge_long(
     const int64_t ob = rp_o[u], oe = rp_o[u + 1], nb = rp_n[u];
     const int64_t p0 = pair_ptr[u], p1 = pair_ptr[u + 1];
     const int64_t np = p1 - p0;
-    const int32_t Lu = lab[u];
+    const int32_t Lu = lab ? lab[u] : 0;
     const int32_t rA0 = pA[p0], rR0 = pR[p0];  // prefix arrays hold P + 1 entries
     const bool staged = np <= kLongPairs;
     if (staged) {
@@ -339,7 +385,7 @@ __global__ void __launch_bounds__(THREADS) merge_long(
       col_n[pos] = c;
       w_n[pos] = (int32_t)wv;
       ks += wv;
-      if (lab[c] == Lu) is += wv;
+      if (lab && lab[c] == Lu) is += wv;
     }
     for (int64_t q = p0 + tid; q < p1; q += THREADS) {
       if (!(pflag[q] & kPairAdded)) continue;
@@ -350,7 +396,7 @@ __global__ void __launch_bounds__(THREADS) merge_long(
       col_n[pos] = c;
       w_n[pos] = (int32_t)wv;
       ks += wv;
-      if (lab[c] == Lu) is += wv;
+      if (lab && lab[c] == Lu) is += wv;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -412,14 +458,14 @@ __global__ void __launch_bounds__(256, 5) merge_rows(
       // idle group in the warp's last round, or a long row (merge_long)
     } else if (pair_ptr[u] == pair_ptr[u + 1]) {
       int64_t ob = rp_o[u], oe = rp_o[u + 1], nb = rp_n[u];
-      int32_t Lu = lab[u];
+      int32_t Lu = lab ? lab[u] : 0;
       for (int64_t e = ob + g; e < oe; e += G) {
         int32_t c = col_o[e];
         int32_t wv = w_o[e];
         col_n[nb + (e - ob)] = c;
         w_n[nb + (e - ob)] = wv;
         ks += wv;
-        if (lab[c] == Lu) is += wv;
+        if (lab && lab[c] == Lu) is += wv;
       }
     } else if (pair_ptr[u + 1] - pair_ptr[u] < G) {
       // few pairs: the group's lanes hold them (lane q: pair p0 + q, and the
@@ -428,7 +474,7 @@ __global__ void __launch_bounds__(256, 5) merge_rows(
       const int64_t ob = rp_o[u], oe = rp_o[u + 1], nb = rp_n[u];
       const int64_t p0 = pair_ptr[u];
       const int np = (int)(pair_ptr[u + 1] - p0);
-      const int32_t Lu = lab[u];
+      const int32_t Lu = lab ? lab[u] : 0;
       const int32_t rA0 = pA[p0], rR0 = pR[p0];
       const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane_id() & ~(G - 1)));
       int32_t pc = INT_MAX, pa = 0, pr = 0;
@@ -467,7 +513,7 @@ __global__ void __launch_bounds__(256, 5) merge_rows(
         col_n[pos] = c;
         w_n[pos] = (int32_t)wv;
         ks += wv;
-        if (lab[c] == Lu) is += wv;
+        if (lab && lab[c] == Lu) is += wv;
       }
       for (int64_t q = p0 + g; q < p0 + np; q += G) {
         if (!(pflag[q] & kPairAdded)) continue;
@@ -478,12 +524,12 @@ __global__ void __launch_bounds__(256, 5) merge_rows(
         col_n[pos] = c;
         w_n[pos] = (int32_t)wv;
         ks += wv;
-        if (lab[c] == Lu) is += wv;
+        if (lab && lab[c] == Lu) is += wv;
       }
     } else {
       int64_t ob = rp_o[u], oe = rp_o[u + 1], nb = rp_n[u];
       int64_t p0 = pair_ptr[u], p1 = pair_ptr[u + 1];
-      int32_t Lu = lab[u];
+      int32_t Lu = lab ? lab[u] : 0;
       int32_t rA0 = pA[p0], rR0 = pR[p0];
       uint64_t hi = (uint64_t)(uint32_t)u << 32;
       for (int64_t e = ob + g; e < oe; e += G) {
@@ -498,7 +544,7 @@ __global__ void __launch_bounds__(256, 5) merge_rows(
         col_n[pos] = c;
         w_n[pos] = (int32_t)wv;
         ks += wv;
-        if (lab[c] == Lu) is += wv;
+        if (lab && lab[c] == Lu) is += wv;
       }
       for (int64_t q = p0 + g; q < p1; q += G) {
         if (!(pflag[q] & kPairAdded)) continue;
@@ -509,7 +555,7 @@ __global__ void __launch_bounds__(256, 5) merge_rows(
         col_n[pos] = c;
         w_n[pos] = (int32_t)wv;
         ks += wv;
-        if (lab[c] == Lu) is += wv;
+        if (lab && lab[c] == Lu) is += wv;
       }
     }
     ks = group_sum<G>(ks);
@@ -552,7 +598,7 @@ int validate_batch(dcd_ctx* c, const dcd_edge* ins, int64_t n_ins, const dcd_edg
   return DCD_OK;
 }
 
-int merge_batch(dcd_ctx* c, const int32_t* labels0, MergeOut* out) {
+int merge_batch(dcd_ctx* c, const int32_t* labels0, bool static_start, MergeOut* out) {
   cudaStream_t s = c->stream;
   const int64_t n = c->n;
   const int64_t n_ins = c->n_ins, n_del = c->n_del;
@@ -650,6 +696,16 @@ int merge_batch(dcd_ctx* c, const int32_t* labels0, MergeOut* out) {
   DCD_TRY(removed.alloc(&c->mem, P + 1));
   DCD_TRY_CUDA(cudaMemsetAsync(out->pair_ptr.get(), 0, (n + 1) * sizeof(int64_t), s));
 
+  // sum_i e_{i->C(i)} under the start labels on G_t: zero for a static start
+  // (singletons, no self-loops); from the previous update's value plus the
+  // batch's change when the context kept it (in_valid); else summed over
+  // every entry by the merge, which then gathers the label of each column
+  const bool from_prev = !static_start && c->in_valid;
+  const int32_t* lab_gather = (static_start || from_prev) ? nullptr : labels0;
+  Buf<int64_t> in_delta;
+  DCD_TRY(in_delta.alloc(&c->mem, c->G));
+  DCD_TRY_CUDA(cudaMemsetAsync(in_delta.get(), 0, c->G * sizeof(int64_t), s));
+
   const int cur = c->cur, nxt = 1 - c->cur;
   const int64_t* rp_o = c->rp[cur].get();
   const int32_t* col_o = c->col[cur].get();
@@ -659,7 +715,9 @@ int merge_batch(dcd_ctx* c, const int32_t* labels0, MergeOut* out) {
     ::dcd::count_launch(), reduce_pairs<<<grid_for(R, T), T, 0, s>>>(keys, vals, R, head.get(), pid.get(), c->ins.get(), n_ins,
                                               out->pkey.get(), out->pw.get(), out->pflag.get());
     ::dcd::count_launch(), pair_status<<<grid_for(P, T), T, 0, s>>>(out->pkey.get(), out->pw.get(), out->pflag.get(), P, rp_o, col_o, w_o,
-                                             added.get(), removed.get(), out->pair_ptr.get(), err);
+                                             added.get(), removed.get(), out->pair_ptr.get(), err,
+                                             from_prev ? labels0 : nullptr, c->G > 1 ? c->gid.get() : nullptr,
+                                             in_delta.get());
     DCD_LAUNCH_CHECK();
   }
   // pair_ptr: per-source counts -> exclusive scan (n + 1 entries)
@@ -697,12 +755,12 @@ int merge_batch(dcd_ctx* c, const int32_t* labels0, MergeOut* out) {
   DCD_TRY(par.on(0, &s_long));
   ::dcd::count_launch(), merge_long<256><<<4 * c->sms, 256, 0, s_long>>>(
       long_rows.get(), long_cnt.get(), rp_o, col_o, w_o, rp_n, c->col[nxt].get(), c->w[nxt].get(), pp,
-      out->pkey.get(), out->pw.get(), out->pflag.get(), added.get(), removed.get(), labels0, out->k.get(),
+      out->pkey.get(), out->pw.get(), out->pflag.get(), added.get(), removed.get(), lab_gather, out->k.get(),
       c->G > 1 ? c->gid.get() : nullptr, c->gs.get());
 #define DCD_MERGE(Gs)                                                                                       \
   ::dcd::count_launch(), merge_rows<Gs><<<wave_grid(merge_rows<Gs>, n * Gs, T), T, 0, s>>>(n, rp_o, col_o, w_o, rp_n, c->col[nxt].get(),            \
                                                    c->w[nxt].get(), pp, out->pkey.get(), out->pw.get(),     \
-                                                   out->pflag.get(), added.get(), removed.get(), labels0,  \
+                                                   out->pflag.get(), added.get(), removed.get(), lab_gather, \
                                                    out->k.get(), c->G > 1 ? c->gid.get() : nullptr,         \
                                                    c->gs.get())
   if (avg <= 6) DCD_MERGE(4);
@@ -712,6 +770,11 @@ int merge_batch(dcd_ctx* c, const int32_t* labels0, MergeOut* out) {
 #undef DCD_MERGE
   DCD_LAUNCH_CHECK();
   DCD_TRY(par.join());
+  if (from_prev) {
+    ::dcd::count_launch(), seed_in<<<cdiv(c->G, 128), 128, 0, s>>>(c->gs.get(), c->G, c->in_prev.get(),
+                                                                    in_delta.get());
+    DCD_LAUNCH_CHECK();
+  }
   return DCD_OK;
 }
 

@@ -206,6 +206,11 @@ struct dcd_ctx {
   cudaEvent_t join_ev[dcd::kMaxBins] = {};
   cudaEvent_t fork_ev = nullptr;
   dcd::BinPlan bin_plan = dcd::default_bin_plan();  // degree bins of the local-move kernels
+  // sum_i e_{i->C(i)} of C_t on G_t per graph, kept by the last update so the
+  // next merge need not gather every entry's label (in_valid: it is current;
+  // cleared by anything that replaces C_t other than a Louvain update)
+  bool in_valid = false;
+  dcd::Buf<int64_t> in_prev, in_next;
   // level 0 of the last update's local move (dcd_get_level0_bins): active
   // vertices per bin, vertices one sweep of each bin's grid covers, and
   // whether the bins ran side by side
@@ -296,7 +301,7 @@ struct MergeOut {
   Buf<int64_t> pair_ptr;   // n + 1: pairs of source u are [pair_ptr[u], pair_ptr[u+1])
   int64_t npairs = 0;
 };
-int merge_batch(dcd_ctx* c, const int32_t* labels0, MergeOut* out);
+int merge_batch(dcd_ctx* c, const int32_t* labels0, bool static_start, MergeOut* out);
 
 // screen.cu: Algorithm 2 plus the deletion rule -> rset (n bytes).
 int screen_batch(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* labels0, const int64_t* k,

@@ -307,3 +307,23 @@ def test_weight_overflow_is_reported(dcd):
     assert ei.value.code == dcd.DCD_EOVERFLOW
     rp, col, w = ctx.graph()
     assert w.tolist() == [2_000_000_000, 2_000_000_000]
+
+
+def test_set_labels_mid_stream(dcd, orc, synth):
+    # replacing C_t between steps: the next step's level-0 sums start from the
+    # new labels (the kept sum of the old ones must not be reused)
+    s = synth.sbm_10k(n=2000, blocks=20, steps=5)
+    ctx = dcd.Context(s.n, mode=dcd.MODE_DELTA)
+    ref = orc.Context(s.n)
+    rng = np.random.default_rng(41)
+    for t, (ins, dels) in enumerate(s.steps):
+        if t in (2, 4):
+            new = rng.integers(0, 40, s.n).astype(np.int32)
+            ctx.set_labels(new)
+            ref.set_labels(new)
+        ctx.apply_batch(ins, dels)
+        ref.apply_batch(ins, dels)
+        lab, q, st = ctx.update()
+        rlab, rq, rst = ref.update(orc.DELTA)
+        assert_step_equal(st, rst, lab, rlab, q, rq, ctx.rset(), ref.rset())
+    ctx.close()
