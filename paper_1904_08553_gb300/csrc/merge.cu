@@ -1,5 +1,5 @@
 // merge.cu -- Delta_t into G_t: batch records, radix sort by (source, sink),
-// distinct pairs, and a row-parallel sort-merge of the CSR that also produces
+// distinct pairs, and a tiled merge of the CSR with the pairs that also produces
 // the weighted degrees d_w (Sec. III-A), 2m and sum_i e_{i->C(i)} under the
 // inherited labels.
 //
@@ -208,14 +208,6 @@ __device__ __forceinline__ int64_t lower_bound_i32(const int32_t* __restrict__ a
   return lo;
 }
 
-__device__ __forceinline__ int64_t lower_bound_u64(const uint64_t* __restrict__ a, int64_t lo, int64_t hi, uint64_t x) {
-  while (lo < hi) {
-    int64_t mid = (lo + hi) >> 1;
-    if (a[mid] < x) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
-
 // Per pair: was the edge in G_{t-1}; does the merge add or remove a row entry.
 // With lab0 (C_{t-1}) given, also the change the pair makes to
 // sum_i e_{i->C(i)} under C_{t-1}: its new weight minus its old one when both
@@ -290,292 +282,221 @@ __global__ void seed_in(GraphState* __restrict__ gs, int G, const int64_t* __res
     gs[g].in_cur += in_prev[g] + in_delta[g];
 }
 
-// Rows longer than kLongRow entries (old or new) are merged by a CTA each
-// (merge_long) instead of by G lanes: a hub row would otherwise hold its
-// group for thousands of iterations and set the kernel's length.
-constexpr int64_t kLongRow = 512;
+// ---- tiled merge ----
+//
+// The merge as one merge of two sorted sequences: the old entries (key =
+// source << 32 | sink, in CSR order) and the pairs (same keys), an entry
+// before a pair of equal key.  With A(q), R(q) the added and removed pairs
+// among the first q, an old entry e lands at e + A(q) - R(q) (q: pairs of
+// smaller key) and an added pair q at i + A(q) - R(q) (i: old entries of
+// smaller key), so rows need not be merged one by one: the merged sequence is
+// cut into tiles of kMergeTile items, a CTA each, whatever rows they cover.
+constexpr int kMergeTile = 2048;
+constexpr int kMergeThreads = 256;
+constexpr int kMergeRows = 1024;  // row starts staged per tile (more: searched in global memory)
 
-__global__ void new_degrees(const int64_t* __restrict__ rp, const int64_t* __restrict__ pair_ptr,
-                            const int32_t* __restrict__ pA, const int32_t* __restrict__ pR, int64_t n,
-                            int64_t* __restrict__ deg, int32_t* __restrict__ long_rows,
-                            int32_t* __restrict__ long_cnt) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (blockIdx.x * (int64_t)blockDim.x) + (threadIdx.x & ~31); base < n; base += stride) {
-    const int64_t u = base + lane_id();
-    bool lng = false;
-    if (u < n) {
-      const int64_t p0 = pair_ptr[u], p1 = pair_ptr[u + 1];
-      const int64_t od = rp[u + 1] - rp[u];
-      const int64_t nd = od + (pA[p1] - pA[p0]) - (pR[p1] - pR[p0]);
-      deg[u] = nd;
-      lng = od > kLongRow || nd > kLongRow;
-    }
-    const unsigned bal = __ballot_sync(0xffffffffu, lng);
-    if (bal) {
-      int32_t slot = 0;
-      if (lane_id() == 0) slot = atomicAdd(long_cnt, __popc(bal));
-      slot = __shfl_sync(0xffffffffu, slot, 0);
-      if (lng) long_rows[slot + __popc(bal & lanemask_lt())] = (int32_t)u;
-    }
+// Row u's start in the new CSR: rp_o[u] + A(pair_ptr[u]) - R(pair_ptr[u]).
+__global__ void new_rows(const int64_t* __restrict__ rp_o, const int64_t* __restrict__ pair_ptr,
+                         const int32_t* __restrict__ pA, const int32_t* __restrict__ pR, int64_t n,
+                         int64_t* __restrict__ rp_n) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u <= n; u += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = pair_ptr[u];
+    rp_n[u] = rp_o[u] + pA[p] - pR[p];
   }
 }
 
-// One CTA per long row (the list from new_degrees): the row's pairs are staged
-// in shared memory when they fit, the entries are placed as in merge_rows, and
-// k_u, 2m and sum_i e_{i->C(i)} are reduced over the CTA.
-constexpr int kLongPairs = 1024;
+// Tile t starts at merged item d = t * kMergeTile: se[t] old entries and sq[t]
+// pairs come before it, su[t] is the row of item d.  Rows are found on
+// W(u) = rp_o[u] + pair_ptr[u] (the merged items of rows before u), then
+// the split inside the row by a merge-path search over its sinks.
+__global__ void merge_split(int64_t n, const int64_t* __restrict__ rp_o, const int32_t* __restrict__ col_o,
+                            const int64_t* __restrict__ pp, const uint64_t* __restrict__ pkey, int64_t nt,
+                            int64_t total, int64_t* __restrict__ se, int64_t* __restrict__ sq,
+                            int64_t* __restrict__ su) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= nt; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t dd = t * kMergeTile < total ? t * kMergeTile : total;
+    if (dd == total) {
+      se[t] = rp_o[n];
+      sq[t] = pp[n];
+      su[t] = n > 0 ? n - 1 : 0;
+      continue;
+    }
+    int64_t lo = 0, hi = n - 1;  // last row with W(u) <= dd
+    while (lo < hi) {
+      const int64_t mid = (lo + hi + 1) >> 1;
+      if (rp_o[mid] + pp[mid] <= dd) lo = mid; else hi = mid - 1;
+    }
+    const int64_t u = lo;
+    const int64_t ob = rp_o[u], deg = rp_o[u + 1] - ob, p0 = pp[u], np = pp[u + 1] - p0;
+    const int64_t r = dd - ob - p0;  // items of row u before dd: i entries, r - i pairs
+    int64_t a = r - np > 0 ? r - np : 0, b = r < deg ? r : deg;
+    while (a < b) {
+      const int64_t mid = (a + b) >> 1;
+      if (col_o[ob + mid] <= (int32_t)(pkey[p0 + r - 1 - mid] & 0xffffffffu)) a = mid + 1; else b = mid;
+    }
+    se[t] = ob + a;
+    sq[t] = p0 + r - a;
+    su[t] = u;
+  }
+}
 
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS) merge_long(
-    const int32_t* __restrict__ long_rows, const int32_t* __restrict__ long_cnt, const int64_t* __restrict__ rp_o,
-    const int32_t* __restrict__ col_o, const int32_t* __restrict__ w_o, const int64_t* __restrict__ rp_n,
-    int32_t* __restrict__ col_n, int32_t* __restrict__ w_n, const int64_t* __restrict__ pair_ptr,
-    const uint64_t* __restrict__ pkey, const int64_t* __restrict__ pw, const uint8_t* __restrict__ pflag,
-    const int32_t* __restrict__ pA, const int32_t* __restrict__ pR, const int32_t* __restrict__ lab,
+__device__ __forceinline__ int lower_bound_smem(const uint64_t* a, int n, uint64_t x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// Adds a row's share of the weights into kdeg: lanes of one row sum with
+// redux (exact from 16-bit slices) and the lowest adds.
+__device__ __forceinline__ void add_row_weight(int64_t* kdeg, int64_t u, int64_t wv) {
+  const unsigned peers = __match_any_sync(0xffffffffu, u);
+  const unsigned lo = (unsigned)wv & 0xffffu, hi = (unsigned)(wv >> 16);
+  const unsigned long long sum =
+      (unsigned long long)__reduce_add_sync(peers, lo) + ((unsigned long long)__reduce_add_sync(peers, hi) << 16);
+  if (u >= 0 && sum != 0 && (int)(__ffs(peers) - 1) == (int)lane_id())
+    atomicAdd((unsigned long long*)&kdeg[u], sum);
+}
+
+// One tile of the merge.  Weights written are int32 (checked by pair_status),
+// so a lane's weight is below 2^31 and the slice sums above are exact.
+__global__ void __launch_bounds__(kMergeThreads) merge_tile(
+    int64_t n, const int64_t* __restrict__ rp_o, const int32_t* __restrict__ col_o,
+    const int32_t* __restrict__ w_o, const int64_t* __restrict__ se, const int64_t* __restrict__ sq,
+    const int64_t* __restrict__ su, const uint64_t* __restrict__ pkey, const int64_t* __restrict__ pw,
+    const uint8_t* __restrict__ pflag, const int32_t* __restrict__ pA, const int32_t* __restrict__ pR, int64_t P,
+    int32_t* __restrict__ col_n, int32_t* __restrict__ w_n, const int32_t* __restrict__ lab,
     int64_t* __restrict__ kdeg, const int32_t* __restrict__ gid, GraphState* __restrict__ gs) {
-  __shared__ int32_t s_pc[kLongPairs];
-  __shared__ int32_t s_pa[kLongPairs + 1], s_pr[kLongPairs + 1];
-  __shared__ long long red_k[THREADS / 32], red_i[THREADS / 32];
-  const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5;
-  const int64_t cnt = *long_cnt;
-  for (int64_t i = blockIdx.x; i < cnt; i += gridDim.x) {
-    const int32_t u = long_rows[i];
-    const int64_t ob = rp_o[u], oe = rp_o[u + 1], nb = rp_n[u];
-    const int64_t p0 = pair_ptr[u], p1 = pair_ptr[u + 1];
-    const int64_t np = p1 - p0;
-    const int32_t Lu = lab ? lab[u] : 0;
-    const int32_t rA0 = pA[p0], rR0 = pR[p0];  // prefix arrays hold P + 1 entries
-    const bool staged = np <= kLongPairs;
+  __shared__ uint64_t s_pk[kMergeTile];
+  __shared__ uint64_t s_ek[kMergeTile];
+  __shared__ int64_t s_rp[kMergeRows + 1];
+  __shared__ unsigned long long s_red[2][kMergeThreads / 32];
+  __shared__ int s_uni;
+  const int tid = threadIdx.x;
+  const int64_t t = blockIdx.x;
+  const int64_t e0 = se[t], q0 = sq[t], ua = su[t], ub = su[t + 1];
+  const int ne = (int)(se[t + 1] - e0), np = (int)(sq[t + 1] - q0);
+  const int64_t nr = ub - ua + 1;  // rows ua..ub hold the tile's entries
+  const bool staged = nr + 1 <= kMergeRows + 1;
+  for (int j = tid; j < np; j += kMergeThreads) s_pk[j] = pkey[q0 + j];
+  if (staged)
+    for (int j = tid; j <= nr; j += kMergeThreads) s_rp[j] = rp_o[ua + j];
+  __syncthreads();
+  // entry keys
+  for (int j = tid; j < ne; j += kMergeThreads) {
+    const int64_t e = e0 + j;
+    int64_t u;
     if (staged) {
-      for (int64_t q = tid; q <= np; q += THREADS) {
-        s_pa[q] = pA[p0 + q] - rA0;
-        s_pr[q] = pR[p0 + q] - rR0;
-        if (q < np) s_pc[q] = (int32_t)(pkey[p0 + q] & 0xffffffffu);
+      int lo = 0, hi = (int)nr - 1;  // last row start <= e
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_rp[mid] <= e) lo = mid; else hi = mid - 1;
+      }
+      u = ua + lo;
+    } else {
+      int64_t lo = ua, hi = ub;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (rp_o[mid] <= e) lo = mid; else hi = mid - 1;
+      }
+      u = lo;
+    }
+    s_ek[j] = (uint64_t)u << 32 | (uint32_t)col_o[e];
+  }
+  __syncthreads();
+  int cur_g = -1;
+  long long m2_loc = 0, in_loc = 0;
+  auto account = [&](int64_t u, int32_t cc, int64_t wv) {
+    const int gu = graph_of(gid, u);
+    if (gu != cur_g) {
+      if (cur_g >= 0 && (m2_loc | in_loc)) {
+        atomicAdd((unsigned long long*)&gs[cur_g].m2, (unsigned long long)m2_loc);
+        atomicAdd((unsigned long long*)&gs[cur_g].in_cur, (unsigned long long)in_loc);
+      }
+      cur_g = gu;
+      m2_loc = in_loc = 0;
+    }
+    m2_loc += wv;
+    if (lab && lab[cc] == lab[u]) in_loc += wv;
+  };
+  // old entries (warp-uniform trip count for the row sums)
+  for (int j0 = 0; j0 < ne; j0 += kMergeThreads) {
+    const int j = j0 + tid;
+    int64_t u = -1, wv = 0;
+    if (j < ne) {
+      const int64_t e = e0 + j;
+      const uint64_t key = s_ek[j];
+      const int64_t q = q0 + lower_bound_smem(s_pk, np, key);
+      // the equal pair follows its entry, possibly in the next tile
+      const bool match = q - q0 < np ? s_pk[q - q0] == key : (q < P && pkey[q] == key);
+      const uint32_t f = match ? pflag[q] : 0u;
+      if (!(f & kPairRemoved)) {
+        const int32_t cc = (int32_t)(key & 0xffffffffu);
+        wv = w_o[e];
+        if (match && (f & kPairIns)) wv = (f & kPairDel) ? pw[q] : wv + pw[q];
+        const int64_t pos = e + pA[q] - pR[q];
+        col_n[pos] = cc;
+        w_n[pos] = (int32_t)wv;
+        u = (int64_t)(key >> 32);
+        account(u, cc, wv);
       }
     }
-    __syncthreads();
-    int64_t ks = 0, is = 0;
-    const uint64_t hi = (uint64_t)(uint32_t)u << 32;
-    for (int64_t e = ob + tid; e < oe; e += THREADS) {
-      const int32_t c = col_o[e];
-      int64_t q;
-      bool match;
-      int32_t aq, rq;
-      if (staged) {
-        int64_t lo = 0, hi2 = np;
-        while (lo < hi2) {
-          const int64_t mid = (lo + hi2) >> 1;
-          if (s_pc[mid] < c) lo = mid + 1; else hi2 = mid;
-        }
-        q = p0 + lo;
-        match = lo < np && s_pc[lo] == c;
-        aq = s_pa[lo];
-        rq = s_pr[lo];
-      } else {
-        q = lower_bound_u64(pkey, p0, p1, hi | (uint32_t)c);
-        match = q < p1 && pkey[q] == (hi | (uint32_t)c);
-        aq = pA[q] - rA0;
-        rq = pR[q] - rR0;
+    add_row_weight(kdeg, u, wv);
+  }
+  // added pairs
+  for (int j0 = 0; j0 < np; j0 += kMergeThreads) {
+    const int j = j0 + tid;
+    int64_t u = -1, wv = 0;
+    if (j < np) {
+      const int64_t q = q0 + j;
+      if (pflag[q] & kPairAdded) {
+        const uint64_t key = s_pk[j];
+        const int64_t i = e0 + lower_bound_smem(s_ek, ne, key);
+        const int32_t cc = (int32_t)(key & 0xffffffffu);
+        wv = pw[q];
+        const int64_t pos = i + pA[q] - pR[q];
+        col_n[pos] = cc;
+        w_n[pos] = (int32_t)wv;
+        u = (int64_t)(key >> 32);
+        account(u, cc, wv);
       }
-      const uint8_t f = match ? pflag[q] : 0;
-      if (f & kPairRemoved) continue;
-      int64_t wv = w_o[e];
-      if (match && (f & kPairIns)) wv = (f & kPairDel) ? pw[q] : wv + pw[q];
-      const int64_t pos = nb + (e - ob) - rq + aq;
-      col_n[pos] = c;
-      w_n[pos] = (int32_t)wv;
-      ks += wv;
-      if (lab && lab[c] == Lu) is += wv;
     }
-    for (int64_t q = p0 + tid; q < p1; q += THREADS) {
-      if (!(pflag[q] & kPairAdded)) continue;
-      const int32_t c = (int32_t)(pkey[q] & 0xffffffffu);
-      const int64_t o = lower_bound_i32(col_o, ob, oe, c) - ob;
-      const int64_t pos = nb + o - (pR[q] - rR0) + (pA[q] - rA0);
-      const int64_t wv = pw[q];
-      col_n[pos] = c;
-      w_n[pos] = (int32_t)wv;
-      ks += wv;
-      if (lab && lab[c] == Lu) is += wv;
-    }
+    add_row_weight(kdeg, u, wv);
+  }
+  // 2m and sum_i e_{i->C(i)}: one add per CTA when the tile lies in one graph
+  const int g0 = cur_g;
+  if (tid == 0) s_uni = -2;
+  __syncthreads();
+  if (g0 >= 0) atomicCAS(&s_uni, -2, g0);
+  __syncthreads();
+  const int gref = s_uni;
+  const bool uni = __syncthreads_and(g0 < 0 || g0 == gref);
+  if (uni) {
+    unsigned long long a = (unsigned long long)m2_loc, b = (unsigned long long)in_loc;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      ks += __shfl_xor_sync(0xffffffffu, ks, o);
-      is += __shfl_xor_sync(0xffffffffu, is, o);
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
     }
-    if (lane == 0) {
-      red_k[wid] = ks;
-      red_i[wid] = is;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      long long tk = 0, ti = 0;
-      for (int x = 0; x < THREADS / 32; x++) {
-        tk += red_k[x];
-        ti += red_i[x];
-      }
-      kdeg[u] = tk;
-      const int gu = graph_of(gid, u);
-      atomicAdd((unsigned long long*)&gs[gu].m2, (unsigned long long)tk);
-      atomicAdd((unsigned long long*)&gs[gu].in_cur, (unsigned long long)ti);
+    if (lane_id() == 0) {
+      s_red[0][tid >> 5] = a;
+      s_red[1][tid >> 5] = b;
     }
     __syncthreads();
-  }
-}
-
-template <int G>
-__device__ __forceinline__ int64_t group_sum(int64_t x) {
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o, G);
-  return x;
-}
-
-// G lanes per row.  An untouched row is copied; a touched row is merged with
-// its pairs: an old entry lands at its old offset minus the removed pairs and
-// plus the added pairs that sort before it; an added pair lands after the old
-// entries below it, corrected the same way.
-template <int G>
-__global__ void __launch_bounds__(256, 5) merge_rows(
-    int64_t n, const int64_t* __restrict__ rp_o, const int32_t* __restrict__ col_o, const int32_t* __restrict__ w_o,
-    const int64_t* __restrict__ rp_n, int32_t* __restrict__ col_n, int32_t* __restrict__ w_n,
-    const int64_t* __restrict__ pair_ptr, const uint64_t* __restrict__ pkey, const int64_t* __restrict__ pw,
-    const uint8_t* __restrict__ pflag, const int32_t* __restrict__ pA, const int32_t* __restrict__ pR,
-    const int32_t* __restrict__ lab, int64_t* __restrict__ kdeg, const int32_t* __restrict__ gid,
-    GraphState* __restrict__ gs) {
-  const int g = threadIdx.x % G;
-  // warp-uniform loop: every lane reaches the group shuffles
-  const int64_t gid0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * (32 / G);
-  const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
-  // 2m and sum_i e_{i->C(i)} per graph: accumulated while consecutive rows of
-  // a group stay in one graph, flushed by the group leader when it changes
-  int64_t m2_loc = 0, in_loc = 0;
-  int cur_g = -1;
-  for (int64_t ubase = gid0; ubase < n; ubase += ngroups) {
-    const int64_t u = ubase + (int64_t)(lane_id() / G);
-    int64_t ks = 0, is = 0;
-    const bool lng = u < n && (rp_o[u + 1] - rp_o[u] > kLongRow || rp_n[u + 1] - rp_n[u] > kLongRow);
-    if (u >= n || lng) {
-      // idle group in the warp's last round, or a long row (merge_long)
-    } else if (pair_ptr[u] == pair_ptr[u + 1]) {
-      int64_t ob = rp_o[u], oe = rp_o[u + 1], nb = rp_n[u];
-      int32_t Lu = lab ? lab[u] : 0;
-      for (int64_t e = ob + g; e < oe; e += G) {
-        int32_t c = col_o[e];
-        int32_t wv = w_o[e];
-        col_n[nb + (e - ob)] = c;
-        w_n[nb + (e - ob)] = wv;
-        ks += wv;
-        if (lab && lab[c] == Lu) is += wv;
+    if (tid == 0 && gref >= 0) {
+      unsigned long long sa = 0, sb = 0;
+      for (int x = 0; x < kMergeThreads / 32; x++) {
+        sa += s_red[0][x];
+        sb += s_red[1][x];
       }
-    } else if (pair_ptr[u + 1] - pair_ptr[u] < G) {
-      // few pairs: the group's lanes hold them (lane q: pair p0 + q, and the
-      // prefix counts up to it), so an entry finds its place among them with
-      // shuffles instead of a binary search in global memory
-      const int64_t ob = rp_o[u], oe = rp_o[u + 1], nb = rp_n[u];
-      const int64_t p0 = pair_ptr[u];
-      const int np = (int)(pair_ptr[u + 1] - p0);
-      const int32_t Lu = lab ? lab[u] : 0;
-      const int32_t rA0 = pA[p0], rR0 = pR[p0];
-      const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane_id() & ~(G - 1)));
-      int32_t pc = INT_MAX, pa = 0, pr = 0;
-      uint32_t pf = 0;
-      long long pwv = 0;
-      if (g <= np) {
-        pa = pA[p0 + g] - rA0;
-        pr = pR[p0 + g] - rR0;
-        if (g < np) {
-          pc = (int32_t)(pkey[p0 + g] & 0xffffffffu);
-          pf = pflag[p0 + g];
-          pwv = pw[p0 + g];
-        }
-      }
-      for (int64_t e0 = ob; e0 < oe; e0 += G) {
-        const int64_t e = e0 + g;
-        const bool valid = e < oe;
-        const int32_t c = valid ? col_o[e] : INT_MAX;
-        // pairs of the row with a smaller column: the lanes hold the pair
-        // columns in ascending order (INT_MAX past the last), so a branch-free
-        // binary search over the G lanes counts them
-        int q = 0;
-#pragma unroll
-        for (int stp = G / 2; stp > 0; stp >>= 1)
-          if (__shfl_sync(gmask, pc, q + stp - 1, G) < c) q += stp;
-        const int32_t kq = __shfl_sync(gmask, pc, q, G);
-        const uint32_t fq = __shfl_sync(gmask, pf, q, G);
-        const long long wq = __shfl_sync(gmask, pwv, q, G);
-        const int32_t aq = __shfl_sync(gmask, pa, q, G), rq = __shfl_sync(gmask, pr, q, G);
-        const bool match = valid && kq == c;
-        const uint32_t f = match ? fq : 0u;
-        if (!valid || (f & kPairRemoved)) continue;
-        int64_t wv = w_o[e];
-        if (match && (f & kPairIns)) wv = (f & kPairDel) ? (int64_t)wq : wv + (int64_t)wq;
-        const int64_t pos = nb + (e - ob) - rq + aq;
-        col_n[pos] = c;
-        w_n[pos] = (int32_t)wv;
-        ks += wv;
-        if (lab && lab[c] == Lu) is += wv;
-      }
-      for (int64_t q = p0 + g; q < p0 + np; q += G) {
-        if (!(pflag[q] & kPairAdded)) continue;
-        const int32_t c = (int32_t)(pkey[q] & 0xffffffffu);
-        const int64_t o = lower_bound_i32(col_o, ob, oe, c) - ob;
-        const int64_t pos = nb + o - (pR[q] - rR0) + (pA[q] - rA0);
-        const int64_t wv = pw[q];
-        col_n[pos] = c;
-        w_n[pos] = (int32_t)wv;
-        ks += wv;
-        if (lab && lab[c] == Lu) is += wv;
-      }
-    } else {
-      int64_t ob = rp_o[u], oe = rp_o[u + 1], nb = rp_n[u];
-      int64_t p0 = pair_ptr[u], p1 = pair_ptr[u + 1];
-      int32_t Lu = lab ? lab[u] : 0;
-      int32_t rA0 = pA[p0], rR0 = pR[p0];
-      uint64_t hi = (uint64_t)(uint32_t)u << 32;
-      for (int64_t e = ob + g; e < oe; e += G) {
-        int32_t c = col_o[e];
-        int64_t q = lower_bound_u64(pkey, p0, p1, hi | (uint32_t)c);
-        bool match = q < p1 && pkey[q] == (hi | (uint32_t)c);
-        uint8_t f = match ? pflag[q] : 0;
-        if (f & kPairRemoved) continue;
-        int64_t wv = w_o[e];
-        if (match && (f & kPairIns)) wv = (f & kPairDel) ? pw[q] : wv + pw[q];
-        int64_t pos = nb + (e - ob) - (pR[q] - rR0) + (pA[q] - rA0);
-        col_n[pos] = c;
-        w_n[pos] = (int32_t)wv;
-        ks += wv;
-        if (lab && lab[c] == Lu) is += wv;
-      }
-      for (int64_t q = p0 + g; q < p1; q += G) {
-        if (!(pflag[q] & kPairAdded)) continue;
-        int32_t c = (int32_t)(pkey[q] & 0xffffffffu);
-        int64_t o = lower_bound_i32(col_o, ob, oe, c) - ob;
-        int64_t pos = nb + o - (pR[q] - rR0) + (pA[q] - rA0);
-        int64_t wv = pw[q];
-        col_n[pos] = c;
-        w_n[pos] = (int32_t)wv;
-        ks += wv;
-        if (lab && lab[c] == Lu) is += wv;
+      if (sa | sb) {
+        atomicAdd((unsigned long long*)&gs[gref].m2, sa);
+        atomicAdd((unsigned long long*)&gs[gref].in_cur, sb);
       }
     }
-    ks = group_sum<G>(ks);
-    is = group_sum<G>(is);
-    if (g == 0 && u < n && !lng) {
-      kdeg[u] = ks;
-      const int gu = graph_of(gid, u);
-      if (gu != cur_g) {
-        if (cur_g >= 0 && (m2_loc | in_loc)) {
-          atomicAdd((unsigned long long*)&gs[cur_g].m2, (unsigned long long)m2_loc);
-          atomicAdd((unsigned long long*)&gs[cur_g].in_cur, (unsigned long long)in_loc);
-        }
-        cur_g = gu;
-        m2_loc = in_loc = 0;
-      }
-      m2_loc += ks;
-      in_loc += is;
-    }
-  }
-  if (g == 0 && cur_g >= 0 && (m2_loc | in_loc)) {
+  } else if (cur_g >= 0 && (m2_loc | in_loc)) {
     atomicAdd((unsigned long long*)&gs[cur_g].m2, (unsigned long long)m2_loc);
     atomicAdd((unsigned long long*)&gs[cur_g].in_cur, (unsigned long long)in_loc);
   }
@@ -732,44 +653,31 @@ int merge_batch(dcd_ctx* c, const int32_t* labels0, bool static_start, MergeOut*
   DCD_TRY(c->col[nxt].ensure(&c->mem, cap));
   DCD_TRY(c->w[nxt].ensure(&c->mem, cap));
   int64_t* rp_n = c->rp[nxt].get();
-  Buf<int32_t> long_rows, long_cnt;
-  DCD_TRY(long_rows.alloc(&c->mem, n));
-  DCD_TRY(long_cnt.alloc(&c->mem, 1));
-  DCD_TRY_CUDA(cudaMemsetAsync(long_cnt.get(), 0, sizeof(int32_t), s));
-  ::dcd::count_launch(), new_degrees<<<grid_for(n, T), T, 0, s>>>(rp_o, out->pair_ptr.get(), added.get(), removed.get(),
-                                                                   n, rp_n, long_rows.get(), long_cnt.get());
+  ::dcd::count_launch(), new_rows<<<grid_for(n + 1, T), T, 0, s>>>(rp_o, out->pair_ptr.get(), added.get(),
+                                                                    removed.get(), n, rp_n);
   DCD_LAUNCH_CHECK();
-  DCD_TRY(exclusive_scan<int64_t>(rp_n, rp_n, n + 1, nullptr, stmp64, s));
 
-  // ---- merge rows, degrees, m2, in ----
+  // ---- merge (tiles of the merged sequence), degrees, m2, in ----
   DCD_TRY(out->k.alloc(&c->mem, n));
+  DCD_TRY_CUDA(cudaMemsetAsync(out->k.get(), 0, n * sizeof(int64_t), s));
   DCD_TRY_CUDA(cudaMemsetAsync(c->gs.get(), 0, c->G * sizeof(GraphState), s));
-  const int64_t avg = (cap + n - 1) / n;
-  const int64_t* pp = out->pair_ptr.get();
-  // merge_rows skips the rows above kLongRow entries, which merge_long takes:
-  // the two write disjoint rows (and add into 2m and sum e_{i->C(i)} with
-  // atomics), so they run side by side
-  SideBySide par(c, n);
-  DCD_TRY(par.fork());
-  cudaStream_t s_long;
-  DCD_TRY(par.on(0, &s_long));
-  ::dcd::count_launch(), merge_long<256><<<4 * c->sms, 256, 0, s_long>>>(
-      long_rows.get(), long_cnt.get(), rp_o, col_o, w_o, rp_n, c->col[nxt].get(), c->w[nxt].get(), pp,
-      out->pkey.get(), out->pw.get(), out->pflag.get(), added.get(), removed.get(), lab_gather, out->k.get(),
-      c->G > 1 ? c->gid.get() : nullptr, c->gs.get());
-#define DCD_MERGE(Gs)                                                                                       \
-  ::dcd::count_launch(), merge_rows<Gs><<<wave_grid(merge_rows<Gs>, n * Gs, T), T, 0, s>>>(n, rp_o, col_o, w_o, rp_n, c->col[nxt].get(),            \
-                                                   c->w[nxt].get(), pp, out->pkey.get(), out->pw.get(),     \
-                                                   out->pflag.get(), added.get(), removed.get(), lab_gather, \
-                                                   out->k.get(), c->G > 1 ? c->gid.get() : nullptr,         \
-                                                   c->gs.get())
-  if (avg <= 6) DCD_MERGE(4);
-  else if (avg <= 12) DCD_MERGE(8);
-  else if (avg <= 24) DCD_MERGE(16);
-  else DCD_MERGE(32);
-#undef DCD_MERGE
-  DCD_LAUNCH_CHECK();
-  DCD_TRY(par.join());
+  const int64_t total = c->nnz + P;
+  const int64_t nt = cdiv(total, (int64_t)kMergeTile);
+  if (nt > 0) {
+    Buf<int64_t> split;
+    DCD_TRY(split.alloc(&c->mem, 3 * (nt + 1)));
+    int64_t* se = split.get();
+    int64_t* sq = se + (nt + 1);
+    int64_t* su = sq + (nt + 1);
+    ::dcd::count_launch(), merge_split<<<grid_for(nt + 1, T), T, 0, s>>>(n, rp_o, col_o, out->pair_ptr.get(),
+                                                                          out->pkey.get(), nt, total, se, sq, su);
+    DCD_LAUNCH_CHECK();
+    ::dcd::count_launch(), merge_tile<<<(unsigned)nt, kMergeThreads, 0, s>>>(
+        n, rp_o, col_o, w_o, se, sq, su, out->pkey.get(), out->pw.get(), out->pflag.get(), added.get(),
+        removed.get(), P, c->col[nxt].get(), c->w[nxt].get(), lab_gather, out->k.get(),
+        c->G > 1 ? c->gid.get() : nullptr, c->gs.get());
+    DCD_LAUNCH_CHECK();
+  }
   if (from_prev) {
     ::dcd::count_launch(), seed_in<<<cdiv(c->G, 128), 128, 0, s>>>(c->gs.get(), c->G, c->in_prev.get(),
                                                                     in_delta.get());
