@@ -388,6 +388,8 @@ def gpu_arm(args):
             "ms_local_move": float(np.mean([s.ms_local_move for s in stats])),
             "ms_apply": float(np.mean([s.ms_apply for s in stats])),
             "ms_coarsen": float(np.mean([s.ms_coarsen for s in stats])),
+            "coarse0_delta_steps": int(sum(s.coarse0_delta for s in stats)),
+            "coarse0_entries_mean": float(np.mean([s.coarse0_entries for s in stats])),
             "ms_finish": float(np.mean([s.ms_finish for s in stats])),
             "passes_per_step": passes / len(stats),
             "passes_level0_per_step": passes0 / len(stats),
@@ -496,6 +498,8 @@ def rmat_leg(args):
         "ms_screen": float(np.mean([s.ms_screen for s in stats])),
         "ms_local_move": float(np.mean([s.ms_local_move for s in stats])),
         "ms_coarsen": float(np.mean([s.ms_coarsen for s in stats])),
+        "coarse0_delta_steps": int(sum(s.coarse0_delta for s in stats)),
+        "coarse0_entries_mean": float(np.mean([s.coarse0_entries for s in stats])),
         "level0_local_move_gbs": gbs, "level0_frac": (gbs / peak) if gbs else None, "peak_kind": peak_kind,
         "timing": "CUDA events on the context stream around each update", "clocks": clk.summary(),
     }

@@ -73,7 +73,10 @@ typedef struct {
   int32_t max_levels; /* default 64                                                   */
   int32_t tau_inv;    /* a pass (level) gaining at most |N| / tau_inv stops it; 1e6  */
   int32_t alg;        /* DCD_ALG_*; default DCD_ALG_LOUVAIN                           */
-  int32_t reserved[11];
+  int32_t coarsen_full; /* 1: build level 0's coarse graph from every entry of G_t in
+                           every update; 0 (default): from the previous update's one
+                           when it allows (see dcd_step_stats.coarse0_delta)         */
+  int32_t reserved[10];
 } dcd_config;
 
 typedef struct {
@@ -116,6 +119,15 @@ typedef struct {
   int64_t verts_level0;  /* vertices evaluated at level 0 (all its passes)          */
   int64_t refine_iters;  /* DCD_ALG_SLM: local-move passes of the refinements       */
   int64_t refine_moves;  /* DCD_ALG_SLM: moves of the refinements                   */
+  int64_t coarse0_delta; /* 1: level 0's coarse graph was updated from the previous
+                            update's (same communities as a rebuild, Sec. III-D: R_t
+                            only changes level 0): the coarse graph of G_{t-1} under
+                            C_{t-1}, plus the batch's weight changes, plus the rows
+                            of the vertices that level 0 moved.  Taken for a single
+                            Louvain graph whose level-0 and previous communities
+                            number at most 4096, after a non-static update        */
+  int64_t coarse0_entries; /* entries that built level 0's coarse graph: nnz of G_t,
+                              or batch pairs + rows of the moved vertices          */
 } dcd_step_stats;
 
 typedef struct dcd_ctx dcd_ctx;

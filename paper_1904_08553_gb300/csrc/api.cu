@@ -286,7 +286,8 @@ int dcd_create(int64_t n, const dcd_config* cfg, void* cuda_stream, dcd_ctx** ou
   dcd_config_default(&cf);
   if (cfg) cf = *cfg;
   if (cf.mode < DCD_MODE_STATIC || cf.mode > DCD_MODE_LEARNED || cf.max_iters <= 0 || cf.max_levels <= 0 ||
-      cf.tau_inv <= 0 || (cf.alg != DCD_ALG_LOUVAIN && cf.alg != DCD_ALG_SLM))
+      cf.tau_inv <= 0 || (cf.alg != DCD_ALG_LOUVAIN && cf.alg != DCD_ALG_SLM) ||
+      (cf.coarsen_full != 0 && cf.coarsen_full != 1))
     return DCD_EINVAL;
   if (cf.alg == DCD_ALG_SLM && n >= ((int64_t)1 << 30)) return DCD_EINVAL;
   dcd_ctx* c = new (std::nothrow) dcd_ctx();
@@ -390,6 +391,8 @@ int dcd_destroy(dcd_ctx* c) {
     c->feat_X.reset(); c->feat_y.reset(); c->feat_v.reset(); c->level0.reset();
     c->gs.reset(); c->goff_d.reset(); c->gid.reset();
     c->in_prev.reset(); c->in_next.reset();
+    c->kc_mat.reset(); c->kc_mat_nx.reset(); c->kc_idx.reset(); c->kc_idx_nx.reset();
+    c->kc_lab.reset(); c->kc_lab_nx.reset(); c->h0.reset(); c->h0_ccid.reset();
     if (c->mem.arena) cudaFreeAsync(c->mem.arena, c->stream);
     c->mem.arena = nullptr;
     cudaStreamSynchronize(c->stream);
@@ -599,6 +602,20 @@ int dcd::update_impl(dcd_ctx* c, dcd_step_stats* st, dcd_step_stats* per_graph, 
   trace("update: R_t done");
 
   // ---- Algorithm 1 with R_t at level 0 ----
+  // level-0 delta coarsening: usable when K holds G_{t-1} under the start
+  // labels; K is rebuilt for the next update unless a judge may replace the
+  // labels this run commits
+  {
+    const bool on = c->cfg.alg == DCD_ALG_LOUVAIN && c->G == 1 && !c->cfg.coarsen_full;
+    c->n1 = decltype(c->n1){};
+    c->kc_nx_ready = false;
+    c->n1.track = on && !(learned && c->judge);
+    c->n1.usable = on && mode != DCD_MODE_STATIC && c->kc_valid;
+    c->n1.pkey = mo.pkey.get();
+    c->n1.pdelta = mo.pdelta.get();
+    c->n1.P = mo.npairs;
+    c->n1.cprev = c->labels.get();
+  }
   DCD_TRY(c->labels_nx.ensure(&c->mem, n));
   if (collect) DCD_TRY(c->level0.ensure(&c->mem, n));
   // the screening's community sums are those of C_{t-1} on G_t, the start of level 0
@@ -638,6 +655,8 @@ int dcd::update_impl(dcd_ctx* c, dcd_step_stats* st, dcd_step_stats* per_graph, 
   if (st) {
     st->r_screen = r_screen;
     st->pool = (learned || collect) ? c->feat_n : 0;
+    st->coarse0_delta = c->n1.used ? 1 : 0;
+    st->coarse0_entries = c->n1.entries;
   }
 
   // sum_i e_{i->C(i)} of C_t on G_t, kept for the next merge: Louvain's
@@ -659,6 +678,20 @@ int dcd::update_impl(dcd_ctx* c, dcd_step_stats* st, dcd_step_stats* per_graph, 
     std::swap(c->in_prev.mem, c->in_next.mem);
   }
   c->in_valid = keep_in;
+  if (c->kc_nx_ready) {
+    std::swap(c->kc_mat.p, c->kc_mat_nx.p);
+    std::swap(c->kc_mat.n, c->kc_mat_nx.n);
+    std::swap(c->kc_mat.mem, c->kc_mat_nx.mem);
+    std::swap(c->kc_idx.p, c->kc_idx_nx.p);
+    std::swap(c->kc_idx.n, c->kc_idx_nx.n);
+    std::swap(c->kc_idx.mem, c->kc_idx_nx.mem);
+    std::swap(c->kc_lab.p, c->kc_lab_nx.p);
+    std::swap(c->kc_lab.n, c->kc_lab_nx.n);
+    std::swap(c->kc_lab.mem, c->kc_lab_nx.mem);
+    c->kc_n = c->kc_n_nx;
+  }
+  c->kc_valid = c->kc_nx_ready;
+  c->kc_nx_ready = false;
   c->cur = nxt;
   c->nnz = nnz_new;
   std::swap(c->labels.p, c->labels_nx.p);
@@ -744,6 +777,7 @@ int dcd_set_labels(dcd_ctx* c, const int32_t* labels) {
     if (labels[v] < 0 || labels[v] >= c->n) return DCD_EINVAL;
   DCD_SCOPE(c);
   c->in_valid = false;  // the kept sum_i e_{i->C(i)} belongs to the replaced labels
+  c->kc_valid = false;  // and so does the kept coarse graph
   DCD_TRY_CUDA(cudaMemcpyAsync(c->labels.get(), labels, c->n * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
   DCD_TRY_CUDA(cudaStreamSynchronize(c->stream));
   if (c->t == 0) c->t = 1;

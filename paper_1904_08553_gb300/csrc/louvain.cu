@@ -21,6 +21,7 @@
 //   hub_*        longer rows: split into chunks over many CTAs, per-hub tables
 //                in global memory
 #include <cstdio>
+#include <type_traits>
 #include <vector>
 
 #include "agg.cuh"
@@ -1634,6 +1635,7 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
     if (rc != DCD_OK) return rc;
     DCD_TRY_CUDA(ec);
     DCD_TRY_CUDA(cudaGraphInstantiate(&gg.x, gg.g, 0));
+    trace("level: pass loop instantiated");
     if (level == 0) {  // the level-0 bin record (dcd_get_level0_bins)
       c->l0_nb = bins.plan.nb;
       c->l0_side = any && total >= kForkMin;
@@ -1648,6 +1650,7 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
     DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
     DCD_TRY_CUDA(cudaMemcpyAsync(c->hgs, gs, G * sizeof(GraphState), cudaMemcpyDeviceToHost, s));
     DCD_TRY_CUDA(cudaStreamSynchronize(s));
+    trace("level: pass loop ran");
     if (c->hsc->loop_err) {
       note_cuda_error(cudaErrorUnknown, "local-move pass loop passed its cap", __FILE__, __LINE__);
       return DCD_ETIMEOUT;
@@ -1738,18 +1741,312 @@ int launch_emit(dcd_ctx* c, const Csr<W>& g, int64_t m0, const int32_t* ccid, in
   return DCD_OK;
 }
 
+// ---- per-step delta coarsening of level 0 ----
+//
+// R_t changes level 0 only (Sec. III-D); above it the run works on the
+// coarse graph.  The coarse graph of G_t under the level-0 labels L0 equals
+// K (the coarse graph of G_{t-1} under C_{t-1}, kept by the last update),
+// plus every pair's weight change in cell (C_{t-1}(u), C_{t-1}(v)), plus, for
+// every vertex v with L0(v) != C_{t-1}(v), its row moved from the cells of
+// C_{t-1} to those of L0 (with the mirror entries of neighbours that stayed).
+// Level 0 only assigns labels of existing communities, so every label of L0
+// has a row in K; the result is folded onto the compacted ids of L0 and is
+// the same matrix the full emit produces.  Cells are added modulo the width
+// of VT (weight changes can be negative); the final cells are the exact sums.
+
+// Two's-complement sum over the lanes of `peers`, modulo the width of VT.
+__device__ __forceinline__ unsigned peer_sum(unsigned peers, long long x, unsigned) {
+  return __reduce_add_sync(peers, (unsigned)x);
+}
+__device__ __forceinline__ unsigned long long peer_sum(unsigned peers, long long x, unsigned long long) {
+  const unsigned long long u = (unsigned long long)x;
+  unsigned long long sum = 0;
+#pragma unroll
+  for (int q = 0; q < 4; q++)
+    sum += (unsigned long long)__reduce_add_sync(peers, (unsigned)(u >> (16 * q)) & 0xffffu) << (16 * q);
+  return sum;
+}
+
+// One add per distinct cell of the warp (cell < 0: nothing).
+template <typename VT>
+__device__ __forceinline__ void cell_add(VT* D, long long cell, long long x) {
+  const unsigned peers = __match_any_sync(0xffffffffu, (unsigned long long)cell);
+  const VT sum = peer_sum(peers, x, VT(0));
+  if (cell >= 0 && sum != VT(0) && (int)(__ffs(peers) - 1) == (int)lane_id()) atomicAdd(&D[cell], sum);
+}
+
+template <typename VT>
+__global__ void n1_load(const unsigned long long* __restrict__ K, int64_t cells, VT* __restrict__ D) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cells; i += (int64_t)gridDim.x * blockDim.x)
+    D[i] = (VT)K[i];
+}
+
+// The batch: pair (u, v) adds its weight change to cell (C(u), C(v)).
+template <typename VT>
+__global__ void n1_pairs(const uint64_t* __restrict__ pkey, const int64_t* __restrict__ pdelta, int64_t P,
+                         const int32_t* __restrict__ cprev, const int32_t* __restrict__ kidx, int64_t nk,
+                         VT* __restrict__ D, uint32_t* __restrict__ bad) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31u); p0 < P; p0 += stride) {
+    const int64_t p = p0 + lane_id();
+    long long cell = -1, x = 0;
+    if (p < P) {
+      x = pdelta[p];
+      if (x != 0) {
+        const uint64_t k = pkey[p];
+        const long long a = kidx[cprev[(int32_t)(k >> 32)]], b = kidx[cprev[(int32_t)(k & 0xffffffffu)]];
+        if (a >= 0 && b >= 0) cell = a * nk + b;
+        else atomicOr(bad, 1u);
+      }
+    }
+    cell_add(D, cell, x);
+  }
+}
+
+// Vertices whose level-0 label differs from C_{t-1}: their rows as work
+// items of at most kN1Chunk entries (v << 32 | chunk), so that a moved hub
+// does not hold one warp for its whole row.
+constexpr int kN1Chunk = 256;
+
+__global__ void n1_movers_list(int64_t n, const int32_t* __restrict__ L0, const int32_t* __restrict__ cprev,
+                               const int64_t* __restrict__ rp, int64_t* __restrict__ items,
+                               int32_t* __restrict__ cnt, unsigned long long* __restrict__ entries) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int lane = lane_id();
+  for (int64_t b0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31u); b0 < n; b0 += stride) {
+    const int64_t v = b0 + lane;
+    const bool mv = v < n && L0[v] != cprev[v];
+    if (!__any_sync(0xffffffffu, mv)) continue;
+    const int64_t d = mv ? rp[v + 1] - rp[v] : 0;
+    const int nch = (int)((d + kN1Chunk - 1) / kN1Chunk);
+    int incl = nch;  // inclusive prefix of the chunk counts over the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const unsigned long long dsum = peer_sum(0xffffffffu, (long long)d, 0ull);
+    int32_t base = 0;
+    if (lane == 0 && total > 0) {
+      base = atomicAdd(cnt, total);
+      atomicAdd(entries, dsum);
+    }
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int j = 0; j < nch; j++) items[base + incl - nch + j] = (int64_t)v << 32 | (uint32_t)j;
+  }
+}
+
+// A warp per item (a chunk of a moved vertex v's row): entry (v, u, w)
+// leaves cell (C v, C u) for (L0 v, L0 u); when u stayed, its mirror entry
+// (u, v) leaves (C u, C v) for (C u, L0 v).  (When u moved too, u's own row
+// carries the mirror.)
+template <typename VT>
+__global__ void n1_movers(const int64_t* __restrict__ items, const int32_t* __restrict__ cnt,
+                          const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                          const int32_t* __restrict__ w, const int32_t* __restrict__ L0,
+                          const int32_t* __restrict__ cprev, const int32_t* __restrict__ kidx, int64_t nk,
+                          VT* __restrict__ D, uint32_t* __restrict__ bad) {
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t M = *cnt;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < M; i += nw) {
+    const int64_t it = items[i];
+    const int32_t v = (int32_t)(it >> 32);
+    const int64_t b = rp[v] + (int64_t)(uint32_t)it * kN1Chunk;
+    const int64_t rest = rp[v + 1] - b;
+    const int d = rest < kN1Chunk ? (int)rest : kN1Chunk;
+    const long long cv = kidx[cprev[v]], lv = kidx[L0[v]];
+    for (int e0 = 0; e0 < d; e0 += 32) {
+      const int e = e0 + lane_id();
+      long long c1 = -1, c2 = -1, c3 = -1, c4 = -1, x = 0;
+      const int32_t u = e < d ? col[b + e] : 0;
+      const long long cu = e < d ? kidx[cprev[u]] : 0, lu = e < d ? kidx[L0[u]] : 0;
+      if (e < d && (cv < 0 || lv < 0 || cu < 0 || lu < 0)) atomicOr(bad, 1u);
+      else if (e < d) {
+        x = w[b + e];
+        c1 = cv * nk + cu;
+        c2 = lv * nk + lu;
+        if (cu == lu) {
+          c3 = cu * nk + cv;
+          c4 = cu * nk + lv;
+        }
+      }
+      cell_add(D, c1, -x);
+      cell_add(D, c2, x);
+      cell_add(D, c3, -x);
+      cell_add(D, c4, x);
+    }
+  }
+}
+
+// Cell (a, b) of K's index space to (cid(label a), cid(label b)) of L0.
+template <typename VT>
+__global__ void n1_compact(const VT* __restrict__ D, int64_t nk, const int32_t* __restrict__ klab,
+                           const int32_t* __restrict__ cid, const int32_t* __restrict__ L0, int64_t nc,
+                           VT* __restrict__ H, uint32_t* __restrict__ bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nk * nk; i += (int64_t)gridDim.x * blockDim.x) {
+    const VT x = D[i];
+    if (x == VT(0)) continue;
+    // a non-zero cell has members on both sides: their labels are in use
+    const int32_t la = klab[i / nk], lb = klab[i % nk];
+    const int64_t a = cid[la], b = cid[lb];
+    if (a < 0 || a >= nc || b < 0 || b >= nc) {
+      atomicOr(bad, 1u);
+      continue;
+    }
+    H[a * nc + b] = x;
+  }
+}
+
+// K for the next update, from this update's level-0 matrix H (nc0 x nc0):
+// F(i) = the final label of level-1 vertex i (any member's), then the cells
+// of H folded onto the final communities in label order.
+__global__ void n1_final_of(int64_t n, const int32_t* __restrict__ ccid, const int32_t* __restrict__ fin,
+                            int32_t* __restrict__ F, int32_t* __restrict__ used) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    F[ccid[v]] = fin[v];
+    used[fin[v]] = 1;
+  }
+}
+
+__global__ void n1_index(int64_t n, const int32_t* __restrict__ used, const int32_t* __restrict__ idx,
+                         int32_t* __restrict__ kidx, int32_t* __restrict__ klab) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x) {
+    const bool u = used[l] != 0;
+    kidx[l] = u ? idx[l] : -1;
+    if (u) klab[idx[l]] = (int32_t)l;
+  }
+}
+
+template <typename VT>
+__global__ void n1_fold(const VT* __restrict__ H, int64_t nc0, const int32_t* __restrict__ F,
+                        const int32_t* __restrict__ kidx, int64_t nk, unsigned long long* __restrict__ K) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nc0 * nc0;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const VT x = H[i];
+    if (x != VT(0))
+      atomicAdd(&K[(int64_t)kidx[F[i / nc0]] * nk + kidx[F[i % nc0]]], (unsigned long long)x);
+  }
+}
+
+// Level 0's coarse matrix by the delta rule into H (nc x nc, zeroed).
+// *ok false (H unusable) when an index check failed: a label without a row
+// of K, which the rule excludes; the caller then rebuilds from every entry.
+template <typename VT>
+int n1_build(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* L0, const int32_t* cid, int64_t nc, VT* H,
+             unsigned long long* entries, bool* ok) {
+  cudaStream_t s = c->stream;
+  const int T = 256;
+  const int64_t nk = c->kc_n;
+  Buf<VT> D;
+  Buf<int64_t> items;
+  Buf<int32_t> cnt;
+  Buf<uint32_t> bad;
+  DCD_TRY(D.alloc(&c->mem, nk * nk));
+  DCD_TRY(items.alloc(&c->mem, g.n + g.nnz / kN1Chunk + 32));
+  DCD_TRY(cnt.alloc(&c->mem, 1));
+  DCD_TRY(bad.alloc(&c->mem, 1));
+  DCD_TRY_CUDA(cudaMemsetAsync(cnt.get(), 0, sizeof(int32_t), s));
+  DCD_TRY_CUDA(cudaMemsetAsync(bad.get(), 0, sizeof(uint32_t), s));
+  ::dcd::count_launch(), n1_load<VT><<<grid_for(nk * nk, T), T, 0, s>>>(c->kc_mat.get(), nk * nk, D.get());
+  if (c->n1.P > 0)
+    ::dcd::count_launch(), n1_pairs<VT><<<grid_for(c->n1.P, T), T, 0, s>>>(
+        c->n1.pkey, c->n1.pdelta, c->n1.P, c->n1.cprev, c->kc_idx.get(), nk, D.get(), bad.get());
+  ::dcd::count_launch(), n1_movers_list<<<grid_for(g.n, T), T, 0, s>>>(g.n, L0, c->n1.cprev, g.rp, items.get(),
+                                                                        cnt.get(), entries);
+  ::dcd::count_launch(), n1_movers<VT><<<wave_grid(n1_movers<VT>, g.n * 32, T), T, 0, s>>>(
+      items.get(), cnt.get(), g.rp, g.col, g.w, L0, c->n1.cprev, c->kc_idx.get(), nk, D.get(), bad.get());
+  ::dcd::count_launch(), n1_compact<VT><<<grid_for(nk * nk, T), T, 0, s>>>(D.get(), nk, c->kc_lab.get(), cid, L0,
+                                                                            nc, H, bad.get());
+  DCD_LAUNCH_CHECK();
+  DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch + 2, bad.get(), sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch + 3, cnt.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  DCD_TRY_CUDA(cudaStreamSynchronize(s));
+  *ok = *reinterpret_cast<uint32_t*>(c->hscratch + 2) == 0;
+  tracef("level-0 delta rule: %lld pairs, %d row chunks of moved vertices, %lld x %lld kept cells", (long long)c->n1.P,
+         *reinterpret_cast<int32_t*>(c->hscratch + 3), (long long)nk, (long long)nk);
+  return DCD_OK;
+}
+
+// K of this update's final labels (into the *_nx buffers; taken at commit).
+template <typename VT>
+int n1_keep_t(dcd_ctx* c, int64_t n, const int32_t* fin) {
+  cudaStream_t s = c->stream;
+  const int T = 256;
+  const int64_t nc0 = c->n1.h0_nc;
+  Buf<int32_t> F, used, idx;
+  Buf<int32_t> stmp;
+  DCD_TRY(F.alloc(&c->mem, nc0 > 0 ? nc0 : 1));
+  DCD_TRY(used.alloc(&c->mem, n + 1));
+  DCD_TRY(idx.alloc(&c->mem, n + 1));
+  DCD_TRY(stmp.alloc(&c->mem, scan_tmp_count(n + 1) + 1));
+  DCD_TRY_CUDA(cudaMemsetAsync(used.get(), 0, (n + 1) * sizeof(int32_t), s));
+  ::dcd::count_launch(), n1_final_of<<<grid_for(n, T), T, 0, s>>>(n, c->h0_ccid.get(), fin, F.get(), used.get());
+  DCD_LAUNCH_CHECK();
+  DCD_TRY(exclusive_scan<int32_t>(used.get(), idx.get(), n + 1, nullptr, stmp.get(), s));
+  DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch, idx.get() + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  DCD_TRY_CUDA(cudaStreamSynchronize(s));
+  const int64_t nk = *reinterpret_cast<int32_t*>(c->hscratch);
+  if (nk > kDenseNc) return DCD_OK;  // cannot happen (nk <= nc0); kept out of K's size bound
+  DCD_TRY(c->kc_idx_nx.ensure(&c->mem, n));
+  DCD_TRY(c->kc_lab_nx.ensure(&c->mem, nk > 0 ? nk : 1));
+  DCD_TRY(c->kc_mat_nx.ensure(&c->mem, nk * nk > 0 ? nk * nk : 1));
+  DCD_TRY_CUDA(cudaMemsetAsync(c->kc_mat_nx.get(), 0, nk * nk * sizeof(unsigned long long), s));
+  ::dcd::count_launch(), n1_index<<<grid_for(n, T), T, 0, s>>>(n, used.get(), idx.get(), c->kc_idx_nx.get(),
+                                                                c->kc_lab_nx.get());
+  ::dcd::count_launch(), n1_fold<VT><<<grid_for(nc0 * nc0, T), T, 0, s>>>(
+      reinterpret_cast<const VT*>(c->h0.get()), nc0, F.get(), c->kc_idx_nx.get(), nk, c->kc_mat_nx.get());
+  DCD_LAUNCH_CHECK();
+  c->kc_n_nx = nk;
+  c->kc_nx_ready = true;
+  return DCD_OK;
+}
+
+int n1_keep(dcd_ctx* c, int64_t n, const int32_t* fin) {
+  c->kc_nx_ready = false;
+  if (!c->n1.track || !c->n1.h0_ready) return DCD_OK;
+  return c->n1.h0_wide ? n1_keep_t<unsigned long long>(c, n, fin) : n1_keep_t<unsigned>(c, n, fin);
+}
+
 // Dense coarsening (nc <= kDenseNc): matrix, emit, count, scan, write.
 template <typename W, typename VT>
-int coarsen_dense(dcd_ctx* c, const Csr<W>& g, const int32_t* ccid, int64_t nc, CoarseGraph* out) {
+int coarsen_dense(dcd_ctx* c, const Csr<W>& g, const int32_t* ccid, int64_t nc, CoarseGraph* out, bool level0,
+                  const int32_t* L, const int32_t* cid) {
   cudaStream_t s = c->stream;
   const int T = 256;
   const int64_t m0 = g.nnz;
-  Buf<VT> dense;
+  Buf<VT> dense_local;
   Buf<int64_t> stmp;
-  DCD_TRY(dense.alloc(&c->mem, nc * nc));
+  Buf<unsigned long long> ent;
+  VT* dense = nullptr;
+  // level 0 keeps its matrix for the next update's delta coarsening
+  const bool keep = level0 && c->n1.track;
+  if (keep) {
+    DCD_TRY(c->h0.ensure(&c->mem, (size_t)nc * nc * sizeof(VT) + 16));
+    dense = reinterpret_cast<VT*>(c->h0.get());
+    c->n1.h0_nc = nc;
+    c->n1.h0_wide = sizeof(VT) == 8;
+  } else {
+    DCD_TRY(dense_local.alloc(&c->mem, nc * nc));
+    dense = dense_local.get();
+  }
   DCD_TRY(stmp.alloc(&c->mem, scan_tmp_count(nc + 1) + 1));
-  DCD_TRY_CUDA(cudaMemsetAsync(dense.get(), 0, nc * nc * sizeof(VT), s));
-  if (m0 > 0) {
+  DCD_TRY(ent.alloc(&c->mem, 1));
+  DCD_TRY_CUDA(cudaMemsetAsync(dense, 0, nc * nc * sizeof(VT), s));
+  DCD_TRY_CUDA(cudaMemsetAsync(ent.get(), 0, sizeof(unsigned long long), s));
+  bool delta = false;
+  if constexpr (std::is_same<W, int32_t>::value) {
+    if (level0 && c->n1.usable && c->kc_valid) {
+      bool ok = false;
+      DCD_TRY(n1_build<VT>(c, g, L, cid, nc, dense, ent.get(), &ok));
+      delta = ok;
+      if (!ok) {  // rebuild from every entry
+        DCD_TRY_CUDA(cudaMemsetAsync(dense, 0, nc * nc * sizeof(VT), s));
+        DCD_TRY_CUDA(cudaMemsetAsync(ent.get(), 0, sizeof(unsigned long long), s));
+      }
+    }
+  }
+  if (!delta && m0 > 0) {
     // a CTA copy of the matrix when it fits in shared memory (two CTAs an SM)
     const size_t msm = (size_t)nc * nc * sizeof(VT);
     if (msm <= kDenseSmem) {
@@ -1758,48 +2055,67 @@ int coarsen_dense(dcd_ctx* c, const Csr<W>& g, const int32_t* ccid, int64_t nc, 
       const int grid = wave_grid(emit_dense<W, VT, true>, cdiv(m0, 32) * 32, kEmitThreads, msm);
       const int64_t per_warp = cdiv(cdiv(m0, (int64_t)grid * (kEmitThreads / 32)), 32) * 32;
       ::dcd::count_launch(), emit_dense<W, VT, true><<<grid, kEmitThreads, msm, s>>>(
-          g.n, m0, g.rp, g.col, g.w, ccid, (uint32_t)nc, per_warp, dense.get());
+          g.n, m0, g.rp, g.col, g.w, ccid, (uint32_t)nc, per_warp, dense);
     } else {
       const int grid = wave_grid(emit_dense<W, VT, false>, cdiv(m0, 32) * 32, kEmitThreads);
       const int64_t per_warp = cdiv(cdiv(m0, (int64_t)grid * (kEmitThreads / 32)), 32) * 32;
       ::dcd::count_launch(), emit_dense<W, VT, false><<<grid, kEmitThreads, 0, s>>>(
-          g.n, m0, g.rp, g.col, g.w, ccid, (uint32_t)nc, per_warp, dense.get());
+          g.n, m0, g.rp, g.col, g.w, ccid, (uint32_t)nc, per_warp, dense);
     }
     DCD_LAUNCH_CHECK();
   }
   DCD_TRY(out->rp.alloc(&c->mem, nc + 1));
   DCD_TRY_CUDA(cudaMemsetAsync(out->rp.get(), 0, (nc + 1) * sizeof(int64_t), s));
-  ::dcd::count_launch(), dense_count<VT><<<grid_for(nc * 32, T), T, 0, s>>>(dense.get(), nc, out->rp.get());
+  ::dcd::count_launch(), dense_count<VT><<<grid_for(nc * 32, T), T, 0, s>>>(dense, nc, out->rp.get());
   DCD_LAUNCH_CHECK();
   DCD_TRY(exclusive_scan<int64_t>(out->rp.get(), out->rp.get(), nc + 1, nullptr, stmp.get(), s));
   DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch, out->rp.get() + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch + 1, ent.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   DCD_TRY_CUDA(cudaStreamSynchronize(s));
   const int64_t U = c->hscratch[0];
+  if (level0) {
+    c->n1.used = delta;
+    c->n1.entries = delta ? c->n1.P + c->hscratch[1] : m0;
+    c->n1.h0_ready = keep;
+    tracef("level-0 coarse graph: %s, %lld entries read, %lld communities", delta ? "delta rule" : "every entry",
+           (long long)c->n1.entries, (long long)nc);
+  }
   DCD_TRY(out->col.alloc(&c->mem, U));
   DCD_TRY(out->w.alloc(&c->mem, U));
-  ::dcd::count_launch(), dense_write<VT><<<grid_for(nc * 32, T), T, 0, s>>>(dense.get(), nc, out->rp.get(),
+  ::dcd::count_launch(), dense_write<VT><<<grid_for(nc * 32, T), T, 0, s>>>(dense, nc, out->rp.get(),
                                                                              out->col.get(), out->w.get());
   DCD_LAUNCH_CHECK();
   out->view = Csr<int64_t>{nc, U, out->rp.get(), out->col.get(), out->w.get()};
   return DCD_OK;
 }
 
+// level0: the coarsening of G_t's level-0 labels (the delta rule may apply,
+// and the matrix is kept for the next update).
 template <typename W>
-int coarsen(dcd_ctx* c, const Csr<W>& g, const int32_t* L, const int32_t* cid, int64_t nc, CoarseGraph* out) {
+int coarsen(dcd_ctx* c, const Csr<W>& g, const int32_t* L, const int32_t* cid, int64_t nc, CoarseGraph* out,
+            bool level0 = false) {
   cudaStream_t s = c->stream;
   const int T = 256;
   const int64_t m0 = g.nnz;
+  if (level0) c->n1.entries = m0;
   if (nc <= kDenseNc) {
-    Buf<int32_t> ccid;
-    DCD_TRY(ccid.alloc(&c->mem, g.n > 0 ? g.n : 1));
+    Buf<int32_t> ccid_local;
+    int32_t* ccid = nullptr;
+    if (level0 && c->n1.track) {
+      DCD_TRY(c->h0_ccid.ensure(&c->mem, g.n > 0 ? g.n : 1));
+      ccid = c->h0_ccid.get();
+    } else {
+      DCD_TRY(ccid_local.alloc(&c->mem, g.n > 0 ? g.n : 1));
+      ccid = ccid_local.get();
+    }
     if (g.n > 0) {
-      ::dcd::count_launch(), coarse_of<<<grid_for(g.n, T), T, 0, s>>>(g.n, L, cid, ccid.get());
+      ::dcd::count_launch(), coarse_of<<<grid_for(g.n, T), T, 0, s>>>(g.n, L, cid, ccid);
       DCD_LAUNCH_CHECK();
     }
     int64_t m2max = 0;
     for (int x = 0; x < c->G; x++) m2max = c->hgs[x].m2 > m2max ? c->hgs[x].m2 : m2max;
-    if (m2max < ((int64_t)1 << 31)) return coarsen_dense<W, unsigned>(c, g, ccid.get(), nc, out);
-    return coarsen_dense<W, unsigned long long>(c, g, ccid.get(), nc, out);
+    if (m2max < ((int64_t)1 << 31)) return coarsen_dense<W, unsigned>(c, g, ccid, nc, out, level0, L, cid);
+    return coarsen_dense<W, unsigned long long>(c, g, ccid, nc, out, level0, L, cid);
   }
   Buf<uint64_t> k0, k1, v0, v1;
   Buf<int32_t> head, uid;
@@ -2138,7 +2454,7 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
     DCD_TRY_CUDA(cudaMemcpyAsync(gs, c->hgs, G * sizeof(GraphState), cudaMemcpyHostToDevice, s));
     // ---- compact: next level (all graphs together; finished graphs only
     // carry their labels along) ----
-    if (level == 1) DCD_TRY(coarsen<int32_t>(c, *g_l0, L, cid.get(), nc, &cg[nx]));
+    if (level == 1) DCD_TRY(coarsen<int32_t>(c, *g_l0, L, cid.get(), nc, &cg[nx], G == 1));
     else DCD_TRY(coarsen<int64_t>(c, *g_lc, L, cid.get(), nc, &cg[nx]));
     DCD_TRY(kc[nx].alloc(&c->mem, nc));
     DCD_TRY(Lc[nx].alloc(&c->mem, nc));
@@ -2187,6 +2503,7 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
     DCD_TRY_CUDA(cudaMemcpyAsync(c->hgs, gs, G * sizeof(GraphState), cudaMemcpyDeviceToHost, s));
     DCD_TRY_CUDA(cudaStreamSynchronize(s));
   }
+  if (G == 1) DCD_TRY(n1_keep(c, n0, out_labels));
   float tf = 0.f;
   cudaEventElapsedTime(&tf, c->ev[7], c->ev[8]);
   auto fill = [&](dcd_step_stats* o, int x) {

@@ -218,7 +218,7 @@ __global__ void pair_status(const uint64_t* __restrict__ pkey, const int64_t* __
                             int32_t* __restrict__ added, int32_t* __restrict__ removed,
                             int64_t* __restrict__ src_cnt, uint32_t* __restrict__ err,
                             const int32_t* __restrict__ lab0, const int32_t* __restrict__ gid,
-                            int64_t* __restrict__ in_delta) {
+                            int64_t* __restrict__ in_delta, int64_t* __restrict__ pdelta) {
   // warp-uniform trip count: the lanes of a warp sum their in_delta changes
   // per graph before one lane adds them (most pairs of a step add into the
   // same word)
@@ -241,10 +241,11 @@ __global__ void pair_status(const uint64_t* __restrict__ pkey, const int64_t* __
         int64_t nw = (present && !isdel) ? (int64_t)w[pos] + pw[p] : pw[p];
         if (nw > INT32_MAX) atomicOr(err, kErrOverflow);
       }
+      // deletes remove the whole edge first, then inserts add their weight
+      const int64_t w_old = present ? (int64_t)w[pos] : 0;
+      const int64_t w_new = ((present && !isdel) ? w_old : 0) + (isins ? pw[p] : 0);
+      pdelta[p] = w_new - w_old;
       if (lab0 && lab0[u] == lab0[v]) {
-        // deletes remove the whole edge first, then inserts add their weight
-        const int64_t w_old = present ? (int64_t)w[pos] : 0;
-        const int64_t w_new = ((present && !isdel) ? w_old : 0) + (isins ? pw[p] : 0);
         dlt = w_new - w_old;
         graph = graph_of(gid, u);
       }
@@ -612,6 +613,7 @@ int merge_batch(dcd_ctx* c, const int32_t* labels0, bool static_start, MergeOut*
   DCD_TRY(out->pw.alloc(&c->mem, P));
   DCD_TRY(out->pflag.alloc(&c->mem, P));
   DCD_TRY(out->pair_ptr.alloc(&c->mem, n + 1));
+  DCD_TRY(out->pdelta.alloc(&c->mem, P));
   Buf<int32_t> added, removed;
   DCD_TRY(added.alloc(&c->mem, P + 1));
   DCD_TRY(removed.alloc(&c->mem, P + 1));
@@ -638,7 +640,7 @@ int merge_batch(dcd_ctx* c, const int32_t* labels0, bool static_start, MergeOut*
     ::dcd::count_launch(), pair_status<<<grid_for(P, T), T, 0, s>>>(out->pkey.get(), out->pw.get(), out->pflag.get(), P, rp_o, col_o, w_o,
                                              added.get(), removed.get(), out->pair_ptr.get(), err,
                                              from_prev ? labels0 : nullptr, c->G > 1 ? c->gid.get() : nullptr,
-                                             in_delta.get());
+                                             in_delta.get(), out->pdelta.get());
     DCD_LAUNCH_CHECK();
   }
   // pair_ptr: per-source counts -> exclusive scan (n + 1 entries)

@@ -211,6 +211,35 @@ struct dcd_ctx {
   // cleared by anything that replaces C_t other than a Louvain update)
   bool in_valid = false;
   dcd::Buf<int64_t> in_prev, in_next;
+  // Per-step delta coarsening of level 0 (dense coarse graphs only): K is
+  // the coarse graph of G_t under C_t (the last committed labels) as a dense
+  // kc_n x kc_n matrix over the communities of C_t in label order; kc_idx maps
+  // a label to its row (-1: no community); kc_lab is the inverse.  The next
+  // update builds its level-0 coarse graph from K, the batch's weight changes
+  // and the rows of the vertices that changed community at level 0, instead
+  // of from every entry of G_{t+1}.  The *_nx copies are built during an
+  // update and take over at its commit.
+  bool kc_valid = false;
+  int64_t kc_n = 0, kc_n_nx = 0;
+  bool kc_nx_ready = false;
+  dcd::Buf<unsigned long long> kc_mat, kc_mat_nx;
+  dcd::Buf<int32_t> kc_idx, kc_idx_nx, kc_lab, kc_lab_nx;
+  // this update's inputs and level-0 matrix for it
+  struct {
+    bool track = false;            // build K for the next update
+    bool usable = false;           // K holds G_{t-1} under the start labels
+    const uint64_t* pkey = nullptr;  // the batch's pairs and their weight changes
+    const int64_t* pdelta = nullptr;
+    int64_t P = 0;
+    const int32_t* cprev = nullptr;  // C_{t-1}
+    bool used = false;             // this update took the delta path
+    int64_t entries = 0;           // entries the level-0 coarsening read
+    bool h0_ready = false;         // h0 holds this update's level-0 matrix
+    int64_t h0_nc = 0;
+    bool h0_wide = false;          // 64-bit cells
+  } n1;
+  dcd::Buf<unsigned char> h0;      // level-0 dense coarse matrix of this update
+  dcd::Buf<int32_t> h0_ccid;       // level-1 vertex of every vertex
   // level 0 of the last update's local move (dcd_get_level0_bins): active
   // vertices per bin, vertices one sweep of each bin's grid covers, and
   // whether the bins ran side by side
@@ -299,6 +328,7 @@ struct MergeOut {
   Buf<int64_t> pw;         // summed insert weight per pair (0 = no insert)
   Buf<uint8_t> pflag;      // bit0 insert, bit1 delete, bit2 edge was in G_{t-1}
   Buf<int64_t> pair_ptr;   // n + 1: pairs of source u are [pair_ptr[u], pair_ptr[u+1])
+  Buf<int64_t> pdelta;     // per pair: its weight in G_t minus its weight in G_{t-1}
   int64_t npairs = 0;
 };
 int merge_batch(dcd_ctx* c, const int32_t* labels0, bool static_start, MergeOut* out);

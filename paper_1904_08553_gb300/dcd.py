@@ -59,7 +59,8 @@ class Edge(ctypes.Structure):
 
 class Config(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("max_levels", ctypes.c_int32),
-                ("tau_inv", ctypes.c_int32), ("alg", ctypes.c_int32), ("reserved", ctypes.c_int32 * 11)]
+                ("tau_inv", ctypes.c_int32), ("alg", ctypes.c_int32), ("coarsen_full", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 10)]
 
 
 _STAT_I64 = ["t", "n", "nnz", "m2", "r_size", "levels", "iters_total", "iters_level0", "moves_total",
@@ -81,7 +82,9 @@ class StepStats(ctypes.Structure):
                                                             ("edges_level0", ctypes.c_int64),
                                                             ("verts_level0", ctypes.c_int64),
                                                             ("refine_iters", ctypes.c_int64),
-                                                            ("refine_moves", ctypes.c_int64)])
+                                                            ("refine_moves", ctypes.c_int64),
+                                                            ("coarse0_delta", ctypes.c_int64),
+                                                            ("coarse0_entries", ctypes.c_int64)])
 
     @property
     def N(self) -> int:
@@ -414,10 +417,12 @@ class Context(_Bins):
     """One dynamic graph on vertices [0, n) (dcd_ctx)."""
 
     def __init__(self, n: int, mode: int = MODE_DELTA, stream=None, max_iters: int = 500,
-                 max_levels: int = 64, tau_inv: int = 1_000_000, alg: int = ALG_LOUVAIN):
+                 max_levels: int = 64, tau_inv: int = 1_000_000, alg: int = ALG_LOUVAIN,
+                 coarsen_full: bool = False):
         cfg = dcd_config_default()
         cfg.mode, cfg.max_iters, cfg.max_levels, cfg.tau_inv = mode, max_iters, max_levels, tau_inv
         cfg.alg = alg
+        cfg.coarsen_full = 1 if coarsen_full else 0
         self.n = int(n)
         self._h = dcd_create(self.n, cfg, stream)
 
