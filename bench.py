@@ -37,6 +37,24 @@ LFR_STEPS = 12
 METRIC = "ms per time-step update"
 BYTES_PER_ENTRY = 12   # int32 col + int32 weight + int32 neighbour label, per directed entry visited
 BYTES_PER_VERTEX = 40  # row_ptr pair, k, label, a_C, |C|, proposal, list entry per active vertex
+LM_KERNELS = ["lm_seg<8,2> (degree <= 16)", "lm_seg<16,2> (<= 32)", "lm_seg<16,4> (<= 64)",
+              "lm_seg<32,4> (<= 128)", "lm_seg<32,8> (<= 256)", "lm_cta<128,4> (<= 512)",
+              "lm_cta<256,4> (<= 1024)", "lm_cta<512,4> (<= 2048)", "lm_cta<512,8> (<= 4096)",
+              "hub_agg + hub_gain + hub_pick + hub_clear (> 4096)"]
+
+
+def kernel_rows(rows, peak):
+    """Per-kernel roofline rows from dcd_eval_bins: algorithmic bytes of one
+    evaluation of the bin over its isolated CUDA-event time."""
+    out = []
+    for var, nv, ne, ms in rows:
+        if nv == 0:
+            continue
+        by = BYTES_PER_ENTRY * ne + BYTES_PER_VERTEX * nv
+        gbs = by / (ms * 1e-3) / 1e9 if ms > 0 else None
+        out.append({"kernel": LM_KERNELS[var], "vertices": nv, "entries": ne, "ms": ms, "bytes": by,
+                    "gbs": gbs, "frac": (gbs / peak) if gbs else None})
+    return out
 
 
 def workload_desc(n: int = LFR_N) -> str:
@@ -262,14 +280,20 @@ def gpu_arm(args):
         ctx.apply_batch_device(d_ins[t], len(ins), d_del[t], len(dels))
         return ctx.update(labels_out=None)
 
+    # device memory for the stream's largest graph and batch, reserved once
+    # (untimed), so that no update waits on a buffer growing
+    nnz_max = 2 * sum(len(i) for i, _ in stream.steps)
+    rec_max = max(len(i) + len(d) for i, d in stream.steps)
+
     # ---- device-resident inputs ----
     ctx = dcd.Context(n, mode=dcd.MODE_DELTA, stream=ts)
-    run(ctx, 0)
-    if not args.no_autotune:
-        ctx.autotune(reps=3)  # degree-bin plan for this graph (untimed)
-    plan = ctx.bins()
-    for t in range(1, 1 + args.warmup):
+    ctx.reserve(nnz_max, rec_max)
+    tune_after = min(max(args.autotune_at, 1), 1 + args.warmup)
+    for t in range(0, 1 + args.warmup):
         run(ctx, t)
+        if t + 1 == tune_after and not args.no_autotune:
+            ctx.autotune(reps=3)  # degree-bin plan for this graph (untimed)
+    plan = ctx.bins()
     if len(segs) > 1:
         ctx.save(ckpt)
     stats, total_ms, launches = [], 0.0, 0
@@ -278,6 +302,7 @@ def gpu_arm(args):
             if si > 0:  # the state after the warm-up again (untimed)
                 ctx.close()
                 ctx = dcd.Context.load(ckpt, stream=ts)
+                ctx.reserve(nnz_max, rec_max)
             if world > 1:
                 dist.barrier()
             torch.cuda.synchronize()
@@ -293,6 +318,9 @@ def gpu_arm(args):
             total_ms += e0.elapsed_time(e1)
     total_ms = shard.max_over_ranks(total_ms, device=dev)
     clocks = clk.summary()
+    # each degree bin's kernels alone on the last state (untimed): the
+    # per-kernel figures that the side-by-side bins of a pass overlap
+    kernels = kernel_rows(ctx.eval_bins(reps=3), peaks()[0])
     ctx.close()
 
     # ---- end to end through the public API with host buffers ----
@@ -309,6 +337,7 @@ def gpu_arm(args):
             pinned.append((pi, pd))
         lab_host = torch.empty(n, dtype=torch.int32).pin_memory().numpy()
         ctx = dcd.Context(n, mode=dcd.MODE_DELTA, stream=ts)
+        ctx.reserve(nnz_max, rec_max)
         ctx.set_bins(*plan)
         for t in range(0, 1 + args.warmup):
             run(ctx, t, host=True, lab_host=lab_host)
@@ -318,6 +347,7 @@ def gpu_arm(args):
             if si > 0:  # same state as the device-resident leg after its warm-up
                 ctx.close()
                 ctx = dcd.Context.load(ckpt, stream=ts)
+                ctx.reserve(nnz_max, rec_max)
                 torch.cuda.synchronize()
             a = time.perf_counter()
             for t in seg:
@@ -407,6 +437,9 @@ def gpu_arm(args):
             "all_levels_gbs": pass_gbs,
             "all_levels_frac": (pass_gbs / peak) if pass_gbs else None,
             "bins": bins,
+            "kernels_alone": kernels,
+            "kernels_alone_note": ("each bin's kernels timed alone (dcd_eval_bins, CUDA events, mean of 3) "
+                                   "on the last timed state, evaluating every vertex of positive degree"),
         },
         "gpu_launches": int(launches),
         "clocks": clocks,
@@ -848,6 +881,10 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default degree-bin plan (a fixed kernel sequence, for profiling)")
     ap.add_argument("--n", type=int, default=LFR_N, help="vertex count (smaller cases for profiling)")
+    ap.add_argument("--autotune-at", type=int, default=1,
+                    help="tune the degree-bin plan after this many steps (at most 1 + warm-up; untimed). "
+                         "The tuner evaluates every vertex once per candidate plan outside the pass-loop "
+                         "graph, so a later step gives a profiler the local-move kernels on a larger graph")
     ap.add_argument("--workload", default="lfr_2m", choices=["lfr_2m", "learned", "batched", "resolution"])
     ap.add_argument("--graphs", type=int, default=512)
     ap.add_argument("--train-seeds", type=int, default=40)

@@ -229,6 +229,31 @@ int dcd_set_bins(dcd_ctx* ctx, int32_t nb, const int32_t* variant, const int64_t
 int dcd_get_bins(const dcd_ctx* ctx, int32_t* nb, int32_t* variant, int64_t* hi);
 int dcd_autotune(dcd_ctx* ctx, int32_t reps, float* best_ms);
 
+/* Reserves device memory for graphs of up to nnz directed entries (two per
+ * undirected edge) and batches of up to `records` records (inserts plus
+ * deletes staged for one update): both CSR buffers, the batch staging
+ * buffers and the per-update scratch arena.  Updates within those sizes then
+ * take their memory from what is reserved instead of growing buffers on the
+ * way (growth maps new device memory while the update waits); larger graphs
+ * or batches still work, the buffers grow as before.  No counterpart in the
+ * paper: a service for callers that keep allocation out of the update path.
+ * G_t and a staged batch are kept.  Errors: DCD_EINVAL (ctx NULL, nnz or
+ * records negative, records >= 2^30), DCD_ENOMEM, DCD_ECUDA. */
+int dcd_reserve(dcd_ctx* ctx, int64_t nnz, int64_t records);
+
+/* One local-move evaluation (the candidate scan of Algorithm 1's inner loop)
+ * of every vertex of G_t under C_t with the bin plan in force, repeated reps
+ * times with no move applied; each bin's kernels run alone, one bin after
+ * another, timed with CUDA events on the context stream.  For measurement
+ * and profiling: the per-kernel figures the overlapped bins of a pass hide.
+ * Outputs (host, DCD_MAX_BINS entries each): *nb bins; variant[b], verts[b]
+ * (vertices of positive degree in bin b), entries[b] (their degree sum) and
+ * ms[b] (mean time of one evaluation of bin b).  Errors: DCD_EINVAL (a NULL
+ * pointer), DCD_ESTATE (before the first update, reps < 1), DCD_ENOMEM,
+ * DCD_ECUDA. */
+int dcd_eval_bins(dcd_ctx* ctx, int32_t reps, int32_t* nb, int32_t* variant, int64_t* verts, int64_t* entries,
+                  float* ms);
+
 /* Level 0 of the last update's local move (Algorithm 1 over R_t), as run:
  * *nb bins of the plan in force; count[b] the active vertices of bin b;
  * per_sweep[b] the vertices one sweep of bin b's kernel grid covers (a bin

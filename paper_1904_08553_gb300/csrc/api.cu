@@ -221,6 +221,20 @@ int DevMem::begin_step(size_t hint) {
   return DCD_OK;
 }
 
+int DevMem::reserve(size_t bytes) {
+  if (in_step) return DCD_ESTATE;
+  if (arena_size >= bytes) return DCD_OK;
+  if (arena) cudaFreeAsync(arena, stream);
+  arena = nullptr;
+  arena_size = 0;
+  void* q = nullptr;
+  DCD_TRY(alloc_persistent(&q, bytes));
+  arena = static_cast<char*>(q);
+  arena_size = bytes;
+  last_use = 0;
+  return DCD_OK;
+}
+
 void DevMem::end_step() {
   if (in_step) last_use = arena_off + overflow;
   arena_off = 0;
@@ -719,6 +733,29 @@ int dcd::update_impl(dcd_ctx* c, dcd_step_stats* st, dcd_step_stats* per_graph, 
 
 extern "C" {
 
+// Device bytes the step arena of an update needs: G_t of at most nnz_cap
+// entries, a batch of R directed records.
+static size_t step_bytes(const dcd_ctx* c, int64_t nnz_cap, int64_t R) {
+  return (size_t)(40 * nnz_cap + 64 * c->n + 48 * R) + ((size_t)64 << 20);
+}
+
+int dcd_reserve(dcd_ctx* c, int64_t nnz, int64_t records) {
+  if (!c || nnz < 0 || records < 0 || records >= (int64_t)INT32_MAX / 2) return DCD_EINVAL;
+  DCD_SCOPE(c);
+  const int cur = c->cur, nxt = 1 - c->cur;
+  // the buffers of G_t keep their entries; the other pair is empty
+  DCD_TRY(grow_keep(&c->mem, c->col[cur], (size_t)nnz, (size_t)c->nnz, c->stream));
+  DCD_TRY(grow_keep(&c->mem, c->w[cur], (size_t)nnz, (size_t)c->nnz, c->stream));
+  DCD_TRY(c->rp[nxt].ensure(&c->mem, c->n + 1));
+  DCD_TRY(c->col[nxt].ensure(&c->mem, nnz));
+  DCD_TRY(c->w[nxt].ensure(&c->mem, nnz));
+  DCD_TRY(grow_keep(&c->mem, c->ins, (size_t)records, (size_t)c->n_ins, c->stream));
+  DCD_TRY(grow_keep(&c->mem, c->del, (size_t)records, (size_t)c->n_del, c->stream));
+  DCD_TRY(c->mem.reserve(step_bytes(c, nnz, 2 * records)));
+  DCD_TRY_CUDA(cudaStreamSynchronize(c->stream));
+  return DCD_OK;
+}
+
 int dcd_update(dcd_ctx* c, int32_t* labels_out, double* q_out, dcd_step_stats* stats) {
   if (!c) return DCD_EINVAL;
   DCD_SCOPE(c);
@@ -727,7 +764,7 @@ int dcd_update(dcd_ctx* c, int32_t* labels_out, double* q_out, dcd_step_stats* s
   const int64_t launches0 = dcd::g_launches.load();
   const int64_t R = 2 * (c->n_ins + c->n_del);
   const int64_t nnz_cap = c->nnz + 2 * c->n_ins;
-  int rc = c->mem.begin_step((size_t)(40 * nnz_cap + 64 * c->n + 48 * R) + ((size_t)64 << 20));
+  int rc = c->mem.begin_step(step_bytes(c, nnz_cap, R));
   if (rc == DCD_OK) {
     // labels_out is written before the commit: a failed copy fails the step
     const UpdateFinish copy_labels = [](dcd_ctx* cc, void* out) -> int {
@@ -849,6 +886,19 @@ int dcd_autotune(dcd_ctx* c, int32_t reps, float* best_ms) {
   if (!c) return DCD_EINVAL;
   DCD_SCOPE(c);
   return autotune_impl(c, reps, best_ms);
+}
+
+int dcd_eval_bins(dcd_ctx* c, int32_t reps, int32_t* nb, int32_t* variant, int64_t* verts, int64_t* entries,
+                  float* ms) {
+  if (!c || !nb || !variant || !verts || !entries || !ms) return DCD_EINVAL;
+  if (c->t == 0 || reps < 1) return DCD_ESTATE;
+  DCD_SCOPE(c);
+  DCD_TRY(c->mem.begin_step((size_t)(32 * c->n) + ((size_t)64 << 20)));
+  const int k = c->cur;
+  const Csr<int32_t> g{c->n, c->nnz, c->rp[k].get(), c->col[k].get(), c->w[k].get()};
+  const int rc = eval_bins(c, g, c->labels.get(), reps, nb, variant, verts, entries, ms);
+  c->mem.end_step();
+  return rc;
 }
 
 int dcd_set_screen(dcd_ctx* c, dcd_mlp* mlp, float theta_keep, float theta_add, int32_t judge) {

@@ -107,6 +107,7 @@ struct DevMem {
   void release(void* p);                         // no-op for arena memory
   int begin_step(size_t hint);
   void end_step();
+  int reserve(size_t bytes);  // an arena of at least bytes, outside a step
 };
 
 template <typename T>
@@ -153,6 +154,28 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
   return m;
+}
+
+// Loads of data that a pass reads once (CSR columns and weights, bin lists):
+// the streaming cache operator, which allocates the lines evict-first in L1
+// and L2, so that streaming G_t (far larger than L2) does not push out the
+// arrays the same kernels gather from at random (labels, community sums,
+// degrees, row bounds).
+__device__ __forceinline__ int32_t ld_stream(const int32_t* p) {
+  int32_t v;
+  asm("ld.global.cs.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ int64_t ld_stream(const int64_t* p) {
+  int64_t v;
+  asm("ld.global.cs.s64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+
+// Stores of data that the kernel writes once and a later pass reads once
+// (the next CSR): the streaming cache operator, evict-first as above.
+__device__ __forceinline__ void st_stream(int32_t* p, int32_t v) {
+  asm volatile("st.global.cs.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // Multiplicative hash of a label into a power-of-two table.

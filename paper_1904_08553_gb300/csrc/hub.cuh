@@ -58,10 +58,10 @@ __global__ void __launch_bounds__(256) hub_agg(V g, HubTables t) {
     for (int64_t q0 = e0 + wib * 32; q0 < e1; q0 += blockDim.x) {
       const int64_t e = q0 + lane;
       bool valid = e < e1;
-      const int32_t u = valid ? g.col[b + e] : -1;
+      const int32_t u = valid ? ld_stream(g.col + b + e) : -1;
       valid = valid && u != v;
       const int32_t lab = valid ? g.L[u] : -1;
-      const W wt = valid ? g.w[b + e] : W(0);
+      const W wt = valid ? ld_stream(g.w + b + e) : W(0);
       const unsigned peers = __match_any_sync(0xffffffffu, lab);
       const int64_t sum = group_sum<ST>(peers, wt);
       if (valid && (int)(__ffs(peers) - 1) == lane) {

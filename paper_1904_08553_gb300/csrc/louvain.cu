@@ -12,14 +12,16 @@
 // the change of sum_i e_{i->C(i)}, a full reduction gives sum_C a_C^2.
 //
 // Kernels (degree-binned; a bin is a list of active vertex ids, see BinPlan):
-//   lm_warp      rows of at most 32 (or 16) entries: a warp (half warp) per
-//                vertex, labels grouped with match_any, summed with redux.sync
-//   lm_warp_tbl  rows of at most 128 / 256 entries: a warp per vertex with a
-//                warp-private shared table
-//   lm_large     rows of at most 512 .. 4096 entries: a CTA per vertex with a
+//   lm_seg       rows of at most 16 .. 256 entries: a segment of 8, 16 or 32
+//                lanes per vertex, each segment with its own table in shared
+//                memory
+//   lm_cta       rows of at most 512 .. 4096 entries: a CTA per vertex with a
 //                shared table
 //   hub_*        longer rows: split into chunks over many CTAs, per-hub tables
 //                in global memory
+// Compaction (graph of the next level): dense nc x nc sums for few
+// communities, sort-by-key reduction for many; level 0 of an update can be
+// built from the previous update's coarse graph (delta coarsening, below).
 #include <cstdio>
 #include <type_traits>
 #include <vector>
@@ -122,6 +124,20 @@ __device__ __forceinline__ void put_features(const LV<W>& g, int64_t i, int64_t 
 // S lanes per vertex (32 / S vertices a warp), Q entries per lane: rows of at
 // most S x Q entries.  Each segment owns a table in shared memory; the
 // segments of a warp run in lockstep on their own rows.
+//
+// The rows of a segment are software-pipelined, so that the dependent chain
+// list -> row_ptr -> col -> L of a row is spread over several iterations
+// instead of waiting in one.  With Q <= 4 (four stages): while row k is
+// aggregated in the table, the neighbour communities of row k+1 are being
+// gathered (with its k_v, a_C, |C| and 2m), the entries and community of row
+// k+2 loaded, the bounds of row k+3 read and the list entry of row k+4
+// fetched.  With Q = 8 the entries of two rows would not fit the register
+// budget of four resident CTAs, so one stage less: row k's communities are
+// gathered at the start of its iteration, while row k+1's entries, row k+2's
+// bounds and row k+3's list entry are in flight.
+// S lanes per vertex (32 / S vertices a warp), Q entries per lane: rows of at
+// most S x Q entries.  Each segment owns a table in shared memory; the
+// segments of a warp run in lockstep on their own rows.
 template <typename W, typename ST, int S, int Q>
 __global__ void __launch_bounds__(256) lm_seg(LV<W> g, const int32_t* __restrict__ list, int64_t cnt,
                                               int32_t* __restrict__ prop) {
@@ -146,7 +162,7 @@ __global__ void __launch_bounds__(256) lm_seg(LV<W> g, const int32_t* __restrict
   for (int64_t wb = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * P; wb < cnt; wb += nw * P) {
     const int64_t i = wb + sub;
     const bool has = i < cnt;
-    const int32_t v = has ? list[i] : 0;
+    const int32_t v = has ? ld_stream(list + i) : 0;
     const int64_t b = g.rp[v];
     const int d = has ? (int)(g.rp[v + 1] - b) : 0;
     const int dmax = S == 32 ? d : (int)__reduce_max_sync(0xffffffffu, (unsigned)d);
@@ -159,8 +175,8 @@ __global__ void __launch_bounds__(256) lm_seg(LV<W> g, const int32_t* __restrict
       lab[q] = -1;
       wt[q] = W(0);
       if (e < d) {
-        lab[q] = g.col[b + e];
-        wt[q] = g.w[b + e];
+        lab[q] = ld_stream(g.col + b + e);
+        wt[q] = ld_stream(g.w + b + e);
       }
     }
 #pragma unroll
@@ -257,8 +273,8 @@ __global__ void __launch_bounds__(T) lm_cta(LV<W> g, const int32_t* __restrict__
       lab[q] = -1;
       wt[q] = W(0);
       if (e < d) {
-        lab[q] = g.col[b + e];
-        wt[q] = g.w[b + e];
+        lab[q] = ld_stream(g.col + b + e);
+        wt[q] = ld_stream(g.w + b + e);
       }
     }
 #pragma unroll
@@ -544,8 +560,8 @@ __device__ __forceinline__ int64_t moved_row_delta(const LV<W>& g, int32_t x, co
   const int64_t e1 = g.rp[x + 1];
   int64_t acc = 0;
   for (int64_t e = g.rp[x] + tid; e < e1; e += nt) {
-    const int32_t y = g.col[e];
-    const int64_t wt = (int64_t)g.w[e];
+    const int32_t y = ld_stream(g.col + e);
+    const int64_t wt = (int64_t)ld_stream(g.w + e);
     const bool ym = mvit[y] == iter;
     const int32_t ny = g.L[y];
     const int32_t oy = ym ? Lprev[y] : ny;
@@ -896,6 +912,14 @@ __global__ void fill_i32(int32_t* __restrict__ x, int64_t n, int32_t val) {
 __global__ void mark_used(int64_t n, const int32_t* __restrict__ L, int32_t* __restrict__ used) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
     if (!used[L[v]]) used[L[v]] = 1;  // a read first: most labels are already marked
+}
+
+// The same flags from the tracked community sizes: label x is used iff
+// |x| > 0.  A coalesced pass over the labels, where mark_used writes a few
+// hundred hot addresses from every vertex when communities are large.
+__global__ void used_from_size(int64_t n, const int32_t* __restrict__ size, int32_t* __restrict__ used) {
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
+    used[x] = size[x] > 0 ? 1 : 0;
 }
 
 // Row of entry e for the entry-linear walks below: a warp walks a range of
@@ -1690,7 +1714,7 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
 // Compaction of one level: returns nc; fills the coarse graph when nc < n.
 template <typename W>
 int used_labels(dcd_ctx* c, const Csr<W>& g, const int32_t* L, Buf<int32_t>& cid, int64_t* nc,
-                const int32_t* gid, Buf<int32_t>* gid_next) {
+                const int32_t* gid, Buf<int32_t>* gid_next, const int32_t* size = nullptr) {
   cudaStream_t s = c->stream;
   const int T = 256;
   const int64_t nv = g.n;
@@ -1698,7 +1722,8 @@ int used_labels(dcd_ctx* c, const Csr<W>& g, const int32_t* L, Buf<int32_t>& cid
   Buf<int32_t> tmp;
   DCD_TRY(tmp.alloc(&c->mem, scan_tmp_count(nv + 1)));
   DCD_TRY_CUDA(cudaMemsetAsync(cid.get(), 0, (nv + 1) * sizeof(int32_t), s));
-  ::dcd::count_launch(), mark_used<<<grid_for(nv, T), T, 0, s>>>(nv, L, cid.get());
+  if (size) ::dcd::count_launch(), used_from_size<<<grid_for(nv, T), T, 0, s>>>(nv, size, cid.get());
+  else ::dcd::count_launch(), mark_used<<<grid_for(nv, T), T, 0, s>>>(nv, L, cid.get());
   DCD_LAUNCH_CHECK();
   DCD_TRY(exclusive_scan<int32_t>(cid.get(), cid.get(), nv + 1, nullptr, tmp.get(), s));
   ::dcd::count_launch(), gs_reset_nc<<<cdiv(c->G, 128), 128, 0, s>>>(c->gs.get(), c->G);
@@ -1905,7 +1930,7 @@ __global__ void n1_final_of(int64_t n, const int32_t* __restrict__ ccid, const i
                             int32_t* __restrict__ F, int32_t* __restrict__ used) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     F[ccid[v]] = fin[v];
-    used[fin[v]] = 1;
+    if (!used[fin[v]]) used[fin[v]] = 1;  // a read first: few final labels, many vertices
   }
 }
 
@@ -2325,6 +2350,62 @@ int tune_bins(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* L, const BinPlan
   return DCD_OK;
 }
 
+// One local-move evaluation of every vertex of g under L with the plan in
+// force, reps times; each bin's kernels run alone, one bin after another, and
+// are timed with CUDA events on the context stream.  Outputs per bin: vertices,
+// entries (degree sum) and the mean time of one evaluation.  No move is
+// applied.
+int eval_bins(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* L, int reps, int32_t* nb, int32_t* var,
+              int64_t* verts, int64_t* entries, float* ms) {
+  cudaStream_t s = c->stream;
+  const int T = 256;
+  const int64_t n = g.n;
+  Buf<int64_t> k, a;
+  Buf<int32_t> size, prop;
+  DCD_TRY(k.alloc(&c->mem, n));
+  DCD_TRY(a.alloc(&c->mem, n));
+  DCD_TRY(size.alloc(&c->mem, n));
+  DCD_TRY(prop.alloc(&c->mem, n));
+  ::dcd::count_launch(), row_sums<<<grid_for(n * 32, T), T, 0, s>>>(n, g.rp, g.w, k.get());
+  DCD_LAUNCH_CHECK();
+  DCD_TRY(community_sums(c, n, L, k.get(), a.get(), size.get()));
+  int64_t m2max = 0;
+  for (int x = 0; x < c->G; x++) m2max = c->hgs[x].m2 > m2max ? c->hgs[x].m2 : m2max;
+  LV<int32_t> lv{g.rp, g.col, g.w, k.get(), L, a.get(), size.get(), m2max};
+  if (c->G > 1) {
+    lv.gid = c->gid.get();
+    lv.gs = c->gs.get();
+  }
+  Bins bins;
+  DCD_TRY(make_bins<int32_t>(c, g, nullptr, &bins));
+  *nb = bins.plan.nb;
+  struct Events {
+    cudaEvent_t e[kMaxBins] = {};
+    ~Events() {
+      for (auto x : e)
+        if (x) cudaEventDestroy(x);
+    }
+  } end;
+  for (int x = 0; x < bins.plan.nb; x++) {
+    DCD_TRY_CUDA(cudaEventCreate(&end.e[x]));
+    var[x] = bins.plan.var[x];
+    verts[x] = bins.cnt[x];
+    entries[x] = bins.deg[x];
+    ms[x] = 0.f;
+  }
+  if (bins.total) DCD_TRY(launch_lm<int32_t>(c, lv, bins, prop.get()));  // warm-up
+  for (int r = 0; r < reps; r++) {
+    if (bins.total) DCD_TRY(launch_lm<int32_t>(c, lv, bins, prop.get(), end.e));
+    DCD_TRY_CUDA(cudaStreamSynchronize(s));
+    for (int x = 0; x < bins.plan.nb; x++) {
+      float t = 0.f;
+      if (bins.cnt[x]) DCD_TRY_CUDA(cudaEventElapsedTime(&t, c->bin_start[x], end.e[x]));
+      ms[x] += t / (float)reps;
+    }
+  }
+  return DCD_OK;
+}
+
 int community_sums(dcd_ctx* c, int64_t n, const int32_t* labels, const int64_t* k, int64_t* a, int32_t* size) {
   cudaStream_t s = c->stream;
   DCD_TRY_CUDA(cudaMemsetAsync(a, 0, n * sizeof(int64_t), s));
@@ -2423,8 +2504,9 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
     int64_t nc = 0;
     const int nx = which ^ 1;
     Buf<int32_t>* gnext = G > 1 ? &gidc[nx] : nullptr;
-    if (level == 0) DCD_TRY(used_labels<int32_t>(c, *g_l0, L, cid, &nc, gid, gnext));
-    else DCD_TRY(used_labels<int64_t>(c, *g_lc, L, cid, &nc, gid, gnext));
+    // the level's tracked sizes give the used labels
+    if (level == 0) DCD_TRY(used_labels<int32_t>(c, *g_l0, L, cid, &nc, gid, gnext, size.get()));
+    else DCD_TRY(used_labels<int64_t>(c, *g_lc, L, cid, &nc, gid, gnext, size.get()));
     trace("level: labels counted");
     level++;
     // level stop per graph: nothing merged, or (from the second level on) a

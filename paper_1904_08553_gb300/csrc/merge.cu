@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(kMergeThreads) merge_tile(
       }
       u = lo;
     }
-    s_ek[j] = (uint64_t)u << 32 | (uint32_t)col_o[e];
+    s_ek[j] = (uint64_t)u << 32 | (uint32_t)ld_stream(col_o + e);
   }
   __syncthreads();
   int cur_g = -1;
@@ -435,11 +435,11 @@ __global__ void __launch_bounds__(kMergeThreads) merge_tile(
       const uint32_t f = match ? pflag[q] : 0u;
       if (!(f & kPairRemoved)) {
         const int32_t cc = (int32_t)(key & 0xffffffffu);
-        wv = w_o[e];
+        wv = ld_stream(w_o + e);
         if (match && (f & kPairIns)) wv = (f & kPairDel) ? pw[q] : wv + pw[q];
         const int64_t pos = e + pA[q] - pR[q];
-        col_n[pos] = cc;
-        w_n[pos] = (int32_t)wv;
+        st_stream(col_n + pos, cc);
+        st_stream(w_n + pos, (int32_t)wv);
         u = (int64_t)(key >> 32);
         account(u, cc, wv);
       }
@@ -458,8 +458,8 @@ __global__ void __launch_bounds__(kMergeThreads) merge_tile(
         const int32_t cc = (int32_t)(key & 0xffffffffu);
         wv = pw[q];
         const int64_t pos = i + pA[q] - pR[q];
-        col_n[pos] = cc;
-        w_n[pos] = (int32_t)wv;
+        st_stream(col_n + pos, cc);
+        st_stream(w_n + pos, (int32_t)wv);
         u = (int64_t)(key >> 32);
         account(u, cc, wv);
       }

@@ -124,11 +124,11 @@ __device__ __forceinline__ LaneRow lane_row(const SV& g, int32_t v) {
   const int64_t b = g.rp[v];
   const int d = (int)(g.rp[v + 1] - b);
   bool valid = lane < d;
-  const int32_t y = valid ? g.col[b + lane] : -1;
+  const int32_t y = valid ? ld_stream(g.col + b + lane) : -1;
   valid = valid && y != v;
   LaneRow r;
   r.lab = valid ? g.L[y] : -1;
-  r.wt = valid ? g.w[b + lane] : 0;
+  r.wt = valid ? ld_stream(g.w + b + lane) : 0;
   return r;
 }
 
@@ -207,10 +207,10 @@ __device__ __forceinline__ VT slot_table_fill(const SV& g, int32_t v, const Slot
   for (int64_t e0 = 0; e0 < d; e0 += NT) {
     const int64_t e = e0 + tid;
     bool valid = e < d;
-    const int32_t y = valid ? g.col[b + e] : -1;
+    const int32_t y = valid ? ld_stream(g.col + b + e) : -1;
     valid = valid && y != v;
     const int32_t lab = valid ? g.L[y] : -1;
-    const int32_t wt = valid ? g.w[b + e] : 0;
+    const int32_t wt = valid ? ld_stream(g.w + b + e) : 0;
     bool claimed = false;
     uint32_t sl = 0;
     if (valid) {

@@ -381,6 +381,8 @@ int mlp_forward_on(struct dcd_mlp* m, const float* X, int64_t n, float* p, cudaS
 // context's plan.  ms[x] receives candidate x's time per evaluation.
 int tune_bins(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* L, const BinPlan* cands, int ncand, int reps,
               float* ms, int* best);
+int eval_bins(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* L, int reps, int32_t* nb, int32_t* var,
+              int64_t* verts, int64_t* entries, float* ms);
 
 // louvain.cu: community sums a (by label) and sizes from k and labels.
 int community_sums(dcd_ctx* c, int64_t n, const int32_t* labels, const int64_t* k, int64_t* a,

@@ -34,7 +34,7 @@ EXPORTED = [
     "dcd_group_create", "dcd_group_destroy", "dcd_group_apply_batch", "dcd_group_update",
     "dcd_set_bins", "dcd_get_bins", "dcd_autotune", "dcd_group_set_bins", "dcd_group_get_bins",
     "dcd_group_autotune", "dcd_save", "dcd_load", "dcd_get_state", "dcd_mlp_save",
-    "dcd_mlp_load", "dcd_set_fault", "dcd_get_level0_bins",
+    "dcd_mlp_load", "dcd_set_fault", "dcd_get_level0_bins", "dcd_eval_bins", "dcd_reserve",
 ]
 MAX_BINS = 12
 (LM_SEG16, LM_SEG32, LM_SEG64, LM_WARP128, LM_WARP256, LM_CTA512, LM_CTA1K, LM_CTA2K, LM_CTA4K,
@@ -148,6 +148,8 @@ def lib():
             "dcd_get_bins": (INT, [P, P, P, P]),
             "dcd_autotune": (INT, [P, I32, P]),
             "dcd_get_level0_bins": (INT, [P, P, P, P, P]),
+            "dcd_eval_bins": (INT, [P, I32, P, P, P, P, P]),
+            "dcd_reserve": (INT, [P, I64, I64]),
             "dcd_group_set_bins": (INT, [P, I32, P, P]),
             "dcd_group_get_bins": (INT, [P, P, P, P]),
             "dcd_group_autotune": (INT, [P, I32, P]),
@@ -362,6 +364,23 @@ def dcd_get_level0_bins(h):
     return cnt[:nb.value].tolist(), sw[:nb.value].tolist(), bool(side.value)
 
 
+def dcd_reserve(h, nnz: int, records: int) -> None:
+    _check(lib().dcd_reserve(h, int(nnz), int(records)), "dcd_reserve")
+
+
+def dcd_eval_bins(h, reps: int = 3):
+    """One local-move evaluation of every vertex of G_t under C_t, each bin's
+    kernels timed alone: a list of (variant, vertices, entries, ms) per bin."""
+    nb = ctypes.c_int32(0)
+    var = np.zeros(MAX_BINS, np.int32)
+    verts = np.zeros(MAX_BINS, np.int64)
+    ent = np.zeros(MAX_BINS, np.int64)
+    ms = np.zeros(MAX_BINS, np.float32)
+    _check(lib().dcd_eval_bins(h, int(reps), ctypes.byref(nb), var.ctypes.data, verts.ctypes.data,
+                               ent.ctypes.data, ms.ctypes.data), "dcd_eval_bins")
+    return [(int(var[b]), int(verts[b]), int(ent[b]), float(ms[b])) for b in range(nb.value)]
+
+
 def dcd_group_set_bins(h, variants, his) -> None:
     _set_bins(lib().dcd_group_set_bins, h, variants, his)
 
@@ -447,6 +466,16 @@ class Context(_Bins):
         """(count per bin, vertices per grid sweep, side by side) of the last
         update's level-0 local move."""
         return dcd_get_level0_bins(self._h)
+
+    def reserve(self, nnz: int, records: int) -> None:
+        """Reserve device memory for graphs of up to nnz directed entries and
+        batches of up to `records` records (dcd_reserve)."""
+        dcd_reserve(self._h, nnz, records)
+
+    def eval_bins(self, reps: int = 3):
+        """Each degree bin's local-move kernels timed alone on G_t under C_t:
+        [(variant, vertices, entries, ms), ...] (dcd_eval_bins)."""
+        return dcd_eval_bins(self._h, reps)
 
     def close(self):
         if getattr(self, "_h", None):

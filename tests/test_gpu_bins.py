@@ -127,3 +127,63 @@ def test_invalid_plans_are_refused(dcd, variants, his):
         ctx.set_bins(variants, his)
     assert ctx.bins() == before
     ctx.close()
+
+
+def test_eval_bins_counts_every_row_and_keeps_the_state(dcd, synth):
+    """dcd_eval_bins times each bin alone on G_t under C_t: its vertex and
+    entry counts cover every row of positive degree once, and the context
+    (labels, graph) is unchanged by it."""
+    s = lfr_small(synth)
+    ctx = dcd.Context(s.n, mode=dcd.MODE_DELTA)
+    for ins, dels in s.steps[:2]:
+        ctx.apply_batch(ins, dels)
+        lab, _, _ = ctx.update()
+    rp, col, w = ctx.graph()
+    deg = np.diff(rp)
+    plan = ctx.bins()
+    rows = ctx.eval_bins(reps=2)
+    assert [r[0] for r in rows] == plan[0]
+    assert sum(r[1] for r in rows) == int((deg > 0).sum())
+    assert sum(r[2] for r in rows) == int(deg.sum()) == len(col)
+    lo = 0
+    for (var, nv, ne, ms), hi in zip(rows, plan[1]):
+        sel = (deg > lo) & ((deg <= hi) if hi >= 0 else True)
+        assert nv == int(sel.sum()) and ne == int(deg[sel].sum())
+        assert ms >= 0.0 and (ms > 0.0 or nv == 0)
+        lo = hi
+    assert np.array_equal(ctx.labels(), lab)
+    rp2, col2, w2 = ctx.graph()
+    assert np.array_equal(rp, rp2) and np.array_equal(col, col2) and np.array_equal(w, w2)
+    ctx.close()
+
+
+def test_reserve_keeps_results_and_state(dcd, orc, synth):
+    """dcd_reserve only pre-sizes buffers: a context that reserved memory
+    before its first update, and one that reserved in the middle of the
+    stream (G_t and a staged batch kept), give the oracle's results bit for
+    bit; bad sizes are refused."""
+    s = lfr_small(synth)
+    nnz_max = 2 * sum(len(i) for i, _ in s.steps)
+    rec_max = max(len(i) + len(d) for i, d in s.steps)
+    a = dcd.Context(s.n, mode=dcd.MODE_DELTA)
+    a.reserve(nnz_max, rec_max)
+    b = dcd.Context(s.n, mode=dcd.MODE_DELTA)
+    ref = orc.Context(s.n)
+    for bad in ((-1, 10), (10, -1), (10, 1 << 30)):
+        with pytest.raises(dcd.DcdError) as e:
+            a.reserve(*bad)
+        assert e.value.code == dcd.DCD_EINVAL
+    for t, (ins, dels) in enumerate(s.steps):
+        a.apply_batch(ins, dels)
+        b.apply_batch(ins, dels)
+        ref.apply_batch(ins, dels)
+        if t == 2:
+            b.reserve(nnz_max, rec_max)  # a staged batch and G_{t-1} stay
+        la, qa, sa = a.update()
+        lb, qb, sb = b.update()
+        rl, rq, _ = ref.update(orc.DELTA)
+        assert np.array_equal(la, rl) and np.array_equal(lb, rl)
+        assert abs(qa - rq) <= 1e-12 * max(1.0, abs(rq)) and qb == qa
+        assert sa.nnz == sb.nnz
+    a.close()
+    b.close()
