@@ -37,6 +37,11 @@ LFR_STEPS = 12
 METRIC = "ms per time-step update"
 BYTES_PER_ENTRY = 12   # int32 col + int32 weight + int32 neighbour label, per directed entry visited
 BYTES_PER_VERTEX = 40  # row_ptr pair, k, label, a_C, |C|, proposal, list entry per active vertex
+# DRAM bytes per algorithmic byte of the local-move kernels: 525.7 MB of
+# dram__bytes_read.sum + dram__bytes_write.sum over 433.7 MB algorithmic, from
+# the ncu capture of one evaluation of every vertex of the n = 1,000,000
+# stream at t = 7 (the caches cold, as ncu leaves them before each pass)
+LM_TRAFFIC_RATIO = 525.7 / 433.7
 LM_KERNELS = ["lm_seg<8,2> (degree <= 16)", "lm_seg<16,2> (<= 32)", "lm_seg<16,4> (<= 64)",
               "lm_seg<32,4> (<= 128)", "lm_seg<32,8> (<= 256)", "lm_cta<128,4> (<= 512)",
               "lm_cta<256,4> (<= 1024)", "lm_cta<512,4> (<= 2048)", "lm_cta<512,8> (<= 4096)",
@@ -286,7 +291,7 @@ def gpu_arm(args):
     rec_max = max(len(i) + len(d) for i, d in stream.steps)
 
     # ---- device-resident inputs ----
-    ctx = dcd.Context(n, mode=dcd.MODE_DELTA, stream=ts)
+    ctx = dcd.Context(n, mode=dcd.MODE_DELTA, stream=ts, pass_loop_host=args.pass_loop == "host")
     ctx.reserve(nnz_max, rec_max)
     tune_after = min(max(args.autotune_at, 1), 1 + args.warmup)
     for t in range(0, 1 + args.warmup):
@@ -398,6 +403,8 @@ def gpu_arm(args):
     nnz_mean = float(np.mean([s.nnz for s in stats]))
     cpu = cpu_baseline(stream, nnz_mean) if (world == 1 and not args.no_cpu) else None
     cfg = config_of(n)
+    if args.pass_loop == "host":
+        cfg["pass_loop"] = "host (each local-move pass enqueued by the host)"
     cfg.update({"parallelism": "replicas" if world > 1 else "1 GPU",
                 "timed_steps": (f"t={segs[0][0] + 1}..{segs[0][-1] + 1} of 12"
                                 + (f", replayed {len(segs)} times from a checkpoint of the state after the warm-up "
@@ -430,7 +437,11 @@ def gpu_arm(args):
             "kernel": "level-0 local-move evaluation: the degree-bin kernels of a pass (lm_seg, lm_cta, hub_*) over "
                       "R_t on G_t, run side by side",
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": LM_TRAFFIC_RATIO * lm0_bytes / max(passes0, 1),
+            "traffic_note": ("DRAM bytes of one level-0 evaluation: its algorithmic bytes x 1.21, the "
+                             "DRAM-to-algorithmic ratio of an ncu capture of the same kernels at n = 1,000,000 "
+                             "(cold L2, an upper bound for a pass of the timed loop)"),
             "peak_kind": peak_kind,
             "algorithmic_bytes": f"{BYTES_PER_ENTRY} B x entries scanned + {BYTES_PER_VERTEX} B x vertices evaluated",
             "level0_bytes_per_pass": lm0_bytes / max(passes0, 1),
@@ -881,6 +892,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default degree-bin plan (a fixed kernel sequence, for profiling)")
     ap.add_argument("--n", type=int, default=LFR_N, help="vertex count (smaller cases for profiling)")
+    ap.add_argument("--pass-loop", default="device", choices=["device", "host"],
+                    help="host: the host enqueues each local-move pass (dcd_config.pass_loop = 1) instead of "
+                         "one graph launch per level, so that a kernel profiler lists the pass kernels too")
     ap.add_argument("--autotune-at", type=int, default=1,
                     help="tune the degree-bin plan after this many steps (at most 1 + warm-up; untimed). "
                          "The tuner evaluates every vertex once per candidate plan outside the pass-loop "

@@ -76,7 +76,12 @@ typedef struct {
   int32_t coarsen_full; /* 1: build level 0's coarse graph from every entry of G_t in
                            every update; 0 (default): from the previous update's one
                            when it allows (see dcd_step_stats.coarse0_delta)         */
-  int32_t reserved[10];
+  int32_t pass_loop;    /* 0 (default): the passes of a level run as one CUDA-graph
+                           launch, the loop and its stop rule on the device; 1: the
+                           host enqueues each pass and reads the stop rule after it
+                           (same results; for tools that cannot look into a graph's
+                           conditional nodes, such as a kernel profiler)             */
+  int32_t reserved[9];
 } dcd_config;
 
 typedef struct {

@@ -301,7 +301,7 @@ int dcd_create(int64_t n, const dcd_config* cfg, void* cuda_stream, dcd_ctx** ou
   if (cfg) cf = *cfg;
   if (cf.mode < DCD_MODE_STATIC || cf.mode > DCD_MODE_LEARNED || cf.max_iters <= 0 || cf.max_levels <= 0 ||
       cf.tau_inv <= 0 || (cf.alg != DCD_ALG_LOUVAIN && cf.alg != DCD_ALG_SLM) ||
-      (cf.coarsen_full != 0 && cf.coarsen_full != 1))
+      (cf.coarsen_full != 0 && cf.coarsen_full != 1) || (cf.pass_loop != 0 && cf.pass_loop != 1))
     return DCD_EINVAL;
   if (cf.alg == DCD_ALG_SLM && n >= ((int64_t)1 << 30)) return DCD_EINVAL;
   dcd_ctx* c = new (std::nothrow) dcd_ctx();

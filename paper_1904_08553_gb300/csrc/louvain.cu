@@ -729,7 +729,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 __global__ void pass_stamp(DevScalars* d, int k) { d->stamp[k] = global_ns(); }
 
-__global__ void pass_end(DevScalars* d, cudaGraphConditionalHandle h, int32_t cap) {
+__global__ void pass_end(DevScalars* d, cudaGraphConditionalHandle h, int32_t cap, int in_graph) {
   const unsigned long long t = global_ns();
   d->t_eval_ns += d->stamp[1] - d->stamp[0];
   d->t_apply_ns += t - d->stamp[1];
@@ -737,7 +737,8 @@ __global__ void pass_end(DevScalars* d, cudaGraphConditionalHandle h, int32_t ca
   const bool more = d->any_running != 0;
   const bool capped = more && d->level_passes >= cap;
   if (capped) d->loop_err = 1;
-  cudaGraphSetConditional(h, (more && !capped) ? 1u : 0u);
+  // outside a graph the host reads any_running and loop_err after the pass
+  if (in_graph) cudaGraphSetConditional(h, (more && !capped) ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------- binning
@@ -1592,8 +1593,9 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
   // Every pass of a level enqueues the same work (the pass number lives on
   // the device), so the body is captured once, into the body of a 'while'
   // conditional node, and the whole pass loop of the level is one graph
-  // launch.
-  auto enqueue_pass = [&](cudaGraphConditionalHandle h) -> int {
+  // launch.  With dcd_config.pass_loop = 1 the host enqueues the same body
+  // once per pass instead and reads the loop condition back after it.
+  auto enqueue_pass = [&](cudaGraphConditionalHandle h, bool in_graph) -> int {
     ::dcd::count_launch(), gs_reset_pass<<<cdiv(G, 128), 128, 0, s>>>(gs, G, &d->pass_id);
     DCD_TRY_CUDA(cudaMemsetAsync(moved_cnt.get(), 0, sizeof(int32_t), s));
     DCD_TRY_CUDA(cudaMemsetAsync(moved_big_cnt.get(), 0, sizeof(int32_t), s));
@@ -1616,7 +1618,7 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
     ::dcd::count_launch(), sumsq_acc<<<sq_ctas, T, 0, s>>>(a.get(), nv, gid, gs);
     ::dcd::count_launch(), lm_decide<<<cdiv(G, 128), 128, 0, s>>>(gs, G, 1, c->cfg.max_iters, c->cfg.tau_inv,
                                                                    &d->any_running);
-    ::dcd::count_launch(), pass_end<<<1, 1, 0, s>>>(d, h, c->cfg.max_iters + 2);
+    ::dcd::count_launch(), pass_end<<<1, 1, 0, s>>>(d, h, c->cfg.max_iters + 2, in_graph ? 1 : 0);
     DCD_LAUNCH_CHECK();
     return DCD_OK;
   };
@@ -1636,30 +1638,53 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
   } gg;
   gg.s = s;
   {
-    DCD_TRY_CUDA(cudaGraphCreate(&gg.g, 0));
-    cudaGraphConditionalHandle h;
-    // the condition starts at 1 on every launch: a level runs at least one
-    // pass, even with nothing to evaluate, as the sequential definition does
-    DCD_TRY_CUDA(cudaGraphConditionalHandleCreate(&h, gg.g, 1, cudaGraphCondAssignDefault));
-    cudaGraphNodeParams np{};
-    np.type = cudaGraphNodeTypeConditional;
-    np.conditional.handle = h;
-    np.conditional.type = cudaGraphCondTypeWhile;
-    np.conditional.size = 1;
-    cudaGraphNode_t node;
-    DCD_TRY_CUDA(cudaGraphAddNode(&node, gg.g, nullptr, nullptr, 0, &np));
-    cudaGraph_t body = np.conditional.phGraph_out[0];
-    DCD_TRY_CUDA(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    const int64_t l0 = g_launches.load();
-    const int rc = enqueue_pass(h);
-    cudaGraph_t captured = nullptr;
-    const cudaError_t ec = cudaStreamEndCapture(s, &captured);
-    const int64_t body_launches = g_launches.load() - l0;
-    g_launches -= body_launches;  // counted below, once per pass that ran
-    if (rc != DCD_OK) return rc;
-    DCD_TRY_CUDA(ec);
-    DCD_TRY_CUDA(cudaGraphInstantiate(&gg.x, gg.g, 0));
-    trace("level: pass loop instantiated");
+    int64_t body_launches = 0;
+    DCD_TRY_CUDA(cudaMemsetAsync(&d->level_passes, 0, sizeof(int32_t), s));
+    DCD_TRY_CUDA(cudaMemsetAsync(&d->t_eval_ns, 0, 2 * sizeof(unsigned long long), s));
+    if (c->cfg.pass_loop == 0) {
+      DCD_TRY_CUDA(cudaGraphCreate(&gg.g, 0));
+      cudaGraphConditionalHandle h;
+      // the condition starts at 1 on every launch: a level runs at least one
+      // pass, even with nothing to evaluate, as the sequential definition does
+      DCD_TRY_CUDA(cudaGraphConditionalHandleCreate(&h, gg.g, 1, cudaGraphCondAssignDefault));
+      cudaGraphNodeParams np{};
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = h;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      cudaGraphNode_t node;
+      DCD_TRY_CUDA(cudaGraphAddNode(&node, gg.g, nullptr, nullptr, 0, &np));
+      cudaGraph_t body = np.conditional.phGraph_out[0];
+      DCD_TRY_CUDA(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+      const int64_t l0 = g_launches.load();
+      const int rc = enqueue_pass(h, true);
+      cudaGraph_t captured = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(s, &captured);
+      body_launches = g_launches.load() - l0;
+      g_launches -= body_launches;  // counted below, once per pass that ran
+      if (rc != DCD_OK) return rc;
+      DCD_TRY_CUDA(ec);
+      DCD_TRY_CUDA(cudaGraphInstantiate(&gg.x, gg.g, 0));
+      trace("level: pass loop instantiated");
+      DCD_TRY_CUDA(cudaGraphLaunch(gg.x, s));
+      DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+      DCD_TRY_CUDA(cudaMemcpyAsync(c->hgs, gs, G * sizeof(GraphState), cudaMemcpyDeviceToHost, s));
+      DCD_TRY_CUDA(cudaStreamSynchronize(s));
+    } else {
+      // the same pass, enqueued by the host once per pass; the stop rule is
+      // read back after each (pass_end caps the loop as in the graph)
+      for (;;) {
+        const int64_t l0 = g_launches.load();
+        DCD_TRY(enqueue_pass(cudaGraphConditionalHandle{}, false));
+        body_launches = g_launches.load() - l0;
+        g_launches -= body_launches;
+        DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+        DCD_TRY_CUDA(cudaMemcpyAsync(c->hgs, gs, G * sizeof(GraphState), cudaMemcpyDeviceToHost, s));
+        DCD_TRY_CUDA(cudaStreamSynchronize(s));
+        if (c->hsc->loop_err || !c->hsc->any_running) break;
+      }
+    }
+    trace("level: pass loop ran");
     if (level == 0) {  // the level-0 bin record (dcd_get_level0_bins)
       c->l0_nb = bins.plan.nb;
       c->l0_side = any && total >= kForkMin;
@@ -1668,13 +1693,6 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
         c->l0_sweep[x] = x < bins.plan.nb ? sweep[x] : 0;
       }
     }
-    DCD_TRY_CUDA(cudaMemsetAsync(&d->level_passes, 0, sizeof(int32_t), s));
-    DCD_TRY_CUDA(cudaMemsetAsync(&d->t_eval_ns, 0, 2 * sizeof(unsigned long long), s));
-    DCD_TRY_CUDA(cudaGraphLaunch(gg.x, s));
-    DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
-    DCD_TRY_CUDA(cudaMemcpyAsync(c->hgs, gs, G * sizeof(GraphState), cudaMemcpyDeviceToHost, s));
-    DCD_TRY_CUDA(cudaStreamSynchronize(s));
-    trace("level: pass loop ran");
     if (c->hsc->loop_err) {
       note_cuda_error(cudaErrorUnknown, "local-move pass loop passed its cap", __FILE__, __LINE__);
       return DCD_ETIMEOUT;
@@ -1925,13 +1943,26 @@ __global__ void n1_compact(const VT* __restrict__ D, int64_t nk, const int32_t* 
 
 // K for the next update, from this update's level-0 matrix H (nc0 x nc0):
 // F(i) = the final label of level-1 vertex i (any member's), then the cells
-// of H folded onto the final communities in label order.
-__global__ void n1_final_of(int64_t n, const int32_t* __restrict__ ccid, const int32_t* __restrict__ fin,
-                            int32_t* __restrict__ F, int32_t* __restrict__ used) {
+// of H folded onto the final communities in label order.  A final label is
+// its community's smallest member, so label v is in use exactly when
+// fin[v] == v.  The members of a level-1 vertex share one final label: each
+// CTA keeps the first it sees per level-1 vertex in shared memory (nc0 <=
+// 4096 entries) and writes those once, so the few hundred cells of F are not
+// written by every vertex.
+__global__ void n1_final_of(int64_t n, int64_t nc0, const int32_t* __restrict__ ccid,
+                            const int32_t* __restrict__ fin, int32_t* __restrict__ F, int32_t* __restrict__ used) {
+  extern __shared__ int32_t fs[];
+  for (int64_t i = threadIdx.x; i < nc0; i += blockDim.x) fs[i] = -1;
+  __syncthreads();
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-    F[ccid[v]] = fin[v];
-    if (!used[fin[v]]) used[fin[v]] = 1;  // a read first: few final labels, many vertices
+    const int32_t f = fin[v];
+    used[v] = f == (int32_t)v ? 1 : 0;
+    const int32_t c = ccid[v];
+    if (fs[c] < 0) fs[c] = f;  // every writer of fs[c] writes the same value
   }
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < nc0; i += blockDim.x)
+    if (fs[i] >= 0 && F[i] != fs[i]) F[i] = fs[i];
 }
 
 __global__ void n1_index(int64_t n, const int32_t* __restrict__ used, const int32_t* __restrict__ idx,
@@ -2005,8 +2036,13 @@ int n1_keep_t(dcd_ctx* c, int64_t n, const int32_t* fin) {
   DCD_TRY(used.alloc(&c->mem, n + 1));
   DCD_TRY(idx.alloc(&c->mem, n + 1));
   DCD_TRY(stmp.alloc(&c->mem, scan_tmp_count(n + 1) + 1));
-  DCD_TRY_CUDA(cudaMemsetAsync(used.get(), 0, (n + 1) * sizeof(int32_t), s));
-  ::dcd::count_launch(), n1_final_of<<<grid_for(n, T), T, 0, s>>>(n, c->h0_ccid.get(), fin, F.get(), used.get());
+  DCD_TRY_CUDA(cudaMemsetAsync(used.get() + n, 0, sizeof(int32_t), s));
+  {
+    const int64_t blocks = cdiv(n, (int64_t)T);
+    const int grid = (int)(blocks < 4 * c->sms ? blocks : 4 * c->sms);
+    ::dcd::count_launch(), n1_final_of<<<grid > 0 ? grid : 1, T, nc0 * sizeof(int32_t), s>>>(
+        n, nc0, c->h0_ccid.get(), fin, F.get(), used.get());
+  }
   DCD_LAUNCH_CHECK();
   DCD_TRY(exclusive_scan<int32_t>(used.get(), idx.get(), n + 1, nullptr, stmp.get(), s));
   DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch, idx.get() + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));

@@ -60,7 +60,7 @@ class Edge(ctypes.Structure):
 class Config(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("max_levels", ctypes.c_int32),
                 ("tau_inv", ctypes.c_int32), ("alg", ctypes.c_int32), ("coarsen_full", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 10)]
+                ("pass_loop", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
 
 
 _STAT_I64 = ["t", "n", "nnz", "m2", "r_size", "levels", "iters_total", "iters_level0", "moves_total",
@@ -437,11 +437,12 @@ class Context(_Bins):
 
     def __init__(self, n: int, mode: int = MODE_DELTA, stream=None, max_iters: int = 500,
                  max_levels: int = 64, tau_inv: int = 1_000_000, alg: int = ALG_LOUVAIN,
-                 coarsen_full: bool = False):
+                 coarsen_full: bool = False, pass_loop_host: bool = False):
         cfg = dcd_config_default()
         cfg.mode, cfg.max_iters, cfg.max_levels, cfg.tau_inv = mode, max_iters, max_levels, tau_inv
         cfg.alg = alg
         cfg.coarsen_full = 1 if coarsen_full else 0
+        cfg.pass_loop = 1 if pass_loop_host else 0
         self.n = int(n)
         self._h = dcd_create(self.n, cfg, stream)
 

@@ -75,3 +75,8 @@ def test_create_rejects_bad_configurations_before_touching_the_device(libdcd):
     sizes = (ctypes.c_int64 * 2)(10, 20)
     g = ctypes.c_void_p()
     assert L.dcd_group_create(2, sizes, ctypes.byref(cfg), None, ctypes.byref(g)) == libdcd.DCD_EINVAL
+    cfg = libdcd.dcd_config_default()
+    for field in ("coarsen_full", "pass_loop"):  # switches take 0 or 1
+        setattr(cfg, field, 2)
+        assert L.dcd_create(10, ctypes.byref(cfg), None, ctypes.byref(h)) == libdcd.DCD_EINVAL
+        setattr(cfg, field, 0)

@@ -327,3 +327,26 @@ def test_set_labels_mid_stream(dcd, orc, synth):
         rlab, rq, rst = ref.update(orc.DELTA)
         assert_step_equal(st, rst, lab, rlab, q, rq, ctx.rset(), ref.rset())
     ctx.close()
+
+
+def test_host_pass_loop_matches_oracle(dcd, orc, synth):
+    """dcd_config.pass_loop = 1: the host enqueues each local-move pass
+    instead of one graph launch per level.  The results are the oracle's, and
+    equal the device loop's bit for bit, with the same level-0 bin record."""
+    s = synth.lfr(synth.seed_for(1, 7), n=20_000, n_events=400_000, steps=4, kmin=4, kmax=2000,
+                  smin=20, smax=2000)
+    a = dcd.Context(s.n, mode=dcd.MODE_DELTA, pass_loop_host=True)
+    b = dcd.Context(s.n, mode=dcd.MODE_DELTA)
+    ref = orc.Context(s.n)
+    for ins, dels in s.steps:
+        for x in (a, b, ref):
+            x.apply_batch(ins, dels)
+        la, qa, sa = a.update()
+        lb, qb, sb = b.update()
+        rl, rq, rs = ref.update(orc.DELTA)
+        assert_step_equal(sa, rs, la, rl, qa, rq, a.rset(), ref.rset())
+        assert np.array_equal(la, lb) and qa == qb
+        assert (sa.iters_total, sa.moves_total, sa.levels) == (sb.iters_total, sb.moves_total, sb.levels)
+        assert a.level0_bins() == b.level0_bins()
+    a.close()
+    b.close()
