@@ -48,6 +48,14 @@ LM_KERNELS = ["lm_seg<8,2> (degree <= 16)", "lm_seg<16,2> (<= 32)", "lm_seg<16,4
               "hub_agg + hub_gain + hub_pick + hub_clear (> 4096)"]
 
 
+def level0_bytes(st):
+    """Algorithmic bytes the level-0 local-move kernels read in one update:
+    every pass's active entries and vertices, less the first pass's rows whose
+    proposals the screening supplied."""
+    return (BYTES_PER_ENTRY * (st.edges_level0 - st.edges_level0_screen)
+            + BYTES_PER_VERTEX * (st.verts_level0 - st.verts_level0_screen))
+
+
 def kernel_rows(rows, peak):
     """Per-kernel roofline rows from dcd_eval_bins: algorithmic bytes of one
     evaluation of the bin over its isolated CUDA-event time."""
@@ -376,8 +384,10 @@ def gpu_arm(args):
 
     ms_step = total_ms / args.steps
     lm_ms = sum(s.ms_local_move for s in stats)
-    edges = sum(s.edges_scanned for s in stats)
-    verts = sum(s.verts_scanned for s in stats)
+    # entries and vertices the local-move kernels evaluated: the first level-0
+    # pass takes the screening's proposals for the sources it summed
+    edges = sum(s.edges_scanned - s.edges_level0_screen for s in stats)
+    verts = sum(s.verts_scanned - s.verts_level0_screen for s in stats)
     passes = sum(s.iters_total for s in stats)
     gteps = edges / (lm_ms * 1e-3) / 1e9 if lm_ms > 0 else None
     peak, peak_kind = peaks()
@@ -387,7 +397,7 @@ def gpu_arm(args):
     # dominant part of the local move; the upper levels are graphs of a few
     # hundred vertices whose passes are launch-bound
     lm0_ms = sum(s.ms_local_move0 for s in stats)
-    lm0_bytes = sum(BYTES_PER_ENTRY * s.edges_level0 + BYTES_PER_VERTEX * s.verts_level0 for s in stats)
+    lm0_bytes = sum(level0_bytes(s) for s in stats)
     l0_gbs = lm0_bytes / (lm0_ms * 1e-3) / 1e9 if lm0_ms > 0 else None
     passes0 = sum(s.iters_level0 for s in stats)
     # per degree-bin kernel class: its share of the algorithmic bytes (the
@@ -430,6 +440,9 @@ def gpu_arm(args):
             "ms_finish": float(np.mean([s.ms_finish for s in stats])),
             "passes_per_step": passes / len(stats),
             "passes_level0_per_step": passes0 / len(stats),
+            "first_pass_from_screening": float(np.mean([
+                s.verts_level0_screen / (s.verts_level0 / s.iters_level0) if s.iters_level0 and s.verts_level0 else 0.0
+                for s in stats])),
             "ms_local_move_level0": lm0_ms / len(stats),
             "levels": float(np.mean([s.levels for s in stats])),
         },
@@ -530,7 +543,7 @@ def rmat_leg(args):
     ctx.close()
     peak, peak_kind = peaks()
     lm0_ms = sum(s.ms_local_move0 for s in stats)
-    lm0_bytes = sum(BYTES_PER_ENTRY * s.edges_level0 + BYTES_PER_VERTEX * s.verts_level0 for s in stats)
+    lm0_bytes = sum(level0_bytes(s) for s in stats)
     gbs = lm0_bytes / (lm0_ms * 1e-3) / 1e9 if lm0_ms > 0 else None
     return {
         "workload": (f"rmat{args.rmat_scale}: R-MAT scale {args.rmat_scale} ({n:,} vertices, a=0.57 b=c=0.19), "

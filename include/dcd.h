@@ -133,6 +133,12 @@ typedef struct {
                             number at most 4096, after a non-static update        */
   int64_t coarse0_entries; /* entries that built level 0's coarse graph: nnz of G_t,
                               or batch pairs + rows of the moved vertices          */
+  int64_t edges_level0_screen; /* of edges_level0, entries of the first level-0 pass
+                                  not scanned again: Delta-screening sums a source's
+                                  row by community under C_{t-1} on G_t, the state
+                                  that pass reads, and hands over the source's move
+                                  proposal (the same decision)                     */
+  int64_t verts_level0_screen; /* of verts_level0, the vertices it covers             */
 } dcd_step_stats;
 
 typedef struct dcd_ctx dcd_ctx;

@@ -45,6 +45,19 @@ __device__ __forceinline__ i128 shfl_st(i128 x, int src) {
   return (i128)(((unsigned __int128)hi << 64) | lo);
 }
 
+// The move a vertex in community C proposes from its best (S, D) over the
+// neighbouring communities D != C (Algorithm 1's rule, synchronous reading):
+// move iff S > 0 (staying wins ties); a singleton does not move into a
+// singleton of larger label (the minimum-label guard against two singletons
+// swapping).  size: community sizes under the pass's snapshot.
+template <typename ST>
+__device__ __forceinline__ int32_t move_proposal(ST S, int32_t D, int32_t C, const int32_t* size) {
+  const bool mv = D != INT_MAX && S > 0;
+  const int32_t Dm = mv ? D : C;
+  const int32_t sC = size[C], sD = size[Dm];
+  return (mv && sC == 1 && sD == 1 && Dm > C) ? C : Dm;
+}
+
 // (S, D) order of the greedy choice: larger gain first, then smaller label.
 template <typename ST>
 __device__ __forceinline__ bool better(ST s1, int32_t d1, ST s2, int32_t d2) {

@@ -577,12 +577,22 @@ int dcd::update_impl(dcd_ctx* c, dcd_step_stats* st, dcd_step_stats* per_graph, 
   Buf<int64_t> a;
   Buf<int32_t> size;
   LearnedPool lp;
+  // the first level-0 pass of a Delta-screening update reads the state the
+  // screening reads (C_{t-1}, its sums on G_t): the screening hands over its
+  // proposals for the sources whose rows it sums (one Louvain graph)
+  Buf<int32_t> pre;
+  const bool use_pre = mode == DCD_MODE_DELTA && !collect && c->G == 1 && c->cfg.alg == DCD_ALG_LOUVAIN;
   if (mode == DCD_MODE_DELTA || learned || collect) {
     DCD_TRY(a.alloc(&c->mem, n));
     DCD_TRY(size.alloc(&c->mem, n));
     DCD_TRY(rds.alloc(&c->mem, n));
+    if (use_pre) {
+      DCD_TRY(pre.alloc(&c->mem, n));
+      DCD_TRY_CUDA(cudaMemsetAsync(pre.get(), 0xff, n * sizeof(int32_t), s));  // -1: none
+    }
     DCD_TRY(community_sums(c, n, src_labels, mo.k.get(), a.get(), size.get()));
-    DCD_TRY(screen_batch(c, g, src_labels, mo.k.get(), a.get(), mo, rds.get()));
+    DCD_TRY(screen_batch(c, g, src_labels, mo.k.get(), a.get(), mo, rds.get(), size.get(),
+                         use_pre ? pre.get() : nullptr));
     DCD_TRY_CUDA(cudaMemcpyAsync(c->hscratch + 9, &d->r_size, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     DCD_TRY_CUDA(cudaStreamSynchronize(s));
     r_screen = c->hscratch[9];
@@ -638,7 +648,7 @@ int dcd::update_impl(dcd_ctx* c, dcd_step_stats* st, dcd_step_stats* per_graph, 
   else
     DCD_TRY(run_louvain(c, g, L0.get(), active, mo.k, c->labels_nx.get(), st,
                         collect ? c->level0.get() : nullptr, per_graph, a.n ? a.get() : nullptr,
-                        size.n ? size.get() : nullptr));
+                        size.n ? size.get() : nullptr, pre.n ? pre.get() : nullptr));
   if (collect) DCD_TRY(screen_labels(c, src_labels, c->level0.get()));
   if (learned && c->judge && st) {
     // the judge: plain Delta-screening from the same state; keep it when the

@@ -55,6 +55,13 @@ struct LV {
   int64_t* f_eB = nullptr;
   int32_t* f_dB = nullptr;
   double* f_sB = nullptr;
+  // level 0 of a Delta-screening update: pre[v] >= 0 is v's proposal of the
+  // level's first pass, taken by the screening from the same state; while
+  // *first == 0 (no pass of the level has ended) the kernels store it
+  // instead of evaluating v's row again
+  const int32_t* pre = nullptr;
+  const int32_t* first = nullptr;
+  __device__ __forceinline__ int32_t pre_of(int32_t v) const { return (pre && *first == 0) ? pre[v] : -1; }
 };
 
 __device__ __forceinline__ double to_double(long long x) { return (double)x; }
@@ -67,17 +74,9 @@ __device__ __forceinline__ double to_double(i128 x) {
 // The proposal of a vertex from its best (S, D): move on S > 0, subject to
 // the guard.  Evaluated by every lane of the (uniform) argmax result, so the
 // caller stores it with a predicated write instead of a divergent branch.
-__device__ __forceinline__ int32_t proposal(long long S, int32_t D, int32_t C, const int32_t* size) {
-  const bool mv = D != INT_MAX && S > 0;
-  const int32_t Dm = mv ? D : C;
-  const int32_t sC = size[C], sD = size[Dm];
-  return (mv && sC == 1 && sD == 1 && Dm > C) ? C : Dm;
-}
-__device__ __forceinline__ int32_t proposal(i128 S, int32_t D, int32_t C, const int32_t* size) {
-  const bool mv = D != INT_MAX && S > 0;
-  const int32_t Dm = mv ? D : C;
-  const int32_t sC = size[C], sD = size[Dm];
-  return (mv && sC == 1 && sD == 1 && Dm > C) ? C : Dm;
+template <typename ST>
+__device__ __forceinline__ int32_t proposal(ST S, int32_t D, int32_t C, const int32_t* size) {
+  return move_proposal(S, D, C, size);
 }
 
 // ---------------------------------------------------------------- local move
@@ -163,8 +162,9 @@ __global__ void __launch_bounds__(256) lm_seg(LV<W> g, const int32_t* __restrict
     const int64_t i = wb + sub;
     const bool has = i < cnt;
     const int32_t v = has ? ld_stream(list + i) : 0;
+    const int32_t pv = has ? g.pre_of(v) : -1;  // the screening's first-pass proposal
     const int64_t b = g.rp[v];
-    const int d = has ? (int)(g.rp[v + 1] - b) : 0;
+    const int d = (has && pv < 0) ? (int)(g.rp[v + 1] - b) : 0;
     const int dmax = S == 32 ? d : (int)__reduce_max_sync(0xffffffffu, (unsigned)d);
     const int32_t C = g.L[v];
     int32_t lab[Q];
@@ -217,9 +217,9 @@ __global__ void __launch_bounds__(256) lm_seg(LV<W> g, const int32_t* __restrict
       }
     }
     seg_argmax<S>(Sb, D, smask);
-    const int32_t pv = proposal(Sb, D, C, g.size);
+    const int32_t pr = pv >= 0 ? pv : proposal(Sb, D, C, g.size);
     if (sl == 0 && has) {
-      prop[i] = pv;
+      prop[i] = pr;
       if (g.f_eC) put_features(g, i, eC, keys, vals, mask, Sb, D);
     }
     __syncwarp();
@@ -262,8 +262,9 @@ __global__ void __launch_bounds__(T) lm_cta(LV<W> g, const int32_t* __restrict__
   __syncthreads();
   for (int64_t i = blockIdx.x; i < cnt; i += gridDim.x) {
     const int32_t v = list[i];
+    const int32_t pv = g.pre_of(v);  // the screening's first-pass proposal
     const int64_t b = g.rp[v];
-    const int d = (int)(g.rp[v + 1] - b);
+    const int d = pv < 0 ? (int)(g.rp[v + 1] - b) : 0;
     const int32_t C = g.L[v];
     int32_t lab[Q];
     W wt[Q];
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(T) lm_cta(LV<W> g, const int32_t* __restrict__
       D = lane < NW ? redD[lane] : INT_MAX;
       warp_argmax(Sb, D);
       if (lane == 0) {
-        prop[i] = proposal(Sb, D, C, g.size);
+        prop[i] = pv >= 0 ? pv : proposal(Sb, D, C, g.size);
         if (g.f_eC) put_features(g, i, eC, keys, vals, mask, Sb, D);
       }
     }
@@ -751,7 +752,8 @@ __global__ void pass_end(DevScalars* d, cudaGraphConditionalHandle h, int32_t ca
 __global__ void __launch_bounds__(256) bin_count(const int64_t* __restrict__ rp, int64_t n,
                                                  const uint8_t* __restrict__ active, DevScalars* d,
                                                  const int32_t* __restrict__ gid,
-                                                 const GraphState* __restrict__ gs, BinPlan plan) {
+                                                 const GraphState* __restrict__ gs, BinPlan plan,
+                                                 const int32_t* __restrict__ pre) {
   constexpr int NW = 256 / 32;
   __shared__ unsigned long long wc[NW][kMaxBins], wdb[NW][kMaxBins];
   __shared__ long long wmax[NW][kMaxBins];
@@ -762,7 +764,7 @@ __global__ void __launch_bounds__(256) bin_count(const int64_t* __restrict__ rp,
     wmax[wid][b] = 0;
   }
   __syncwarp();
-  unsigned long long deg_sum = 0, act = 0;
+  unsigned long long deg_sum = 0, act = 0, pre_deg = 0, pre_cnt = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (blockIdx.x * (int64_t)blockDim.x) + (threadIdx.x & ~31); base < n; base += stride) {
     const int64_t v = base + lane;
@@ -770,6 +772,12 @@ __global__ void __launch_bounds__(256) bin_count(const int64_t* __restrict__ rp,
     const int64_t deg = ok ? rp[v + 1] - rp[v] : 0;
     deg_sum += (unsigned long long)deg;
     act += ok ? 1 : 0;
+    // a first-pass proposal from the screening, which the table kernels take
+    // (the hub kernels evaluate their rows all the same)
+    if (pre && deg > 0 && pre[v] >= 0 && plan.var[bin_of(plan, deg)] != kLmHub) {
+      pre_deg += (unsigned long long)deg;
+      pre_cnt += 1;
+    }
     const int bin = (ok && deg > 0) ? bin_of(plan, deg) : -1;
     const unsigned peers = __match_any_sync(0xffffffffu, bin);
     const int64_t ds = group_sum_exact(peers, deg);
@@ -783,6 +791,14 @@ __global__ void __launch_bounds__(256) bin_count(const int64_t* __restrict__ rp,
   }
   deg_sum = warp_sum(deg_sum);
   act = warp_sum(act);
+  if (pre) {
+    pre_deg = warp_sum(pre_deg);
+    pre_cnt = warp_sum(pre_cnt);
+    if (lane == 0 && pre_cnt) {
+      atomicAdd((unsigned long long*)&d->pre_deg, pre_deg);
+      atomicAdd((unsigned long long*)&d->pre_verts, pre_cnt);
+    }
+  }
   __syncthreads();
   if (threadIdx.x < plan.nb) {
     const int b = threadIdx.x;
@@ -1328,6 +1344,7 @@ struct LevelRun {
   float ms_lm = 0.f, ms_apply = 0.f;
   float ms_bin[4] = {0.f, 0.f, 0.f, 0.f};
   int64_t edges_bin[4] = {0, 0, 0, 0}, verts_bin[4] = {0, 0, 0, 0};
+  int64_t edges_pre = 0, verts_pre = 0;  // first-pass evaluations the screening supplied
 };
 
 // Degree bins of the active vertices of one level and the hub tables.
@@ -1336,11 +1353,13 @@ struct Bins {
   Buf<int32_t> list;
   int64_t cnt[kMaxBins] = {}, deg[kMaxBins] = {}, maxd[kMaxBins] = {}, off[kMaxBins + 1] = {};
   int64_t total = 0, act_deg = 0, n_active = 0;
+  int64_t pre_verts = 0, pre_deg = 0;  // of them, first-pass proposals from the screening
   HubBufs hub;  // tables of the hub bin (hub.cuh)
 };
 
 template <typename W>
-int make_bins(dcd_ctx* c, const Csr<W>& g, const uint8_t* active, Bins* b, const int32_t* gid = nullptr) {
+int make_bins(dcd_ctx* c, const Csr<W>& g, const uint8_t* active, Bins* b, const int32_t* gid = nullptr,
+              const int32_t* pre = nullptr) {
   cudaStream_t s = c->stream;
   DevScalars* d = c->dsc.get();
   const int64_t nv = g.n;
@@ -1349,7 +1368,8 @@ int make_bins(dcd_ctx* c, const Csr<W>& g, const uint8_t* active, Bins* b, const
   const BinPlan& plan = b->plan;
   DCD_TRY_CUDA(cudaMemsetAsync(&d->act_deg, 0, 2 * sizeof(int64_t), s));  // act_deg, ncomm
   DCD_TRY_CUDA(cudaMemsetAsync(&d->bcnt[0], 0, 3 * kMaxBins * sizeof(int64_t), s));  // bcnt, bdeg, bmax
-  ::dcd::count_launch(), bin_count<<<grid_for(nv, T), T, 0, s>>>(g.rp, nv, active, d, gid, c->gs.get(), plan);
+  DCD_TRY_CUDA(cudaMemsetAsync(&d->pre_verts, 0, 2 * sizeof(int64_t), s));           // pre_verts, pre_deg
+  ::dcd::count_launch(), bin_count<<<grid_for(nv, T), T, 0, s>>>(g.rp, nv, active, d, gid, c->gs.get(), plan, pre);
   DCD_LAUNCH_CHECK();
   DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
   DCD_TRY_CUDA(cudaStreamSynchronize(s));
@@ -1364,6 +1384,8 @@ int make_bins(dcd_ctx* c, const Csr<W>& g, const uint8_t* active, Bins* b, const
   b->off[plan.nb] = b->total;
   b->act_deg = c->hsc->act_deg;
   b->n_active = c->hsc->ncomm;  // bin_count leaves the active count here
+  b->pre_verts = c->hsc->pre_verts;
+  b->pre_deg = c->hsc->pre_deg;
   Buf<int32_t> cursor;
   DCD_TRY(b->list.alloc(&c->mem, b->total));
   DCD_TRY(cursor.alloc(&c->mem, kMaxBins));
@@ -1545,7 +1567,8 @@ struct GraphTally {
 
 template <typename W>
 int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<int64_t>& a, Buf<int32_t>& size,
-              const uint8_t* active, const int32_t* gid, int level, LevelRun* out, GraphTally* tally) {
+              const uint8_t* active, const int32_t* gid, int level, LevelRun* out, GraphTally* tally,
+              const int32_t* pre = nullptr) {
   cudaStream_t s = c->stream;
   DevScalars* d = c->dsc.get();
   GraphState* gs = c->gs.get();
@@ -1559,7 +1582,7 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
                                                                  &d->any_running);
   DCD_LAUNCH_CHECK();
   Bins bins;
-  DCD_TRY(make_bins<W>(c, g, active, &bins, gid));
+  DCD_TRY(make_bins<W>(c, g, active, &bins, gid, pre));
   trace("level: binned");
   const int64_t total = bins.total;
   // list positions from big_from on hold rows longer than 256 entries: their
@@ -1582,6 +1605,10 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
   LV<W> lv{g.rp, g.col, g.w, kbuf.get(), L, a.get(), size.get(), G == 1 ? c->hgs[0].m2 : 0};
   lv.gid = gid;
   lv.gs = gid ? gs : nullptr;
+  if (pre) {  // the first pass takes the screening's proposals
+    lv.pre = pre;
+    lv.first = &d->level_passes;
+  }
   int64_t m2max = 0;
   for (int x = 0; x < G; x++) m2max = c->hgs[x].m2 > m2max ? c->hgs[x].m2 : m2max;
   LV<W> lvl = lv;
@@ -1704,6 +1731,8 @@ int run_level(dcd_ctx* c, const Csr<W>& g, int32_t* L, Buf<int64_t>& kbuf, Buf<i
     out->ms_apply = (float)(c->hsc->t_apply_ns * 1e-6);
     out->edges = bins.act_deg * passes;
     out->verts = bins.n_active * passes;
+    out->edges_pre = pre ? bins.pre_deg : 0;
+    out->verts_pre = pre ? bins.pre_verts : 0;
     for (int x = 0; x < bins.plan.nb; x++) {
       const int k = lm_variant_class(bins.plan.var[x]);
       out->edges_bin[k] += bins.deg[x] * passes;
@@ -2454,7 +2483,7 @@ int community_sums(dcd_ctx* c, int64_t n, const int32_t* labels, const int64_t* 
 
 int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint8_t* active0, Buf<int64_t>& k0,
                 int32_t* out_labels, dcd_step_stats* st, int32_t* level0_out, dcd_step_stats* per_graph,
-                const int64_t* a0, const int32_t* size0) {
+                const int64_t* a0, const int32_t* size0, const int32_t* pre0) {
   cudaStream_t s = c->stream;
   GraphState* gs = c->gs.get();
   const int G = c->G;
@@ -2489,7 +2518,7 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
   float ms_bin[4] = {0.f, 0.f, 0.f, 0.f};
   int64_t edges_bin[4] = {0, 0, 0, 0}, verts_bin[4] = {0, 0, 0, 0};
   float ms_lm = 0.f, ms_apply = 0.f, ms_coarsen = 0.f, ms_lm0 = 0.f;
-  int64_t edges0 = 0, verts0 = 0;
+  int64_t edges0 = 0, verts0 = 0, edges0_pre = 0, verts0_pre = 0;
   bool first_level = true;
 
   // current level: level 0 uses g0 / labels0 / k0; later levels own their data
@@ -2508,7 +2537,7 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
   for (;;) {
     LevelRun lr;
     if (level == 0) {
-      DCD_TRY(run_level<int32_t>(c, *g_l0, L, *kcur, a, size, active, gid, (int)level, &lr, &tally));
+      DCD_TRY(run_level<int32_t>(c, *g_l0, L, *kcur, a, size, active, gid, (int)level, &lr, &tally, pre0));
       if (level0_out)
         DCD_TRY_CUDA(cudaMemcpyAsync(level0_out, L, n0 * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     } else {
@@ -2524,6 +2553,8 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
       ms_lm0 = lr.ms_lm;
       edges0 = lr.edges;
       verts0 = lr.verts;
+      edges0_pre = lr.edges_pre;
+      verts0_pre = lr.verts_pre;
     }
     edges_total += lr.edges;
     verts_total += lr.verts;
@@ -2667,6 +2698,8 @@ int run_louvain(dcd_ctx* c, const Csr<int32_t>& g0, int32_t* labels0, const uint
     st->ms_local_move0 = ms_lm0;
     st->edges_level0 = edges0;
     st->verts_level0 = verts0;
+    st->edges_level0_screen = edges0_pre;
+    st->verts_level0_screen = verts0_pre;
     st->ms_apply = ms_apply;
     st->ms_coarsen = ms_coarsen;
     st->ms_finish = tf;
@@ -3073,7 +3106,8 @@ struct SlmLevel {
     plan.hi[1] = INT64_MAX;
     DCD_TRY_CUDA(cudaMemsetAsync(&d->act_deg, 0, 2 * sizeof(int64_t), s));
     DCD_TRY_CUDA(cudaMemsetAsync(&d->bcnt[0], 0, 3 * kMaxBins * sizeof(int64_t), s));
-    ::dcd::count_launch(), bin_count<<<grid_for(n, T), T, 0, s>>>(g.rp, n, active, d, nullptr, nullptr, plan);
+    ::dcd::count_launch(), bin_count<<<grid_for(n, T), T, 0, s>>>(g.rp, n, active, d, nullptr, nullptr, plan,
+                                                                   nullptr);
     DCD_LAUNCH_CHECK();
     DCD_TRY_CUDA(cudaMemcpyAsync(c->hsc, d, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
     DCD_TRY_CUDA(cudaStreamSynchronize(s));

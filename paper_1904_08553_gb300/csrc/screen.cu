@@ -51,6 +51,13 @@ struct SV {
   int32_t* jstar;
   long long* g1;   // two words per source (low, high) of gain1
   uint8_t* flags;  // bit0: intra-community delete (mark Gamma(i)); bit1: winner
+  // first-pass proposals (may be NULL): phase A sums a source's row by
+  // community under C_{t-1} on G_t, the state the first local-move pass of
+  // level 0 reads, so it also takes that pass's choice for the source (the
+  // best neighbouring community, the S > 0 rule and the singleton guard) and
+  // stores it in pre[source]; sources it does not sum keep -1
+  const int32_t* size;
+  int32_t* pre;
 };
 
 // (S, D, j) order of the j* choice: larger gain, then smaller C(j), then smaller j.
@@ -297,6 +304,22 @@ __global__ void __launch_bounds__(256) scr_a_warp(SV g, int64_t off, int64_t cnt
       const LaneRow r = lane_row(g, u);
       const int64_t eC = lane_get<ST>(r, C);
       const int64_t ku = g.k[u], aC = g.a[C];
+      if (g.pre) {
+        // the local move's choice (the lanes hold the row): lanes grouped by
+        // neighbouring community, the first lane of each group takes its
+        // gain, one argmax over the warp
+        const bool cand = r.lab >= 0 && r.lab != C;
+        const unsigned peers = __match_any_sync(0xffffffffu, cand ? r.lab : -1);
+        const int64_t el = group_sum<ST>(peers, r.wt);
+        ST Sb = gain_lowest<ST>();
+        int32_t Db = INT_MAX;
+        if (cand && (int)(__ffs(peers) - 1) == lane) {
+          Sb = gain<ST>(g.m2_of(u), ku, el, eC, g.a[r.lab], aC);
+          Db = r.lab;
+        }
+        warp_argmax(Sb, Db);
+        if (lane == 0) g.pre[u] = move_proposal(Sb, Db, C, g.size);
+      }
       int32_t D = INT_MAX;
       J = INT_MAX;
       S = gain_lowest<ST>();
@@ -351,6 +374,22 @@ __global__ void __launch_bounds__(256) scr_a_wtbl(SV g, int64_t off, int64_t cnt
       __syncwarp();
       const int64_t eC = seg_total<32>(own, 0xffffffffu);
       const int64_t ku = g.k[u], aC = g.a[C];
+      if (g.pre) {  // the local move's choice over the table's communities
+        ST Sb = gain_lowest<ST>();
+        int32_t Db = INT_MAX;
+        const int nd = *t.ns;
+        for (int x = lane; x < nd; x += 32) {
+          const uint32_t sl = t.slots[x];
+          const int32_t key = t.keys[sl];
+          const ST y = gain<ST>(g.m2_of(u), ku, (int64_t)t.vals[sl], eC, g.a[key], aC);
+          if (better(y, key, Sb, Db)) {
+            Sb = y;
+            Db = key;
+          }
+        }
+        warp_argmax(Sb, Db);
+        if (lane == 0) g.pre[u] = move_proposal(Sb, Db, C, g.size);
+      }
       int32_t D = INT_MAX;
       J = INT_MAX;
       S = gain_lowest<ST>();
@@ -390,6 +429,8 @@ __global__ void __launch_bounds__(THREADS) scr_a_block(SV g, int64_t off, int64_
   __shared__ ST redS[NW];
   __shared__ int32_t redD[NW], redJ[NW];
   __shared__ VT redE[NW];
+  __shared__ ST preS[NW];
+  __shared__ int32_t preD[NW];
   __shared__ int s_flags;
   const int tid = threadIdx.x, lane = lane_id(), wid = tid >> 5;
   const SlotTable<VT> t = slot_table<VT>(smem, cap);
@@ -414,6 +455,25 @@ __global__ void __launch_bounds__(THREADS) scr_a_block(SV g, int64_t off, int64_
       const VT own = slot_table_fill<ST, VT>(g, u, t, mask, tid, THREADS, C);
       const int64_t eC = cta_total<NW>(own, redE);
       const int64_t ku = g.k[u], aC = g.a[C];
+      if (g.pre) {  // the local move's choice over the table's communities
+        ST Sb = gain_lowest<ST>();
+        int32_t Db = INT_MAX;
+        const int nd = *t.ns;
+        for (int x = tid; x < nd; x += THREADS) {
+          const uint32_t sl = t.slots[x];
+          const int32_t key = t.keys[sl];
+          const ST y = gain<ST>(g.m2_of(u), ku, (int64_t)t.vals[sl], eC, g.a[key], aC);
+          if (better(y, key, Sb, Db)) {
+            Sb = y;
+            Db = key;
+          }
+        }
+        warp_argmax(Sb, Db);
+        if (lane == 0) {
+          preS[wid] = Sb;
+          preD[wid] = Db;
+        }
+      }
       int32_t D = INT_MAX;
       J = INT_MAX;
       S = gain_lowest<ST>();
@@ -439,6 +499,12 @@ __global__ void __launch_bounds__(THREADS) scr_a_block(SV g, int64_t off, int64_
       D = lane < NW ? redD[lane] : INT_MAX;
       J = lane < NW ? redJ[lane] : INT_MAX;
       warp_argmax3(S, D, J);
+      if (g.pre && wid == 0) {
+        ST Sb = lane < NW ? preS[lane] : gain_lowest<ST>();
+        int32_t Db = lane < NW ? preD[lane] : INT_MAX;
+        warp_argmax(Sb, Db);
+        if (lane == 0) g.pre[u] = move_proposal(Sb, Db, C, g.size);
+      }
       slot_table_clear(t, tid, THREADS);
       __syncthreads();
       if (tid == 0) *t.ns = 0;
@@ -944,7 +1010,7 @@ int screen_impl(dcd_ctx* c, SV& sv, const Csr<int32_t>& g, const int64_t* cnt, i
 }  // namespace
 
 int screen_batch(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* labels0, const int64_t* k, const int64_t* a,
-                 const MergeOut& mo, uint8_t* rset) {
+                 const MergeOut& mo, uint8_t* rset, const int32_t* size, int32_t* pre) {
   cudaStream_t s = c->stream;
   DevScalars* d = c->dsc.get();
   const int64_t n = g.n;
@@ -980,7 +1046,7 @@ int screen_batch(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* labels0, cons
     for (int x = 0; x < c->G; x++) m2max = c->hgs[x].m2 > m2max ? c->hgs[x].m2 : m2max;
     SV sv{g.rp, g.col, g.w, k, labels0, a, mo.pkey.get(), mo.pflag.get(), mo.pair_ptr.get(), c->hgs[0].m2,
           c->G > 1 ? c->gid.get() : nullptr, c->gs.get(), mark.get(), cflag.get(), src.get(), jstar.get(),
-          g1.get(), flags.get()};
+          g1.get(), flags.get(), size, pre};
     if (m2max >= ((int64_t)1 << 31)) DCD_TRY(screen_impl<i128>(c, sv, g, cnt, nsrc));
     else DCD_TRY(screen_impl<long long>(c, sv, g, cnt, nsrc));
   }

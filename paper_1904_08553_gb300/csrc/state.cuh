@@ -41,6 +41,8 @@ struct DevScalars {
   unsigned long long t_eval_ns, t_apply_ns;  // a level's evaluation and apply time, summed over its passes
   int32_t loop_err;  // the device pass loop hit its hard cap (cannot happen: the stop rule ends it first)
   int32_t pad3;
+  int64_t pre_verts;  // level 0: active vertices whose first-pass proposal the screening made
+  int64_t pre_deg;    // and the sum of their degrees
 };
 
 // Per-graph state of one update.  A context holds G graphs on disjoint vertex
@@ -334,8 +336,12 @@ struct MergeOut {
 int merge_batch(dcd_ctx* c, const int32_t* labels0, bool static_start, MergeOut* out);
 
 // screen.cu: Algorithm 2 plus the deletion rule -> rset (n bytes).
+// size and pre may be NULL; with pre, the first local-move pass's proposal of
+// every source whose row phase A sums is written to pre[source] (others -1;
+// the caller fills pre with -1).
 int screen_batch(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* labels0, const int64_t* k,
-                 const int64_t* a, const MergeOut& mo, uint8_t* rset);
+                 const int64_t* a, const MergeOut& mo, uint8_t* rset, const int32_t* size = nullptr,
+                 int32_t* pre = nullptr);
 
 // louvain.cu: Algorithm 1 from level-0 labels (modified in place into the
 // level-0 result), level-0 active flags (NULL = all), k and m2 of G_t.
@@ -343,7 +349,8 @@ int screen_batch(dcd_ctx* c, const Csr<int32_t>& g, const int32_t* labels0, cons
 // a0 / size0 (may be NULL): community sums of labels0, when the caller has them.
 int run_louvain(dcd_ctx* c, const Csr<int32_t>& g, int32_t* labels0, const uint8_t* active0,
                 Buf<int64_t>& k, int32_t* out_labels, dcd_step_stats* st, int32_t* level0_out = nullptr,
-                dcd_step_stats* per_graph = nullptr, const int64_t* a0 = nullptr, const int32_t* size0 = nullptr);
+                dcd_step_stats* per_graph = nullptr, const int64_t* a0 = nullptr, const int32_t* size0 = nullptr,
+                const int32_t* pre0 = nullptr);
 
 // louvain.cu: multi-level smart local moving (dSLM) from level-0 labels and
 // level-0 active flags (NULL = all), k and 2m of G_t (one graph a context).

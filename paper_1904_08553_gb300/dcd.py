@@ -84,7 +84,9 @@ class StepStats(ctypes.Structure):
                                                             ("refine_iters", ctypes.c_int64),
                                                             ("refine_moves", ctypes.c_int64),
                                                             ("coarse0_delta", ctypes.c_int64),
-                                                            ("coarse0_entries", ctypes.c_int64)])
+                                                            ("coarse0_entries", ctypes.c_int64),
+                                                            ("edges_level0_screen", ctypes.c_int64),
+                                                            ("verts_level0_screen", ctypes.c_int64)])
 
     @property
     def N(self) -> int:

@@ -51,8 +51,8 @@ def test_status_text_and_defaults(libdcd):
 def test_struct_layouts_match_header(libdcd):
     assert ctypes.sizeof(libdcd.Edge) == 12
     assert ctypes.sizeof(libdcd.Config) == 64
-    # 14 int64 + double + 6 int64 + double + 16 float + 8 int64 + 2 float + 4 int64
-    assert ctypes.sizeof(libdcd.StepStats) == 14 * 8 + 8 + 6 * 8 + 8 + 16 * 4 + 8 * 8 + 2 * 4 + 4 * 8 + 2 * 8
+    # 14 int64 + double + 6 int64 + double + 16 float + 8 int64 + 2 float + 8 int64
+    assert ctypes.sizeof(libdcd.StepStats) == 14 * 8 + 8 + 6 * 8 + 8 + 16 * 4 + 8 * 8 + 2 * 4 + 4 * 8 + 4 * 8
 
 
 def test_create_rejects_bad_n_before_touching_the_device(libdcd):

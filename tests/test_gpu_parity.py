@@ -350,3 +350,32 @@ def test_host_pass_loop_matches_oracle(dcd, orc, synth):
         assert a.level0_bins() == b.level0_bins()
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("mode", ["delta", "base"])
+def test_first_pass_proposals_from_screening(dcd, orc, synth, mode):
+    """A Delta-screening update's first level-0 pass reads the state the
+    screening reads (C_{t-1} and its sums on G_t), so the screening hands over
+    its proposals for the sources whose rows it sums and the pass skips those
+    rows.  The results stay the oracle's, bit for bit; the hand-over covers
+    part of one pass in DELTA mode and nothing in BASE mode (no screening) or
+    in the static first update."""
+    s = synth.lfr(synth.seed_for(1, 7), n=20_000, n_events=400_000, steps=4, kmin=4, kmax=2000,
+                  smin=20, smax=2000)
+    m, om = {"delta": (dcd.MODE_DELTA, orc.DELTA), "base": (dcd.MODE_BASE, orc.BASE)}[mode]
+    ctx = dcd.Context(s.n, mode=m)
+    ref = orc.Context(s.n)
+    for t, (ins, dels) in enumerate(s.steps):
+        ctx.apply_batch(ins, dels)
+        ref.apply_batch(ins, dels)
+        lab, q, st = ctx.update()
+        rlab, rq, rst = ref.update(om)
+        assert_step_equal(st, rst, lab, rlab, q, rq, ctx.rset(), ref.rset())
+        one_pass_v = st.verts_level0 // max(st.iters_level0, 1)
+        one_pass_e = st.edges_level0 // max(st.iters_level0, 1)
+        if mode == "delta" and t > 0:
+            assert 0 < st.verts_level0_screen <= one_pass_v, (st.verts_level0_screen, one_pass_v)
+            assert 0 < st.edges_level0_screen <= one_pass_e
+        else:
+            assert st.verts_level0_screen == 0 and st.edges_level0_screen == 0
+    ctx.close()
