@@ -37,11 +37,11 @@ LFR_STEPS = 12
 METRIC = "ms per time-step update"
 BYTES_PER_ENTRY = 12   # int32 col + int32 weight + int32 neighbour label, per directed entry visited
 BYTES_PER_VERTEX = 40  # row_ptr pair, k, label, a_C, |C|, proposal, list entry per active vertex
-# DRAM bytes per algorithmic byte of the local-move kernels: 525.7 MB of
+# DRAM bytes per algorithmic byte of the local-move kernels: 525.9 MB of
 # dram__bytes_read.sum + dram__bytes_write.sum over 433.7 MB algorithmic, from
 # the ncu capture of one evaluation of every vertex of the n = 1,000,000
 # stream at t = 7 (the caches cold, as ncu leaves them before each pass)
-LM_TRAFFIC_RATIO = 525.7 / 433.7
+LM_TRAFFIC_RATIO = 525.9 / 433.7
 LM_KERNELS = ["lm_seg<8,2> (degree <= 16)", "lm_seg<16,2> (<= 32)", "lm_seg<16,4> (<= 64)",
               "lm_seg<32,4> (<= 128)", "lm_seg<32,8> (<= 256)", "lm_cta<128,4> (<= 512)",
               "lm_cta<256,4> (<= 1024)", "lm_cta<512,4> (<= 2048)", "lm_cta<512,8> (<= 4096)",
