@@ -80,3 +80,15 @@ def test_create_rejects_bad_configurations_before_touching_the_device(libdcd):
         setattr(cfg, field, 2)
         assert L.dcd_create(10, ctypes.byref(cfg), None, ctypes.byref(h)) == libdcd.DCD_EINVAL
         setattr(cfg, field, 0)
+
+
+def test_measurement_aids_reject_bad_arguments_before_touching_the_device(libdcd):
+    """dcd_reserve and dcd_eval_bins check their arguments on the host: a NULL
+    context or NULL outputs are refused with DCD_EINVAL, no CUDA call made."""
+    L = libdcd.lib()
+    assert L.dcd_reserve(None, 10, 10) == libdcd.DCD_EINVAL
+    nb = ctypes.c_int32(0)
+    buf = (ctypes.c_int64 * 12)()
+    var = (ctypes.c_int32 * 12)()
+    ms = (ctypes.c_float * 12)()
+    assert L.dcd_eval_bins(None, 1, ctypes.byref(nb), var, buf, buf, ms) == libdcd.DCD_EINVAL
